@@ -1,0 +1,6 @@
+"""CPU oracle for the complex CCSD iteration (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU legs of ``bench.py``
+(``cpu_baseline`` and ``--impl reference``) may import this package. It shares
+no code with the CUDA library and never imports it.
+"""

@@ -1,0 +1,119 @@
+"""Brute force in the N-electron determinant space: the pin for the CCSD oracle.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/ccsd_ref.py``).
+
+This module never uses the Appendix-A working equations. It builds the
+second-quantised Hamiltonian of Eq. Hamiltonian as an explicit matrix over all
+C(n, N) Slater determinants, forms the similarity-transformed Hamiltonian
+H_bar = exp(-T) H exp(T) of Eq. CCSD with explicit operator matrices for T1 and T2
+(Eq. t_amp, with the 1/4 normalisation of T2), and projects on the reference, the
+singles and the doubles. It also diagonalises H (full CI).
+
+Conventions: spinors 0..n-1 with the N = o lowest occupied in the reference;
+a determinant is a sorted tuple of occupied spinors; a+_p acting on a determinant
+carries the sign (-1)^(number of occupied spinors with index < p).
+E_pq = a+_p a_q; a+_p a+_q a_s a_r = E_pr E_qs - delta_qr E_ps.
+"""
+from __future__ import annotations
+
+import itertools
+import math
+
+import numpy as np
+
+
+def determinants(n: int, nel: int):
+    dets = [tuple(c) for c in itertools.combinations(range(n), nel)]
+    return dets, {d: k for k, d in enumerate(dets)}
+
+
+def excitation_matrices(n: int, nel: int) -> np.ndarray:
+    """E[p, q] = matrix of a+_p a_q in the determinant basis, shape (n, n, d, d)."""
+    dets, index = determinants(n, nel)
+    d = len(dets)
+    E = np.zeros((n, n, d, d))
+    for col, det in enumerate(dets):
+        occ = set(det)
+        for q in det:
+            s1 = sum(1 for x in det if x < q)  # sign of a_q
+            rem = occ - {q}
+            for p in range(n):
+                if p in rem:
+                    continue
+                s2 = sum(1 for x in rem if x < p)  # sign of a+_p
+                new = tuple(sorted(rem | {p}))
+                E[p, q, index[new], col] += (-1) ** (s1 + s2)
+    return E
+
+
+def hamiltonian(h: np.ndarray, V: np.ndarray, E: np.ndarray) -> np.ndarray:
+    """H = sum_pq h_pq E_pq + 1/4 sum_pqrs <pq||rs> (E_pr E_qs - delta_qr E_ps)."""
+    H = np.einsum("pq,pqxy->xy", h, E)
+    M = np.einsum("pqrs,prxz->qsxz", V, E, optimize=True)
+    H = H + 0.25 * np.einsum("qsxz,qszy->xy", M, E, optimize=True)
+    H = H - 0.25 * np.einsum("pqqs,psxy->xy", V, E, optimize=True)
+    return H
+
+
+def core_hamiltonian(f: np.ndarray, V: np.ndarray, o: int) -> np.ndarray:
+    """h_pq = f_pq - sum_k <pk||qk>: the one-body part that yields Fock matrix f."""
+    return f - np.einsum("pkqk->pq", V[:, :o, :, :o])
+
+
+class Space:
+    """Determinant space of an o-electron system in n = o + v spinors."""
+
+    def __init__(self, o: int, v: int):
+        self.o, self.v, self.n = o, v, o + v
+        self.E = excitation_matrices(self.n, o)
+        self.dets, self.index = determinants(self.n, o)
+        self.ref = np.zeros(len(self.dets))
+        self.ref[self.index[tuple(range(o))]] = 1.0
+
+    def cluster_operator(self, t1: np.ndarray, t2: np.ndarray) -> np.ndarray:
+        """T = sum_ia t^a_i E_ai + 1/4 sum_ijab t^{ab}_{ij} E_ai E_bj."""
+        o = self.o
+        Evo = self.E[o:, :o]  # E[a, i] = a+_a a_i
+        T1 = np.einsum("ia,aixy->xy", t1, Evo)
+        P = np.einsum("ijab,aixz->jbxz", t2, Evo, optimize=True)
+        T2 = 0.25 * np.einsum("jbxz,bjzy->xy", P, Evo, optimize=True)
+        return T1 + T2
+
+    def expm_nilpotent(self, T: np.ndarray) -> np.ndarray:
+        """exp(T) = sum_k T^k / k!, exact because T raises the excitation level."""
+        out = np.eye(T.shape[0], dtype=np.complex128)
+        term = np.eye(T.shape[0], dtype=np.complex128)
+        for k in range(1, self.o + 2):
+            term = term @ T / k
+            out = out + term
+        assert not np.any(term @ T), "T is not nilpotent at order o + 1"
+        return out
+
+    def projections(self, f: np.ndarray, V: np.ndarray, t1: np.ndarray, t2: np.ndarray):
+        """(E_ref, <0|H_bar|0>, <ia|H_bar|0>, <ijab|H_bar|0>) with |ijab> = E_ai E_bj |0>."""
+        o, v = self.o, self.v
+        h = core_hamiltonian(f, V, o)
+        H = hamiltonian(h, V, self.E)
+        T = self.cluster_operator(t1, t2)
+        ket = self.expm_nilpotent(-T) @ (H @ (self.expm_nilpotent(T) @ self.ref))
+        e_ref = self.ref @ H @ self.ref
+        e_cc = self.ref @ ket
+        Evo = self.E[o:, :o]
+        singles = np.einsum("aixy,y->iax", Evo, self.ref)  # |ia> vectors
+        S1 = np.einsum("iax,x->ia", singles, ket)
+        doubles = np.einsum("aixz,bjzy,y->ijabx", Evo, Evo, self.ref, optimize=True)
+        S2 = np.einsum("ijabx,x->ijab", doubles, ket, optimize=True)
+        return e_ref, e_cc, S1, S2
+
+    def fci(self, f: np.ndarray, V: np.ndarray):
+        """Full CI: (E_ref, eigenvalue of the state with the largest reference weight)."""
+        h = core_hamiltonian(f, V, self.o)
+        H = hamiltonian(h, V, self.E)
+        assert np.allclose(H, H.conj().T, atol=1e-12)
+        w, U = np.linalg.eigh(H)
+        k = int(np.argmax(np.abs(self.ref @ U)))
+        return float(np.real(self.ref @ H @ self.ref)), float(w[k])
+
+
+def n_determinants(o: int, v: int) -> int:
+    return math.comb(o + v, o)

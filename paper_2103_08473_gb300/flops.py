@@ -1,0 +1,34 @@
+"""Operation counts used for throughput reporting.
+
+The paper's cost metric for a CCSD run is C = O^2 V^4 (O correlated occupied,
+V correlated virtual spinors), the count of its costliest contraction, the
+particle-particle ladder (Sec. "Uranyl tris-nitrate", definition of C).
+
+Throughput is reported with 8 real flops per complex multiply-add (4M count).
+The ladder's algorithmic count uses the antisymmetry-packed sums
+(sum over c<d, i<j, a<b), the dense count 8 O^2 V^4 is reported beside it.
+"""
+
+
+def cost_metric(o: int, v: int) -> int:
+    """C = O^2 V^4."""
+    return o * o * v ** 4
+
+
+def pairs(n: int) -> int:
+    return n * (n - 1) // 2
+
+
+def ladder_flops_packed(o: int, v: int) -> int:
+    """8 [o(o-1)/2] [v(v-1)/2]^2: complex GEMM (ij pairs) x (cd pairs) x (ab pairs)."""
+    return 8 * pairs(o) * pairs(v) ** 2
+
+
+def ladder_flops_dense(o: int, v: int) -> int:
+    """8 o^2 v^4 (= 8 C)."""
+    return 8 * cost_metric(o, v)
+
+
+def ring_flops(o: int, v: int) -> int:
+    """8 (ov)^3: the ring GEMM (ai) x (ck) x (bj)."""
+    return 8 * (o * v) ** 3
