@@ -1,0 +1,160 @@
+/*
+ * ccsd.h - C ABI of libccsd, a single-GPU (sm_103a) engine for the per-iteration
+ * amplitude residual of Kramers-unrestricted complex CCSD.
+ *
+ * The problem statement follows the paper (arXiv:2103.08473):
+ *   - Hamiltonian with complex one-body part and antisymmetrised two-electron
+ *     integrals V^{pq}_{rs} = <pq||rs> (Eq. Hamiltonian, Eq. two_electron);
+ *   - CCSD amplitude equations <Phi_l| exp(-T) H exp(T) |Phi_0> = 0 (Eq. CCSD)
+ *     evaluated with the working equations of Appendix A;
+ *   - MP2 initial guess, denominator ("Jacobi") update and DIIS
+ *     (Sec. "Coupled cluster implementation");
+ *   - all tensors are created before iterating (same section).
+ *
+ * Conventions shared by every call
+ *   - Complex numbers are interleaved (re, im) doubles: ccsd_z is layout-
+ *     compatible with C99 double _Complex, std::complex<double>,
+ *     cuDoubleComplex and numpy complex128.
+ *   - Spinors are ordered occupied first: p in [0, o) occupied, [o, o+v) virtual.
+ *   - t1 / r1:  [i][a], row-major, o*v elements, t1[i*v + a] = t^a_i.
+ *   - t2 / r2:  [i][j][a][b], row-major, o*o*v*v elements, full storage of
+ *               t^{ab}_{ij}, antisymmetric in (i,j) and in (a,b). Packing by
+ *               antisymmetry is internal.
+ *   - Density-fitting factors B: [Q][p][r], naux*n*n elements, Hermitian in
+ *     (p, r); (pr|qs) = sum_Q B^Q_pr B^Q_qs and <pq||rs> = (pr|qs) - (ps|qr).
+ *   - Full integrals V: [p][q][r][s], n^4 elements, V[p][q][r][s] = <pq||rs>.
+ *   - Fock: n*n Hermitian, [p][q] = f_pq; NULL means diag(eps).
+ *
+ * Ownership: ccsd_create copies every input; the caller keeps its buffers.
+ * Output buffers belong to the caller. With on_device != 0, pointers are device
+ * pointers on the context's device; otherwise host pointers (pageable or
+ * pinned). The context owns all device memory it allocates and frees it in
+ * ccsd_destroy.
+ *
+ * Errors: every call returns a ccsd_status; nothing throws across the ABI, and
+ * nothing calls exit/abort or traps on the device. ccsd_last_error() returns a
+ * human-readable message for the last failing call on that context. A context
+ * is not thread-safe: use one host thread per context at a time.
+ *
+ * Streams: all device work of a context is issued on opts.stream (a
+ * cudaStream_t; NULL = the legacy default stream). Calls that return host
+ * values synchronise that stream.
+ */
+#ifndef CCSD_H
+#define CCSD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ccsd_ctx ccsd_ctx;
+
+/* Interleaved complex double. */
+typedef struct {
+  double re, im;
+} ccsd_z;
+
+typedef enum {
+  CCSD_OK = 0,
+  CCSD_ERR_ARG = 1,           /* invalid argument (sizes, NULL pointers, non-Hermitian input) */
+  CCSD_ERR_OOM = 2,           /* device allocation failed */
+  CCSD_ERR_CUDA = 3,          /* a CUDA runtime call or kernel launch failed */
+  CCSD_ERR_NOT_CONVERGED = 4, /* iteration cap reached before the tolerance */
+  CCSD_ERR_DIVERGED = 5,      /* NaN/Inf in the update; amplitudes left at the last finite iterate */
+  CCSD_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up */
+  CCSD_ERR_UNSUPPORTED = 7    /* option combination not built */
+} ccsd_status;
+
+typedef enum {
+  CCSD_INT_DF = 0,  /* ints = B[naux][n][n] */
+  CCSD_INT_FULL = 1 /* ints = V[n][n][n][n] = <pq||rs> (small n only); naux ignored */
+} ccsd_int_kind;
+
+typedef enum {
+  CCSD_PREC_FP64 = 0, /* every contraction in complex FP64 */
+  CCSD_PREC_SPLIT = 1 /* large contractions as split-precision tensor-core GEMMs, FP64 recombination */
+} ccsd_precision;
+
+typedef struct {
+  int max_iter;       /* iteration cap for ccsd_iterate (default 50) */
+  double tol;         /* convergence threshold on the update norm (default 1e-10) */
+  int norm;           /* 0: max |S/D| (default), 1: 2-norm of S/D over unique amplitudes */
+  int diis_dim;       /* DIIS subspace size, 0 = off (default 8) */
+  int diis_start;     /* first iteration that extrapolates (default 2) */
+  double level_shift; /* added to virtual orbital energies in the denominators only (default 0) */
+  int precision;      /* ccsd_precision (default CCSD_PREC_FP64) */
+  int slices;         /* split precision: number of slices per operand (default 0 = automatic) */
+  int store_w;        /* 1: store <ab||cd> (packed); 0: rebuild ladder tiles from B (default 1) */
+  int profile;        /* 1: record per-term CUDA-event timings (default 0) */
+  void* stream;       /* cudaStream_t, NULL = legacy default stream */
+} ccsd_opts;
+
+/* Fill opts with the defaults listed above. */
+void ccsd_default_opts(ccsd_opts* opts);
+
+/*
+ * Create a context: copy eps (n doubles, host), the optional Fock matrix
+ * (n*n, host) and the integrals (host) to the device, build the integral
+ * blocks (oooo, ooov, oovv, vovo, vovv, and <ab||cd> packed over a<b, c<d),
+ * allocate every tensor of the iteration up front and set the amplitudes to the
+ * MP2 guess (one denominator update from t = 0).
+ * Errors: CCSD_ERR_ARG for o < 1, v < 1, naux < 1 (DF), NULL pointers, a Fock
+ * matrix or DF factor that is not Hermitian to 1e-12 relative; CCSD_ERR_OOM.
+ * On error *out is set to NULL.
+ */
+ccsd_status ccsd_create(int o, int v, const double* eps, const ccsd_z* fock, ccsd_int_kind kind,
+                        const ccsd_z* ints, int naux, const ccsd_opts* opts, ccsd_ctx** out);
+
+/*
+ * Residuals S^a_i, S^{ab}_{ij} of Appendix A at the given amplitudes
+ * (t1: o*v, t2: o*o*v*v; outputs r1, r2 of the same sizes). Does not change the
+ * context's current amplitudes. t1/t2 may be NULL to use the current ones.
+ */
+ccsd_status ccsd_residual(ccsd_ctx* ctx, const ccsd_z* t1, const ccsd_z* t2, ccsd_z* r1, ccsd_z* r2,
+                          int on_device);
+
+/*
+ * Run up to max_iter iterations from the current amplitudes (max_iter <= 0:
+ * opts.max_iter): residual, denominator update t <- t + S/D, DIIS, norm.
+ * Returns CCSD_OK on convergence (norm <= opts.tol), CCSD_ERR_NOT_CONVERGED at
+ * the cap, CCSD_ERR_DIVERGED on NaN/Inf. iters_done / res_norm may be NULL.
+ */
+ccsd_status ccsd_iterate(ccsd_ctx* ctx, int max_iter, int* iters_done, double* res_norm);
+
+/* Energy of the current amplitudes: sum_ia f_ia t^a_i + 1/4 sum <ij||ab> tau^{ab}_{ij}. */
+ccsd_status ccsd_energy(ccsd_ctx* ctx, ccsd_z* e);
+
+/* Copy the current amplitudes out / in (checkpoint and resume). Setting resets DIIS. */
+ccsd_status ccsd_get_amplitudes(ccsd_ctx* ctx, ccsd_z* t1, ccsd_z* t2, int on_device);
+ccsd_status ccsd_set_amplitudes(ccsd_ctx* ctx, const ccsd_z* t1, const ccsd_z* t2, int on_device);
+
+/*
+ * Copy an intermediate of the last residual evaluation to `out` (count complex
+ * elements expected). Names and layouts: "tau" [i][j][a][b], "Hvv" [a][c],
+ * "Gvv" [a][c], "Hoo" [k][i], "Goo" [k][i], "Hov" [k][c], "Hvoov" [i][a][k][c]
+ * (= H^{ak}_{ci}), "C" [k][b][i][j], "A" [k][l][i][j], "ladder" [i][j][a][b]
+ * (= 1/2 sum_cd <ab||cd> tau^{cd}_{ij}). CCSD_ERR_ARG for an unknown name or a
+ * wrong count.
+ */
+ccsd_status ccsd_get_tensor(ccsd_ctx* ctx, const char* name, ccsd_z* out, size_t count, int on_device);
+
+/*
+ * Per-term device timings of the last residual (opts.profile = 1): writes up to
+ * `cap` (name, milliseconds) pairs; *n receives the number of terms. Names are
+ * static strings owned by the library.
+ */
+ccsd_status ccsd_timings(ccsd_ctx* ctx, const char** names, double* ms, int cap, int* n);
+
+/* Message for the last failing call on ctx (or of the last failed create when ctx is NULL). */
+const char* ccsd_last_error(const ccsd_ctx* ctx);
+
+/* Free every device buffer of the context. NULL is a no-op. */
+void ccsd_destroy(ccsd_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CCSD_H */

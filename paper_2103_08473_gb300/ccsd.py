@@ -1,0 +1,234 @@
+"""ctypes binding of libccsd (include/ccsd.h): argument marshalling only.
+
+Every step of the CCSD iteration runs in the CUDA library; this module converts
+numpy arrays / torch CUDA tensors to pointers and status codes to exceptions.
+There is no CPU fallback: if libccsd.so is missing or cannot be loaded, every
+entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libccsd.so")
+
+STATUS = {0: "CCSD_OK", 1: "CCSD_ERR_ARG", 2: "CCSD_ERR_OOM", 3: "CCSD_ERR_CUDA", 4: "CCSD_ERR_NOT_CONVERGED",
+          5: "CCSD_ERR_DIVERGED", 6: "CCSD_ERR_TIMEOUT", 7: "CCSD_ERR_UNSUPPORTED"}
+OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NOT_CONVERGED, ERR_DIVERGED, ERR_TIMEOUT, ERR_UNSUPPORTED = range(8)
+INT_DF, INT_FULL = 0, 1
+PREC_FP64, PREC_SPLIT = 0, 1
+
+
+class ccsd_z(C.Structure):
+    _fields_ = [("re", C.c_double), ("im", C.c_double)]
+
+
+class ccsd_opts(C.Structure):
+    _fields_ = [("max_iter", C.c_int), ("tol", C.c_double), ("norm", C.c_int), ("diis_dim", C.c_int),
+                ("diis_start", C.c_int), ("level_shift", C.c_double), ("precision", C.c_int),
+                ("slices", C.c_int), ("store_w", C.c_int), ("profile", C.c_int), ("stream", C.c_void_p)]
+
+
+class CCSDError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+# (name, restype, argtypes) of every entry point declared in include/ccsd.h
+_P = C.c_void_p
+SIGNATURES = [
+    ("ccsd_default_opts", None, [C.POINTER(ccsd_opts)]),
+    ("ccsd_create", C.c_int, [C.c_int, C.c_int, _P, _P, C.c_int, _P, C.c_int, C.POINTER(ccsd_opts), C.POINTER(_P)]),
+    ("ccsd_residual", C.c_int, [_P, _P, _P, _P, _P, C.c_int]),
+    ("ccsd_iterate", C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    ("ccsd_energy", C.c_int, [_P, C.POINTER(ccsd_z)]),
+    ("ccsd_get_amplitudes", C.c_int, [_P, _P, _P, C.c_int]),
+    ("ccsd_set_amplitudes", C.c_int, [_P, _P, _P, C.c_int]),
+    ("ccsd_get_tensor", C.c_int, [_P, C.c_char_p, _P, C.c_size_t, C.c_int]),
+    ("ccsd_timings", C.c_int, [_P, C.POINTER(C.c_char_p), C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int)]),
+    ("ccsd_last_error", C.c_char_p, [_P]),
+    ("ccsd_destroy", None, [_P]),
+]
+
+
+def load(path: str | None = None):
+    """Load libccsd.so (raises OSError if it is missing: there is no fallback).
+
+    With no argument the in-tree library is loaded once and cached; an explicit
+    path is always loaded afresh.
+    """
+    global _lib
+    if path is None and _lib is not None:
+        return _lib
+    target = LIB_PATH if path is None else path
+    if not os.path.exists(target):
+        raise OSError(f"libccsd.so not found at {target}; run __graft_entry__.build() first")
+    lib = C.CDLL(target)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None or os.path.abspath(target) == LIB_PATH:
+        _lib = lib
+    return lib
+
+
+def default_opts(**kw) -> ccsd_opts:
+    lib = load()
+    o = ccsd_opts()
+    lib.ccsd_default_opts(C.byref(o))
+    for k, v in kw.items():
+        if k == "stream":
+            o.stream = C.c_void_p(v if isinstance(v, int) else getattr(v, "cuda_stream", 0))
+        else:
+            setattr(o, k, v)
+    return o
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, dtype=np.complex128):
+    """(pointer, on_device, keepalive) of a numpy array or torch CUDA tensor."""
+    if x is None:
+        return None, 0, None
+    if _is_torch(x):
+        if not x.is_cuda or not x.is_contiguous():
+            raise ValueError("torch tensors must be contiguous CUDA tensors")
+        return C.c_void_p(x.data_ptr()), 1, x
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a.ctypes.data_as(C.c_void_p), 0, a
+
+
+class CCSD:
+    """One CCSD problem on the GPU (wraps a ccsd_ctx)."""
+
+    def __init__(self, o, v, eps, B=None, V=None, fock=None, **opts):
+        lib = load()
+        self.o, self.v = int(o), int(v)
+        self.n = self.o + self.v
+        self._opts = default_opts(**opts)
+        eps_a = np.ascontiguousarray(eps, dtype=np.float64)
+        if eps_a.shape != (self.n,):
+            raise ValueError("eps must have o + v entries")
+        if (B is None) == (V is None):
+            raise ValueError("give exactly one of B (DF factors) or V (full integrals)")
+        if B is not None:
+            ints = np.ascontiguousarray(B, dtype=np.complex128)
+            kind, naux = INT_DF, ints.shape[0]
+            if ints.shape != (naux, self.n, self.n):
+                raise ValueError("B must be (naux, n, n)")
+        else:
+            ints = np.ascontiguousarray(V, dtype=np.complex128)
+            kind, naux = INT_FULL, 0
+            if ints.shape != (self.n,) * 4:
+                raise ValueError("V must be (n, n, n, n)")
+        fk = None if fock is None else np.ascontiguousarray(fock, dtype=np.complex128)
+        h = C.c_void_p()
+        st = lib.ccsd_create(self.o, self.v, eps_a.ctypes.data_as(C.c_void_p),
+                             None if fk is None else fk.ctypes.data_as(C.c_void_p), kind,
+                             ints.ctypes.data_as(C.c_void_p), naux, C.byref(self._opts), C.byref(h))
+        if st != OK:
+            raise CCSDError(st, lib.ccsd_last_error(None).decode())
+        self._h = h
+        self._lib = lib
+
+    # -- helpers
+    def _check(self, st, allow=()):
+        if st != OK and st not in allow:
+            raise CCSDError(st, self._lib.ccsd_last_error(self._h).decode())
+        return st
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.ccsd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def shapes(self):
+        return (self.o, self.v), (self.o, self.o, self.v, self.v)
+
+    # -- ABI calls
+    def residual(self, t1=None, t2=None, out=None):
+        """(S1, S2) of Appendix A at (t1, t2) (numpy -> numpy, torch CUDA -> torch CUDA)."""
+        s1, s2 = self.shapes
+        dev = t1 is not None and _is_torch(t1)
+        if out is None:
+            if dev:
+                import torch
+                out = (torch.empty(s1, dtype=torch.complex128, device=t1.device),
+                       torch.empty(s2, dtype=torch.complex128, device=t1.device))
+            else:
+                out = (np.empty(s1, np.complex128), np.empty(s2, np.complex128))
+        p1, d1, k1 = _ptr(t1)
+        p2, d2, k2 = _ptr(t2)
+        q1, e1, _ = _ptr(out[0]) if _is_torch(out[0]) else (out[0].ctypes.data_as(C.c_void_p), 0, None)
+        q2, e2, _ = _ptr(out[1]) if _is_torch(out[1]) else (out[1].ctypes.data_as(C.c_void_p), 0, None)
+        on_dev = 1 if (d1 or e1) else 0
+        if t1 is not None and (d1 != e1 or d2 != e2 or d1 != d2):
+            raise ValueError("inputs and outputs must all be host arrays or all CUDA tensors")
+        self._check(self._lib.ccsd_residual(self._h, p1, p2, q1, q2, on_dev))
+        return out
+
+    def iterate(self, max_iter=0):
+        """Run iterations; returns (status, iterations, norm). Raises on CUDA/arg errors."""
+        it = C.c_int(0)
+        nrm = C.c_double(0.0)
+        st = self._lib.ccsd_iterate(self._h, int(max_iter), C.byref(it), C.byref(nrm))
+        self._check(st, allow=(ERR_NOT_CONVERGED, ERR_DIVERGED))
+        return st, it.value, nrm.value
+
+    def energy(self) -> complex:
+        e = ccsd_z()
+        self._check(self._lib.ccsd_energy(self._h, C.byref(e)))
+        return complex(e.re, e.im)
+
+    def get_amplitudes(self, out=None):
+        s1, s2 = self.shapes
+        if out is None:
+            out = (np.empty(s1, np.complex128), np.empty(s2, np.complex128))
+        p1, d1, _ = _ptr(out[0]) if _is_torch(out[0]) else (out[0].ctypes.data_as(C.c_void_p), 0, None)
+        p2, d2, _ = _ptr(out[1]) if _is_torch(out[1]) else (out[1].ctypes.data_as(C.c_void_p), 0, None)
+        self._check(self._lib.ccsd_get_amplitudes(self._h, p1, p2, d1))
+        return out
+
+    def set_amplitudes(self, t1, t2):
+        p1, d1, k1 = _ptr(t1)
+        p2, d2, k2 = _ptr(t2)
+        self._check(self._lib.ccsd_set_amplitudes(self._h, p1, p2, d1))
+
+    def get_tensor(self, name):
+        o, v = self.o, self.v
+        shapes = {"tau": (o, o, v, v), "Hvv": (v, v), "Gvv": (v, v), "Hoo": (o, o), "Goo": (o, o),
+                  "Hov": (o, v), "Hvoov": (o, v, o, v), "C": (o, v, o, o), "A": (o, o, o, o),
+                  "ladder": (o, o, v, v)}
+        out = np.empty(shapes[name], np.complex128)
+        self._check(self._lib.ccsd_get_tensor(self._h, name.encode(), out.ctypes.data_as(C.c_void_p), out.size, 0))
+        return out
+
+    def timings(self):
+        n = C.c_int(0)
+        self._check(self._lib.ccsd_timings(self._h, None, None, 0, C.byref(n)))
+        names = (C.c_char_p * n.value)()
+        ms = (C.c_double * n.value)()
+        self._check(self._lib.ccsd_timings(self._h, names, ms, n.value, C.byref(n)))
+        return [(names[k].decode(), ms[k]) for k in range(n.value)]

@@ -1,0 +1,935 @@
+// C ABI of libccsd (include/ccsd.h): context creation, the Appendix A residual
+// plan, the denominator update + DIIS iteration (CUDA-graph replayed), energy,
+// amplitude checkpointing and inspection.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ccsd.h"
+#include "ops.h"
+#include "plan.h"
+#include "zgemm.h"
+
+using namespace ccsd;
+
+namespace {
+thread_local std::string g_create_error;
+
+const char* kIntermediates[] = {"tau", "Hvv", "Gvv", "Hoo", "Goo", "Hov", "Hvoov", "C", "A", "ladder"};
+}  // namespace
+
+struct ccsd_ctx {
+  int o = 0, v = 0, n = 0, naux = 0;
+  int64_t Po = 0, Pv = 0;
+  ccsd_opts opts{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  std::vector<void*> allocs;
+
+  // constants
+  double* dvec = nullptr;  // real diagonal of the Fock matrix (n)
+  z *foo = nullptr, *fov = nullptr, *fvv = nullptr;
+  z *oooo = nullptr, *ooov = nullptr, *oovv = nullptr, *vovo = nullptr, *vovv = nullptr;
+  z *Wpk = nullptr, *vovv_pk = nullptr, *oovv_pk = nullptr, *J = nullptr, *Cinit = nullptr;
+  // amplitudes and residual
+  z *t1 = nullptr, *t2 = nullptr, *S1 = nullptr, *S2 = nullptr;
+  z *t1_prev = nullptr, *t2_prev = nullptr, *t1_save = nullptr, *t2_save = nullptr;
+  // intermediates
+  z *tau = nullptr, *tau_pk = nullptr, *X = nullptr;
+  z *Hvv = nullptr, *Gvv = nullptr, *Hoo = nullptr, *Goo = nullptr, *Hov = nullptr, *Yov = nullptr, *Zoo = nullptr;
+  z *Hr = nullptr, *R = nullptr, *W1 = nullptr;
+  z *C = nullptr, *Yovoo = nullptr, *Ypk = nullptr, *Yfull = nullptr;
+  z *Afull = nullptr, *Yoooo = nullptr, *Apk = nullptr, *Lpk = nullptr, *Hpk = nullptr;
+  z* scratch = nullptr;
+  // iteration state
+  double* upd_partials = nullptr;
+  double* stats = nullptr;
+  double* stats_host = nullptr;  // pinned
+  z* e_partials = nullptr;
+  z* e_dev = nullptr;
+  z* e_host = nullptr;  // pinned
+  DiisArgs diis;
+  Plan* plan = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  // profiling
+  std::vector<std::string> tnames;
+  std::vector<double> tms;
+};
+
+namespace {
+
+ccsd_status set_err(ccsd_ctx* c, ccsd_status st, const std::string& msg) {
+  if (c) c->err = msg;
+  else g_create_error = msg;
+  return st;
+}
+
+#define CK(call)                                                                                     \
+  do {                                                                                               \
+    cudaError_t e_ = (call);                                                                         \
+    if (e_ != cudaSuccess)                                                                           \
+      return set_err(ctx, e_ == cudaErrorMemoryAllocation ? CCSD_ERR_OOM : CCSD_ERR_CUDA,            \
+                     std::string(#call) + ": " + cudaGetErrorString(e_));                            \
+  } while (0)
+
+template <typename Tp>
+ccsd_status dalloc(ccsd_ctx* ctx, Tp** p, int64_t count) {
+  void* m = nullptr;
+  size_t bytes = (size_t)std::max<int64_t>(count, 1) * sizeof(Tp);
+  cudaError_t e = cudaMalloc(&m, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(ctx, CCSD_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+  }
+  ctx->allocs.push_back(m);
+  *p = (Tp*)m;
+  return CCSD_OK;
+}
+
+#define CS(call)                        \
+  do {                                  \
+    ccsd_status s_ = (call);            \
+    if (s_ != CCSD_OK) return s_;       \
+  } while (0)
+
+// out[d0][d1][d2][d3] (+)= alpha * in[...] where output dim d is input dim perm[d].
+cudaError_t permute4(const z* in, const int64_t idims[4], const int perm[4], z* out, z alpha, double beta, int conj,
+                     cudaStream_t s) {
+  PermuteArgs a;
+  a.rank = 4;
+  int64_t ist[4];
+  ist[3] = 1;
+  for (int k = 2; k >= 0; --k) ist[k] = ist[k + 1] * idims[k + 1];
+  int64_t od[4];
+  for (int d = 0; d < 4; ++d) od[d] = idims[perm[d]];
+  int64_t ost[4];
+  ost[3] = 1;
+  for (int k = 2; k >= 0; --k) ost[k] = ost[k + 1] * od[k + 1];
+  for (int d = 0; d < 4; ++d) {
+    a.dims[d] = od[d];
+    a.istr[d] = ist[perm[d]];
+    a.ostr[d] = ost[d];
+  }
+  a.in = in;
+  a.out = out;
+  a.alpha = alpha;
+  a.beta = beta;
+  a.conj = conj;
+  return permute_add(a, s);
+}
+
+// Space ranges: 'o' = [0, o), 'v' = [o, n).
+void space(const ccsd_ctx* c, char s, int64_t& off, int64_t& len) {
+  off = s == 'o' ? 0 : c->o;
+  len = s == 'o' ? c->o : c->v;
+}
+
+// Extract B[Q][P-range][R-range] into a contiguous [naux][np][nr] buffer.
+cudaError_t extract_B(const ccsd_ctx* c, const z* B, char P, char Rs, z* out, cudaStream_t s) {
+  int64_t p0, np, r0, nr;
+  space(c, P, p0, np);
+  space(c, Rs, r0, nr);
+  PermuteArgs a;
+  a.rank = 3;
+  a.dims[0] = c->naux;
+  a.dims[1] = np;
+  a.dims[2] = nr;
+  a.istr[0] = (int64_t)c->n * c->n;
+  a.istr[1] = c->n;
+  a.istr[2] = 1;
+  a.ostr[0] = np * nr;
+  a.ostr[1] = nr;
+  a.ostr[2] = 1;
+  a.in = B + p0 * c->n + r0;
+  a.out = out;
+  return permute_add(a, s);
+}
+
+// Coulomb block D[(p,r)][(q,s)] = sum_Q B^Q_pr B^Q_qs for spaces (P,R) x (Q,S).
+ccsd_status coulomb_df(ccsd_ctx* ctx, const z* B, char P, char Rr, char Q, char S, z* D, z* tmp1, z* tmp2) {
+  int64_t po, np, ro, nr, qo, nq, so, ns;
+  space(ctx, P, po, np);
+  space(ctx, Rr, ro, nr);
+  space(ctx, Q, qo, nq);
+  space(ctx, S, so, ns);
+  CK(extract_B(ctx, B, P, Rr, tmp1, ctx->stream));
+  CK(extract_B(ctx, B, Q, S, tmp2, ctx->stream));
+  ZGemmArgs g;
+  g.M = np * nr;
+  g.N = nq * ns;
+  g.K = ctx->naux;
+  g.A = tmp1;
+  g.lda = g.M;
+  g.transA = 1;
+  g.B = tmp2;
+  g.ldb = g.N;
+  g.C = D;
+  g.ldc = g.N;
+  CK(zgemm_f64(g, ctx->stream));
+  return CCSD_OK;
+}
+
+// <pq||rs> block for spaces "PQRS" from the DF factors, written as out[p][q][r][s].
+ccsd_status build_block_df(ccsd_ctx* ctx, const z* B, const char* sp, z* out) {
+  int64_t o_, np, nq, nr, ns;
+  space(ctx, sp[0], o_, np);
+  space(ctx, sp[1], o_, nq);
+  space(ctx, sp[2], o_, nr);
+  space(ctx, sp[3], o_, ns);
+  const int64_t nb = (int64_t)ctx->naux * ctx->n * ctx->n;
+  z *t1 = nullptr, *t2 = nullptr, *D = nullptr;
+  std::vector<void*> mine;
+  auto cleanup = [&]() {
+    for (void* p : mine) cudaFree(p);
+  };
+  auto get = [&](z** p, int64_t cnt) -> bool {
+    void* m = nullptr;
+    if (cudaMalloc(&m, (size_t)std::max<int64_t>(cnt, 1) * sizeof(z)) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    mine.push_back(m);
+    *p = (z*)m;
+    return true;
+  };
+  if (!get(&t1, nb) || !get(&t2, nb) || !get(&D, np * nr * nq * ns)) {
+    cleanup();
+    return set_err(ctx, CCSD_ERR_OOM, "integral build temporaries");
+  }
+  ccsd_status st = coulomb_df(ctx, B, sp[0], sp[2], sp[1], sp[3], D, t1, t2);
+  if (st != CCSD_OK) { cleanup(); return st; }
+  // direct part: out[p][q][r][s] = D[p][r][q][s]
+  {
+    const int64_t idims[4] = {np, nr, nq, ns};
+    const int perm[4] = {0, 2, 1, 3};
+    cudaError_t e = permute4(D, idims, perm, out, zmake(1, 0), 0.0, 0, ctx->stream);
+    if (e != cudaSuccess) { cleanup(); return set_err(ctx, CCSD_ERR_CUDA, cudaGetErrorString(e)); }
+  }
+  // exchange part: out[p][q][r][s] -= X[p][s][q][r], X = (ps|qr)
+  if (sp[2] != sp[3]) {
+    st = coulomb_df(ctx, B, sp[0], sp[3], sp[1], sp[2], D, t1, t2);
+    if (st != CCSD_OK) { cleanup(); return st; }
+  }
+  {
+    const int64_t idims[4] = {np, ns, nq, nr};  // X[p][s][q][r]
+    const int perm[4] = {0, 2, 3, 1};           // out dims (p, q, r, s) <- X dims (0, 2, 3, 1)
+    cudaError_t e = permute4(D, idims, perm, out, zmake(-1, 0), 1.0, 0, ctx->stream);
+    if (e != cudaSuccess) { cleanup(); return set_err(ctx, CCSD_ERR_CUDA, cudaGetErrorString(e)); }
+  }
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  cleanup();
+  if (e != cudaSuccess) return set_err(ctx, CCSD_ERR_CUDA, cudaGetErrorString(e));
+  return CCSD_OK;
+}
+
+// W[P(a,b)][P(c,d)] = <ab||cd> packed, from the DF factors (dense (ac|bd) as a temporary).
+ccsd_status build_w_df(ccsd_ctx* ctx, const z* B) {
+  const int64_t v = ctx->v;
+  const int64_t nb = (int64_t)ctx->naux * v * v;
+  void *m1 = nullptr, *m2 = nullptr, *mD = nullptr;
+  if (cudaMalloc(&m1, nb * sizeof(z)) != cudaSuccess || cudaMalloc(&m2, nb * sizeof(z)) != cudaSuccess ||
+      cudaMalloc(&mD, v * v * v * v * sizeof(z)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(m1);
+    cudaFree(m2);
+    cudaFree(mD);
+    return set_err(ctx, CCSD_ERR_OOM, "vvvv build temporaries");
+  }
+  ccsd_status st = coulomb_df(ctx, B, 'v', 'v', 'v', 'v', (z*)mD, (z*)m1, (z*)m2);
+  if (st == CCSD_OK) {
+    cudaError_t e = pack_vvvv((z*)mD, ctx->Wpk, v, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) st = set_err(ctx, CCSD_ERR_CUDA, cudaGetErrorString(e));
+  }
+  cudaFree(m1);
+  cudaFree(m2);
+  cudaFree(mD);
+  return st;
+}
+
+// Block of the full integral tensor V[n][n][n][n] for spaces "PQRS".
+ccsd_status build_block_full(ccsd_ctx* ctx, const z* V, const char* sp, z* out) {
+  const int64_t n = ctx->n;
+  int64_t off[4], len[4];
+  for (int k = 0; k < 4; ++k) space(ctx, sp[k], off[k], len[k]);
+  PermuteArgs a;
+  a.rank = 4;
+  const int64_t st[4] = {n * n * n, n * n, n, 1};
+  int64_t ost = 1;
+  for (int k = 3; k >= 0; --k) {
+    a.dims[k] = len[k];
+    a.istr[k] = st[k];
+    a.ostr[k] = ost;
+    ost *= len[k];
+  }
+  a.in = V + off[0] * st[0] + off[1] * st[1] + off[2] * st[2] + off[3];
+  a.out = out;
+  CK(permute_add(a, ctx->stream));
+  return CCSD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// The residual plan: Appendix A, one contraction per printed term.
+// Labels i,j,k,l run over occupied and a,b,c,d over virtual spinors.
+// ---------------------------------------------------------------------------
+ccsd_status build_residual_plan(ccsd_ctx* ctx) {
+  const int o = ctx->o, v = ctx->v;
+  const int64_t Po = ctx->Po, Pv = ctx->Pv;
+  Plan* P = new Plan(o, v, &ctx->scratch, ctx->stream);
+  ctx->plan = P;
+  P->set_gemm([](const ZGemmArgs& g, cudaStream_t s) { return zgemm_f64(g, s); });
+  const z one = zmake(1, 0), mone = zmake(-1, 0), half = zmake(0.5, 0);
+  auto V = [&](z* p, const char* lab) { return P->view(p, lab, true); };
+  auto W = [&](z* p, const char* lab) { return P->view(p, lab, false); };
+
+  // tau^{ab}_{ij} = t^{ab}_{ij} + P^-_ij (t^a_i t^b_j), and its (i<j, c<d) packed copy
+  z *t1 = ctx->t1, *t2 = ctx->t2, *tau = ctx->tau, *taupk = ctx->tau_pk, *X = ctx->X;
+  P->custom("tau", [=](cudaStream_t s) {
+    cudaError_t e = tau_build(t1, t2, tau, o, v, 1.0, 1.0, 1, s);
+    if (e != cudaSuccess) return e;
+    return pack_pairs(tau, taupk, o, v, 1, s);
+  });
+  // X^{ad}_{li} = 1/2 t^{ad}_{li} + t^a_l t^d_i (the pair amplitude of the H^{ak}_{ci} term)
+  P->custom("Hvoov", [=](cudaStream_t s) { return tau_build(t1, t2, X, o, v, 0.5, 1.0, 0, s); });
+
+  // H^a_c = F^a_c + 1/2 sum_kld V^{kl}_{cd} tau^{da}_{kl}
+  P->add("Hvv", W(ctx->Hvv, "ac"), one, V(ctx->fvv, "ac"), false, 0.0);
+  P->contract("Hvv", W(ctx->Hvv, "ac"), half, V(ctx->oovv, "klcd"), false, W(tau, "klda"), false, 1.0);
+  // G^a_c = H^a_c + sum_kd V^{ak}_{cd} t^d_k - sum_k F^k_c t^a_k
+  P->add("Gvv", W(ctx->Gvv, "ac"), one, W(ctx->Hvv, "ac"), false, 0.0);
+  P->contract("Gvv", W(ctx->Gvv, "ac"), one, V(ctx->vovv, "akcd"), false, W(t1, "kd"), false, 1.0);
+  P->contract("Gvv", W(ctx->Gvv, "ac"), mone, V(ctx->fov, "kc"), false, W(t1, "ka"), false, 1.0);
+  // H^k_i = -F^k_i + 1/2 sum_lcd V^{kl}_{cd} tau^{cd}_{li}
+  P->add("Hoo", W(ctx->Hoo, "ki"), mone, V(ctx->foo, "ki"), false, 0.0);
+  P->contract("Hoo", W(ctx->Hoo, "ki"), half, V(ctx->oovv, "klcd"), false, W(tau, "licd"), false, 1.0);
+  // G^k_i = H^k_i - sum_lc V^{kl}_{ic} t^c_l - sum_c F^k_c t^c_i
+  P->add("Goo", W(ctx->Goo, "ki"), one, W(ctx->Hoo, "ki"), false, 0.0);
+  P->contract("Goo", W(ctx->Goo, "ki"), mone, V(ctx->ooov, "klic"), false, W(t1, "lc"), false, 1.0);
+  P->contract("Goo", W(ctx->Goo, "ki"), mone, V(ctx->fov, "kc"), false, W(t1, "ic"), false, 1.0);
+  // H^k_c = F^k_c + sum_ld V^{kl}_{cd} t^d_l
+  P->add("Hov", W(ctx->Hov, "kc"), one, V(ctx->fov, "kc"), false, 0.0);
+  P->contract("Hov", W(ctx->Hov, "kc"), one, V(ctx->oovv, "klcd"), false, W(t1, "ld"), false, 1.0);
+  // H^{ak}_{ci} (stored [i][a][k][c]) = V^{ak}_{ci} + sum_d V^{ak}_{cd} t^d_i - sum_l V^{kl}_{ic} t^a_l
+  //                                   + sum_ld V^{kl}_{cd} (1/2 t^{ad}_{li} + t^a_l t^d_i)
+  P->add("Hvoov", W(ctx->Hr, "iakc"), one, V(ctx->J, "iakc"), false, 0.0);
+  P->contract("Hvoov", W(ctx->Hr, "iakc"), one, V(ctx->vovv, "akcd"), false, W(t1, "id"), false, 1.0);
+  P->contract("Hvoov", W(ctx->Hr, "iakc"), mone, V(ctx->ooov, "klic"), false, W(t1, "la"), false, 1.0);
+  P->contract("Hvoov", W(ctx->Hr, "iakc"), one, W(X, "liad"), false, V(ctx->oovv, "klcd"), false, 1.0);
+  // C^{kb}_{ij} = V^{ij+}_{kb} + P^-_ij sum_c V^{bk}_{ci} t^c_j - 1/2 sum_cd V^{bk}_{cd} tau^{cd}_{ij}
+  P->add("C", W(ctx->C, "kbij"), one, V(ctx->Cinit, "kbij"), false, 0.0);
+  P->contract("C", W(ctx->Yovoo, "kbij"), one, V(ctx->vovo, "bkci"), false, W(t1, "jc"), false, 0.0);
+  P->add("C", W(ctx->C, "kbij"), one, W(ctx->Yovoo, "kbij"), false, 1.0);
+  P->add("C", W(ctx->C, "kbij"), mone, W(ctx->Yovoo, "kbji"), false, 1.0);
+  {
+    ZGemmArgs g;  // Ypk[(b,k)][P(ij)] = sum_{c<d} V^{bk}_{cd} tau^{cd}_{ij}
+    g.M = (int64_t)v * o;
+    g.N = Po;
+    g.K = Pv;
+    g.A = ctx->vovv_pk;
+    g.lda = Pv;
+    g.B = taupk;
+    g.ldb = Pv;
+    g.transB = 1;
+    g.C = ctx->Ypk;
+    g.ldc = Po;
+    P->gemm("C:gemm", g);
+    z *ypk = ctx->Ypk, *yf = ctx->Yfull;
+    P->custom("C:unpack", [=](cudaStream_t s) {
+      UnpackArgs u;
+      u.in = ypk;
+      u.out = yf;
+      u.n1 = (int64_t)v * o;
+      u.n2 = o;
+      u.alpha = mone;
+      u.beta = 0.0;
+      return unpack_pairs(u, s);
+    });
+    P->add("C", W(ctx->C, "kbij"), one, W(ctx->Yfull, "bkij"), false, 1.0);
+  }
+  // A^{kl}_{ij} = V^{kl}_{ij} + P^-_ij sum_c V^{kl}_{ic} t^c_j + 1/2 sum_cd V^{kl}_{cd} tau^{cd}_{ij}
+  P->add("A", W(ctx->Afull, "klij"), one, V(ctx->oooo, "klij"), false, 0.0);
+  P->contract("A", W(ctx->Yoooo, "klij"), one, V(ctx->ooov, "klic"), false, W(t1, "jc"), false, 0.0);
+  P->add("A", W(ctx->Afull, "klij"), one, W(ctx->Yoooo, "klij"), false, 1.0);
+  P->add("A", W(ctx->Afull, "klij"), mone, W(ctx->Yoooo, "klji"), false, 1.0);
+  {
+    z *af = ctx->Afull, *apk = ctx->Apk;
+    P->custom("A:pack", [=](cudaStream_t s) { return pack_pairs(af, apk, o, o, 1, s); });
+    ZGemmArgs g;  // Apk[P(kl)][P(ij)] += sum_{c<d} V^{kl}_{cd} tau^{cd}_{ij}
+    g.M = Po;
+    g.N = Po;
+    g.K = Pv;
+    g.A = ctx->oovv_pk;
+    g.lda = Pv;
+    g.B = taupk;
+    g.ldb = Pv;
+    g.transB = 1;
+    g.C = ctx->Apk;
+    g.ldc = Po;
+    g.beta = one;
+    P->gemm("A:gemm", g);
+  }
+
+  // S^{ab}_{ij}: driver V^{ij+}_{ab}
+  P->add("driver", W(ctx->S2, "ijab"), one, V(ctx->oovv, "ijab"), true, 0.0);
+  // ring: sum_kc P^-_ij P^-_ab (H^{ak}_{ci} t^{cb}_{jk}),  R[i][a][j][b] = sum_kc H^{ak}_{ci} t^{cb}_{jk}
+  P->contract("ring", W(ctx->R, "iajb"), one, W(ctx->Hr, "iakc"), false, W(t2, "jkcb"), false, 0.0);
+  P->add("ring", W(ctx->S2, "ijab"), one, W(ctx->R, "iajb"), false, 1.0);
+  P->add("ring", W(ctx->S2, "ijab"), mone, W(ctx->R, "jaib"), false, 1.0);
+  P->add("ring", W(ctx->S2, "ijab"), mone, W(ctx->R, "ibja"), false, 1.0);
+  P->add("ring", W(ctx->S2, "ijab"), one, W(ctx->R, "jbia"), false, 1.0);
+  // sum_k P^-_ji G^k_j t^{ab}_{ik}:  W1[j][i][a][b] = sum_k G^k_j t^{ab}_{ik}
+  P->contract("goo", W(ctx->W1, "jiab"), one, W(ctx->Goo, "kj"), false, W(t2, "ikab"), false, 0.0);
+  P->add("goo", W(ctx->S2, "ijab"), one, W(ctx->W1, "jiab"), false, 1.0);
+  P->add("goo", W(ctx->S2, "ijab"), mone, W(ctx->W1, "ijab"), false, 1.0);
+  // sum_c P^-_ij (V^{cj+}_{ab} t^c_i):  W1[i][j][a][b] = sum_c t^c_i conj(V^{cj}_{ab})
+  P->contract("vt1", W(ctx->W1, "ijab"), one, W(t1, "ic"), false, V(ctx->vovv, "cjab"), true, 0.0);
+  P->add("vt1", W(ctx->S2, "ijab"), one, W(ctx->W1, "ijab"), false, 1.0);
+  P->add("vt1", W(ctx->S2, "ijab"), mone, W(ctx->W1, "jiab"), false, 1.0);
+  // sum_c P^-_ab G^a_c t^{cb}_{ij}:  W1[a][i][j][b] = sum_c G^a_c t^{cb}_{ij}
+  P->contract("gvv", W(ctx->W1, "aijb"), one, W(ctx->Gvv, "ac"), false, W(t2, "ijcb"), false, 0.0);
+  P->add("gvv", W(ctx->S2, "ijab"), one, W(ctx->W1, "aijb"), false, 1.0);
+  P->add("gvv", W(ctx->S2, "ijab"), mone, W(ctx->W1, "bija"), false, 1.0);
+  // sum_k P^-_ab (C^{ka}_{ij} t^b_k):  W1[a][i][j][b] = sum_k C^{ka}_{ij} t^b_k
+  P->contract("ct1", W(ctx->W1, "aijb"), one, W(ctx->C, "kaij"), false, W(t1, "kb"), false, 0.0);
+  P->add("ct1", W(ctx->S2, "ijab"), one, W(ctx->W1, "aijb"), false, 1.0);
+  P->add("ct1", W(ctx->S2, "ijab"), mone, W(ctx->W1, "bija"), false, 1.0);
+  // 1/2 sum_kl A^{kl}_{ij} tau^{ab}_{kl}  (packed: sum_{k<l})
+  {
+    ZGemmArgs g;  // Hpk[P(ij)][P(ab)] = sum_{k<l} A^{kl}_{ij} tau^{ab}_{kl}
+    g.M = Po;
+    g.N = Pv;
+    g.K = Po;
+    g.A = ctx->Apk;
+    g.lda = Po;
+    g.transA = 1;
+    g.B = taupk;
+    g.ldb = Pv;
+    g.C = ctx->Hpk;
+    g.ldc = Pv;
+    P->gemm("hole:gemm", g);
+    z *hpk = ctx->Hpk, *s2 = ctx->S2;
+    P->custom("hole:unpack", [=](cudaStream_t s) {
+      UnpackArgs u;
+      u.in = hpk;
+      u.out = s2;
+      u.n1 = o;
+      u.n2 = v;
+      u.unpack_rows = 1;
+      return unpack_pairs(u, s);
+    });
+  }
+  // particle-particle ladder 1/2 sum_cd V^{ab}_{cd} tau^{cd}_{ij}  (packed: sum_{c<d})
+  {
+    ZGemmArgs g;  // Lpk[P(ij)][P(ab)] = sum_{c<d} tau^{cd}_{ij} <ab||cd>
+    g.M = Po;
+    g.N = Pv;
+    g.K = Pv;
+    g.A = taupk;
+    g.lda = Pv;
+    g.B = ctx->Wpk;
+    g.ldb = Pv;
+    g.transB = 1;
+    g.C = ctx->Lpk;
+    g.ldc = Pv;
+    P->gemm("ladder:gemm", g);
+    z *lpk = ctx->Lpk, *s2 = ctx->S2;
+    P->custom("ladder:unpack", [=](cudaStream_t s) {
+      UnpackArgs u;
+      u.in = lpk;
+      u.out = s2;
+      u.n1 = o;
+      u.n2 = v;
+      u.unpack_rows = 1;
+      return unpack_pairs(u, s);
+    });
+  }
+
+  // S^a_i
+  P->add("S1", W(ctx->S1, "ia"), one, V(ctx->fov, "ia"), true, 0.0);                                   // F^{i+}_a
+  P->contract("S1", W(ctx->S1, "ia"), one, W(ctx->Hvv, "ac"), false, W(t1, "ic"), false, 1.0);          // H^a_c t^c_i
+  P->contract("S1", W(ctx->S1, "ia"), one, W(ctx->Hoo, "ki"), false, W(t1, "ka"), false, 1.0);          // H^k_i t^a_k
+  P->contract("S1", W(ctx->S1, "ia"), one, W(ctx->Hov, "kc"), false, W(t2, "ikac"), false, 1.0);        // H^k_c t^{ac}_{ik}
+  P->add("S1", W(ctx->Yov, "kc"), one, W(ctx->Hov, "kc"), false, 0.0);                                   // H^k_c - 2 F^k_c
+  P->add("S1", W(ctx->Yov, "kc"), zmake(-2, 0), V(ctx->fov, "kc"), false, 1.0);
+  P->contract("S1", W(ctx->Zoo, "ik"), one, W(ctx->Yov, "kc"), false, W(t1, "ic"), false, 0.0);
+  P->contract("S1", W(ctx->S1, "ia"), one, W(ctx->Zoo, "ik"), false, W(t1, "ka"), false, 1.0);
+  P->contract("S1", W(ctx->S1, "ia"), half, V(ctx->vovv, "akcd"), false, W(tau, "ikcd"), false, 1.0);    // 1/2 V^{ak}_{cd} tau^{cd}_{ik}
+  P->contract("S1", W(ctx->S1, "ia"), half, V(ctx->ooov, "klic"), false, W(tau, "klca"), false, 1.0);    // 1/2 V^{kl}_{ic} tau^{ca}_{kl}
+  P->contract("S1", W(ctx->S1, "ia"), mone, V(ctx->vovo, "akci"), false, W(t1, "kc"), false, 1.0);       // - V^{ak}_{ci} t^c_k
+
+  if (P->status() != cudaSuccess) return set_err(ctx, CCSD_ERR_CUDA, "residual plan: " + P->error());
+  for (void* m : P->owned()) ctx->allocs.push_back(m);
+  P->owned().clear();
+  CS(dalloc(ctx, &ctx->scratch, P->scratch_elems()));
+  (void)Po;
+  (void)Pv;
+  return CCSD_OK;
+}
+
+cudaError_t run_ops(ccsd_ctx* ctx, bool profile) {
+  auto& ops = ctx->plan->ops();
+  if (!profile) {
+    for (auto& op : ops) {
+      cudaError_t e = op.run(ctx->stream);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+  std::vector<cudaEvent_t> ev(ops.size() + 1);
+  for (auto& e : ev) cudaEventCreate(&e);
+  cudaEventRecord(ev[0], ctx->stream);
+  for (size_t k = 0; k < ops.size(); ++k) {
+    cudaError_t e = ops[k].run(ctx->stream);
+    if (e != cudaSuccess) return e;
+    cudaEventRecord(ev[k + 1], ctx->stream);
+  }
+  cudaError_t e = cudaEventSynchronize(ev.back());
+  ctx->tnames.clear();
+  ctx->tms.clear();
+  for (size_t k = 0; k < ops.size(); ++k) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+    ctx->tnames.push_back(ops[k].name);
+    ctx->tms.push_back(ms);
+  }
+  for (auto& x : ev) cudaEventDestroy(x);
+  return e;
+}
+
+// One iteration: backup, residual, t <- t + S/D (S <- S/D), norms, DIIS.
+cudaError_t iteration_ops(ccsd_ctx* ctx, bool profile) {
+  const int64_t n1 = (int64_t)ctx->o * ctx->v, n2 = n1 * ctx->o * ctx->v;
+  cudaError_t e = cudaMemcpyAsync(ctx->t1_prev, ctx->t1, n1 * sizeof(z), cudaMemcpyDeviceToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ctx->t2_prev, ctx->t2, n2 * sizeof(z), cudaMemcpyDeviceToDevice, ctx->stream);
+  if (e == cudaSuccess) e = run_ops(ctx, profile);
+  if (e == cudaSuccess)
+    e = denom_update(ctx->t1, ctx->t2, ctx->S1, ctx->S2, ctx->dvec, ctx->o, ctx->v, ctx->opts.level_shift,
+                     ctx->upd_partials, ctx->stream);
+  if (e == cudaSuccess) e = norm_finalize(ctx->upd_partials, update_blocks(), ctx->stats, ctx->stream);
+  if (e == cudaSuccess && ctx->opts.diis_dim > 0) e = diis_step(ctx->diis, ctx->t1, ctx->t2, ctx->S1, ctx->S2, ctx->stream);
+  return e;
+}
+
+ccsd_status copy_in(ccsd_ctx* ctx, z* dst, const void* src, int64_t count, int on_device) {
+  CK(cudaMemcpyAsync(dst, src, count * sizeof(z), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                     ctx->stream));
+  return CCSD_OK;
+}
+ccsd_status copy_out(ccsd_ctx* ctx, void* dst, const z* src, int64_t count, int on_device) {
+  CK(cudaMemcpyAsync(dst, src, count * sizeof(z), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  return CCSD_OK;
+}
+
+bool hermitian(const ccsd_z* m, int64_t n, int64_t count) {
+  for (int64_t q = 0; q < count; ++q) {
+    const ccsd_z* a = m + q * n * n;
+    double mx = 0.0, dev = 0.0;
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t j = 0; j < n; ++j) {
+        const ccsd_z x = a[i * n + j], y = a[j * n + i];
+        mx = std::max(mx, std::hypot(x.re, x.im));
+        dev = std::max(dev, std::hypot(x.re - y.re, x.im + y.im));
+      }
+    if (!(dev <= 1e-12 * std::max(mx, 1e-300)) && dev > 0.0) return false;
+  }
+  return true;
+}
+
+ccsd_status create_impl(int o, int v, const double* eps, const ccsd_z* fock, ccsd_int_kind kind, const ccsd_z* ints,
+                        int naux, const ccsd_opts* opts, ccsd_ctx* ctx) {
+  if (o < 1 || v < 1) return set_err(ctx, CCSD_ERR_ARG, "o and v must be >= 1");
+  if (!eps || !ints) return set_err(ctx, CCSD_ERR_ARG, "eps and ints must not be NULL");
+  if (kind == CCSD_INT_DF && naux < 1) return set_err(ctx, CCSD_ERR_ARG, "naux must be >= 1 for DF integrals");
+  if (kind != CCSD_INT_DF && kind != CCSD_INT_FULL) return set_err(ctx, CCSD_ERR_ARG, "unknown integral kind");
+  ctx->o = o;
+  ctx->v = v;
+  ctx->n = o + v;
+  ctx->naux = kind == CCSD_INT_DF ? naux : 0;
+  ctx->Po = pair_count(o);
+  ctx->Pv = pair_count(v);
+  if (opts) ctx->opts = *opts;
+  else ccsd_default_opts(&ctx->opts);
+  if (ctx->opts.diis_dim < 0 || ctx->opts.diis_dim > 16) return set_err(ctx, CCSD_ERR_ARG, "diis_dim must be in [0, 16]");
+  if (ctx->opts.precision != CCSD_PREC_FP64)
+    return set_err(ctx, CCSD_ERR_UNSUPPORTED, "only the FP64 precision mode is available in this build");
+  if (!ctx->opts.store_w) return set_err(ctx, CCSD_ERR_UNSUPPORTED, "store_w = 0 is not available in this build");
+  const int n = ctx->n;
+  if (fock && !hermitian(fock, n, 1)) return set_err(ctx, CCSD_ERR_ARG, "Fock matrix is not Hermitian");
+  if (kind == CCSD_INT_DF && !hermitian(ints, n, naux)) return set_err(ctx, CCSD_ERR_ARG, "B^Q is not Hermitian in (p,r)");
+  if (ctx->opts.stream) {
+    ctx->stream = (cudaStream_t)ctx->opts.stream;
+  } else {
+    CK(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+    ctx->own_stream = true;
+  }
+
+  // Fock blocks and the denominator diagonal
+  std::vector<ccsd_z> F((size_t)n * n, ccsd_z{0.0, 0.0});
+  if (fock) std::memcpy(F.data(), fock, sizeof(ccsd_z) * n * n);
+  else
+    for (int p = 0; p < n; ++p) F[(size_t)p * n + p].re = eps[p];
+  std::vector<double> dv(n);
+  for (int p = 0; p < n; ++p) dv[p] = F[(size_t)p * n + p].re;
+  std::vector<ccsd_z> foo((size_t)o * o), fov((size_t)o * v), fvv((size_t)v * v);
+  for (int i = 0; i < o; ++i)
+    for (int j = 0; j < o; ++j) foo[(size_t)i * o + j] = F[(size_t)i * n + j];
+  for (int i = 0; i < o; ++i)
+    for (int a = 0; a < v; ++a) fov[(size_t)i * v + a] = F[(size_t)i * n + o + a];
+  for (int a = 0; a < v; ++a)
+    for (int b = 0; b < v; ++b) fvv[(size_t)a * v + b] = F[(size_t)(o + a) * n + o + b];
+  CS(dalloc(ctx, &ctx->dvec, n));
+  CS(dalloc(ctx, &ctx->foo, (int64_t)o * o));
+  CS(dalloc(ctx, &ctx->fov, (int64_t)o * v));
+  CS(dalloc(ctx, &ctx->fvv, (int64_t)v * v));
+  CK(cudaMemcpyAsync(ctx->dvec, dv.data(), sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->foo, foo.data(), sizeof(z) * o * o, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->fov, fov.data(), sizeof(z) * o * v, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->fvv, fvv.data(), sizeof(z) * v * v, cudaMemcpyHostToDevice, ctx->stream));
+
+  // integral blocks
+  const int64_t oo = (int64_t)o * o, vv = (int64_t)v * v, ov = (int64_t)o * v;
+  CS(dalloc(ctx, &ctx->oooo, oo * oo));
+  CS(dalloc(ctx, &ctx->ooov, oo * ov));
+  CS(dalloc(ctx, &ctx->oovv, oo * vv));
+  CS(dalloc(ctx, &ctx->vovo, ov * ov));
+  CS(dalloc(ctx, &ctx->vovv, ov * vv));
+  CS(dalloc(ctx, &ctx->Wpk, ctx->Pv * ctx->Pv));
+  {
+    void* dints = nullptr;
+    const int64_t cnt = kind == CCSD_INT_DF ? (int64_t)naux * n * n : (int64_t)n * n * n * n;
+    if (cudaMalloc(&dints, cnt * sizeof(z)) != cudaSuccess) {
+      cudaGetLastError();
+      return set_err(ctx, CCSD_ERR_OOM, "device copy of the integrals");
+    }
+    ccsd_status st = CCSD_OK;
+    cudaError_t e = cudaMemcpyAsync(dints, ints, cnt * sizeof(z), cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) st = set_err(ctx, CCSD_ERR_CUDA, cudaGetErrorString(e));
+    const char* names[5] = {"oooo", "ooov", "oovv", "vovo", "vovv"};
+    z* outs[5] = {ctx->oooo, ctx->ooov, ctx->oovv, ctx->vovo, ctx->vovv};
+    for (int b = 0; b < 5 && st == CCSD_OK; ++b)
+      st = kind == CCSD_INT_DF ? build_block_df(ctx, (const z*)dints, names[b], outs[b])
+                               : build_block_full(ctx, (const z*)dints, names[b], outs[b]);
+    if (st == CCSD_OK) {
+      if (kind == CCSD_INT_DF) {
+        st = build_w_df(ctx, (const z*)dints);
+      } else {
+        z* vvvv = nullptr;
+        if (cudaMalloc(&vvvv, vv * vv * sizeof(z)) != cudaSuccess) {
+          cudaGetLastError();
+          st = set_err(ctx, CCSD_ERR_OOM, "vvvv temporary");
+        } else {
+          st = build_block_full(ctx, (const z*)dints, "vvvv", vvvv);
+          if (st == CCSD_OK) {
+            e = pack_pairs(vvvv, ctx->Wpk, v, v, 1, ctx->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+            if (e != cudaSuccess) st = set_err(ctx, CCSD_ERR_CUDA, cudaGetErrorString(e));
+          }
+          cudaFree(vvvv);
+        }
+      }
+    }
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(dints);
+    if (st != CCSD_OK) return st;
+  }
+  // derived constant layouts
+  CS(dalloc(ctx, &ctx->vovv_pk, ov * ctx->Pv));
+  CS(dalloc(ctx, &ctx->oovv_pk, ctx->Po * ctx->Pv));
+  CS(dalloc(ctx, &ctx->J, ov * ov));
+  CS(dalloc(ctx, &ctx->Cinit, ov * oo));
+  CK(pack_pairs(ctx->vovv, ctx->vovv_pk, ov, v, 0, ctx->stream));
+  CK(pack_pairs(ctx->oovv, ctx->oovv_pk, o, v, 1, ctx->stream));
+  {
+    const int64_t d_vovo[4] = {v, o, v, o};  // [a][k][c][i] -> J[i][a][k][c]
+    const int pJ[4] = {3, 0, 1, 2};
+    CK(permute4(ctx->vovo, d_vovo, pJ, ctx->J, zmake(1, 0), 0.0, 0, ctx->stream));
+    const int64_t d_ooov[4] = {o, o, o, v};  // [i][j][k][b] -> Cinit[k][b][i][j] = conj
+    const int pC[4] = {2, 3, 0, 1};
+    CK(permute4(ctx->ooov, d_ooov, pC, ctx->Cinit, zmake(1, 0), 0.0, 1, ctx->stream));
+  }
+
+  // amplitudes, residuals and intermediates
+  const int64_t n2 = oo * vv;
+  CS(dalloc(ctx, &ctx->t1, ov));
+  CS(dalloc(ctx, &ctx->t2, n2));
+  CS(dalloc(ctx, &ctx->S1, ov));
+  CS(dalloc(ctx, &ctx->S2, n2));
+  CS(dalloc(ctx, &ctx->t1_prev, ov));
+  CS(dalloc(ctx, &ctx->t2_prev, n2));
+  CS(dalloc(ctx, &ctx->t1_save, ov));
+  CS(dalloc(ctx, &ctx->t2_save, n2));
+  CS(dalloc(ctx, &ctx->tau, n2));
+  CS(dalloc(ctx, &ctx->tau_pk, ctx->Po * ctx->Pv));
+  CS(dalloc(ctx, &ctx->X, n2));
+  CS(dalloc(ctx, &ctx->Hvv, vv));
+  CS(dalloc(ctx, &ctx->Gvv, vv));
+  CS(dalloc(ctx, &ctx->Hoo, oo));
+  CS(dalloc(ctx, &ctx->Goo, oo));
+  CS(dalloc(ctx, &ctx->Hov, ov));
+  CS(dalloc(ctx, &ctx->Yov, ov));
+  CS(dalloc(ctx, &ctx->Zoo, oo));
+  CS(dalloc(ctx, &ctx->Hr, n2));
+  CS(dalloc(ctx, &ctx->R, n2));
+  CS(dalloc(ctx, &ctx->W1, n2));
+  CS(dalloc(ctx, &ctx->C, ov * oo));
+  CS(dalloc(ctx, &ctx->Yovoo, ov * oo));
+  CS(dalloc(ctx, &ctx->Ypk, ov * ctx->Po));
+  CS(dalloc(ctx, &ctx->Yfull, ov * oo));
+  CS(dalloc(ctx, &ctx->Afull, oo * oo));
+  CS(dalloc(ctx, &ctx->Yoooo, oo * oo));
+  CS(dalloc(ctx, &ctx->Apk, ctx->Po * ctx->Po));
+  CS(dalloc(ctx, &ctx->Lpk, ctx->Po * ctx->Pv));
+  CS(dalloc(ctx, &ctx->Hpk, ctx->Po * ctx->Pv));
+  CS(dalloc(ctx, &ctx->upd_partials, 2 * update_blocks()));
+  CS(dalloc(ctx, &ctx->stats, 4));
+  CS(dalloc(ctx, &ctx->e_partials, energy_blocks()));
+  CS(dalloc(ctx, &ctx->e_dev, 1));
+  CK(cudaMallocHost(&ctx->stats_host, 4 * sizeof(double)));
+  CK(cudaMallocHost(&ctx->e_host, sizeof(z)));
+  CK(cudaMemsetAsync(ctx->t1, 0, ov * sizeof(z), ctx->stream));
+  CK(cudaMemsetAsync(ctx->t2, 0, n2 * sizeof(z), ctx->stream));
+
+  // DIIS subspace
+  if (ctx->opts.diis_dim > 0) {
+    DiisArgs& d = ctx->diis;
+    d.o = o;
+    d.v = v;
+    d.m = ctx->opts.diis_dim;
+    d.start = ctx->opts.diis_start;
+    d.L = ov + ctx->Po * ctx->Pv;
+    CS(dalloc(ctx, &d.hist_t, d.m * d.L));
+    CS(dalloc(ctx, &d.hist_e, d.m * d.L));
+    CS(dalloc(ctx, &d.Bmat, (int64_t)d.m * d.m));
+    CS(dalloc(ctx, &d.coef, d.m));
+    CS(dalloc(ctx, &d.partials, (int64_t)d.m * diis_blocks()));
+    CS(dalloc(ctx, &d.state, 1));
+    CK(diis_reset(d, ctx->stream));
+  }
+
+  CS(build_residual_plan(ctx));
+
+  // MP2 guess: one denominator update from t = 0
+  CK(run_ops(ctx, false));
+  CK(denom_update(ctx->t1, ctx->t2, ctx->S1, ctx->S2, ctx->dvec, o, v, ctx->opts.level_shift, ctx->upd_partials,
+                  ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return CCSD_OK;
+}
+
+void free_ctx(ccsd_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+  for (void* p : ctx->allocs) cudaFree(p);
+  if (ctx->plan) {
+    for (void* p : ctx->plan->owned()) cudaFree(p);
+    delete ctx->plan;
+  }
+  if (ctx->stats_host) cudaFreeHost(ctx->stats_host);
+  if (ctx->e_host) cudaFreeHost(ctx->e_host);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ccsd_default_opts(ccsd_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->max_iter = 50;
+  o->tol = 1e-10;
+  o->norm = 0;
+  o->diis_dim = 8;
+  o->diis_start = 2;
+  o->level_shift = 0.0;
+  o->precision = CCSD_PREC_FP64;
+  o->slices = 0;
+  o->store_w = 1;
+  o->profile = 0;
+  o->stream = nullptr;
+}
+
+ccsd_status ccsd_create(int o, int v, const double* eps, const ccsd_z* fock, ccsd_int_kind kind, const ccsd_z* ints,
+                        int naux, const ccsd_opts* opts, ccsd_ctx** out) {
+  if (!out) return set_err(nullptr, CCSD_ERR_ARG, "out must not be NULL");
+  *out = nullptr;
+  ccsd_ctx* ctx = new ccsd_ctx();
+  ccsd_status st = create_impl(o, v, eps, fock, kind, ints, naux, opts, ctx);
+  if (st != CCSD_OK) {
+    g_create_error = ctx->err;
+    free_ctx(ctx);
+    return st;
+  }
+  *out = ctx;
+  return CCSD_OK;
+}
+
+ccsd_status ccsd_residual(ccsd_ctx* ctx, const ccsd_z* t1, const ccsd_z* t2, ccsd_z* r1, ccsd_z* r2, int on_device) {
+  if (!ctx) return CCSD_ERR_ARG;
+  if ((t1 == nullptr) != (t2 == nullptr)) return set_err(ctx, CCSD_ERR_ARG, "t1 and t2 must both be given or both NULL");
+  const int64_t n1 = (int64_t)ctx->o * ctx->v, n2 = n1 * ctx->o * ctx->v;
+  if (t1) {
+    CK(cudaMemcpyAsync(ctx->t1_save, ctx->t1, n1 * sizeof(z), cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->t2_save, ctx->t2, n2 * sizeof(z), cudaMemcpyDeviceToDevice, ctx->stream));
+    CS(copy_in(ctx, ctx->t1, t1, n1, on_device));
+    CS(copy_in(ctx, ctx->t2, t2, n2, on_device));
+  }
+  CK(run_ops(ctx, ctx->opts.profile != 0));
+  if (r1) CS(copy_out(ctx, r1, ctx->S1, n1, on_device));
+  if (r2) CS(copy_out(ctx, r2, ctx->S2, n2, on_device));
+  if (t1) {
+    CK(cudaMemcpyAsync(ctx->t1, ctx->t1_save, n1 * sizeof(z), cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->t2, ctx->t2_save, n2 * sizeof(z), cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return CCSD_OK;
+}
+
+ccsd_status ccsd_iterate(ccsd_ctx* ctx, int max_iter, int* iters_done, double* res_norm) {
+  if (!ctx) return CCSD_ERR_ARG;
+  if (max_iter <= 0) max_iter = ctx->opts.max_iter;
+  const bool profile = ctx->opts.profile != 0;
+  if (!profile && !ctx->graph) {
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = iteration_ops(ctx, false);
+    cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return set_err(ctx, CCSD_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(&ctx->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return set_err(ctx, CCSD_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  }
+  int it = 0;
+  double nrm = INFINITY;
+  ccsd_status st = CCSD_ERR_NOT_CONVERGED;
+  for (it = 1; it <= max_iter; ++it) {
+    if (profile) {
+      CK(iteration_ops(ctx, true));
+    } else {
+      CK(cudaGraphLaunch(ctx->graph, ctx->stream));
+    }
+    CK(cudaMemcpyAsync(ctx->stats_host, ctx->stats, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    nrm = ctx->opts.norm == 1 ? ctx->stats_host[1] : ctx->stats_host[0];
+    if (!std::isfinite(ctx->stats_host[0]) || !std::isfinite(ctx->stats_host[1])) {
+      const int64_t n1 = (int64_t)ctx->o * ctx->v, n2 = n1 * ctx->o * ctx->v;
+      CK(cudaMemcpyAsync(ctx->t1, ctx->t1_prev, n1 * sizeof(z), cudaMemcpyDeviceToDevice, ctx->stream));
+      CK(cudaMemcpyAsync(ctx->t2, ctx->t2_prev, n2 * sizeof(z), cudaMemcpyDeviceToDevice, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      st = set_err(ctx, CCSD_ERR_DIVERGED, "non-finite amplitude update at iteration " + std::to_string(it));
+      break;
+    }
+    if (nrm <= ctx->opts.tol) {
+      st = CCSD_OK;
+      break;
+    }
+  }
+  if (it > max_iter) it = max_iter;
+  if (iters_done) *iters_done = it;
+  if (res_norm) *res_norm = nrm;
+  if (st == CCSD_ERR_NOT_CONVERGED) set_err(ctx, st, "not converged in " + std::to_string(max_iter) + " iterations");
+  return st;
+}
+
+ccsd_status ccsd_energy(ccsd_ctx* ctx, ccsd_z* e) {
+  if (!ctx || !e) return ctx ? set_err(ctx, CCSD_ERR_ARG, "e must not be NULL") : CCSD_ERR_ARG;
+  CK(energy_eval(ctx->fov, ctx->oovv, ctx->t1, ctx->t2, ctx->o, ctx->v, ctx->e_partials, ctx->e_dev, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->e_host, ctx->e_dev, sizeof(z), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  e->re = ctx->e_host->x;
+  e->im = ctx->e_host->y;
+  return CCSD_OK;
+}
+
+ccsd_status ccsd_get_amplitudes(ccsd_ctx* ctx, ccsd_z* t1, ccsd_z* t2, int on_device) {
+  if (!ctx) return CCSD_ERR_ARG;
+  const int64_t n1 = (int64_t)ctx->o * ctx->v, n2 = n1 * ctx->o * ctx->v;
+  if (t1) CS(copy_out(ctx, t1, ctx->t1, n1, on_device));
+  if (t2) CS(copy_out(ctx, t2, ctx->t2, n2, on_device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return CCSD_OK;
+}
+
+ccsd_status ccsd_set_amplitudes(ccsd_ctx* ctx, const ccsd_z* t1, const ccsd_z* t2, int on_device) {
+  if (!ctx) return CCSD_ERR_ARG;
+  if (!t1 || !t2) return set_err(ctx, CCSD_ERR_ARG, "t1 and t2 must not be NULL");
+  const int64_t n1 = (int64_t)ctx->o * ctx->v, n2 = n1 * ctx->o * ctx->v;
+  CS(copy_in(ctx, ctx->t1, t1, n1, on_device));
+  CS(copy_in(ctx, ctx->t2, t2, n2, on_device));
+  if (ctx->opts.diis_dim > 0) CK(diis_reset(ctx->diis, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return CCSD_OK;
+}
+
+ccsd_status ccsd_get_tensor(ccsd_ctx* ctx, const char* name, ccsd_z* out, size_t count, int on_device) {
+  if (!ctx || !name || !out) return ctx ? set_err(ctx, CCSD_ERR_ARG, "NULL argument") : CCSD_ERR_ARG;
+  const int64_t o = ctx->o, v = ctx->v, oo = o * o, vv = v * v, ov = o * v;
+  const z* src = nullptr;
+  int64_t cnt = 0;
+  std::string nm(name);
+  if (nm == "tau") { src = ctx->tau; cnt = oo * vv; }
+  else if (nm == "Hvv") { src = ctx->Hvv; cnt = vv; }
+  else if (nm == "Gvv") { src = ctx->Gvv; cnt = vv; }
+  else if (nm == "Hoo") { src = ctx->Hoo; cnt = oo; }
+  else if (nm == "Goo") { src = ctx->Goo; cnt = oo; }
+  else if (nm == "Hov") { src = ctx->Hov; cnt = ov; }
+  else if (nm == "Hvoov") { src = ctx->Hr; cnt = oo * vv; }
+  else if (nm == "C") { src = ctx->C; cnt = ov * oo; }
+  else if (nm == "A") {
+    UnpackArgs u;
+    u.in = ctx->Apk;
+    u.out = ctx->Yoooo;
+    u.n1 = o;
+    u.n2 = o;
+    u.unpack_rows = 1;
+    u.beta = 0.0;
+    CK(unpack_pairs(u, ctx->stream));
+    src = ctx->Yoooo;
+    cnt = oo * oo;
+  } else if (nm == "ladder") {
+    UnpackArgs u;
+    u.in = ctx->Lpk;
+    u.out = ctx->W1;
+    u.n1 = o;
+    u.n2 = v;
+    u.unpack_rows = 1;
+    u.beta = 0.0;
+    CK(unpack_pairs(u, ctx->stream));
+    src = ctx->W1;
+    cnt = oo * vv;
+  } else {
+    return set_err(ctx, CCSD_ERR_ARG, "unknown tensor name '" + nm + "'");
+  }
+  if ((int64_t)count != cnt) return set_err(ctx, CCSD_ERR_ARG, "count must be " + std::to_string(cnt) + " for " + nm);
+  CS(copy_out(ctx, out, src, cnt, on_device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  (void)kIntermediates;
+  return CCSD_OK;
+}
+
+ccsd_status ccsd_timings(ccsd_ctx* ctx, const char** names, double* ms, int cap, int* n) {
+  if (!ctx) return CCSD_ERR_ARG;
+  const int cnt = (int)ctx->tnames.size();
+  if (n) *n = cnt;
+  for (int k = 0; k < cnt && k < cap; ++k) {
+    if (names) names[k] = ctx->tnames[k].c_str();
+    if (ms) ms[k] = ctx->tms[k];
+  }
+  return CCSD_OK;
+}
+
+const char* ccsd_last_error(const ccsd_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+void ccsd_destroy(ccsd_ctx* ctx) { free_ctx(ctx); }
+
+}  // extern "C"

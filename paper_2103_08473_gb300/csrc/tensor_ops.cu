@@ -1,0 +1,550 @@
+// HBM-bound kernels of libccsd: index permutations (the P^-_pq antisymmetrisers
+// and the reorders of the transpose-transpose-GEMM-transpose contractions),
+// antisymmetric pair packing, tau, the denominator ("Jacobi") update with its
+// norms, the energy, and DIIS. All reductions are two-stage with a fixed order,
+// so every result is bit-reproducible run to run.
+#include "ops.h"
+#include "zgemm.h"
+
+namespace ccsd {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kUpdateBlocks = 152 * 4;
+constexpr int kEnergyBlocks = 152 * 2;
+constexpr int kDiisBlocks = 152 * 2;
+
+__device__ __forceinline__ z ld_conj(const z* p, int conj) {
+  z v = *p;
+  if (conj) v.y = -v.y;
+  return v;
+}
+
+// ---- permutations ----------------------------------------------------------
+
+// Output-ordered elementwise copy: coalesced when the innermost output dim is also
+// innermost in the input.
+__global__ void permute_direct_kernel(PermuteArgs g, int64_t total) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = e, io = 0, oo = 0;
+    for (int d = g.rank - 1; d >= 0; --d) {
+      int64_t c = r % g.dims[d];
+      r /= g.dims[d];
+      io += c * g.istr[d];
+      oo += c * g.ostr[d];
+    }
+    z v = ld_conj(g.in + io, g.conj);
+    z* o = g.out + oo;
+    *o = g.beta != 0.0 ? zaxpby(g.alpha, v, g.beta, *o) : zmul(g.alpha, v);
+  }
+}
+
+// 32 x 32 shared-memory transpose over output dims (p, q): q is innermost in the
+// output, p is innermost (stride 1) in the input, so both the loads and the
+// stores are coalesced. The remaining dims are walked by blockIdx.y.
+__global__ void permute_tiled_kernel(PermuteArgs g, int p, int64_t nrest, int64_t tiles_p, int64_t tiles_q) {
+  __shared__ z tile[32][33];
+  const int q = g.rank - 1;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int64_t r = blockIdx.y; r < nrest; r += gridDim.y) {
+    int64_t rr = r, ib = 0, ob = 0;
+    for (int d = g.rank - 1; d >= 0; --d) {
+      if (d == p || d == q) continue;
+      int64_t c = rr % g.dims[d];
+      rr /= g.dims[d];
+      ib += c * g.istr[d];
+      ob += c * g.ostr[d];
+    }
+    for (int64_t t = blockIdx.x; t < tiles_p * tiles_q; t += gridDim.x) {
+      const int64_t p0 = (t / tiles_q) * 32, q0 = (t % tiles_q) * 32;
+      for (int yy = ty; yy < 32; yy += 8) {
+        int64_t pp = p0 + tx, qq = q0 + yy;
+        if (pp < g.dims[p] && qq < g.dims[q]) tile[yy][tx] = ld_conj(g.in + ib + pp * g.istr[p] + qq * g.istr[q], g.conj);
+      }
+      __syncthreads();
+      for (int yy = ty; yy < 32; yy += 8) {
+        int64_t qq = q0 + tx, pp = p0 + yy;
+        if (pp < g.dims[p] && qq < g.dims[q]) {
+          z v = tile[tx][yy];
+          z* o = g.out + ob + pp * g.ostr[p] + qq * g.ostr[q];
+          *o = g.beta != 0.0 ? zaxpby(g.alpha, v, g.beta, *o) : zmul(g.alpha, v);
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__global__ void zscale_kernel(z* C, int64_t M, int64_t N, int64_t ldc, int64_t sC, int batch, z beta) {
+  const int64_t total = M * N * batch;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t n = e % N, m = (e / N) % M, b = e / (M * N);
+    z* p = C + b * sC + m * ldc + n;
+    *p = (beta.x == 0.0 && beta.y == 0.0) ? make_double2(0.0, 0.0) : zmul(beta, *p);
+  }
+}
+
+// ---- amplitudes ------------------------------------------------------------
+
+__global__ void tau_kernel(const z* __restrict__ t1, const z* __restrict__ t2, z* __restrict__ out, int o, int v,
+                           double c2, double c11, int anti) {
+  const int64_t total = (int64_t)o * o * v * v;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(e % v), a = (int)((e / v) % v);
+    const int y = (int)((e / ((int64_t)v * v)) % o), x = (int)(e / ((int64_t)v * v * o));
+    z r = zmul(t1[(int64_t)x * v + a], t1[(int64_t)y * v + b]);
+    if (anti) r = zsub(r, zmul(t1[(int64_t)y * v + a], t1[(int64_t)x * v + b]));
+    z t = t2 ? t2[e] : make_double2(0.0, 0.0);
+    out[e] = make_double2(c2 * t.x + c11 * r.x, c2 * t.y + c11 * r.y);
+  }
+}
+
+__global__ void pack_pairs_kernel(const z* __restrict__ in, z* __restrict__ out, int64_t n1, int64_t n2,
+                                  int pack_rows) {
+  const int64_t P2 = pair_count(n2);
+  const int64_t R = pack_rows ? pair_count(n1) : n1;
+  const int64_t total = R * P2;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t col = e % P2, row = e / P2;
+    int64_t a, b;
+    pair_decode(col, n2, a, b);
+    int64_t rin = row;
+    if (pack_rows) {
+      int64_t x, y;
+      pair_decode(row, n1, x, y);
+      rin = x * n1 + y;
+    }
+    out[e] = in[(rin * n2 + a) * n2 + b];
+  }
+}
+
+__global__ void unpack_pairs_kernel(UnpackArgs g) {
+  const int64_t P2 = pair_count(g.n2);
+  const int64_t R = g.unpack_rows ? g.n1 * g.n1 : g.n1;
+  const int64_t total = R * g.n2 * g.n2;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = e % g.n2, a = (e / g.n2) % g.n2, r = e / (g.n2 * g.n2);
+    double sgn = 1.0;
+    int64_t prow = r;
+    bool zero = (a == b);
+    if (g.unpack_rows) {
+      const int64_t x = r / g.n1, y = r % g.n1;
+      if (x == y) zero = true;
+      else if (x < y) prow = pair_index(x, y, g.n1);
+      else { prow = pair_index(y, x, g.n1); sgn = -sgn; }
+    }
+    z val = make_double2(0.0, 0.0);
+    if (!zero) {
+      int64_t pc;
+      if (a < b) pc = pair_index(a, b, g.n2);
+      else { pc = pair_index(b, a, g.n2); sgn = -sgn; }
+      val = zscale(sgn, zmul(g.alpha, g.in[prow * P2 + pc]));
+    }
+    z* op = g.out + e;
+    *op = g.beta != 0.0 ? make_double2(g.beta * op->x + val.x, g.beta * op->y + val.y) : val;
+  }
+}
+
+__global__ void pack_vvvv_kernel(const z* __restrict__ D, z* __restrict__ W, int64_t v) {
+  const int64_t P = pair_count(v);
+  const int64_t total = P * P;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t a, b, c, d;
+    pair_decode(e / P, v, a, b);
+    pair_decode(e % P, v, c, d);
+    // <ab||cd> = (ac|bd) - (ad|bc), D[a][c][b][d] = (ac|bd)
+    z x = D[((a * v + c) * v + b) * v + d];
+    z y = D[((a * v + d) * v + b) * v + c];
+    W[e] = zsub(x, y);
+  }
+}
+
+// ---- update and norms ------------------------------------------------------
+
+template <typename T>
+__device__ T block_reduce_sum(T x, T* sh) {
+  for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = x;
+  __syncthreads();
+  T r = 0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sh[i];
+  __syncthreads();
+  return r;
+}
+__device__ double block_reduce_max(double x, double* sh) {
+  for (int off = 16; off > 0; off >>= 1) {
+    double y = __shfl_down_sync(0xffffffffu, x, off);
+    x = (y > x || y != y) ? y : x;  // NaN wins
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = x;
+  __syncthreads();
+  double r = 0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r = (sh[i] > r || sh[i] != sh[i]) ? sh[i] : r;
+  __syncthreads();
+  return r;
+}
+
+__global__ void denom_update_kernel(z* __restrict__ t1, z* __restrict__ t2, z* __restrict__ S1,
+                                    z* __restrict__ S2, const double* __restrict__ e, int o, int v, double shift,
+                                    double* partials) {
+  __shared__ double sh[32];
+  const int64_t n1 = (int64_t)o * v, n2 = (int64_t)o * o * v * v;
+  double mx = 0.0, s2 = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n1 + n2;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    if (k < n1) {
+      const int a = (int)(k % v), i = (int)(k / v);
+      const double D = e[i] - (e[o + a] + shift);
+      z d = S1[k];
+      d.x /= D;
+      d.y /= D;
+      t1[k] = zadd(t1[k], d);
+      S1[k] = d;
+      const double m2 = d.x * d.x + d.y * d.y;
+      const double am = sqrt(m2);
+      mx = (am > mx || am != am) ? am : mx;
+      s2 += m2;
+    } else {
+      const int64_t q = k - n1;
+      const int b = (int)(q % v), a = (int)((q / v) % v);
+      const int j = (int)((q / ((int64_t)v * v)) % o), i = (int)(q / ((int64_t)v * v * o));
+      const double D = e[i] + e[j] - (e[o + a] + shift) - (e[o + b] + shift);
+      z d = S2[q];
+      d.x /= D;
+      d.y /= D;
+      t2[q] = zadd(t2[q], d);
+      S2[q] = d;
+      const double m2 = d.x * d.x + d.y * d.y;
+      const double am = sqrt(m2);
+      mx = (am > mx || am != am) ? am : mx;
+      if (i < j && a < b) s2 += m2;
+    }
+  }
+  const double bm = block_reduce_max(mx, sh);
+  const double bs = block_reduce_sum(s2, sh);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = bm;
+    partials[2 * blockIdx.x + 1] = bs;
+  }
+}
+
+__global__ void norm_finalize_kernel(const double* partials, int nb, double* stats) {
+  __shared__ double sh[32];
+  double mx = 0.0, s = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    const double m = partials[2 * i];
+    mx = (m > mx || m != m) ? m : mx;
+    s += partials[2 * i + 1];
+  }
+  const double bm = block_reduce_max(mx, sh);
+  const double bs = block_reduce_sum(s, sh);
+  if (threadIdx.x == 0) {
+    stats[0] = bm;
+    stats[1] = sqrt(bs);
+  }
+}
+
+// ---- energy ----------------------------------------------------------------
+
+__global__ void energy_kernel(const z* __restrict__ fov, const z* __restrict__ oovv, const z* __restrict__ t1,
+                              const z* __restrict__ t2, int o, int v, z* partials) {
+  __shared__ double sh[32];
+  const int64_t n1 = (int64_t)o * v, n2 = (int64_t)o * o * v * v;
+  double er = 0.0, ei = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n1 + n2;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    z p;
+    if (k < n1) {
+      p = zmul(fov[k], t1[k]);
+    } else {
+      const int64_t q = k - n1;
+      const int b = (int)(q % v), a = (int)((q / v) % v);
+      const int j = (int)((q / ((int64_t)v * v)) % o), i = (int)(q / ((int64_t)v * v * o));
+      z tau = zadd(t2[q], zsub(zmul(t1[(int64_t)i * v + a], t1[(int64_t)j * v + b]),
+                               zmul(t1[(int64_t)j * v + a], t1[(int64_t)i * v + b])));
+      p = zscale(0.25, zmul(oovv[q], tau));
+    }
+    er += p.x;
+    ei += p.y;
+  }
+  er = block_reduce_sum(er, sh);
+  ei = block_reduce_sum(ei, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = make_double2(er, ei);
+}
+
+__global__ void energy_finalize_kernel(const z* partials, int nb, z* out) {
+  __shared__ double sh[32];
+  double er = 0.0, ei = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    er += partials[i].x;
+    ei += partials[i].y;
+  }
+  er = block_reduce_sum(er, sh);
+  ei = block_reduce_sum(ei, sh);
+  if (threadIdx.x == 0) *out = make_double2(er, ei);
+}
+
+// ---- DIIS ------------------------------------------------------------------
+
+// Unique-element index k in [0, L) -> position in the full t1 / t2 arrays.
+__device__ __forceinline__ int64_t unique_to_full(int64_t k, int o, int v) {
+  const int64_t n1 = (int64_t)o * v;
+  if (k < n1) return k;
+  const int64_t q = k - n1, Pv = pair_count(v);
+  int64_t i, j, a, b;
+  pair_decode(q / Pv, o, i, j);
+  pair_decode(q % Pv, v, a, b);
+  return n1 + ((i * o + j) * v + a) * v + b;
+}
+
+__global__ void diis_push_kernel(DiisArgs d, const z* __restrict__ t1, const z* __restrict__ t2,
+                                 const z* __restrict__ e1, const z* __restrict__ e2) {
+  const int slot = d.state->head;
+  const int64_t n1 = (int64_t)d.o * d.v;
+  z* ht = d.hist_t + slot * d.L;
+  z* he = d.hist_e + slot * d.L;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < d.L;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t f = unique_to_full(k, d.o, d.v);
+    ht[k] = f < n1 ? t1[f] : t2[f - n1];
+    he[k] = f < n1 ? e1[f] : e2[f - n1];
+  }
+}
+
+// Re <e_new, e_slot> for every stored slot; per-block partials [slot][block].
+__global__ void diis_dots_kernel(DiisArgs d) {
+  __shared__ double sh[32];
+  const int newslot = d.state->head;
+  const int count = d.state->count + 1 > d.m ? d.m : d.state->count + 1;
+  const z* en = d.hist_e + newslot * d.L;
+  for (int s = 0; s < count; ++s) {
+    const z* es = d.hist_e + s * d.L;
+    double acc = 0.0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < d.L;
+         k += (int64_t)gridDim.x * blockDim.x) {
+      const z x = en[k], y = es[k];
+      acc += x.x * y.x + x.y * y.y;
+    }
+    acc = block_reduce_sum(acc, sh);
+    if (threadIdx.x == 0) d.partials[s * gridDim.x + blockIdx.x] = acc;
+  }
+}
+
+// One block: finish the dots, advance the ring buffer, and (if due) solve
+// [[B, 1], [1^T, 0]] [c; lam] = [0; 1] by LU with partial pivoting in age order.
+__global__ void diis_solve_kernel(DiisArgs d, int nb) {
+  __shared__ double sh[32];
+  __shared__ double M[17][18];
+  DiisState* st = d.state;
+  const int newslot = st->head;
+  const int count = st->count + 1 > d.m ? d.m : st->count + 1;
+  for (int s = 0; s < count; ++s) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += d.partials[s * nb + i];
+    acc = block_reduce_sum(acc, sh);
+    if (threadIdx.x == 0) {
+      d.Bmat[newslot * d.m + s] = acc;
+      d.Bmat[s * d.m + newslot] = acc;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  st->count = count;
+  st->head = (newslot + 1) % d.m;
+  st->iter += 1;
+  st->used = 0;
+  if (st->iter < d.start || count < 2) return;
+  // age order: oldest slot first
+  const int oldest = (st->head - count + d.m) % d.m;
+  const int n = count + 1;
+  for (int r = 0; r < count; ++r) {
+    const int sr = (oldest + r) % d.m;
+    for (int c = 0; c < count; ++c) M[r][c] = d.Bmat[sr * d.m + (oldest + c) % d.m];
+    M[r][count] = 1.0;
+    M[r][n] = 0.0;
+  }
+  for (int c = 0; c < count; ++c) M[count][c] = 1.0;
+  M[count][count] = 0.0;
+  M[count][n] = 1.0;
+  for (int k = 0; k < n; ++k) {
+    int piv = k;
+    double best = fabs(M[k][k]);
+    for (int r = k + 1; r < n; ++r)
+      if (fabs(M[r][k]) > best) { best = fabs(M[r][k]); piv = r; }
+    if (piv != k)
+      for (int c = 0; c <= n; ++c) { double tmp = M[k][c]; M[k][c] = M[piv][c]; M[piv][c] = tmp; }
+    const double dkk = M[k][k];
+    if (dkk == 0.0) return;  // singular subspace: keep the plain update
+    for (int r = k + 1; r < n; ++r) {
+      const double f = M[r][k] / dkk;
+      for (int c = k; c <= n; ++c) M[r][c] -= f * M[k][c];
+    }
+  }
+  double x[17];
+  for (int r = n - 1; r >= 0; --r) {
+    double s = M[r][n];
+    for (int c = r + 1; c < n; ++c) s -= M[r][c] * x[c];
+    x[r] = s / M[r][r];
+  }
+  for (int r = 0; r < count; ++r) d.coef[r] = x[r];
+  st->used = 1;
+}
+
+// t = sum_r coef[r] * hist_t[slot(r)], written to the full t1 / t2 (antisymmetric fill).
+__global__ void diis_combine_kernel(DiisArgs d, z* __restrict__ t1, z* __restrict__ t2) {
+  const DiisState st = *d.state;
+  if (!st.used) return;
+  const int oldest = (st.head - st.count + d.m) % d.m;
+  const int64_t n1 = (int64_t)d.o * d.v, n2 = (int64_t)d.o * d.o * d.v * d.v;
+  const int64_t Pv = pair_count(d.v);
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n1 + n2;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    int64_t u;
+    double sgn = 1.0;
+    bool zero = false;
+    if (k < n1) {
+      u = k;
+    } else {
+      const int64_t q = k - n1;
+      const int64_t b = q % d.v, a = (q / d.v) % d.v;
+      const int64_t j = (q / ((int64_t)d.v * d.v)) % d.o, i = q / ((int64_t)d.v * d.v * d.o);
+      if (i == j || a == b) zero = true;
+      int64_t pij = 0, pab = 0;
+      if (!zero) {
+        if (i < j) pij = pair_index(i, j, d.o); else { pij = pair_index(j, i, d.o); sgn = -sgn; }
+        if (a < b) pab = pair_index(a, b, d.v); else { pab = pair_index(b, a, d.v); sgn = -sgn; }
+      }
+      u = n1 + pij * Pv + pab;
+    }
+    z acc = make_double2(0.0, 0.0);
+    if (!zero)
+      for (int r = 0; r < st.count; ++r) {
+        const double c = d.coef[r];
+        const z h = d.hist_t[((oldest + r) % d.m) * d.L + u];
+        acc.x += c * h.x;
+        acc.y += c * h.y;
+      }
+    acc = zscale(sgn, acc);
+    if (k < n1) t1[k] = acc; else t2[k - n1] = acc;
+  }
+}
+
+__global__ void diis_reset_kernel(DiisState* st) {
+  st->count = 0;
+  st->head = 0;
+  st->iter = 0;
+  st->used = 0;
+}
+
+}  // namespace
+
+// ---- launchers -----------------------------------------------------------------
+
+cudaError_t zscale_matrix(const ZGemmArgs& g, cudaStream_t s) {
+  zscale_kernel<<<grid_for(g.M * g.N * g.batch, kThreads), kThreads, 0, s>>>(g.C, g.M, g.N, g.ldc, g.sC, g.batch,
+                                                                                g.beta);
+  return cudaGetLastError();
+}
+
+cudaError_t permute_add(const PermuteArgs& a, cudaStream_t s) {
+  if (a.rank < 1 || a.rank > kMaxRank) return cudaErrorInvalidValue;
+  int64_t total = 1;
+  for (int d = 0; d < a.rank; ++d) total *= a.dims[d];
+  if (total == 0) return cudaSuccess;
+  const int q = a.rank - 1;
+  int p = -1;
+  if (a.istr[q] != 1 && a.dims[q] > 1)
+    for (int d = 0; d < q; ++d)
+      if (a.istr[d] == 1 && a.dims[d] > 1) p = d;
+  if (p < 0) {
+    permute_direct_kernel<<<grid_for(total, kThreads), kThreads, 0, s>>>(a, total);
+  } else {
+    const int64_t tp = (a.dims[p] + 31) / 32, tq = (a.dims[q] + 31) / 32;
+    const int64_t nrest = total / (a.dims[p] * a.dims[q]);
+    int64_t gx = tp * tq;
+    if (gx > 4096) gx = 4096;
+    int64_t gy = nrest;
+    if (gy > 65535) gy = 65535;
+    permute_tiled_kernel<<<dim3((unsigned)gx, (unsigned)gy), dim3(32, 8), 0, s>>>(a, p, nrest, tp, tq);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t tau_build(const z* t1, const z* t2, z* out, int o, int v, double c2, double c11, int anti,
+                      cudaStream_t s) {
+  const int64_t total = (int64_t)o * o * v * v;
+  tau_kernel<<<grid_for(total, kThreads), kThreads, 0, s>>>(t1, t2, out, o, v, c2, c11, anti);
+  return cudaGetLastError();
+}
+
+cudaError_t pack_pairs(const z* in, z* out, int64_t n1, int64_t n2, int pack_rows, cudaStream_t s) {
+  const int64_t total = (pack_rows ? pair_count(n1) : n1) * pair_count(n2);
+  if (total == 0) return cudaSuccess;
+  pack_pairs_kernel<<<grid_for(total, kThreads), kThreads, 0, s>>>(in, out, n1, n2, pack_rows);
+  return cudaGetLastError();
+}
+
+cudaError_t unpack_pairs(const UnpackArgs& a, cudaStream_t s) {
+  const int64_t total = (a.unpack_rows ? a.n1 * a.n1 : a.n1) * a.n2 * a.n2;
+  if (total == 0) return cudaSuccess;
+  unpack_pairs_kernel<<<grid_for(total, kThreads), kThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t pack_vvvv(const z* D, z* W, int64_t v, cudaStream_t s) {
+  const int64_t P = pair_count(v);
+  if (P == 0) return cudaSuccess;
+  pack_vvvv_kernel<<<grid_for(P * P, kThreads), kThreads, 0, s>>>(D, W, v);
+  return cudaGetLastError();
+}
+
+int update_blocks() { return kUpdateBlocks; }
+
+cudaError_t denom_update(z* t1, z* t2, z* S1, z* S2, const double* e, int o, int v, double shift,
+                         double* partials, cudaStream_t s) {
+  denom_update_kernel<<<kUpdateBlocks, kThreads, 0, s>>>(t1, t2, S1, S2, e, o, v, shift, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t norm_finalize(const double* partials, int nblocks, double* stats, cudaStream_t s) {
+  norm_finalize_kernel<<<1, 1024, 0, s>>>(partials, nblocks, stats);
+  return cudaGetLastError();
+}
+
+int energy_blocks() { return kEnergyBlocks; }
+
+cudaError_t energy_eval(const z* fov, const z* oovv, const z* t1, const z* t2, int o, int v, z* partials,
+                        z* e_out, cudaStream_t s) {
+  energy_kernel<<<kEnergyBlocks, kThreads, 0, s>>>(fov, oovv, t1, t2, o, v, partials);
+  energy_finalize_kernel<<<1, 1024, 0, s>>>(partials, kEnergyBlocks, e_out);
+  return cudaGetLastError();
+}
+
+int diis_blocks() { return kDiisBlocks; }
+
+cudaError_t diis_reset(const DiisArgs& d, cudaStream_t s) {
+  diis_reset_kernel<<<1, 1, 0, s>>>(d.state);
+  return cudaGetLastError();
+}
+
+cudaError_t diis_step(const DiisArgs& d, z* t1, z* t2, const z* e1, const z* e2, cudaStream_t s) {
+  if (d.m < 1 || d.m > 16) return cudaErrorInvalidValue;
+  diis_push_kernel<<<grid_for(d.L, kThreads), kThreads, 0, s>>>(d, t1, t2, e1, e2);
+  diis_dots_kernel<<<kDiisBlocks, kThreads, 0, s>>>(d);
+  diis_solve_kernel<<<1, 1024, 0, s>>>(d, kDiisBlocks);
+  const int64_t n = (int64_t)d.o * d.v + (int64_t)d.o * d.o * d.v * d.v;
+  diis_combine_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(d, t1, t2);
+  return cudaGetLastError();
+}
+
+}  // namespace ccsd

@@ -1,0 +1,99 @@
+"""Host-side checks of the C ABI (no GPU needed).
+
+The library must build for sm_103a, load, and export every entry point that
+include/ccsd.h declares; argument errors are reported as status codes before
+any device work.
+"""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2103_08473_gb300 import build, ccsd
+    path = build.build()
+    return ccsd.load(path)
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(ccsd_\w+)\s*\(", text))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("ccsd_create", "ccsd_residual", "ccsd_iterate", "ccsd_energy", "ccsd_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2103_08473_gb300 import ccsd
+    bound = {name for name, _, _ in ccsd.SIGNATURES}
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert name in bound, f"{name} has no binding signature"
+
+
+def test_default_opts(lib):
+    from paper_2103_08473_gb300 import ccsd
+    o = ccsd.default_opts()
+    assert o.max_iter == 50 and o.diis_dim == 8 and o.diis_start == 2 and o.tol == 1e-10 and o.store_w == 1
+
+
+def _create(lib, o, v, eps, B, naux, opts=None):
+    from paper_2103_08473_gb300 import ccsd
+    h = C.c_void_p()
+    st = lib.ccsd_create(o, v, eps.ctypes.data_as(C.c_void_p) if eps is not None else None, None, 0,
+                         B.ctypes.data_as(C.c_void_p) if B is not None else None, naux,
+                         C.byref(opts) if opts is not None else None, C.byref(h))
+    return st, h
+
+
+@pytest.mark.parametrize("case", ["o0", "v0", "naux0", "null_eps", "null_ints", "nonhermitian", "diis17"])
+def test_create_rejects_bad_arguments(lib, case):
+    from paper_2103_08473_gb300 import ccsd, inputs
+    s = inputs.make_system(2, 3, 4, seed=1)
+    eps, B, o, v, naux = s.eps, s.B.copy(), 2, 3, 4
+    opts = None
+    if case == "o0":
+        o = 0
+    elif case == "v0":
+        v = 0
+    elif case == "naux0":
+        naux = 0
+    elif case == "null_eps":
+        eps = None
+    elif case == "null_ints":
+        B = None
+    elif case == "nonhermitian":
+        B[1, 0, 2] += 1e-6
+    elif case == "diis17":
+        opts = ccsd.default_opts(diis_dim=17)
+    st, h = _create(lib, o, v, eps, B, naux, opts)
+    assert st == ccsd.ERR_ARG
+    assert not h.value
+    assert len(lib.ccsd_last_error(None)) > 0
+
+
+def test_null_context_calls_return_arg_error(lib):
+    from paper_2103_08473_gb300 import ccsd
+    assert lib.ccsd_iterate(None, 1, None, None) == ccsd.ERR_ARG
+    assert lib.ccsd_energy(None, None) == ccsd.ERR_ARG
+    lib.ccsd_destroy(None)
+
+
+def test_binding_fails_loudly_without_library(tmp_path):
+    from paper_2103_08473_gb300 import ccsd
+    with pytest.raises(OSError):
+        ccsd.load(str(tmp_path / "missing.so"))
