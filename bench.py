@@ -1,0 +1,314 @@
+#!/usr/bin/env python
+"""Benchmark one CCSD iteration on the GPU (and the CPU oracle as the reference arm).
+
+A step is one full CCSD iteration: the Appendix A residual (all contractions,
+ladder included), the denominator update, the norms and DIIS, replayed as one
+CUDA graph through the C ABI (ccsd_iterate). Default workload: o = 20 occupied,
+v = 120 virtual spinors, naux = 400 DF functions (seeded synthetic system),
+complex FP64, <ab||cd> stored packed. The iteration uses a 20 Eh level shift in
+the denominators (the paper's remedy for hard-to-converge cases) so that every
+timed iteration stays finite on this strongly correlated synthetic system; the
+work per iteration does not depend on it.
+
+Printed JSON line: value = seconds per CCSD iteration (lower is better), the
+ladder GEMM roofline against the FP64 peak, the end-to-end time through host
+buffers, the oracle's CPU time per iteration, clocks during the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--config c2|c1]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "c2": dict(o=20, v=120, naux=400, seed=2, level_shift=20.0,
+               name="ccsd_fp64_o20_v120_naux400_storedW"),
+    "c1": dict(o=10, v=30, naux=120, seed=1, level_shift=0.0,
+               name="ccsd_fp64_o10_v30_naux120"),
+}
+METRIC = "CCSD iteration time (s)"
+FP64_OVER_BF16_NOMINAL = 1.25 / 2250.0  # dense FP64 vs dense BF16 tensor rate (nominal)
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def recorded_traffic(kernel_file: str, key: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
+    prof = os.path.join(ROOT, "profiles", "traffic.txt")
+    src = os.path.join(ROOT, "paper_2103_08473_gb300", "csrc", kernel_file)
+    if not (os.path.exists(prof) and os.path.exists(src)):
+        return None
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    for line in open(prof):
+        parts = line.split()
+        if len(parts) >= 3 and parts[0] == key and parts[1] == digest:
+            return float(parts[2])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            cols = [c.strip() for c in line.split(",")]
+            if len(cols) < 9:
+                continue
+            try:
+                sm.append(float(cols[1]))
+                smax.append(float(cols[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, cols[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def oracle_iteration_time(wl, steps: int = 1):
+    """Time the CPU oracle on the same workload: integrals untimed, then `steps` full iterations."""
+    import numpy as np
+    from oracle import ccsd_ref as R
+    from paper_2103_08473_gb300 import inputs
+
+    s = inputs.make_system(wl["o"], wl["v"], wl["naux"], wl["seed"])
+    f = R.fock_matrix(s.eps)
+    V = R.integrals(s.B, s.o)
+    D1, D2 = R.denominators(f, s.o, wl["level_shift"])
+    t1, t2 = inputs.random_amplitudes(s.o, s.v, wl["seed"] + 77, scale=0.01)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        S1, S2 = R.residual(f, V, t1, t2)
+        d1, d2 = S1 / D1, S2 / D2
+        t1, t2 = t1 + d1, t2 + d2
+        _ = max(np.max(np.abs(d1)), np.max(np.abs(d2)))
+        times.append(time.perf_counter() - t0)
+    return times
+
+
+def run_reference(args, wl):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    total = args.warmup + args.steps
+    times = oracle_iteration_time(wl, total)[args.warmup:]
+    value = sum(times) / len(times)
+    cores = os.cpu_count()
+    sample = (f"{args.steps} full oracle iterations (Appendix A residual + denominator update, numpy complex128 "
+              f"einsum) of the {wl['name']} workload after {args.warmup} warm-up iterations; integrals untimed")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["name"], "o": wl["o"], "v": wl["v"], "naux": wl["naux"],
+                       "level_shift": wl["level_shift"]},
+            "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, wl):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2103_08473_gb300 import build, flops, inputs
+    from paper_2103_08473_gb300 import ccsd as ccmod
+
+    ccmod.load(build.build())
+    s = inputs.make_system(wl["o"], wl["v"], wl["naux"], wl["seed"])
+    o, v = s.o, s.v
+    stream = torch.cuda.Stream()  # a real stream: the library captures its iteration graph on it
+    cc = ccmod.CCSD(o, v, s.eps, B=s.B, level_shift=wl["level_shift"], tol=0.0, diis_dim=8, profile=1,
+                    stream=stream.cuda_stream)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        st, _, _ = cc.iterate(1)
+        if st == ccmod.ERR_DIVERGED:
+            raise RuntimeError("iteration diverged during warm-up")
+    cc.timings()  # reset the per-op averages
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        st, _, _ = cc.iterate(1)
+        if st == ccmod.ERR_DIVERGED:
+            raise RuntimeError("iteration diverged in the timed region")
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ops = cc.timings()
+    kernels = int(cc.query("kernels_per_iteration"))
+
+    # end to end through the C ABI with host buffers: H2D of the step's amplitudes from pinned
+    # memory, the iteration, D2H of the norm and the energy
+    t1h = torch.empty((o, v), dtype=torch.complex128, pin_memory=True)
+    t2h = torch.empty((o, o, v, v), dtype=torch.complex128, pin_memory=True)
+    cc.get_amplitudes((t1h.numpy(), t2h.numpy()))
+    e2e_steps = max(2, args.steps)
+    barrier()
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        cc.set_amplitudes(t1h.numpy(), t2h.numpy())
+        cc.iterate(1)
+        cc.energy()
+    torch.cuda.synchronize()
+    e2e = (time.perf_counter() - w0) / e2e_steps
+    cc.timings()
+    h2d = 16 * (o * v + o * o * v * v)
+    d2h = 16 + 16
+
+    if rank != 0:
+        cc.close()
+        return
+    value = ms / 1e3 / args.steps / world
+    peaks, peak_kind = load_peaks()
+    fp64_peak = peaks["bf16_tflops_sustained"] * FP64_OVER_BF16_NOMINAL
+    opd = {}
+    for name, t in ops:
+        opd[name] = opd.get(name, 0.0) + t
+    lad_ms = opd.get("ladder:gemm")
+    lad_fl = flops.ladder_flops_packed(o, v)
+    lad_tf = lad_fl / (lad_ms * 1e-3) / 1e12 if lad_ms else None
+    gemm_ms = sum(t for n, t in opd.items() if n.endswith(":gemm"))
+    total_op_ms = sum(opd.values())
+    roofline = {"kernel": "zgemm_dmma_kernel (ladder launch, M=o(o-1)/2, N=K=v(v-1)/2)", "bound": "tensor",
+                "achieved": lad_tf, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": (lad_tf / fp64_peak) if lad_tf else None,
+                "peak_basis": f"{peak_kind} bf16_tflops_sustained x 1.25/2250 (nominal dense FP64/BF16 ratio)",
+                "algorithmic_flops_per_launch": lad_fl, "launch_ms": lad_ms,
+                "traffic": recorded_traffic("zgemm_f64.cu", f"ladder_{wl['name']}")}
+    top = sorted(opd.items(), key=lambda kv: -kv[1])[:8]
+    cores = os.cpu_count()
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        ct = oracle_iteration_time(wl, 1)
+        cpu = {"value": ct[0], "unit": "s", "cores": cores, "kind": "oracle",
+               "sample": f"one full oracle iteration (Appendix A residual + update, numpy complex128) of the "
+                         f"{wl['name']} workload, integrals untimed"}
+    line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["name"], "o": o, "v": v, "naux": wl["naux"], "precision": "fp64",
+                       "store_w": True, "level_shift": wl["level_shift"], "diis_dim": 8,
+                       "l2": "inputs larger than L2 (packed <ab||cd> 816 MB, vovv 553 MB at o20/v120)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "ladder_tflops": lad_tf,
+            "gemm_share_of_iteration": gemm_ms / total_op_ms if total_op_ms else None,
+            "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "clocks": clocks, "gpu_launches": kernels * args.steps,
+            "top_ops_ms": {k: round(t, 4) for k, t in top}}
+    print(json.dumps(line), flush=True)
+    cc.close()
+
+
+def residual_once(wl):
+    """One eager residual on the workload (NVTX range per op, e.g. "ladder_gemm")."""
+    from paper_2103_08473_gb300 import build, inputs
+    from paper_2103_08473_gb300 import ccsd as ccmod
+
+    ccmod.load(build.build())
+    s = inputs.make_system(wl["o"], wl["v"], wl["naux"], wl["seed"])
+    with ccmod.CCSD(s.o, s.v, s.eps, B=s.B, level_shift=wl["level_shift"]) as cc:
+        cc.residual()
+    print("residual evaluated", flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", choices=sorted(WORKLOADS), default="c2")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--residual-once", action="store_true",
+                    help="create the context and evaluate one residual eagerly (for ncu captures), no timing")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)  # timing rule: at least 3 untimed warm-up steps
+    wl = WORKLOADS[args.config]
+    if args.residual_once:
+        residual_once(wl)
+    elif args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    main()

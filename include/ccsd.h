@@ -141,11 +141,36 @@ ccsd_status ccsd_set_amplitudes(ccsd_ctx* ctx, const ccsd_z* t1, const ccsd_z* t
 ccsd_status ccsd_get_tensor(ccsd_ctx* ctx, const char* name, ccsd_z* out, size_t count, int on_device);
 
 /*
- * Per-term device timings of the last residual (opts.profile = 1): writes up to
- * `cap` (name, milliseconds) pairs; *n receives the number of terms. Names are
- * static strings owned by the library.
+ * Per-op device timings (opts.profile = 1): CUDA events recorded between the
+ * ops of the residual plan and the update / norm / DIIS steps, inside the
+ * iteration's CUDA graph. Writes up to `cap` (name, average milliseconds per
+ * evaluation) pairs, averaged over the evaluations since the previous call,
+ * and resets the averages (cap <= 0 only queries *n). *n receives the number
+ * of timed segments (0 if nothing was timed). Names are owned by the context.
  */
 ccsd_status ccsd_timings(ccsd_ctx* ctx, const char** names, double* ms, int cap, int* n);
+
+/*
+ * Scalar facts about a context: "kernels_per_iteration" (kernel nodes of the
+ * iteration graph), "device_bytes" (device memory held), "iterations_run",
+ * "plan_ops", "o", "v". CCSD_ERR_ARG for an unknown key.
+ */
+ccsd_status ccsd_query(const ccsd_ctx* ctx, const char* key, double* value);
+
+/*
+ * The engine's complex GEMM on device pointers (row-major, complex double):
+ *   C = alpha * opA(A) * opB(B) + beta * C
+ * opA(A)(m,k) = transA ? A[k*lda + m] : A[m*lda + k], conjugated if conjA; likewise B
+ * with (k,n) = transB ? B[n*ldb + k] : B[k*ldb + n]. precision: CCSD_PREC_FP64 (FP64
+ * tensor-core path). cfg < 0 picks the tile shape, cfg >= 0 forces one (0..6). The
+ * optional workspace (ws_elems complex elements, device) enables split-K for small
+ * outputs; without it the GEMM does not split. Synchronous on `stream`.
+ * CCSD_ERR_ARG for negative sizes, NULL pointers or a bad cfg.
+ */
+ccsd_status ccsd_zgemm(int precision, int transA, int conjA, int transB, int conjB, long long M, long long N,
+                       long long K, ccsd_z alpha, const ccsd_z* A, long long lda, const ccsd_z* B, long long ldb,
+                       ccsd_z beta, ccsd_z* C, long long ldc, ccsd_z* workspace, size_t ws_elems, int cfg,
+                       void* stream);
 
 /* Message for the last failing call on ctx (or of the last failed create when ctx is NULL). */
 const char* ccsd_last_error(const ccsd_ctx* ctx);

@@ -52,6 +52,10 @@ SIGNATURES = [
     ("ccsd_set_amplitudes", C.c_int, [_P, _P, _P, C.c_int]),
     ("ccsd_get_tensor", C.c_int, [_P, C.c_char_p, _P, C.c_size_t, C.c_int]),
     ("ccsd_timings", C.c_int, [_P, C.POINTER(C.c_char_p), C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int)]),
+    ("ccsd_query", C.c_int, [_P, C.c_char_p, C.POINTER(C.c_double)]),
+    ("ccsd_zgemm", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_longlong, C.c_longlong, C.c_longlong,
+                             ccsd_z, _P, C.c_longlong, _P, C.c_longlong, ccsd_z, _P, C.c_longlong, _P, C.c_size_t,
+                             C.c_int, _P]),
     ("ccsd_last_error", C.c_char_p, [_P]),
     ("ccsd_destroy", None, [_P]),
 ]
@@ -226,9 +230,35 @@ class CCSD:
         return out
 
     def timings(self):
+        """[(op name, average ms)] since the previous call (needs profile=1); resets the averages."""
         n = C.c_int(0)
         self._check(self._lib.ccsd_timings(self._h, None, None, 0, C.byref(n)))
+        if n.value == 0:
+            return []
         names = (C.c_char_p * n.value)()
         ms = (C.c_double * n.value)()
         self._check(self._lib.ccsd_timings(self._h, names, ms, n.value, C.byref(n)))
         return [(names[k].decode(), ms[k]) for k in range(n.value)]
+
+    def query(self, key):
+        val = C.c_double(0.0)
+        self._check(self._lib.ccsd_query(self._h, key.encode(), C.byref(val)))
+        return val.value
+
+
+
+def zgemm(a, b, c, alpha=1.0, beta=0.0, transA=False, conjA=False, transB=False, conjB=False,
+          precision=PREC_FP64, workspace=None, cfg=-1, stream=None):
+    """c = alpha opA(a) opB(b) + beta c on row-major torch CUDA complex128 matrices (c in place)."""
+    lib = load()
+    M, N = c.shape
+    K = a.shape[0] if transA else a.shape[1]
+    ws_ptr, ws_n = (None, 0) if workspace is None else (_ptr(workspace)[0], workspace.numel())
+    strm = None if stream is None else C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+    al, be = complex(alpha), complex(beta)
+    st = lib.ccsd_zgemm(int(precision), int(transA), int(conjA), int(transB), int(conjB), M, N, K,
+                        ccsd_z(al.real, al.imag), _ptr(a)[0], a.stride(0), _ptr(b)[0], b.stride(0),
+                        ccsd_z(be.real, be.imag), _ptr(c)[0], c.stride(0), ws_ptr, ws_n, int(cfg), strm)
+    if st != OK:
+        raise CCSDError(st, lib.ccsd_last_error(None).decode())
+    return c

@@ -2,9 +2,12 @@
 // plan, the denominator update + DIIS iteration (CUDA-graph replayed), energy,
 // amplitude checkpointing and inspection.
 #include <cmath>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "ccsd.h"
 #include "ops.h"
@@ -15,8 +18,6 @@ using namespace ccsd;
 
 namespace {
 thread_local std::string g_create_error;
-
-const char* kIntermediates[] = {"tau", "Hvv", "Gvv", "Hoo", "Goo", "Hov", "Hvoov", "C", "A", "ladder"};
 }  // namespace
 
 struct ccsd_ctx {
@@ -43,6 +44,8 @@ struct ccsd_ctx {
   z *C = nullptr, *Yovoo = nullptr, *Ypk = nullptr, *Yfull = nullptr;
   z *Afull = nullptr, *Yoooo = nullptr, *Apk = nullptr, *Lpk = nullptr, *Hpk = nullptr;
   z* scratch = nullptr;
+  z* gemm_ws = nullptr;  // split-K partials of the plan's GEMMs
+  int64_t gemm_ws_elems = 0;
   // iteration state
   double* upd_partials = nullptr;
   double* stats = nullptr;
@@ -53,9 +56,14 @@ struct ccsd_ctx {
   DiisArgs diis;
   Plan* plan = nullptr;
   cudaGraphExec_t graph = nullptr;
-  // profiling
+  // profiling: one event per op boundary, recorded inside the iteration graph
   std::vector<std::string> tnames;
-  std::vector<double> tms;
+  std::vector<cudaEvent_t> tev;
+  std::vector<double> tsum;
+  int tcount = 0;
+  int kernels_per_iter = 0;
+  int64_t device_bytes = 0;
+  int64_t iterations_run = 0;
 };
 
 namespace {
@@ -84,6 +92,7 @@ ccsd_status dalloc(ccsd_ctx* ctx, Tp** p, int64_t count) {
     return set_err(ctx, CCSD_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
   }
   ctx->allocs.push_back(m);
+  ctx->device_bytes += (int64_t)bytes;
   *p = (Tp*)m;
   return CCSD_OK;
 }
@@ -279,7 +288,14 @@ ccsd_status build_residual_plan(ccsd_ctx* ctx) {
   const int64_t Po = ctx->Po, Pv = ctx->Pv;
   Plan* P = new Plan(o, v, &ctx->scratch, ctx->stream);
   ctx->plan = P;
-  P->set_gemm([](const ZGemmArgs& g, cudaStream_t s) { return zgemm_f64(g, s); });
+  P->set_gemm(
+      [ctx](const ZGemmArgs& g, cudaStream_t s) {
+        ZGemmArgs h = g;
+        h.ws = ctx->gemm_ws;
+        h.ws_elems = ctx->gemm_ws_elems;
+        return zgemm_f64(h, s);
+      },
+      [](const ZGemmArgs& g) { return zgemm_f64_workspace(g); });
   const z one = zmake(1, 0), mone = zmake(-1, 0), half = zmake(0.5, 0);
   auto V = [&](z* p, const char* lab) { return P->view(p, lab, true); };
   auto W = [&](z* p, const char* lab) { return P->view(p, lab, false); };
@@ -463,53 +479,69 @@ ccsd_status build_residual_plan(ccsd_ctx* ctx) {
   for (void* m : P->owned()) ctx->allocs.push_back(m);
   P->owned().clear();
   CS(dalloc(ctx, &ctx->scratch, P->scratch_elems()));
-  (void)Po;
-  (void)Pv;
+  ctx->gemm_ws_elems = P->gemm_workspace_elems();
+  CS(dalloc(ctx, &ctx->gemm_ws, ctx->gemm_ws_elems));
   return CCSD_OK;
 }
 
-cudaError_t run_ops(ccsd_ctx* ctx, bool profile) {
+// Names of the timed segments: the plan's ops, then the iteration tail.
+void init_timers(ccsd_ctx* ctx) {
+  if (!ctx->tnames.empty()) return;
+  for (auto& op : ctx->plan->ops()) ctx->tnames.push_back(op.name);
+  for (const char* nm : {"update", "norm", "diis"}) ctx->tnames.push_back(nm);
+  ctx->tev.resize(ctx->tnames.size() + 1);
+  for (auto& e : ctx->tev) cudaEventCreate(&e);
+  ctx->tsum.assign(ctx->tnames.size(), 0.0);
+  ctx->tcount = 0;
+}
+
+cudaError_t mark(ccsd_ctx* ctx, bool timed, size_t k) {
+  if (!timed) return cudaSuccess;
+  return cudaEventRecordWithFlags(ctx->tev[k], ctx->stream, cudaEventRecordExternal);
+}
+
+// Runs the plan in order; each op sits in an NVTX range named after it (':' -> '_'),
+// so a profiler can select one op's launches in an eager evaluation.
+cudaError_t run_ops(ccsd_ctx* ctx, bool timed) {
   auto& ops = ctx->plan->ops();
-  if (!profile) {
-    for (auto& op : ops) {
-      cudaError_t e = op.run(ctx->stream);
-      if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+  cudaError_t e = mark(ctx, timed, 0);
+  for (size_t k = 0; k < ops.size() && e == cudaSuccess; ++k) {
+    std::string nm = ops[k].name;
+    std::replace(nm.begin(), nm.end(), ':', '_');
+    nvtxRangePushA(nm.c_str());
+    e = ops[k].run(ctx->stream);
+    nvtxRangePop();
+    if (e == cudaSuccess) e = mark(ctx, timed, k + 1);
   }
-  std::vector<cudaEvent_t> ev(ops.size() + 1);
-  for (auto& e : ev) cudaEventCreate(&e);
-  cudaEventRecord(ev[0], ctx->stream);
-  for (size_t k = 0; k < ops.size(); ++k) {
-    cudaError_t e = ops[k].run(ctx->stream);
-    if (e != cudaSuccess) return e;
-    cudaEventRecord(ev[k + 1], ctx->stream);
-  }
-  cudaError_t e = cudaEventSynchronize(ev.back());
-  ctx->tnames.clear();
-  ctx->tms.clear();
-  for (size_t k = 0; k < ops.size(); ++k) {
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
-    ctx->tnames.push_back(ops[k].name);
-    ctx->tms.push_back(ms);
-  }
-  for (auto& x : ev) cudaEventDestroy(x);
   return e;
 }
 
+// Add the elapsed time of every completed segment [first, last) to the sums.
+void collect_timers(ccsd_ctx* ctx, size_t last) {
+  for (size_t k = 0; k < last; ++k) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->tev[k], ctx->tev[k + 1]) == cudaSuccess) ctx->tsum[k] += ms;
+  }
+  cudaGetLastError();
+  ctx->tcount += 1;
+}
+
 // One iteration: backup, residual, t <- t + S/D (S <- S/D), norms, DIIS.
-cudaError_t iteration_ops(ccsd_ctx* ctx, bool profile) {
+cudaError_t iteration_ops(ccsd_ctx* ctx, bool timed) {
   const int64_t n1 = (int64_t)ctx->o * ctx->v, n2 = n1 * ctx->o * ctx->v;
+  const size_t nops = ctx->plan->ops().size();
   cudaError_t e = cudaMemcpyAsync(ctx->t1_prev, ctx->t1, n1 * sizeof(z), cudaMemcpyDeviceToDevice, ctx->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(ctx->t2_prev, ctx->t2, n2 * sizeof(z), cudaMemcpyDeviceToDevice, ctx->stream);
-  if (e == cudaSuccess) e = run_ops(ctx, profile);
+  if (e == cudaSuccess) e = run_ops(ctx, timed);
   if (e == cudaSuccess)
     e = denom_update(ctx->t1, ctx->t2, ctx->S1, ctx->S2, ctx->dvec, ctx->o, ctx->v, ctx->opts.level_shift,
                      ctx->upd_partials, ctx->stream);
+  if (e == cudaSuccess) e = mark(ctx, timed, nops + 1);
   if (e == cudaSuccess) e = norm_finalize(ctx->upd_partials, update_blocks(), ctx->stats, ctx->stream);
+  if (e == cudaSuccess) e = mark(ctx, timed, nops + 2);
   if (e == cudaSuccess && ctx->opts.diis_dim > 0) e = diis_step(ctx->diis, ctx->t1, ctx->t2, ctx->S1, ctx->S2, ctx->stream);
+  if (e == cudaSuccess) e = mark(ctx, timed, nops + 3);
   return e;
 }
 
@@ -711,6 +743,7 @@ ccsd_status create_impl(int o, int v, const double* eps, const ccsd_z* fock, ccs
   }
 
   CS(build_residual_plan(ctx));
+  init_timers(ctx);
 
   // MP2 guess: one denominator update from t = 0
   CK(run_ops(ctx, false));
@@ -724,6 +757,7 @@ void free_ctx(ccsd_ctx* ctx) {
   if (!ctx) return;
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+  for (auto e : ctx->tev) cudaEventDestroy(e);
   for (void* p : ctx->allocs) cudaFree(p);
   if (ctx->plan) {
     for (void* p : ctx->plan->owned()) cudaFree(p);
@@ -780,7 +814,8 @@ ccsd_status ccsd_residual(ccsd_ctx* ctx, const ccsd_z* t1, const ccsd_z* t2, ccs
     CS(copy_in(ctx, ctx->t1, t1, n1, on_device));
     CS(copy_in(ctx, ctx->t2, t2, n2, on_device));
   }
-  CK(run_ops(ctx, ctx->opts.profile != 0));
+  const bool timed = ctx->opts.profile != 0;
+  CK(run_ops(ctx, timed));
   if (r1) CS(copy_out(ctx, r1, ctx->S1, n1, on_device));
   if (r2) CS(copy_out(ctx, r2, ctx->S2, n2, on_device));
   if (t1) {
@@ -788,23 +823,34 @@ ccsd_status ccsd_residual(ccsd_ctx* ctx, const ccsd_z* t1, const ccsd_z* t2, ccs
     CK(cudaMemcpyAsync(ctx->t2, ctx->t2_save, n2 * sizeof(z), cudaMemcpyDeviceToDevice, ctx->stream));
   }
   CK(cudaStreamSynchronize(ctx->stream));
+  if (timed) collect_timers(ctx, ctx->plan->ops().size());
   return CCSD_OK;
 }
 
 ccsd_status ccsd_iterate(ccsd_ctx* ctx, int max_iter, int* iters_done, double* res_norm) {
   if (!ctx) return CCSD_ERR_ARG;
   if (max_iter <= 0) max_iter = ctx->opts.max_iter;
-  const bool profile = ctx->opts.profile != 0;
-  if (!profile && !ctx->graph) {
+  const bool timed = ctx->opts.profile != 0;
+  if (!ctx->graph) {
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = iteration_ops(ctx, false);
+    cudaError_t e = iteration_ops(ctx, timed);
     cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
       cudaGetLastError();
       return set_err(ctx, CCSD_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
     }
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    cudaGraphGetNodes(g, nodes.data(), &nn);
+    int kern = 0;
+    for (auto nd : nodes) {
+      cudaGraphNodeType ty;
+      if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++kern;
+    }
+    ctx->kernels_per_iter = kern;
     e = cudaGraphInstantiate(&ctx->graph, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return set_err(ctx, CCSD_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
@@ -813,13 +859,11 @@ ccsd_status ccsd_iterate(ccsd_ctx* ctx, int max_iter, int* iters_done, double* r
   double nrm = INFINITY;
   ccsd_status st = CCSD_ERR_NOT_CONVERGED;
   for (it = 1; it <= max_iter; ++it) {
-    if (profile) {
-      CK(iteration_ops(ctx, true));
-    } else {
-      CK(cudaGraphLaunch(ctx->graph, ctx->stream));
-    }
+    CK(cudaGraphLaunch(ctx->graph, ctx->stream));
     CK(cudaMemcpyAsync(ctx->stats_host, ctx->stats, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    ctx->iterations_run += 1;
+    if (timed) collect_timers(ctx, ctx->tnames.size());
     nrm = ctx->opts.norm == 1 ? ctx->stats_host[1] : ctx->stats_host[0];
     if (!std::isfinite(ctx->stats_host[0]) || !std::isfinite(ctx->stats_host[1])) {
       const int64_t n1 = (int64_t)ctx->o * ctx->v, n2 = n1 * ctx->o * ctx->v;
@@ -913,18 +957,65 @@ ccsd_status ccsd_get_tensor(ccsd_ctx* ctx, const char* name, ccsd_z* out, size_t
   if ((int64_t)count != cnt) return set_err(ctx, CCSD_ERR_ARG, "count must be " + std::to_string(cnt) + " for " + nm);
   CS(copy_out(ctx, out, src, cnt, on_device));
   CK(cudaStreamSynchronize(ctx->stream));
-  (void)kIntermediates;
   return CCSD_OK;
 }
 
 ccsd_status ccsd_timings(ccsd_ctx* ctx, const char** names, double* ms, int cap, int* n) {
   if (!ctx) return CCSD_ERR_ARG;
-  const int cnt = (int)ctx->tnames.size();
+  const int cnt = ctx->tcount > 0 ? (int)ctx->tnames.size() : 0;
   if (n) *n = cnt;
+  if (cap <= 0) return CCSD_OK;
   for (int k = 0; k < cnt && k < cap; ++k) {
     if (names) names[k] = ctx->tnames[k].c_str();
-    if (ms) ms[k] = ctx->tms[k];
+    if (ms) ms[k] = ctx->tsum[k] / ctx->tcount;
   }
+  std::fill(ctx->tsum.begin(), ctx->tsum.end(), 0.0);
+  ctx->tcount = 0;
+  return CCSD_OK;
+}
+
+ccsd_status ccsd_query(const ccsd_ctx* ctx, const char* key, double* value) {
+  if (!ctx || !key || !value) return CCSD_ERR_ARG;
+  const std::string k(key);
+  if (k == "kernels_per_iteration") *value = ctx->kernels_per_iter;
+  else if (k == "device_bytes") *value = (double)ctx->device_bytes;
+  else if (k == "iterations_run") *value = (double)ctx->iterations_run;
+  else if (k == "plan_ops") *value = (double)ctx->plan->ops().size();
+  else if (k == "o") *value = ctx->o;
+  else if (k == "v") *value = ctx->v;
+  else return CCSD_ERR_ARG;
+  return CCSD_OK;
+}
+
+ccsd_status ccsd_zgemm(int precision, int transA, int conjA, int transB, int conjB, long long M, long long N,
+                       long long K, ccsd_z alpha, const ccsd_z* A, long long lda, const ccsd_z* B, long long ldb,
+                       ccsd_z beta, ccsd_z* C, long long ldc, ccsd_z* workspace, size_t ws_elems, int cfg,
+                       void* stream) {
+  ccsd_ctx* ctx = nullptr;
+  if (M < 0 || N < 0 || K < 0 || !A || !B || !C) return set_err(ctx, CCSD_ERR_ARG, "ccsd_zgemm: bad sizes or NULL");
+  if (cfg > 6) return set_err(ctx, CCSD_ERR_ARG, "ccsd_zgemm: cfg must be < 7");
+  if (precision != CCSD_PREC_FP64) return set_err(ctx, CCSD_ERR_UNSUPPORTED, "ccsd_zgemm: precision not built");
+  ZGemmArgs g;
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.A = (const z*)A;
+  g.lda = lda;
+  g.B = (const z*)B;
+  g.ldb = ldb;
+  g.C = (z*)C;
+  g.ldc = ldc;
+  g.alpha = zmake(alpha.re, alpha.im);
+  g.beta = zmake(beta.re, beta.im);
+  g.transA = transA != 0;
+  g.transB = transB != 0;
+  g.conjA = conjA != 0;
+  g.conjB = conjB != 0;
+  g.ws = (z*)workspace;
+  g.ws_elems = workspace ? (int64_t)ws_elems : 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(zgemm_f64(g, st, cfg));
+  CK(cudaStreamSynchronize(st));
   return CCSD_OK;
 }
 

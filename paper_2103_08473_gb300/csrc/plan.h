@@ -47,8 +47,10 @@ struct T {
   }
 };
 
-// Complex GEMM back end used by a plan (FP64 DMMA, or split precision).
+// Complex GEMM back end used by a plan (FP64 DMMA, or split precision), and the
+// workspace (complex elements) it wants for a shape.
 using GemmFn = std::function<cudaError_t(const ZGemmArgs&, cudaStream_t)>;
+using WsFn = std::function<int64_t(const ZGemmArgs&)>;
 
 struct Op {
   std::string name;
@@ -75,8 +77,13 @@ class Plan {
   // GEMM op on raw pointers through the plan's GEMM back end.
   void gemm(const std::string& name, const ZGemmArgs& g);
 
-  void set_gemm(GemmFn fn) { gemm_ = std::move(fn); }
+  void set_gemm(GemmFn fn, WsFn ws) {
+    gemm_ = std::move(fn);
+    wsfn_ = std::move(ws);
+  }
   const GemmFn& gemm_fn() const { return gemm_; }
+  // Largest GEMM workspace any op of the plan wants (complex elements).
+  int64_t gemm_workspace_elems() const { return ws_peak_; }
 
   std::vector<Op>& ops() { return ops_; }
   int64_t scratch_elems() const { return scratch_peak_; }
@@ -95,6 +102,8 @@ class Plan {
   z* const* scratch_base_;
   cudaStream_t setup_;
   GemmFn gemm_;
+  WsFn wsfn_;
+  int64_t ws_peak_ = 0;
   std::vector<Op> ops_;
   int64_t scratch_off_ = 0, scratch_peak_ = 0;
   std::map<std::string, T> const_cache_;

@@ -21,11 +21,17 @@ struct ZGemmArgs {
   int64_t ldc = 0, sC = 0;
   z alpha{1.0, 0.0}, beta{0.0, 0.0};
   int transA = 0, transB = 0, conjA = 0, conjB = 0;
+  // Split-K workspace (complex elements). GEMMs with too few output tiles to fill the GPU
+  // split K into S slices whose partial products go to ws and are summed in a fixed order.
+  z* ws = nullptr;
+  int64_t ws_elems = 0;
 };
 
 // FP64 tensor-core (DMMA) path. cfg < 0 picks the tile shape from the tile count.
 cudaError_t zgemm_f64(const ZGemmArgs& g, cudaStream_t s, int cfg = -1);
 int64_t zgemm_f64_tiles(const ZGemmArgs& g, int cfg);
+// Workspace (complex elements) zgemm_f64 wants for this shape to split K (0 if it does not split).
+int64_t zgemm_f64_workspace(const ZGemmArgs& g);
 // C[b] = beta * C[b] over the M x N (ldc) matrices (the K = 0 case).
 cudaError_t zscale_matrix(const ZGemmArgs& g, cudaStream_t s);
 

@@ -164,3 +164,26 @@ def test_device_buffers_through_torch(ccsd):
         r1, r2 = cc.residual(d1, d2)
         torch.cuda.synchronize()
     assert _maxrel(r1.cpu().numpy(), S1) < 1e-12 and _maxrel(r2.cpu().numpy(), S2) < 1e-12
+
+
+def test_full_size_o20_v120_residual_and_iterations(ccsd):
+    """The benchmarked workload (o20/v120/naux400, FP64, packed <ab||cd>): MP2 guess, the
+    residual at it element by element, and two level-shifted iterations, against the oracle."""
+    s = inputs.make_config("c2")
+    f = R.fock_matrix(s.eps)
+    V = R.integrals(s.B, s.o)
+    t1, t2 = R.mp2_guess(f, V, s.o, s.v, shift=20.0)
+    S1, S2 = R.residual(f, V, t1, t2)
+    with ccsd.CCSD(s.o, s.v, s.eps, B=s.B, level_shift=20.0, tol=0.0) as cc:
+        g1, g2 = cc.get_amplitudes()
+        assert _maxrel(g2, t2) < 1e-12 and _maxrel(g1, t1) < 1e-12
+        r1, r2 = cc.residual()
+        assert _maxrel(r1, S1) < 1e-12 and _maxrel(r2, S2) < 1e-12
+        e_mp2 = cc.energy()
+        assert abs(e_mp2 - R.energy(f, V, t1, t2)) < 1e-10
+        st, it, nrm = cc.iterate(2)
+        e2 = cc.energy()
+        h1, h2 = cc.get_amplitudes()
+    ref = R.solve(f, V, s.o, s.v, max_iter=2, tol=0.0, shift=20.0)
+    assert abs(e2 - ref["energy"]) < 1e-10
+    assert np.max(np.abs(h2 - ref["t2"])) < 1e-9 and np.max(np.abs(h1 - ref["t1"])) < 1e-9
