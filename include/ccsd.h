@@ -172,7 +172,39 @@ ccsd_status ccsd_zgemm(int precision, int transA, int conjA, int transB, int con
                        ccsd_z beta, ccsd_z* C, long long ldc, ccsd_z* workspace, size_t ws_elems, int cfg,
                        void* stream);
 
-/* Message for the last failing call on ctx (or of the last failed create when ctx is NULL). */
+/*
+ * ccsd_zgemm for callers that cannot allocate device memory. The paper has no
+ * counterpart: this is a service of the library, not a step of the method.
+ *
+ * Who needs it: callers that run inside another framework's memory budget (a
+ * caching allocator such as PyTorch's owns the device memory, and memory taken
+ * behind its back can make its own allocations fail), callers in a
+ * latency-critical loop (cudaMalloc / cudaFree can synchronise the device), and
+ * callers that must keep the device footprint they fixed at start-up. Such a
+ * caller cannot hand ccsd_zgemm a split-K workspace.
+ *
+ * Same arguments and result as ccsd_zgemm without the workspace: the split-K
+ * partials go to a fixed array of 2^18 complex doubles (4 MiB) that the library
+ * keeps in device memory; every GPU that loads the library holds it until the
+ * process exits. The call allocates nothing (no cudaMalloc, cudaFree or any
+ * allocating library routine). The first call on a device, with that device
+ * current, looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture. Limit: M*N <= 2^17 complex
+ * elements (at least two split partials must fit); larger outputs return
+ * CCSD_ERR_ARG with a message naming the limit (use ccsd_zgemm with a
+ * workspace for those). All calls share the one array and it keeps the last
+ * call's contents; nothing in it has to start at zero, because every partial a
+ * call reads it wrote itself earlier in that call. Calls that overlap on the
+ * GPU (different streams or host threads at the same time) race on the array:
+ * serialise them. Synchronous on `stream`; errors via ccsd_last_error(NULL).
+ */
+ccsd_status ccsd_zgemm_noalloc(int precision, int transA, int conjA, int transB, int conjB, long long M,
+                               long long N, long long K, ccsd_z alpha, const ccsd_z* A, long long lda,
+                               const ccsd_z* B, long long ldb, ccsd_z beta, ccsd_z* C, long long ldc, int cfg,
+                               void* stream);
+
+/* Message for the last failing call on ctx; with ctx NULL, of the last failed call made without a
+ * context (ccsd_create, ccsd_zgemm, ccsd_zgemm_noalloc) on this host thread. */
 const char* ccsd_last_error(const ccsd_ctx* ctx);
 
 /* Free every device buffer of the context. NULL is a no-op. */

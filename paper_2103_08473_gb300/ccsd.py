@@ -56,6 +56,9 @@ SIGNATURES = [
     ("ccsd_zgemm", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_longlong, C.c_longlong, C.c_longlong,
                              ccsd_z, _P, C.c_longlong, _P, C.c_longlong, ccsd_z, _P, C.c_longlong, _P, C.c_size_t,
                              C.c_int, _P]),
+    ("ccsd_zgemm_noalloc", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_longlong, C.c_longlong,
+                                     C.c_longlong, ccsd_z, _P, C.c_longlong, _P, C.c_longlong, ccsd_z, _P,
+                                     C.c_longlong, C.c_int, _P]),
     ("ccsd_last_error", C.c_char_p, [_P]),
     ("ccsd_destroy", None, [_P]),
 ]
@@ -259,6 +262,23 @@ def zgemm(a, b, c, alpha=1.0, beta=0.0, transA=False, conjA=False, transB=False,
     st = lib.ccsd_zgemm(int(precision), int(transA), int(conjA), int(transB), int(conjB), M, N, K,
                         ccsd_z(al.real, al.imag), _ptr(a)[0], a.stride(0), _ptr(b)[0], b.stride(0),
                         ccsd_z(be.real, be.imag), _ptr(c)[0], c.stride(0), ws_ptr, ws_n, int(cfg), strm)
+    if st != OK:
+        raise CCSDError(st, lib.ccsd_last_error(None).decode())
+    return c
+
+
+def zgemm_noalloc(a, b, c, alpha=1.0, beta=0.0, transA=False, conjA=False, transB=False, conjB=False,
+                  precision=PREC_FP64, cfg=-1, stream=None):
+    """ccsd_zgemm_noalloc: like zgemm, with the split-K partials in the library's fixed device array
+    (for callers that cannot allocate device memory). c is updated in place."""
+    lib = load()
+    M, N = c.shape
+    K = a.shape[0] if transA else a.shape[1]
+    strm = None if stream is None else C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+    al, be = complex(alpha), complex(beta)
+    st = lib.ccsd_zgemm_noalloc(int(precision), int(transA), int(conjA), int(transB), int(conjB), M, N, K,
+                                ccsd_z(al.real, al.imag), _ptr(a)[0], a.stride(0), _ptr(b)[0], b.stride(0),
+                                ccsd_z(be.real, be.imag), _ptr(c)[0], c.stride(0), int(cfg), strm)
     if st != OK:
         raise CCSDError(st, lib.ccsd_last_error(None).decode())
     return c

@@ -10,6 +10,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "ccsd.h"
+#include "errors.h"
 #include "ops.h"
 #include "plan.h"
 #include "zgemm.h"
@@ -19,6 +20,10 @@ using namespace ccsd;
 namespace {
 thread_local std::string g_create_error;
 }  // namespace
+
+namespace ccsd {
+void set_context_free_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace ccsd
 
 struct ccsd_ctx {
   int o = 0, v = 0, n = 0, naux = 0;
