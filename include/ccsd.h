@@ -85,10 +85,12 @@ typedef struct {
   int diis_start;     /* first iteration that extrapolates (default 2) */
   double level_shift; /* added to virtual orbital energies in the denominators only (default 0) */
   int precision;      /* ccsd_precision (default CCSD_PREC_FP64) */
-  int slices;         /* split precision: number of slices per operand (default 0 = automatic) */
+  int slices;         /* split precision: 4-bit e4m3 digits per operand, 1..14 (default 0 = 11) */
   int store_w;        /* 1: store <ab||cd> (packed); 0: rebuild ladder tiles from B (default 1) */
   int profile;        /* 1: record per-term CUDA-event timings (default 0) */
   void* stream;       /* cudaStream_t, NULL = legacy default stream */
+  double split_min_flops; /* split precision: contractions of at least this many flops (8 per complex
+                             multiply-add) run on the tensor cores; the ladder always does (default 2e10) */
 } ccsd_opts;
 
 /* Fill opts with the defaults listed above. */
@@ -171,6 +173,33 @@ ccsd_status ccsd_zgemm(int precision, int transA, int conjA, int transB, int con
                        long long K, ccsd_z alpha, const ccsd_z* A, long long lda, const ccsd_z* B, long long ldb,
                        ccsd_z beta, ccsd_z* C, long long ldc, ccsd_z* workspace, size_t ws_elems, int cfg,
                        void* stream);
+
+/*
+ * Split-precision complex GEMM (Ozaki-style digit slices on the tcgen05 tensor
+ * cores), same operation and layouts as ccsd_zgemm:
+ *   C = alpha * opA(A) * opB(B) + beta * C   (complex double in and out, device pointers)
+ * kind 0: e4m3 digits (kind::f8f6f4), bits <= 4; kind 1: bf16 digits (kind::f16), bits <= 8.
+ * Each row of opA(A) and each column of opB(B) is scaled by a power of two and cut into
+ * `slices` integer digits of `bits` bits; digit products of equal weight are summed
+ * exactly in FP32 tensor-memory accumulators over K ranges short enough to stay exact,
+ * and combined in FP64. Error ~ 2^(-bits*slices) relative to the row/column scales.
+ * workspace: device memory of at least ccsd_split_workspace(...) bytes. Synchronous on
+ * `stream`. CCSD_ERR_TIMEOUT if a bounded device wait gave up.
+ */
+size_t ccsd_split_workspace(int kind, int bits, int slices, long long M, long long N, long long K);
+ccsd_status ccsd_split_zgemm(int kind, int bits, int slices, int transA, int conjA, int transB, int conjB,
+                             long long M, long long N, long long K, ccsd_z alpha, const ccsd_z* A, long long lda,
+                             const ccsd_z* B, long long ldb, ccsd_z beta, ccsd_z* C, long long ldc,
+                             void* workspace, size_t ws_bytes, void* stream);
+
+/*
+ * Accumulation probe of the split GEMM's tensor-core path: C[m][n] = sum_k A[m][k] B[n][k]
+ * (real, row-major, device) for integer-valued A, B that fit the digit type of `kind`
+ * (|x| <= 16 for e4m3, <= 256 for bf16), accumulated in one FP32 TMEM accumulator over
+ * the whole K. Used to test that integer sums below 2^24 come out exact.
+ */
+ccsd_status ccsd_split_probe(int kind, long long M, long long N, long long K, const double* A, const double* B,
+                             double* C, void* workspace, size_t ws_bytes, void* stream);
 
 /*
  * ccsd_zgemm for callers that cannot allocate device memory. The paper has no

@@ -29,7 +29,8 @@ class ccsd_z(C.Structure):
 class ccsd_opts(C.Structure):
     _fields_ = [("max_iter", C.c_int), ("tol", C.c_double), ("norm", C.c_int), ("diis_dim", C.c_int),
                 ("diis_start", C.c_int), ("level_shift", C.c_double), ("precision", C.c_int),
-                ("slices", C.c_int), ("store_w", C.c_int), ("profile", C.c_int), ("stream", C.c_void_p)]
+                ("slices", C.c_int), ("store_w", C.c_int), ("profile", C.c_int), ("stream", C.c_void_p),
+                ("split_min_flops", C.c_double)]
 
 
 class CCSDError(RuntimeError):
@@ -59,6 +60,12 @@ SIGNATURES = [
     ("ccsd_zgemm_noalloc", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_longlong, C.c_longlong,
                                      C.c_longlong, ccsd_z, _P, C.c_longlong, _P, C.c_longlong, ccsd_z, _P,
                                      C.c_longlong, C.c_int, _P]),
+    ("ccsd_split_workspace", C.c_size_t, [C.c_int, C.c_int, C.c_int, C.c_longlong, C.c_longlong, C.c_longlong]),
+    ("ccsd_split_zgemm", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_longlong,
+                                   C.c_longlong, C.c_longlong, ccsd_z, _P, C.c_longlong, _P, C.c_longlong, ccsd_z, _P,
+                                   C.c_longlong, _P, C.c_size_t, _P]),
+    ("ccsd_split_probe", C.c_int, [C.c_int, C.c_longlong, C.c_longlong, C.c_longlong, _P, _P, _P, _P, C.c_size_t,
+                                   _P]),
     ("ccsd_last_error", C.c_char_p, [_P]),
     ("ccsd_destroy", None, [_P]),
 ]
@@ -282,3 +289,42 @@ def zgemm_noalloc(a, b, c, alpha=1.0, beta=0.0, transA=False, conjA=False, trans
     if st != OK:
         raise CCSDError(st, lib.ccsd_last_error(None).decode())
     return c
+
+
+SPLIT_E4M3, SPLIT_BF16 = 0, 1
+
+
+def split_zgemm(a, b, c, alpha=1.0, beta=0.0, transA=False, conjA=False, transB=False, conjB=False,
+                kind=SPLIT_E4M3, bits=4, slices=11, stream=None):
+    """ccsd_split_zgemm on row-major torch CUDA complex128 matrices (c updated in place)."""
+    import torch
+    lib = load()
+    M, N = c.shape
+    K = a.shape[0] if transA else a.shape[1]
+    need = lib.ccsd_split_workspace(kind, bits, slices, M, N, K)
+    ws = torch.empty(max(need, 1), dtype=torch.uint8, device=c.device)
+    strm = None if stream is None else C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+    al, be = complex(alpha), complex(beta)
+    st = lib.ccsd_split_zgemm(kind, bits, slices, int(transA), int(conjA), int(transB), int(conjB), M, N, K,
+                              ccsd_z(al.real, al.imag), _ptr(a)[0], a.stride(0), _ptr(b)[0], b.stride(0),
+                              ccsd_z(be.real, be.imag), _ptr(c)[0], c.stride(0), C.c_void_p(ws.data_ptr()), need,
+                              strm)
+    if st != OK:
+        raise CCSDError(st, lib.ccsd_last_error(None).decode())
+    return c
+
+
+def split_probe(a, b, kind=SPLIT_E4M3):
+    """ccsd_split_probe on torch CUDA float64 integer-valued matrices a (M x K), b (N x K)."""
+    import torch
+    lib = load()
+    M, K = a.shape
+    N = b.shape[0]
+    need = lib.ccsd_split_workspace(kind, 8 if kind == SPLIT_BF16 else 4, 1, M, N, K)
+    ws = torch.empty(need, dtype=torch.uint8, device=a.device)
+    out = torch.empty((M, N), dtype=torch.float64, device=a.device)
+    st = lib.ccsd_split_probe(kind, M, N, K, C.c_void_p(a.data_ptr()), C.c_void_p(b.data_ptr()),
+                              C.c_void_p(out.data_ptr()), C.c_void_p(ws.data_ptr()), need, None)
+    if st != OK:
+        raise CCSDError(st, lib.ccsd_last_error(None).decode())
+    return out

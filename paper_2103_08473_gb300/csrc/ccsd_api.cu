@@ -13,6 +13,7 @@
 #include "errors.h"
 #include "ops.h"
 #include "plan.h"
+#include "split.h"
 #include "zgemm.h"
 
 using namespace ccsd;
@@ -51,10 +52,19 @@ struct ccsd_ctx {
   z* scratch = nullptr;
   z* gemm_ws = nullptr;  // split-K partials of the plan's GEMMs
   int64_t gemm_ws_elems = 0;
+  // split precision: digit slices on the tensor cores for the large contractions
+  bool use_split = false;
+  SplitConfig split;
+  double split_min_flops = 2e10;
+  void* split_ws = nullptr;  // per-call digit slices of both operands
+  int64_t split_ws_bytes = 0;
+  int* split_err = nullptr;  // set by the tensor-core kernel if a bounded wait gave up
+  SliceSet Wsl, tausl;       // <ab||cd> digits (built once) and tau digits (per evaluation)
   // iteration state
   double* upd_partials = nullptr;
   double* stats = nullptr;
   double* stats_host = nullptr;  // pinned
+  int* err_host = nullptr;        // pinned copy of split_err
   z* e_partials = nullptr;
   z* e_dev = nullptr;
   z* e_host = nullptr;  // pinned
@@ -293,14 +303,31 @@ ccsd_status build_residual_plan(ccsd_ctx* ctx) {
   const int64_t Po = ctx->Po, Pv = ctx->Pv;
   Plan* P = new Plan(o, v, &ctx->scratch, ctx->stream);
   ctx->plan = P;
+  // Large single GEMMs go to the split-precision tensor-core path in split mode.
+  auto to_split = [ctx](const ZGemmArgs& g) {
+    return ctx->use_split && g.batch == 1 && 8.0 * (double)g.M * (double)g.N * (double)g.K >= ctx->split_min_flops;
+  };
   P->set_gemm(
-      [ctx](const ZGemmArgs& g, cudaStream_t s) {
+      [ctx, to_split](const ZGemmArgs& g, cudaStream_t s) {
+        if (to_split(g)) {
+          SliceSet SA, SB;
+          uint8_t* w = static_cast<uint8_t*>(ctx->split_ws);
+          cudaError_t e = make_slices(g.A, g.M, g.K, g.lda, g.transA, g.conjA, ctx->split, SA, w, s);
+          if (e == cudaSuccess)
+            e = make_slices(g.B, g.N, g.K, g.ldb, g.transB ? 0 : 1, g.conjB, ctx->split, SB,
+                            w + slice_bytes(g.M, g.K, ctx->split), s);
+          if (e == cudaSuccess) e = split_gemm(SA, SB, g.C, g.ldc, g.alpha, g.beta, ctx->split_err, s);
+          return e;
+        }
         ZGemmArgs h = g;
         h.ws = ctx->gemm_ws;
         h.ws_elems = ctx->gemm_ws_elems;
         return zgemm_f64(h, s);
       },
-      [](const ZGemmArgs& g) { return zgemm_f64_workspace(g); });
+      [to_split](const ZGemmArgs& g) { return to_split(g) ? (int64_t)0 : zgemm_f64_workspace(g); },
+      [ctx, to_split](const ZGemmArgs& g) {
+        return to_split(g) ? slice_bytes(g.M, g.K, ctx->split) + slice_bytes(g.N, g.K, ctx->split) : (int64_t)0;
+      });
   const z one = zmake(1, 0), mone = zmake(-1, 0), half = zmake(0.5, 0);
   auto V = [&](z* p, const char* lab) { return P->view(p, lab, true); };
   auto W = [&](z* p, const char* lab) { return P->view(p, lab, false); };
@@ -454,7 +481,18 @@ ccsd_status build_residual_plan(ccsd_ctx* ctx) {
     g.transB = 1;
     g.C = ctx->Lpk;
     g.ldc = Pv;
-    P->gemm("ladder:gemm", g);
+    if (ctx->use_split) {
+      // W digits were cut once at creation; only tau is sliced per evaluation
+      P->note_aux_bytes(slice_bytes(Po, Pv, ctx->split));
+      z* lpk = ctx->Lpk;
+      P->custom("ladder:gemm", [ctx, taupk, lpk, Po, Pv](cudaStream_t s) {
+        cudaError_t e = make_slices(taupk, Po, Pv, Pv, 0, 0, ctx->split, ctx->tausl, ctx->split_ws, s);
+        if (e == cudaSuccess) e = split_gemm(ctx->tausl, ctx->Wsl, lpk, Pv, zmake(1, 0), zmake(0, 0), ctx->split_err, s);
+        return e;
+      }, 8.0 * (double)Po * (double)Pv * (double)Pv);
+    } else {
+      P->gemm("ladder:gemm", g);
+    }
     z *lpk = ctx->Lpk, *s2 = ctx->S2;
     P->custom("ladder:unpack", [=](cudaStream_t s) {
       UnpackArgs u;
@@ -486,6 +524,12 @@ ccsd_status build_residual_plan(ccsd_ctx* ctx) {
   CS(dalloc(ctx, &ctx->scratch, P->scratch_elems()));
   ctx->gemm_ws_elems = P->gemm_workspace_elems();
   CS(dalloc(ctx, &ctx->gemm_ws, ctx->gemm_ws_elems));
+  if (ctx->use_split) {
+    ctx->split_ws_bytes = P->aux_bytes();
+    uint8_t* w = nullptr;
+    CS(dalloc(ctx, &w, ctx->split_ws_bytes));
+    ctx->split_ws = w;
+  }
   return CCSD_OK;
 }
 
@@ -591,8 +635,16 @@ ccsd_status create_impl(int o, int v, const double* eps, const ccsd_z* fock, ccs
   if (opts) ctx->opts = *opts;
   else ccsd_default_opts(&ctx->opts);
   if (ctx->opts.diis_dim < 0 || ctx->opts.diis_dim > 16) return set_err(ctx, CCSD_ERR_ARG, "diis_dim must be in [0, 16]");
-  if (ctx->opts.precision != CCSD_PREC_FP64)
-    return set_err(ctx, CCSD_ERR_UNSUPPORTED, "only the FP64 precision mode is available in this build");
+  if (ctx->opts.precision != CCSD_PREC_FP64 && ctx->opts.precision != CCSD_PREC_SPLIT)
+    return set_err(ctx, CCSD_ERR_ARG, "unknown precision mode");
+  if (ctx->opts.precision == CCSD_PREC_SPLIT) {
+    ctx->use_split = true;
+    ctx->split.kind = kSplitE4M3;
+    ctx->split.b = 4;
+    ctx->split.s = ctx->opts.slices > 0 ? ctx->opts.slices : 11;
+    ctx->split_min_flops = ctx->opts.split_min_flops;
+    if (ctx->split.s > 14) return set_err(ctx, CCSD_ERR_ARG, "slices must be <= 14 (4-bit e4m3 digits)");
+  }
   if (!ctx->opts.store_w) return set_err(ctx, CCSD_ERR_UNSUPPORTED, "store_w = 0 is not available in this build");
   const int n = ctx->n;
   if (fock && !hermitian(fock, n, 1)) return set_err(ctx, CCSD_ERR_ARG, "Fock matrix is not Hermitian");
@@ -673,6 +725,14 @@ ccsd_status create_impl(int o, int v, const double* eps, const ccsd_z* fock, ccs
     cudaFree(dints);
     if (st != CCSD_OK) return st;
   }
+  CS(dalloc(ctx, &ctx->split_err, 1));
+  CK(cudaMemsetAsync(ctx->split_err, 0, sizeof(int), ctx->stream));
+  if (ctx->use_split) {
+    // <ab||cd> is constant: cut its digits once
+    uint8_t* mem = nullptr;
+    CS(dalloc(ctx, &mem, slice_bytes(ctx->Pv, ctx->Pv, ctx->split)));
+    CK(make_slices(ctx->Wpk, ctx->Pv, ctx->Pv, ctx->Pv, 0, 0, ctx->split, ctx->Wsl, mem, ctx->stream));
+  }
   // derived constant layouts
   CS(dalloc(ctx, &ctx->vovv_pk, ov * ctx->Pv));
   CS(dalloc(ctx, &ctx->oovv_pk, ctx->Po * ctx->Pv));
@@ -727,6 +787,8 @@ ccsd_status create_impl(int o, int v, const double* eps, const ccsd_z* fock, ccs
   CS(dalloc(ctx, &ctx->e_dev, 1));
   CK(cudaMallocHost(&ctx->stats_host, 4 * sizeof(double)));
   CK(cudaMallocHost(&ctx->e_host, sizeof(z)));
+  CK(cudaMallocHost(&ctx->err_host, sizeof(int)));
+  *ctx->err_host = 0;
   CK(cudaMemsetAsync(ctx->t1, 0, ov * sizeof(z), ctx->stream));
   CK(cudaMemsetAsync(ctx->t2, 0, n2 * sizeof(z), ctx->stream));
 
@@ -770,6 +832,7 @@ void free_ctx(ccsd_ctx* ctx) {
   }
   if (ctx->stats_host) cudaFreeHost(ctx->stats_host);
   if (ctx->e_host) cudaFreeHost(ctx->e_host);
+  if (ctx->err_host) cudaFreeHost(ctx->err_host);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
@@ -792,6 +855,7 @@ void ccsd_default_opts(ccsd_opts* o) {
   o->store_w = 1;
   o->profile = 0;
   o->stream = nullptr;
+  o->split_min_flops = 2e10;
 }
 
 ccsd_status ccsd_create(int o, int v, const double* eps, const ccsd_z* fock, ccsd_int_kind kind, const ccsd_z* ints,
@@ -821,6 +885,7 @@ ccsd_status ccsd_residual(ccsd_ctx* ctx, const ccsd_z* t1, const ccsd_z* t2, ccs
   }
   const bool timed = ctx->opts.profile != 0;
   CK(run_ops(ctx, timed));
+  if (ctx->use_split) CK(cudaMemcpyAsync(ctx->err_host, ctx->split_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   if (r1) CS(copy_out(ctx, r1, ctx->S1, n1, on_device));
   if (r2) CS(copy_out(ctx, r2, ctx->S2, n2, on_device));
   if (t1) {
@@ -829,6 +894,8 @@ ccsd_status ccsd_residual(ccsd_ctx* ctx, const ccsd_z* t1, const ccsd_z* t2, ccs
   }
   CK(cudaStreamSynchronize(ctx->stream));
   if (timed) collect_timers(ctx, ctx->plan->ops().size());
+  if (ctx->use_split && *ctx->err_host)
+    return set_err(ctx, CCSD_ERR_TIMEOUT, "a bounded wait in the tensor-core GEMM gave up");
   return CCSD_OK;
 }
 
@@ -866,7 +933,13 @@ ccsd_status ccsd_iterate(ccsd_ctx* ctx, int max_iter, int* iters_done, double* r
   for (it = 1; it <= max_iter; ++it) {
     CK(cudaGraphLaunch(ctx->graph, ctx->stream));
     CK(cudaMemcpyAsync(ctx->stats_host, ctx->stats, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (ctx->use_split) CK(cudaMemcpyAsync(ctx->err_host, ctx->split_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    if (ctx->use_split && *ctx->err_host) {
+      st = set_err(ctx, CCSD_ERR_TIMEOUT, "a bounded wait in the tensor-core GEMM gave up (code " +
+                                               std::to_string(*ctx->err_host) + ")");
+      break;
+    }
     ctx->iterations_run += 1;
     if (timed) collect_timers(ctx, ctx->tnames.size());
     nrm = ctx->opts.norm == 1 ? ctx->stats_host[1] : ctx->stats_host[0];

@@ -118,6 +118,7 @@ void Plan::custom(const std::string& name, std::function<cudaError_t(cudaStream_
 
 void Plan::gemm(const std::string& name, const ZGemmArgs& g) {
   if (wsfn_) ws_peak_ = std::max(ws_peak_, wsfn_(g));
+  if (auxfn_) aux_peak_ = std::max(aux_peak_, auxfn_(g));
   GemmFn fn = gemm_;
   ops_.push_back(Op{name, [fn, g](cudaStream_t s) { return fn(g, s); }, 8.0 * g.M * g.N * g.K * g.batch});
 }
@@ -295,6 +296,7 @@ void Plan::contract(const std::string& name, const T& C, z alpha, const T& A0, b
     g.alpha = galpha;
     g.beta = zmake(gbeta, 0.0);
     if (wsfn_) ws_peak_ = std::max(ws_peak_, wsfn_(g));
+    if (auxfn_) aux_peak_ = std::max(aux_peak_, auxfn_(g));
     GemmFn fn = gemm_;
     ops_.push_back(Op{name + ":gemm", [=](cudaStream_t s) {
                         ZGemmArgs h = g;

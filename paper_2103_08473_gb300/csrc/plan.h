@@ -16,6 +16,7 @@
 // planning (its size is the high-water mark of the plan).
 #pragma once
 
+#include <algorithm>
 #include <functional>
 #include <map>
 #include <string>
@@ -77,10 +78,15 @@ class Plan {
   // GEMM op on raw pointers through the plan's GEMM back end.
   void gemm(const std::string& name, const ZGemmArgs& g);
 
-  void set_gemm(GemmFn fn, WsFn ws) {
+  // ws: split-K workspace (complex elements); aux: other per-call workspace (bytes),
+  // e.g. the digit slices of a split-precision GEMM. Both are sized by their peaks.
+  void set_gemm(GemmFn fn, WsFn ws, WsFn aux = nullptr) {
     gemm_ = std::move(fn);
     wsfn_ = std::move(ws);
+    auxfn_ = std::move(aux);
   }
+  void note_aux_bytes(int64_t b) { aux_peak_ = std::max(aux_peak_, b); }
+  int64_t aux_bytes() const { return aux_peak_; }
   const GemmFn& gemm_fn() const { return gemm_; }
   // Largest GEMM workspace any op of the plan wants (complex elements).
   int64_t gemm_workspace_elems() const { return ws_peak_; }
@@ -102,8 +108,8 @@ class Plan {
   z* const* scratch_base_;
   cudaStream_t setup_;
   GemmFn gemm_;
-  WsFn wsfn_;
-  int64_t ws_peak_ = 0;
+  WsFn wsfn_, auxfn_;
+  int64_t ws_peak_ = 0, aux_peak_ = 0;
   std::vector<Op> ops_;
   int64_t scratch_off_ = 0, scratch_peak_ = 0;
   std::map<std::string, T> const_cache_;

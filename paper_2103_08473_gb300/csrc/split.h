@@ -1,0 +1,63 @@
+// Split-precision complex GEMM (Ozaki-style digit slices on tcgen05 tensor cores).
+//
+//   C = alpha * op(A) * op(B) + beta * C      (complex double in and out)
+//
+// Each operand row (A) or column (B) is scaled by a power of two 2^e so that its
+// largest real/imaginary magnitude is below 1, then cut into s signed integer
+// digits of b bits (round to nearest): x = sum_p d_p 2^{-b p} + r, |r| <= 2^{-b s - 1}.
+// Digits are exact in the narrow type (e4m3 holds every integer up to 16, bf16 up
+// to 256). The product of two digit matrices is an integer matrix; the tensor
+// cores form it in FP32 with every partial sum an integer below 2^24, hence
+// exactly. Products of equal weight 2^{-b(p+q)} ("levels") share one FP32
+// accumulator over a K range short enough to stay exact; each level range is
+// then scaled and added into C in FP64. Levels p + q <= s + 1 are kept
+// (triangular scheme).
+//
+// Complex products use four real products per digit pair (4M) into separate
+// real/imaginary TMEM accumulators; A_im * B_im enters the real part through the
+// instruction descriptor's negate-B bit.
+#pragma once
+
+#include <cuda.h>
+
+#include "common.cuh"
+#include "zgemm.h"
+
+namespace ccsd {
+
+enum SplitKind { kSplitE4M3 = 0, kSplitBF16 = 1 };
+
+// Digit slices of one operand, laid out for TMA: rows (p*2 + part) * rows_pad + r,
+// columns k in [0, Kp) (zero padded), one byte (e4m3) or two bytes (bf16) per digit.
+struct SliceSet {
+  void* digits = nullptr;   // device
+  double* scale = nullptr;  // device, 2^e per row (rows entries)
+  int64_t rows = 0, rows_pad = 0, K = 0, Kp = 0;
+  int s = 0, b = 0, kind = kSplitE4M3;
+  CUtensorMap tmap;  // 2D map over the digit array, box {128 bytes, 128 rows}, 128B swizzle
+  bool have_map = false;
+};
+
+struct SplitConfig {
+  int kind = kSplitE4M3;
+  int b = 4;          // bits per digit
+  int s = 11;         // digits per operand
+  int triangular = 1; // keep pairs with p + q <= s + 1 (else all s^2 pairs)
+};
+
+// Bytes of device memory a SliceSet of this shape needs (digits + scales).
+int64_t slice_bytes(int64_t rows, int64_t K, const SplitConfig& cfg);
+// Digits of op(X) viewed as rows x K (element (r,k) = trans ? X[k*ld + r] : X[r*ld + k],
+// conjugated if conj), written into `out` (whose digits/scale point at device memory
+// of slice_bytes). Sets out's shape fields and encodes its tensor map.
+cudaError_t make_slices(const z* X, int64_t rows, int64_t K, int64_t ld, int trans, int conj,
+                        const SplitConfig& cfg, SliceSet& out, void* mem, cudaStream_t s);
+// C = alpha * A B^T + beta * C from slice sets A (M rows) and B (N rows) over the same K.
+// err: device int, set nonzero by the kernel if a bounded wait gave up.
+cudaError_t split_gemm(const SliceSet& A, const SliceSet& B, z* C, int64_t ldc, z alpha, z beta,
+                       int* err, cudaStream_t s);
+// Probe: C (FP64 real, M x N) = A_digits(slice 0, real part) * B_digits(slice 0, real part)^T with
+// no scaling, for exactness checks of the tensor-core accumulation on integer inputs.
+cudaError_t split_probe(const SliceSet& A, const SliceSet& B, double* C, int* err, cudaStream_t s);
+
+}  // namespace ccsd

@@ -1,0 +1,667 @@
+// Split-precision complex GEMM on tcgen05 (see split.h for the scheme).
+//
+// Kernel structure (one CTA per 128 x 128 complex output tile, 6 warps):
+//   warp 0  TMA producer: per K block (128 bytes of digits per row) and slice
+//           pair of the current level group, loads the A_re, A_im (128 rows) and
+//           B_re, B_im (128 rows) digit tiles into a 3-stage ring of 128B-swizzled
+//           shared tiles. K blocks are the outer loop and the group's pairs the
+//           inner one, so all CTAs walk the same narrow K front of the small
+//           operand and it stays in L2.
+//   warp 1  allocates all 512 TMEM columns; one thread issues the UMMAs
+//           (M = 128, N = 128, K = 32 e4m3 / 16 bf16 per instruction):
+//             re += Ar Br, re += Ai (-Bi), im += Ar Bi, im += Ai Br
+//           into one of two TMEM accumulator sets (re, im: 128 columns each),
+//           and commits each smem stage back to the producer.
+//   warps 2-5  epilogue: after each level group, read the FP32 accumulator rows
+//           (tcgen05.ld 32x32b), scale by 2^(e_row + e_col - b L) and add
+//           alpha * value into C in FP64, then release the TMEM set.
+// Every mbarrier wait is bounded (clock64 budget); a wait that gives up sets the
+// error word and the CTA drains its in-flight copies, frees TMEM and exits.
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <cudaTypedefs.h>
+
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "split.h"
+
+namespace ccsd {
+namespace {
+
+constexpr int kStages = 3;
+constexpr uint32_t kTile = 128 * 128;        // bytes of one 128-row x 128-byte digit tile
+constexpr uint32_t kStageBytes = 4 * kTile;  // A_re, A_im, B_re, B_im
+constexpr uint32_t kSmemBytes = kStages * kStageBytes + 1024 + 256;
+constexpr int kMaxGroups = 128;
+constexpr int kMaxPairs = 512;
+
+struct SplitSched {
+  int ngroups;
+  int first[kMaxGroups + 1];  // pairs of group g: [first[g], first[g+1])
+  int kb0[kMaxGroups], kb1[kMaxGroups];
+  double gscale[kMaxGroups];  // 2^{-b L}
+  unsigned char pp[kMaxPairs], pq[kMaxPairs];
+};
+
+struct SplitArgs {
+  int64_t M, N, Mp, Np;
+  int tiles_m;
+  z* C;
+  int64_t ldc;
+  z alpha;
+  const double* rs;
+  const double* cs;
+  double* probe;  // probe output (real M x N) or null
+  int* err;
+  long long wait_cycles;
+  SplitSched sched;
+};
+
+// ---- PTX wrappers ----------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the phase of the given parity; gives up after `budget` clock cycles or
+// when another role raised the abort flag (unless ignore_abort).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long budget, volatile int* abort_flag,
+                                          bool ignore_abort = false) {
+  const long long t0 = clock64();
+  while (!mbar_test(bar, parity)) {
+    if (!ignore_abort && *abort_flag) return false;
+    if (clock64() - t0 > budget) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major operand in the canonical 128-byte
+// swizzled layout written by TMA (8-row groups 1024 bytes apart).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                    // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset: 8 rows x 128 bytes
+  d |= (uint64_t)1 << 46;                    // descriptor version
+  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: D = F32, A/B K-major, M = 128, N = 128.
+__host__ __device__ constexpr uint32_t make_idesc(int kind, int negB) {
+  return (1u << 4) | ((kind == kSplitBF16 ? 1u : 0u) << 7) | ((kind == kSplitBF16 ? 1u : 0u) << 10) |
+         ((uint32_t)negB << 14) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+template <int KIND>
+__device__ __forceinline__ void umma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if constexpr (KIND == kSplitBF16) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  } else {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  }
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// ---- the GEMM kernel ----------------------------------------------------------
+
+template <int KIND, bool PROBE>
+__global__ void __launch_bounds__(192, 1)
+    split_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                 const __grid_constant__ SplitArgs args) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  const uint32_t bar0 = base + kStages * kStageBytes;
+  // barrier addresses (8 bytes each)
+  auto full = [&](int s) { return bar0 + 8u * s; };
+  auto empty = [&](int s) { return bar0 + 8u * (kStages + s); };
+  auto accfull = [&](int b) { return bar0 + 8u * (2 * kStages + b); };
+  auto accempty = [&](int b) { return bar0 + 8u * (2 * kStages + 2 + b); };
+  const uint32_t done = bar0 + 8u * (2 * kStages + 4);
+  uint8_t* gen = smem_raw + (base - raw);
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(gen + kStages * kStageBytes + 8 * (2 * kStages + 5));
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tm = blockIdx.x % args.tiles_m, tn = blockIdx.x / args.tiles_m;
+  const int64_t m0 = (int64_t)tm * 128, n0 = (int64_t)tn * 128;
+  const SplitSched& S = args.sched;
+  constexpr int BKE = KIND == kSplitBF16 ? 64 : 128;  // digits per 128-byte row segment
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accfull(b), 1);
+      mbar_init(accempty(b), 128);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    tc_fence_before();
+  }
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+  const long long budget = args.wait_cycles;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      int it = 0;
+      bool ok = true;
+      for (int g = 0; g < S.ngroups && ok; ++g)
+        for (int kb = S.kb0[g]; kb < S.kb1[g] && ok; ++kb)
+          for (int pi = S.first[g]; pi < S.first[g + 1]; ++pi, ++it) {
+            const int p = S.pp[pi], q = S.pq[pi];
+            const int st = it % kStages;
+            const uint32_t ph = (uint32_t)(it / kStages) & 1u;
+            if (!mbar_wait(empty(st), ph ^ 1u, budget, abort_flag)) {
+              ok = false;
+              break;
+            }
+            const uint32_t sa = base + st * kStageBytes;
+            const int x = kb * BKE;
+            mbar_expect_tx(full(st), PROBE ? 2 * kTile : 4 * kTile);
+            tma_load_2d(sa, &tmA, x, (int)((p * 2 + 0) * args.Mp + m0), full(st));
+            if (!PROBE) tma_load_2d(sa + kTile, &tmA, x, (int)((p * 2 + 1) * args.Mp + m0), full(st));
+            tma_load_2d(sa + 2 * kTile, &tmB, x, (int)((q * 2 + 0) * args.Np + n0), full(st));
+            if (!PROBE) tma_load_2d(sa + 3 * kTile, &tmB, x, (int)((q * 2 + 1) * args.Np + n0), full(st));
+          }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicOr(args.err, 1);
+      }
+      // drain: every copy this thread issued must have landed before the CTA exits
+      const int last = it;
+      for (int j = (last > kStages ? last - kStages : 0); j < last; ++j)
+        mbar_wait(full(j % kStages), (uint32_t)(j / kStages) & 1u, budget, abort_flag, true);
+    }
+  } else if (warp == 1) {
+    // ---------------- UMMA issuer ----------------
+    if (lane == 0) {
+      const uint32_t id = make_idesc(KIND, 0), idn = make_idesc(KIND, 1);
+      int it = 0;
+      bool ok = true;
+      for (int g = 0; g < S.ngroups && ok; ++g) {
+        const int buf = g & 1, use = g >> 1;
+        if (!mbar_wait(accempty(buf), ((uint32_t)use & 1u) ^ 1u, budget, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t dre = tmem + (uint32_t)buf * 256u, dim = dre + 128u;
+        bool first = true;
+        for (int kb = S.kb0[g]; kb < S.kb1[g] && ok; ++kb)
+          for (int pi = S.first[g]; pi < S.first[g + 1]; ++pi, ++it) {
+            const int st = it % kStages;
+            const uint32_t ph = (uint32_t)(it / kStages) & 1u;
+            if (!mbar_wait(full(st), ph, budget, abort_flag)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t sa = base + st * kStageBytes;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint32_t acc = (first && kk == 0) ? 0u : 1u;
+              const uint64_t aR = sw128_desc(sa + kk * 32), bR = sw128_desc(sa + 2 * kTile + kk * 32);
+              umma<KIND>(dre, aR, bR, id, acc);
+              if (!PROBE) {
+                const uint64_t aI = sw128_desc(sa + kTile + kk * 32), bI = sw128_desc(sa + 3 * kTile + kk * 32);
+                umma<KIND>(dre, aI, bI, idn, 1u);
+                umma<KIND>(dim, aR, bI, id, acc);
+                umma<KIND>(dim, aI, bR, id, 1u);
+              }
+            }
+            umma_commit(empty(st));
+            first = false;
+          }
+        if (ok) umma_commit(accfull(buf));
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicOr(args.err, 2);
+      }
+      // all issued MMAs complete before TMEM is released
+      umma_commit(done);
+      mbar_wait(done, 0u, budget, abort_flag, true);
+    }
+    __syncwarp();
+  } else {
+    // ---------------- epilogue: warps 2..5 ----------------
+    const int q4 = warp & 3;
+    const int64_t m = m0 + q4 * 32 + lane;
+    const bool mrow = m < args.M;
+    const double rsc = (!PROBE && mrow) ? args.rs[m] : 0.0;
+    for (int g = 0; g < S.ngroups; ++g) {
+      const int buf = g & 1, use = g >> 1;
+      if (!mbar_wait(accfull(buf), (uint32_t)use & 1u, budget, abort_flag)) {
+        *abort_flag = 1;
+        atomicOr(args.err, 4);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t trow = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)buf * 256u;
+      const double gs = S.gscale[g];
+#pragma unroll 1
+      for (int c0 = 0; c0 < 128; c0 += 32) {
+        uint32_t re[32], im[32];
+        tmem_ld32(trow + c0, re);
+        if (!PROBE) tmem_ld32(trow + 128 + c0, im);
+        tmem_wait_ld();
+        if (mrow) {
+          if (PROBE) {
+            for (int j = 0; j < 32; ++j) {
+              const int64_t n = n0 + c0 + j;
+              if (n < args.N) args.probe[m * args.N + n] = (double)__uint_as_float(re[j]);
+            }
+          } else {
+            z* crow = args.C + m * args.ldc;
+            for (int j = 0; j < 32; ++j) {
+              const int64_t n = n0 + c0 + j;
+              if (n < args.N) {
+                const double sc = rsc * args.cs[n] * gs;
+                const z v = make_double2((double)__uint_as_float(re[j]) * sc, (double)__uint_as_float(im[j]) * sc);
+                crow[n] = zadd(crow[n], zmul(args.alpha, v));
+              }
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(accempty(buf));
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  }
+}
+
+// ---- digit slicing ----------------------------------------------------------
+
+__device__ double block_max(double x, double* sh) {
+  for (int off = 16; off > 0; off >>= 1) x = fmax(x, __shfl_down_sync(0xffffffffu, x, off));
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[w] = x;
+  __syncthreads();
+  double r = 0.0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r = fmax(r, sh[i]);
+  return r;
+}
+
+template <int KIND>
+__device__ __forceinline__ void put_digit(uint8_t* out, int64_t idx, double d) {
+  if constexpr (KIND == kSplitBF16) {
+    reinterpret_cast<__nv_bfloat16*>(out)[idx] = __float2bfloat16_rn((float)d);
+  } else {
+    out[idx] = __nv_fp8_e4m3((float)d).__x;
+  }
+}
+
+// Digits by integer arithmetic: one conversion of x 2^-e (|x 2^-e| < 1) to a
+// 62-bit fixed-point integer V, then digit p is the rounded top b bits of what is
+// left (round half up), subtracted off before the next. FP64 work is one multiply
+// and one conversion per element; the digits come from the integer pipes.
+__device__ __forceinline__ long long fixed62(double x) { return __double2ll_rn(x * 4611686018427387904.0); }
+__device__ __forceinline__ int next_digit(long long& V, int shift) {
+  const long long d = (V + (1LL << (shift - 1))) >> shift;
+  V -= d << shift;
+  return (int)d;
+}
+
+__device__ __forceinline__ uint32_t pack4_e4m3(int d0, int d1, int d2, int d3) {
+  const __nv_fp8x2_storage_t lo = __nv_cvt_float2_to_fp8x2(make_float2((float)d0, (float)d1), __NV_SATFINITE, __NV_E4M3);
+  const __nv_fp8x2_storage_t hi = __nv_cvt_float2_to_fp8x2(make_float2((float)d2, (float)d3), __NV_SATFINITE, __NV_E4M3);
+  return (uint32_t)lo | ((uint32_t)hi << 16);
+}
+__device__ __forceinline__ uint2 pack4_bf16(int d0, int d1, int d2, int d3) {
+  __nv_bfloat162 a = __floats2bfloat162_rn((float)d0, (float)d1);
+  __nv_bfloat162 c = __floats2bfloat162_rn((float)d2, (float)d3);
+  uint2 w;
+  w.x = *reinterpret_cast<uint32_t*>(&a);
+  w.y = *reinterpret_cast<uint32_t*>(&c);
+  return w;
+}
+
+template <int KIND>
+__global__ void slice_kernel(const z* __restrict__ X, int64_t rows, int64_t K, int64_t ld, int trans, int conj, int s,
+                             int b, uint8_t* __restrict__ out, int64_t rows_pad, int64_t Kp, double* __restrict__ scale) {
+  __shared__ double sh[32];
+  for (int64_t r = blockIdx.x; r < rows_pad; r += gridDim.x) {
+    const bool live = r < rows;
+    double mx = 0.0;
+    if (live)
+      for (int64_t k = threadIdx.x; k < K; k += blockDim.x) {
+        const z v = trans ? X[k * ld + r] : X[r * ld + k];
+        mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+      }
+    mx = block_max(mx, sh);
+    int e = 0;
+    if (mx > 0.0) frexp(mx, &e);  // mx = f 2^e, 0.5 <= f < 1: every |x| 2^-e < 1
+    if (live && threadIdx.x == 0) scale[r] = ldexp(1.0, e);
+    const double inv = ldexp(1.0, -e);
+    // four consecutive k per thread: one 4-byte (e4m3) or 8-byte (bf16) store per digit plane
+    for (int64_t k0 = 4 * (int64_t)threadIdx.x; k0 < Kp; k0 += 4 * (int64_t)blockDim.x) {
+      long long Vr[4], Vi[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t k = k0 + u;
+        double xr = 0.0, xi = 0.0;
+        if (live && k < K) {
+          const z v = trans ? X[k * ld + r] : X[r * ld + k];
+          xr = v.x * inv;
+          xi = (conj ? -v.y : v.y) * inv;
+        }
+        Vr[u] = fixed62(xr);
+        Vi[u] = fixed62(xi);
+      }
+      int shift = 62;
+      for (int p = 0; p < s; ++p) {
+        shift -= b;
+        int dr[4], di[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          dr[u] = next_digit(Vr[u], shift);
+          di[u] = next_digit(Vi[u], shift);
+        }
+        const int64_t o0 = ((int64_t)(p * 2 + 0) * rows_pad + r) * Kp + k0;
+        const int64_t o1 = ((int64_t)(p * 2 + 1) * rows_pad + r) * Kp + k0;
+        if constexpr (KIND == kSplitBF16) {
+          *reinterpret_cast<uint2*>(out + 2 * o0) = pack4_bf16(dr[0], dr[1], dr[2], dr[3]);
+          *reinterpret_cast<uint2*>(out + 2 * o1) = pack4_bf16(di[0], di[1], di[2], di[3]);
+        } else {
+          *reinterpret_cast<uint32_t*>(out + o0) = pack4_e4m3(dr[0], dr[1], dr[2], dr[3]);
+          *reinterpret_cast<uint32_t*>(out + o1) = pack4_e4m3(di[0], di[1], di[2], di[3]);
+        }
+      }
+    }
+  }
+}
+
+// Integer-valued doubles to digits (probe input), real part only, slice 0.
+template <int KIND>
+__global__ void raw_digits_kernel(const double* __restrict__ X, int64_t rows, int64_t K, uint8_t* __restrict__ out,
+                                  int64_t rows_pad, int64_t Kp) {
+  const int64_t total = rows_pad * Kp;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / Kp, k = e % Kp;
+    put_digit<KIND>(out, e, (r < rows && k < K) ? X[r * K + k] : 0.0);
+  }
+}
+
+// ---- host helpers -----------------------------------------------------------
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, []() {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+int esize(int kind) { return kind == kSplitBF16 ? 2 : 1; }
+int bke(int kind) { return kind == kSplitBF16 ? 64 : 128; }
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+cudaError_t encode_map(SliceSet& S) {
+  auto enc = get_encode();
+  if (!enc) return cudaErrorNotSupported;
+  const int es = esize(S.kind);
+  cuuint64_t dims[2] = {(cuuint64_t)S.Kp, (cuuint64_t)(S.s * 2 * S.rows_pad)};
+  cuuint64_t strides[1] = {(cuuint64_t)(S.Kp * es)};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / es), 128u};
+  cuuint32_t estr[2] = {1u, 1u};
+  CUresult r = enc(&S.tmap, S.kind == kSplitBF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+                   S.digits, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  S.have_map = (r == CUDA_SUCCESS);
+  return S.have_map ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+double maxdigit(int p, int b) { return p == 0 ? std::ldexp(1.0, b) : std::ldexp(1.0, b - 1); }
+
+// Level groups: pairs (p, q) with equal weight 2^{-b(p+q+2)} (0-based p, q) share an
+// accumulator over K ranges short enough that every partial sum stays below 2^24.
+bool build_schedule(int s, int b, int tri, int kblocks, int kind, bool probe, SplitSched& S) {
+  std::memset(&S, 0, sizeof(S));
+  int ng = 0, np = 0;
+  const int lmax = tri ? s - 1 : 2 * s - 2;  // 0-based level p + q
+  for (int L = 0; L <= lmax; ++L) {
+    double sum = 0.0;
+    int cnt = 0;
+    for (int p = 0; p < s; ++p) {
+      const int q = L - p;
+      if (q < 0 || q >= s) continue;
+      sum += maxdigit(p, b) * maxdigit(q, b);
+      ++cnt;
+      if (probe) break;
+    }
+    if (cnt == 0) continue;
+    const double products_per_k = probe ? 1.0 : 2.0;  // complex: two real products per k per accumulator
+    const double klen = std::floor((16777216.0 - 1.0) / (products_per_k * sum));
+    int kb_per = (int)std::floor(klen / bke(kind));
+    if (kb_per < 1) return false;
+    for (int k0 = 0; k0 < kblocks; k0 += kb_per) {
+      if (ng >= kMaxGroups || np + cnt > kMaxPairs) return false;
+      S.first[ng] = np;
+      S.kb0[ng] = k0;
+      S.kb1[ng] = std::min(kblocks, k0 + kb_per);
+      S.gscale[ng] = std::ldexp(1.0, -b * (L + 2));
+      for (int p = 0; p < s; ++p) {
+        const int q = L - p;
+        if (q < 0 || q >= s) continue;
+        S.pp[np] = (unsigned char)p;
+        S.pq[np] = (unsigned char)q;
+        ++np;
+        if (probe) break;
+      }
+      ++ng;
+    }
+    if (probe) break;
+  }
+  S.first[ng] = np;
+  S.ngroups = ng;
+  return true;
+}
+
+template <int KIND, bool PROBE>
+cudaError_t launch_split(const SliceSet& A, const SliceSet& B, const SplitArgs& a, cudaStream_t s) {
+  auto kern = split_kernel<KIND, PROBE>;
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [&]() {
+    attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+  });
+  if (attr_err != cudaSuccess) return attr_err;
+  const int64_t tiles_n = (a.N + 127) / 128;
+  const int64_t grid = (int64_t)a.tiles_m * tiles_n;
+  if (grid <= 0) return cudaSuccess;
+  if (grid > 0x7fffffff) return cudaErrorInvalidValue;
+  kern<<<(unsigned)grid, 192, kSmemBytes, s>>>(A.tmap, B.tmap, a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int64_t slice_bytes(int64_t rows, int64_t K, const SplitConfig& cfg) {
+  const int64_t rows_pad = round_up(std::max<int64_t>(rows, 1), 128);
+  const int64_t Kp = round_up(std::max<int64_t>(K, 1), bke(cfg.kind));
+  return round_up((int64_t)cfg.s * 2 * rows_pad * Kp * esize(cfg.kind), 1024) + round_up(rows_pad * 8, 1024);
+}
+
+cudaError_t make_slices(const z* X, int64_t rows, int64_t K, int64_t ld, int trans, int conj, const SplitConfig& cfg,
+                        SliceSet& out, void* mem, cudaStream_t s) {
+  if (cfg.s < 1 || cfg.s > 14 || cfg.b < 1 || cfg.b > (cfg.kind == kSplitBF16 ? 8 : 4) || cfg.b * cfg.s > 56)
+    return cudaErrorInvalidValue;
+  out.rows = rows;
+  out.rows_pad = round_up(std::max<int64_t>(rows, 1), 128);
+  out.K = K;
+  out.Kp = round_up(std::max<int64_t>(K, 1), bke(cfg.kind));
+  out.s = cfg.s;
+  out.b = cfg.b;
+  out.kind = cfg.kind;
+  out.digits = mem;
+  out.scale = reinterpret_cast<double*>(static_cast<uint8_t*>(mem) +
+                                        round_up((int64_t)cfg.s * 2 * out.rows_pad * out.Kp * esize(cfg.kind), 1024));
+  cudaError_t e = encode_map(out);
+  if (e != cudaSuccess) return e;
+  const int grid = (int)std::min<int64_t>(out.rows_pad, 152 * 16);
+  if (cfg.kind == kSplitBF16)
+    slice_kernel<kSplitBF16><<<grid, 256, 0, s>>>(X, rows, K, ld, trans, conj, cfg.s, cfg.b, (uint8_t*)out.digits,
+                                                  out.rows_pad, out.Kp, out.scale);
+  else
+    slice_kernel<kSplitE4M3><<<grid, 256, 0, s>>>(X, rows, K, ld, trans, conj, cfg.s, cfg.b, (uint8_t*)out.digits,
+                                                  out.rows_pad, out.Kp, out.scale);
+  return cudaGetLastError();
+}
+
+cudaError_t split_gemm(const SliceSet& A, const SliceSet& B, z* C, int64_t ldc, z alpha, z beta, int* err,
+                       cudaStream_t s) {
+  if (A.kind != B.kind || A.Kp != B.Kp || A.s != B.s || A.b != B.b || !A.have_map || !B.have_map)
+    return cudaErrorInvalidValue;
+  if (beta.x != 1.0 || beta.y != 0.0) {
+    ZGemmArgs g;
+    g.M = A.rows;
+    g.N = B.rows;
+    g.C = C;
+    g.ldc = ldc;
+    g.beta = beta;
+    cudaError_t e = zscale_matrix(g, s);
+    if (e != cudaSuccess) return e;
+  }
+  SplitArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.M = A.rows;
+  a.N = B.rows;
+  a.Mp = A.rows_pad;
+  a.Np = B.rows_pad;
+  a.tiles_m = (int)((A.rows + 127) / 128);
+  a.C = C;
+  a.ldc = ldc;
+  a.alpha = alpha;
+  a.rs = A.scale;
+  a.cs = B.scale;
+  a.err = err;
+  a.wait_cycles = 4000000000LL;  // ~2 s at 2 GHz
+  if (!build_schedule(A.s, A.b, 1, (int)(A.Kp / bke(A.kind)), A.kind, false, a.sched)) return cudaErrorInvalidValue;
+  return A.kind == kSplitBF16 ? launch_split<kSplitBF16, false>(A, B, a, s) : launch_split<kSplitE4M3, false>(A, B, a, s);
+}
+
+cudaError_t split_probe_raw(int kind, const double* Aint, const double* Bint, int64_t M, int64_t N, int64_t K,
+                            double* C, void* mem, int* err, cudaStream_t s) {
+  SplitConfig cfg;
+  cfg.kind = kind;
+  cfg.s = 1;
+  cfg.b = kind == kSplitBF16 ? 8 : 4;
+  SliceSet A, B;
+  const int64_t ba = slice_bytes(M, K, cfg);
+  uint8_t* m8 = static_cast<uint8_t*>(mem);
+  for (SliceSet* S : {&A, &B}) {
+    const int64_t rows = S == &A ? M : N;
+    S->rows = rows;
+    S->rows_pad = round_up(std::max<int64_t>(rows, 1), 128);
+    S->K = K;
+    S->Kp = round_up(std::max<int64_t>(K, 1), bke(kind));
+    S->s = 1;
+    S->b = cfg.b;
+    S->kind = kind;
+    S->digits = S == &A ? (void*)m8 : (void*)(m8 + ba);
+    S->scale = nullptr;
+    cudaError_t e = encode_map(*S);
+    if (e != cudaSuccess) return e;
+    const double* src = S == &A ? Aint : Bint;
+    const int64_t tot = S->rows_pad * S->Kp;
+    if (kind == kSplitBF16)
+      raw_digits_kernel<kSplitBF16><<<grid_for(tot, 256), 256, 0, s>>>(src, rows, K, (uint8_t*)S->digits, S->rows_pad,
+                                                                       S->Kp);
+    else
+      raw_digits_kernel<kSplitE4M3><<<grid_for(tot, 256), 256, 0, s>>>(src, rows, K, (uint8_t*)S->digits, S->rows_pad,
+                                                                       S->Kp);
+  }
+  SplitArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.M = M;
+  a.N = N;
+  a.Mp = A.rows_pad;
+  a.Np = B.rows_pad;
+  a.tiles_m = (int)((M + 127) / 128);
+  a.probe = C;
+  a.err = err;
+  a.wait_cycles = 4000000000LL;
+  SplitSched& S = a.sched;
+  std::memset(&S, 0, sizeof(S));
+  S.ngroups = 1;
+  S.first[0] = 0;
+  S.first[1] = 1;
+  S.kb0[0] = 0;
+  S.kb1[0] = (int)(A.Kp / bke(kind));
+  S.gscale[0] = 1.0;
+  return kind == kSplitBF16 ? launch_split<kSplitBF16, true>(A, B, a, s) : launch_split<kSplitE4M3, true>(A, B, a, s);
+}
+
+}  // namespace ccsd

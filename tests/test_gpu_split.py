@@ -1,0 +1,84 @@
+"""Split-precision complex GEMM on tcgen05 (ccsd_split_zgemm) and its accumulation probe.
+
+The probe checks the premise of the scheme: integer-valued digit products summed
+in the FP32 tensor-memory accumulator are exact while every partial sum stays
+below 2^24. The GEMM is checked against numpy complex128 (and the FP64 DMMA
+GEMM) with the error bound of the digit count: ~2^(-bits*slices) relative.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    from paper_2103_08473_gb300 import build, ccsd
+    ccsd.load(build.build())
+    return torch, ccsd
+
+
+@pytest.mark.parametrize("kind,lim,K", [(0, 16, 4096), (0, 16, 1000), (1, 128, 512), (1, 100, 200)])
+def test_probe_integer_accumulation_is_exact(env, kind, lim, K):
+    torch, ccsd = env
+    rng = np.random.default_rng(kind * 7 + K)
+    M, N = 200, 130
+    a = rng.integers(-lim, lim + 1, size=(M, K)).astype(np.float64)
+    b = rng.integers(-lim, lim + 1, size=(N, K)).astype(np.float64)
+    assert K * lim * lim < 2 ** 24
+    want = (a.astype(np.int64) @ b.astype(np.int64).T).astype(np.float64)
+    got = ccsd.split_probe(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), kind=kind).cpu().numpy()
+    assert np.array_equal(got, want)
+
+
+def _rand(rng, *shape):
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+@pytest.mark.parametrize("kind,bits,slices,tol", [(0, 4, 11, 2e-12), (0, 4, 6, 2e-6), (1, 7, 7, 2e-13), (1, 6, 5, 3e-8)])
+def test_split_zgemm_matches_complex128(env, kind, bits, slices, tol):
+    torch, ccsd = env
+    rng = np.random.default_rng(slices * 10 + kind)
+    M, N, K = 300, 200, 1000
+    a, b, c0 = _rand(rng, M, K), _rand(rng, K, N), _rand(rng, M, N)
+    alpha, beta = 0.75 - 0.5j, 0.25 + 1.0j
+    want = alpha * (a @ b) + beta * c0
+    dc = torch.from_numpy(c0).cuda()
+    ccsd.split_zgemm(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), dc, alpha, beta, kind=kind, bits=bits,
+                     slices=slices)
+    err = np.max(np.abs(dc.cpu().numpy() - want)) / np.max(np.abs(want))
+    assert err < tol, err
+
+
+@pytest.mark.parametrize("tA,cA,tB,cB", [(0, 0, 1, 0), (1, 1, 0, 0), (0, 1, 1, 1), (1, 0, 0, 1)])
+def test_split_zgemm_transpose_and_conjugate(env, tA, cA, tB, cB):
+    torch, ccsd = env
+    rng = np.random.default_rng(tA * 8 + cA * 4 + tB * 2 + cB)
+    M, N, K = 131, 257, 300
+    a = _rand(rng, *((K, M) if tA else (M, K)))
+    b = _rand(rng, *((N, K) if tB else (K, N)))
+    opa = (a.T if tA else a)
+    opa = np.conj(opa) if cA else opa
+    opb = (b.T if tB else b)
+    opb = np.conj(opb) if cB else opb
+    want = opa @ opb
+    dc = torch.zeros((M, N), dtype=torch.complex128, device="cuda")
+    ccsd.split_zgemm(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), dc, 1.0, 0.0, bool(tA), bool(cA),
+                     bool(tB), bool(cB))
+    assert np.max(np.abs(dc.cpu().numpy() - want)) / np.max(np.abs(want)) < 2e-12
+
+
+def test_split_zgemm_ladder_shape_matches_fp64_path(env):
+    """The ladder GEMM of the o20/v120 workload: M = 190 (i<j), N = K = 7140 (a<b, c<d)."""
+    torch, ccsd = env
+    rng = np.random.default_rng(5)
+    M, N, K = 190, 7140, 7140
+    a = torch.from_numpy(_rand(rng, M, K) * 0.01).cuda()
+    b = torch.from_numpy(_rand(rng, N, K) * 0.03).cuda()
+    ref = torch.zeros((M, N), dtype=torch.complex128, device="cuda")
+    ccsd.zgemm(a, b, ref, transB=True)
+    out = torch.zeros((M, N), dtype=torch.complex128, device="cuda")
+    ccsd.split_zgemm(a, b, out, transB=True)
+    err = (out - ref).abs().max().item() / ref.abs().max().item()
+    assert err < 2e-12, err
