@@ -33,11 +33,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOADS = {
-    "c2": dict(o=20, v=120, naux=400, seed=2, level_shift=20.0,
+    "c2": dict(o=20, v=120, naux=400, seed=2, level_shift=20.0, precision="fp64",
                name="ccsd_fp64_o20_v120_naux400_storedW"),
-    "c1": dict(o=10, v=30, naux=120, seed=1, level_shift=0.0,
+    "c1": dict(o=10, v=30, naux=120, seed=1, level_shift=0.0, precision="fp64",
                name="ccsd_fp64_o10_v30_naux120"),
+    "c3": dict(o=40, v=240, naux=800, seed=3, level_shift=40.0, precision="split",
+               name="ccsd_split_o40_v240_naux800_storedW"),
 }
+SPLIT_SLICES = 9  # 4-bit digits: |dE| 7.6e-10 Eh vs FP64 after 8 iterations at o20/v120
 METRIC = "CCSD iteration time (s)"
 FP64_OVER_BF16_NOMINAL = 1.25 / 2250.0  # dense FP64 vs dense BF16 tensor rate (nominal)
 
@@ -162,6 +165,42 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
+def make_ctx(ccmod, s, wl, precision, slices, stream, profile=1):
+    kw = dict(level_shift=wl["level_shift"], tol=0.0, diis_dim=8, profile=profile, stream=stream.cuda_stream)
+    if precision == "split":
+        kw.update(precision=ccmod.PREC_SPLIT, slices=slices)
+    return ccmod.CCSD(s.o, s.v, s.eps, B=s.B, **kw)
+
+
+def timed_iterations(ccmod, cc, stream, warmup, steps, barrier=lambda: None, sampler=None):
+    """warm-up, then `steps` iterations bracketed by CUDA events on the library's stream."""
+    import torch
+    for _ in range(warmup):
+        st, _, _ = cc.iterate(1)
+        if st == ccmod.ERR_DIVERGED:
+            raise RuntimeError("iteration diverged during warm-up")
+    cc.timings()  # reset the per-op averages
+    if sampler:
+        sampler.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        st, _, _ = cc.iterate(1)
+        if st == ccmod.ERR_DIVERGED:
+            raise RuntimeError("iteration diverged in the timed region")
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop() if sampler else None
+    ops = {}
+    for name, t in cc.timings():
+        ops[name] = ops.get(name, 0.0) + t
+    return e0.elapsed_time(e1), ops, clocks
+
+
 def run_ours(args, wl):
     import numpy as np
     import torch
@@ -177,41 +216,24 @@ def run_ours(args, wl):
     ccmod.load(build.build())
     s = inputs.make_system(wl["o"], wl["v"], wl["naux"], wl["seed"])
     o, v = s.o, s.v
+    precision = args.precision or wl["precision"]
+    slices = args.slices or SPLIT_SLICES
     stream = torch.cuda.Stream()  # a real stream: the library captures its iteration graph on it
-    cc = ccmod.CCSD(o, v, s.eps, B=s.B, level_shift=wl["level_shift"], tol=0.0, diis_dim=8, profile=1,
-                    stream=stream.cuda_stream)
+    cc = make_ctx(ccmod, s, wl, precision, slices, stream)
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
 
-    for _ in range(args.warmup):
-        st, _, _ = cc.iterate(1)
-        if st == ccmod.ERR_DIVERGED:
-            raise RuntimeError("iteration diverged during warm-up")
-    cc.timings()  # reset the per-op averages
     sampler = ClockSampler(local)
-    sampler.start()
-    barrier()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        st, _, _ = cc.iterate(1)
-        if st == ccmod.ERR_DIVERGED:
-            raise RuntimeError("iteration diverged in the timed region")
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
+    ms, opd, clocks = timed_iterations(ccmod, cc, stream, args.warmup, args.steps, barrier, sampler)
     if world > 1:
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
-    ops = cc.timings()
     kernels = int(cc.query("kernels_per_iteration"))
+    e_main = cc.energy()
+    t_main = cc.get_amplitudes()
 
     # end to end through the C ABI with host buffers: H2D of the step's amplitudes from pinned
     # memory, the iteration, D2H of the norm and the energy
@@ -229,62 +251,96 @@ def run_ours(args, wl):
     torch.cuda.synchronize()
     e2e = (time.perf_counter() - w0) / e2e_steps
     cc.timings()
+    cc.close()
     h2d = 16 * (o * v + o * o * v * v)
     d2h = 16 + 16
 
+    # companion: the other precision on the same workload and the same iteration count, for the
+    # split-precision speedup and its energy / amplitude error against the FP64 GPU path
+    companion = None
+    if precision == "fp64" and not args.no_split_companion:
+        cs = make_ctx(ccmod, s, wl, "split", slices, stream)
+        ms2, opd2, _ = timed_iterations(ccmod, cs, stream, args.warmup, args.steps)
+        e_split = cs.energy()
+        t_split = cs.get_amplitudes()
+        cs.close()
+        companion = {"precision": "split", "slices": slices, "bits_per_slice": 4, "digit_type": "e4m3",
+                     "ms_per_step": ms2 / args.steps, "speedup_vs_fp64": ms / ms2,
+                     "abs_dE_vs_fp64_gpu": abs(e_split - e_main),
+                     "max_amp_err_vs_fp64_gpu": float(max(np.max(np.abs(t_split[0] - t_main[0])),
+                                                          np.max(np.abs(t_split[1] - t_main[1])))),
+                     "iterations_compared": args.warmup + args.steps,
+                     "ladder_ms": opd2.get("ladder:gemm")}
+
     if rank != 0:
-        cc.close()
         return
     value = ms / 1e3 / args.steps / world
     peaks, peak_kind = load_peaks()
-    fp64_peak = peaks["bf16_tflops_sustained"] * FP64_OVER_BF16_NOMINAL
-    opd = {}
-    for name, t in ops:
-        opd[name] = opd.get(name, 0.0) + t
     lad_ms = opd.get("ladder:gemm")
     lad_fl = flops.ladder_flops_packed(o, v)
     lad_tf = lad_fl / (lad_ms * 1e-3) / 1e12 if lad_ms else None
     gemm_ms = sum(t for n, t in opd.items() if n.endswith(":gemm"))
     total_op_ms = sum(opd.values())
-    roofline = {"kernel": "zgemm_dmma_kernel (ladder launch, M=o(o-1)/2, N=K=v(v-1)/2)", "bound": "tensor",
-                "achieved": lad_tf, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": (lad_tf / fp64_peak) if lad_tf else None,
-                "peak_basis": f"{peak_kind} bf16_tflops_sustained x 1.25/2250 (nominal dense FP64/BF16 ratio)",
-                "algorithmic_flops_per_launch": lad_fl, "launch_ms": lad_ms,
-                "traffic": recorded_traffic("zgemm_f64.cu", f"ladder_{wl['name']}")}
+    if precision == "fp64":
+        fp64_peak = peaks["bf16_tflops_sustained"] * FP64_OVER_BF16_NOMINAL
+        roofline = {"kernel": "zgemm_dmma_kernel (ladder launch, M=o(o-1)/2, N=K=v(v-1)/2)", "bound": "tensor",
+                    "achieved": lad_tf, "peak": fp64_peak, "unit": "TFLOP/s",
+                    "frac": (lad_tf / fp64_peak) if lad_tf else None,
+                    "peak_basis": f"{peak_kind} bf16_tflops_sustained x 1.25/2250 (nominal dense FP64/BF16 ratio)",
+                    "algorithmic_flops_per_launch": lad_fl, "launch_ms": lad_ms,
+                    "traffic": recorded_traffic("zgemm_f64.cu", f"ladder_{wl['name']}")}
+    else:
+        # the split ladder launch executes P = s(s+1)/2 digit pairs x 4 real e4m3 GEMMs of 2 M N K each
+        pairs = slices * (slices + 1) // 2
+        M, N = flops.pairs(o), flops.pairs(v)
+        fp8_fl = pairs * 8.0 * M * N * N
+        fp8_peak = peaks["bf16_tflops"] * 2.0
+        ach = fp8_fl / (lad_ms * 1e-3) / 1e12 if lad_ms else None
+        roofline = {"kernel": "split_kernel<e4m3> (ladder: digits of tau x cached digits of <ab||cd>)",
+                    "bound": "tensor", "achieved": ach, "peak": fp8_peak, "unit": "TFLOP/s",
+                    "frac": (ach / fp8_peak) if ach else None,
+                    "peak_basis": f"{peak_kind} bf16_tflops (burst) x 2 (nominal dense FP8/BF16 ratio)",
+                    "algorithmic_flops_per_launch": fp8_fl, "launch_ms": lad_ms,
+                    "fp64_equivalent_tflops": lad_tf,
+                    "traffic": recorded_traffic("zgemm_split.cu", f"ladder_{wl['name']}")}
     top = sorted(opd.items(), key=lambda kv: -kv[1])[:8]
     cores = os.cpu_count()
     cpu = None
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and wl["o"] * wl["v"] <= 2400:
         ct = oracle_iteration_time(wl, 1)
         cpu = {"value": ct[0], "unit": "s", "cores": cores, "kind": "oracle",
                "sample": f"one full oracle iteration (Appendix A residual + update, numpy complex128) of the "
                          f"{wl['name']} workload, integrals untimed"}
     line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl["name"], "o": o, "v": v, "naux": wl["naux"], "precision": "fp64",
+            "vs_baseline": None, "dtype": "f64" if precision == "fp64" else "e4m3 digits, f32 accumulate, f64",
+            "data": "synthetic",
+            "config": {"workload": wl["name"], "o": o, "v": v, "naux": wl["naux"], "precision": precision,
+                       "slices": slices if precision == "split" else None,
                        "store_w": True, "level_shift": wl["level_shift"], "diis_dim": 8,
-                       "l2": "inputs larger than L2 (packed <ab||cd> 816 MB, vovv 553 MB at o20/v120)",
+                       "l2": "inputs larger than L2 (packed <ab||cd> and vovv exceed 129 MB)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "ladder_tflops": lad_tf,
             "gemm_share_of_iteration": gemm_ms / total_op_ms if total_op_ms else None,
-            "roofline": roofline, "cpu_baseline": cpu,
+            "roofline": roofline, "split": companion, "cpu_baseline": cpu,
             "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "clocks": clocks, "gpu_launches": kernels * args.steps,
+            "energy": [e_main.real, e_main.imag],
             "top_ops_ms": {k: round(t, 4) for k, t in top}}
     print(json.dumps(line), flush=True)
-    cc.close()
 
 
-def residual_once(wl):
+def residual_once(wl, precision, slices):
     """One eager residual on the workload (NVTX range per op, e.g. "ladder_gemm")."""
     from paper_2103_08473_gb300 import build, inputs
     from paper_2103_08473_gb300 import ccsd as ccmod
 
     ccmod.load(build.build())
     s = inputs.make_system(wl["o"], wl["v"], wl["naux"], wl["seed"])
-    with ccmod.CCSD(s.o, s.v, s.eps, B=s.B, level_shift=wl["level_shift"]) as cc:
+    kw = dict(level_shift=wl["level_shift"])
+    if precision == "split":
+        kw.update(precision=ccmod.PREC_SPLIT, slices=slices)
+    with ccmod.CCSD(s.o, s.v, s.eps, B=s.B, **kw) as cc:
         cc.residual()
     print("residual evaluated", flush=True)
 
@@ -297,13 +353,17 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", choices=sorted(WORKLOADS), default="c2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", choices=["fp64", "split"], default=None,
+                    help="default: fp64 for c1/c2, split for c3")
+    ap.add_argument("--slices", type=int, default=0, help=f"split digits per operand (default {SPLIT_SLICES})")
+    ap.add_argument("--no-split-companion", action="store_true")
     ap.add_argument("--residual-once", action="store_true",
                     help="create the context and evaluate one residual eagerly (for ncu captures), no timing")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)  # timing rule: at least 3 untimed warm-up steps
     wl = WORKLOADS[args.config]
     if args.residual_once:
-        residual_once(wl)
+        residual_once(wl, args.precision or wl["precision"], args.slices or SPLIT_SLICES)
     elif args.impl == "reference":
         run_reference(args, wl)
     else:

@@ -90,7 +90,9 @@ typedef struct {
   int profile;        /* 1: record per-term CUDA-event timings (default 0) */
   void* stream;       /* cudaStream_t, NULL = legacy default stream */
   double split_min_flops; /* split precision: contractions of at least this many flops (8 per complex
-                             multiply-add) run on the tensor cores; the ladder always does (default 2e10) */
+                             multiply-add) run on the tensor cores when a cost model of this GPU says
+                             that is faster than FP64; the ladder always does; <= 0 sends every GEMM
+                             there (default 1e9) */
 } ccsd_opts;
 
 /* Fill opts with the defaults listed above. */

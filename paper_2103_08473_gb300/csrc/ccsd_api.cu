@@ -303,9 +303,14 @@ ccsd_status build_residual_plan(ccsd_ctx* ctx) {
   const int64_t Po = ctx->Po, Pv = ctx->Pv;
   Plan* P = new Plan(o, v, &ctx->scratch, ctx->stream);
   ctx->plan = P;
-  // Large single GEMMs go to the split-precision tensor-core path in split mode.
+  // In split mode a single GEMM of at least split_min_flops goes to the tensor-core digit
+  // path when its modelled time beats the FP64 path (~1 TFLOP/s on this chip); with
+  // split_min_flops <= 0 every GEMM goes there.
   auto to_split = [ctx](const ZGemmArgs& g) {
-    return ctx->use_split && g.batch == 1 && 8.0 * (double)g.M * (double)g.N * (double)g.K >= ctx->split_min_flops;
+    if (!ctx->use_split || g.batch != 1) return false;
+    const double fl = 8.0 * (double)g.M * (double)g.N * (double)g.K;
+    if (ctx->split_min_flops <= 0.0) return true;
+    return fl >= ctx->split_min_flops && split_cost_estimate(g.M, g.N, g.K, ctx->split) < fl / 0.95e12;
   };
   P->set_gemm(
       [ctx, to_split](const ZGemmArgs& g, cudaStream_t s) {
@@ -316,7 +321,10 @@ ccsd_status build_residual_plan(ccsd_ctx* ctx) {
           if (e == cudaSuccess)
             e = make_slices(g.B, g.N, g.K, g.ldb, g.transB ? 0 : 1, g.conjB, ctx->split, SB,
                             w + slice_bytes(g.M, g.K, ctx->split), s);
-          if (e == cudaSuccess) e = split_gemm(SA, SB, g.C, g.ldc, g.alpha, g.beta, ctx->split_err, s);
+          uint8_t* part = w + slice_bytes(g.M, g.K, ctx->split) + slice_bytes(g.N, g.K, ctx->split);
+          if (e == cudaSuccess)
+            e = split_gemm(SA, SB, g.C, g.ldc, g.alpha, g.beta, ctx->split_err, part,
+                           split_part_bytes(g.M, g.N, g.K, ctx->split), s);
           return e;
         }
         ZGemmArgs h = g;
@@ -326,7 +334,9 @@ ccsd_status build_residual_plan(ccsd_ctx* ctx) {
       },
       [to_split](const ZGemmArgs& g) { return to_split(g) ? (int64_t)0 : zgemm_f64_workspace(g); },
       [ctx, to_split](const ZGemmArgs& g) {
-        return to_split(g) ? slice_bytes(g.M, g.K, ctx->split) + slice_bytes(g.N, g.K, ctx->split) : (int64_t)0;
+        return to_split(g) ? slice_bytes(g.M, g.K, ctx->split) + slice_bytes(g.N, g.K, ctx->split) +
+                                 split_part_bytes(g.M, g.N, g.K, ctx->split)
+                           : (int64_t)0;
       });
   const z one = zmake(1, 0), mone = zmake(-1, 0), half = zmake(0.5, 0);
   auto V = [&](z* p, const char* lab) { return P->view(p, lab, true); };
@@ -483,11 +493,14 @@ ccsd_status build_residual_plan(ccsd_ctx* ctx) {
     g.ldc = Pv;
     if (ctx->use_split) {
       // W digits were cut once at creation; only tau is sliced per evaluation
-      P->note_aux_bytes(slice_bytes(Po, Pv, ctx->split));
+      P->note_aux_bytes(slice_bytes(Po, Pv, ctx->split) + split_part_bytes(Po, Pv, Pv, ctx->split));
       z* lpk = ctx->Lpk;
       P->custom("ladder:gemm", [ctx, taupk, lpk, Po, Pv](cudaStream_t s) {
         cudaError_t e = make_slices(taupk, Po, Pv, Pv, 0, 0, ctx->split, ctx->tausl, ctx->split_ws, s);
-        if (e == cudaSuccess) e = split_gemm(ctx->tausl, ctx->Wsl, lpk, Pv, zmake(1, 0), zmake(0, 0), ctx->split_err, s);
+        uint8_t* part = static_cast<uint8_t*>(ctx->split_ws) + slice_bytes(Po, Pv, ctx->split);
+        if (e == cudaSuccess)
+          e = split_gemm(ctx->tausl, ctx->Wsl, lpk, Pv, zmake(1, 0), zmake(0, 0), ctx->split_err, part,
+                         split_part_bytes(Po, Pv, Pv, ctx->split), s);
         return e;
       }, 8.0 * (double)Po * (double)Pv * (double)Pv);
     } else {
@@ -855,7 +868,7 @@ void ccsd_default_opts(ccsd_opts* o) {
   o->store_w = 1;
   o->profile = 0;
   o->stream = nullptr;
-  o->split_min_flops = 2e10;
+  o->split_min_flops = 1e9;
 }
 
 ccsd_status ccsd_create(int o, int v, const double* eps, const ccsd_z* fock, ccsd_int_kind kind, const ccsd_z* ints,

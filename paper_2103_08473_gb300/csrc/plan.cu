@@ -241,9 +241,10 @@ void Plan::contract(const std::string& name, const T& C, z alpha, const T& A0, b
     tA = false;
   }
   if (!bestBok) {
-    Bp = permuted(B, kx + fb, cB, name);
+    // [free][summed] (K contiguous): the layout the digit slicer of the split path reads fastest
+    Bp = permuted(B, fb + kx, cB, name);
     cB = false;
-    tB = false;
+    tB = true;
   }
   int64_t M = 1, N = 1, KK = 1;
   for (char c : fa) M *= A.dims[A.lab.find(c)];

@@ -52,12 +52,20 @@ int64_t slice_bytes(int64_t rows, int64_t K, const SplitConfig& cfg);
 // of slice_bytes). Sets out's shape fields and encodes its tensor map.
 cudaError_t make_slices(const z* X, int64_t rows, int64_t K, int64_t ld, int trans, int conj,
                         const SplitConfig& cfg, SliceSet& out, void* mem, cudaStream_t s);
+// Modelled seconds of one split GEMM of this shape (used to route contractions).
+double split_cost_estimate(int64_t M, int64_t N, int64_t K, const SplitConfig& cfg);
+// Bytes of FP64 partial products split_gemm wants when it splits K across CTAs
+// (outputs with fewer tiles than SMs); 0 when it does not split.
+int64_t split_part_bytes(int64_t M, int64_t N, int64_t K, const SplitConfig& cfg);
 // C = alpha * A B^T + beta * C from slice sets A (M rows) and B (N rows) over the same K.
-// err: device int, set nonzero by the kernel if a bounded wait gave up.
+// err: device int, set nonzero by the kernel if a bounded wait gave up. part_ws: device
+// memory for the K-split partials (split_part_bytes); without it K is not split.
 cudaError_t split_gemm(const SliceSet& A, const SliceSet& B, z* C, int64_t ldc, z alpha, z beta,
-                       int* err, cudaStream_t s);
-// Probe: C (FP64 real, M x N) = A_digits(slice 0, real part) * B_digits(slice 0, real part)^T with
-// no scaling, for exactness checks of the tensor-core accumulation on integer inputs.
-cudaError_t split_probe(const SliceSet& A, const SliceSet& B, double* C, int* err, cudaStream_t s);
+                       int* err, void* part_ws, int64_t part_bytes, cudaStream_t s);
+// Probe: C (FP64 real, M x N) = A B^T for integer-valued A (M x K) and B (N x K) stored as
+// single digits, summed in one FP32 accumulator over all of K (exactness checks of the
+// tensor-core accumulation). mem: 2 slice sets of one digit each.
+cudaError_t split_probe_raw(int kind, const double* Aint, const double* Bint, int64_t M, int64_t N, int64_t K,
+                            double* C, void* mem, int* err, cudaStream_t s);
 
 }  // namespace ccsd

@@ -5,11 +5,6 @@
 #include "errors.h"
 #include "split.h"
 
-namespace ccsd {
-cudaError_t split_probe_raw(int kind, const double* Aint, const double* Bint, int64_t M, int64_t N, int64_t K,
-                            double* C, void* mem, int* err, cudaStream_t s);
-}
-
 using namespace ccsd;
 
 namespace {
@@ -36,7 +31,7 @@ extern "C" {
 size_t ccsd_split_workspace(int kind, int bits, int slices, long long M, long long N, long long K) {
   if (!config_ok(kind, bits, slices) || M < 0 || N < 0 || K < 0) return 0;
   const SplitConfig c = config(kind, bits, slices);
-  return (size_t)(slice_bytes(M, K, c) + slice_bytes(N, K, c)) + kErrBytes;
+  return (size_t)(slice_bytes(M, K, c) + slice_bytes(N, K, c) + split_part_bytes(M, N, K, c)) + kErrBytes;
 }
 
 ccsd_status ccsd_split_zgemm(int kind, int bits, int slices, int transA, int conjA, int transB, int conjB, long long M,
@@ -60,8 +55,10 @@ ccsd_status ccsd_split_zgemm(int kind, int bits, int slices, int transA, int con
   // op(B) is K x N: its columns are the rows of the B digit set
   if (e == cudaSuccess)
     e = make_slices((const z*)B, N, K, ldb, transB ? 0 : 1, conjB, c, SB, w + kErrBytes + slice_bytes(M, K, c), st);
+  uint8_t* part = w + kErrBytes + slice_bytes(M, K, c) + slice_bytes(N, K, c);
   if (e == cudaSuccess)
-    e = split_gemm(SA, SB, (z*)C, ldc, zmake(alpha.re, alpha.im), zmake(beta.re, beta.im), err, st);
+    e = split_gemm(SA, SB, (z*)C, ldc, zmake(alpha.re, alpha.im), zmake(beta.re, beta.im), err, part,
+                   split_part_bytes(M, N, K, c), st);
   int h_err = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

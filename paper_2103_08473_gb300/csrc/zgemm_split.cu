@@ -21,6 +21,7 @@
 #include <cuda_fp8.h>
 #include <cudaTypedefs.h>
 
+#include <climits>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -34,29 +35,28 @@ constexpr int kStages = 3;
 constexpr uint32_t kTile = 128 * 128;        // bytes of one 128-row x 128-byte digit tile
 constexpr uint32_t kStageBytes = 4 * kTile;  // A_re, A_im, B_re, B_im
 constexpr uint32_t kSmemBytes = kStages * kStageBytes + 1024 + 256;
-constexpr int kMaxGroups = 128;
-constexpr int kMaxPairs = 512;
+constexpr int kMaxLevels = 16;
 
-struct SplitSched {
-  int ngroups;
-  int first[kMaxGroups + 1];  // pairs of group g: [first[g], first[g+1])
-  int kb0[kMaxGroups], kb1[kMaxGroups];
-  double gscale[kMaxGroups];  // 2^{-b L}
-  unsigned char pp[kMaxPairs], pq[kMaxPairs];
-};
-
+// Level groups are enumerated on the fly by every role in the same order:
+// for level L = 0..lmax (weight 2^{-b(L+2)}), for K chunks of kbper[L] blocks
+// (short enough that every FP32 partial sum of the level stays below 2^24),
+// intersected with this CTA's K range [klo, khi); the pairs of a level are
+// (p, L - p), p = max(0, L - s + 1) .. min(L, s - 1).
 struct SplitArgs {
   int64_t M, N, Mp, Np;
-  int tiles_m;
+  int tiles_m, tiles;       // output tiles along M, and in total
+  int s, b, lmax, kblocks;  // digits, bits, last level, K blocks
+  int kbper[kMaxLevels];    // K blocks per exact chunk, per level
+  int ksplits, kb_split;    // CTAs along K and K blocks each
   z* C;
   int64_t ldc;
   z alpha;
+  z* part;                  // ksplits > 1: FP64 partial products [ks][M][N] (pre-zeroed)
   const double* rs;
   const double* cs;
-  double* probe;  // probe output (real M x N) or null
+  double* probe;            // probe output (real M x N) or null
   int* err;
   long long wait_cycles;
-  SplitSched sched;
 };
 
 // ---- PTX wrappers ----------------------------------------------------------
@@ -172,9 +172,10 @@ __global__ void __launch_bounds__(192, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tm = blockIdx.x % args.tiles_m, tn = blockIdx.x / args.tiles_m;
+  const int tile = blockIdx.x % args.tiles, ks = blockIdx.x / args.tiles;
+  const int tm = tile % args.tiles_m, tn = tile / args.tiles_m;
   const int64_t m0 = (int64_t)tm * 128, n0 = (int64_t)tn * 128;
-  const SplitSched& S = args.sched;
+  const int klo = ks * args.kb_split, khi = min(args.kblocks, klo + args.kb_split);
   constexpr int BKE = KIND == kSplitBF16 ? 64 : 128;  // digits per 128-byte row segment
 
   if (threadIdx.x == 0) {
@@ -206,24 +207,28 @@ __global__ void __launch_bounds__(192, 1)
     if (lane == 0) {
       int it = 0;
       bool ok = true;
-      for (int g = 0; g < S.ngroups && ok; ++g)
-        for (int kb = S.kb0[g]; kb < S.kb1[g] && ok; ++kb)
-          for (int pi = S.first[g]; pi < S.first[g + 1]; ++pi, ++it) {
-            const int p = S.pp[pi], q = S.pq[pi];
-            const int st = it % kStages;
-            const uint32_t ph = (uint32_t)(it / kStages) & 1u;
-            if (!mbar_wait(empty(st), ph ^ 1u, budget, abort_flag)) {
-              ok = false;
-              break;
+      for (int L = 0; L <= args.lmax && ok; ++L)
+        for (int c0 = 0; c0 < args.kblocks && ok; c0 += args.kbper[L]) {
+          const int gb0 = max(c0, klo), gb1 = min(c0 + args.kbper[L], khi);
+          const int p0 = max(0, L - args.s + 1), p1 = min(L, args.s - 1);
+          for (int kb = gb0; kb < gb1 && ok; ++kb)
+            for (int p = p0; p <= p1; ++p, ++it) {
+              const int q = L - p;
+              const int st = it % kStages;
+              const uint32_t ph = (uint32_t)(it / kStages) & 1u;
+              if (!mbar_wait(empty(st), ph ^ 1u, budget, abort_flag)) {
+                ok = false;
+                break;
+              }
+              const uint32_t sa = base + st * kStageBytes;
+              const int x = kb * BKE;
+              mbar_expect_tx(full(st), PROBE ? 2 * kTile : 4 * kTile);
+              tma_load_2d(sa, &tmA, x, (int)((p * 2 + 0) * args.Mp + m0), full(st));
+              if (!PROBE) tma_load_2d(sa + kTile, &tmA, x, (int)((p * 2 + 1) * args.Mp + m0), full(st));
+              tma_load_2d(sa + 2 * kTile, &tmB, x, (int)((q * 2 + 0) * args.Np + n0), full(st));
+              if (!PROBE) tma_load_2d(sa + 3 * kTile, &tmB, x, (int)((q * 2 + 1) * args.Np + n0), full(st));
             }
-            const uint32_t sa = base + st * kStageBytes;
-            const int x = kb * BKE;
-            mbar_expect_tx(full(st), PROBE ? 2 * kTile : 4 * kTile);
-            tma_load_2d(sa, &tmA, x, (int)((p * 2 + 0) * args.Mp + m0), full(st));
-            if (!PROBE) tma_load_2d(sa + kTile, &tmA, x, (int)((p * 2 + 1) * args.Mp + m0), full(st));
-            tma_load_2d(sa + 2 * kTile, &tmB, x, (int)((q * 2 + 0) * args.Np + n0), full(st));
-            if (!PROBE) tma_load_2d(sa + 3 * kTile, &tmB, x, (int)((q * 2 + 1) * args.Np + n0), full(st));
-          }
+        }
       if (!ok) {
         *abort_flag = 1;
         atomicOr(args.err, 1);
@@ -237,44 +242,49 @@ __global__ void __launch_bounds__(192, 1)
     // ---------------- UMMA issuer ----------------
     if (lane == 0) {
       const uint32_t id = make_idesc(KIND, 0), idn = make_idesc(KIND, 1);
-      int it = 0;
+      int it = 0, g = 0;
       bool ok = true;
-      for (int g = 0; g < S.ngroups && ok; ++g) {
-        const int buf = g & 1, use = g >> 1;
-        if (!mbar_wait(accempty(buf), ((uint32_t)use & 1u) ^ 1u, budget, abort_flag)) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        const uint32_t dre = tmem + (uint32_t)buf * 256u, dim = dre + 128u;
-        bool first = true;
-        for (int kb = S.kb0[g]; kb < S.kb1[g] && ok; ++kb)
-          for (int pi = S.first[g]; pi < S.first[g + 1]; ++pi, ++it) {
-            const int st = it % kStages;
-            const uint32_t ph = (uint32_t)(it / kStages) & 1u;
-            if (!mbar_wait(full(st), ph, budget, abort_flag)) {
-              ok = false;
-              break;
-            }
-            tc_fence_after();
-            const uint32_t sa = base + st * kStageBytes;
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-              const uint32_t acc = (first && kk == 0) ? 0u : 1u;
-              const uint64_t aR = sw128_desc(sa + kk * 32), bR = sw128_desc(sa + 2 * kTile + kk * 32);
-              umma<KIND>(dre, aR, bR, id, acc);
-              if (!PROBE) {
-                const uint64_t aI = sw128_desc(sa + kTile + kk * 32), bI = sw128_desc(sa + 3 * kTile + kk * 32);
-                umma<KIND>(dre, aI, bI, idn, 1u);
-                umma<KIND>(dim, aR, bI, id, acc);
-                umma<KIND>(dim, aI, bR, id, 1u);
-              }
-            }
-            umma_commit(empty(st));
-            first = false;
+      for (int L = 0; L <= args.lmax && ok; ++L)
+        for (int c0 = 0; c0 < args.kblocks && ok; c0 += args.kbper[L]) {
+          const int gb0 = max(c0, klo), gb1 = min(c0 + args.kbper[L], khi);
+          if (gb0 >= gb1) continue;
+          const int p0 = max(0, L - args.s + 1), p1 = min(L, args.s - 1);
+          const int buf = g & 1, use = g >> 1;
+          if (!mbar_wait(accempty(buf), ((uint32_t)use & 1u) ^ 1u, budget, abort_flag)) {
+            ok = false;
+            break;
           }
-        if (ok) umma_commit(accfull(buf));
-      }
+          tc_fence_after();
+          const uint32_t dre = tmem + (uint32_t)buf * 256u, dim = dre + 128u;
+          bool first = true;
+          for (int kb = gb0; kb < gb1 && ok; ++kb)
+            for (int p = p0; p <= p1; ++p, ++it) {
+              const int st = it % kStages;
+              const uint32_t ph = (uint32_t)(it / kStages) & 1u;
+              if (!mbar_wait(full(st), ph, budget, abort_flag)) {
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+              const uint32_t sa = base + st * kStageBytes;
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk) {
+                const uint32_t acc = (first && kk == 0) ? 0u : 1u;
+                const uint64_t aR = sw128_desc(sa + kk * 32), bR = sw128_desc(sa + 2 * kTile + kk * 32);
+                umma<KIND>(dre, aR, bR, id, acc);
+                if (!PROBE) {
+                  const uint64_t aI = sw128_desc(sa + kTile + kk * 32), bI = sw128_desc(sa + 3 * kTile + kk * 32);
+                  umma<KIND>(dre, aI, bI, idn, 1u);
+                  umma<KIND>(dim, aR, bI, id, acc);
+                  umma<KIND>(dim, aI, bR, id, 1u);
+                }
+              }
+              umma_commit(empty(st));
+              first = false;
+            }
+          if (ok) umma_commit(accfull(buf));
+          ++g;
+        }
       if (!ok) {
         *abort_flag = 1;
         atomicOr(args.err, 2);
@@ -290,44 +300,64 @@ __global__ void __launch_bounds__(192, 1)
     const int64_t m = m0 + q4 * 32 + lane;
     const bool mrow = m < args.M;
     const double rsc = (!PROBE && mrow) ? args.rs[m] : 0.0;
-    for (int g = 0; g < S.ngroups; ++g) {
-      const int buf = g & 1, use = g >> 1;
-      if (!mbar_wait(accfull(buf), (uint32_t)use & 1u, budget, abort_flag)) {
-        *abort_flag = 1;
-        atomicOr(args.err, 4);
-        break;
-      }
-      tc_fence_after();
-      const uint32_t trow = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)buf * 256u;
-      const double gs = S.gscale[g];
+    z* const out = args.ksplits > 1 ? args.part + (int64_t)ks * args.M * args.N : args.C;
+    const int64_t ldo = args.ksplits > 1 ? args.N : args.ldc;
+    const z alpha = args.ksplits > 1 ? make_double2(1.0, 0.0) : args.alpha;
+    int g = 0;
+    bool ok = true;
+    for (int L = 0; L <= args.lmax && ok; ++L)
+      for (int c0 = 0; c0 < args.kblocks && ok; c0 += args.kbper[L]) {
+        const int gb0 = max(c0, klo), gb1 = min(c0 + args.kbper[L], khi);
+        if (gb0 >= gb1) continue;
+        const int buf = g & 1, use = g >> 1;
+        if (!mbar_wait(accfull(buf), (uint32_t)use & 1u, budget, abort_flag)) {
+          *abort_flag = 1;
+          atomicOr(args.err, 4);
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t trow = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)buf * 256u;
+        const double gs = ldexp(1.0, -args.b * (L + 2));
+        // real alpha folds into the per-row factor: 1 DMUL + 2 DFMA per complex element
+        const bool real_alpha = alpha.y == 0.0;
+        const double rowf = rsc * gs * (real_alpha ? alpha.x : 1.0);
 #pragma unroll 1
-      for (int c0 = 0; c0 < 128; c0 += 32) {
-        uint32_t re[32], im[32];
-        tmem_ld32(trow + c0, re);
-        if (!PROBE) tmem_ld32(trow + 128 + c0, im);
-        tmem_wait_ld();
-        if (mrow) {
-          if (PROBE) {
-            for (int j = 0; j < 32; ++j) {
-              const int64_t n = n0 + c0 + j;
-              if (n < args.N) args.probe[m * args.N + n] = (double)__uint_as_float(re[j]);
-            }
-          } else {
-            z* crow = args.C + m * args.ldc;
-            for (int j = 0; j < 32; ++j) {
-              const int64_t n = n0 + c0 + j;
-              if (n < args.N) {
-                const double sc = rsc * args.cs[n] * gs;
-                const z v = make_double2((double)__uint_as_float(re[j]) * sc, (double)__uint_as_float(im[j]) * sc);
-                crow[n] = zadd(crow[n], zmul(args.alpha, v));
+        for (int c = 0; c < 128; c += 32) {
+          uint32_t re[32], im[32];
+          tmem_ld32(trow + c, re);
+          if (!PROBE) tmem_ld32(trow + 128 + c, im);
+          tmem_wait_ld();
+          if (mrow) {
+            if (PROBE) {
+              for (int j = 0; j < 32; ++j) {
+                const int64_t n = n0 + c + j;
+                if (n < args.N) args.probe[m * args.N + n] = (double)__uint_as_float(re[j]);
+              }
+            } else {
+              z* orow = out + m * ldo;
+              const int64_t rem = args.N - (n0 + c);
+              const int jmax = rem < 32 ? (int)rem : 32;
+              for (int j = 0; j < jmax; ++j) {
+                const int64_t n = n0 + c + j;
+                const double sc = rowf * args.cs[n];
+                z o = orow[n];
+                if (real_alpha) {
+                  o.x = fma((double)__uint_as_float(re[j]), sc, o.x);
+                  o.y = fma((double)__uint_as_float(im[j]), sc, o.y);
+                } else {
+                  const z v = make_double2((double)__uint_as_float(re[j]) * sc, (double)__uint_as_float(im[j]) * sc);
+                  o = zadd(o, zmul(alpha, v));
+                }
+                orow[n] = o;
               }
             }
           }
         }
+        tc_fence_before();
+        mbar_arrive(accempty(buf));
+        ++g;
       }
-      tc_fence_before();
-      mbar_arrive(accempty(buf));
-    }
   }
   __syncthreads();
   if (warp == 1) {
@@ -438,6 +468,86 @@ __global__ void slice_kernel(const z* __restrict__ X, int64_t rows, int64_t K, i
   }
 }
 
+// Operands whose rows are strided (element (r, k) at X[k*ld + r]): pass 1 finds each row's
+// power-of-two scale with one thread per row (reads coalesced across rows); pass 2 moves
+// 32-row x 64-k tiles through shared memory so both the reads (along r) and the digit
+// stores (along k) are coalesced.
+// Exponent of each row's largest |re|, |im| as an integer max (deterministic): 32 rows x 8
+// K-strides per block, the K range split across blockIdx.y. ex[] starts at INT_MIN.
+__global__ void rowexp_t_kernel(const z* __restrict__ X, int64_t rows, int64_t K, int64_t ld, int* __restrict__ ex) {
+  __shared__ double sh[8][33];
+  const int64_t r = (int64_t)blockIdx.x * 32 + threadIdx.x;
+  double mx = 0.0;
+  if (r < rows)
+    for (int64_t k = (int64_t)blockIdx.y * 8 + threadIdx.y; k < K; k += (int64_t)gridDim.y * 8) {
+      const z v = X[k * ld + r];
+      mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+    }
+  sh[threadIdx.y][threadIdx.x] = mx;
+  __syncthreads();
+  if (threadIdx.y == 0 && r < rows) {
+    for (int y = 1; y < 8; ++y) mx = fmax(mx, sh[y][threadIdx.x]);
+    if (mx > 0.0) {
+      int e = 0;
+      frexp(mx, &e);
+      atomicMax(ex + r, e);
+    }
+  }
+}
+
+__global__ void rowexp_finalize_kernel(const int* __restrict__ ex, int64_t rows, double* __restrict__ scale,
+                                       double* __restrict__ inv) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
+    const int e = ex[r] < -2000 ? 0 : ex[r];  // untouched (all-zero row): memset pattern 0x80808080
+    scale[r] = ldexp(1.0, e);
+    inv[r] = ldexp(1.0, -e);
+  }
+}
+
+template <int KIND>
+__global__ void slice_t_kernel(const z* __restrict__ X, int64_t rows, int64_t K, int64_t ld, int conj, int s, int b,
+                               uint8_t* __restrict__ out, int64_t rows_pad, int64_t Kp, const double* __restrict__ inv) {
+  __shared__ z tile[64][33];
+  const int64_t r0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 64;
+  for (int idx = threadIdx.x; idx < 64 * 32; idx += blockDim.x) {
+    const int kk = idx / 32, rr = idx % 32;
+    const int64_t r = r0 + rr, k = k0 + kk;
+    tile[kk][rr] = (r < rows && k < K) ? X[k * ld + r] : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  for (int item = threadIdx.x; item < 32 * 16; item += blockDim.x) {
+    const int rr = item / 16, kg = item % 16;
+    const int64_t r = r0 + rr, k = k0 + 4 * kg;
+    const double iv = r < rows ? inv[r] : 0.0;
+    long long Vr[4], Vi[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const z v = tile[4 * kg + u][rr];
+      Vr[u] = fixed62(v.x * iv);
+      Vi[u] = fixed62((conj ? -v.y : v.y) * iv);
+    }
+    int shift = 62;
+    for (int p = 0; p < s; ++p) {
+      shift -= b;
+      int dr[4], di[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        dr[u] = next_digit(Vr[u], shift);
+        di[u] = next_digit(Vi[u], shift);
+      }
+      const int64_t o0 = ((int64_t)(p * 2 + 0) * rows_pad + r) * Kp + k;
+      const int64_t o1 = ((int64_t)(p * 2 + 1) * rows_pad + r) * Kp + k;
+      if constexpr (KIND == kSplitBF16) {
+        *reinterpret_cast<uint2*>(out + 2 * o0) = pack4_bf16(dr[0], dr[1], dr[2], dr[3]);
+        *reinterpret_cast<uint2*>(out + 2 * o1) = pack4_bf16(di[0], di[1], di[2], di[3]);
+      } else {
+        *reinterpret_cast<uint32_t*>(out + o0) = pack4_e4m3(dr[0], dr[1], dr[2], dr[3]);
+        *reinterpret_cast<uint32_t*>(out + o1) = pack4_e4m3(di[0], di[1], di[2], di[3]);
+      }
+    }
+  }
+}
+
 // Integer-valued doubles to digits (probe input), real part only, slice 0.
 template <int KIND>
 __global__ void raw_digits_kernel(const double* __restrict__ X, int64_t rows, int64_t K, uint8_t* __restrict__ out,
@@ -485,48 +595,55 @@ cudaError_t encode_map(SliceSet& S) {
 
 double maxdigit(int p, int b) { return p == 0 ? std::ldexp(1.0, b) : std::ldexp(1.0, b - 1); }
 
-// Level groups: pairs (p, q) with equal weight 2^{-b(p+q+2)} (0-based p, q) share an
-// accumulator over K ranges short enough that every partial sum stays below 2^24.
-bool build_schedule(int s, int b, int tri, int kblocks, int kind, bool probe, SplitSched& S) {
-  std::memset(&S, 0, sizeof(S));
-  int ng = 0, np = 0;
-  const int lmax = tri ? s - 1 : 2 * s - 2;  // 0-based level p + q
-  for (int L = 0; L <= lmax; ++L) {
+// K blocks per exact chunk of each level: the pairs (p, L - p) of level L share one
+// FP32 accumulator, so a chunk may add at most (2^24 - 1) / (products_per_k * sum |d_p d_q|)
+// values of k before every partial sum could exceed 2^24.
+bool fill_levels(SplitArgs& a, int s, int b, int kblocks, int kind) {
+  if (s < 1 || s > kMaxLevels) return false;
+  a.s = s;
+  a.b = b;
+  a.lmax = s - 1;
+  a.kblocks = kblocks;
+  for (int L = 0; L <= a.lmax; ++L) {
     double sum = 0.0;
-    int cnt = 0;
-    for (int p = 0; p < s; ++p) {
-      const int q = L - p;
-      if (q < 0 || q >= s) continue;
-      sum += maxdigit(p, b) * maxdigit(q, b);
-      ++cnt;
-      if (probe) break;
-    }
-    if (cnt == 0) continue;
-    const double products_per_k = probe ? 1.0 : 2.0;  // complex: two real products per k per accumulator
-    const double klen = std::floor((16777216.0 - 1.0) / (products_per_k * sum));
-    int kb_per = (int)std::floor(klen / bke(kind));
-    if (kb_per < 1) return false;
-    for (int k0 = 0; k0 < kblocks; k0 += kb_per) {
-      if (ng >= kMaxGroups || np + cnt > kMaxPairs) return false;
-      S.first[ng] = np;
-      S.kb0[ng] = k0;
-      S.kb1[ng] = std::min(kblocks, k0 + kb_per);
-      S.gscale[ng] = std::ldexp(1.0, -b * (L + 2));
-      for (int p = 0; p < s; ++p) {
-        const int q = L - p;
-        if (q < 0 || q >= s) continue;
-        S.pp[np] = (unsigned char)p;
-        S.pq[np] = (unsigned char)q;
-        ++np;
-        if (probe) break;
-      }
-      ++ng;
-    }
-    if (probe) break;
+    for (int p = std::max(0, L - s + 1); p <= std::min(L, s - 1); ++p) sum += maxdigit(p, b) * maxdigit(L - p, b);
+    const double klen = std::floor((16777216.0 - 1.0) / (2.0 * sum));  // complex: 2 products per k
+    const int kb = (int)std::floor(klen / bke(kind));
+    if (kb < 1) return false;
+    a.kbper[L] = kb;
   }
-  S.first[ng] = np;
-  S.ngroups = ng;
   return true;
+}
+
+// K split across CTAs when the output has too few tiles to fill the GPU.
+// Each split keeps >= 16 K blocks so that a level group's MMA work stays above its
+// FP64 flush in the epilogue.
+void plan_ksplit(int64_t tiles, int kblocks, int& ksplits, int& kb_split) {
+  ksplits = 1;
+  if (tiles < 152) {
+    int64_t want = (2 * 152 + tiles - 1) / tiles;
+    ksplits = (int)std::max<int64_t>(1, std::min<int64_t>(want, kblocks / 16));
+  }
+  kb_split = (kblocks + ksplits - 1) / ksplits;
+  ksplits = (kblocks + kb_split - 1) / kb_split;
+}
+
+// C = alpha * sum_ks part[ks] + beta * C, summed in split order.
+__global__ void part_reduce_kernel(const z* __restrict__ part, int ks, int64_t M, int64_t N, z* __restrict__ C,
+                                   int64_t ldc, z alpha, z beta) {
+  const int64_t MN = M * N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < MN; e += (int64_t)gridDim.x * blockDim.x) {
+    double ar = 0.0, ai = 0.0;
+    for (int k = 0; k < ks; ++k) {
+      const z w = part[k * MN + e];
+      ar += w.x;
+      ai += w.y;
+    }
+    z* cp = C + (e / N) * ldc + (e % N);
+    z out = zmul(alpha, make_double2(ar, ai));
+    if (beta.x != 0.0 || beta.y != 0.0) out = zadd(out, zmul(beta, *cp));
+    *cp = out;
+  }
 }
 
 template <int KIND, bool PROBE>
@@ -538,8 +655,7 @@ cudaError_t launch_split(const SliceSet& A, const SliceSet& B, const SplitArgs& 
     attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
   });
   if (attr_err != cudaSuccess) return attr_err;
-  const int64_t tiles_n = (a.N + 127) / 128;
-  const int64_t grid = (int64_t)a.tiles_m * tiles_n;
+  const int64_t grid = (int64_t)a.tiles * a.ksplits;
   if (grid <= 0) return cudaSuccess;
   if (grid > 0x7fffffff) return cudaErrorInvalidValue;
   kern<<<(unsigned)grid, 192, kSmemBytes, s>>>(A.tmap, B.tmap, a);
@@ -551,7 +667,8 @@ cudaError_t launch_split(const SliceSet& A, const SliceSet& B, const SplitArgs& 
 int64_t slice_bytes(int64_t rows, int64_t K, const SplitConfig& cfg) {
   const int64_t rows_pad = round_up(std::max<int64_t>(rows, 1), 128);
   const int64_t Kp = round_up(std::max<int64_t>(K, 1), bke(cfg.kind));
-  return round_up((int64_t)cfg.s * 2 * rows_pad * Kp * esize(cfg.kind), 1024) + round_up(rows_pad * 8, 1024);
+  // digits, then per-row scale and inverse scale (doubles) and exponent (int)
+  return round_up((int64_t)cfg.s * 2 * rows_pad * Kp * esize(cfg.kind), 1024) + 3 * round_up(rows_pad * 8, 1024);
 }
 
 cudaError_t make_slices(const z* X, int64_t rows, int64_t K, int64_t ld, int trans, int conj, const SplitConfig& cfg,
@@ -570,6 +687,25 @@ cudaError_t make_slices(const z* X, int64_t rows, int64_t K, int64_t ld, int tra
                                         round_up((int64_t)cfg.s * 2 * out.rows_pad * out.Kp * esize(cfg.kind), 1024));
   cudaError_t e = encode_map(out);
   if (e != cudaSuccess) return e;
+  if (trans) {
+    double* inv = out.scale + round_up(out.rows_pad * 8, 1024) / 8;
+    int* ex = reinterpret_cast<int*>(inv + round_up(out.rows_pad * 8, 1024) / 8);
+    cudaError_t e = cudaMemsetAsync(ex, 0x80, (size_t)rows * sizeof(int), s);  // 0x80808080 < every exponent
+    if (e != cudaSuccess) return e;
+    const int64_t rb = (rows + 31) / 32;
+    const int64_t ky = std::max<int64_t>(1, std::min<int64_t>((K + 63) / 64, (152 * 64 + rb - 1) / rb));
+    rowexp_t_kernel<<<dim3((unsigned)rb, (unsigned)std::min<int64_t>(ky, 65535)), dim3(32, 8), 0, s>>>(X, rows, K, ld, ex);
+    rowexp_finalize_kernel<<<grid_for(rows, 256), 256, 0, s>>>(ex, rows, out.scale, inv);
+    const dim3 grid((unsigned)(out.rows_pad / 32), (unsigned)(out.Kp / 64));
+    if (grid.y > 65535) return cudaErrorInvalidValue;
+    if (cfg.kind == kSplitBF16)
+      slice_t_kernel<kSplitBF16><<<grid, 256, 0, s>>>(X, rows, K, ld, conj, cfg.s, cfg.b, (uint8_t*)out.digits,
+                                                      out.rows_pad, out.Kp, inv);
+    else
+      slice_t_kernel<kSplitE4M3><<<grid, 256, 0, s>>>(X, rows, K, ld, conj, cfg.s, cfg.b, (uint8_t*)out.digits,
+                                                      out.rows_pad, out.Kp, inv);
+    return cudaGetLastError();
+  }
   const int grid = (int)std::min<int64_t>(out.rows_pad, 152 * 16);
   if (cfg.kind == kSplitBF16)
     slice_kernel<kSplitBF16><<<grid, 256, 0, s>>>(X, rows, K, ld, trans, conj, cfg.s, cfg.b, (uint8_t*)out.digits,
@@ -580,20 +716,39 @@ cudaError_t make_slices(const z* X, int64_t rows, int64_t K, int64_t ld, int tra
   return cudaGetLastError();
 }
 
+double split_cost_estimate(int64_t M, int64_t N, int64_t K, const SplitConfig& cfg) {
+  // Model of one split GEMM on this GPU: the tensor-core digit products at ~2.8 PFLOP/s
+  // (e4m3; half for bf16), each level group's FP64 flush (~6 FP64 operations per complex
+  // output element of every 128x128 tile) at ~5e11 operations/s, and slicing both operands
+  // (read twice, digits written once) at ~5 TB/s. Padding to whole tiles and K blocks counted.
+  const int bk = bke(cfg.kind);
+  const double Mp = (double)round_up(M, 128), Np = (double)round_up(N, 128), Kp = (double)round_up(K, bk);
+  const double pairs = 0.5 * cfg.s * (cfg.s + 1);
+  const double mma = pairs * 8.0 * Mp * Np * Kp / (cfg.kind == kSplitBF16 ? 1.4e15 : 2.8e15);
+  SplitArgs a;
+  std::memset(&a, 0, sizeof(a));
+  const int kblocks = (int)(Kp / bk);
+  double groups = 0.0;
+  if (!fill_levels(a, cfg.s, cfg.b, kblocks, cfg.kind)) return 1e30;
+  for (int L = 0; L <= a.lmax; ++L) groups += std::ceil((double)kblocks / a.kbper[L]);
+  const double tiles = (Mp / 128.0) * (Np / 128.0);
+  const double flush = tiles * groups * 16384.0 * 6.0 / 5e11;
+  const double slicing = ((double)(M + N) * K * 32.0 + (double)(M + N) * Kp * 2.0 * cfg.s * esize(cfg.kind)) / 5e12;
+  return std::max(mma, flush) + slicing;
+}
+
+int64_t split_part_bytes(int64_t M, int64_t N, int64_t K, const SplitConfig& cfg) {
+  const int64_t tiles = ((M + 127) / 128) * ((N + 127) / 128);
+  const int kblocks = (int)((std::max<int64_t>(K, 1) + bke(cfg.kind) - 1) / bke(cfg.kind));
+  int ks, kbs;
+  plan_ksplit(tiles, kblocks, ks, kbs);
+  return ks > 1 ? (int64_t)ks * M * N * (int64_t)sizeof(z) : 0;
+}
+
 cudaError_t split_gemm(const SliceSet& A, const SliceSet& B, z* C, int64_t ldc, z alpha, z beta, int* err,
-                       cudaStream_t s) {
+                       void* part_ws, int64_t part_bytes, cudaStream_t s) {
   if (A.kind != B.kind || A.Kp != B.Kp || A.s != B.s || A.b != B.b || !A.have_map || !B.have_map)
     return cudaErrorInvalidValue;
-  if (beta.x != 1.0 || beta.y != 0.0) {
-    ZGemmArgs g;
-    g.M = A.rows;
-    g.N = B.rows;
-    g.C = C;
-    g.ldc = ldc;
-    g.beta = beta;
-    cudaError_t e = zscale_matrix(g, s);
-    if (e != cudaSuccess) return e;
-  }
   SplitArgs a;
   std::memset(&a, 0, sizeof(a));
   a.M = A.rows;
@@ -601,6 +756,7 @@ cudaError_t split_gemm(const SliceSet& A, const SliceSet& B, z* C, int64_t ldc, 
   a.Mp = A.rows_pad;
   a.Np = B.rows_pad;
   a.tiles_m = (int)((A.rows + 127) / 128);
+  a.tiles = a.tiles_m * (int)((B.rows + 127) / 128);
   a.C = C;
   a.ldc = ldc;
   a.alpha = alpha;
@@ -608,8 +764,32 @@ cudaError_t split_gemm(const SliceSet& A, const SliceSet& B, z* C, int64_t ldc, 
   a.cs = B.scale;
   a.err = err;
   a.wait_cycles = 4000000000LL;  // ~2 s at 2 GHz
-  if (!build_schedule(A.s, A.b, 1, (int)(A.Kp / bke(A.kind)), A.kind, false, a.sched)) return cudaErrorInvalidValue;
-  return A.kind == kSplitBF16 ? launch_split<kSplitBF16, false>(A, B, a, s) : launch_split<kSplitE4M3, false>(A, B, a, s);
+  const int kblocks = (int)(A.Kp / bke(A.kind));
+  if (!fill_levels(a, A.s, A.b, kblocks, A.kind)) return cudaErrorInvalidValue;
+  plan_ksplit(a.tiles, kblocks, a.ksplits, a.kb_split);
+  const int64_t need = a.ksplits > 1 ? (int64_t)a.ksplits * a.M * a.N * (int64_t)sizeof(z) : 0;
+  if (a.ksplits > 1 && (part_ws == nullptr || part_bytes < need)) {
+    a.ksplits = 1;
+    a.kb_split = kblocks;
+  }
+  cudaError_t e = cudaSuccess;
+  if (a.ksplits > 1) {
+    a.part = static_cast<z*>(part_ws);
+    e = cudaMemsetAsync(part_ws, 0, need, s);
+  } else if (beta.x != 1.0 || beta.y != 0.0) {
+    ZGemmArgs g;
+    g.M = A.rows;
+    g.N = B.rows;
+    g.C = C;
+    g.ldc = ldc;
+    g.beta = beta;
+    e = zscale_matrix(g, s);
+  }
+  if (e != cudaSuccess) return e;
+  e = A.kind == kSplitBF16 ? launch_split<kSplitBF16, false>(A, B, a, s) : launch_split<kSplitE4M3, false>(A, B, a, s);
+  if (e != cudaSuccess || a.ksplits == 1) return e;
+  part_reduce_kernel<<<grid_for(a.M * a.N, 256), 256, 0, s>>>(a.part, a.ksplits, a.M, a.N, C, ldc, alpha, beta);
+  return cudaGetLastError();
 }
 
 cudaError_t split_probe_raw(int kind, const double* Aint, const double* Bint, int64_t M, int64_t N, int64_t K,
@@ -650,17 +830,18 @@ cudaError_t split_probe_raw(int kind, const double* Aint, const double* Bint, in
   a.Mp = A.rows_pad;
   a.Np = B.rows_pad;
   a.tiles_m = (int)((M + 127) / 128);
+  a.tiles = a.tiles_m * (int)((N + 127) / 128);
   a.probe = C;
   a.err = err;
   a.wait_cycles = 4000000000LL;
-  SplitSched& S = a.sched;
-  std::memset(&S, 0, sizeof(S));
-  S.ngroups = 1;
-  S.first[0] = 0;
-  S.first[1] = 1;
-  S.kb0[0] = 0;
-  S.kb1[0] = (int)(A.Kp / bke(kind));
-  S.gscale[0] = 1.0;
+  // one group: the single pair (0, 0) over the whole K in one accumulator
+  a.s = 1;
+  a.b = cfg.b;
+  a.lmax = 0;
+  a.kblocks = (int)(A.Kp / bke(kind));
+  a.kbper[0] = a.kblocks;
+  a.ksplits = 1;
+  a.kb_split = a.kblocks;
   return kind == kSplitBF16 ? launch_split<kSplitBF16, true>(A, B, a, s) : launch_split<kSplitE4M3, true>(A, B, a, s);
 }
 
