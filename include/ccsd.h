@@ -86,13 +86,16 @@ typedef struct {
   double level_shift; /* added to virtual orbital energies in the denominators only (default 0) */
   int precision;      /* ccsd_precision (default CCSD_PREC_FP64) */
   int slices;         /* split precision: 4-bit e4m3 digits per operand, 1..14 (default 0 = 11) */
-  int store_w;        /* 1: store <ab||cd> (packed); 0: rebuild ladder tiles from B (default 1) */
+  int store_w;        /* 1: store <ab||cd> (packed); 0: never store it, rebuild it in blocks of rows
+                         from the DF factors inside each ladder evaluation (DF input only) (default 1) */
   int profile;        /* 1: record per-term CUDA-event timings (default 0) */
   void* stream;       /* cudaStream_t, NULL = legacy default stream */
   double split_min_flops; /* split precision: contractions of at least this many flops (8 per complex
                              multiply-add) run on the tensor cores when a cost model of this GPU says
                              that is faster than FP64; the ladder always does; <= 0 sends every GEMM
                              there (default 1e9) */
+  int df_block;       /* store_w = 0: virtual indices a per rebuilt block of <ab||cd> rows
+                         (default 0 = as many as fit about 2 GB of (ac|bd)) */
 } ccsd_opts;
 
 /* Fill opts with the defaults listed above. */

@@ -30,7 +30,7 @@ class ccsd_opts(C.Structure):
     _fields_ = [("max_iter", C.c_int), ("tol", C.c_double), ("norm", C.c_int), ("diis_dim", C.c_int),
                 ("diis_start", C.c_int), ("level_shift", C.c_double), ("precision", C.c_int),
                 ("slices", C.c_int), ("store_w", C.c_int), ("profile", C.c_int), ("stream", C.c_void_p),
-                ("split_min_flops", C.c_double)]
+                ("split_min_flops", C.c_double), ("df_block", C.c_int)]
 
 
 class CCSDError(RuntimeError):

@@ -60,6 +60,10 @@ struct ccsd_ctx {
   int64_t split_ws_bytes = 0;
   int* split_err = nullptr;  // set by the tensor-core kernel if a bounded wait gave up
   SliceSet Wsl, tausl;       // <ab||cd> digits (built once) and tau digits (per evaluation)
+  void* tausl_mem = nullptr; // tau digits of the on-the-fly ladder (kept across its blocks)
+  // store_w = 0: B^Q over virtuals, and per-block (ac|bd) and packed <ab||cd> rows
+  z *Bvv = nullptr, *Dblk = nullptr, *Wblk = nullptr;
+  int df_block = 0;
   // iteration state
   double* upd_partials = nullptr;
   double* stats = nullptr;
@@ -295,6 +299,115 @@ ccsd_status build_block_full(ccsd_ctx* ctx, const z* V, const char* sp, z* out) 
 }
 
 // ---------------------------------------------------------------------------
+// Particle-particle ladder with <ab||cd> never stored: for blocks of a, rebuild
+// D[(a,c)][(b,d)] = (ac|bd) = sum_Q B^Q_ac B^Q_bd for b > a (one GEMM over Q), pack the rows
+// <ab||cd> = (ac|bd) - (ad|bc) for a < b, c < d, and contract them at once against tau:
+// Lpk[P(ij)][P(ab)] = sum_{c<d} tau^{cd}_{ij} <ab||cd> for those a b columns.
+// ---------------------------------------------------------------------------
+struct DfBlock {
+  int64_t a0, a1, AB0, AB1;
+};
+
+std::vector<DfBlock> df_blocks(int64_t v, int64_t blk) {
+  std::vector<DfBlock> out;
+  for (int64_t a0 = 0; a0 < v - 1; a0 += blk) {
+    DfBlock b;
+    b.a0 = a0;
+    b.a1 = std::min(v - 1, a0 + blk);
+    b.AB0 = pair_index(a0, a0 + 1, v);
+    b.AB1 = b.a1 >= v - 1 ? pair_count(v) : pair_index(b.a1, b.a1 + 1, v);
+    out.push_back(b);
+  }
+  return out;
+}
+
+ccsd_status plan_df_ladder(ccsd_ctx* ctx, Plan* P) {
+  const int64_t v = ctx->v, naux = ctx->naux, Po = ctx->Po, Pv = ctx->Pv;
+  int64_t blk = ctx->opts.df_block;
+  if (blk <= 0) blk = std::max<int64_t>(1, (int64_t)(2e9 / (16.0 * (double)v * v * v)));
+  blk = std::min<int64_t>(blk, std::max<int64_t>(v - 1, 1));
+  ctx->df_block = (int)blk;
+  const auto blocks = df_blocks(v, blk);
+  int64_t dmax = 0, wmax = 0;
+  for (const auto& b : blocks) {
+    dmax = std::max(dmax, (b.a1 - b.a0) * v * (v - b.a0 - 1) * v);
+    wmax = std::max(wmax, b.AB1 - b.AB0);
+  }
+  CS(dalloc(ctx, &ctx->Dblk, dmax));
+  CS(dalloc(ctx, &ctx->Wblk, wmax * Pv));
+  // GEMM shapes of the blocks, for the workspace peaks
+  for (const auto& b : blocks) {
+    ZGemmArgs gd;
+    gd.M = (b.a1 - b.a0) * v;
+    gd.N = (v - b.a0 - 1) * v;
+    gd.K = naux;
+    P->note_gemm(gd);
+    ZGemmArgs gl;
+    gl.M = Po;
+    gl.N = b.AB1 - b.AB0;
+    gl.K = Pv;
+    gl.transB = 1;
+    if (ctx->use_split)
+      P->note_aux_bytes(slice_bytes(gl.N, Pv, ctx->split) + split_part_bytes(Po, gl.N, Pv, ctx->split));
+    else
+      P->note_gemm(gl);
+  }
+  if (ctx->use_split) {
+    uint8_t* m = nullptr;
+    CS(dalloc(ctx, &m, slice_bytes(Po, Pv, ctx->split)));
+    ctx->tausl_mem = m;
+  }
+  const double fl = 8.0 * (double)Po * (double)Pv * (double)Pv;
+  P->custom("ladder:gemm", [ctx, blocks, v, naux, Po, Pv](cudaStream_t s) {
+    const GemmFn& gemm = ctx->plan->gemm_fn();
+    cudaError_t e = cudaSuccess;
+    if (ctx->use_split)
+      e = make_slices(ctx->tau_pk, Po, Pv, Pv, 0, 0, ctx->split, ctx->tausl, ctx->tausl_mem, s);
+    for (const auto& b : blocks) {
+      if (e != cudaSuccess) break;
+      ZGemmArgs gd;  // D[(a,c)][(b,d)] = sum_Q B^Q_{ac} B^Q_{bd}, a in [a0, a1), b > a0
+      gd.M = (b.a1 - b.a0) * v;
+      gd.N = (v - b.a0 - 1) * v;
+      gd.K = naux;
+      gd.A = ctx->Bvv + b.a0 * v;
+      gd.lda = v * v;
+      gd.transA = 1;
+      gd.B = ctx->Bvv + (b.a0 + 1) * v;
+      gd.ldb = v * v;
+      gd.C = ctx->Dblk;
+      gd.ldc = gd.N;
+      e = gemm(gd, s);
+      if (e == cudaSuccess) e = pack_vvvv_rows(ctx->Dblk, ctx->Wblk, v, b.a0, b.a1, s);
+      const int64_t nb = b.AB1 - b.AB0;
+      if (e != cudaSuccess || nb <= 0) continue;
+      if (ctx->use_split) {
+        SliceSet SW;
+        uint8_t* w = static_cast<uint8_t*>(ctx->split_ws);
+        e = make_slices(ctx->Wblk, nb, Pv, Pv, 0, 0, ctx->split, SW, w, s);
+        if (e == cudaSuccess)
+          e = split_gemm(ctx->tausl, SW, ctx->Lpk + b.AB0, Pv, zmake(1, 0), zmake(0, 0), ctx->split_err,
+                         w + slice_bytes(nb, Pv, ctx->split), split_part_bytes(Po, nb, Pv, ctx->split), s);
+      } else {
+        ZGemmArgs gl;  // Lpk[:, AB0:AB1] = tau_pk W_blk^T
+        gl.M = Po;
+        gl.N = nb;
+        gl.K = Pv;
+        gl.A = ctx->tau_pk;
+        gl.lda = Pv;
+        gl.B = ctx->Wblk;
+        gl.ldb = Pv;
+        gl.transB = 1;
+        gl.C = ctx->Lpk + b.AB0;
+        gl.ldc = Pv;
+        e = gemm(gl, s);
+      }
+    }
+    return e;
+  }, fl);
+  return CCSD_OK;
+}
+
+// ---------------------------------------------------------------------------
 // The residual plan: Appendix A, one contraction per printed term.
 // Labels i,j,k,l run over occupied and a,b,c,d over virtual spinors.
 // ---------------------------------------------------------------------------
@@ -491,7 +604,9 @@ ccsd_status build_residual_plan(ccsd_ctx* ctx) {
     g.transB = 1;
     g.C = ctx->Lpk;
     g.ldc = Pv;
-    if (ctx->use_split) {
+    if (!ctx->opts.store_w) {
+      CS(plan_df_ladder(ctx, P));
+    } else if (ctx->use_split) {
       // W digits were cut once at creation; only tau is sliced per evaluation
       P->note_aux_bytes(slice_bytes(Po, Pv, ctx->split) + split_part_bytes(Po, Pv, Pv, ctx->split));
       z* lpk = ctx->Lpk;
@@ -658,7 +773,8 @@ ccsd_status create_impl(int o, int v, const double* eps, const ccsd_z* fock, ccs
     ctx->split_min_flops = ctx->opts.split_min_flops;
     if (ctx->split.s > 14) return set_err(ctx, CCSD_ERR_ARG, "slices must be <= 14 (4-bit e4m3 digits)");
   }
-  if (!ctx->opts.store_w) return set_err(ctx, CCSD_ERR_UNSUPPORTED, "store_w = 0 is not available in this build");
+  if (!ctx->opts.store_w && kind != CCSD_INT_DF)
+    return set_err(ctx, CCSD_ERR_UNSUPPORTED, "store_w = 0 needs DF factors (CCSD_INT_DF)");
   const int n = ctx->n;
   if (fock && !hermitian(fock, n, 1)) return set_err(ctx, CCSD_ERR_ARG, "Fock matrix is not Hermitian");
   if (kind == CCSD_INT_DF && !hermitian(ints, n, naux)) return set_err(ctx, CCSD_ERR_ARG, "B^Q is not Hermitian in (p,r)");
@@ -699,7 +815,8 @@ ccsd_status create_impl(int o, int v, const double* eps, const ccsd_z* fock, ccs
   CS(dalloc(ctx, &ctx->oovv, oo * vv));
   CS(dalloc(ctx, &ctx->vovo, ov * ov));
   CS(dalloc(ctx, &ctx->vovv, ov * vv));
-  CS(dalloc(ctx, &ctx->Wpk, ctx->Pv * ctx->Pv));
+  if (ctx->opts.store_w) CS(dalloc(ctx, &ctx->Wpk, ctx->Pv * ctx->Pv));
+  else CS(dalloc(ctx, &ctx->Bvv, (int64_t)naux * v * v));
   {
     void* dints = nullptr;
     const int64_t cnt = kind == CCSD_INT_DF ? (int64_t)naux * n * n : (int64_t)n * n * n * n;
@@ -716,7 +833,10 @@ ccsd_status create_impl(int o, int v, const double* eps, const ccsd_z* fock, ccs
       st = kind == CCSD_INT_DF ? build_block_df(ctx, (const z*)dints, names[b], outs[b])
                                : build_block_full(ctx, (const z*)dints, names[b], outs[b]);
     if (st == CCSD_OK) {
-      if (kind == CCSD_INT_DF) {
+      if (kind == CCSD_INT_DF && !ctx->opts.store_w) {
+        e = extract_B(ctx, (const z*)dints, 'v', 'v', ctx->Bvv, ctx->stream);
+        if (e != cudaSuccess) st = set_err(ctx, CCSD_ERR_CUDA, cudaGetErrorString(e));
+      } else if (kind == CCSD_INT_DF) {
         st = build_w_df(ctx, (const z*)dints);
       } else {
         z* vvvv = nullptr;
@@ -740,7 +860,7 @@ ccsd_status create_impl(int o, int v, const double* eps, const ccsd_z* fock, ccs
   }
   CS(dalloc(ctx, &ctx->split_err, 1));
   CK(cudaMemsetAsync(ctx->split_err, 0, sizeof(int), ctx->stream));
-  if (ctx->use_split) {
+  if (ctx->use_split && ctx->opts.store_w) {
     // <ab||cd> is constant: cut its digits once
     uint8_t* mem = nullptr;
     CS(dalloc(ctx, &mem, slice_bytes(ctx->Pv, ctx->Pv, ctx->split)));
@@ -869,6 +989,7 @@ void ccsd_default_opts(ccsd_opts* o) {
   o->profile = 0;
   o->stream = nullptr;
   o->split_min_flops = 1e9;
+  o->df_block = 0;
 }
 
 ccsd_status ccsd_create(int o, int v, const double* eps, const ccsd_z* fock, ccsd_int_kind kind, const ccsd_z* ints,

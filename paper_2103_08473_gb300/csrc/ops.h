@@ -51,6 +51,9 @@ cudaError_t unpack_pairs(const UnpackArgs& a, cudaStream_t s);
 
 // W[P(a,b)][P(c,d)] = D[a][c][b][d] - D[a][d][b][c]  (D dense v^4 Coulomb block (ac|bd))
 cudaError_t pack_vvvv(const z* D, z* W, int64_t v, cudaStream_t s);
+// Rows of the same packed W for a in [a0, a1), b in (a, v), from the block
+// D[(a - a0) v + c][(b - a0 - 1) v + d] = (ac|bd) (b > a0 only): W[P(a,b) - P(a0,a0+1)][P(c,d)].
+cudaError_t pack_vvvv_rows(const z* D, z* W, int64_t v, int64_t a0, int64_t a1, cudaStream_t s);
 
 // Denominator update over t1 (o*v) and full t2 (o*o*v*v):
 //   d = S / D, t += d, S <- d.   D^a_i = e_i - e_a - shift, D^{ab}_{ij} = e_i + e_j - e_a - e_b - 2 shift

@@ -86,6 +86,11 @@ class Plan {
     auxfn_ = std::move(aux);
   }
   void note_aux_bytes(int64_t b) { aux_peak_ = std::max(aux_peak_, b); }
+  // Size the workspaces for a GEMM that a custom op will run through gemm_fn().
+  void note_gemm(const ZGemmArgs& g) {
+    if (wsfn_) ws_peak_ = std::max(ws_peak_, wsfn_(g));
+    if (auxfn_) aux_peak_ = std::max(aux_peak_, auxfn_(g));
+  }
   int64_t aux_bytes() const { return aux_peak_; }
   const GemmFn& gemm_fn() const { return gemm_; }
   // Largest GEMM workspace any op of the plan wants (complex elements).

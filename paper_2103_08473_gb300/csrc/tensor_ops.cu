@@ -165,6 +165,21 @@ __global__ void pack_vvvv_kernel(const z* __restrict__ D, z* __restrict__ W, int
   }
 }
 
+__global__ void pack_vvvv_rows_kernel(const z* __restrict__ D, z* __restrict__ W, int64_t v, int64_t a0, int64_t AB0,
+                                      int64_t rows) {
+  const int64_t P = pair_count(v), Nd = (v - a0 - 1) * v;
+  const int64_t total = rows * P;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t a, b, c, d;
+    pair_decode(AB0 + e / P, v, a, b);
+    pair_decode(e % P, v, c, d);
+    const z* Da = D + (a - a0) * v * Nd;
+    // <ab||cd> = (ac|bd) - (ad|bc)
+    W[e] = zsub(Da[c * Nd + (b - a0 - 1) * v + d], Da[d * Nd + (b - a0 - 1) * v + c]);
+  }
+}
+
 // ---- update and norms ------------------------------------------------------
 
 template <typename T>
@@ -505,6 +520,15 @@ cudaError_t pack_vvvv(const z* D, z* W, int64_t v, cudaStream_t s) {
   const int64_t P = pair_count(v);
   if (P == 0) return cudaSuccess;
   pack_vvvv_kernel<<<grid_for(P * P, kThreads), kThreads, 0, s>>>(D, W, v);
+  return cudaGetLastError();
+}
+
+cudaError_t pack_vvvv_rows(const z* D, z* W, int64_t v, int64_t a0, int64_t a1, cudaStream_t s) {
+  const int64_t AB0 = pair_index(a0, a0 + 1, v);
+  const int64_t AB1 = a1 >= v - 1 ? pair_count(v) : pair_index(a1, a1 + 1, v);
+  const int64_t rows = AB1 - AB0;
+  if (rows <= 0) return cudaSuccess;
+  pack_vvvv_rows_kernel<<<grid_for(rows * pair_count(v), kThreads), kThreads, 0, s>>>(D, W, v, a0, AB0, rows);
   return cudaGetLastError();
 }
 

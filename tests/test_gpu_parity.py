@@ -187,3 +187,21 @@ def test_full_size_o20_v120_residual_and_iterations(ccsd):
     ref = R.solve(f, V, s.o, s.v, max_iter=2, tol=0.0, shift=20.0)
     assert abs(e2 - ref["energy"]) < 1e-10
     assert np.max(np.abs(h2 - ref["t2"])) < 1e-9 and np.max(np.abs(h1 - ref["t1"])) < 1e-9
+
+
+@pytest.mark.parametrize("o,v,naux,seed,blk", [(5, 17, 23, 301, 3), (7, 37, 50, 302, 0), (4, 9, 11, 303, 1)])
+def test_df_ladder_without_stored_w_matches_oracle(ccsd, o, v, naux, seed, blk):
+    """store_w = 0: <ab||cd> is rebuilt from B^Q in blocks of a inside each ladder evaluation."""
+    s, f, fock = _sys(o, v, naux, seed, 0.1, 0.02)
+    V = R.integrals(s.B, o)
+    t1, t2 = inputs.random_amplitudes(o, v, seed + 1, scale=0.1)
+    S1, S2 = R.residual(f, V, t1, t2)
+    with ccsd.CCSD(o, v, s.eps, B=s.B, fock=fock, store_w=0, df_block=blk) as cc:
+        r1, r2 = cc.residual(t1, t2)
+        lad = cc.get_tensor("ladder")
+        st, it, nrm = cc.iterate(3)
+        e = cc.energy()
+    assert _maxrel(r1, S1) < 1e-12 and _maxrel(r2, S2) < 1e-12
+    assert _maxrel(lad, R.ladder(V["vvvv"], R.tau(t1, t2))) < 1e-12
+    ref = R.solve(f, V, o, v, max_iter=3, tol=0.0)
+    assert abs(e - ref["energy"]) < 1e-10

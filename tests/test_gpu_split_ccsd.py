@@ -66,3 +66,18 @@ def test_split_full_size_o20_v120_two_iterations(ccsd):
         t1, t2 = cc.get_amplitudes()
     assert abs(e - ref["energy"]) < 1e-8
     assert max(np.max(np.abs(t1 - ref["t1"])), np.max(np.abs(t2 - ref["t2"]))) < 1e-8
+
+
+def test_split_df_ladder_without_stored_w(ccsd):
+    o, v, naux, seed = 6, 29, 40, 211
+    s = inputs.make_system(o, v, naux, seed, scale=0.05)
+    f = R.fock_matrix(s.eps)
+    V = R.integrals(s.B, o)
+    t1, t2 = inputs.random_amplitudes(o, v, seed + 1, scale=0.05)
+    S1, S2 = R.residual(f, V, t1, t2)
+    with ccsd.CCSD(o, v, s.eps, B=s.B, precision=ccsd.PREC_SPLIT, split_min_flops=0.0, store_w=0,
+                   df_block=4) as cc:
+        r1, r2 = cc.residual(t1, t2)
+        lad = cc.get_tensor("ladder")
+    assert _maxrel(r1, S1) < 1e-10 and _maxrel(r2, S2) < 1e-10
+    assert _maxrel(lad, R.ladder(V["vvvv"], R.tau(t1, t2))) < 1e-10
