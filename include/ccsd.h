@@ -96,6 +96,8 @@ typedef struct {
                              there (default 1e9) */
   int df_block;       /* store_w = 0: virtual indices a per rebuilt block of <ab||cd> rows
                          (default 0 = as many as fit about 2 GB of (ac|bd)) */
+  int autotune;       /* 1: at creation, time every FP64 GEMM of the plan in each tile shape and keep
+                         the fastest (default 0: a cost model picks the shape) */
 } ccsd_opts;
 
 /* Fill opts with the defaults listed above. */
@@ -236,6 +238,31 @@ ccsd_status ccsd_zgemm_noalloc(int precision, int transA, int conjA, int transB,
                                long long N, long long K, ccsd_z alpha, const ccsd_z* A, long long lda,
                                const ccsd_z* B, long long ldb, ccsd_z beta, ccsd_z* C, long long ldc, int cfg,
                                void* stream);
+
+/*
+ * Batched solve of many independent systems (the paper's calculations are one
+ * system at a time; this is a throughput mode of the library). Each system k has
+ * o[k], v[k], eps[k] (n_k doubles), DF factors B[k] ([naux[k]][n_k][n_k]) and the
+ * Fock matrix diag(eps[k]). All systems share opts (opts->stream is the stream the
+ * batch launches on). One batch iteration is one CUDA graph launch in which every
+ * still-active system runs its own iteration on its own stream (fork/join), so the
+ * small systems fill the GPU together; systems drop out as they converge
+ * (norm <= opts->tol) or diverge. Amplitudes start at each system's MP2 guess.
+ */
+typedef struct ccsd_batch ccsd_batch;
+ccsd_status ccsd_batch_create(int nsys, const int* o, const int* v, const double* const* eps,
+                              const ccsd_z* const* B, const int* naux, const ccsd_opts* opts, ccsd_batch** out);
+/* Up to max_iter batch iterations (<= 0: opts.max_iter). Per system (arrays of nsys, may be
+ * NULL): iterations run, last norm, and status (CCSD_OK converged, CCSD_ERR_NOT_CONVERGED,
+ * CCSD_ERR_DIVERGED). Returns CCSD_OK if every system converged, else CCSD_ERR_NOT_CONVERGED
+ * (or the first CUDA error). */
+ccsd_status ccsd_batch_iterate(ccsd_batch* b, int max_iter, int* iters_done, double* res_norm, int* status);
+/* Energies of the current amplitudes of every system (nsys values). */
+ccsd_status ccsd_batch_energy(ccsd_batch* b, ccsd_z* e);
+/* Amplitudes of system k (as ccsd_get_amplitudes). */
+ccsd_status ccsd_batch_get_amplitudes(ccsd_batch* b, int k, ccsd_z* t1, ccsd_z* t2, int on_device);
+const char* ccsd_batch_last_error(const ccsd_batch* b);
+void ccsd_batch_destroy(ccsd_batch* b);
 
 /* Message for the last failing call on ctx; with ctx NULL, of the last failed call made without a
  * context (ccsd_create, ccsd_zgemm, ccsd_zgemm_noalloc) on this host thread. */

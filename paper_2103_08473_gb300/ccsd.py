@@ -30,7 +30,7 @@ class ccsd_opts(C.Structure):
     _fields_ = [("max_iter", C.c_int), ("tol", C.c_double), ("norm", C.c_int), ("diis_dim", C.c_int),
                 ("diis_start", C.c_int), ("level_shift", C.c_double), ("precision", C.c_int),
                 ("slices", C.c_int), ("store_w", C.c_int), ("profile", C.c_int), ("stream", C.c_void_p),
-                ("split_min_flops", C.c_double), ("df_block", C.c_int)]
+                ("split_min_flops", C.c_double), ("df_block", C.c_int), ("autotune", C.c_int)]
 
 
 class CCSDError(RuntimeError):
@@ -66,6 +66,12 @@ SIGNATURES = [
                                    C.c_longlong, _P, C.c_size_t, _P]),
     ("ccsd_split_probe", C.c_int, [C.c_int, C.c_longlong, C.c_longlong, C.c_longlong, _P, _P, _P, _P, C.c_size_t,
                                    _P]),
+    ("ccsd_batch_create", C.c_int, [C.c_int, _P, _P, _P, _P, _P, C.POINTER(ccsd_opts), C.POINTER(_P)]),
+    ("ccsd_batch_iterate", C.c_int, [_P, C.c_int, _P, _P, _P]),
+    ("ccsd_batch_energy", C.c_int, [_P, _P]),
+    ("ccsd_batch_get_amplitudes", C.c_int, [_P, C.c_int, _P, _P, C.c_int]),
+    ("ccsd_batch_last_error", C.c_char_p, [_P]),
+    ("ccsd_batch_destroy", None, [_P]),
     ("ccsd_last_error", C.c_char_p, [_P]),
     ("ccsd_destroy", None, [_P]),
 ]
@@ -328,3 +334,69 @@ def split_probe(a, b, kind=SPLIT_E4M3):
     if st != OK:
         raise CCSDError(st, lib.ccsd_last_error(None).decode())
     return out
+
+
+class Batch:
+    """Many independent systems iterated together (wraps a ccsd_batch)."""
+
+    def __init__(self, systems, **opts):
+        """systems: list of (o, v, eps, B) with B of shape (naux, n, n)."""
+        lib = load()
+        self._lib = lib
+        self.nsys = len(systems)
+        self.shapes = [(int(o), int(v)) for (o, v, _, _) in systems]
+        self._eps = [np.ascontiguousarray(e, dtype=np.float64) for (_, _, e, _) in systems]
+        self._B = [np.ascontiguousarray(b, dtype=np.complex128) for (_, _, _, b) in systems]
+        oa = (C.c_int * self.nsys)(*[s[0] for s in self.shapes])
+        va = (C.c_int * self.nsys)(*[s[1] for s in self.shapes])
+        na = (C.c_int * self.nsys)(*[b.shape[0] for b in self._B])
+        ep = (C.c_void_p * self.nsys)(*[e.ctypes.data for e in self._eps])
+        bp = (C.c_void_p * self.nsys)(*[b.ctypes.data for b in self._B])
+        self._opts = default_opts(**opts)
+        h = C.c_void_p()
+        st = lib.ccsd_batch_create(self.nsys, oa, va, ep, bp, na, C.byref(self._opts), C.byref(h))
+        if st != OK:
+            raise CCSDError(st, lib.ccsd_last_error(None).decode())
+        self._h = h
+
+    def iterate(self, max_iter=0):
+        it = (C.c_int * self.nsys)()
+        nrm = (C.c_double * self.nsys)()
+        sts = (C.c_int * self.nsys)()
+        st = self._lib.ccsd_batch_iterate(self._h, int(max_iter), it, nrm, sts)
+        if st not in (OK, ERR_NOT_CONVERGED):
+            raise CCSDError(st, self._lib.ccsd_batch_last_error(self._h).decode())
+        return st, list(it), list(nrm), list(sts)
+
+    def energies(self):
+        e = (ccsd_z * self.nsys)()
+        st = self._lib.ccsd_batch_energy(self._h, e)
+        if st != OK:
+            raise CCSDError(st, self._lib.ccsd_batch_last_error(self._h).decode())
+        return [complex(x.re, x.im) for x in e]
+
+    def get_amplitudes(self, k):
+        o, v = self.shapes[k]
+        t1, t2 = np.empty((o, v), np.complex128), np.empty((o, o, v, v), np.complex128)
+        st = self._lib.ccsd_batch_get_amplitudes(self._h, int(k), t1.ctypes.data_as(C.c_void_p),
+                                                 t2.ctypes.data_as(C.c_void_p), 0)
+        if st != OK:
+            raise CCSDError(st, self._lib.ccsd_batch_last_error(self._h).decode())
+        return t1, t2
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.ccsd_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

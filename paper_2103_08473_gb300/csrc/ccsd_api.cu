@@ -3,7 +3,10 @@
 // amplitude checkpointing and inspection.
 #include <cmath>
 #include <algorithm>
+#include <array>
 #include <cstring>
+#include <functional>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -64,6 +67,7 @@ struct ccsd_ctx {
   // store_w = 0: B^Q over virtuals, and per-block (ac|bd) and packed <ab||cd> rows
   z *Bvv = nullptr, *Dblk = nullptr, *Wblk = nullptr;
   int df_block = 0;
+  std::function<bool(const ZGemmArgs&)> routes_split;
   // iteration state
   double* upd_partials = nullptr;
   double* stats = nullptr;
@@ -425,6 +429,7 @@ ccsd_status build_residual_plan(ccsd_ctx* ctx) {
     if (ctx->split_min_flops <= 0.0) return true;
     return fl >= ctx->split_min_flops && split_cost_estimate(g.M, g.N, g.K, ctx->split) < fl / 0.95e12;
   };
+  ctx->routes_split = to_split;
   P->set_gemm(
       [ctx, to_split](const ZGemmArgs& g, cudaStream_t s) {
         if (to_split(g)) {
@@ -443,7 +448,7 @@ ccsd_status build_residual_plan(ccsd_ctx* ctx) {
         ZGemmArgs h = g;
         h.ws = ctx->gemm_ws;
         h.ws_elems = ctx->gemm_ws_elems;
-        return zgemm_f64(h, s);
+        return zgemm_f64(h, s, h.cfg);
       },
       [to_split](const ZGemmArgs& g) { return to_split(g) ? (int64_t)0 : zgemm_f64_workspace(g); },
       [ctx, to_split](const ZGemmArgs& g) {
@@ -748,6 +753,53 @@ bool hermitian(const ccsd_z* m, int64_t n, int64_t count) {
   return true;
 }
 
+// Measured tile choice for every FP64 GEMM op of the plan: after one warm-up launch each of
+// the 7 tile configurations runs twice between CUDA events and the fastest is kept. Shapes
+// already in `cache` reuse their result. GEMMs routed to the split path are left alone.
+// Outputs of the timed launches are garbage; the plan is run afresh afterwards.
+using TuneCache = std::map<std::array<int64_t, 5>, int>;
+ccsd_status autotune_plan(ccsd_ctx* ctx, TuneCache& cache) {
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  ccsd_status st = CCSD_OK;
+  for (auto& op : ctx->plan->ops()) {
+    if (!op.cfg || !op.args) continue;
+    const ZGemmArgs& g = *op.args;
+    if (ctx->routes_split && ctx->routes_split(g)) continue;
+    const std::array<int64_t, 5> key = {g.M, g.N, g.K, g.transA, g.transB};
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      *op.cfg = it->second;
+      continue;
+    }
+    int best = -1;
+    float bt = 0.f;
+    for (int c = 0; c < 7 && st == CCSD_OK; ++c) {
+      *op.cfg = c;
+      cudaError_t e = op.run(ctx->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
+      for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = op.run(ctx->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) st = set_err(ctx, CCSD_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+      else if (best < 0 || ms < bt) {
+        best = c;
+        bt = ms;
+      }
+    }
+    *op.cfg = best;
+    cache[key] = best;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return st;
+}
+
+TuneCache* g_tune_cache = nullptr;  // shared by the systems of one batch while it is created
+
 ccsd_status create_impl(int o, int v, const double* eps, const ccsd_z* fock, ccsd_int_kind kind, const ccsd_z* ints,
                         int naux, const ccsd_opts* opts, ccsd_ctx* ctx) {
   if (o < 1 || v < 1) return set_err(ctx, CCSD_ERR_ARG, "o and v must be >= 1");
@@ -944,6 +996,10 @@ ccsd_status create_impl(int o, int v, const double* eps, const ccsd_z* fock, ccs
 
   CS(build_residual_plan(ctx));
   init_timers(ctx);
+  if (ctx->opts.autotune) {
+    TuneCache local;
+    CS(autotune_plan(ctx, g_tune_cache ? *g_tune_cache : local));
+  }
 
   // MP2 guess: one denominator update from t = 0
   CK(run_ops(ctx, false));
@@ -990,6 +1046,7 @@ void ccsd_default_opts(ccsd_opts* o) {
   o->stream = nullptr;
   o->split_min_flops = 1e9;
   o->df_block = 0;
+  o->autotune = 0;
 }
 
 ccsd_status ccsd_create(int o, int v, const double* eps, const ccsd_z* fock, ccsd_int_kind kind, const ccsd_z* ints,
@@ -1230,6 +1287,203 @@ ccsd_status ccsd_zgemm(int precision, int transA, int conjA, int transB, int con
   CK(cudaStreamSynchronize(st));
   return CCSD_OK;
 }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched systems: one context per system, one fork/join CUDA graph per batch
+// iteration over the still-active systems.
+// ---------------------------------------------------------------------------
+struct ccsd_batch {
+  std::vector<ccsd_ctx*> sys;
+  cudaStream_t main = nullptr;
+  bool own_main = false;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  cudaGraphExec_t graph = nullptr;
+  std::vector<int> active, in_graph, iters, status;
+  std::vector<double> norms;
+  double* stats_host = nullptr;  // pinned, 2 per system
+  int* err_host = nullptr;       // pinned, 1 per system
+  std::string err;
+};
+
+namespace {
+
+ccsd_status batch_err(ccsd_batch* b, ccsd_status st, const std::string& msg) {
+  b->err = msg;
+  return st;
+}
+
+void batch_free(ccsd_batch* b) {
+  if (!b) return;
+  if (b->main) cudaStreamSynchronize(b->main);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (ccsd_ctx* c : b->sys) free_ctx(c);
+  for (auto e : b->join) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->stats_host) cudaFreeHost(b->stats_host);
+  if (b->err_host) cudaFreeHost(b->err_host);
+  if (b->own_main && b->main) cudaStreamDestroy(b->main);
+  delete b;
+}
+
+// Capture: fork from the batch stream to every active system's stream, run its iteration
+// (residual, update, norms, DIIS) and copy its norms to pinned memory, join back.
+ccsd_status batch_build_graph(ccsd_batch* b) {
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  b->in_graph = b->active;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(b->main, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) e = cudaEventRecord(b->fork, b->main);
+  for (int k : b->in_graph) {
+    ccsd_ctx* c = b->sys[k];
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, b->fork, 0);
+    if (e == cudaSuccess) e = iteration_ops(c, false);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b->stats_host + 2 * k, c->stats, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && c->use_split)
+      e = cudaMemcpyAsync(b->err_host + k, c->split_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(b->join[k], c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->main, b->join[k], 0);
+  }
+  cudaError_t e2 = cudaStreamEndCapture(b->main, &g);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return batch_err(b, CCSD_ERR_CUDA, std::string("batch graph capture: ") +
+                                            cudaGetErrorString(e != cudaSuccess ? e : e2));
+  }
+  e = cudaGraphInstantiate(&b->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return batch_err(b, CCSD_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+  return CCSD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ccsd_status ccsd_batch_create(int nsys, const int* o, const int* v, const double* const* eps,
+                              const ccsd_z* const* B, const int* naux, const ccsd_opts* opts, ccsd_batch** out) {
+  if (!out) return set_err(nullptr, CCSD_ERR_ARG, "out must not be NULL");
+  *out = nullptr;
+  if (nsys < 1 || !o || !v || !eps || !B || !naux) return set_err(nullptr, CCSD_ERR_ARG, "bad batch arguments");
+  ccsd_opts base;
+  if (opts) base = *opts;
+  else ccsd_default_opts(&base);
+  ccsd_batch* b = new ccsd_batch();
+  if (base.stream) {
+    b->main = (cudaStream_t)base.stream;
+  } else if (cudaStreamCreateWithFlags(&b->main, cudaStreamNonBlocking) == cudaSuccess) {
+    b->own_main = true;
+  } else {
+    batch_free(b);
+    return set_err(nullptr, CCSD_ERR_CUDA, "batch stream");
+  }
+  TuneCache cache;  // shared tile choices across systems of equal GEMM shapes
+  g_tune_cache = &cache;
+  for (int k = 0; k < nsys; ++k) {
+    ccsd_opts ok = base;
+    ok.stream = nullptr;  // every system on its own stream
+    ok.profile = 0;
+    ccsd_ctx* c = nullptr;
+    ccsd_status st = ccsd_create(o[k], v[k], eps[k], nullptr, CCSD_INT_DF, B[k], naux[k], &ok, &c);
+    if (st != CCSD_OK) {
+      g_tune_cache = nullptr;
+      const std::string msg = "system " + std::to_string(k) + ": " + g_create_error;
+      batch_free(b);
+      return set_err(nullptr, st, msg);
+    }
+    b->sys.push_back(c);
+  }
+  g_tune_cache = nullptr;
+  b->join.resize(nsys);
+  bool ok = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+  for (auto& e : b->join) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+  ok = ok && cudaMallocHost(&b->stats_host, 2 * nsys * sizeof(double)) == cudaSuccess;
+  ok = ok && cudaMallocHost(&b->err_host, nsys * sizeof(int)) == cudaSuccess;
+  if (!ok) {
+    batch_free(b);
+    return set_err(nullptr, CCSD_ERR_CUDA, "batch events / pinned memory");
+  }
+  for (int k = 0; k < nsys; ++k) b->err_host[k] = 0;
+  b->active.resize(nsys);
+  for (int k = 0; k < nsys; ++k) b->active[k] = k;
+  b->iters.assign(nsys, 0);
+  b->status.assign(nsys, CCSD_ERR_NOT_CONVERGED);
+  b->norms.assign(nsys, INFINITY);
+  *out = b;
+  return CCSD_OK;
+}
+
+ccsd_status ccsd_batch_iterate(ccsd_batch* b, int max_iter, int* iters_done, double* res_norm, int* status) {
+  if (!b) return CCSD_ERR_ARG;
+  const int nsys = (int)b->sys.size();
+  if (max_iter <= 0) max_iter = b->sys[0]->opts.max_iter;
+  for (int it = 0; it < max_iter && !b->active.empty(); ++it) {
+    if (!b->graph || b->in_graph != b->active) {
+      ccsd_status st = batch_build_graph(b);
+      if (st != CCSD_OK) return st;
+    }
+    cudaError_t e = cudaGraphLaunch(b->graph, b->main);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->main);
+    if (e != cudaSuccess) return batch_err(b, CCSD_ERR_CUDA, std::string("batch iteration: ") + cudaGetErrorString(e));
+    std::vector<int> still;
+    for (int k : b->active) {
+      ccsd_ctx* c = b->sys[k];
+      b->iters[k] += 1;
+      c->iterations_run += 1;
+      const double mx = b->stats_host[2 * k], l2 = b->stats_host[2 * k + 1];
+      const double nrm = c->opts.norm == 1 ? l2 : mx;
+      b->norms[k] = nrm;
+      if (c->use_split && b->err_host[k]) {
+        b->status[k] = CCSD_ERR_TIMEOUT;
+      } else if (!std::isfinite(mx) || !std::isfinite(l2)) {
+        const int64_t n1 = (int64_t)c->o * c->v, n2 = n1 * c->o * c->v;
+        cudaMemcpyAsync(c->t1, c->t1_prev, n1 * sizeof(z), cudaMemcpyDeviceToDevice, c->stream);
+        cudaMemcpyAsync(c->t2, c->t2_prev, n2 * sizeof(z), cudaMemcpyDeviceToDevice, c->stream);
+        cudaStreamSynchronize(c->stream);
+        b->status[k] = CCSD_ERR_DIVERGED;
+      } else if (nrm <= c->opts.tol) {
+        b->status[k] = CCSD_OK;
+      } else {
+        still.push_back(k);
+      }
+    }
+    b->active = still;
+  }
+  bool all_ok = true;
+  for (int k = 0; k < nsys; ++k) {
+    if (iters_done) iters_done[k] = b->iters[k];
+    if (res_norm) res_norm[k] = b->norms[k];
+    if (status) status[k] = b->status[k];
+    all_ok = all_ok && b->status[k] == CCSD_OK;
+  }
+  if (!all_ok) return batch_err(b, CCSD_ERR_NOT_CONVERGED, "not every system converged");
+  return CCSD_OK;
+}
+
+ccsd_status ccsd_batch_energy(ccsd_batch* b, ccsd_z* e) {
+  if (!b || !e) return CCSD_ERR_ARG;
+  for (size_t k = 0; k < b->sys.size(); ++k) {
+    ccsd_status st = ccsd_energy(b->sys[k], e + k);
+    if (st != CCSD_OK) return batch_err(b, st, "system " + std::to_string(k) + ": " + b->sys[k]->err);
+  }
+  return CCSD_OK;
+}
+
+ccsd_status ccsd_batch_get_amplitudes(ccsd_batch* b, int k, ccsd_z* t1, ccsd_z* t2, int on_device) {
+  if (!b || k < 0 || k >= (int)b->sys.size()) return CCSD_ERR_ARG;
+  return ccsd_get_amplitudes(b->sys[k], t1, t2, on_device);
+}
+
+const char* ccsd_batch_last_error(const ccsd_batch* b) { return b ? b->err.c_str() : g_create_error.c_str(); }
+
+void ccsd_batch_destroy(ccsd_batch* b) { batch_free(b); }
 
 const char* ccsd_last_error(const ccsd_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
 

@@ -120,7 +120,13 @@ void Plan::gemm(const std::string& name, const ZGemmArgs& g) {
   if (wsfn_) ws_peak_ = std::max(ws_peak_, wsfn_(g));
   if (auxfn_) aux_peak_ = std::max(aux_peak_, auxfn_(g));
   GemmFn fn = gemm_;
-  ops_.push_back(Op{name, [fn, g](cudaStream_t s) { return fn(g, s); }, 8.0 * g.M * g.N * g.K * g.batch});
+  auto cfg = std::make_shared<int>(-1);
+  auto args = std::make_shared<ZGemmArgs>(g);
+  ops_.push_back(Op{name, [fn, args, cfg](cudaStream_t s) {
+                      ZGemmArgs h = *args;
+                      h.cfg = *cfg;
+                      return fn(h, s);
+                    }, 8.0 * g.M * g.N * g.K * g.batch, cfg, args});
 }
 
 void Plan::add(const std::string& name, const T& C, z alpha, const T& A, bool conjA, double beta) {
@@ -299,13 +305,16 @@ void Plan::contract(const std::string& name, const T& C, z alpha, const T& A0, b
     if (wsfn_) ws_peak_ = std::max(ws_peak_, wsfn_(g));
     if (auxfn_) aux_peak_ = std::max(aux_peak_, auxfn_(g));
     GemmFn fn = gemm_;
+    auto cfg = std::make_shared<int>(-1);
+    auto args = std::make_shared<ZGemmArgs>(g);
     ops_.push_back(Op{name + ":gemm", [=](cudaStream_t s) {
-                        ZGemmArgs h = g;
+                        ZGemmArgs h = *args;
                         h.A = pa.get();
                         h.B = pb.get();
                         h.C = pc.get();
+                        h.cfg = *cfg;
                         return fn(h, s);
-                      }, flops});
+                      }, flops, cfg, args});
   }
   if (need_out_perm) add(name + ":out", C, alpha, Cp, false, beta);
   scratch_off_ = mark;

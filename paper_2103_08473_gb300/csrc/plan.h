@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <functional>
 #include <map>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -57,6 +58,10 @@ struct Op {
   std::string name;
   std::function<cudaError_t(cudaStream_t)> run;
   double flops = 0.0;  // algorithmic real flops (8 per complex multiply-add)
+  // GEMM ops: the arguments (pointers resolved at run time) and the tile configuration the
+  // autotuner may set (-1 = cost model).
+  std::shared_ptr<int> cfg;
+  std::shared_ptr<ZGemmArgs> args;
 };
 
 class Plan {

@@ -25,6 +25,7 @@ struct ZGemmArgs {
   // split K into S slices whose partial products go to ws and are summed in a fixed order.
   z* ws = nullptr;
   int64_t ws_elems = 0;
+  int cfg = -1;  // FP64 tile configuration (0..6), -1 = cost model
 };
 
 // FP64 tensor-core (DMMA) path. cfg < 0 picks the tile shape from the tile count.
