@@ -143,6 +143,22 @@ def ladder(vvvv: np.ndarray, ta: np.ndarray) -> np.ndarray:
     return 0.5 * np.einsum("abcd,ijcd->ijab", vvvv, ta, optimize=True)
 
 
+def ladder_elements(B: np.ndarray, o: int, t1: np.ndarray, t2: np.ndarray, idx) -> np.ndarray:
+    """Selected elements of the ladder 1/2 sum_cd V^{ab}_{cd} tau^{cd}_{ij}, from B^Q directly.
+
+    For each (i, j, a, b) in ``idx`` the row <ab||cd> = (ac|bd) - (ad|bc) over all c, d is
+    formed from the DF factors, so no n^4 tensor is ever built (full-size sampling).
+    """
+    out = np.empty(len(idx), np.complex128)
+    Bv = B[:, o:, o:]
+    for n, (i, j, a, b) in enumerate(idx):
+        coul = Bv[:, a, :].T @ Bv[:, b, :]          # (ac|bd) over (c, d)
+        w = coul - coul.T                           # <ab||cd> = (ac|bd) - (ad|bc)
+        ta = t2[i, j] + np.outer(t1[i], t1[j]) - np.outer(t1[j], t1[i])   # tau^{cd}_{ij}
+        out[n] = 0.5 * np.sum(w * ta)
+    return out
+
+
 def residual(f: np.ndarray, V: dict, t1: np.ndarray, t2: np.ndarray, parts: dict | None = None):
     """S^a_i and S^{ab}_{ij} of Appendix A at amplitudes (t1, t2).
 

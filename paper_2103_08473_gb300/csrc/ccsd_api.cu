@@ -199,7 +199,27 @@ ccsd_status coulomb_df(ccsd_ctx* ctx, const z* B, char P, char Rr, char Q, char 
   g.ldb = g.N;
   g.C = D;
   g.ldc = g.N;
-  CK(zgemm_f64(g, ctx->stream));
+  if (!ctx->use_split) {
+    CK(zgemm_f64(g, ctx->stream));
+    return CCSD_OK;
+  }
+  // split mode: the Coulomb blocks on the tensor cores too, with 11 digits (they are built once)
+  SplitConfig c = ctx->split;
+  c.s = std::max(c.s, 11);
+  const int64_t sa = slice_bytes(g.M, g.K, c), sb = slice_bytes(g.N, g.K, c), sp = split_part_bytes(g.M, g.N, g.K, c);
+  void* mem = nullptr;
+  if (cudaMalloc(&mem, sa + sb + sp) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(ctx, CCSD_ERR_OOM, "slices of the Coulomb build");
+  }
+  uint8_t* w = static_cast<uint8_t*>(mem);
+  SliceSet SA, SB;
+  cudaError_t e = make_slices(g.A, g.M, g.K, g.lda, 1, 0, c, SA, w, ctx->stream);
+  if (e == cudaSuccess) e = make_slices(g.B, g.N, g.K, g.ldb, 1, 0, c, SB, w + sa, ctx->stream);
+  if (e == cudaSuccess) e = split_gemm(SA, SB, D, g.ldc, zmake(1, 0), zmake(0, 0), ctx->split_err, w + sa + sb, sp, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  cudaFree(mem);
+  if (e != cudaSuccess) return set_err(ctx, CCSD_ERR_CUDA, std::string("split Coulomb build: ") + cudaGetErrorString(e));
   return CCSD_OK;
 }
 
@@ -860,6 +880,8 @@ ccsd_status create_impl(int o, int v, const double* eps, const ccsd_z* fock, ccs
   CK(cudaMemcpyAsync(ctx->fov, fov.data(), sizeof(z) * o * v, cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(ctx->fvv, fvv.data(), sizeof(z) * v * v, cudaMemcpyHostToDevice, ctx->stream));
 
+  CS(dalloc(ctx, &ctx->split_err, 1));
+  CK(cudaMemsetAsync(ctx->split_err, 0, sizeof(int), ctx->stream));
   // integral blocks
   const int64_t oo = (int64_t)o * o, vv = (int64_t)v * v, ov = (int64_t)o * v;
   CS(dalloc(ctx, &ctx->oooo, oo * oo));
@@ -910,8 +932,6 @@ ccsd_status create_impl(int o, int v, const double* eps, const ccsd_z* fock, ccs
     cudaFree(dints);
     if (st != CCSD_OK) return st;
   }
-  CS(dalloc(ctx, &ctx->split_err, 1));
-  CK(cudaMemsetAsync(ctx->split_err, 0, sizeof(int), ctx->stream));
   if (ctx->use_split && ctx->opts.store_w) {
     // <ab||cd> is constant: cut its digits once
     uint8_t* mem = nullptr;

@@ -81,3 +81,27 @@ def test_split_df_ladder_without_stored_w(ccsd):
         lad = cc.get_tensor("ladder")
     assert _maxrel(r1, S1) < 1e-10 and _maxrel(r2, S2) < 1e-10
     assert _maxrel(lad, R.ladder(V["vvvv"], R.tau(t1, t2))) < 1e-10
+
+
+def test_split_full_size_o40_v240_sampled_ladder(ccsd):
+    """The o40/v240/naux800 split workload: sampled ladder elements against the oracle (computed
+    element by element from B^Q), and antisymmetry of the residual at full size."""
+    s = inputs.make_config("c3")
+    o, v = s.o, s.v
+    t1, t2 = inputs.random_amplitudes(o, v, 303, scale=0.01)
+    with ccsd.CCSD(o, v, s.eps, B=s.B, precision=ccsd.PREC_SPLIT, slices=11, level_shift=40.0) as cc:
+        r1, r2 = cc.residual(t1, t2)
+        lad = cc.get_tensor("ladder")
+    rng = np.random.default_rng(4)
+    idx = []
+    while len(idx) < 64:
+        i, j, a, b = (int(rng.integers(o)), int(rng.integers(o)), int(rng.integers(v)), int(rng.integers(v)))
+        if i != j and a != b:
+            idx.append((i, j, a, b))
+    want = R.ladder_elements(s.B, o, t1, t2, idx)
+    got = np.array([lad[i, j, a, b] for (i, j, a, b) in idx])
+    scale = np.max(np.abs(lad))
+    assert np.max(np.abs(got - want)) < 1e-11 * scale
+    tol = 1e-13 * np.max(np.abs(r2))
+    assert np.max(np.abs(r2 + r2.transpose(1, 0, 2, 3))) <= tol
+    assert np.max(np.abs(r2 + r2.transpose(0, 1, 3, 2))) <= tol

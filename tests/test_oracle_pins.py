@@ -266,3 +266,17 @@ def test_diis_reproduces_linear_extrapolation():
     np.testing.assert_allclose(d.coefficients(), [0.5, 0.5], atol=1e-15)
     t1, t2 = d.extrapolate()
     np.testing.assert_allclose(t2, 0.5 * (t2a + t2b), atol=1e-16)
+
+
+def test_sampled_ladder_elements_match_full_ladder():
+    """The element-wise ladder used for full-size sampling agrees with the full einsum."""
+    o, v, naux = 4, 11, 13
+    s = inputs.make_system(o, v, naux, 81, scale=0.3)
+    t1, t2 = inputs.random_amplitudes(o, v, 82, scale=0.2)
+    full = R.ladder(R.integrals(s.B, o)["vvvv"], R.tau(t1, t2))
+    rng = np.random.default_rng(3)
+    idx = [tuple(int(x) for x in (rng.integers(o), rng.integers(o), rng.integers(v), rng.integers(v)))
+           for _ in range(40)]
+    got = R.ladder_elements(s.B, o, t1, t2, idx)
+    want = np.array([full[i, j, a, b] for (i, j, a, b) in idx])
+    np.testing.assert_allclose(got, want, atol=1e-14)
