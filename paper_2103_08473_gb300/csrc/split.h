@@ -34,6 +34,7 @@ struct SliceSet {
   double* scale = nullptr;  // device, 2^e per row (rows entries)
   int64_t rows = 0, rows_pad = 0, K = 0, Kp = 0;
   int s = 0, b = 0, kind = kSplitE4M3;
+  int64_t chunk = 0, nchunks = 1;  // K chunking of the slicing work (rows with K contiguous)
   CUtensorMap tmap;  // 2D map over the digit array, box {128 bytes, 128 rows}, 128B swizzle
   bool have_map = false;
 };

@@ -335,21 +335,48 @@ __global__ void __launch_bounds__(192, 1)
                 if (n < args.N) args.probe[m * args.N + n] = (double)__uint_as_float(re[j]);
               }
             } else {
-              z* orow = out + m * ldo;
+              z* orow = out + m * ldo + n0 + c;
+              const double* csc = args.cs + n0 + c;
               const int64_t rem = args.N - (n0 + c);
-              const int jmax = rem < 32 ? (int)rem : 32;
-              for (int j = 0; j < jmax; ++j) {
-                const int64_t n = n0 + c + j;
-                const double sc = rowf * args.cs[n];
-                z o = orow[n];
-                if (real_alpha) {
-                  o.x = fma((double)__uint_as_float(re[j]), sc, o.x);
-                  o.y = fma((double)__uint_as_float(im[j]), sc, o.y);
-                } else {
-                  const z v = make_double2((double)__uint_as_float(re[j]) * sc, (double)__uint_as_float(im[j]) * sc);
-                  o = zadd(o, zmul(alpha, v));
+              if (rem >= 32) {
+                // whole chunk, 8 columns at a time: all loads first so their latencies overlap
+#pragma unroll
+                for (int j0 = 0; j0 < 32; j0 += 8) {
+                  double sc[8];
+                  z ov[8];
+#pragma unroll
+                  for (int j = 0; j < 8; ++j) {
+                    sc[j] = csc[j0 + j];
+                    ov[j] = orow[j0 + j];
+                  }
+#pragma unroll
+                  for (int j = 0; j < 8; ++j) {
+                    const double f = rowf * sc[j];
+                    const double vr = (double)__uint_as_float(re[j0 + j]), vi = (double)__uint_as_float(im[j0 + j]);
+                    if (real_alpha) {
+                      ov[j].x = fma(vr, f, ov[j].x);
+                      ov[j].y = fma(vi, f, ov[j].y);
+                    } else {
+                      ov[j] = zadd(ov[j], zmul(alpha, make_double2(vr * f, vi * f)));
+                    }
+                    orow[j0 + j] = ov[j];
+                  }
                 }
-                orow[n] = o;
+              } else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                  if (j >= rem) break;
+                  const double f = rowf * csc[j];
+                  const double vr = (double)__uint_as_float(re[j]), vi = (double)__uint_as_float(im[j]);
+                  z o = orow[j];
+                  if (real_alpha) {
+                    o.x = fma(vr, f, o.x);
+                    o.y = fma(vi, f, o.y);
+                  } else {
+                    o = zadd(o, zmul(alpha, make_double2(vr * f, vi * f)));
+                  }
+                  orow[j] = o;
+                }
               }
             }
           }
@@ -368,16 +395,6 @@ __global__ void __launch_bounds__(192, 1)
 
 // ---- digit slicing ----------------------------------------------------------
 
-__device__ double block_max(double x, double* sh) {
-  for (int off = 16; off > 0; off >>= 1) x = fmax(x, __shfl_down_sync(0xffffffffu, x, off));
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) sh[w] = x;
-  __syncthreads();
-  double r = 0.0;
-  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r = fmax(r, sh[i]);
-  return r;
-}
 
 template <int KIND>
 __device__ __forceinline__ void put_digit(uint8_t* out, int64_t idx, double d) {
@@ -413,34 +430,57 @@ __device__ __forceinline__ uint2 pack4_bf16(int d0, int d1, int d2, int d3) {
   return w;
 }
 
-template <int KIND>
-__global__ void slice_kernel(const z* __restrict__ X, int64_t rows, int64_t K, int64_t ld, int trans, int conj, int s,
-                             int b, uint8_t* __restrict__ out, int64_t rows_pad, int64_t Kp, double* __restrict__ scale) {
-  __shared__ double sh[32];
-  for (int64_t r = blockIdx.x; r < rows_pad; r += gridDim.x) {
-    const bool live = r < rows;
+// Rows with K contiguous, in two passes over (row, K chunk) work items, one warp each, so
+// that both many short rows and few long rows keep the GPU busy: pass 1 takes each
+// chunk's largest |re|, |im| and folds its exponent into the row's with an integer
+// atomicMax (deterministic); after the scales are set, pass 2 cuts 4 consecutive k per
+// lane, so loads are coalesced and every digit plane is stored 128 bytes per warp.
+__global__ void rowexp_n_kernel(const z* __restrict__ X, int64_t rows, int64_t K, int64_t ld, int64_t chunk,
+                                int64_t nchunks, int* __restrict__ ex) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t w = warp; w < rows * nchunks; w += nwarps) {
+    const int64_t r = w / nchunks, c = w % nchunks;
+    const int64_t k1 = min(K, (c + 1) * chunk);
+    const z* row = X + r * ld;
     double mx = 0.0;
-    if (live)
-      for (int64_t k = threadIdx.x; k < K; k += blockDim.x) {
-        const z v = trans ? X[k * ld + r] : X[r * ld + k];
-        mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
-      }
-    mx = block_max(mx, sh);
-    int e = 0;
-    if (mx > 0.0) frexp(mx, &e);  // mx = f 2^e, 0.5 <= f < 1: every |x| 2^-e < 1
-    if (live && threadIdx.x == 0) scale[r] = ldexp(1.0, e);
-    const double inv = ldexp(1.0, -e);
-    // four consecutive k per thread: one 4-byte (e4m3) or 8-byte (bf16) store per digit plane
-    for (int64_t k0 = 4 * (int64_t)threadIdx.x; k0 < Kp; k0 += 4 * (int64_t)blockDim.x) {
+    for (int64_t k = c * chunk + lane; k < k1; k += 32) {
+      const z v = row[k];
+      mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+    }
+    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if (lane == 0 && mx > 0.0) {
+      int e = 0;
+      frexp(mx, &e);
+      atomicMax(ex + r, e);
+    }
+  }
+}
+
+template <int KIND>
+__global__ void slice_kernel(const z* __restrict__ X, int64_t rows, int64_t K, int64_t ld, int conj, int s, int b,
+                             uint8_t* __restrict__ out, int64_t rows_pad, int64_t Kp, int64_t chunk, int64_t nchunks,
+                             const double* __restrict__ inv) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t w = warp; w < rows_pad * nchunks; w += nwarps) {
+    const int64_t r = w / nchunks, c = w % nchunks;
+    const bool live = r < rows;
+    const z* row = X + r * ld;
+    const double iv = live ? inv[r] : 0.0;
+    const int64_t k1 = min(Kp, (c + 1) * chunk);
+    for (int64_t k0 = c * chunk + 4 * (int64_t)lane; k0 < k1; k0 += 128) {
       long long Vr[4], Vi[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int64_t k = k0 + u;
         double xr = 0.0, xi = 0.0;
         if (live && k < K) {
-          const z v = trans ? X[k * ld + r] : X[r * ld + k];
-          xr = v.x * inv;
-          xi = (conj ? -v.y : v.y) * inv;
+          const z v = row[k];
+          xr = v.x * iv;
+          xi = (conj ? -v.y : v.y) * iv;
         }
         Vr[u] = fixed62(xr);
         Vi[u] = fixed62(xi);
@@ -687,15 +727,28 @@ cudaError_t make_slices(const z* X, int64_t rows, int64_t K, int64_t ld, int tra
                                         round_up((int64_t)cfg.s * 2 * out.rows_pad * out.Kp * esize(cfg.kind), 1024));
   cudaError_t e = encode_map(out);
   if (e != cudaSuccess) return e;
+  double* inv = out.scale + round_up(out.rows_pad * 8, 1024) / 8;
+  int* ex = reinterpret_cast<int*>(inv + round_up(out.rows_pad * 8, 1024) / 8);
+  e = cudaMemsetAsync(ex, 0x80, (size_t)rows * sizeof(int), s);  // 0x80808080 < every exponent
+  if (e != cudaSuccess) return e;
+  constexpr int64_t kWarps = 152 * 64;  // work items wanted in flight
   if (trans) {
-    double* inv = out.scale + round_up(out.rows_pad * 8, 1024) / 8;
-    int* ex = reinterpret_cast<int*>(inv + round_up(out.rows_pad * 8, 1024) / 8);
-    cudaError_t e = cudaMemsetAsync(ex, 0x80, (size_t)rows * sizeof(int), s);  // 0x80808080 < every exponent
-    if (e != cudaSuccess) return e;
     const int64_t rb = (rows + 31) / 32;
     const int64_t ky = std::max<int64_t>(1, std::min<int64_t>((K + 63) / 64, (152 * 64 + rb - 1) / rb));
     rowexp_t_kernel<<<dim3((unsigned)rb, (unsigned)std::min<int64_t>(ky, 65535)), dim3(32, 8), 0, s>>>(X, rows, K, ld, ex);
-    rowexp_finalize_kernel<<<grid_for(rows, 256), 256, 0, s>>>(ex, rows, out.scale, inv);
+  } else {
+    // K chunks of whole 128-element blocks, enough of them that rows x chunks covers the GPU
+    int64_t nch = std::min<int64_t>((kWarps + rows - 1) / rows, (out.Kp + 127) / 128);
+    nch = std::max<int64_t>(nch, 1);
+    const int64_t chunk = round_up((out.Kp + nch - 1) / nch, 128);
+    nch = (out.Kp + chunk - 1) / chunk;
+    out.chunk = chunk;
+    out.nchunks = nch;
+    const int blocks = (int)std::min<int64_t>((rows * nch * 32 + 255) / 256, 152 * 64);
+    rowexp_n_kernel<<<std::max(blocks, 1), 256, 0, s>>>(X, rows, K, ld, chunk, nch, ex);
+  }
+  rowexp_finalize_kernel<<<grid_for(rows, 256), 256, 0, s>>>(ex, rows, out.scale, inv);
+  if (trans) {
     const dim3 grid((unsigned)(out.rows_pad / 32), (unsigned)(out.Kp / 64));
     if (grid.y > 65535) return cudaErrorInvalidValue;
     if (cfg.kind == kSplitBF16)
@@ -706,13 +759,13 @@ cudaError_t make_slices(const z* X, int64_t rows, int64_t K, int64_t ld, int tra
                                                       out.rows_pad, out.Kp, inv);
     return cudaGetLastError();
   }
-  const int grid = (int)std::min<int64_t>(out.rows_pad, 152 * 16);
+  const int blocks = (int)std::min<int64_t>((out.rows_pad * out.nchunks * 32 + 255) / 256, 152 * 64);
   if (cfg.kind == kSplitBF16)
-    slice_kernel<kSplitBF16><<<grid, 256, 0, s>>>(X, rows, K, ld, trans, conj, cfg.s, cfg.b, (uint8_t*)out.digits,
-                                                  out.rows_pad, out.Kp, out.scale);
+    slice_kernel<kSplitBF16><<<blocks, 256, 0, s>>>(X, rows, K, ld, conj, cfg.s, cfg.b, (uint8_t*)out.digits,
+                                                    out.rows_pad, out.Kp, out.chunk, out.nchunks, inv);
   else
-    slice_kernel<kSplitE4M3><<<grid, 256, 0, s>>>(X, rows, K, ld, trans, conj, cfg.s, cfg.b, (uint8_t*)out.digits,
-                                                  out.rows_pad, out.Kp, out.scale);
+    slice_kernel<kSplitE4M3><<<blocks, 256, 0, s>>>(X, rows, K, ld, conj, cfg.s, cfg.b, (uint8_t*)out.digits,
+                                                    out.rows_pad, out.Kp, out.chunk, out.nchunks, inv);
   return cudaGetLastError();
 }
 
