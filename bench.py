@@ -42,7 +42,8 @@ WORKLOADS = {
     "c4": dict(nsys=64, seed=4, level_shift=0.0, precision="fp64", tol=1e-10,
                name="ccsd_batch64_o4-16_v16-64_naux3v"),
 }
-SPLIT_SLICES = 9  # 4-bit digits: |dE| 7.6e-10 Eh vs FP64 after 8 iterations at o20/v120
+SPLIT_SLICES = 8  # 5-bit e4m3 digits: 39 bits of each row scale
+SPLIT_BITS = 5
 METRIC = "CCSD iteration time (s)"
 FP64_OVER_BF16_NOMINAL = 1.25 / 2250.0  # dense FP64 vs dense BF16 tensor rate (nominal)
 
@@ -170,7 +171,7 @@ def run_reference(args, wl):
 def make_ctx(ccmod, s, wl, precision, slices, stream, profile=1):
     kw = dict(level_shift=wl["level_shift"], tol=0.0, diis_dim=8, profile=profile, stream=stream.cuda_stream)
     if precision == "split":
-        kw.update(precision=ccmod.PREC_SPLIT, slices=slices)
+        kw.update(precision=ccmod.PREC_SPLIT, slices=slices, digit_bits=SPLIT_BITS)
     return ccmod.CCSD(s.o, s.v, s.eps, B=s.B, **kw)
 
 
@@ -266,7 +267,7 @@ def run_ours(args, wl):
         e_split = cs.energy()
         t_split = cs.get_amplitudes()
         cs.close()
-        companion = {"precision": "split", "slices": slices, "bits_per_slice": 4, "digit_type": "e4m3",
+        companion = {"precision": "split", "slices": slices, "bits_per_slice": SPLIT_BITS, "digit_type": "e4m3",
                      "ms_per_step": ms2 / args.steps, "speedup_vs_fp64": ms / ms2,
                      "abs_dE_vs_fp64_gpu": abs(e_split - e_main),
                      "max_amp_err_vs_fp64_gpu": float(max(np.max(np.abs(t_split[0] - t_main[0])),
@@ -348,7 +349,7 @@ def run_batch(args, wl):
     tol, maxit = wl["tol"], 200
     precision = args.precision or wl["precision"]
     slices = args.slices or SPLIT_SLICES
-    popts = dict(precision=ccmod.PREC_SPLIT, slices=slices) if precision == "split" else {}
+    popts = dict(precision=ccmod.PREC_SPLIT, slices=slices, digit_bits=SPLIT_BITS) if precision == "split" else {}
     # warm-up (module load, first graph instantiation)
     with ccmod.Batch(spec[:4], tol=tol, max_iter=maxit, **popts) as b:
         b.iterate(3)
@@ -428,7 +429,7 @@ def residual_once(wl, precision, slices):
     s = inputs.make_system(wl["o"], wl["v"], wl["naux"], wl["seed"])
     kw = dict(level_shift=wl["level_shift"])
     if precision == "split":
-        kw.update(precision=ccmod.PREC_SPLIT, slices=slices)
+        kw.update(precision=ccmod.PREC_SPLIT, slices=slices, digit_bits=SPLIT_BITS)
     with ccmod.CCSD(s.o, s.v, s.eps, B=s.B, **kw) as cc:
         cc.residual()
     print("residual evaluated", flush=True)

@@ -85,7 +85,8 @@ typedef struct {
   int diis_start;     /* first iteration that extrapolates (default 2) */
   double level_shift; /* added to virtual orbital energies in the denominators only (default 0) */
   int precision;      /* ccsd_precision (default CCSD_PREC_FP64) */
-  int slices;         /* split precision: 4-bit e4m3 digits per operand, 1..14 (default 0 = 11) */
+  int slices;         /* split precision: e4m3 digits per operand, 1..14 with digit_bits * slices <= 56
+                         (default 0 = about 44 bits: 9 digits of 5 bits, 11 of 4) */
   int store_w;        /* 1: store <ab||cd> (packed); 0: never store it, rebuild it in blocks of rows
                          from the DF factors inside each ladder evaluation (DF input only) (default 1) */
   int profile;        /* 1: record per-term CUDA-event timings (default 0) */
@@ -98,6 +99,9 @@ typedef struct {
                          (default 0 = as many as fit about 2 GB of (ac|bd)) */
   int autotune;       /* 1: at creation, time every FP64 GEMM of the plan in each tile shape and keep
                          the fastest (default 0: a cost model picks the shape) */
+  int digit_bits;     /* split precision: bits per digit, 1..5 (default 0 = 5). Digits are integers
+                         e4m3 holds exactly (|d| <= 16); at 5 bits every row is scaled below 1/2
+                         so that its first digit stays within 16 too */
 } ccsd_opts;
 
 /* Fill opts with the defaults listed above. */
@@ -185,11 +189,13 @@ ccsd_status ccsd_zgemm(int precision, int transA, int conjA, int transB, int con
  * Split-precision complex GEMM (Ozaki-style digit slices on the tcgen05 tensor
  * cores), same operation and layouts as ccsd_zgemm:
  *   C = alpha * opA(A) * opB(B) + beta * C   (complex double in and out, device pointers)
- * kind 0: e4m3 digits (kind::f8f6f4), bits <= 4; kind 1: bf16 digits (kind::f16), bits <= 8.
+ * kind 0: e4m3 digits (kind::f8f6f4), bits <= 5; kind 1: bf16 digits (kind::f16), bits <= 8.
  * Each row of opA(A) and each column of opB(B) is scaled by a power of two and cut into
- * `slices` integer digits of `bits` bits; digit products of equal weight are summed
+ * `slices` integer digits of `bits` bits (at 5 bits in e4m3 the scale leaves
+ * one bit of headroom so that every digit is an integer the type holds exactly); digit products of equal weight are summed
  * exactly in FP32 tensor-memory accumulators over K ranges short enough to stay exact,
- * and combined in FP64. Error ~ 2^(-bits*slices) relative to the row/column scales.
+ * and combined in FP64. Error ~ 2^(-bits*slices) relative to the row/column scales
+ * (2^(1-bits*slices) with headroom).
  * workspace: device memory of at least ccsd_split_workspace(...) bytes. Synchronous on
  * `stream`. CCSD_ERR_TIMEOUT if a bounded device wait gave up.
  */

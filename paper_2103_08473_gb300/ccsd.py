@@ -30,7 +30,8 @@ class ccsd_opts(C.Structure):
     _fields_ = [("max_iter", C.c_int), ("tol", C.c_double), ("norm", C.c_int), ("diis_dim", C.c_int),
                 ("diis_start", C.c_int), ("level_shift", C.c_double), ("precision", C.c_int),
                 ("slices", C.c_int), ("store_w", C.c_int), ("profile", C.c_int), ("stream", C.c_void_p),
-                ("split_min_flops", C.c_double), ("df_block", C.c_int), ("autotune", C.c_int)]
+                ("split_min_flops", C.c_double), ("df_block", C.c_int), ("autotune", C.c_int),
+                ("digit_bits", C.c_int)]
 
 
 class CCSDError(RuntimeError):
@@ -301,7 +302,7 @@ SPLIT_E4M3, SPLIT_BF16 = 0, 1
 
 
 def split_zgemm(a, b, c, alpha=1.0, beta=0.0, transA=False, conjA=False, transB=False, conjB=False,
-                kind=SPLIT_E4M3, bits=4, slices=11, stream=None):
+                kind=SPLIT_E4M3, bits=5, slices=9, stream=None):
     """ccsd_split_zgemm on row-major torch CUDA complex128 matrices (c updated in place)."""
     import torch
     lib = load()

@@ -840,10 +840,14 @@ ccsd_status create_impl(int o, int v, const double* eps, const ccsd_z* fock, ccs
   if (ctx->opts.precision == CCSD_PREC_SPLIT) {
     ctx->use_split = true;
     ctx->split.kind = kSplitE4M3;
-    ctx->split.b = 4;
-    ctx->split.s = ctx->opts.slices > 0 ? ctx->opts.slices : 11;
+    if (ctx->opts.digit_bits < 0 || ctx->opts.digit_bits > 5)
+      return set_err(ctx, CCSD_ERR_ARG, "digit_bits must be in [1, 5] (e4m3 digits), 0 = 5");
+    ctx->split.b = ctx->opts.digit_bits > 0 ? ctx->opts.digit_bits : 5;
+    // default: about 44 bits of every row's scale (9 digits of 5 bits, 11 of 4)
+    ctx->split.s = ctx->opts.slices > 0 ? ctx->opts.slices : (44 + ctx->split.b) / ctx->split.b;
     ctx->split_min_flops = ctx->opts.split_min_flops;
-    if (ctx->split.s > 14) return set_err(ctx, CCSD_ERR_ARG, "slices must be <= 14 (4-bit e4m3 digits)");
+    if (ctx->split.s > 14 || ctx->split.b * ctx->split.s > 56)
+      return set_err(ctx, CCSD_ERR_ARG, "slices must be <= 14 with digit_bits * slices <= 56");
   }
   if (!ctx->opts.store_w && kind != CCSD_INT_DF)
     return set_err(ctx, CCSD_ERR_UNSUPPORTED, "store_w = 0 needs DF factors (CCSD_INT_DF)");
@@ -1067,6 +1071,7 @@ void ccsd_default_opts(ccsd_opts* o) {
   o->split_min_flops = 1e9;
   o->df_block = 0;
   o->autotune = 0;
+  o->digit_bits = 0;
 }
 
 ccsd_status ccsd_create(int o, int v, const double* eps, const ccsd_z* fock, ccsd_int_kind kind, const ccsd_z* ints,

@@ -3,8 +3,9 @@
 //   C = alpha * op(A) * op(B) + beta * C      (complex double in and out)
 //
 // Each operand row (A) or column (B) is scaled by a power of two 2^e so that its
-// largest real/imaginary magnitude is below 1, then cut into s signed integer
-// digits of b bits (round to nearest): x = sum_p d_p 2^{-b p} + r, |r| <= 2^{-b s - 1}.
+// largest real/imaginary magnitude is below 1 (below 1/2 where the digit width needs
+// a bit of headroom, see split_headroom), then cut into s signed integer digits of
+// b bits (round to nearest): x = sum_p d_p 2^{-b p} + r, |r| <= 2^{-b s - 1}.
 // Digits are exact in the narrow type (e4m3 holds every integer up to 16, bf16 up
 // to 256). The product of two digit matrices is an integer matrix; the tensor
 // cores form it in FP32 with every partial sum an integer below 2^24, hence
@@ -39,10 +40,20 @@ struct SliceSet {
   bool have_map = false;
 };
 
+// Largest integer magnitude the digit type holds exactly: every integer up to 16 in e4m3,
+// up to 256 in bf16. Digits of b bits lie in [-2^(b-1), 2^(b-1)] after the first; the first
+// reaches 2^b when rows are scaled below 1. Where 2^b is beyond the exact range, rows are
+// scaled below 1/2 instead (one bit of headroom), so that every digit, the first included,
+// stays within 2^(b-1): e4m3 then carries b = 5. (bf16 stops at b = 8: products of 9-bit
+// digits would leave no whole K block of exact FP32 accumulation.)
+inline int split_exact_max(int kind) { return kind == kSplitBF16 ? 256 : 16; }
+inline int split_headroom(int kind, int b) { return (1 << b) > split_exact_max(kind) ? 1 : 0; }
+inline int split_max_bits(int kind) { return kind == kSplitBF16 ? 8 : 5; }
+
 struct SplitConfig {
   int kind = kSplitE4M3;
-  int b = 4;          // bits per digit
-  int s = 11;         // digits per operand
+  int b = 5;          // bits per digit
+  int s = 9;          // digits per operand
   int triangular = 1; // keep pairs with p + q <= s + 1 (else all s^2 pairs)
 };
 

@@ -21,7 +21,7 @@ SplitConfig config(int kind, int bits, int slices) {
 }
 bool config_ok(int kind, int bits, int slices) {
   return (kind == kSplitE4M3 || kind == kSplitBF16) && slices >= 1 && slices <= 32 && bits >= 1 &&
-         bits <= (kind == kSplitBF16 ? 8 : 4);
+         bits <= split_max_bits(kind);
 }
 constexpr size_t kErrBytes = 256;
 }  // namespace

@@ -536,9 +536,10 @@ __global__ void rowexp_t_kernel(const z* __restrict__ X, int64_t rows, int64_t K
 }
 
 __global__ void rowexp_finalize_kernel(const int* __restrict__ ex, int64_t rows, double* __restrict__ scale,
-                                       double* __restrict__ inv) {
+                                       double* __restrict__ inv, int headroom) {
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
-    const int e = ex[r] < -2000 ? 0 : ex[r];  // untouched (all-zero row): memset pattern 0x80808080
+    // untouched (all-zero row): memset pattern 0x80808080
+    const int e = (ex[r] < -2000 ? 0 : ex[r]) + headroom;
     scale[r] = ldexp(1.0, e);
     inv[r] = ldexp(1.0, -e);
   }
@@ -633,7 +634,7 @@ cudaError_t encode_map(SliceSet& S) {
   return S.have_map ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-double maxdigit(int p, int b) { return p == 0 ? std::ldexp(1.0, b) : std::ldexp(1.0, b - 1); }
+double maxdigit(int p, int b, int headroom) { return p == 0 && !headroom ? std::ldexp(1.0, b) : std::ldexp(1.0, b - 1); }
 
 // K blocks per exact chunk of each level: the pairs (p, L - p) of level L share one
 // FP32 accumulator, so a chunk may add at most (2^24 - 1) / (products_per_k * sum |d_p d_q|)
@@ -644,9 +645,11 @@ bool fill_levels(SplitArgs& a, int s, int b, int kblocks, int kind) {
   a.b = b;
   a.lmax = s - 1;
   a.kblocks = kblocks;
+  const int hb = split_headroom(kind, b);
   for (int L = 0; L <= a.lmax; ++L) {
     double sum = 0.0;
-    for (int p = std::max(0, L - s + 1); p <= std::min(L, s - 1); ++p) sum += maxdigit(p, b) * maxdigit(L - p, b);
+    for (int p = std::max(0, L - s + 1); p <= std::min(L, s - 1); ++p)
+      sum += maxdigit(p, b, hb) * maxdigit(L - p, b, hb);
     const double klen = std::floor((16777216.0 - 1.0) / (2.0 * sum));  // complex: 2 products per k
     const int kb = (int)std::floor(klen / bke(kind));
     if (kb < 1) return false;
@@ -713,7 +716,7 @@ int64_t slice_bytes(int64_t rows, int64_t K, const SplitConfig& cfg) {
 
 cudaError_t make_slices(const z* X, int64_t rows, int64_t K, int64_t ld, int trans, int conj, const SplitConfig& cfg,
                         SliceSet& out, void* mem, cudaStream_t s) {
-  if (cfg.s < 1 || cfg.s > 14 || cfg.b < 1 || cfg.b > (cfg.kind == kSplitBF16 ? 8 : 4) || cfg.b * cfg.s > 56)
+  if (cfg.s < 1 || cfg.s > 14 || cfg.b < 1 || cfg.b > split_max_bits(cfg.kind) || cfg.b * cfg.s > 56)
     return cudaErrorInvalidValue;
   out.rows = rows;
   out.rows_pad = round_up(std::max<int64_t>(rows, 1), 128);
@@ -747,7 +750,7 @@ cudaError_t make_slices(const z* X, int64_t rows, int64_t K, int64_t ld, int tra
     const int blocks = (int)std::min<int64_t>((rows * nch * 32 + 255) / 256, 152 * 64);
     rowexp_n_kernel<<<std::max(blocks, 1), 256, 0, s>>>(X, rows, K, ld, chunk, nch, ex);
   }
-  rowexp_finalize_kernel<<<grid_for(rows, 256), 256, 0, s>>>(ex, rows, out.scale, inv);
+  rowexp_finalize_kernel<<<grid_for(rows, 256), 256, 0, s>>>(ex, rows, out.scale, inv, split_headroom(cfg.kind, cfg.b));
   if (trans) {
     const dim3 grid((unsigned)(out.rows_pad / 32), (unsigned)(out.Kp / 64));
     if (grid.y > 65535) return cudaErrorInvalidValue;

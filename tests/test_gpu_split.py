@@ -36,7 +36,8 @@ def _rand(rng, *shape):
     return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
 
 
-@pytest.mark.parametrize("kind,bits,slices,tol", [(0, 4, 11, 2e-12), (0, 4, 6, 2e-6), (1, 7, 7, 2e-13), (1, 6, 5, 3e-8)])
+@pytest.mark.parametrize("kind,bits,slices,tol", [(0, 4, 11, 2e-12), (0, 4, 6, 2e-6), (1, 7, 7, 2e-13), (1, 6, 5, 3e-8),
+                                                  (0, 5, 9, 2e-12), (0, 5, 6, 6e-8), (0, 5, 8, 6e-11)])
 def test_split_zgemm_matches_complex128(env, kind, bits, slices, tol):
     torch, ccsd = env
     rng = np.random.default_rng(slices * 10 + kind)
@@ -48,6 +49,25 @@ def test_split_zgemm_matches_complex128(env, kind, bits, slices, tol):
     ccsd.split_zgemm(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), dc, alpha, beta, kind=kind, bits=bits,
                      slices=slices)
     err = np.max(np.abs(dc.cpu().numpy() - want)) / np.max(np.abs(want))
+    assert err < tol, err
+
+
+@pytest.mark.parametrize("kind,bits,slices,tol", [(0, 5, 9, 1e-9), (0, 4, 11, 1e-9), (1, 8, 5, 1e-9)])
+def test_split_zgemm_first_digit_at_its_bound(env, kind, bits, slices, tol):
+    """Rows whose largest entry sits just below a power of two (and exactly on one): the
+    first digit then takes its largest magnitude, which must still be exact in the type."""
+    torch, ccsd = env
+    rng = np.random.default_rng(bits * 100 + slices)
+    M, N, K = 150, 140, 520
+    top = 1.0 - 2.0 ** -45
+    a = rng.choice([top, -top, 0.5, -0.75, top / 2, 2.0 ** -20], size=(M, K)) * (2.0 ** rng.integers(-6, 6, (M, 1)))
+    a = a + 1j * rng.choice([top, -top, 0.0, 0.25], size=(M, K)) * (2.0 ** rng.integers(-6, 6, (M, 1)))
+    b = rng.choice([-top, top, 1.0, -0.5, 0.0], size=(K, N)) + 1j * rng.choice([top, -1.0, 0.125], size=(K, N))
+    want = a @ b
+    dc = torch.zeros((M, N), dtype=torch.complex128, device="cuda")
+    ccsd.split_zgemm(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), dc, 1.0, 0.0, kind=kind, bits=bits,
+                     slices=slices)
+    err = np.max(np.abs(dc.cpu().numpy() - want) / np.max(np.abs(want), axis=1, keepdims=True))
     assert err < tol, err
 
 

@@ -24,15 +24,16 @@ def _maxrel(a, b):
     return np.max(np.abs(a - b)) / max(1.0, np.max(np.abs(b)))
 
 
-@pytest.mark.parametrize("o,v,naux,seed,slices,tol", [(7, 37, 50, 201, 11, 1e-10), (5, 130, 40, 202, 11, 1e-10),
-                                                      (6, 21, 30, 203, 8, 1e-7)])
-def test_split_residual_matches_oracle(ccsd, o, v, naux, seed, slices, tol):
+@pytest.mark.parametrize("o,v,naux,seed,slices,bits,tol", [(7, 37, 50, 201, 11, 4, 1e-10), (5, 130, 40, 202, 9, 5, 1e-10),
+                                                           (6, 21, 30, 203, 8, 4, 1e-7), (6, 21, 30, 204, 6, 5, 1e-7)])
+def test_split_residual_matches_oracle(ccsd, o, v, naux, seed, slices, bits, tol):
     s = inputs.make_system(o, v, naux, seed, scale=0.05)
     f = R.fock_matrix(s.eps)
     V = R.integrals(s.B, o)
     t1, t2 = inputs.random_amplitudes(o, v, seed + 1, scale=0.05)
     S1, S2 = R.residual(f, V, t1, t2)
-    with ccsd.CCSD(o, v, s.eps, B=s.B, precision=ccsd.PREC_SPLIT, slices=slices, split_min_flops=0.0) as cc:
+    with ccsd.CCSD(o, v, s.eps, B=s.B, precision=ccsd.PREC_SPLIT, slices=slices, digit_bits=bits,
+                   split_min_flops=0.0) as cc:
         r1, r2 = cc.residual(t1, t2)
         lad = cc.get_tensor("ladder")
     assert _maxrel(r1, S1) < tol and _maxrel(r2, S2) < tol
