@@ -102,6 +102,9 @@ typedef struct {
   int digit_bits;     /* split precision: bits per digit, 1..5 (default 0 = 5). Digits are integers
                          e4m3 holds exactly (|d| <= 16); at 5 bits every row is scaled below 1/2
                          so that its first digit stays within 16 too */
+  int complex_4m;     /* FP64 GEMMs: 1 = four real products per complex product (4M); 0 = three
+                         (3M: Ar Br, Ai Bi, (Ar + Ai)(Br + Bi), combined once per output), about
+                         1.28x fewer FP64 operations (default 0) */
 } ccsd_opts;
 
 /* Fill opts with the defaults listed above. */

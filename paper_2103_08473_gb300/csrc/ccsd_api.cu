@@ -199,13 +199,14 @@ ccsd_status coulomb_df(ccsd_ctx* ctx, const z* B, char P, char Rr, char Q, char 
   g.ldb = g.N;
   g.C = D;
   g.ldc = g.N;
+  g.mult4 = ctx->opts.complex_4m;
   if (!ctx->use_split) {
     CK(zgemm_f64(g, ctx->stream));
     return CCSD_OK;
   }
-  // split mode: the Coulomb blocks on the tensor cores too, with 11 digits (they are built once)
+  // split mode: the Coulomb blocks on the tensor cores too, with at least 44 bits (they are built once)
   SplitConfig c = ctx->split;
-  c.s = std::max(c.s, 11);
+  c.s = std::max(c.s, (44 + c.b) / c.b);
   const int64_t sa = slice_bytes(g.M, g.K, c), sb = slice_bytes(g.N, g.K, c), sp = split_part_bytes(g.M, g.N, g.K, c);
   void* mem = nullptr;
   if (cudaMalloc(&mem, sa + sb + sp) != cudaSuccess) {
@@ -468,6 +469,7 @@ ccsd_status build_residual_plan(ccsd_ctx* ctx) {
         ZGemmArgs h = g;
         h.ws = ctx->gemm_ws;
         h.ws_elems = ctx->gemm_ws_elems;
+        h.mult4 = ctx->opts.complex_4m;
         return zgemm_f64(h, s, h.cfg);
       },
       [to_split](const ZGemmArgs& g) { return to_split(g) ? (int64_t)0 : zgemm_f64_workspace(g); },
@@ -1072,6 +1074,7 @@ void ccsd_default_opts(ccsd_opts* o) {
   o->df_block = 0;
   o->autotune = 0;
   o->digit_bits = 0;
+  o->complex_4m = 0;
 }
 
 ccsd_status ccsd_create(int o, int v, const double* eps, const ccsd_z* fock, ccsd_int_kind kind, const ccsd_z* ints,

@@ -26,6 +26,7 @@ struct ZGemmArgs {
   z* ws = nullptr;
   int64_t ws_elems = 0;
   int cfg = -1;  // FP64 tile configuration (0..6), -1 = cost model
+  int mult4 = 0; // 1: four real products per complex product (4M); 0: three (3M)
 };
 
 // FP64 tensor-core (DMMA) path. cfg < 0 picks the tile shape from the tile count.

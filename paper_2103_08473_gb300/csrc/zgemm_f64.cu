@@ -4,9 +4,15 @@
 //
 // Every contraction of the CCSD residual in the FP64 mode reduces to this call
 // after index permutation (transpose-transpose-GEMM-transpose). A complex
-// multiply-add is four real products (4M): Re += Ar Br - Ai Bi, Im += Ar Bi + Ai Br,
-// issued as four DMMAs per 8x8x4 tile pair into separate real and imaginary
-// accumulators.
+// multiply-add is either four real products (4M): Re += Ar Br - Ai Bi,
+// Im += Ar Bi + Ai Br, as four DMMAs per 8x8x4 tile pair into real and imaginary
+// accumulators; or three (3M, Gauss/Karatsuba): P1 += Ar Br, P2 += Ai Bi,
+// P3 += (Ar + Ai)(Br + Bi) into three accumulators, then Re = P1 - P2 and
+// Im = P3 - P1 - P2 once per output in the epilogue. On this chip DADD, DFMA and
+// DMMA share one FP64 rate, so 3M trades one DMMA (256 multiply-adds) per tile
+// pair for two fragment sums per thread: about 1.28x fewer FP64 operations, with a
+// rounding error still bounded by a small multiple of eps (|Ar|+|Ai|)(|Br|+|Bi|) per
+// product.
 //
 // Tiles are staged in shared memory with cp.async (16-byte copies of one complex
 // element each, so any operand layout and transpose maps onto the same
@@ -36,6 +42,11 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
+// x or -x by the sign bit (integer pipe, keeps conjugation off the FP64 pipe)
+__device__ __forceinline__ double flip(double x, unsigned long long sign) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (long long)sign);
+}
+
 __device__ __forceinline__ void dmma(double& d0, double& d1, double a, double b) {
   asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
                : "+d"(d0), "+d"(d1)
@@ -43,7 +54,7 @@ __device__ __forceinline__ void dmma(double& d0, double& d1, double a, double b)
 }
 
 // BM x BN block tile, 4 warps arranged WM x WN, each warp (BM/WM) x (BN/WN).
-template <int BM, int BN, int WM, int WN>
+template <int BM, int BN, int WM, int WN, bool M3>
 __global__ void __launch_bounds__(128) zgemm_dmma_kernel(ZGemmArgs g, int mfast, int splits, int64_t kslice) {
   constexpr int WTM = BM / WM, WTN = BN / WN;
   constexpr int MT = WTM / 8, NT = WTN / 8;
@@ -87,13 +98,18 @@ __global__ void __launch_bounds__(128) zgemm_dmma_kernel(ZGemmArgs g, int mfast,
     }
   };
 
-  double accr[MT][NT][2], acci[MT][NT][2];
+  // 4M: acc0 = Re, acc1 = Im.  3M: acc0 = P1 (Ar Br), acc1 = P2 (Ai Bi), acc2 = P3 ((Ar+Ai)(Br+Bi)).
+  constexpr int NACC = M3 ? 3 : 2;
+  double acc[NACC][MT][NT][2];
 #pragma unroll
-  for (int i = 0; i < MT; ++i)
+  for (int q = 0; q < NACC; ++q)
 #pragma unroll
-    for (int j = 0; j < NT; ++j) accr[i][j][0] = accr[i][j][1] = acci[i][j][0] = acci[i][j][1] = 0.0;
+    for (int i = 0; i < MT; ++i)
+#pragma unroll
+      for (int j = 0; j < NT; ++j) acc[q][i][j][0] = acc[q][i][j][1] = 0.0;
 
-  const double sa = g.conjA ? -1.0 : 1.0, sb = g.conjB ? -1.0 : 1.0;
+  const unsigned long long sga = g.conjA ? 0x8000000000000000ull : 0ull;
+  const unsigned long long sgb = g.conjB ? 0x8000000000000000ull : 0ull;
   const int64_t nk = kend > kbeg ? (kend - kbeg + BK - 1) / BK : 0;
   if (nk > 0) load_stage(0, kbeg);
   cp_async_commit();
@@ -110,29 +126,45 @@ __global__ void __launch_bounds__(128) zgemm_dmma_kernel(ZGemmArgs g, int mfast,
 #pragma unroll
     for (int ks = 0; ks < BK / 4; ++ks) {
       const int kr = ks * 4 + (lane & 3);
-      double ar[MT], ai[MT], br[NT], bi[NT], bin[NT];
+      double ar[MT], ai[MT], br[NT], bi[NT];
 #pragma unroll
       for (int i = 0; i < MT; ++i) {
         z a = As[st][kr][wm0 + i * 8 + (lane >> 2)];
         ar[i] = a.x;
-        ai[i] = sa * a.y;
+        ai[i] = flip(a.y, sga);
       }
 #pragma unroll
       for (int j = 0; j < NT; ++j) {
         z b = Bs[st][kr][wn0 + j * 8 + (lane >> 2)];
         br[j] = b.x;
-        bi[j] = sb * b.y;
-        bin[j] = -bi[j];
+        bi[j] = flip(b.y, sgb);
       }
+      if constexpr (M3) {
+        double sa[MT], sb[NT];
 #pragma unroll
-      for (int i = 0; i < MT; ++i)
+        for (int i = 0; i < MT; ++i) sa[i] = ar[i] + ai[i];
 #pragma unroll
-        for (int j = 0; j < NT; ++j) {
-          dmma(accr[i][j][0], accr[i][j][1], ar[i], br[j]);
-          dmma(acci[i][j][0], acci[i][j][1], ar[i], bi[j]);
-          dmma(accr[i][j][0], accr[i][j][1], ai[i], bin[j]);
-          dmma(acci[i][j][0], acci[i][j][1], ai[i], br[j]);
-        }
+        for (int j = 0; j < NT; ++j) sb[j] = br[j] + bi[j];
+#pragma unroll
+        for (int i = 0; i < MT; ++i)
+#pragma unroll
+          for (int j = 0; j < NT; ++j) {
+            dmma(acc[0][i][j][0], acc[0][i][j][1], ar[i], br[j]);
+            dmma(acc[1][i][j][0], acc[1][i][j][1], ai[i], bi[j]);
+            dmma(acc[2][i][j][0], acc[2][i][j][1], sa[i], sb[j]);
+          }
+      } else {
+#pragma unroll
+        for (int i = 0; i < MT; ++i)
+#pragma unroll
+          for (int j = 0; j < NT; ++j) {
+            const double bin = flip(bi[j], 0x8000000000000000ull);
+            dmma(acc[0][i][j][0], acc[0][i][j][1], ar[i], br[j]);
+            dmma(acc[1][i][j][0], acc[1][i][j][1], ar[i], bi[j]);
+            dmma(acc[0][i][j][0], acc[0][i][j][1], ai[i], bin);
+            dmma(acc[1][i][j][0], acc[1][i][j][1], ai[i], br[j]);
+          }
+      }
     }
     __syncthreads();
   }
@@ -149,12 +181,18 @@ __global__ void __launch_bounds__(128) zgemm_dmma_kernel(ZGemmArgs g, int mfast,
       for (int h = 0; h < 2; ++h) {
         const int64_t n = bn0 + wn0 + j * 8 + 2 * (lane & 3) + h;
         if (n >= g.N) continue;
-        z acc = make_double2(accr[i][j][h], acci[i][j][h]);
+        z v;
+        if constexpr (M3) {
+          const double p1 = acc[0][i][j][h], p2 = acc[1][i][j][h];
+          v = make_double2(p1 - p2, acc[2][i][j][h] - p1 - p2);
+        } else {
+          v = make_double2(acc[0][i][j][h], acc[1][i][j][h]);
+        }
         if (splits > 1) {
-          W[m * g.N + n] = acc;
+          W[m * g.N + n] = v;
           continue;
         }
-        z out = zmul(g.alpha, acc);
+        z out = zmul(g.alpha, v);
         z* cp = C + m * g.ldc + n;
         if (g.beta.x != 0.0 || g.beta.y != 0.0) out = zadd(out, zmul(g.beta, *cp));
         *cp = out;
@@ -198,7 +236,7 @@ int splits_for(const ZGemmArgs& g, int64_t tiles) {
   return s < 1 ? 1 : (int)s;
 }
 
-template <int BM, int BN, int WM, int WN>
+template <int BM, int BN, int WM, int WN, bool M3>
 cudaError_t launch(const ZGemmArgs& g, cudaStream_t s) {
   const int64_t tm = (g.M + BM - 1) / BM, tn = (g.N + BN - 1) / BN;
   int splits = splits_for(g, tm * tn * g.batch);
@@ -210,7 +248,7 @@ cudaError_t launch(const ZGemmArgs& g, cudaStream_t s) {
   const int mfast = g.M > g.N ? 0 : 1;
   if ((mfast ? tn : tm) > 65535) return cudaErrorInvalidValue;
   dim3 grid((unsigned)(mfast ? tm : tn), (unsigned)(mfast ? tn : tm), (unsigned)(g.batch * splits));
-  zgemm_dmma_kernel<BM, BN, WM, WN><<<grid, 128, 0, s>>>(g, mfast, splits, kslice);
+  zgemm_dmma_kernel<BM, BN, WM, WN, M3><<<grid, 128, 0, s>>>(g, mfast, splits, kslice);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || splits == 1) return e;
   splitk_reduce_kernel<<<grid_for(g.M * g.N * g.batch, 256), 256, 0, s>>>(g, splits);
@@ -262,14 +300,25 @@ cudaError_t zgemm_f64(const ZGemmArgs& g, cudaStream_t s, int cfg) {
   if (g.K <= 0) return zscale_matrix(g, s);
   if (g.batch > 65535) return cudaErrorInvalidValue;
   if (cfg < 0 || cfg >= kNumCfgs) cfg = pick_cfg(g);
+  if (g.mult4) {
+    switch (cfg) {
+      case 0: return launch<64, 64, 2, 2, false>(g, s);
+      case 1: return launch<32, 64, 2, 2, false>(g, s);
+      case 2: return launch<32, 32, 2, 2, false>(g, s);
+      case 3: return launch<16, 64, 1, 4, false>(g, s);
+      case 4: return launch<24, 64, 1, 4, false>(g, s);
+      case 5: return launch<40, 64, 1, 4, false>(g, s);
+      default: return launch<48, 64, 1, 4, false>(g, s);
+    }
+  }
   switch (cfg) {
-    case 0: return launch<64, 64, 2, 2>(g, s);
-    case 1: return launch<32, 64, 2, 2>(g, s);
-    case 2: return launch<32, 32, 2, 2>(g, s);
-    case 3: return launch<16, 64, 1, 4>(g, s);
-    case 4: return launch<24, 64, 1, 4>(g, s);
-    case 5: return launch<40, 64, 1, 4>(g, s);
-    default: return launch<48, 64, 1, 4>(g, s);
+    case 0: return launch<64, 64, 2, 2, true>(g, s);
+    case 1: return launch<32, 64, 2, 2, true>(g, s);
+    case 2: return launch<32, 32, 2, 2, true>(g, s);
+    case 3: return launch<16, 64, 1, 4, true>(g, s);
+    case 4: return launch<24, 64, 1, 4, true>(g, s);
+    case 5: return launch<40, 64, 1, 4, true>(g, s);
+    default: return launch<48, 64, 1, 4, true>(g, s);
   }
 }
 

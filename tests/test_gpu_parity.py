@@ -46,13 +46,14 @@ RES_CASES = [
 
 
 @pytest.mark.parametrize("o,v,naux,seed,scale,fs", RES_CASES)
-def test_residual_matches_oracle(ccsd, o, v, naux, seed, scale, fs):
+@pytest.mark.parametrize("complex_4m", [0, 1], ids=["3M", "4M"])
+def test_residual_matches_oracle(ccsd, o, v, naux, seed, scale, fs, complex_4m):
     s, f, fock = _sys(o, v, naux, seed, scale, fs)
     V = R.integrals(s.B, o)
     t1, t2 = inputs.random_amplitudes(o, v, seed + 1, scale=0.1)
     parts = {}
     S1, S2 = R.residual(f, V, t1, t2, parts=parts)
-    with ccsd.CCSD(o, v, s.eps, B=s.B, fock=fock) as cc:
+    with ccsd.CCSD(o, v, s.eps, B=s.B, fock=fock, complex_4m=complex_4m) as cc:
         r1, r2 = cc.residual(t1, t2)
         assert _maxrel(r1, S1) < 1e-12
         assert _maxrel(r2, S2) < 1e-12
