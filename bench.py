@@ -277,6 +277,24 @@ def run_ours(args, wl):
                      "iterations_compared": args.warmup + args.steps,
                      "ladder_ms": opd2.get("ladder:gemm")}
 
+    # opt-in: both precisions from the MP2 guess for the same number of iterations on fresh
+    # contexts (the split-vs-FP64 error after N iterations, and both iteration times)
+    after_n = None
+    if args.fp64_companion > 0 and precision == "split":
+        n = args.fp64_companion
+        res = {}
+        for prec in ("split", "fp64"):
+            cx = make_ctx(ccmod, s, wl, prec, slices, stream)
+            ms_n, _, _ = timed_iterations(ccmod, cx, stream, 0, n)
+            res[prec] = (ms_n / n, cx.energy(), cx.get_amplitudes())
+            cx.close()
+        (ms_s, e_s, t_s), (ms_f, e_f, t_f) = res["split"], res["fp64"]
+        after_n = {"iterations": n, "split_ms_per_step": ms_s, "fp64_ms_per_step": ms_f,
+                   "speedup_split_vs_fp64": ms_f / ms_s, "abs_dE_split_vs_fp64": abs(e_s - e_f),
+                   "max_amp_err_split_vs_fp64": float(max(np.max(np.abs(t_s[0] - t_f[0])),
+                                                          np.max(np.abs(t_s[1] - t_f[1])))),
+                   "energy_fp64": [e_f.real, e_f.imag]}
+
     if rank != 0:
         return
     value = ms / 1e3 / args.steps / world
@@ -334,7 +352,7 @@ def run_ours(args, wl):
                        "parallelism": "replicas" if world > 1 else "single"},
             "ladder_tflops": lad_tf,
             "gemm_share_of_iteration": gemm_ms / total_op_ms if total_op_ms else None,
-            "roofline": roofline, "split": companion, "cpu_baseline": cpu,
+            "roofline": roofline, "split": companion, "fp64_after_n": after_n, "cpu_baseline": cpu,
             "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "clocks": clocks, "gpu_launches": kernels * args.steps,
             "energy": [e_main.real, e_main.imag],
@@ -456,6 +474,8 @@ def main():
                     help="default: fp64 for c1/c2, split for c3")
     ap.add_argument("--slices", type=int, default=0, help=f"split digits per operand (default {SPLIT_SLICES})")
     ap.add_argument("--no-split-companion", action="store_true")
+    ap.add_argument("--fp64-companion", type=int, default=0, metavar="N",
+                    help="split runs: also run N iterations from the MP2 guess in split and in FP64 and compare")
     ap.add_argument("--complex-4m", action="store_true",
                     help="FP64 GEMMs with four real products per complex product instead of three")
     ap.add_argument("--residual-once", action="store_true",

@@ -218,6 +218,17 @@ ccsd_status ccsd_split_probe(int kind, long long M, long long N, long long K, co
                              double* C, void* workspace, size_t ws_bytes, void* stream);
 
 /*
+ * Self-test of the failure path of the split GEMM's device waits (the paper has no
+ * counterpart). Every wait of the kernel is bounded; this runs one small split GEMM
+ * (its own ~1 MB of device memory, allocated and freed here) whose TMA producer issues
+ * no copies, with a ~2 ms wait budget, so that the MMA issuer's first wait gives up.
+ * The kernel then raises its abort flag, frees its tensor memory and returns.
+ * Returns CCSD_ERR_TIMEOUT when that happened as intended (the device stays usable),
+ * CCSD_ERR_CUDA if the wait did not give up or a CUDA call failed. Synchronous on stream.
+ */
+ccsd_status ccsd_split_wait_selftest(void* stream);
+
+/*
  * ccsd_zgemm for callers that cannot allocate device memory. The paper has no
  * counterpart: this is a service of the library, not a step of the method.
  *

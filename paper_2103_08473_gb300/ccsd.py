@@ -67,6 +67,7 @@ SIGNATURES = [
                                    C.c_longlong, _P, C.c_size_t, _P]),
     ("ccsd_split_probe", C.c_int, [C.c_int, C.c_longlong, C.c_longlong, C.c_longlong, _P, _P, _P, _P, C.c_size_t,
                                    _P]),
+    ("ccsd_split_wait_selftest", C.c_int, [_P]),
     ("ccsd_batch_create", C.c_int, [C.c_int, _P, _P, _P, _P, _P, C.POINTER(ccsd_opts), C.POINTER(_P)]),
     ("ccsd_batch_iterate", C.c_int, [_P, C.c_int, _P, _P, _P]),
     ("ccsd_batch_energy", C.c_int, [_P, _P]),
@@ -335,6 +336,13 @@ def split_probe(a, b, kind=SPLIT_E4M3):
     if st != OK:
         raise CCSDError(st, lib.ccsd_last_error(None).decode())
     return out
+
+
+def split_wait_selftest(stream=None):
+    """ccsd_split_wait_selftest: returns (status, message); TIMEOUT is the intended outcome."""
+    lib = load()
+    st = lib.ccsd_split_wait_selftest(None if stream is None else C.c_void_p(stream))
+    return st, lib.ccsd_last_error(None).decode()
 
 
 class Batch:

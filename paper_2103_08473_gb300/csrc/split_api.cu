@@ -87,4 +87,36 @@ ccsd_status ccsd_split_probe(int kind, long long M, long long N, long long K, co
   return CCSD_OK;
 }
 
+ccsd_status ccsd_split_wait_selftest(void* stream) {
+  // One 128 x 128 x 128 split GEMM whose producer warp issues no copies: the MMA issuer's
+  // wait on the first stage must give up after ~2 ms, raise the abort flag (the epilogue
+  // warps stop waiting too), free TMEM and return with the error word set.
+  const SplitConfig c = config(kSplitE4M3, 5, 2);
+  const int64_t n = 128, sb = slice_bytes(n, n, c);
+  cudaStream_t st = (cudaStream_t)stream;
+  void* mem = nullptr;
+  const size_t bytes = kErrBytes + 2 * (size_t)sb + 3 * (size_t)n * n * sizeof(z);
+  if (cudaMalloc(&mem, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(CCSD_ERR_OOM, "ccsd_split_wait_selftest: device memory");
+  }
+  uint8_t* w = static_cast<uint8_t*>(mem);
+  int* err = reinterpret_cast<int*>(w);
+  z* X = reinterpret_cast<z*>(w + kErrBytes + 2 * sb);  // A, B, C: n x n each
+  SliceSet SA, SB;
+  cudaError_t e = cudaMemsetAsync(mem, 0, bytes, st);
+  if (e == cudaSuccess) e = make_slices(X, n, n, n, 0, 0, c, SA, w + kErrBytes, st);
+  if (e == cudaSuccess) e = make_slices(X + n * n, n, n, n, 0, 0, c, SB, w + kErrBytes + sb, st);
+  if (e == cudaSuccess)
+    e = split_gemm(SA, SB, X + 2 * n * n, n, zmake(1, 0), zmake(0, 0), err, nullptr, 0, st, 4000000LL, 1);
+  int h_err = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(mem);
+  if (e != cudaSuccess) return fail(CCSD_ERR_CUDA, std::string("ccsd_split_wait_selftest: ") + cudaGetErrorString(e));
+  if (h_err == 0) return fail(CCSD_ERR_CUDA, "ccsd_split_wait_selftest: the stalled wait did not give up");
+  return fail(CCSD_ERR_TIMEOUT, "ccsd_split_wait_selftest: bounded wait gave up as intended (code " +
+                                    std::to_string(h_err) + ")");
+}
+
 }  // extern "C"

@@ -57,6 +57,7 @@ struct SplitArgs {
   double* probe;            // probe output (real M x N) or null
   int* err;
   long long wait_cycles;
+  int stall_loads;          // self-test only: the producer issues no loads, so the first wait runs out
 };
 
 // ---- PTX wrappers ----------------------------------------------------------
@@ -204,7 +205,7 @@ __global__ void __launch_bounds__(192, 1)
 
   if (warp == 0) {
     // ---------------- TMA producer ----------------
-    if (lane == 0) {
+    if (lane == 0 && !args.stall_loads) {
       int it = 0;
       bool ok = true;
       for (int L = 0; L <= args.lmax && ok; ++L)
@@ -802,7 +803,7 @@ int64_t split_part_bytes(int64_t M, int64_t N, int64_t K, const SplitConfig& cfg
 }
 
 cudaError_t split_gemm(const SliceSet& A, const SliceSet& B, z* C, int64_t ldc, z alpha, z beta, int* err,
-                       void* part_ws, int64_t part_bytes, cudaStream_t s) {
+                       void* part_ws, int64_t part_bytes, cudaStream_t s, long long wait_cycles, int stall_loads) {
   if (A.kind != B.kind || A.Kp != B.Kp || A.s != B.s || A.b != B.b || !A.have_map || !B.have_map)
     return cudaErrorInvalidValue;
   SplitArgs a;
@@ -819,10 +820,15 @@ cudaError_t split_gemm(const SliceSet& A, const SliceSet& B, z* C, int64_t ldc, 
   a.rs = A.scale;
   a.cs = B.scale;
   a.err = err;
-  a.wait_cycles = 4000000000LL;  // ~2 s at 2 GHz
+  a.wait_cycles = wait_cycles > 0 ? wait_cycles : 4000000000LL;  // default ~2 s at 2 GHz
+  a.stall_loads = stall_loads;
   const int kblocks = (int)(A.Kp / bke(A.kind));
   if (!fill_levels(a, A.s, A.b, kblocks, A.kind)) return cudaErrorInvalidValue;
   plan_ksplit(a.tiles, kblocks, a.ksplits, a.kb_split);
+  if (stall_loads) {
+    a.ksplits = 1;
+    a.kb_split = kblocks;
+  }
   const int64_t need = a.ksplits > 1 ? (int64_t)a.ksplits * a.M * a.N * (int64_t)sizeof(z) : 0;
   if (a.ksplits > 1 && (part_ws == nullptr || part_bytes < need)) {
     a.ksplits = 1;

@@ -102,3 +102,17 @@ def test_split_zgemm_ladder_shape_matches_fp64_path(env):
     ccsd.split_zgemm(a, b, out, transB=True)
     err = (out - ref).abs().max().item() / ref.abs().max().item()
     assert err < 2e-12, err
+
+
+def test_bounded_wait_gives_up_and_the_device_stays_usable(env):
+    """The producer of a small split GEMM issues no copies: the MMA issuer's ~2 ms wait runs
+    out, the kernel reports it and returns; the next split GEMM on the device is correct."""
+    torch, ccsd = env
+    st, msg = ccsd.split_wait_selftest()
+    assert st == ccsd.ERR_TIMEOUT, msg
+    rng = np.random.default_rng(11)
+    a, b = _rand(rng, 64, 96), _rand(rng, 96, 80)
+    dc = torch.zeros((64, 80), dtype=torch.complex128, device="cuda")
+    ccsd.split_zgemm(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), dc)
+    want = a @ b
+    assert np.max(np.abs(dc.cpu().numpy() - want)) / np.max(np.abs(want)) < 2e-12
