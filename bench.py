@@ -41,6 +41,8 @@ WORKLOADS = {
                name="ccsd_split_o40_v240_naux800_storedW"),
     "c4": dict(nsys=64, seed=4, level_shift=0.0, precision="fp64", tol=1e-10,
                name="ccsd_batch64_o4-16_v16-64_naux3v"),
+    "c5": dict(o=60, v=400, naux=1200, seed=5, level_shift=60.0, precision="split", store_w=False,
+               name="ccsd_split_o60_v400_naux1200_dfW"),
 }
 SPLIT_SLICES = 8  # 5-bit e4m3 digits: 39 bits of each row scale
 SPLIT_BITS = 5
@@ -170,7 +172,7 @@ def run_reference(args, wl):
 
 def make_ctx(ccmod, s, wl, precision, slices, stream, profile=1, complex_4m=0):
     kw = dict(level_shift=wl["level_shift"], tol=0.0, diis_dim=8, profile=profile, stream=stream.cuda_stream,
-              complex_4m=complex_4m)
+              complex_4m=complex_4m, store_w=1 if wl.get("store_w", True) else 0)
     if precision == "split":
         kw.update(precision=ccmod.PREC_SPLIT, slices=slices, digit_bits=SPLIT_BITS)
     return ccmod.CCSD(s.o, s.v, s.eps, B=s.B, **kw)
@@ -319,13 +321,18 @@ def run_ours(args, wl):
                     "zgemm_equivalent_tflops": lad_tf,
                     "traffic": recorded_traffic("zgemm_f64.cu", f"ladder_{wl['name']}")}
     else:
-        # the split ladder launch executes P = s(s+1)/2 digit pairs x 4 real e4m3 GEMMs of 2 M N K each
+        # the split ladder launch executes P = s(s+1)/2 digit pairs x 4 real e4m3 GEMMs of 2 M N K each;
+        # without stored <ab||cd> the ladder op also rebuilds (ac|bd) over Q in blocks of a
         pairs = slices * (slices + 1) // 2
         M, N = flops.pairs(o), flops.pairs(v)
-        fp8_fl = pairs * 8.0 * M * N * N
+        cplx = float(M) * N * N + (0.0 if wl.get("store_w", True) else flops.df_rebuild_cmacs(v, wl["naux"]))
+        fp8_fl = pairs * 8.0 * cplx
         fp8_peak = peaks["bf16_tflops"] * 2.0
         ach = fp8_fl / (lad_ms * 1e-3) / 1e12 if lad_ms else None
-        roofline = {"kernel": "split_kernel<e4m3> (ladder: digits of tau x cached digits of <ab||cd>)",
+        lad_name = ("split_kernel<e4m3> (ladder: digits of tau x cached digits of <ab||cd>)"
+                    if wl.get("store_w", True) else
+                    "split_kernel<e4m3> (ladder op: (ac|bd) rebuilt over Q per block of a, then tau x <ab||cd> rows)")
+        roofline = {"kernel": lad_name,
                     "bound": "tensor", "achieved": ach, "peak": fp8_peak, "unit": "TFLOP/s",
                     "frac": (ach / fp8_peak) if ach else None,
                     "peak_basis": f"{peak_kind} bf16_tflops (burst) x 2 (nominal dense FP8/BF16 ratio)",
@@ -347,7 +354,7 @@ def run_ours(args, wl):
             "config": {"workload": wl["name"], "o": o, "v": v, "naux": wl["naux"], "precision": precision,
                        "slices": slices if precision == "split" else None,
                        "complex_mult": "4M" if m4 else "3M",
-                       "store_w": True, "level_shift": wl["level_shift"], "diis_dim": 8,
+                       "store_w": wl.get("store_w", True), "level_shift": wl["level_shift"], "diis_dim": 8,
                        "l2": "inputs larger than L2 (packed <ab||cd> and vovv exceed 129 MB)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "ladder_tflops": lad_tf,

@@ -41,13 +41,15 @@ struct ccsd_ctx {
   // constants
   double* dvec = nullptr;  // real diagonal of the Fock matrix (n)
   z *foo = nullptr, *fov = nullptr, *fvv = nullptr;
-  z *oooo = nullptr, *ooov = nullptr, *oovv = nullptr, *vovo = nullptr, *vovv = nullptr;
+  z *oooo = nullptr, *ooov = nullptr, *oovv = nullptr;
   z *Wpk = nullptr, *vovv_pk = nullptr, *oovv_pk = nullptr, *J = nullptr, *Cinit = nullptr;
   // amplitudes and residual
   z *t1 = nullptr, *t2 = nullptr, *S1 = nullptr, *S2 = nullptr;
   z *t1_prev = nullptr, *t2_prev = nullptr, *t1_save = nullptr, *t2_save = nullptr;
   // intermediates
-  z *tau = nullptr, *tau_pk = nullptr, *X = nullptr;
+  z *tau = nullptr, *tau_pk = nullptr;
+  z* vblk = nullptr;  // rows of <ak||cd> over all (c, d), unpacked block by block from vovv_pk
+  int64_t vblk_rows = 0;
   z *Hvv = nullptr, *Gvv = nullptr, *Hoo = nullptr, *Goo = nullptr, *Hov = nullptr, *Yov = nullptr, *Zoo = nullptr;
   z *Hr = nullptr, *R = nullptr, *W1 = nullptr;
   z *C = nullptr, *Yovoo = nullptr, *Ypk = nullptr, *Yfull = nullptr;
@@ -179,6 +181,34 @@ cudaError_t extract_B(const ccsd_ctx* c, const z* B, char P, char Rs, z* out, cu
   return permute_add(a, s);
 }
 
+// One GEMM of an integral build (a Coulomb block over Q): FP64, or in split mode on the
+// tensor cores with at least 44-bit digits (the integrals are built once).
+ccsd_status coulomb_gemm(ccsd_ctx* ctx, ZGemmArgs g) {
+  g.mult4 = ctx->opts.complex_4m;
+  if (!ctx->use_split) {
+    CK(zgemm_f64(g, ctx->stream));
+    return CCSD_OK;
+  }
+  SplitConfig c = ctx->split;
+  c.s = std::max(c.s, (44 + c.b) / c.b);
+  const int64_t sa = slice_bytes(g.M, g.K, c), sb = slice_bytes(g.N, g.K, c), sp = split_part_bytes(g.M, g.N, g.K, c);
+  void* mem = nullptr;
+  if (cudaMalloc(&mem, sa + sb + sp) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(ctx, CCSD_ERR_OOM, "slices of the Coulomb build");
+  }
+  uint8_t* w = static_cast<uint8_t*>(mem);
+  SliceSet SA, SB;
+  cudaError_t e = make_slices(g.A, g.M, g.K, g.lda, g.transA, 0, c, SA, w, ctx->stream);
+  if (e == cudaSuccess) e = make_slices(g.B, g.N, g.K, g.ldb, g.transB ? 0 : 1, 0, c, SB, w + sa, ctx->stream);
+  if (e == cudaSuccess)
+    e = split_gemm(SA, SB, g.C, g.ldc, zmake(1, 0), zmake(0, 0), ctx->split_err, w + sa + sb, sp, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  cudaFree(mem);
+  if (e != cudaSuccess) return set_err(ctx, CCSD_ERR_CUDA, std::string("split Coulomb build: ") + cudaGetErrorString(e));
+  return CCSD_OK;
+}
+
 // Coulomb block D[(p,r)][(q,s)] = sum_Q B^Q_pr B^Q_qs for spaces (P,R) x (Q,S).
 ccsd_status coulomb_df(ccsd_ctx* ctx, const z* B, char P, char Rr, char Q, char S, z* D, z* tmp1, z* tmp2) {
   int64_t po, np, ro, nr, qo, nq, so, ns;
@@ -199,29 +229,7 @@ ccsd_status coulomb_df(ccsd_ctx* ctx, const z* B, char P, char Rr, char Q, char 
   g.ldb = g.N;
   g.C = D;
   g.ldc = g.N;
-  g.mult4 = ctx->opts.complex_4m;
-  if (!ctx->use_split) {
-    CK(zgemm_f64(g, ctx->stream));
-    return CCSD_OK;
-  }
-  // split mode: the Coulomb blocks on the tensor cores too, with at least 44 bits (they are built once)
-  SplitConfig c = ctx->split;
-  c.s = std::max(c.s, (44 + c.b) / c.b);
-  const int64_t sa = slice_bytes(g.M, g.K, c), sb = slice_bytes(g.N, g.K, c), sp = split_part_bytes(g.M, g.N, g.K, c);
-  void* mem = nullptr;
-  if (cudaMalloc(&mem, sa + sb + sp) != cudaSuccess) {
-    cudaGetLastError();
-    return set_err(ctx, CCSD_ERR_OOM, "slices of the Coulomb build");
-  }
-  uint8_t* w = static_cast<uint8_t*>(mem);
-  SliceSet SA, SB;
-  cudaError_t e = make_slices(g.A, g.M, g.K, g.lda, 1, 0, c, SA, w, ctx->stream);
-  if (e == cudaSuccess) e = make_slices(g.B, g.N, g.K, g.ldb, 1, 0, c, SB, w + sa, ctx->stream);
-  if (e == cudaSuccess) e = split_gemm(SA, SB, D, g.ldc, zmake(1, 0), zmake(0, 0), ctx->split_err, w + sa + sb, sp, ctx->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-  cudaFree(mem);
-  if (e != cudaSuccess) return set_err(ctx, CCSD_ERR_CUDA, std::string("split Coulomb build: ") + cudaGetErrorString(e));
-  return CCSD_OK;
+  return coulomb_gemm(ctx, g);
 }
 
 // <pq||rs> block for spaces "PQRS" from the DF factors, written as out[p][q][r][s].
@@ -275,6 +283,74 @@ ccsd_status build_block_df(ccsd_ctx* ctx, const z* B, const char* sp, z* out) {
   cleanup();
   if (e != cudaSuccess) return set_err(ctx, CCSD_ERR_CUDA, cudaGetErrorString(e));
   return CCSD_OK;
+}
+
+// <ak||cd> packed over c < d (vovv_pk[(a,k)][P(c,d)]) from the DF factors, in blocks of a so
+// that the dense vovv block is never formed: D[(a,c)][(k,d)] = (ac|kd) = sum_Q B^Q_ac B^Q_kd for
+// the block (one GEMM over Q), then <ak||cd> = (ac|kd) - (ad|kc) = D[a][c][k][d] - D[a][d][k][c].
+ccsd_status build_vovv_pk_df(ccsd_ctx* ctx, const z* B) {
+  const int64_t o = ctx->o, v = ctx->v, naux = ctx->naux, Pv = ctx->Pv;
+  const int64_t per_a = v * o * v;  // D elements per a
+  const int64_t blk = std::max<int64_t>(1, std::min<int64_t>(v, (int64_t)(1.0e9 / (16.0 * (double)per_a))));
+  void *mvv = nullptr, *mov = nullptr, *mD = nullptr;
+  if (cudaMalloc(&mvv, naux * v * v * sizeof(z)) != cudaSuccess ||
+      cudaMalloc(&mov, naux * o * v * sizeof(z)) != cudaSuccess ||
+      cudaMalloc(&mD, blk * per_a * sizeof(z)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(mvv);
+    cudaFree(mov);
+    cudaFree(mD);
+    return set_err(ctx, CCSD_ERR_OOM, "vovv build temporaries");
+  }
+  z *bvv = (z*)mvv, *bov = (z*)mov, *D = (z*)mD;
+  ccsd_status st = CCSD_OK;
+  cudaError_t e = extract_B(ctx, B, 'v', 'v', bvv, ctx->stream);
+  if (e == cudaSuccess) e = extract_B(ctx, B, 'o', 'v', bov, ctx->stream);
+  if (e != cudaSuccess) st = set_err(ctx, CCSD_ERR_CUDA, cudaGetErrorString(e));
+  for (int64_t a0 = 0; a0 < v && st == CCSD_OK; a0 += blk) {
+    const int64_t na = std::min(blk, v - a0);
+    ZGemmArgs g;  // D[(a,c)][(k,d)], a in [a0, a0 + na)
+    g.M = na * v;
+    g.N = o * v;
+    g.K = naux;
+    g.A = bvv + a0 * v;
+    g.lda = v * v;
+    g.transA = 1;
+    g.B = bov;
+    g.ldb = o * v;
+    g.C = D;
+    g.ldc = o * v;
+    st = coulomb_gemm(ctx, g);
+    if (st != CCSD_OK) break;
+    e = pack_vovv_rows(D, ctx->vovv_pk + a0 * o * Pv, na, o, v, ctx->stream);
+    if (e != cudaSuccess) st = set_err(ctx, CCSD_ERR_CUDA, cudaGetErrorString(e));
+  }
+  e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess && st == CCSD_OK) st = set_err(ctx, CCSD_ERR_CUDA, cudaGetErrorString(e));
+  cudaFree(mvv);
+  cudaFree(mov);
+  cudaFree(mD);
+  return st;
+}
+
+ccsd_status build_block_full(ccsd_ctx* ctx, const z* V, const char* sp, z* out);
+
+// The same from the full integral tensor (tiny n only): the dense block as a temporary.
+ccsd_status build_vovv_pk_full(ccsd_ctx* ctx, const z* V) {
+  const int64_t ov = (int64_t)ctx->o * ctx->v, vv = (int64_t)ctx->v * ctx->v;
+  void* m = nullptr;
+  if (cudaMalloc(&m, ov * vv * sizeof(z)) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(ctx, CCSD_ERR_OOM, "vovv temporary");
+  }
+  ccsd_status st = build_block_full(ctx, V, "vovv", (z*)m);
+  if (st == CCSD_OK) {
+    cudaError_t e = pack_pairs((z*)m, ctx->vovv_pk, ov, ctx->v, 0, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) st = set_err(ctx, CCSD_ERR_CUDA, cudaGetErrorString(e));
+  }
+  cudaFree(m);
+  return st;
 }
 
 // W[P(a,b)][P(c,d)] = <ab||cd> packed, from the DF factors (dense (ac|bd) as a temporary).
@@ -433,12 +509,96 @@ ccsd_status plan_df_ladder(ccsd_ctx* ctx, Plan* P) {
 }
 
 // ---------------------------------------------------------------------------
+// Split GEMMs of the plan in chunks: the digits of both operands of one call are held to
+// kSplitCallBytes by cutting M, N (whole 128-row tiles) and, where a single row tile is still
+// too long, K (each K chunk is a GEMM of its own, with its own scales, accumulated in FP64).
+// ---------------------------------------------------------------------------
+constexpr int64_t kSplitCallBytes = int64_t(4) << 30;
+
+struct SplitChunks {
+  int64_t mc, nc, kc;
+};
+
+SplitChunks split_chunks(int64_t M, int64_t N, int64_t K, const SplitConfig& c) {
+  SplitChunks ch{std::max<int64_t>(M, 1), std::max<int64_t>(N, 1), std::max<int64_t>(K, 1)};
+  auto half = [](int64_t x) { return std::max<int64_t>(128, (x / 2 + 127) / 128 * 128); };
+  for (int guard = 0; guard < 200; ++guard) {
+    const int64_t ba = slice_bytes(ch.mc, ch.kc, c), bb = slice_bytes(ch.nc, ch.kc, c);
+    if (ba + bb <= kSplitCallBytes) break;
+    if (ba >= bb && ch.mc > 128) ch.mc = half(ch.mc);
+    else if (ch.nc > 128) ch.nc = half(ch.nc);
+    else if (ch.mc > 128) ch.mc = half(ch.mc);
+    else if (ch.kc > 128) ch.kc = half(ch.kc);
+    else break;
+  }
+  return ch;
+}
+
+// Largest K-split partial buffer over the chunk shapes (full and tail chunks).
+int64_t split_chunk_part_bytes(int64_t M, int64_t N, int64_t K, const SplitChunks& ch, const SplitConfig& c) {
+  int64_t best = 0;
+  for (int64_t m : {ch.mc, M % ch.mc})
+    for (int64_t n : {ch.nc, N % ch.nc})
+      for (int64_t k : {ch.kc, K % ch.kc})
+        if (m > 0 && n > 0 && k > 0) best = std::max(best, split_part_bytes(m, n, k, c));
+  return best;
+}
+
+int64_t split_chunked_bytes(int64_t M, int64_t N, int64_t K, const SplitConfig& c) {
+  const SplitChunks ch = split_chunks(M, N, K, c);
+  return slice_bytes(ch.mc, ch.kc, c) + slice_bytes(ch.nc, ch.kc, c) + split_chunk_part_bytes(M, N, K, ch, c);
+}
+
+cudaError_t split_gemm_chunked(ccsd_ctx* ctx, const ZGemmArgs& g, cudaStream_t s) {
+  if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+  if (g.K <= 0) return zscale_matrix(g, s);
+  const SplitConfig& c = ctx->split;
+  const SplitChunks ch = split_chunks(g.M, g.N, g.K, c);
+  uint8_t* w = static_cast<uint8_t*>(ctx->split_ws);
+  uint8_t* wb = w + slice_bytes(ch.mc, ch.kc, c);
+  uint8_t* part = wb + slice_bytes(ch.nc, ch.kc, c);
+  const int64_t part_bytes = split_chunk_part_bytes(g.M, g.N, g.K, ch, c);
+  const int64_t nm = (g.M + ch.mc - 1) / ch.mc, nn = (g.N + ch.nc - 1) / ch.nc;
+  // slice the operand with fewer chunks in the outer loop: the inner one is re-cut per outer chunk
+  const bool m_outer = nm <= nn;
+  cudaError_t e = cudaSuccess;
+  for (int64_t k0 = 0; k0 < g.K && e == cudaSuccess; k0 += ch.kc) {
+    const int64_t kn = std::min(ch.kc, g.K - k0);
+    const z beta = k0 == 0 ? g.beta : zmake(1, 0);
+    auto slice_a = [&](int64_t m0, int64_t mn, SliceSet& SA) {
+      const z* A = g.transA ? g.A + k0 * g.lda + m0 : g.A + m0 * g.lda + k0;
+      return make_slices(A, mn, kn, g.lda, g.transA, g.conjA, c, SA, w, s);
+    };
+    auto slice_b = [&](int64_t n0, int64_t nnn, SliceSet& SB) {
+      const z* B = g.transB ? g.B + n0 * g.ldb + k0 : g.B + k0 * g.ldb + n0;
+      return make_slices(B, nnn, kn, g.ldb, g.transB ? 0 : 1, g.conjB, c, SB, wb, s);
+    };
+    const int64_t outer_n = m_outer ? nm : nn, inner_n = m_outer ? nn : nm;
+    for (int64_t oi = 0; oi < outer_n && e == cudaSuccess; ++oi) {
+      SliceSet SA, SB;
+      const int64_t m0o = oi * ch.mc, n0o = oi * ch.nc;
+      e = m_outer ? slice_a(m0o, std::min(ch.mc, g.M - m0o), SA) : slice_b(n0o, std::min(ch.nc, g.N - n0o), SB);
+      for (int64_t ii = 0; ii < inner_n && e == cudaSuccess; ++ii) {
+        const int64_t m0 = m_outer ? m0o : ii * ch.mc, n0 = m_outer ? ii * ch.nc : n0o;
+        e = m_outer ? slice_b(n0, std::min(ch.nc, g.N - n0), SB) : slice_a(m0, std::min(ch.mc, g.M - m0), SA);
+        if (e == cudaSuccess)
+          e = split_gemm(SA, SB, g.C + m0 * g.ldc + n0, g.ldc, g.alpha, beta, ctx->split_err, part, part_bytes, s);
+      }
+    }
+  }
+  return e;
+}
+
+// ---------------------------------------------------------------------------
 // The residual plan: Appendix A, one contraction per printed term.
 // Labels i,j,k,l run over occupied and a,b,c,d over virtual spinors.
 // ---------------------------------------------------------------------------
 ccsd_status build_residual_plan(ccsd_ctx* ctx) {
   const int o = ctx->o, v = ctx->v;
   const int64_t Po = ctx->Po, Pv = ctx->Pv;
+  // rows a of <ak||cd> unpacked at a time for the H^{ak}_{ci} term (at most about 1 GB)
+  ctx->vblk_rows = std::max<int64_t>(1, std::min<int64_t>(v, (int64_t)(1.0e9 / (16.0 * o * (double)v * v))));
+  CS(dalloc(ctx, &ctx->vblk, ctx->vblk_rows * o * (int64_t)v * v));
   Plan* P = new Plan(o, v, &ctx->scratch, ctx->stream);
   ctx->plan = P;
   // In split mode a single GEMM of at least split_min_flops goes to the tensor-core digit
@@ -453,19 +613,7 @@ ccsd_status build_residual_plan(ccsd_ctx* ctx) {
   ctx->routes_split = to_split;
   P->set_gemm(
       [ctx, to_split](const ZGemmArgs& g, cudaStream_t s) {
-        if (to_split(g)) {
-          SliceSet SA, SB;
-          uint8_t* w = static_cast<uint8_t*>(ctx->split_ws);
-          cudaError_t e = make_slices(g.A, g.M, g.K, g.lda, g.transA, g.conjA, ctx->split, SA, w, s);
-          if (e == cudaSuccess)
-            e = make_slices(g.B, g.N, g.K, g.ldb, g.transB ? 0 : 1, g.conjB, ctx->split, SB,
-                            w + slice_bytes(g.M, g.K, ctx->split), s);
-          uint8_t* part = w + slice_bytes(g.M, g.K, ctx->split) + slice_bytes(g.N, g.K, ctx->split);
-          if (e == cudaSuccess)
-            e = split_gemm(SA, SB, g.C, g.ldc, g.alpha, g.beta, ctx->split_err, part,
-                           split_part_bytes(g.M, g.N, g.K, ctx->split), s);
-          return e;
-        }
+        if (to_split(g)) return split_gemm_chunked(ctx, g, s);
         ZGemmArgs h = g;
         h.ws = ctx->gemm_ws;
         h.ws_elems = ctx->gemm_ws_elems;
@@ -473,17 +621,15 @@ ccsd_status build_residual_plan(ccsd_ctx* ctx) {
         return zgemm_f64(h, s, h.cfg);
       },
       [to_split](const ZGemmArgs& g) { return to_split(g) ? (int64_t)0 : zgemm_f64_workspace(g); },
-      [ctx, to_split](const ZGemmArgs& g) {
-        return to_split(g) ? slice_bytes(g.M, g.K, ctx->split) + slice_bytes(g.N, g.K, ctx->split) +
-                                 split_part_bytes(g.M, g.N, g.K, ctx->split)
-                           : (int64_t)0;
-      });
+      [ctx, to_split](const ZGemmArgs& g) { return to_split(g) ? split_chunked_bytes(g.M, g.N, g.K, ctx->split) : 0; });
   const z one = zmake(1, 0), mone = zmake(-1, 0), half = zmake(0.5, 0);
   auto V = [&](z* p, const char* lab) { return P->view(p, lab, true); };
   auto W = [&](z* p, const char* lab) { return P->view(p, lab, false); };
 
   // tau^{ab}_{ij} = t^{ab}_{ij} + P^-_ij (t^a_i t^b_j), and its (i<j, c<d) packed copy
-  z *t1 = ctx->t1, *t2 = ctx->t2, *tau = ctx->tau, *taupk = ctx->tau_pk, *X = ctx->X;
+  // R (o^2 v^2) hosts, in turn: X of the H^{ak}_{ci} term, the ring product, the packed vt1
+  // product and tau packed over (c<d) for S1 (their lifetimes do not overlap)
+  z *t1 = ctx->t1, *t2 = ctx->t2, *tau = ctx->tau, *taupk = ctx->tau_pk, *X = ctx->R;
   P->custom("tau", [=](cudaStream_t s) {
     cudaError_t e = tau_build(t1, t2, tau, o, v, 1.0, 1.0, 1, s);
     if (e != cudaSuccess) return e;
@@ -495,9 +641,56 @@ ccsd_status build_residual_plan(ccsd_ctx* ctx) {
   // H^a_c = F^a_c + 1/2 sum_kld V^{kl}_{cd} tau^{da}_{kl}
   P->add("Hvv", W(ctx->Hvv, "ac"), one, V(ctx->fvv, "ac"), false, 0.0);
   P->contract("Hvv", W(ctx->Hvv, "ac"), half, V(ctx->oovv, "klcd"), false, W(tau, "klda"), false, 1.0);
-  // G^a_c = H^a_c + sum_kd V^{ak}_{cd} t^d_k - sum_k F^k_c t^a_k
+  // T[i][a][k][c] = sum_d V^{ak}_{cd} t^d_i (the second term of H^{ak}_{ci}) first, into Hr: the rows of
+  // <ak||cd> are unpacked from vovv_pk block by block of a (the dense vovv is never stored) and each
+  // block is one GEMM writing the columns (a, k, c) of its a range in every row i.
+  {
+    const int64_t vb = ctx->vblk_rows, Pv_ = Pv;
+    for (int64_t a0 = 0; a0 < v; a0 += vb) {
+      ZGemmArgs g;
+      g.M = o;
+      g.N = std::min<int64_t>(vb, v - a0) * o * v;
+      g.K = v;
+      g.transB = 1;
+      P->note_gemm(g);
+    }
+    z *vpk = ctx->vovv_pk, *vblk = ctx->vblk, *hr = ctx->Hr;
+    P->custom("Hvoov:gemm", [ctx, o, v, vb, Pv_, vpk, vblk, hr, t1](cudaStream_t s) {
+      const GemmFn& gemm = ctx->plan->gemm_fn();
+      cudaError_t e = cudaSuccess;
+      for (int64_t a0 = 0; a0 < v && e == cudaSuccess; a0 += vb) {
+        const int64_t na = std::min<int64_t>(vb, v - a0);
+        UnpackArgs u;  // vblk[(a - a0, k)][c][d] = <ak||cd>
+        u.in = vpk + a0 * o * Pv_;
+        u.out = vblk;
+        u.n1 = na * o;
+        u.n2 = v;
+        u.beta = 0.0;
+        e = unpack_pairs(u, s);
+        if (e != cudaSuccess) break;
+        ZGemmArgs g;  // Hr[i][(a,k,c)] = sum_d t1[i][d] vblk[(a,k,c)][d]
+        g.M = o;
+        g.N = na * o * v;
+        g.K = v;
+        g.A = t1;
+        g.lda = v;
+        g.B = vblk;
+        g.ldb = v;
+        g.transB = 1;
+        g.C = hr + a0 * o * v;
+        g.ldc = (int64_t)v * o * v;
+        e = gemm(g, s);
+      }
+      return e;
+    }, 8.0 * o * (double)v * o * v * v);
+  }
+  // G^a_c = H^a_c + sum_kd V^{ak}_{cd} t^d_k - sum_k F^k_c t^a_k; the middle term is the trace
+  // sum_k T[k][a][k][c] of the product above
   P->add("Gvv", W(ctx->Gvv, "ac"), one, W(ctx->Hvv, "ac"), false, 0.0);
-  P->contract("Gvv", W(ctx->Gvv, "ac"), one, V(ctx->vovv, "akcd"), false, W(t1, "kd"), false, 1.0);
+  {
+    z *hr = ctx->Hr, *gvv = ctx->Gvv;
+    P->custom("Gvv", [=](cudaStream_t s) { return trace_ik(hr, o, v, gvv, 1.0, 1.0, s); });
+  }
   P->contract("Gvv", W(ctx->Gvv, "ac"), mone, V(ctx->fov, "kc"), false, W(t1, "ka"), false, 1.0);
   // H^k_i = -F^k_i + 1/2 sum_lcd V^{kl}_{cd} tau^{cd}_{li}
   P->add("Hoo", W(ctx->Hoo, "ki"), mone, V(ctx->foo, "ki"), false, 0.0);
@@ -511,15 +704,15 @@ ccsd_status build_residual_plan(ccsd_ctx* ctx) {
   P->contract("Hov", W(ctx->Hov, "kc"), one, V(ctx->oovv, "klcd"), false, W(t1, "ld"), false, 1.0);
   // H^{ak}_{ci} (stored [i][a][k][c]) = V^{ak}_{ci} + sum_d V^{ak}_{cd} t^d_i - sum_l V^{kl}_{ic} t^a_l
   //                                   + sum_ld V^{kl}_{cd} (1/2 t^{ad}_{li} + t^a_l t^d_i)
-  P->add("Hvoov", W(ctx->Hr, "iakc"), one, V(ctx->J, "iakc"), false, 0.0);
-  P->contract("Hvoov", W(ctx->Hr, "iakc"), one, V(ctx->vovv, "akcd"), false, W(t1, "id"), false, 1.0);
+  P->add("Hvoov", W(ctx->Hr, "iakc"), one, V(ctx->J, "iakc"), false, 1.0);
   P->contract("Hvoov", W(ctx->Hr, "iakc"), mone, V(ctx->ooov, "klic"), false, W(t1, "la"), false, 1.0);
   P->contract("Hvoov", W(ctx->Hr, "iakc"), one, W(X, "liad"), false, V(ctx->oovv, "klcd"), false, 1.0);
   // C^{kb}_{ij} = V^{ij+}_{kb} + P^-_ij sum_c V^{bk}_{ci} t^c_j - 1/2 sum_cd V^{bk}_{cd} tau^{cd}_{ij}
   P->add("C", W(ctx->C, "kbij"), one, V(ctx->Cinit, "kbij"), false, 0.0);
-  P->contract("C", W(ctx->Yovoo, "kbij"), one, V(ctx->vovo, "bkci"), false, W(t1, "jc"), false, 0.0);
-  P->add("C", W(ctx->C, "kbij"), one, W(ctx->Yovoo, "kbij"), false, 1.0);
-  P->add("C", W(ctx->C, "kbij"), mone, W(ctx->Yovoo, "kbji"), false, 1.0);
+  // Yovoo[i][b][k][j] = sum_c V^{bk}_{ci} t^c_j = sum_c J[i][b][k][c] t^c_j
+  P->contract("C", W(ctx->Yovoo, "ibkj"), one, V(ctx->J, "ibkc"), false, W(t1, "jc"), false, 0.0);
+  P->add("C", W(ctx->C, "kbij"), one, W(ctx->Yovoo, "ibkj"), false, 1.0);
+  P->add("C", W(ctx->C, "kbij"), mone, W(ctx->Yovoo, "jbki"), false, 1.0);
   {
     ZGemmArgs g;  // Ypk[(b,k)][P(ij)] = sum_{c<d} V^{bk}_{cd} tau^{cd}_{ij}
     g.M = (int64_t)v * o;
@@ -581,8 +774,33 @@ ccsd_status build_residual_plan(ccsd_ctx* ctx) {
   P->contract("goo", W(ctx->W1, "jiab"), one, W(ctx->Goo, "kj"), false, W(t2, "ikab"), false, 0.0);
   P->add("goo", W(ctx->S2, "ijab"), one, W(ctx->W1, "jiab"), false, 1.0);
   P->add("goo", W(ctx->S2, "ijab"), mone, W(ctx->W1, "ijab"), false, 1.0);
-  // sum_c P^-_ij (V^{cj+}_{ab} t^c_i):  W1[i][j][a][b] = sum_c t^c_i conj(V^{cj}_{ab})
-  P->contract("vt1", W(ctx->W1, "ijab"), one, W(t1, "ic"), false, V(ctx->vovv, "cjab"), true, 0.0);
+  // sum_c P^-_ij (V^{cj+}_{ab} t^c_i):  W1[i][j][a][b] = sum_c t^c_i conj(V^{cj}_{ab}); (a, b) is the
+  // antisymmetric pair of both, so the product is formed packed, straight from vovv_pk
+  // (W1pk[i][(j, P(a,b))] in R), and unpacked
+  {
+    ZGemmArgs g;
+    g.M = o;
+    g.N = (int64_t)o * Pv;
+    g.K = v;
+    g.A = t1;
+    g.lda = v;
+    g.B = ctx->vovv_pk;
+    g.ldb = (int64_t)o * Pv;
+    g.conjB = 1;
+    g.C = ctx->R;
+    g.ldc = (int64_t)o * Pv;
+    P->gemm("vt1:gemm", g);
+    z *w1pk = ctx->R, *w1 = ctx->W1;
+    P->custom("vt1", [=](cudaStream_t s) {
+      UnpackArgs u;
+      u.in = w1pk;
+      u.out = w1;
+      u.n1 = (int64_t)o * o;
+      u.n2 = v;
+      u.beta = 0.0;
+      return unpack_pairs(u, s);
+    });
+  }
   P->add("vt1", W(ctx->S2, "ijab"), one, W(ctx->W1, "ijab"), false, 1.0);
   P->add("vt1", W(ctx->S2, "ijab"), mone, W(ctx->W1, "jiab"), false, 1.0);
   // sum_c P^-_ab G^a_c t^{cb}_{ij}:  W1[a][i][j][b] = sum_c G^a_c t^{cb}_{ij}
@@ -669,9 +887,27 @@ ccsd_status build_residual_plan(ccsd_ctx* ctx) {
   P->add("S1", W(ctx->Yov, "kc"), zmake(-2, 0), V(ctx->fov, "kc"), false, 1.0);
   P->contract("S1", W(ctx->Zoo, "ik"), one, W(ctx->Yov, "kc"), false, W(t1, "ic"), false, 0.0);
   P->contract("S1", W(ctx->S1, "ia"), one, W(ctx->Zoo, "ik"), false, W(t1, "ka"), false, 1.0);
-  P->contract("S1", W(ctx->S1, "ia"), half, V(ctx->vovv, "akcd"), false, W(tau, "ikcd"), false, 1.0);    // 1/2 V^{ak}_{cd} tau^{cd}_{ik}
+  {
+    // 1/2 sum_kcd V^{ak}_{cd} tau^{cd}_{ik} = sum_k sum_{c<d}: tau packed over (c<d) into R, one GEMM
+    // against vovv_pk
+    z *taur = ctx->R;
+    P->custom("S1", [=](cudaStream_t s) { return pack_pairs(tau, taur, (int64_t)o * o, v, 0, s); });
+    ZGemmArgs g;
+    g.M = o;
+    g.N = v;
+    g.K = (int64_t)o * Pv;
+    g.A = ctx->R;
+    g.lda = (int64_t)o * Pv;
+    g.B = ctx->vovv_pk;
+    g.ldb = (int64_t)o * Pv;
+    g.transB = 1;
+    g.C = ctx->S1;
+    g.ldc = v;
+    g.beta = one;
+    P->gemm("S1:gemm", g);
+  }
   P->contract("S1", W(ctx->S1, "ia"), half, V(ctx->ooov, "klic"), false, W(tau, "klca"), false, 1.0);    // 1/2 V^{kl}_{ic} tau^{ca}_{kl}
-  P->contract("S1", W(ctx->S1, "ia"), mone, V(ctx->vovo, "akci"), false, W(t1, "kc"), false, 1.0);       // - V^{ak}_{ci} t^c_k
+  P->contract("S1", W(ctx->S1, "ia"), mone, V(ctx->J, "iakc"), false, W(t1, "kc"), false, 1.0);         // - V^{ak}_{ci} t^c_k
 
   if (P->status() != cudaSuccess) return set_err(ctx, CCSD_ERR_CUDA, "residual plan: " + P->error());
   for (void* m : P->owned()) ctx->allocs.push_back(m);
@@ -893,8 +1129,8 @@ ccsd_status create_impl(int o, int v, const double* eps, const ccsd_z* fock, ccs
   CS(dalloc(ctx, &ctx->oooo, oo * oo));
   CS(dalloc(ctx, &ctx->ooov, oo * ov));
   CS(dalloc(ctx, &ctx->oovv, oo * vv));
-  CS(dalloc(ctx, &ctx->vovo, ov * ov));
-  CS(dalloc(ctx, &ctx->vovv, ov * vv));
+  CS(dalloc(ctx, &ctx->vovv_pk, ov * ctx->Pv));
+  CS(dalloc(ctx, &ctx->J, ov * ov));
   if (ctx->opts.store_w) CS(dalloc(ctx, &ctx->Wpk, ctx->Pv * ctx->Pv));
   else CS(dalloc(ctx, &ctx->Bvv, (int64_t)naux * v * v));
   {
@@ -907,11 +1143,27 @@ ccsd_status create_impl(int o, int v, const double* eps, const ccsd_z* fock, ccs
     ccsd_status st = CCSD_OK;
     cudaError_t e = cudaMemcpyAsync(dints, ints, cnt * sizeof(z), cudaMemcpyHostToDevice, ctx->stream);
     if (e != cudaSuccess) st = set_err(ctx, CCSD_ERR_CUDA, cudaGetErrorString(e));
-    const char* names[5] = {"oooo", "ooov", "oovv", "vovo", "vovv"};
-    z* outs[5] = {ctx->oooo, ctx->ooov, ctx->oovv, ctx->vovo, ctx->vovv};
-    for (int b = 0; b < 5 && st == CCSD_OK; ++b)
+    // vovo is needed only as J[i][a][k][c] = <ak||ci>: built into a temporary
+    void* mvovo = nullptr;
+    if (st == CCSD_OK && cudaMalloc(&mvovo, ov * ov * sizeof(z)) != cudaSuccess) {
+      cudaGetLastError();
+      st = set_err(ctx, CCSD_ERR_OOM, "vovo temporary");
+    }
+    const char* names[4] = {"oooo", "ooov", "oovv", "vovo"};
+    z* outs[4] = {ctx->oooo, ctx->ooov, ctx->oovv, (z*)mvovo};
+    for (int b = 0; b < 4 && st == CCSD_OK; ++b)
       st = kind == CCSD_INT_DF ? build_block_df(ctx, (const z*)dints, names[b], outs[b])
                                : build_block_full(ctx, (const z*)dints, names[b], outs[b]);
+    if (st == CCSD_OK) {
+      const int64_t d_vovo[4] = {v, o, v, o};  // [a][k][c][i] -> J[i][a][k][c]
+      const int pJ[4] = {3, 0, 1, 2};
+      e = permute4((z*)mvovo, d_vovo, pJ, ctx->J, zmake(1, 0), 0.0, 0, ctx->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+      if (e != cudaSuccess) st = set_err(ctx, CCSD_ERR_CUDA, cudaGetErrorString(e));
+    }
+    cudaFree(mvovo);
+    if (st == CCSD_OK)
+      st = kind == CCSD_INT_DF ? build_vovv_pk_df(ctx, (const z*)dints) : build_vovv_pk_full(ctx, (const z*)dints);
     if (st == CCSD_OK) {
       if (kind == CCSD_INT_DF && !ctx->opts.store_w) {
         e = extract_B(ctx, (const z*)dints, 'v', 'v', ctx->Bvv, ctx->stream);
@@ -945,16 +1197,10 @@ ccsd_status create_impl(int o, int v, const double* eps, const ccsd_z* fock, ccs
     CK(make_slices(ctx->Wpk, ctx->Pv, ctx->Pv, ctx->Pv, 0, 0, ctx->split, ctx->Wsl, mem, ctx->stream));
   }
   // derived constant layouts
-  CS(dalloc(ctx, &ctx->vovv_pk, ov * ctx->Pv));
   CS(dalloc(ctx, &ctx->oovv_pk, ctx->Po * ctx->Pv));
-  CS(dalloc(ctx, &ctx->J, ov * ov));
   CS(dalloc(ctx, &ctx->Cinit, ov * oo));
-  CK(pack_pairs(ctx->vovv, ctx->vovv_pk, ov, v, 0, ctx->stream));
   CK(pack_pairs(ctx->oovv, ctx->oovv_pk, o, v, 1, ctx->stream));
   {
-    const int64_t d_vovo[4] = {v, o, v, o};  // [a][k][c][i] -> J[i][a][k][c]
-    const int pJ[4] = {3, 0, 1, 2};
-    CK(permute4(ctx->vovo, d_vovo, pJ, ctx->J, zmake(1, 0), 0.0, 0, ctx->stream));
     const int64_t d_ooov[4] = {o, o, o, v};  // [i][j][k][b] -> Cinit[k][b][i][j] = conj
     const int pC[4] = {2, 3, 0, 1};
     CK(permute4(ctx->ooov, d_ooov, pC, ctx->Cinit, zmake(1, 0), 0.0, 1, ctx->stream));
@@ -972,7 +1218,6 @@ ccsd_status create_impl(int o, int v, const double* eps, const ccsd_z* fock, ccs
   CS(dalloc(ctx, &ctx->t2_save, n2));
   CS(dalloc(ctx, &ctx->tau, n2));
   CS(dalloc(ctx, &ctx->tau_pk, ctx->Po * ctx->Pv));
-  CS(dalloc(ctx, &ctx->X, n2));
   CS(dalloc(ctx, &ctx->Hvv, vv));
   CS(dalloc(ctx, &ctx->Gvv, vv));
   CS(dalloc(ctx, &ctx->Hoo, oo));

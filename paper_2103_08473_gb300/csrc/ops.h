@@ -55,6 +55,12 @@ cudaError_t pack_vvvv(const z* D, z* W, int64_t v, cudaStream_t s);
 // D[(a - a0) v + c][(b - a0 - 1) v + d] = (ac|bd) (b > a0 only): W[P(a,b) - P(a0,a0+1)][P(c,d)].
 cudaError_t pack_vvvv_rows(const z* D, z* W, int64_t v, int64_t a0, int64_t a1, cudaStream_t s);
 
+// <ak||cd> packed over c < d for na rows a from the Coulomb block D[(a,x)][(k,y)] = (ax|ky):
+// W[(a,k)][P(c,d)] = D[a][c][k][d] - D[a][d][k][c].
+cudaError_t pack_vovv_rows(const z* D, z* W, int64_t na, int64_t o, int64_t v, cudaStream_t s);
+// out[a][c] = alpha * sum_k H[k][a][k][c] + beta * out[a][c] for H stored [i][a][k][c] (o, v, o, v).
+cudaError_t trace_ik(const z* H, int64_t o, int64_t v, z* out, double alpha, double beta, cudaStream_t s);
+
 // Denominator update over t1 (o*v) and full t2 (o*o*v*v):
 //   d = S / D, t += d, S <- d.   D^a_i = e_i - e_a - shift, D^{ab}_{ij} = e_i + e_j - e_a - e_b - 2 shift
 // (e = the real diagonal of the Fock matrix). Writes per-block partial max|d| and

@@ -180,6 +180,38 @@ __global__ void pack_vvvv_rows_kernel(const z* __restrict__ D, z* __restrict__ W
   }
 }
 
+// <ak||cd> packed over c < d for a block of na rows a, from the Coulomb block
+// D[(a,x)][(k,y)] = (ax|ky):  W[(a,k)][P(c,d)] = D[a][c][k][d] - D[a][d][k][c].
+__global__ void pack_vovv_rows_kernel(const z* __restrict__ D, z* __restrict__ W, int64_t na, int64_t o,
+                                      int64_t v) {
+  const int64_t P = pair_count(v), total = na * o * P;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / P, a = r / o, k = r % o;
+    int64_t c, d;
+    pair_decode(e % P, v, c, d);
+    const z* Da = D + a * v * o * v;
+    W[e] = zsub(Da[(c * o + k) * v + d], Da[(d * o + k) * v + c]);
+  }
+}
+
+// out[a][c] = alpha * sum_k H[k][a][k][c] + beta * out[a][c] for H stored [i][a][k][c] (o v o v).
+__global__ void trace_ik_kernel(const z* __restrict__ H, int64_t o, int64_t v, z* __restrict__ out, double alpha,
+                                double beta) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < v * v;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = e / v, c = e % v;
+    double sr = 0.0, si = 0.0;
+    for (int64_t k = 0; k < o; ++k) {
+      const z h = H[((k * v + a) * o + k) * v + c];
+      sr += h.x;
+      si += h.y;
+    }
+    const z prev = beta != 0.0 ? out[e] : make_double2(0.0, 0.0);
+    out[e] = make_double2(alpha * sr + beta * prev.x, alpha * si + beta * prev.y);
+  }
+}
+
 // ---- update and norms ------------------------------------------------------
 
 template <typename T>
@@ -529,6 +561,19 @@ cudaError_t pack_vvvv_rows(const z* D, z* W, int64_t v, int64_t a0, int64_t a1, 
   const int64_t rows = AB1 - AB0;
   if (rows <= 0) return cudaSuccess;
   pack_vvvv_rows_kernel<<<grid_for(rows * pair_count(v), kThreads), kThreads, 0, s>>>(D, W, v, a0, AB0, rows);
+  return cudaGetLastError();
+}
+
+cudaError_t pack_vovv_rows(const z* D, z* W, int64_t na, int64_t o, int64_t v, cudaStream_t s) {
+  const int64_t total = na * o * pair_count(v);
+  if (total <= 0) return cudaSuccess;
+  pack_vovv_rows_kernel<<<grid_for(total, kThreads), kThreads, 0, s>>>(D, W, na, o, v);
+  return cudaGetLastError();
+}
+
+cudaError_t trace_ik(const z* H, int64_t o, int64_t v, z* out, double alpha, double beta, cudaStream_t s) {
+  if (v <= 0) return cudaSuccess;
+  trace_ik_kernel<<<grid_for(v * v, kThreads), kThreads, 0, s>>>(H, o, v, out, alpha, beta);
   return cudaGetLastError();
 }
 

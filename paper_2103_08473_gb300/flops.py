@@ -24,6 +24,22 @@ def ladder_flops_packed(o: int, v: int) -> int:
     return 8 * pairs(o) * pairs(v) ** 2
 
 
+def df_default_block(v: int) -> int:
+    """Rows a per rebuilt block of (ac|bd) when <ab||cd> is not stored (about 2 GB of D)."""
+    return max(1, min(int(2e9 / (16.0 * v ** 3)), max(v - 1, 1)))
+
+
+def df_rebuild_cmacs(v: int, naux: int, blk: int = 0) -> float:
+    """Complex multiply-adds of the (ac|bd) rebuild over Q: one GEMM per block a in [a0, a1)
+    of M = (a1 - a0) v rows (a, c), N = (v - a0 - 1) v columns (b > a0, d), K = naux."""
+    blk = blk or df_default_block(v)
+    total = 0.0
+    for a0 in range(0, v - 1, blk):
+        a1 = min(v - 1, a0 + blk)
+        total += float(a1 - a0) * v * float(v - a0 - 1) * v * naux
+    return total
+
+
 def ladder_flops_dense(o: int, v: int) -> int:
     """8 o^2 v^4 (= 8 C)."""
     return 8 * cost_metric(o, v)

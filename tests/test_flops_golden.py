@@ -23,3 +23,12 @@ def test_packed_ladder_count_is_an_eighth_of_dense_asymptotically():
     r = flops.ladder_flops_packed(o, v) / flops.ladder_flops_dense(o, v)
     assert abs(r - 1 / 8) < 0.01
     assert flops.ladder_flops_packed(20, 120) == 8 * 190 * 7140 ** 2
+
+
+def test_df_rebuild_count_one_row_per_block_closed_form():
+    """With one row a per block the rebuild is sum_a v (v - a - 1) v naux = naux v^3 (v - 1) / 2."""
+    from paper_2103_08473_gb300 import flops
+    for v, naux in [(7, 5), (40, 11)]:
+        assert flops.df_rebuild_cmacs(v, naux, blk=1) == naux * v ** 3 * (v - 1) / 2
+        # any blocking covers the same (a, c, b > a0, d) rectangle rows: never fewer than that
+        assert flops.df_rebuild_cmacs(v, naux, blk=3) >= naux * v ** 3 * (v - 1) / 2
