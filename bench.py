@@ -41,7 +41,7 @@ WORKLOADS = {
                name="ccsd_split_o40_v240_naux800_storedW"),
     "c4": dict(nsys=64, seed=4, level_shift=0.0, precision="fp64", tol=1e-10,
                name="ccsd_batch64_o4-16_v16-64_naux3v"),
-    "c5": dict(o=60, v=400, naux=1200, seed=5, level_shift=60.0, precision="split", store_w=False,
+    "c5": dict(o=60, v=400, naux=1200, seed=5, level_shift=120.0, precision="split", store_w=False,
                name="ccsd_split_o60_v400_naux1200_dfW"),
 }
 SPLIT_SLICES = 8  # 5-bit e4m3 digits: 39 bits of each row scale

@@ -96,7 +96,7 @@ typedef struct {
                              that is faster than FP64; the ladder always does; <= 0 sends every GEMM
                              there (default 1e9) */
   int df_block;       /* store_w = 0: virtual indices a per rebuilt block of <ab||cd> rows
-                         (default 0 = as many as fit about 2 GB of (ac|bd)) */
+                         (default 0 = as many as fit about 6 GB of (ac|bd)) */
   int autotune;       /* 1: at creation, time every FP64 GEMM of the plan in each tile shape and keep
                          the fastest (default 0: a cost model picks the shape) */
   int digit_bits;     /* split precision: bits per digit, 1..5 (default 0 = 5). Digits are integers

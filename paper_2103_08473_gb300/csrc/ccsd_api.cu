@@ -68,6 +68,7 @@ struct ccsd_ctx {
   void* tausl_mem = nullptr; // tau digits of the on-the-fly ladder (kept across its blocks)
   // store_w = 0: B^Q over virtuals, and per-block (ac|bd) and packed <ab||cd> rows
   z *Bvv = nullptr, *Dblk = nullptr, *Wblk = nullptr;
+  SliceSet Bsl;  // split mode: digits of B^Q_vv as rows (a, c) over Q, cut once (both operands of the rebuild)
   int df_block = 0;
   std::function<bool(const ZGemmArgs&)> routes_split;
   // iteration state
@@ -425,7 +426,7 @@ std::vector<DfBlock> df_blocks(int64_t v, int64_t blk) {
 ccsd_status plan_df_ladder(ccsd_ctx* ctx, Plan* P) {
   const int64_t v = ctx->v, naux = ctx->naux, Po = ctx->Po, Pv = ctx->Pv;
   int64_t blk = ctx->opts.df_block;
-  if (blk <= 0) blk = std::max<int64_t>(1, (int64_t)(2e9 / (16.0 * (double)v * v * v)));
+  if (blk <= 0) blk = std::max<int64_t>(1, (int64_t)(6e9 / (16.0 * (double)v * v * v)));
   blk = std::min<int64_t>(blk, std::max<int64_t>(v - 1, 1));
   ctx->df_block = (int)blk;
   const auto blocks = df_blocks(v, blk);
@@ -436,13 +437,21 @@ ccsd_status plan_df_ladder(ccsd_ctx* ctx, Plan* P) {
   }
   CS(dalloc(ctx, &ctx->Dblk, dmax));
   CS(dalloc(ctx, &ctx->Wblk, wmax * Pv));
+  if (ctx->use_split) {
+    // B^Q_vv is constant: its digits (rows (a, c), K = Q) are cut once; every block's rebuild
+    // reads row ranges of them
+    uint8_t* m = nullptr;
+    CS(dalloc(ctx, &m, slice_bytes(v * v, naux, ctx->split)));
+    CK(make_slices(ctx->Bvv, v * v, naux, v * v, 1, 0, ctx->split, ctx->Bsl, m, ctx->stream));
+  }
   // GEMM shapes of the blocks, for the workspace peaks
   for (const auto& b : blocks) {
     ZGemmArgs gd;
     gd.M = (b.a1 - b.a0) * v;
     gd.N = (v - b.a0 - 1) * v;
     gd.K = naux;
-    P->note_gemm(gd);
+    if (ctx->use_split) P->note_aux_bytes(split_part_bytes(gd.M, gd.N, gd.K, ctx->split));
+    else P->note_gemm(gd);
     ZGemmArgs gl;
     gl.M = Po;
     gl.N = b.AB1 - b.AB0;
@@ -477,7 +486,12 @@ ccsd_status plan_df_ladder(ccsd_ctx* ctx, Plan* P) {
       gd.ldb = v * v;
       gd.C = ctx->Dblk;
       gd.ldc = gd.N;
-      e = gemm(gd, s);
+      if (ctx->use_split)
+        e = split_gemm(slice_rows(ctx->Bsl, b.a0 * v, gd.M), slice_rows(ctx->Bsl, (b.a0 + 1) * v, gd.N), gd.C,
+                       gd.ldc, zmake(1, 0), zmake(0, 0), ctx->split_err, ctx->split_ws,
+                       split_part_bytes(gd.M, gd.N, gd.K, ctx->split), s);
+      else
+        e = gemm(gd, s);
       if (e == cudaSuccess) e = pack_vvvv_rows(ctx->Dblk, ctx->Wblk, v, b.a0, b.a1, s);
       const int64_t nb = b.AB1 - b.AB0;
       if (e != cudaSuccess || nb <= 0) continue;

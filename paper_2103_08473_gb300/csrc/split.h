@@ -36,6 +36,7 @@ struct SliceSet {
   int64_t rows = 0, rows_pad = 0, K = 0, Kp = 0;
   int s = 0, b = 0, kind = kSplitE4M3;
   int64_t chunk = 0, nchunks = 1;  // K chunking of the slicing work (rows with K contiguous)
+  int64_t row0 = 0;                // a row view: its first row within the digit set
   CUtensorMap tmap;  // 2D map over the digit array, box {128 bytes, 128 rows}, 128B swizzle
   bool have_map = false;
 };
@@ -56,6 +57,17 @@ struct SplitConfig {
   int s = 9;          // digits per operand
   int triangular = 1; // keep pairs with p + q <= s + 1 (else all s^2 pairs)
 };
+
+// Rows [r0, r0 + n) of a slice set, as an operand of split_gemm (no copy). The tiles of a view
+// also read digits of the rows after it (or the zero fill past the set); those only reach
+// outputs beyond the view's extent, which the kernel does not write.
+inline SliceSet slice_rows(const SliceSet& S, int64_t r0, int64_t n) {
+  SliceSet V = S;
+  V.rows = n;
+  V.scale = S.scale + r0;
+  V.row0 = S.row0 + r0;
+  return V;
+}
 
 // Bytes of device memory a SliceSet of this shape needs (digits + scales).
 int64_t slice_bytes(int64_t rows, int64_t K, const SplitConfig& cfg);

@@ -44,6 +44,7 @@ constexpr int kMaxLevels = 16;
 // (p, L - p), p = max(0, L - s + 1) .. min(L, s - 1).
 struct SplitArgs {
   int64_t M, N, Mp, Np;
+  int64_t a_row0, b_row0;   // first digit row of each operand (row views of a larger digit set)
   int tiles_m, tiles;       // output tiles along M, and in total
   int s, b, lmax, kblocks;  // digits, bits, last level, K blocks
   int kbper[kMaxLevels];    // K blocks per exact chunk, per level
@@ -224,10 +225,11 @@ __global__ void __launch_bounds__(192, 1)
               const uint32_t sa = base + st * kStageBytes;
               const int x = kb * BKE;
               mbar_expect_tx(full(st), PROBE ? 2 * kTile : 4 * kTile);
-              tma_load_2d(sa, &tmA, x, (int)((p * 2 + 0) * args.Mp + m0), full(st));
-              if (!PROBE) tma_load_2d(sa + kTile, &tmA, x, (int)((p * 2 + 1) * args.Mp + m0), full(st));
-              tma_load_2d(sa + 2 * kTile, &tmB, x, (int)((q * 2 + 0) * args.Np + n0), full(st));
-              if (!PROBE) tma_load_2d(sa + 3 * kTile, &tmB, x, (int)((q * 2 + 1) * args.Np + n0), full(st));
+              const int64_t ya = args.a_row0 + m0, yb = args.b_row0 + n0;
+              tma_load_2d(sa, &tmA, x, (int)((p * 2 + 0) * args.Mp + ya), full(st));
+              if (!PROBE) tma_load_2d(sa + kTile, &tmA, x, (int)((p * 2 + 1) * args.Mp + ya), full(st));
+              tma_load_2d(sa + 2 * kTile, &tmB, x, (int)((q * 2 + 0) * args.Np + yb), full(st));
+              if (!PROBE) tma_load_2d(sa + 3 * kTile, &tmB, x, (int)((q * 2 + 1) * args.Np + yb), full(st));
             }
         }
       if (!ok) {
@@ -812,6 +814,8 @@ cudaError_t split_gemm(const SliceSet& A, const SliceSet& B, z* C, int64_t ldc, 
   a.N = B.rows;
   a.Mp = A.rows_pad;
   a.Np = B.rows_pad;
+  a.a_row0 = A.row0;
+  a.b_row0 = B.row0;
   a.tiles_m = (int)((A.rows + 127) / 128);
   a.tiles = a.tiles_m * (int)((B.rows + 127) / 128);
   a.C = C;

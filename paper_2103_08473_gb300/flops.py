@@ -25,8 +25,8 @@ def ladder_flops_packed(o: int, v: int) -> int:
 
 
 def df_default_block(v: int) -> int:
-    """Rows a per rebuilt block of (ac|bd) when <ab||cd> is not stored (about 2 GB of D)."""
-    return max(1, min(int(2e9 / (16.0 * v ** 3)), max(v - 1, 1)))
+    """Rows a per rebuilt block of (ac|bd) when <ab||cd> is not stored (about 6 GB of D)."""
+    return max(1, min(int(6e9 / (16.0 * v ** 3)), max(v - 1, 1)))
 
 
 def df_rebuild_cmacs(v: int, naux: int, blk: int = 0) -> float:
