@@ -106,3 +106,29 @@ def test_split_full_size_o40_v240_sampled_ladder(ccsd):
     tol = 1e-13 * np.max(np.abs(r2))
     assert np.max(np.abs(r2 + r2.transpose(1, 0, 2, 3))) <= tol
     assert np.max(np.abs(r2 + r2.transpose(0, 1, 3, 2))) <= tol
+
+
+def test_split_full_size_o60_v400_df_ladder_sampled(ccsd):
+    """The o60/v400/naux1200 workload with <ab||cd> never stored (rebuilt from B^Q per block inside
+    the ladder): sampled ladder elements against the oracle computed element by element from B^Q,
+    and antisymmetry of the residual at full size."""
+    s = inputs.make_config("c5")
+    o, v = s.o, s.v
+    t1, t2 = inputs.random_amplitudes(o, v, 505, scale=0.01)
+    with ccsd.CCSD(o, v, s.eps, B=s.B, precision=ccsd.PREC_SPLIT, store_w=0, level_shift=120.0) as cc:
+        r1, r2 = cc.residual(t1, t2)
+        lad = cc.get_tensor("ladder")
+    rng = np.random.default_rng(6)
+    idx = []
+    while len(idx) < 48:
+        i, j, a, b = (int(rng.integers(o)), int(rng.integers(o)), int(rng.integers(v)), int(rng.integers(v)))
+        if i != j and a != b:
+            idx.append((i, j, a, b))
+    want = R.ladder_elements(s.B, o, t1, t2, idx)
+    got = np.array([lad[i, j, a, b] for (i, j, a, b) in idx])
+    scale = np.max(np.abs(lad))
+    del lad
+    assert np.max(np.abs(got - want)) < 1e-10 * scale
+    tol = 1e-13 * np.max(np.abs(r2))
+    assert np.max(np.abs(r2 + r2.transpose(1, 0, 2, 3))) <= tol
+    assert np.max(np.abs(r2 + r2.transpose(0, 1, 3, 2))) <= tol
