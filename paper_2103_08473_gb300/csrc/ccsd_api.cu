@@ -63,6 +63,7 @@ struct ccsd_ctx {
   double split_min_flops = 2e10;
   void* split_ws = nullptr;  // per-call digit slices of both operands
   int64_t split_ws_bytes = 0;
+  int64_t split_budget = int64_t(4) << 30;  // digit bytes of both operands per split call
   int* split_err = nullptr;  // set by the tensor-core kernel if a bounded wait gave up
   SliceSet Wsl, tausl;       // <ab||cd> digits (built once) and tau digits (per evaluation)
   void* tausl_mem = nullptr; // tau digits of the on-the-fly ladder (kept across its blocks)
@@ -523,22 +524,31 @@ ccsd_status plan_df_ladder(ccsd_ctx* ctx, Plan* P) {
 }
 
 // ---------------------------------------------------------------------------
-// Split GEMMs of the plan in chunks: the digits of both operands of one call are held to
-// kSplitCallBytes by cutting M, N (whole 128-row tiles) and, where a single row tile is still
-// too long, K (each K chunk is a GEMM of its own, with its own scales, accumulated in FP64).
+// Split GEMMs of the plan in chunks: the digits of both operands of one call are held to a
+// budget (a quarter of the device memory free when the plan is made, 4 to 16 GB) by cutting
+// M, N (whole 128-row tiles) and, where a single row tile is still too long, K (each K chunk
+// is a GEMM of its own, with its own scales, accumulated in FP64).
 // ---------------------------------------------------------------------------
-constexpr int64_t kSplitCallBytes = int64_t(4) << 30;
+int64_t split_call_budget() {
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    free_b = 0;
+  }
+  const int64_t lo = int64_t(4) << 30, hi = int64_t(16) << 30;
+  return std::min(hi, std::max(lo, (int64_t)(free_b / 4)));
+}
 
 struct SplitChunks {
   int64_t mc, nc, kc;
 };
 
-SplitChunks split_chunks(int64_t M, int64_t N, int64_t K, const SplitConfig& c) {
+SplitChunks split_chunks(int64_t M, int64_t N, int64_t K, const SplitConfig& c, int64_t budget) {
   SplitChunks ch{std::max<int64_t>(M, 1), std::max<int64_t>(N, 1), std::max<int64_t>(K, 1)};
   auto half = [](int64_t x) { return std::max<int64_t>(128, (x / 2 + 127) / 128 * 128); };
   for (int guard = 0; guard < 200; ++guard) {
     const int64_t ba = slice_bytes(ch.mc, ch.kc, c), bb = slice_bytes(ch.nc, ch.kc, c);
-    if (ba + bb <= kSplitCallBytes) break;
+    if (ba + bb <= budget) break;
     if (ba >= bb && ch.mc > 128) ch.mc = half(ch.mc);
     else if (ch.nc > 128) ch.nc = half(ch.nc);
     else if (ch.mc > 128) ch.mc = half(ch.mc);
@@ -558,8 +568,8 @@ int64_t split_chunk_part_bytes(int64_t M, int64_t N, int64_t K, const SplitChunk
   return best;
 }
 
-int64_t split_chunked_bytes(int64_t M, int64_t N, int64_t K, const SplitConfig& c) {
-  const SplitChunks ch = split_chunks(M, N, K, c);
+int64_t split_chunked_bytes(int64_t M, int64_t N, int64_t K, const SplitConfig& c, int64_t budget) {
+  const SplitChunks ch = split_chunks(M, N, K, c, budget);
   return slice_bytes(ch.mc, ch.kc, c) + slice_bytes(ch.nc, ch.kc, c) + split_chunk_part_bytes(M, N, K, ch, c);
 }
 
@@ -567,7 +577,7 @@ cudaError_t split_gemm_chunked(ccsd_ctx* ctx, const ZGemmArgs& g, cudaStream_t s
   if (g.M <= 0 || g.N <= 0) return cudaSuccess;
   if (g.K <= 0) return zscale_matrix(g, s);
   const SplitConfig& c = ctx->split;
-  const SplitChunks ch = split_chunks(g.M, g.N, g.K, c);
+  const SplitChunks ch = split_chunks(g.M, g.N, g.K, c, ctx->split_budget);
   uint8_t* w = static_cast<uint8_t*>(ctx->split_ws);
   uint8_t* wb = w + slice_bytes(ch.mc, ch.kc, c);
   uint8_t* part = wb + slice_bytes(ch.nc, ch.kc, c);
@@ -625,6 +635,7 @@ ccsd_status build_residual_plan(ccsd_ctx* ctx) {
     return fl >= ctx->split_min_flops && split_cost_estimate(g.M, g.N, g.K, ctx->split) < fl / 0.95e12;
   };
   ctx->routes_split = to_split;
+  if (ctx->use_split) ctx->split_budget = split_call_budget();
   P->set_gemm(
       [ctx, to_split](const ZGemmArgs& g, cudaStream_t s) {
         if (to_split(g)) return split_gemm_chunked(ctx, g, s);
@@ -635,7 +646,9 @@ ccsd_status build_residual_plan(ccsd_ctx* ctx) {
         return zgemm_f64(h, s, h.cfg);
       },
       [to_split](const ZGemmArgs& g) { return to_split(g) ? (int64_t)0 : zgemm_f64_workspace(g); },
-      [ctx, to_split](const ZGemmArgs& g) { return to_split(g) ? split_chunked_bytes(g.M, g.N, g.K, ctx->split) : 0; });
+      [ctx, to_split](const ZGemmArgs& g) {
+        return to_split(g) ? split_chunked_bytes(g.M, g.N, g.K, ctx->split, ctx->split_budget) : 0;
+      });
   const z one = zmake(1, 0), mone = zmake(-1, 0), half = zmake(0.5, 0);
   auto V = [&](z* p, const char* lab) { return P->view(p, lab, true); };
   auto W = [&](z* p, const char* lab) { return P->view(p, lab, false); };
