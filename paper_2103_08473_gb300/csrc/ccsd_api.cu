@@ -51,7 +51,7 @@ struct ccsd_ctx {
   z* vblk = nullptr;  // rows of <ak||cd> over all (c, d), unpacked block by block from vovv_pk
   int64_t vblk_rows = 0;
   z *Hvv = nullptr, *Gvv = nullptr, *Hoo = nullptr, *Goo = nullptr, *Hov = nullptr, *Yov = nullptr, *Zoo = nullptr;
-  z *Hr = nullptr, *R = nullptr, *W1 = nullptr;
+  z *Hr = nullptr, *R = nullptr;
   z *C = nullptr, *Yovoo = nullptr, *Ypk = nullptr, *Yfull = nullptr;
   z *Afull = nullptr, *Yoooo = nullptr, *Apk = nullptr, *Lpk = nullptr, *Hpk = nullptr;
   z* scratch = nullptr;
@@ -654,8 +654,9 @@ ccsd_status build_residual_plan(ccsd_ctx* ctx) {
   auto W = [&](z* p, const char* lab) { return P->view(p, lab, false); };
 
   // tau^{ab}_{ij} = t^{ab}_{ij} + P^-_ij (t^a_i t^b_j), and its (i<j, c<d) packed copy
-  // R (o^2 v^2) hosts, in turn: X of the H^{ak}_{ci} term, the ring product, the packed vt1
-  // product and tau packed over (c<d) for S1 (their lifetimes do not overlap)
+  // R (o^2 v^2) hosts, in turn: X of the H^{ak}_{ci} term, the ring product, the products of the
+  // goo, vt1 (packed), gvv and ct1 terms before their antisymmetrisation, and tau packed over
+  // (c<d) for S1 (their lifetimes do not overlap)
   z *t1 = ctx->t1, *t2 = ctx->t2, *tau = ctx->tau, *taupk = ctx->tau_pk, *X = ctx->R;
   P->custom("tau", [=](cudaStream_t s) {
     cudaError_t e = tau_build(t1, t2, tau, o, v, 1.0, 1.0, 1, s);
@@ -798,12 +799,12 @@ ccsd_status build_residual_plan(ccsd_ctx* ctx) {
   P->add("ring", W(ctx->S2, "ijab"), mone, W(ctx->R, "ibja"), false, 1.0);
   P->add("ring", W(ctx->S2, "ijab"), one, W(ctx->R, "jbia"), false, 1.0);
   // sum_k P^-_ji G^k_j t^{ab}_{ik}:  W1[j][i][a][b] = sum_k G^k_j t^{ab}_{ik}
-  P->contract("goo", W(ctx->W1, "jiab"), one, W(ctx->Goo, "kj"), false, W(t2, "ikab"), false, 0.0);
-  P->add("goo", W(ctx->S2, "ijab"), one, W(ctx->W1, "jiab"), false, 1.0);
-  P->add("goo", W(ctx->S2, "ijab"), mone, W(ctx->W1, "ijab"), false, 1.0);
+  P->contract("goo", W(ctx->R, "jiab"), one, W(ctx->Goo, "kj"), false, W(t2, "ikab"), false, 0.0);
+  P->add("goo", W(ctx->S2, "ijab"), one, W(ctx->R, "jiab"), false, 1.0);
+  P->add("goo", W(ctx->S2, "ijab"), mone, W(ctx->R, "ijab"), false, 1.0);
   // sum_c P^-_ij (V^{cj+}_{ab} t^c_i):  W1[i][j][a][b] = sum_c t^c_i conj(V^{cj}_{ab}); (a, b) is the
   // antisymmetric pair of both, so the product is formed packed, straight from vovv_pk
-  // (W1pk[i][(j, P(a,b))] in R), and unpacked
+  // (W1pk[i][(j, P(a,b))] in R) and added to S2 with (i, j) antisymmetrised in one pass
   {
     ZGemmArgs g;
     g.M = o;
@@ -817,27 +818,26 @@ ccsd_status build_residual_plan(ccsd_ctx* ctx) {
     g.C = ctx->R;
     g.ldc = (int64_t)o * Pv;
     P->gemm("vt1:gemm", g);
-    z *w1pk = ctx->R, *w1 = ctx->W1;
+    z *w1pk = ctx->R, *s2 = ctx->S2;
     P->custom("vt1", [=](cudaStream_t s) {
-      UnpackArgs u;
+      UnpackArgs u;  // S2[i][j][a][b] += W1[i][j][a][b] - W1[j][i][a][b]
       u.in = w1pk;
-      u.out = w1;
+      u.out = s2;
       u.n1 = (int64_t)o * o;
       u.n2 = v;
-      u.beta = 0.0;
+      u.anti_rows = o;
+      u.beta = 1.0;
       return unpack_pairs(u, s);
     });
   }
-  P->add("vt1", W(ctx->S2, "ijab"), one, W(ctx->W1, "ijab"), false, 1.0);
-  P->add("vt1", W(ctx->S2, "ijab"), mone, W(ctx->W1, "jiab"), false, 1.0);
   // sum_c P^-_ab G^a_c t^{cb}_{ij}:  W1[a][i][j][b] = sum_c G^a_c t^{cb}_{ij}
-  P->contract("gvv", W(ctx->W1, "aijb"), one, W(ctx->Gvv, "ac"), false, W(t2, "ijcb"), false, 0.0);
-  P->add("gvv", W(ctx->S2, "ijab"), one, W(ctx->W1, "aijb"), false, 1.0);
-  P->add("gvv", W(ctx->S2, "ijab"), mone, W(ctx->W1, "bija"), false, 1.0);
+  P->contract("gvv", W(ctx->R, "aijb"), one, W(ctx->Gvv, "ac"), false, W(t2, "ijcb"), false, 0.0);
+  P->add("gvv", W(ctx->S2, "ijab"), one, W(ctx->R, "aijb"), false, 1.0);
+  P->add("gvv", W(ctx->S2, "ijab"), mone, W(ctx->R, "bija"), false, 1.0);
   // sum_k P^-_ab (C^{ka}_{ij} t^b_k):  W1[a][i][j][b] = sum_k C^{ka}_{ij} t^b_k
-  P->contract("ct1", W(ctx->W1, "aijb"), one, W(ctx->C, "kaij"), false, W(t1, "kb"), false, 0.0);
-  P->add("ct1", W(ctx->S2, "ijab"), one, W(ctx->W1, "aijb"), false, 1.0);
-  P->add("ct1", W(ctx->S2, "ijab"), mone, W(ctx->W1, "bija"), false, 1.0);
+  P->contract("ct1", W(ctx->R, "aijb"), one, W(ctx->C, "kaij"), false, W(t1, "kb"), false, 0.0);
+  P->add("ct1", W(ctx->S2, "ijab"), one, W(ctx->R, "aijb"), false, 1.0);
+  P->add("ct1", W(ctx->S2, "ijab"), mone, W(ctx->R, "bija"), false, 1.0);
   // 1/2 sum_kl A^{kl}_{ij} tau^{ab}_{kl}  (packed: sum_{k<l})
   {
     ZGemmArgs g;  // Hpk[P(ij)][P(ab)] = sum_{k<l} A^{kl}_{ij} tau^{ab}_{kl}
@@ -1241,8 +1241,10 @@ ccsd_status create_impl(int o, int v, const double* eps, const ccsd_z* fock, ccs
   CS(dalloc(ctx, &ctx->S2, n2));
   CS(dalloc(ctx, &ctx->t1_prev, ov));
   CS(dalloc(ctx, &ctx->t2_prev, n2));
-  CS(dalloc(ctx, &ctx->t1_save, ov));
-  CS(dalloc(ctx, &ctx->t2_save, n2));
+  // the backup of ccsd_residual (amplitudes given by the caller) and the one an iteration keeps
+  // for a non-finite update are never live at the same time: one buffer serves both
+  ctx->t1_save = ctx->t1_prev;
+  ctx->t2_save = ctx->t2_prev;
   CS(dalloc(ctx, &ctx->tau, n2));
   CS(dalloc(ctx, &ctx->tau_pk, ctx->Po * ctx->Pv));
   CS(dalloc(ctx, &ctx->Hvv, vv));
@@ -1254,7 +1256,6 @@ ccsd_status create_impl(int o, int v, const double* eps, const ccsd_z* fock, ccs
   CS(dalloc(ctx, &ctx->Zoo, oo));
   CS(dalloc(ctx, &ctx->Hr, n2));
   CS(dalloc(ctx, &ctx->R, n2));
-  CS(dalloc(ctx, &ctx->W1, n2));
   CS(dalloc(ctx, &ctx->C, ov * oo));
   CS(dalloc(ctx, &ctx->Yovoo, ov * oo));
   CS(dalloc(ctx, &ctx->Ypk, ov * ctx->Po));
@@ -1512,13 +1513,13 @@ ccsd_status ccsd_get_tensor(ccsd_ctx* ctx, const char* name, ccsd_z* out, size_t
   } else if (nm == "ladder") {
     UnpackArgs u;
     u.in = ctx->Lpk;
-    u.out = ctx->W1;
+    u.out = ctx->R;
     u.n1 = o;
     u.n2 = v;
     u.unpack_rows = 1;
     u.beta = 0.0;
     CK(unpack_pairs(u, ctx->stream));
-    src = ctx->W1;
+    src = ctx->R;
     cnt = oo * vv;
   } else {
     return set_err(ctx, CCSD_ERR_ARG, "unknown tensor name '" + nm + "'");

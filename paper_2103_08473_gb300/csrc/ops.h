@@ -34,16 +34,17 @@ cudaError_t tau_build(const z* t1, const z* t2, z* out, int o, int v, double c2,
 // the input, pair_count(n1) in the output).
 cudaError_t pack_pairs(const z* in, z* out, int64_t n1, int64_t n2, int pack_rows, cudaStream_t s);
 
-// Unpack-accumulate: out[r][a][b] += alpha * sgn(a,b) * in[r][P(min,max)] (zero on a == b).
-// With unpack_rows the leading pair is packed too (sgn over both pairs). With swap12, the
-// output leading pair index order is (y, x) instead of (x, y) only when unpack_rows == 0 and
-// rows are a pair of distinct spaces: out index [r2][r1][a][b] with r = r1 * n1b + r2.
+// Unpack-accumulate: out[r][a][b] = beta * out + alpha * sgn(a,b) * in[r][P(min,max)] (zero on
+// a == b). With unpack_rows the leading pair is packed too (sgn over both pairs). With
+// anti_rows = m (unpack_rows == 0, n1 = m * m rows r = (x, y)), the rows are antisymmetrised on
+// the way: out[(x,y)][a][b] = beta * out + alpha * sgn(a,b) * (in[(x,y)][P] - in[(y,x)][P]).
 struct UnpackArgs {
   const z* in = nullptr;
   z* out = nullptr;
   int64_t n1 = 0;   // leading pair extent (unpack_rows) or number of rows R
   int64_t n2 = 0;   // trailing pair extent
   int unpack_rows = 0;
+  int64_t anti_rows = 0;
   z alpha{1.0, 0.0};
   double beta = 1.0;  // out = beta * out + ...
 };

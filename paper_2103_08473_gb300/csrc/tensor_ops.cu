@@ -143,7 +143,12 @@ __global__ void unpack_pairs_kernel(UnpackArgs g) {
       int64_t pc;
       if (a < b) pc = pair_index(a, b, g.n2);
       else { pc = pair_index(b, a, g.n2); sgn = -sgn; }
-      val = zscale(sgn, zmul(g.alpha, g.in[prow * P2 + pc]));
+      z x = g.in[prow * P2 + pc];
+      if (g.anti_rows > 0) {  // rows r = (x, y): in[(x, y)] - in[(y, x)]
+        const int64_t rx = r / g.anti_rows, ry = r % g.anti_rows;
+        x = zsub(x, g.in[(ry * g.anti_rows + rx) * P2 + pc]);
+      }
+      val = zscale(sgn, zmul(g.alpha, x));
     }
     z* op = g.out + e;
     *op = g.beta != 0.0 ? make_double2(g.beta * op->x + val.x, g.beta * op->y + val.y) : val;

@@ -55,7 +55,8 @@ __device__ __forceinline__ void dmma(double& d0, double& d1, double a, double b)
 
 // BM x BN block tile, 4 warps arranged WM x WN, each warp (BM/WM) x (BN/WN).
 template <int BM, int BN, int WM, int WN, bool M3>
-__global__ void __launch_bounds__(128) zgemm_dmma_kernel(ZGemmArgs g, int mfast, int splits, int64_t kslice) {
+__global__ void __launch_bounds__(128) zgemm_dmma_kernel(ZGemmArgs g, int mfast, int64_t tm, int64_t tn, int splits,
+                                                         int64_t kslice) {
   constexpr int WTM = BM / WM, WTN = BN / WN;
   constexpr int MT = WTM / 8, NT = WTN / 8;
   __shared__ __align__(16) z As[2][BK][BM];
@@ -63,8 +64,10 @@ __global__ void __launch_bounds__(128) zgemm_dmma_kernel(ZGemmArgs g, int mfast,
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wm0 = (warp / WN) * WTM, wn0 = (warp % WN) * WTN;
-  const int64_t bm0 = (int64_t)(mfast ? blockIdx.x : blockIdx.y) * BM;
-  const int64_t bn0 = (int64_t)(mfast ? blockIdx.y : blockIdx.x) * BN;
+  // linear tile index over grid x; M tiles fastest when mfast, else N tiles
+  const int64_t lin = blockIdx.x;
+  const int64_t bm0 = (mfast ? lin % tm : lin / tn) * BM;
+  const int64_t bn0 = (mfast ? lin / tm : lin % tn) * BN;
   const int64_t bz = blockIdx.z / splits, sp = blockIdx.z % splits;
   const z* __restrict__ A = g.A + bz * g.sA;
   const z* __restrict__ B = g.B + bz * g.sB;
@@ -246,9 +249,9 @@ cudaError_t launch(const ZGemmArgs& g, cudaStream_t s) {
   // rasterise so that consecutive blocks share a tile of the larger operand
   // (A holds M*K elements, B holds N*K): M-tiles fastest when B is the larger one
   const int mfast = g.M > g.N ? 0 : 1;
-  if ((mfast ? tn : tm) > 65535) return cudaErrorInvalidValue;
-  dim3 grid((unsigned)(mfast ? tm : tn), (unsigned)(mfast ? tn : tm), (unsigned)(g.batch * splits));
-  zgemm_dmma_kernel<BM, BN, WM, WN, M3><<<grid, 128, 0, s>>>(g, mfast, splits, kslice);
+  if (tm * tn > 0x7fffffff || (int64_t)g.batch * splits > 65535) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)(tm * tn), 1, (unsigned)(g.batch * splits));
+  zgemm_dmma_kernel<BM, BN, WM, WN, M3><<<grid, 128, 0, s>>>(g, mfast, tm, tn, splits, kslice);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || splits == 1) return e;
   splitk_reduce_kernel<<<grid_for(g.M * g.N * g.batch, 256), 256, 0, s>>>(g, splits);
