@@ -159,6 +159,22 @@ def ladder_elements(B: np.ndarray, o: int, t1: np.ndarray, t2: np.ndarray, idx) 
     return out
 
 
+def ladder_rows(B: np.ndarray, o: int, tau: np.ndarray, pairs) -> np.ndarray:
+    """The ladder 1/2 sum_cd V^{ab}_{cd} tau^{cd}_{ij} at every (i, j) for chosen (a, b).
+
+    For each (a, b) in ``pairs`` the row <ab||cd> = (ac|bd) - (ad|bc) over all (c, d) is formed
+    from the DF factors and contracted with the full tau (no n^4 tensor is built). Returns an
+    array [len(pairs), o, o].
+    """
+    Bv = B[:, o:, o:]
+    out = np.empty((len(pairs), o, o), np.complex128)
+    for n, (a, b) in enumerate(pairs):
+        coul = Bv[:, a, :].T @ Bv[:, b, :]          # (ac|bd) over (c, d)
+        w = coul - coul.T                           # <ab||cd>
+        out[n] = 0.5 * np.einsum("cd,ijcd->ij", w, tau)
+    return out
+
+
 def residual(f: np.ndarray, V: dict, t1: np.ndarray, t2: np.ndarray, parts: dict | None = None):
     """S^a_i and S^{ab}_{ij} of Appendix A at amplitudes (t1, t2).
 

@@ -280,3 +280,17 @@ def test_sampled_ladder_elements_match_full_ladder():
     got = R.ladder_elements(s.B, o, t1, t2, idx)
     want = np.array([full[i, j, a, b] for (i, j, a, b) in idx])
     np.testing.assert_allclose(got, want, atol=1e-14)
+
+
+def test_ladder_rows_match_full_ladder():
+    """Whole (a, b) rows of the ladder formed from B^Q (used to time the oracle at sizes where
+    <ab||cd> cannot be stored) agree with the full einsum ladder."""
+    o, v, naux = 3, 9, 7
+    s = inputs.make_system(o, v, naux, 83, scale=0.3)
+    t1, t2 = inputs.random_amplitudes(o, v, 84, scale=0.2)
+    tau = R.tau(t1, t2)
+    full = R.ladder(R.integrals(s.B, o)["vvvv"], tau)
+    pairs = [(0, 1), (2, 7), (8, 3), (4, 4)]
+    got = R.ladder_rows(s.B, o, tau, pairs)
+    for n, (a, b) in enumerate(pairs):
+        np.testing.assert_allclose(got[n], full[:, :, a, b], atol=1e-14)
