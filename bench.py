@@ -150,6 +150,35 @@ def oracle_iteration_time(wl, steps: int = 1):
     return times
 
 
+def oracle_ladder_rows_time(wl, npairs: int):
+    """Time the oracle's ladder on a sample of (a, b) rows at full size (<ab||cd> rows formed from
+    B^Q, contracted with the full tau) and extrapolate by the number of a < b rows: the ladder
+    term alone, a lower bound on one oracle iteration. Returns (seconds, sample description)."""
+    import numpy as np
+    from oracle import ccsd_ref as R
+    from paper_2103_08473_gb300 import inputs
+
+    s = inputs.make_system(wl["o"], wl["v"], wl["naux"], wl["seed"])
+    t1, t2 = inputs.random_amplitudes(s.o, s.v, wl["seed"] + 77, scale=0.01)
+    tau = R.tau(t1, t2)
+    del t2
+    rng = np.random.default_rng(9)
+    pairs = []
+    while len(pairs) < npairs:
+        a, b = int(rng.integers(s.v)), int(rng.integers(s.v))
+        if a < b:
+            pairs.append((a, b))
+    R.ladder_rows(s.B, s.o, tau, pairs[:1])  # first touch of tau and B
+    t0 = time.perf_counter()
+    R.ladder_rows(s.B, s.o, tau, pairs)
+    dt = time.perf_counter() - t0
+    rows = s.v * (s.v - 1) // 2
+    est = dt / npairs * rows
+    return est, (f"the oracle's ladder term only: {npairs} sampled (a<b) rows of 1/2 sum_cd <ab||cd> tau^cd_ij "
+                 f"at every (i, j), <ab||cd> formed from B^Q (numpy complex128), {dt:.1f} s, extrapolated by "
+                 f"the {rows} rows; a lower bound on one oracle iteration of {wl['name']}")
+
+
 def run_reference(args, wl):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -347,6 +376,9 @@ def run_ours(args, wl):
         cpu = {"value": ct[0], "unit": "s", "cores": cores, "kind": "oracle",
                "sample": f"one full oracle iteration (Appendix A residual + update, numpy complex128) of the "
                          f"{wl['name']} workload, integrals untimed"}
+    elif world == 1 and not args.no_cpu_baseline:
+        est, sample = oracle_ladder_rows_time(wl, 12 if wl["v"] <= 240 else 3)
+        cpu = {"value": est, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample}
     line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if precision == "fp64" else "e4m3 digits, f32 accumulate, f64",

@@ -105,6 +105,9 @@ typedef struct {
   int complex_4m;     /* FP64 GEMMs: 1 = four real products per complex product (4M); 0 = three
                          (3M: Ar Br, Ai Bi, (Ar + Ai)(Br + Bi), combined once per output), about
                          1.28x fewer FP64 operations (default 0) */
+  double split_budget; /* split precision: bytes of digits (both operands) one tensor-core GEMM call
+                          may hold; larger GEMMs run in chunks of M, N and then K (default 0 = a
+                          quarter of the free device memory at creation, 4 to 16 GB) */
 } ccsd_opts;
 
 /* Fill opts with the defaults listed above. */

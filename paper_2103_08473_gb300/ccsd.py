@@ -31,7 +31,7 @@ class ccsd_opts(C.Structure):
                 ("diis_start", C.c_int), ("level_shift", C.c_double), ("precision", C.c_int),
                 ("slices", C.c_int), ("store_w", C.c_int), ("profile", C.c_int), ("stream", C.c_void_p),
                 ("split_min_flops", C.c_double), ("df_block", C.c_int), ("autotune", C.c_int),
-                ("digit_bits", C.c_int), ("complex_4m", C.c_int)]
+                ("digit_bits", C.c_int), ("complex_4m", C.c_int), ("split_budget", C.c_double)]
 
 
 class CCSDError(RuntimeError):

@@ -626,16 +626,19 @@ ccsd_status build_residual_plan(ccsd_ctx* ctx) {
   Plan* P = new Plan(o, v, &ctx->scratch, ctx->stream);
   ctx->plan = P;
   // In split mode a single GEMM of at least split_min_flops goes to the tensor-core digit
-  // path when its modelled time beats the FP64 path (~1 TFLOP/s on this chip); with
-  // split_min_flops <= 0 every GEMM goes there.
-  auto to_split = [ctx](const ZGemmArgs& g) {
+  // path when its modelled time beats the FP64 path (measured on this chip: 1.3e12 of the
+  // conventional 8 flops per complex multiply-add per second with 3M products, 0.95e12 with
+  // 4M); with split_min_flops <= 0 every GEMM goes there.
+  const double fp64_rate = ctx->opts.complex_4m ? 0.95e12 : 1.3e12;
+  auto to_split = [ctx, fp64_rate](const ZGemmArgs& g) {
     if (!ctx->use_split || g.batch != 1) return false;
     const double fl = 8.0 * (double)g.M * (double)g.N * (double)g.K;
     if (ctx->split_min_flops <= 0.0) return true;
-    return fl >= ctx->split_min_flops && split_cost_estimate(g.M, g.N, g.K, ctx->split) < fl / 0.95e12;
+    return fl >= ctx->split_min_flops && split_cost_estimate(g.M, g.N, g.K, ctx->split) < fl / fp64_rate;
   };
   ctx->routes_split = to_split;
-  if (ctx->use_split) ctx->split_budget = split_call_budget();
+  if (ctx->use_split)
+    ctx->split_budget = ctx->opts.split_budget > 0.0 ? (int64_t)ctx->opts.split_budget : split_call_budget();
   P->set_gemm(
       [ctx, to_split](const ZGemmArgs& g, cudaStream_t s) {
         if (to_split(g)) return split_gemm_chunked(ctx, g, s);
@@ -1348,6 +1351,7 @@ void ccsd_default_opts(ccsd_opts* o) {
   o->autotune = 0;
   o->digit_bits = 0;
   o->complex_4m = 0;
+  o->split_budget = 0.0;
 }
 
 ccsd_status ccsd_create(int o, int v, const double* eps, const ccsd_z* fock, ccsd_int_kind kind, const ccsd_z* ints,

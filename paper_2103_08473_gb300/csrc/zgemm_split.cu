@@ -778,7 +778,8 @@ cudaError_t make_slices(const z* X, int64_t rows, int64_t K, int64_t ld, int tra
 double split_cost_estimate(int64_t M, int64_t N, int64_t K, const SplitConfig& cfg) {
   // Model of one split GEMM on this GPU: the tensor-core digit products at ~2.8 PFLOP/s
   // (e4m3; half for bf16), each level group's FP64 flush (~6 FP64 operations per complex
-  // output element of every 128x128 tile) at ~5e11 operations/s, and slicing both operands
+  // output element of every 128x128 tile, with its read and write of the output) at ~3.8e11
+  // operations/s (fitted to short-K launches, where the flushes dominate), and slicing both operands
   // (read twice, digits written once) at ~5 TB/s. Padding to whole tiles and K blocks counted.
   const int bk = bke(cfg.kind);
   const double Mp = (double)round_up(M, 128), Np = (double)round_up(N, 128), Kp = (double)round_up(K, bk);
@@ -791,7 +792,7 @@ double split_cost_estimate(int64_t M, int64_t N, int64_t K, const SplitConfig& c
   if (!fill_levels(a, cfg.s, cfg.b, kblocks, cfg.kind)) return 1e30;
   for (int L = 0; L <= a.lmax; ++L) groups += std::ceil((double)kblocks / a.kbper[L]);
   const double tiles = (Mp / 128.0) * (Np / 128.0);
-  const double flush = tiles * groups * 16384.0 * 6.0 / 5e11;
+  const double flush = tiles * groups * 16384.0 * 6.0 / 3.8e11;
   const double slicing = ((double)(M + N) * K * 32.0 + (double)(M + N) * Kp * 2.0 * cfg.s * esize(cfg.kind)) / 5e12;
   return std::max(mma, flush) + slicing;
 }

@@ -206,3 +206,23 @@ def test_df_ladder_without_stored_w_matches_oracle(ccsd, o, v, naux, seed, blk):
     assert _maxrel(lad, R.ladder(V["vvvv"], R.tau(t1, t2))) < 1e-12
     ref = R.solve(f, V, o, v, max_iter=3, tol=0.0)
     assert abs(e - ref["energy"]) < 1e-10
+
+
+@pytest.mark.parametrize("o,v", [(1, 4), (3, 1), (2, 2), (1, 1)])
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+def test_degenerate_shapes_match_oracle(ccsd, o, v, precision):
+    """No (i<j) pair (o = 1), no (a<b) pair (v = 1), one pair of each: the doubles vanish or
+    shrink to single pairs; residual, a few iterations and the energy still follow the oracle."""
+    s, f, fock = _sys(o, v, 5, 300 + 10 * o + v, scale=0.3, fock_scale=0.1)
+    V = R.integrals(s.B, o)
+    t1, t2 = inputs.random_amplitudes(o, v, 7, scale=0.1)
+    S1, S2 = R.residual(f, V, t1, t2)
+    kw = dict(precision=ccsd.PREC_SPLIT, split_min_flops=0.0) if precision == "split" else {}
+    tol = 1e-10 if precision == "split" else 1e-12
+    with ccsd.CCSD(o, v, s.eps, B=s.B, fock=fock, tol=0.0, **kw) as cc:
+        r1, r2 = cc.residual(t1, t2)       # the context keeps its own (MP2) amplitudes
+        assert _maxrel(r1, S1) < tol and _maxrel(r2, S2) < tol
+        ref = R.solve(f, V, o, v, max_iter=3, tol=0.0)
+        st, it, nrm = cc.iterate(3)
+        assert it == 3
+        assert abs(cc.energy() - ref["energy"]) < 1e-9

@@ -132,3 +132,18 @@ def test_split_full_size_o60_v400_df_ladder_sampled(ccsd):
     tol = 1e-13 * np.max(np.abs(r2))
     assert np.max(np.abs(r2 + r2.transpose(1, 0, 2, 3))) <= tol
     assert np.max(np.abs(r2 + r2.transpose(0, 1, 3, 2))) <= tol
+
+
+def test_split_residual_in_small_chunks_matches_oracle(ccsd):
+    """A digit budget of 300 kB per tensor-core call forces every split GEMM of the plan into
+    chunks of M, N and K (K chunks are GEMMs of their own scales, summed in FP64)."""
+    o, v, naux, seed = 6, 48, 40, 207
+    s = inputs.make_system(o, v, naux, seed, scale=0.05)
+    f = R.fock_matrix(s.eps)
+    V = R.integrals(s.B, o)
+    t1, t2 = inputs.random_amplitudes(o, v, seed + 1, scale=0.05)
+    S1, S2 = R.residual(f, V, t1, t2)
+    with ccsd.CCSD(o, v, s.eps, B=s.B, precision=ccsd.PREC_SPLIT, split_min_flops=0.0,
+                   split_budget=3e5) as cc:
+        r1, r2 = cc.residual(t1, t2)
+    assert _maxrel(r1, S1) < 1e-10 and _maxrel(r2, S2) < 1e-10
