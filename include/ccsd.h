@@ -86,7 +86,7 @@ typedef struct {
   double level_shift; /* added to virtual orbital energies in the denominators only (default 0) */
   int precision;      /* ccsd_precision (default CCSD_PREC_FP64) */
   int slices;         /* split precision: e4m3 digits per operand, 1..14 with digit_bits * slices <= 56
-                         (default 0 = about 44 bits: 9 digits of 5 bits, 11 of 4) */
+                         (default 0 = about 39 bits: 8 digits of 5 bits, 10 of 4) */
   int store_w;        /* 1: store <ab||cd> (packed); 0: never store it, rebuild it in blocks of rows
                          from the DF factors inside each ladder evaluation (DF input only) (default 1) */
   int profile;        /* 1: record per-term CUDA-event timings (default 0) */

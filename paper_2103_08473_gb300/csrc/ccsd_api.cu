@@ -1111,8 +1111,8 @@ ccsd_status create_impl(int o, int v, const double* eps, const ccsd_z* fock, ccs
     if (ctx->opts.digit_bits < 0 || ctx->opts.digit_bits > 5)
       return set_err(ctx, CCSD_ERR_ARG, "digit_bits must be in [1, 5] (e4m3 digits), 0 = 5");
     ctx->split.b = ctx->opts.digit_bits > 0 ? ctx->opts.digit_bits : 5;
-    // default: about 44 bits of every row's scale (9 digits of 5 bits, 11 of 4)
-    ctx->split.s = ctx->opts.slices > 0 ? ctx->opts.slices : (44 + ctx->split.b) / ctx->split.b;
+    // default: about 39 bits of every row's scale (8 digits of 5 bits, 10 of 4)
+    ctx->split.s = ctx->opts.slices > 0 ? ctx->opts.slices : (39 + ctx->split.b) / ctx->split.b;
     ctx->split_min_flops = ctx->opts.split_min_flops;
     if (ctx->split.s > 14 || ctx->split.b * ctx->split.s > 56)
       return set_err(ctx, CCSD_ERR_ARG, "slices must be <= 14 with digit_bits * slices <= 56");

@@ -396,6 +396,226 @@ __global__ void __launch_bounds__(192, 1)
   }
 }
 
+// ---- the short-K GEMM kernel --------------------------------------------------
+//
+// For K of a few blocks the main kernel is bound by its FP64 flushes: every weight level is
+// one group, so each output tile is read and rewritten once per level. Here every level
+// keeps its own FP32 accumulator in tensor memory over the whole K (exact: K is within every
+// level's bound), on 128 x 32 output tiles: level L's real and imaginary parts are TMEM
+// columns 64 L .. 64 L + 31 and 64 L + 32 .. 64 L + 63 (at most 8 levels in 512 columns).
+// The epilogue combines the levels in FP64 registers and writes each output once (after
+// releasing tensor memory, so the next tile's products overlap the stores). With transC the
+// kernel computes the transpose (its rows are the output's columns), so that the long
+// dimension fills the 128-row tiles and the stores of a warp are contiguous. Persistent over
+// tiles; every wait bounded, as in the main kernel.
+
+constexpr int kSkStages = 4;
+constexpr uint32_t kSkTileA = 128 * 128;  // bytes of a 128-row x 128-byte digit tile
+constexpr uint32_t kSkTileB = 32 * 128;   // bytes of a 32-row x 128-byte digit tile
+constexpr uint32_t kSkStageBytes = 2 * kSkTileA + 2 * kSkTileB;
+constexpr uint32_t kSkSmemBytes = kSkStages * kSkStageBytes + 1024 + 256;
+constexpr int kSkBN = 32;
+
+__host__ __device__ constexpr uint32_t make_idesc_n32(int kind, int negB) {
+  return (1u << 4) | ((kind == kSplitBF16 ? 1u : 0u) << 7) | ((kind == kSplitBF16 ? 1u : 0u) << 10) |
+         ((uint32_t)negB << 14) | (((uint32_t)kSkBN >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+struct SmallKArgs {
+  int64_t M, N, Mp, Np, a_row0, b_row0;
+  int tiles_m, tiles;
+  int s, b, lmax, kblocks;
+  z* C;
+  int64_t ldc;
+  z alpha, beta;
+  int transC;
+  const double* rs;
+  const double* cs;
+  int* err;
+  long long wait_cycles;
+};
+
+template <int KIND>
+__global__ void __launch_bounds__(192, 1)
+    split_smallk_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                        SmallKArgs args) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  const uint32_t bar0 = base + kSkStages * kSkStageBytes;
+  auto full = [&](int s) { return bar0 + 8u * s; };
+  auto empty = [&](int s) { return bar0 + 8u * (kSkStages + s); };
+  const uint32_t accfull = bar0 + 8u * (2 * kSkStages);
+  const uint32_t accempty = bar0 + 8u * (2 * kSkStages + 1);
+  const uint32_t done = bar0 + 8u * (2 * kSkStages + 2);
+  uint8_t* gen = smem_raw + (base - raw);
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(gen + kSkStages * kSkStageBytes + 8 * (2 * kSkStages + 3));
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int BKE = KIND == kSplitBF16 ? 64 : 128;
+  const int S = args.s;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kSkStages; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), 1);
+    }
+    mbar_init(accfull, 1);
+    mbar_init(accempty, 128);
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    tc_fence_before();
+  }
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+  const long long budget = args.wait_cycles;
+
+  if (warp == 0) {
+    // ---------------- TMA producer: (k block, p, q) with p + q <= s - 1, tile after tile ----------------
+    if (lane == 0) {
+      int it = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < args.tiles && ok; tile += gridDim.x) {
+        const int64_t m0 = (int64_t)(tile % args.tiles_m) * 128, n0 = (int64_t)(tile / args.tiles_m) * kSkBN;
+        const int64_t ya = args.a_row0 + m0, yb = args.b_row0 + n0;
+        for (int kb = 0; kb < args.kblocks && ok; ++kb)
+          for (int p = 0; p < S && ok; ++p)
+            for (int q = 0; q < S - p; ++q, ++it) {
+              const int st = it % kSkStages;
+              const uint32_t ph = (uint32_t)(it / kSkStages) & 1u;
+              if (!mbar_wait(empty(st), ph ^ 1u, budget, abort_flag)) {
+                ok = false;
+                break;
+              }
+              const uint32_t sa = base + st * kSkStageBytes;
+              const int x = kb * BKE;
+              mbar_expect_tx(full(st), 2 * kSkTileA + 2 * kSkTileB);
+              tma_load_2d(sa, &tmA, x, (int)((p * 2 + 0) * args.Mp + ya), full(st));
+              tma_load_2d(sa + kSkTileA, &tmA, x, (int)((p * 2 + 1) * args.Mp + ya), full(st));
+              tma_load_2d(sa + 2 * kSkTileA, &tmB, x, (int)((q * 2 + 0) * args.Np + yb), full(st));
+              tma_load_2d(sa + 2 * kSkTileA + kSkTileB, &tmB, x, (int)((q * 2 + 1) * args.Np + yb), full(st));
+            }
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicOr(args.err, 1);
+      }
+      const int last = it;  // drain: every copy issued has landed before the CTA exits
+      for (int j = (last > kSkStages ? last - kSkStages : 0); j < last; ++j)
+        mbar_wait(full(j % kSkStages), (uint32_t)(j / kSkStages) & 1u, budget, abort_flag, true);
+    }
+  } else if (warp == 1) {
+    // ---------------- UMMA issuer: pair (p, q) into level p + q's accumulator ----------------
+    if (lane == 0) {
+      const uint32_t id = make_idesc_n32(KIND, 0), idn = make_idesc_n32(KIND, 1);
+      int it = 0, t = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < args.tiles && ok; tile += gridDim.x, ++t) {
+        if (!mbar_wait(accempty, ((uint32_t)t & 1u) ^ 1u, budget, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        uint32_t started = 0;  // levels whose accumulator holds this tile's partial sums
+        for (int kb = 0; kb < args.kblocks && ok; ++kb)
+          for (int p = 0; p < S && ok; ++p)
+            for (int q = 0; q < S - p; ++q, ++it) {
+              const int st = it % kSkStages;
+              const uint32_t ph = (uint32_t)(it / kSkStages) & 1u;
+              if (!mbar_wait(full(st), ph, budget, abort_flag)) {
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+              const int L = p + q;
+              const uint32_t dre = tmem + (uint32_t)L * 64u, dim = dre + 32u;
+              const uint32_t sa = base + st * kSkStageBytes, sb = sa + 2 * kSkTileA;
+              const bool first = !(started & (1u << L));
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk) {
+                const uint32_t acc = (first && kk == 0) ? 0u : 1u;
+                const uint64_t aR = sw128_desc(sa + kk * 32), aI = sw128_desc(sa + kSkTileA + kk * 32);
+                const uint64_t bR = sw128_desc(sb + kk * 32), bI = sw128_desc(sb + kSkTileB + kk * 32);
+                umma<KIND>(dre, aR, bR, id, acc);
+                umma<KIND>(dre, aI, bI, idn, 1u);
+                umma<KIND>(dim, aR, bI, id, acc);
+                umma<KIND>(dim, aI, bR, id, 1u);
+              }
+              started |= 1u << L;
+              umma_commit(empty(st));
+            }
+        if (ok) umma_commit(accfull);
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicOr(args.err, 2);
+      }
+      umma_commit(done);  // all issued MMAs complete before TMEM is released
+      mbar_wait(done, 0u, budget, abort_flag, true);
+    }
+    __syncwarp();
+  } else {
+    // ---------------- epilogue: warps 2..5, one row of the tile per thread ----------------
+    const int q4 = warp & 3;
+    int t = 0;
+    for (int tile = blockIdx.x; tile < args.tiles; tile += gridDim.x, ++t) {
+      if (!mbar_wait(accfull, (uint32_t)t & 1u, budget, abort_flag)) {
+        *abort_flag = 1;
+        atomicOr(args.err, 4);
+        break;
+      }
+      tc_fence_after();
+      const int64_t m0 = (int64_t)(tile % args.tiles_m) * 128, n0 = (int64_t)(tile / args.tiles_m) * kSkBN;
+      const int64_t m = m0 + q4 * 32 + lane;
+      double ar[kSkBN], ai[kSkBN];
+#pragma unroll
+      for (int j = 0; j < kSkBN; ++j) ar[j] = ai[j] = 0.0;
+      const uint32_t trow = tmem + ((uint32_t)(q4 * 32) << 16);
+      for (int L = 0; L <= args.lmax; ++L) {
+        uint32_t re[32], im[32];
+        tmem_ld32(trow + (uint32_t)L * 64u, re);
+        tmem_ld32(trow + (uint32_t)L * 64u + 32u, im);
+        tmem_wait_ld();
+        const double gs = ldexp(1.0, -args.b * (L + 2));
+#pragma unroll
+        for (int j = 0; j < kSkBN; ++j) {
+          ar[j] = fma((double)__uint_as_float(re[j]), gs, ar[j]);
+          ai[j] = fma((double)__uint_as_float(im[j]), gs, ai[j]);
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(accempty);  // tensor memory is free for the next tile
+      if (m < args.M) {
+        const double rsc = args.rs[m];
+        const bool read_c = args.beta.x != 0.0 || args.beta.y != 0.0;
+#pragma unroll
+        for (int j = 0; j < kSkBN; ++j) {
+          const int64_t n = n0 + j;
+          if (n >= args.N) break;
+          const double f = rsc * args.cs[n];
+          z val = zmul(args.alpha, make_double2(ar[j] * f, ai[j] * f));
+          z* cp = args.transC ? args.C + n * args.ldc + m : args.C + m * args.ldc + n;
+          if (read_c) val = zadd(val, zmul(args.beta, *cp));
+          *cp = val;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  }
+}
+
 // ---- digit slicing ----------------------------------------------------------
 
 
@@ -413,9 +633,12 @@ __device__ __forceinline__ void put_digit(uint8_t* out, int64_t idx, double d) {
 // left (round half up), subtracted off before the next. FP64 work is one multiply
 // and one conversion per element; the digits come from the integer pipes.
 __device__ __forceinline__ long long fixed62(double x) { return __double2ll_rn(x * 4611686018427387904.0); }
+// Ties round away from zero, so that the digits of -x are exactly the negated digits of x
+// (products of antisymmetric tensors stay exactly antisymmetric).
 __device__ __forceinline__ int next_digit(long long& V, int shift) {
-  const long long d = (V + (1LL << (shift - 1))) >> shift;
-  V -= d << shift;
+  const long long h = 1LL << (shift - 1);
+  const long long d = V >= 0 ? (V + h) >> shift : -((h - V) >> shift);
+  V -= d * (1LL << shift);
   return (int)d;
 }
 
@@ -637,6 +860,33 @@ cudaError_t encode_map(SliceSet& S) {
   return S.have_map ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// The same map over the digit array with a box of box_rows rows.
+cudaError_t encode_map_rows(const SliceSet& S, uint32_t box_rows, CUtensorMap* out) {
+  auto enc = get_encode();
+  if (!enc) return cudaErrorNotSupported;
+  const int es = esize(S.kind);
+  cuuint64_t dims[2] = {(cuuint64_t)S.Kp, (cuuint64_t)(S.s * 2 * S.rows_pad)};
+  cuuint64_t strides[1] = {(cuuint64_t)(S.Kp * es)};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / es), box_rows};
+  cuuint32_t estr[2] = {1u, 1u};
+  CUresult r = enc(out, S.kind == kSplitBF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+                   S.digits, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+int num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      n = 148;
+    }
+  }
+  return n;
+}
+
 double maxdigit(int p, int b, int headroom) { return p == 0 && !headroom ? std::ldexp(1.0, b) : std::ldexp(1.0, b - 1); }
 
 // K blocks per exact chunk of each level: the pairs (p, L - p) of level L share one
@@ -658,6 +908,17 @@ bool fill_levels(SplitArgs& a, int s, int b, int kblocks, int kind) {
     if (kb < 1) return false;
     a.kbper[L] = kb;
   }
+  return true;
+}
+
+// The short-K kernel takes a launch when every level fits its tensor memory (at most 8
+// levels) and one accumulator per level stays exact over the whole K, and K is short
+// enough (a few blocks) that the main kernel would be bound by its per-level flushes.
+constexpr int kSmallKMaxBlocks = 4;
+bool smallk_eligible(const SplitArgs& a) {
+  if (a.lmax + 1 > 8 || a.kblocks > kSmallKMaxBlocks) return false;
+  for (int L = 0; L <= a.lmax; ++L)
+    if (a.kbper[L] < a.kblocks) return false;
   return true;
 }
 
@@ -706,6 +967,60 @@ cudaError_t launch_split(const SliceSet& A, const SliceSet& B, const SplitArgs& 
   if (grid > 0x7fffffff) return cudaErrorInvalidValue;
   kern<<<(unsigned)grid, 192, kSmemBytes, s>>>(A.tmap, B.tmap, a);
   return cudaGetLastError();
+}
+
+template <int KIND>
+cudaError_t launch_smallk(const CUtensorMap& mapA, const CUtensorMap& mapB, const SmallKArgs& a, cudaStream_t s) {
+  auto kern = split_smallk_kernel<KIND>;
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [&]() {
+    attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSkSmemBytes);
+  });
+  if (attr_err != cudaSuccess) return attr_err;
+  if (a.tiles <= 0) return cudaSuccess;
+  const int grid = std::min(a.tiles, num_sms());
+  kern<<<grid, 192, kSkSmemBytes, s>>>(mapA, mapB, a);
+  return cudaGetLastError();
+}
+
+// C = alpha A B^T + beta C on the short-K kernel; the operand with more rows goes to the
+// 128-row side (with the output transposed when that is B).
+cudaError_t split_gemm_smallk(const SliceSet& A, const SliceSet& B, const SplitArgs& lv, z* C, int64_t ldc, z alpha,
+                              z beta, int* err, long long wait_cycles, cudaStream_t s) {
+  const bool swap = A.rows < B.rows;
+  const SliceSet& KA = swap ? B : A;
+  const SliceSet& KB = swap ? A : B;
+  SmallKArgs k;
+  std::memset(&k, 0, sizeof(k));
+  k.M = KA.rows;
+  k.N = KB.rows;
+  k.Mp = KA.rows_pad;
+  k.Np = KB.rows_pad;
+  k.a_row0 = KA.row0;
+  k.b_row0 = KB.row0;
+  const int64_t tm = (k.M + 127) / 128, tn = (k.N + kSkBN - 1) / kSkBN;
+  if (tm * tn > 0x7fffffff) return cudaErrorInvalidValue;
+  k.tiles_m = (int)tm;
+  k.tiles = (int)(tm * tn);
+  k.s = lv.s;
+  k.b = lv.b;
+  k.lmax = lv.lmax;
+  k.kblocks = lv.kblocks;
+  k.C = C;
+  k.ldc = ldc;
+  k.alpha = alpha;
+  k.beta = beta;
+  k.transC = swap ? 1 : 0;
+  k.rs = KA.scale;
+  k.cs = KB.scale;
+  k.err = err;
+  k.wait_cycles = wait_cycles > 0 ? wait_cycles : 4000000000LL;
+  CUtensorMap mapB;
+  cudaError_t e = encode_map_rows(KB, (uint32_t)kSkBN, &mapB);
+  if (e != cudaSuccess) return e;
+  return KA.kind == kSplitBF16 ? launch_smallk<kSplitBF16>(KA.tmap, mapB, k, s)
+                               : launch_smallk<kSplitE4M3>(KA.tmap, mapB, k, s);
 }
 
 }  // namespace
@@ -792,6 +1107,16 @@ double split_cost_estimate(int64_t M, int64_t N, int64_t K, const SplitConfig& c
   if (!fill_levels(a, cfg.s, cfg.b, kblocks, cfg.kind)) return 1e30;
   for (int L = 0; L <= a.lmax; ++L) groups += std::ceil((double)kblocks / a.kbper[L]);
   const double tiles = (Mp / 128.0) * (Np / 128.0);
+  const double slicing0 = ((double)(M + N) * K * 32.0 + (double)(M + N) * Kp * 2.0 * cfg.s * esize(cfg.kind)) / 5e12;
+  if (smallk_eligible(a)) {
+    // short K: 128 x 32 tiles with the long side as rows, products at ~40% of the tensor rate
+    // (N = 32 instructions), every output written once
+    const double lo = (double)std::min(M, N), hi = (double)std::max(M, N);
+    const double sk_mma = pairs * 8.0 * (double)round_up((int64_t)hi, 128) * (double)round_up((int64_t)lo, 32) * Kp /
+                          (0.4 * (cfg.kind == kSplitBF16 ? 1.4e15 : 2.8e15));
+    const double store = (double)M * N * 32.0 / 5e12;
+    return std::max(sk_mma, store) + slicing0;
+  }
   const double flush = tiles * groups * 16384.0 * 6.0 / 3.8e11;
   const double slicing = ((double)(M + N) * K * 32.0 + (double)(M + N) * Kp * 2.0 * cfg.s * esize(cfg.kind)) / 5e12;
   return std::max(mma, flush) + slicing;
@@ -829,6 +1154,8 @@ cudaError_t split_gemm(const SliceSet& A, const SliceSet& B, z* C, int64_t ldc, 
   a.stall_loads = stall_loads;
   const int kblocks = (int)(A.Kp / bke(A.kind));
   if (!fill_levels(a, A.s, A.b, kblocks, A.kind)) return cudaErrorInvalidValue;
+  if (!stall_loads && smallk_eligible(a))
+    return split_gemm_smallk(A, B, a, C, ldc, alpha, beta, err, wait_cycles, s);
   plan_ksplit(a.tiles, kblocks, a.ksplits, a.kb_split);
   if (stall_loads) {
     a.ksplits = 1;

@@ -116,3 +116,26 @@ def test_bounded_wait_gives_up_and_the_device_stays_usable(env):
     ccsd.split_zgemm(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), dc)
     want = a @ b
     assert np.max(np.abs(dc.cpu().numpy() - want)) / np.max(np.abs(want)) < 2e-12
+
+
+@pytest.mark.parametrize("M,N,K,slices,conjA,conjB,beta", [
+    (20, 3000, 120, 8, 0, 0, 0.0),     # the short side as the 32-wide tiles, output transposed
+    (3000, 40, 64, 8, 1, 0, 0.5 - 1j),  # no swap, conj(A), beta applied in the epilogue
+    (300, 200, 512, 7, 0, 1, 1.0),    # four K blocks, the longest K the short-K kernel takes
+    (130, 33, 1, 8, 1, 1, 0.0),       # K = 1, ragged tiles on both sides
+])
+def test_short_k_kernel_matches_complex128(env, M, N, K, slices, conjA, conjB, beta):
+    """GEMMs of at most four K blocks with at most eight digit levels run on the short-K kernel
+    (every level its own accumulator in tensor memory, one store per output)."""
+    torch, ccsd = env
+    rng = np.random.default_rng(M + N + K)
+    a, b, c0 = _rand(rng, M, K), _rand(rng, N, K), _rand(rng, M, N)
+    alpha = 0.5 + 0.25j
+    opa = np.conj(a) if conjA else a
+    opb = np.conj(b) if conjB else b
+    want = alpha * (opa @ opb.T) + beta * c0
+    dc = torch.from_numpy(c0).cuda()
+    ccsd.split_zgemm(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), dc, alpha, beta, conjA=bool(conjA),
+                     transB=True, conjB=bool(conjB), bits=5, slices=slices)
+    err = np.max(np.abs(dc.cpu().numpy() - want)) / np.max(np.abs(want))
+    assert err < (2e-10 if slices == 8 else 6e-9), err
