@@ -409,11 +409,14 @@ __global__ void __launch_bounds__(192, 1)
 // dimension fills the 128-row tiles and the stores of a warp are contiguous. Persistent over
 // tiles; every wait bounded, as in the main kernel.
 
-constexpr int kSkStages = 4;
-constexpr uint32_t kSkTileA = 128 * 128;  // bytes of a 128-row x 128-byte digit tile
-constexpr uint32_t kSkTileB = 32 * 128;   // bytes of a 32-row x 128-byte digit tile
-constexpr uint32_t kSkStageBytes = 2 * kSkTileA + 2 * kSkTileB;
-constexpr uint32_t kSkSmemBytes = kSkStages * kSkStageBytes + 1024 + 256;
+constexpr int kSkAStages = 3;               // A tiles (one digit plane, real and imaginary)
+constexpr int kSkBBufs = 2;                 // B buffers (every digit plane of one K block)
+constexpr int kSkMaxLevels = 8;
+constexpr uint32_t kSkTileA = 128 * 128;    // bytes of a 128-row x 128-byte digit tile
+constexpr uint32_t kSkTileB = 32 * 128;     // bytes of a 32-row x 128-byte digit tile
+constexpr uint32_t kSkAStage = 2 * kSkTileA;
+constexpr uint32_t kSkBBuf = kSkMaxLevels * 2 * kSkTileB;
+constexpr uint32_t kSkSmemBytes = kSkAStages * kSkAStage + kSkBBufs * kSkBBuf + 1024 + 256;
 constexpr int kSkBN = 32;
 
 __host__ __device__ constexpr uint32_t make_idesc_n32(int kind, int negB) {
@@ -435,6 +438,8 @@ struct SmallKArgs {
   long long wait_cycles;
 };
 
+// Per K block: every B digit plane is loaded once into a B buffer, then each A plane p once
+// into an A stage, and the products of p with every q <= s - 1 - p are issued from them.
 template <int KIND>
 __global__ void __launch_bounds__(192, 1)
     split_smallk_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -442,14 +447,19 @@ __global__ void __launch_bounds__(192, 1)
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
-  const uint32_t bar0 = base + kSkStages * kSkStageBytes;
-  auto full = [&](int s) { return bar0 + 8u * s; };
-  auto empty = [&](int s) { return bar0 + 8u * (kSkStages + s); };
-  const uint32_t accfull = bar0 + 8u * (2 * kSkStages);
-  const uint32_t accempty = bar0 + 8u * (2 * kSkStages + 1);
-  const uint32_t done = bar0 + 8u * (2 * kSkStages + 2);
+  const uint32_t abase = base, bbase = base + kSkAStages * kSkAStage;
+  const uint32_t bar0 = bbase + kSkBBufs * kSkBBuf;
+  auto afull = [&](int s) { return bar0 + 8u * s; };
+  auto aempty = [&](int s) { return bar0 + 8u * (kSkAStages + s); };
+  auto bfull = [&](int s) { return bar0 + 8u * (2 * kSkAStages + s); };
+  auto bempty = [&](int s) { return bar0 + 8u * (2 * kSkAStages + kSkBBufs + s); };
+  constexpr int kBars = 2 * kSkAStages + 2 * kSkBBufs;
+  const uint32_t accfull = bar0 + 8u * kBars;
+  const uint32_t accempty = bar0 + 8u * (kBars + 1);
+  const uint32_t done = bar0 + 8u * (kBars + 2);
   uint8_t* gen = smem_raw + (base - raw);
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(gen + kSkStages * kSkStageBytes + 8 * (2 * kSkStages + 3));
+  uint32_t* tmem_holder =
+      reinterpret_cast<uint32_t*>(gen + kSkAStages * kSkAStage + kSkBBufs * kSkBBuf + 8 * (kBars + 3));
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -457,9 +467,13 @@ __global__ void __launch_bounds__(192, 1)
   const int S = args.s;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kSkStages; ++s) {
-      mbar_init(full(s), 1);
-      mbar_init(empty(s), 1);
+    for (int s = 0; s < kSkAStages; ++s) {
+      mbar_init(afull(s), 1);
+      mbar_init(aempty(s), 1);
+    }
+    for (int s = 0; s < kSkBBufs; ++s) {
+      mbar_init(bfull(s), 1);
+      mbar_init(bempty(s), 1);
     }
     mbar_init(accfull, 1);
     mbar_init(accempty, 128);
@@ -479,44 +493,56 @@ __global__ void __launch_bounds__(192, 1)
   const long long budget = args.wait_cycles;
 
   if (warp == 0) {
-    // ---------------- TMA producer: (k block, p, q) with p + q <= s - 1, tile after tile ----------------
+    // ---------------- TMA producer ----------------
     if (lane == 0) {
-      int it = 0;
+      int ja = 0, jb = 0;
       bool ok = true;
       for (int tile = blockIdx.x; tile < args.tiles && ok; tile += gridDim.x) {
         const int64_t m0 = (int64_t)(tile % args.tiles_m) * 128, n0 = (int64_t)(tile / args.tiles_m) * kSkBN;
         const int64_t ya = args.a_row0 + m0, yb = args.b_row0 + n0;
-        for (int kb = 0; kb < args.kblocks && ok; ++kb)
-          for (int p = 0; p < S && ok; ++p)
-            for (int q = 0; q < S - p; ++q, ++it) {
-              const int st = it % kSkStages;
-              const uint32_t ph = (uint32_t)(it / kSkStages) & 1u;
-              if (!mbar_wait(empty(st), ph ^ 1u, budget, abort_flag)) {
-                ok = false;
-                break;
-              }
-              const uint32_t sa = base + st * kSkStageBytes;
-              const int x = kb * BKE;
-              mbar_expect_tx(full(st), 2 * kSkTileA + 2 * kSkTileB);
-              tma_load_2d(sa, &tmA, x, (int)((p * 2 + 0) * args.Mp + ya), full(st));
-              tma_load_2d(sa + kSkTileA, &tmA, x, (int)((p * 2 + 1) * args.Mp + ya), full(st));
-              tma_load_2d(sa + 2 * kSkTileA, &tmB, x, (int)((q * 2 + 0) * args.Np + yb), full(st));
-              tma_load_2d(sa + 2 * kSkTileA + kSkTileB, &tmB, x, (int)((q * 2 + 1) * args.Np + yb), full(st));
+        for (int kb = 0; kb < args.kblocks && ok; ++kb, ++jb) {
+          const int x = kb * BKE;
+          {
+            const int bs = jb % kSkBBufs;
+            if (!mbar_wait(bempty(bs), ((uint32_t)(jb / kSkBBufs) & 1u) ^ 1u, budget, abort_flag)) {
+              ok = false;
+              break;
             }
+            const uint32_t dst = bbase + bs * kSkBBuf;
+            mbar_expect_tx(bfull(bs), (uint32_t)S * 2u * kSkTileB);
+            for (int q = 0; q < S; ++q)
+              for (int r = 0; r < 2; ++r)
+                tma_load_2d(dst + (uint32_t)(q * 2 + r) * kSkTileB, &tmB, x, (int)((q * 2 + r) * args.Np + yb),
+                            bfull(bs));
+          }
+          for (int p = 0; p < S; ++p, ++ja) {
+            const int as = ja % kSkAStages;
+            if (!mbar_wait(aempty(as), ((uint32_t)(ja / kSkAStages) & 1u) ^ 1u, budget, abort_flag)) {
+              ok = false;
+              break;
+            }
+            const uint32_t dst = abase + as * kSkAStage;
+            mbar_expect_tx(afull(as), kSkAStage);
+            tma_load_2d(dst, &tmA, x, (int)((p * 2 + 0) * args.Mp + ya), afull(as));
+            tma_load_2d(dst + kSkTileA, &tmA, x, (int)((p * 2 + 1) * args.Mp + ya), afull(as));
+          }
+        }
       }
       if (!ok) {
         *abort_flag = 1;
         atomicOr(args.err, 1);
       }
-      const int last = it;  // drain: every copy issued has landed before the CTA exits
-      for (int j = (last > kSkStages ? last - kSkStages : 0); j < last; ++j)
-        mbar_wait(full(j % kSkStages), (uint32_t)(j / kSkStages) & 1u, budget, abort_flag, true);
+      // drain: every copy issued has landed before the CTA exits
+      for (int j = (ja > kSkAStages ? ja - kSkAStages : 0); j < ja; ++j)
+        mbar_wait(afull(j % kSkAStages), (uint32_t)(j / kSkAStages) & 1u, budget, abort_flag, true);
+      for (int j = (jb > kSkBBufs ? jb - kSkBBufs : 0); j < jb; ++j)
+        mbar_wait(bfull(j % kSkBBufs), (uint32_t)(j / kSkBBufs) & 1u, budget, abort_flag, true);
     }
   } else if (warp == 1) {
     // ---------------- UMMA issuer: pair (p, q) into level p + q's accumulator ----------------
     if (lane == 0) {
       const uint32_t id = make_idesc_n32(KIND, 0), idn = make_idesc_n32(KIND, 1);
-      int it = 0, t = 0;
+      int ja = 0, jb = 0, t = 0;
       bool ok = true;
       for (int tile = blockIdx.x; tile < args.tiles && ok; tile += gridDim.x, ++t) {
         if (!mbar_wait(accempty, ((uint32_t)t & 1u) ^ 1u, budget, abort_flag)) {
@@ -525,33 +551,43 @@ __global__ void __launch_bounds__(192, 1)
         }
         tc_fence_after();
         uint32_t started = 0;  // levels whose accumulator holds this tile's partial sums
-        for (int kb = 0; kb < args.kblocks && ok; ++kb)
-          for (int p = 0; p < S && ok; ++p)
-            for (int q = 0; q < S - p; ++q, ++it) {
-              const int st = it % kSkStages;
-              const uint32_t ph = (uint32_t)(it / kSkStages) & 1u;
-              if (!mbar_wait(full(st), ph, budget, abort_flag)) {
-                ok = false;
-                break;
-              }
-              tc_fence_after();
+        for (int kb = 0; kb < args.kblocks && ok; ++kb, ++jb) {
+          const int bs = jb % kSkBBufs;
+          if (!mbar_wait(bfull(bs), (uint32_t)(jb / kSkBBufs) & 1u, budget, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sb = bbase + bs * kSkBBuf;
+          for (int p = 0; p < S && ok; ++p, ++ja) {
+            const int as = ja % kSkAStages;
+            if (!mbar_wait(afull(as), (uint32_t)(ja / kSkAStages) & 1u, budget, abort_flag)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t sa = abase + as * kSkAStage;
+            for (int q = 0; q < S - p; ++q) {
               const int L = p + q;
               const uint32_t dre = tmem + (uint32_t)L * 64u, dim = dre + 32u;
-              const uint32_t sa = base + st * kSkStageBytes, sb = sa + 2 * kSkTileA;
+              const uint32_t sbr = sb + (uint32_t)(q * 2) * kSkTileB, sbi = sbr + kSkTileB;
               const bool first = !(started & (1u << L));
 #pragma unroll
               for (int kk = 0; kk < 4; ++kk) {
                 const uint32_t acc = (first && kk == 0) ? 0u : 1u;
                 const uint64_t aR = sw128_desc(sa + kk * 32), aI = sw128_desc(sa + kSkTileA + kk * 32);
-                const uint64_t bR = sw128_desc(sb + kk * 32), bI = sw128_desc(sb + kSkTileB + kk * 32);
+                const uint64_t bR = sw128_desc(sbr + kk * 32), bI = sw128_desc(sbi + kk * 32);
                 umma<KIND>(dre, aR, bR, id, acc);
                 umma<KIND>(dre, aI, bI, idn, 1u);
                 umma<KIND>(dim, aR, bI, id, acc);
                 umma<KIND>(dim, aI, bR, id, 1u);
               }
               started |= 1u << L;
-              umma_commit(empty(st));
             }
+            umma_commit(aempty(as));
+          }
+          if (ok) umma_commit(bempty(bs));
+        }
         if (ok) umma_commit(accfull);
       }
       if (!ok) {
