@@ -611,33 +611,36 @@ __global__ void __launch_bounds__(192, 1)
       tc_fence_after();
       const int64_t m0 = (int64_t)(tile % args.tiles_m) * 128, n0 = (int64_t)(tile / args.tiles_m) * kSkBN;
       const int64_t m = m0 + q4 * 32 + lane;
-      double ar[kSkBN], ai[kSkBN];
+      // Every level's sum is an integer below 2^24 in magnitude (exact in FP32); the levels are
+      // combined exactly in 64-bit integers, sum_L acc_L 2^(b (lmax - L)) < 2^62, on the integer
+      // pipes, and converted to FP64 once (the FP64 pipe of this chip is the scarce one).
+      long long ar[kSkBN], ai[kSkBN];
 #pragma unroll
-      for (int j = 0; j < kSkBN; ++j) ar[j] = ai[j] = 0.0;
+      for (int j = 0; j < kSkBN; ++j) ar[j] = ai[j] = 0;
       const uint32_t trow = tmem + ((uint32_t)(q4 * 32) << 16);
       for (int L = 0; L <= args.lmax; ++L) {
         uint32_t re[32], im[32];
         tmem_ld32(trow + (uint32_t)L * 64u, re);
         tmem_ld32(trow + (uint32_t)L * 64u + 32u, im);
         tmem_wait_ld();
-        const double gs = ldexp(1.0, -args.b * (L + 2));
+        const long long w = 1LL << (args.b * (args.lmax - L));
 #pragma unroll
         for (int j = 0; j < kSkBN; ++j) {
-          ar[j] = fma((double)__uint_as_float(re[j]), gs, ar[j]);
-          ai[j] = fma((double)__uint_as_float(im[j]), gs, ai[j]);
+          ar[j] += (long long)__float2int_rn(__uint_as_float(re[j])) * w;
+          ai[j] += (long long)__float2int_rn(__uint_as_float(im[j])) * w;
         }
       }
       tc_fence_before();
       mbar_arrive(accempty);  // tensor memory is free for the next tile
       if (m < args.M) {
-        const double rsc = args.rs[m];
+        const double rsc = args.rs[m] * ldexp(1.0, -args.b * (args.lmax + 2));
         const bool read_c = args.beta.x != 0.0 || args.beta.y != 0.0;
 #pragma unroll
         for (int j = 0; j < kSkBN; ++j) {
           const int64_t n = n0 + j;
           if (n >= args.N) break;
           const double f = rsc * args.cs[n];
-          z val = zmul(args.alpha, make_double2(ar[j] * f, ai[j] * f));
+          z val = zmul(args.alpha, make_double2((double)ar[j] * f, (double)ai[j] * f));
           z* cp = args.transC ? args.C + n * args.ldc + m : args.C + m * args.ldc + n;
           if (read_c) val = zadd(val, zmul(args.beta, *cp));
           *cp = val;
