@@ -966,9 +966,22 @@ bool smallk_eligible(const SplitArgs& a) {
 // FP64 flush in the epilogue.
 void plan_ksplit(int64_t tiles, int kblocks, int& ksplits, int& kb_split) {
   ksplits = 1;
-  if (tiles < 152) {
-    int64_t want = (2 * 152 + tiles - 1) / tiles;
+  const int64_t sms = num_sms();
+  if (tiles < sms) {
+    int64_t want = (2 * sms + tiles - 1) / tiles;
     ksplits = (int)std::max<int64_t>(1, std::min<int64_t>(want, kblocks / 16));
+  } else if (tiles < 4 * sms) {
+    // a few waves of tiles: the split factor that best fills whole waves (a last wave of
+    // 1.5 waves leaves a third of the GPU idle), if it beats no split by more than 5%
+    double best = (double)tiles / (double)(((tiles + sms - 1) / sms) * sms);
+    for (int ks = 2; ks <= 8 && ks <= kblocks / 16; ++ks) {
+      const int64_t ctas = tiles * ks;
+      const double fill = (double)ctas / (double)(((ctas + sms - 1) / sms) * sms);
+      if (fill > best + 0.05) {
+        best = fill;
+        ksplits = ks;
+      }
+    }
   }
   kb_split = (kblocks + ksplits - 1) / ksplits;
   ksplits = (kblocks + kb_split - 1) / kb_split;
