@@ -94,7 +94,7 @@ typedef struct {
   double split_min_flops; /* split precision: contractions of at least this many flops (8 per complex
                              multiply-add) run on the tensor cores when a cost model of this GPU says
                              that is faster than FP64; the ladder always does; <= 0 sends every GEMM
-                             there (default 1e9) */
+                             there (default 1e8) */
   int df_block;       /* store_w = 0: virtual indices a per rebuilt block of <ab||cd> rows
                          (default 0 = as many as fit about 6 GB of (ac|bd)) */
   int autotune;       /* 1: at creation, time every FP64 GEMM of the plan in each tile shape and keep

@@ -1346,7 +1346,7 @@ void ccsd_default_opts(ccsd_opts* o) {
   o->store_w = 1;
   o->profile = 0;
   o->stream = nullptr;
-  o->split_min_flops = 1e9;
+  o->split_min_flops = 1e8;
   o->df_block = 0;
   o->autotune = 0;
   o->digit_bits = 0;

@@ -49,7 +49,7 @@ def test_default_opts(lib):
     from paper_2103_08473_gb300 import ccsd
     o = ccsd.default_opts()
     assert o.max_iter == 50 and o.diis_dim == 8 and o.diis_start == 2 and o.tol == 1e-10 and o.store_w == 1
-    assert o.split_min_flops == 1e9 and o.precision == 0
+    assert o.split_min_flops == 1e8 and o.precision == 0
     assert o.slices == 0 and o.digit_bits == 0 and o.complex_4m == 0
 
 

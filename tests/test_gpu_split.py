@@ -139,3 +139,22 @@ def test_short_k_kernel_matches_complex128(env, M, N, K, slices, conjA, conjB, b
                      transB=True, conjB=bool(conjB), bits=5, slices=slices)
     err = np.max(np.abs(dc.cpu().numpy() - want)) / np.max(np.abs(want))
     assert err < (2e-10 if slices == 8 else 6e-9), err
+
+
+def test_split_zgemm_k_split_filling_whole_waves(env):
+    """224 output tiles (1.5 waves of the GPU's SMs) and 32 K blocks: K is split in two so that
+    the CTAs fill whole waves; the partial products are summed in a fixed order."""
+    torch, ccsd = env
+    rng = np.random.default_rng(224)
+    M, N, K = 14 * 128, 16 * 128, 32 * 128
+    a = torch.from_numpy(_rand(rng, M, K)).cuda()
+    b = torch.from_numpy(_rand(rng, N, K)).cuda()
+    c0 = _rand(rng, M, N)
+    outs = []
+    for _ in range(2):
+        dc = torch.from_numpy(c0).cuda()
+        ccsd.split_zgemm(a, b, dc, 1.0, -0.5, transB=True, bits=5, slices=8)
+        outs.append(dc.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+    want = a.cpu().numpy() @ b.cpu().numpy().T - 0.5 * c0
+    assert np.max(np.abs(outs[0] - want)) / np.max(np.abs(want)) < 2e-10
