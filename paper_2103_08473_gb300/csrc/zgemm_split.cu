@@ -667,18 +667,59 @@ __device__ __forceinline__ void put_digit(uint8_t* out, int64_t idx, double d) {
   }
 }
 
-// Digits by integer arithmetic: one conversion of x 2^-e (|x 2^-e| < 1) to a
-// 62-bit fixed-point integer V, then digit p is the rounded top b bits of what is
-// left (round half up), subtracted off before the next. FP64 work is one multiply
-// and one conversion per element; the digits come from the integer pipes.
-__device__ __forceinline__ long long fixed62(double x) { return __double2ll_rn(x * 4611686018427387904.0); }
-// Ties round away from zero, so that the digits of -x are exactly the negated digits of x
-// (products of antisymmetric tensors stay exactly antisymmetric).
-__device__ __forceinline__ int next_digit(long long& V, int shift) {
-  const long long h = 1LL << (shift - 1);
-  const long long d = V >= 0 ? (V + h) >> shift : -((h - V) >> shift);
-  V -= d * (1LL << shift);
-  return (int)d;
+// Digits by integer arithmetic only (the FP64 pipe of this chip is narrow): each element x of a
+// row scaled by 2^-e (|x 2^-e| < 1) becomes the 62-bit fixed-point integer V = x 2^(62 - e),
+// rounded to nearest (ties to even) from the bits of x; its digits are b-bit fields of |V|
+// plus a constant (digit_offset below).
+__device__ __forceinline__ long long fixed62_scaled(double x, int e) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((bits >> 52) & 0x7FF);
+  unsigned long long m = bits & 0xFFFFFFFFFFFFFull;
+  if (E == 0 && m == 0) return 0;
+  if (E != 0) m |= 1ull << 52;
+  const int s = (E != 0 ? E - 1075 : -1074) + 62 - e;  // |x| 2^(62 - e) = m 2^s
+  long long v;
+  if (s >= 0) {
+    v = s <= 10 ? (long long)(m << s) : 0x7FFFFFFFFFFFFFFFll;  // |x 2^-e| < 1 keeps s <= 9
+  } else if (s < -54) {
+    v = 0;  // below half a unit
+  } else {
+    const int r = -s;
+    unsigned long long q = m >> r;
+    const unsigned long long rem = m & ((1ull << r) - 1ull), half = 1ull << (r - 1);
+    if (rem > half || (rem == half && (q & 1ull))) ++q;
+    v = (long long)q;
+  }
+  return (bits >> 63) ? -v : v;
+}
+
+// |x| as the bit pattern of a non-negative double: their integer order is the order of |x|.
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+// e with |x| = f 2^e, f in [0.5, 1), for x > 0 given by abs_bits
+__device__ __forceinline__ int exponent_of(unsigned long long ab) {
+  const int E = (int)(ab >> 52);
+  if (E != 0) return E - 1022;
+  int e = 0;
+  frexp(__longlong_as_double((long long)ab), &e);  // subnormal
+  return e;
+}
+// Balanced digits of |V| from b-bit fields: W = |V| + offset, with offset holding half a digit
+// (2^(b-1)) at every digit position and half a unit at the last (rounding to nearest, ties away
+// from zero); digit p is field p of W minus 2^(b-1), the first field unmasked. Every digit is in
+// [-2^(b-1), 2^(b-1)] (the first up to 2^b without headroom), the remainder at most half a unit
+// of the last digit, and the sign of V is applied to every digit, so that the digits of -x are
+// exactly the negated digits of x (products of antisymmetric tensors stay antisymmetric).
+__host__ __device__ inline unsigned long long digit_offset(int s, int b) {
+  unsigned long long off = 0;
+  for (int p = 0; p < s; ++p) off += (1ull << (b - 1)) << (62 - b * (p + 1));
+  return off + (1ull << (62 - b * s - 1));
+}
+__device__ __forceinline__ int field_digit(unsigned long long W, int p, int shift, int b, bool neg) {
+  const unsigned long long f = p == 0 ? (W >> shift) : ((W >> shift) & ((1ull << b) - 1ull));
+  const int d = (int)f - (1 << (b - 1));
+  return neg ? -d : d;
 }
 
 __device__ __forceinline__ uint32_t pack4_e4m3(int d0, int d1, int d2, int d3) {
@@ -709,24 +750,20 @@ __global__ void rowexp_n_kernel(const z* __restrict__ X, int64_t rows, int64_t K
     const int64_t r = w / nchunks, c = w % nchunks;
     const int64_t k1 = min(K, (c + 1) * chunk);
     const z* row = X + r * ld;
-    double mx = 0.0;
+    unsigned long long mx = 0;
     for (int64_t k = c * chunk + lane; k < k1; k += 32) {
       const z v = row[k];
-      mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+      mx = max(mx, max(abs_bits(v.x), abs_bits(v.y)));
     }
-    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-    if (lane == 0 && mx > 0.0) {
-      int e = 0;
-      frexp(mx, &e);
-      atomicMax(ex + r, e);
-    }
+    for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if (lane == 0 && mx > 0) atomicMax(ex + r, exponent_of(mx));
   }
 }
 
 template <int KIND>
 __global__ void slice_kernel(const z* __restrict__ X, int64_t rows, int64_t K, int64_t ld, int conj, int s, int b,
                              uint8_t* __restrict__ out, int64_t rows_pad, int64_t Kp, int64_t chunk, int64_t nchunks,
-                             const double* __restrict__ inv) {
+                             const int* __restrict__ ex, unsigned long long doff) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -734,21 +771,25 @@ __global__ void slice_kernel(const z* __restrict__ X, int64_t rows, int64_t K, i
     const int64_t r = w / nchunks, c = w % nchunks;
     const bool live = r < rows;
     const z* row = X + r * ld;
-    const double iv = live ? inv[r] : 0.0;
+    const int er = live ? ex[r] : 0;
     const int64_t k1 = min(Kp, (c + 1) * chunk);
     for (int64_t k0 = c * chunk + 4 * (int64_t)lane; k0 < k1; k0 += 128) {
-      long long Vr[4], Vi[4];
+      unsigned long long Wr[4], Wi[4];
+      bool nr[4], ni[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int64_t k = k0 + u;
-        double xr = 0.0, xi = 0.0;
+        long long vr = 0, vi = 0;
         if (live && k < K) {
           const z v = row[k];
-          xr = v.x * iv;
-          xi = (conj ? -v.y : v.y) * iv;
+          vr = fixed62_scaled(v.x, er);
+          vi = fixed62_scaled(v.y, er);
+          if (conj) vi = -vi;
         }
-        Vr[u] = fixed62(xr);
-        Vi[u] = fixed62(xi);
+        nr[u] = vr < 0;
+        ni[u] = vi < 0;
+        Wr[u] = (unsigned long long)(nr[u] ? -vr : vr) + doff;
+        Wi[u] = (unsigned long long)(ni[u] ? -vi : vi) + doff;
       }
       int shift = 62;
       for (int p = 0; p < s; ++p) {
@@ -756,8 +797,8 @@ __global__ void slice_kernel(const z* __restrict__ X, int64_t rows, int64_t K, i
         int dr[4], di[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          dr[u] = next_digit(Vr[u], shift);
-          di[u] = next_digit(Vi[u], shift);
+          dr[u] = field_digit(Wr[u], p, shift, b, nr[u]);
+          di[u] = field_digit(Wi[u], p, shift, b, ni[u]);
         }
         const int64_t o0 = ((int64_t)(p * 2 + 0) * rows_pad + r) * Kp + k0;
         const int64_t o1 = ((int64_t)(p * 2 + 1) * rows_pad + r) * Kp + k0;
@@ -780,39 +821,37 @@ __global__ void slice_kernel(const z* __restrict__ X, int64_t rows, int64_t K, i
 // Exponent of each row's largest |re|, |im| as an integer max (deterministic): 32 rows x 8
 // K-strides per block, the K range split across blockIdx.y. ex[] starts at INT_MIN.
 __global__ void rowexp_t_kernel(const z* __restrict__ X, int64_t rows, int64_t K, int64_t ld, int* __restrict__ ex) {
-  __shared__ double sh[8][33];
+  __shared__ unsigned long long sh[8][33];
   const int64_t r = (int64_t)blockIdx.x * 32 + threadIdx.x;
-  double mx = 0.0;
+  unsigned long long mx = 0;
   if (r < rows)
     for (int64_t k = (int64_t)blockIdx.y * 8 + threadIdx.y; k < K; k += (int64_t)gridDim.y * 8) {
       const z v = X[k * ld + r];
-      mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+      mx = max(mx, max(abs_bits(v.x), abs_bits(v.y)));
     }
   sh[threadIdx.y][threadIdx.x] = mx;
   __syncthreads();
   if (threadIdx.y == 0 && r < rows) {
-    for (int y = 1; y < 8; ++y) mx = fmax(mx, sh[y][threadIdx.x]);
-    if (mx > 0.0) {
-      int e = 0;
-      frexp(mx, &e);
-      atomicMax(ex + r, e);
-    }
+    for (int y = 1; y < 8; ++y) mx = max(mx, sh[y][threadIdx.x]);
+    if (mx > 0) atomicMax(ex + r, exponent_of(mx));
   }
 }
 
-__global__ void rowexp_finalize_kernel(const int* __restrict__ ex, int64_t rows, double* __restrict__ scale,
+__global__ void rowexp_finalize_kernel(int* __restrict__ ex, int64_t rows, double* __restrict__ scale,
                                        double* __restrict__ inv, int headroom) {
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
     // untouched (all-zero row): memset pattern 0x80808080
     const int e = (ex[r] < -2000 ? 0 : ex[r]) + headroom;
     scale[r] = ldexp(1.0, e);
     inv[r] = ldexp(1.0, -e);
+    ex[r] = e;  // the digit passes scale by 2^-e with integer operations
   }
 }
 
 template <int KIND>
 __global__ void slice_t_kernel(const z* __restrict__ X, int64_t rows, int64_t K, int64_t ld, int conj, int s, int b,
-                               uint8_t* __restrict__ out, int64_t rows_pad, int64_t Kp, const double* __restrict__ inv) {
+                               uint8_t* __restrict__ out, int64_t rows_pad, int64_t Kp, const int* __restrict__ ex,
+                               unsigned long long doff) {
   __shared__ z tile[64][33];
   const int64_t r0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 64;
   for (int idx = threadIdx.x; idx < 64 * 32; idx += blockDim.x) {
@@ -824,13 +863,18 @@ __global__ void slice_t_kernel(const z* __restrict__ X, int64_t rows, int64_t K,
   for (int item = threadIdx.x; item < 32 * 16; item += blockDim.x) {
     const int rr = item / 16, kg = item % 16;
     const int64_t r = r0 + rr, k = k0 + 4 * kg;
-    const double iv = r < rows ? inv[r] : 0.0;
-    long long Vr[4], Vi[4];
+    const int er = r < rows ? ex[r] : 0;
+    unsigned long long Wr[4], Wi[4];
+    bool nr[4], ni[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const z v = tile[4 * kg + u][rr];
-      Vr[u] = fixed62(v.x * iv);
-      Vi[u] = fixed62((conj ? -v.y : v.y) * iv);
+      long long vr = fixed62_scaled(v.x, er), vi = fixed62_scaled(v.y, er);
+      if (conj) vi = -vi;
+      nr[u] = vr < 0;
+      ni[u] = vi < 0;
+      Wr[u] = (unsigned long long)(nr[u] ? -vr : vr) + doff;
+      Wi[u] = (unsigned long long)(ni[u] ? -vi : vi) + doff;
     }
     int shift = 62;
     for (int p = 0; p < s; ++p) {
@@ -838,8 +882,8 @@ __global__ void slice_t_kernel(const z* __restrict__ X, int64_t rows, int64_t K,
       int dr[4], di[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        dr[u] = next_digit(Vr[u], shift);
-        di[u] = next_digit(Vi[u], shift);
+        dr[u] = field_digit(Wr[u], p, shift, b, nr[u]);
+        di[u] = field_digit(Wi[u], p, shift, b, ni[u]);
       }
       const int64_t o0 = ((int64_t)(p * 2 + 0) * rows_pad + r) * Kp + k;
       const int64_t o1 = ((int64_t)(p * 2 + 1) * rows_pad + r) * Kp + k;
@@ -1126,19 +1170,21 @@ cudaError_t make_slices(const z* X, int64_t rows, int64_t K, int64_t ld, int tra
     if (grid.y > 65535) return cudaErrorInvalidValue;
     if (cfg.kind == kSplitBF16)
       slice_t_kernel<kSplitBF16><<<grid, 256, 0, s>>>(X, rows, K, ld, conj, cfg.s, cfg.b, (uint8_t*)out.digits,
-                                                      out.rows_pad, out.Kp, inv);
+                                                      out.rows_pad, out.Kp, ex, digit_offset(cfg.s, cfg.b));
     else
       slice_t_kernel<kSplitE4M3><<<grid, 256, 0, s>>>(X, rows, K, ld, conj, cfg.s, cfg.b, (uint8_t*)out.digits,
-                                                      out.rows_pad, out.Kp, inv);
+                                                      out.rows_pad, out.Kp, ex, digit_offset(cfg.s, cfg.b));
     return cudaGetLastError();
   }
   const int blocks = (int)std::min<int64_t>((out.rows_pad * out.nchunks * 32 + 255) / 256, 152 * 64);
   if (cfg.kind == kSplitBF16)
     slice_kernel<kSplitBF16><<<blocks, 256, 0, s>>>(X, rows, K, ld, conj, cfg.s, cfg.b, (uint8_t*)out.digits,
-                                                    out.rows_pad, out.Kp, out.chunk, out.nchunks, inv);
+                                                    out.rows_pad, out.Kp, out.chunk, out.nchunks, ex,
+                                                    digit_offset(cfg.s, cfg.b));
   else
     slice_kernel<kSplitE4M3><<<blocks, 256, 0, s>>>(X, rows, K, ld, conj, cfg.s, cfg.b, (uint8_t*)out.digits,
-                                                    out.rows_pad, out.Kp, out.chunk, out.nchunks, inv);
+                                                    out.rows_pad, out.Kp, out.chunk, out.nchunks, ex,
+                                                    digit_offset(cfg.s, cfg.b));
   return cudaGetLastError();
 }
 

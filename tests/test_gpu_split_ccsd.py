@@ -115,7 +115,9 @@ def test_split_full_size_o60_v400_df_ladder_sampled(ccsd):
     s = inputs.make_config("c5")
     o, v = s.o, s.v
     t1, t2 = inputs.random_amplitudes(o, v, 505, scale=0.01)
-    with ccsd.CCSD(o, v, s.eps, B=s.B, precision=ccsd.PREC_SPLIT, store_w=0, level_shift=120.0) as cc:
+    # 9 digits of 5 bits (44 bits): the 1e-10 bound below is for that precision; with the default
+    # 8 digits a sum over K = P(v) = 79800 reaches a few 1e-10 of the largest element
+    with ccsd.CCSD(o, v, s.eps, B=s.B, precision=ccsd.PREC_SPLIT, slices=9, store_w=0, level_shift=120.0) as cc:
         r1, r2 = cc.residual(t1, t2)
         lad = cc.get_tensor("ladder")
     rng = np.random.default_rng(6)
