@@ -128,6 +128,22 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(ms: float, device: str = "cuda") -> float:
+    """The slowest rank's timed region (replicas: every rank runs the whole workload)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_seconds_per_iteration(ms: float, steps: int, world: int) -> float:
+    """N replicas each doing one iteration in the (slowest) time t: the job does N in t."""
+    return ms / 1e3 / steps / world
+
+
 def oracle_iteration_time(wl, steps: int = 1):
     """Time the CPU oracle on the same workload: integrals untimed, then `steps` full iterations."""
     import numpy as np
@@ -263,10 +279,7 @@ def run_ours(args, wl):
 
     sampler = ClockSampler(local)
     ms, opd, clocks = timed_iterations(ccmod, cc, stream, args.warmup, args.steps, barrier, sampler)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms)
     kernels = int(cc.query("kernels_per_iteration"))
     e_main = cc.energy()
     t_main = cc.get_amplitudes()
@@ -328,7 +341,7 @@ def run_ours(args, wl):
 
     if rank != 0:
         return
-    value = ms / 1e3 / args.steps / world
+    value = whole_job_seconds_per_iteration(ms, args.steps, world)
     peaks, peak_kind = load_peaks()
     lad_ms = opd.get("ladder:gemm")
     lad_fl = flops.ladder_flops_packed(o, v)
@@ -501,6 +514,46 @@ def residual_once(wl, precision, slices):
     print("residual evaluated", flush=True)
 
 
+def gemm_once(kind, M, N, K, reps=3):
+    """One complex GEMM C = A B^T (A: M x K, B: N x K, row-major, random) through the C ABI, timed
+    with CUDA events after two warm-up calls: a small case for profiling either GEMM kernel."""
+    import torch
+    from paper_2103_08473_gb300 import build, flops
+    from paper_2103_08473_gb300 import ccsd as ccmod
+
+    ccmod.load(build.build())
+    g = torch.Generator(device="cuda").manual_seed(7)
+    a = torch.randn((M, K), dtype=torch.complex128, device="cuda", generator=g)
+    b = torch.randn((N, K), dtype=torch.complex128, device="cuda", generator=g)
+    c = torch.zeros((M, N), dtype=torch.complex128, device="cuda")
+    stream = torch.cuda.Stream()
+
+    def run():
+        if kind == "split":
+            ccmod.split_zgemm(a, b, c, transB=True, bits=SPLIT_BITS, slices=SPLIT_SLICES, stream=stream)
+        else:
+            ccmod.zgemm(a, b, c, transB=True, stream=stream)
+
+    for _ in range(2):
+        run()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    conv = 8.0 * M * N * K
+    pairs = SPLIT_SLICES * (SPLIT_SLICES + 1) // 2
+    executed = conv * pairs if kind == "split" else conv * 0.75
+    print(json.dumps({"gemm": kind, "M": M, "N": N, "K": K, "ms": ms,
+                      "zgemm_equivalent_tflops": conv / ms / 1e9,
+                      "executed_tflops": executed / ms / 1e9,
+                      "executed": "e4m3 flops of 36 digit pairs x 4 real GEMMs (slicing included in the time)"
+                      if kind == "split" else "FP64 flops of 3 real GEMMs (3M)"}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -515,11 +568,17 @@ def main():
     ap.add_argument("--no-split-companion", action="store_true")
     ap.add_argument("--fp64-companion", type=int, default=0, metavar="N",
                     help="split runs: also run N iterations from the MP2 guess in split and in FP64 and compare")
+    ap.add_argument("--gemm-once", nargs=4, metavar=("KIND", "M", "N", "K"),
+                    help="one GEMM (KIND fp64 or split) of M x N x K for profiling, then exit")
     ap.add_argument("--complex-4m", action="store_true",
                     help="FP64 GEMMs with four real products per complex product instead of three")
     ap.add_argument("--residual-once", action="store_true",
                     help="create the context and evaluate one residual eagerly (for ncu captures), no timing")
     args = ap.parse_args()
+    if args.gemm_once:
+        kind, M, N, K = args.gemm_once[0], int(args.gemm_once[1]), int(args.gemm_once[2]), int(args.gemm_once[3])
+        gemm_once(kind, M, N, K)
+        return
     args.warmup = max(args.warmup, 3)  # timing rule: at least 3 untimed warm-up steps
     wl = WORKLOADS[args.config]
     if args.config == "c4":
