@@ -1086,7 +1086,7 @@ ccsd_status autotune_plan(ccsd_ctx* ctx, TuneCache& cache) {
   return st;
 }
 
-TuneCache* g_tune_cache = nullptr;  // shared by the systems of one batch while it is created
+thread_local TuneCache* g_tune_cache = nullptr;  // shared by the systems of one batch while it is created
 
 ccsd_status create_impl(int o, int v, const double* eps, const ccsd_z* fock, ccsd_int_kind kind, const ccsd_z* ints,
                         int naux, const ccsd_opts* opts, ccsd_ctx* ctx) {
