@@ -14,7 +14,7 @@ Printed JSON line: value = seconds per CCSD iteration (lower is better), the
 ladder GEMM roofline against the FP64 peak, the end-to-end time through host
 buffers, the oracle's CPU time per iteration, clocks during the timed region.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--config c2|c1]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--config o20v120|o10v30|o40v240|o60v400|batch64]
 """
 from __future__ import annotations
 
@@ -33,15 +33,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOADS = {
-    "c2": dict(o=20, v=120, naux=400, seed=2, level_shift=20.0, precision="fp64",
+    "o20v120": dict(o=20, v=120, naux=400, seed=2, level_shift=20.0, precision="fp64",
                name="ccsd_fp64_o20_v120_naux400_storedW"),
-    "c1": dict(o=10, v=30, naux=120, seed=1, level_shift=0.0, precision="fp64",
+    "o10v30": dict(o=10, v=30, naux=120, seed=1, level_shift=0.0, precision="fp64",
                name="ccsd_fp64_o10_v30_naux120"),
-    "c3": dict(o=40, v=240, naux=800, seed=3, level_shift=40.0, precision="split",
+    "o40v240": dict(o=40, v=240, naux=800, seed=3, level_shift=40.0, precision="split",
                name="ccsd_split_o40_v240_naux800_storedW"),
-    "c4": dict(nsys=64, seed=4, level_shift=0.0, precision="fp64", tol=1e-10,
+    "batch64": dict(nsys=64, seed=4, level_shift=0.0, precision="fp64", tol=1e-10,
                name="ccsd_batch64_o4-16_v16-64_naux3v"),
-    "c5": dict(o=60, v=400, naux=1200, seed=5, level_shift=120.0, precision="split", store_w=False,
+    "o60v400": dict(o=60, v=400, naux=1200, seed=5, level_shift=120.0, precision="split", store_w=False,
                name="ccsd_split_o60_v400_naux1200_dfW"),
 }
 SPLIT_SLICES = 8  # 5-bit e4m3 digits: 39 bits of each row scale
@@ -560,10 +560,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", choices=sorted(WORKLOADS), default="c2")
+    ap.add_argument("--config", choices=sorted(WORKLOADS), default="o20v120")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", choices=["fp64", "split"], default=None,
-                    help="default: fp64 for c1/c2, split for c3")
+                    help="default: fp64 for o10v30/o20v120/batch64, split for o40v240/o60v400")
     ap.add_argument("--slices", type=int, default=0, help=f"split digits per operand (default {SPLIT_SLICES})")
     ap.add_argument("--no-split-companion", action="store_true")
     ap.add_argument("--fp64-companion", type=int, default=0, metavar="N",
@@ -581,7 +581,7 @@ def main():
         return
     args.warmup = max(args.warmup, 3)  # timing rule: at least 3 untimed warm-up steps
     wl = WORKLOADS[args.config]
-    if args.config == "c4":
+    if args.config == "batch64":
         run_batch(args, wl)
     elif args.residual_once:
         residual_once(wl, args.precision or wl["precision"], args.slices or SPLIT_SLICES)

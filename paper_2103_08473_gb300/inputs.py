@@ -22,10 +22,10 @@ import numpy as np
 
 # Named workloads (o occupied spinors, v virtual spinors, naux DF functions, seed).
 CONFIGS = {
-    "c1": dict(o=10, v=30, naux=120, seed=1),
-    "c2": dict(o=20, v=120, naux=400, seed=2),
-    "c3": dict(o=40, v=240, naux=800, seed=3),
-    "c5": dict(o=60, v=400, naux=1200, seed=5),
+    "o10v30": dict(o=10, v=30, naux=120, seed=1),
+    "o20v120": dict(o=20, v=120, naux=400, seed=2),
+    "o40v240": dict(o=40, v=240, naux=800, seed=3),
+    "o60v400": dict(o=60, v=400, naux=1200, seed=5),
 }
 
 

@@ -79,7 +79,7 @@ def test_full_integral_input_matches_df_input(ccsd):
 
 
 def test_mp2_guess_and_energy(ccsd):
-    s = inputs.make_config("c1")
+    s = inputs.make_config("o10v30")
     f = R.fock_matrix(s.eps)
     V = R.integrals(s.B, s.o)
     t1, t2 = R.mp2_guess(f, V, s.o, s.v)
@@ -92,7 +92,7 @@ def test_mp2_guess_and_energy(ccsd):
 
 def test_c1_converges_to_oracle(ccsd):
     """10/30/120 workload: converge to 1e-10; |dE| <= 1e-10 Eh, amplitudes within 1e-9."""
-    s = inputs.make_config("c1")
+    s = inputs.make_config("o10v30")
     f = R.fock_matrix(s.eps)
     V = R.integrals(s.B, s.o)
     ref = R.solve(f, V, s.o, s.v, max_iter=60, tol=1e-10)
@@ -170,7 +170,7 @@ def test_device_buffers_through_torch(ccsd):
 def test_full_size_o20_v120_residual_and_iterations(ccsd):
     """The benchmarked workload (o20/v120/naux400, FP64, packed <ab||cd>): MP2 guess, the
     residual at it element by element, and two level-shifted iterations, against the oracle."""
-    s = inputs.make_config("c2")
+    s = inputs.make_config("o20v120")
     f = R.fock_matrix(s.eps)
     V = R.integrals(s.B, s.o)
     t1, t2 = R.mp2_guess(f, V, s.o, s.v, shift=20.0)

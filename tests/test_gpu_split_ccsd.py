@@ -42,7 +42,7 @@ def test_split_residual_matches_oracle(ccsd, o, v, naux, seed, slices, bits, tol
 
 
 def test_split_c1_converges_to_oracle_energy(ccsd):
-    s = inputs.make_config("c1")
+    s = inputs.make_config("o10v30")
     f = R.fock_matrix(s.eps)
     V = R.integrals(s.B, s.o)
     ref = R.solve(f, V, s.o, s.v, max_iter=60, tol=1e-10)
@@ -57,7 +57,7 @@ def test_split_c1_converges_to_oracle_energy(ccsd):
 
 def test_split_full_size_o20_v120_two_iterations(ccsd):
     """o20/v120/naux400 with the default routing (ladder, ring, H^{ak}_{ci} and C on the tensor cores)."""
-    s = inputs.make_config("c2")
+    s = inputs.make_config("o20v120")
     f = R.fock_matrix(s.eps)
     V = R.integrals(s.B, s.o)
     ref = R.solve(f, V, s.o, s.v, max_iter=2, tol=0.0, shift=20.0)
@@ -87,7 +87,7 @@ def test_split_df_ladder_without_stored_w(ccsd):
 def test_split_full_size_o40_v240_sampled_ladder(ccsd):
     """The o40/v240/naux800 split workload: sampled ladder elements against the oracle (computed
     element by element from B^Q), and antisymmetry of the residual at full size."""
-    s = inputs.make_config("c3")
+    s = inputs.make_config("o40v240")
     o, v = s.o, s.v
     t1, t2 = inputs.random_amplitudes(o, v, 303, scale=0.01)
     with ccsd.CCSD(o, v, s.eps, B=s.B, precision=ccsd.PREC_SPLIT, slices=11, level_shift=40.0) as cc:
@@ -112,7 +112,7 @@ def test_split_full_size_o60_v400_df_ladder_sampled(ccsd):
     """The o60/v400/naux1200 workload with <ab||cd> never stored (rebuilt from B^Q per block inside
     the ladder): sampled ladder elements against the oracle computed element by element from B^Q,
     and antisymmetry of the residual at full size."""
-    s = inputs.make_config("c5")
+    s = inputs.make_config("o60v400")
     o, v = s.o, s.v
     t1, t2 = inputs.random_amplitudes(o, v, 505, scale=0.01)
     # 9 digits of 5 bits (44 bits): the 1e-10 bound below is for that precision; with the default
