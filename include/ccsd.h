@@ -197,11 +197,14 @@ ccsd_status ccsd_zgemm(int precision, int transA, int conjA, int transB, int con
  *   C = alpha * opA(A) * opB(B) + beta * C   (complex double in and out, device pointers)
  * kind 0: e4m3 digits (kind::f8f6f4), bits <= 5; kind 1: bf16 digits (kind::f16), bits <= 8.
  * Each row of opA(A) and each column of opB(B) is scaled by a power of two and cut into
- * `slices` integer digits of `bits` bits (at 5 bits in e4m3 the scale leaves
- * one bit of headroom so that every digit is an integer the type holds exactly); digit products of equal weight are summed
- * exactly in FP32 tensor-memory accumulators over K ranges short enough to stay exact,
- * and combined in FP64. Error ~ 2^(-bits*slices) relative to the row/column scales
- * (2^(1-bits*slices) with headroom).
+ * `slices` integer digits of `bits` bits (at 5 bits in e4m3 the scale leaves one bit of
+ * headroom so that every digit is an integer the type holds exactly); the digits of -x are
+ * exactly the negated digits of x. Digit products of equal weight are summed exactly in
+ * FP32 tensor-memory accumulators over K ranges short enough to stay exact, and combined
+ * in FP64. A K of at most 4 blocks (512 e4m3, 256 bf16 elements) with at most 8 digits
+ * runs on a second kernel that keeps every weight in tensor memory and writes each output
+ * once. Error ~ 2^(-bits*slices) relative to the row/column scales (2^(1-bits*slices)
+ * with headroom).
  * workspace: device memory of at least ccsd_split_workspace(...) bytes. Synchronous on
  * `stream`. CCSD_ERR_TIMEOUT if a bounded device wait gave up.
  */
