@@ -268,6 +268,31 @@ def test_diis_reproduces_linear_extrapolation():
     np.testing.assert_allclose(t2, 0.5 * (t2a + t2b), atol=1e-16)
 
 
+@pytest.mark.parametrize("m,pushed", [(3, 3), (5, 5), (8, 8), (8, 11)])
+def test_diis_coefficients_minimise_the_error_norm(m, pushed):
+    """The DIIS coefficients are the minimiser of |sum_i c_i e_i|^2 over sum_i c_i = 1 (Pulay),
+    here found independently by least squares in the null space of the constraint; with more
+    vectors pushed than kept, the newest `max_vec` are the ones used."""
+    o, v = 3, 5
+    d = R.DIIS(m)
+    errs = []
+    for k in range(pushed):
+        t1, t2 = inputs.random_amplitudes(o, v, 100 + k)
+        e1, e2 = inputs.random_amplitudes(o, v, 200 + k, scale=0.3)
+        d.push(t1, t2, e1, e2)
+        iu, ju = np.triu_indices(o, 1)
+        au, bu = np.triu_indices(v, 1)
+        uniq = e2[iu, ju][:, au, bu].ravel()
+        errs.append(np.concatenate([e1.ravel(), uniq]))
+    E = np.array(errs[-m:]).T                      # columns: the kept error vectors
+    Er = np.vstack([E.real, E.imag])               # Re<e_i, e_j> = (Er^T Er)_ij
+    c0 = np.full(m, 1.0 / m)
+    null = np.linalg.svd(np.ones((1, m)))[2][1:].T  # basis of sum(c) = 0
+    y = np.linalg.lstsq(Er @ null, -Er @ c0, rcond=None)[0]
+    want = c0 + null @ y
+    np.testing.assert_allclose(d.coefficients(), want, rtol=1e-9, atol=1e-11)
+
+
 def test_sampled_ladder_elements_match_full_ladder():
     """The element-wise ladder used for full-size sampling agrees with the full einsum."""
     o, v, naux = 4, 11, 13
