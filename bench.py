@@ -215,9 +215,9 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
-def make_ctx(ccmod, s, wl, precision, slices, stream, profile=1, complex_4m=0):
+def make_ctx(ccmod, s, wl, precision, slices, stream, profile=1, complex_4m=0, method=0):
     kw = dict(level_shift=wl["level_shift"], tol=0.0, diis_dim=8, profile=profile, stream=stream.cuda_stream,
-              complex_4m=complex_4m, store_w=1 if wl.get("store_w", True) else 0)
+              complex_4m=complex_4m, store_w=1 if wl.get("store_w", True) else 0, method=method)
     if precision == "split":
         kw.update(precision=ccmod.PREC_SPLIT, slices=slices, digit_bits=SPLIT_BITS)
     return ccmod.CCSD(s.o, s.v, s.eps, B=s.B, **kw)
@@ -271,7 +271,8 @@ def run_ours(args, wl):
     slices = args.slices or SPLIT_SLICES
     stream = torch.cuda.Stream()  # a real stream: the library captures its iteration graph on it
     m4 = 1 if args.complex_4m else 0
-    cc = make_ctx(ccmod, s, wl, precision, slices, stream, complex_4m=m4)
+    meth = ccmod.METHOD_CCD if args.method == "ccd" else ccmod.METHOD_CCSD
+    cc = make_ctx(ccmod, s, wl, precision, slices, stream, complex_4m=m4, method=meth)
 
     def barrier():
         if world > 1:
@@ -398,7 +399,7 @@ def run_ours(args, wl):
             "data": "synthetic",
             "config": {"workload": wl["name"], "o": o, "v": v, "naux": wl["naux"], "precision": precision,
                        "slices": slices if precision == "split" else None,
-                       "complex_mult": "4M" if m4 else "3M",
+                       "complex_mult": "4M" if m4 else "3M", "method": args.method,
                        "store_w": wl.get("store_w", True), "level_shift": wl["level_shift"], "diis_dim": 8,
                        "l2": "inputs larger than L2 (packed <ab||cd> and vovv exceed 129 MB)",
                        "parallelism": "replicas" if world > 1 else "single"},
@@ -570,6 +571,8 @@ def main():
                     help="split runs: also run N iterations from the MP2 guess in split and in FP64 and compare")
     ap.add_argument("--gemm-once", nargs=4, metavar=("KIND", "M", "N", "K"),
                     help="one GEMM (KIND fp64 or split) of M x N x K for profiling, then exit")
+    ap.add_argument("--method", choices=["ccsd", "ccd"], default="ccsd",
+                    help="ccd: the doubles equations with t1 held at zero")
     ap.add_argument("--complex-4m", action="store_true",
                     help="FP64 GEMMs with four real products per complex product instead of three")
     ap.add_argument("--residual-once", action="store_true",

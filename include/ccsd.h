@@ -77,6 +77,13 @@ typedef enum {
   CCSD_PREC_SPLIT = 1 /* large contractions as split-precision tensor-core GEMMs, FP64 recombination */
 } ccsd_precision;
 
+typedef enum {
+  CCSD_METHOD_CCSD = 0, /* singles and doubles (Appendix A) */
+  CCSD_METHOD_CCD = 1   /* doubles only: the same doubles equations with t1 held at zero (its
+                           update is zeroed each iteration; the singles terms are evaluated and
+                           vanish); the variant the paper also times */
+} ccsd_method;
+
 typedef struct {
   int max_iter;       /* iteration cap for ccsd_iterate (default 50) */
   double tol;         /* convergence threshold on the update norm (default 1e-10) */
@@ -108,6 +115,7 @@ typedef struct {
   double split_budget; /* split precision: bytes of digits (both operands) one tensor-core GEMM call
                           may hold; larger GEMMs run in chunks of M, N and then K (default 0 = a
                           quarter of the free device memory at creation, 4 to 16 GB) */
+  int method;          /* ccsd_method (default CCSD_METHOD_CCSD) */
 } ccsd_opts;
 
 /* Fill opts with the defaults listed above. */

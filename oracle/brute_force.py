@@ -115,5 +115,19 @@ class Space:
         return float(np.real(self.ref @ H @ self.ref)), float(w[k])
 
 
+    def ci_doubles(self, f: np.ndarray, V: np.ndarray):
+        """CI in the reference and its double excitations only: (E_ref, eigenvalue of the state
+        with the largest reference weight). For two electrons this is CCD (T2 squared vanishes)."""
+        h = core_hamiltonian(f, V, self.o)
+        H = hamiltonian(h, V, self.E)
+        occ = set(range(self.o))
+        keep = [k for k, d in enumerate(self.dets) if self.o - len(occ.intersection(d)) in (0, 2)]
+        Hs = H[np.ix_(keep, keep)]
+        ref = self.ref[keep]
+        w, U = np.linalg.eigh(Hs)
+        k = int(np.argmax(np.abs(ref @ U)))
+        return float(np.real(self.ref @ H @ self.ref)), float(w[k])
+
+
 def n_determinants(o: int, v: int) -> int:
     return math.comb(o + v, o)

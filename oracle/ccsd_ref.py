@@ -307,8 +307,9 @@ class DIIS:
 
 def solve(f: np.ndarray, V: dict, o: int, v: int, max_iter: int = 50, tol: float = 1e-10,
           diis_dim: int = 8, diis_start: int = 2, shift: float = 0.0, t_init=None,
-          callback=None):
-    """CCSD iterations from the MP2 guess (or ``t_init``).
+          callback=None, method: str = "ccsd"):
+    """CCSD iterations from the MP2 guess (or ``t_init``); method="ccd" holds t1 at zero (CCD:
+    the doubles equations of Appendix A with T1 = 0, the variant the paper also times).
 
     Each iteration: S = residual(t); d = S/D; norm = max|d|; t <- t + d; then, if DIIS is on
     and the iteration number is >= diis_start with >= 2 stored vectors, t <- sum_i c_i t_i.
@@ -319,6 +320,10 @@ def solve(f: np.ndarray, V: dict, o: int, v: int, max_iter: int = 50, tol: float
         t1, t2 = mp2_guess(f, V, o, v, shift)
     else:
         t1, t2 = (np.array(x, dtype=np.complex128) for x in t_init)
+    if method == "ccd":
+        t1 = np.zeros_like(t1)
+    elif method != "ccsd":
+        raise ValueError("method must be 'ccsd' or 'ccd'")
     diis = DIIS(diis_dim) if diis_dim > 0 else None
     norm = np.inf
     it = 0
@@ -326,6 +331,8 @@ def solve(f: np.ndarray, V: dict, o: int, v: int, max_iter: int = 50, tol: float
     for it in range(1, max_iter + 1):
         S1, S2 = residual(f, V, t1, t2)
         d1, d2 = S1 / D1, S2 / D2
+        if method == "ccd":
+            d1 = np.zeros_like(d1)
         norm = max(np.max(np.abs(d1), initial=0.0), np.max(np.abs(d2), initial=0.0))
         t1, t2 = t1 + d1, t2 + d2
         if diis is not None:

@@ -20,6 +20,7 @@ STATUS = {0: "CCSD_OK", 1: "CCSD_ERR_ARG", 2: "CCSD_ERR_OOM", 3: "CCSD_ERR_CUDA"
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NOT_CONVERGED, ERR_DIVERGED, ERR_TIMEOUT, ERR_UNSUPPORTED = range(8)
 INT_DF, INT_FULL = 0, 1
 PREC_FP64, PREC_SPLIT = 0, 1
+METHOD_CCSD, METHOD_CCD = 0, 1
 
 
 class ccsd_z(C.Structure):
@@ -31,7 +32,8 @@ class ccsd_opts(C.Structure):
                 ("diis_start", C.c_int), ("level_shift", C.c_double), ("precision", C.c_int),
                 ("slices", C.c_int), ("store_w", C.c_int), ("profile", C.c_int), ("stream", C.c_void_p),
                 ("split_min_flops", C.c_double), ("df_block", C.c_int), ("autotune", C.c_int),
-                ("digit_bits", C.c_int), ("complex_4m", C.c_int), ("split_budget", C.c_double)]
+                ("digit_bits", C.c_int), ("complex_4m", C.c_int), ("split_budget", C.c_double),
+                ("method", C.c_int)]
 
 
 class CCSDError(RuntimeError):

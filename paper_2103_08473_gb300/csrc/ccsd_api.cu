@@ -1004,6 +1004,9 @@ cudaError_t iteration_ops(ccsd_ctx* ctx, bool timed) {
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(ctx->t2_prev, ctx->t2, n2 * sizeof(z), cudaMemcpyDeviceToDevice, ctx->stream);
   if (e == cudaSuccess) e = run_ops(ctx, timed);
+  // CCD: the singles equations are not solved, t1 stays zero (its update is zeroed)
+  if (e == cudaSuccess && ctx->opts.method == CCSD_METHOD_CCD)
+    e = cudaMemsetAsync(ctx->S1, 0, (size_t)n1 * sizeof(z), ctx->stream);
   if (e == cudaSuccess)
     e = denom_update(ctx->t1, ctx->t2, ctx->S1, ctx->S2, ctx->dvec, ctx->o, ctx->v, ctx->opts.level_shift,
                      ctx->upd_partials, ctx->stream);
@@ -1103,6 +1106,8 @@ ccsd_status create_impl(int o, int v, const double* eps, const ccsd_z* fock, ccs
   if (opts) ctx->opts = *opts;
   else ccsd_default_opts(&ctx->opts);
   if (ctx->opts.diis_dim < 0 || ctx->opts.diis_dim > 16) return set_err(ctx, CCSD_ERR_ARG, "diis_dim must be in [0, 16]");
+  if (ctx->opts.method != CCSD_METHOD_CCSD && ctx->opts.method != CCSD_METHOD_CCD)
+    return set_err(ctx, CCSD_ERR_ARG, "unknown method");
   if (ctx->opts.precision != CCSD_PREC_FP64 && ctx->opts.precision != CCSD_PREC_SPLIT)
     return set_err(ctx, CCSD_ERR_ARG, "unknown precision mode");
   if (ctx->opts.precision == CCSD_PREC_SPLIT) {
@@ -1303,8 +1308,9 @@ ccsd_status create_impl(int o, int v, const double* eps, const ccsd_z* fock, ccs
     CS(autotune_plan(ctx, g_tune_cache ? *g_tune_cache : local));
   }
 
-  // MP2 guess: one denominator update from t = 0
+  // MP2 guess: one denominator update from t = 0 (CCD: the singles stay zero)
   CK(run_ops(ctx, false));
+  if (ctx->opts.method == CCSD_METHOD_CCD) CK(cudaMemsetAsync(ctx->S1, 0, (size_t)ov * sizeof(z), ctx->stream));
   CK(denom_update(ctx->t1, ctx->t2, ctx->S1, ctx->S2, ctx->dvec, o, v, ctx->opts.level_shift, ctx->upd_partials,
                   ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -1352,6 +1358,7 @@ void ccsd_default_opts(ccsd_opts* o) {
   o->digit_bits = 0;
   o->complex_4m = 0;
   o->split_budget = 0.0;
+  o->method = CCSD_METHOD_CCSD;
 }
 
 ccsd_status ccsd_create(int o, int v, const double* eps, const ccsd_z* fock, ccsd_int_kind kind, const ccsd_z* ints,

@@ -50,7 +50,7 @@ def test_default_opts(lib):
     o = ccsd.default_opts()
     assert o.max_iter == 50 and o.diis_dim == 8 and o.diis_start == 2 and o.tol == 1e-10 and o.store_w == 1
     assert o.split_min_flops == 1e8 and o.precision == 0
-    assert o.slices == 0 and o.digit_bits == 0 and o.complex_4m == 0
+    assert o.slices == 0 and o.digit_bits == 0 and o.complex_4m == 0 and o.method == ccsd.METHOD_CCSD
 
 
 def _create(lib, o, v, eps, B, naux, opts=None):
@@ -62,7 +62,7 @@ def _create(lib, o, v, eps, B, naux, opts=None):
     return st, h
 
 
-@pytest.mark.parametrize("case", ["o0", "v0", "naux0", "null_eps", "null_ints", "nonhermitian", "diis17", "bits6", "bits_x_slices"])
+@pytest.mark.parametrize("case", ["o0", "v0", "naux0", "null_eps", "null_ints", "nonhermitian", "diis17", "bits6", "bits_x_slices", "method2"])
 def test_create_rejects_bad_arguments(lib, case):
     from paper_2103_08473_gb300 import ccsd, inputs
     s = inputs.make_system(2, 3, 4, seed=1)
@@ -84,6 +84,8 @@ def test_create_rejects_bad_arguments(lib, case):
         opts = ccsd.default_opts(diis_dim=17)
     elif case == "bits6":  # e4m3 holds every integer digit only up to 16: at most 5 bits
         opts = ccsd.default_opts(precision=ccsd.PREC_SPLIT, digit_bits=6)
+    elif case == "method2":
+        opts = ccsd.default_opts(method=2)
     elif case == "bits_x_slices":
         opts = ccsd.default_opts(precision=ccsd.PREC_SPLIT, digit_bits=5, slices=12)
     st, h = _create(lib, o, v, eps, B, naux, opts)

@@ -226,3 +226,23 @@ def test_degenerate_shapes_match_oracle(ccsd, o, v, precision):
         st, it, nrm = cc.iterate(3)
         assert it == 3
         assert abs(cc.energy() - ref["energy"]) < 1e-9
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+def test_ccd_tracks_oracle(ccsd, precision):
+    """CCD (method = CCD): t1 stays exactly zero, and fixed iterations and the energy follow the
+    oracle's CCD (the doubles equations with T1 = 0)."""
+    o, v, naux = 6, 21, 40
+    s, f, fock = _sys(o, v, naux, 109, 0.05, 0.01)
+    V = R.integrals(s.B, o)
+    ref = R.solve(f, V, o, v, max_iter=5, tol=0.0, method="ccd")
+    kw = dict(precision=ccsd.PREC_SPLIT, split_min_flops=0.0) if precision == "split" else {}
+    tol = 1e-9 if precision == "split" else 1e-11
+    with ccsd.CCSD(o, v, s.eps, B=s.B, fock=fock, tol=0.0, method=ccsd.METHOD_CCD, **kw) as cc:
+        st, it, nrm = cc.iterate(5)
+        e = cc.energy()
+        t1, t2 = cc.get_amplitudes()
+    assert it == 5
+    assert np.max(np.abs(t1)) == 0.0
+    assert abs(e - ref["energy"]) < tol
+    assert np.max(np.abs(t2 - ref["t2"])) < 10 * tol

@@ -127,6 +127,21 @@ def test_two_electron_ccsd_equals_full_ci(v, naux, seed, scale):
     assert abs(res["energy"] - (e_fci - e_ref)) < 1e-10
 
 
+@pytest.mark.parametrize("v,naux,seed,fock_offdiag", [(6, 8, 61, 0.0), (8, 10, 62, 0.04)])
+def test_two_electron_ccd_equals_doubles_ci(v, naux, seed, fock_offdiag):
+    """CCD (t1 held at zero) for two electrons: T2 squared vanishes, so its energy is the
+    lowest-lying root of H in the reference plus doubles space (explicit diagonalisation)."""
+    o = 2
+    s, f, Vf, V = _system(o, v, naux, seed, scale=0.3, fock_offdiag=fock_offdiag)
+    res = R.solve(f, V, o, v, max_iter=300, tol=1e-12, method="ccd")
+    assert res["converged"] and np.max(np.abs(res["t1"])) == 0.0
+    e_ref, e_cid = BF.Space(o, v).ci_doubles(f, Vf)
+    assert abs(res["energy"] - (e_cid - e_ref)) < 1e-10
+    # the singles matter: CCSD (= full CI for two electrons) differs
+    e_ccsd = R.solve(f, V, o, v, max_iter=300, tol=1e-12)["energy"]
+    assert abs(e_ccsd - res["energy"]) > 1e-8
+
+
 def test_two_electron_full_ci_with_nondiagonal_fock():
     o, v = 2, 8
     s, f, Vf, V = _system(o, v, 10, 24, scale=0.25, fock_offdiag=0.05)
