@@ -1,4 +1,4 @@
-"""Brute force in the N-electron determinant space: the pin for the CCSD oracle.
+"""Brute force in the N-electron determinant space: the pin for the CCSD and triples oracles.
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/ccsd_ref.py``).
 
@@ -7,7 +7,9 @@ second-quantised Hamiltonian of Eq. Hamiltonian as an explicit matrix over all
 C(n, N) Slater determinants, forms the similarity-transformed Hamiltonian
 H_bar = exp(-T) H exp(T) of Eq. CCSD with explicit operator matrices for T1 and T2
 (Eq. t_amp, with the 1/4 normalisation of T2), and projects on the reference, the
-singles and the doubles. It also diagonalises H (full CI).
+singles and the doubles. It also diagonalises H (full CI), projects on the
+triple excitations, and gives the Moller-Plesset perturbed wavefunctions through
+second order (the pins of the triples corrections).
 
 Conventions: spinors 0..n-1 with the N = o lowest occupied in the reference;
 a determinant is a sorted tuple of occupied spinors; a+_p acting on a determinant
@@ -127,6 +129,40 @@ class Space:
         w, U = np.linalg.eigh(Hs)
         k = int(np.argmax(np.abs(ref @ U)))
         return float(np.real(self.ref @ H @ self.ref)), float(w[k])
+
+
+    def triples(self) -> np.ndarray:
+        """|ijk abc> = E_ai E_bj E_ck |0> for all labels, as an array [i, j, k, a, b, c, x]."""
+        Evo = self.E[self.o:, :self.o]
+        s1 = np.einsum("ckxy,y->ckx", Evo, self.ref)
+        s2 = np.einsum("bjxz,ckz->jkbcx", Evo, s1, optimize=True)
+        return np.einsum("aixz,jkbcz->ijkabcx", Evo, s2, optimize=True)
+
+    def excitation_level(self) -> np.ndarray:
+        """Number of virtual spinors occupied in each determinant."""
+        return np.array([sum(1 for p in d if p >= self.o) for d in self.dets])
+
+    def moller_plesset(self, f: np.ndarray, V: np.ndarray):
+        """Rayleigh-Schrodinger perturbation theory with H0 = sum of the diagonal Fock energies
+        of each determinant's spinors (f must be diagonal, so that H0 has the reference as
+        eigenvector and the singles do not couple at first order).
+
+        Returns (H, H - H0, psi1, psi2) in intermediate normalisation:
+        (E0 - H0) psi1 = Q V |0>, (E0 - H0) psi2 = Q (V - E1) psi1, Q = 1 - |0><0|."""
+        assert np.allclose(f, np.diag(np.diag(f))), "Moller-Plesset partitioning needs a diagonal f"
+        H = hamiltonian(core_hamiltonian(f, V, self.o), V, self.E)
+        e = np.real(np.diag(f))
+        h0 = np.array([sum(e[p] for p in d) for d in self.dets])
+        W = H - np.diag(h0)
+        r = self.index[tuple(range(self.o))]
+        gap = h0[r] - h0
+        gap[r] = 1.0
+        q = np.ones(len(self.dets))
+        q[r] = 0.0
+        psi1 = q * (W @ self.ref) / gap
+        e1 = self.ref @ W @ self.ref
+        psi2 = q * ((W - e1 * np.eye(len(self.dets))) @ psi1) / gap
+        return H, W, psi1, psi2
 
 
 def n_determinants(o: int, v: int) -> int:
