@@ -153,6 +153,37 @@ ccsd_status ccsd_iterate(ccsd_ctx* ctx, int max_iter, int* iters_done, double* r
 /* Energy of the current amplitudes: sum_ia f_ia t^a_i + 1/4 sum <ij||ab> tau^{ab}_{ij}. */
 ccsd_status ccsd_energy(ccsd_ctx* ctx, ccsd_z* e);
 
+/*
+ * Perturbative triples corrections at the current amplitudes (normally converged),
+ * following the appendix "Working equations for perturbative Triples" (Eqs. W-term,
+ * Z-term, Y-term, 4order-term, 5order-term). The outputs are real and in Hartree, and each
+ * is a correction to add to the CCSD energy:
+ *   out[0] = E(+T)  = -sum |X|^2 / D                        (fourth order)
+ *   out[1] = E((T)) = E(+T) - sum Re(X Z) / D               (fifth order)
+ *   out[2] = E(-T)  = E(+T) + sum Re(X conj(Y))             (alternative fifth order)
+ * The sums run over i<j<k and a<b<c, which equals the appendix's full sums divided by 36.
+ *   - X is W^{abc} + W^{bca} + W^{cab}, the connected triples <Phi^{abc}_{ijk}| V T2 |Phi_0>.
+ *     The integrals of W are read as <ab||ie> and <am||jk>, the Hermitian partners of the
+ *     printed <ie||ab> and <jk||am>.
+ *   - Z is the conjugate of <Phi^{abc}_{ijk}| V T1 + F T2 |Phi_0>.
+ *   - Y is the triples part of exp(T1 + T2)|Phi_0>.
+ *   - D = e_a + e_b + e_c - e_i - e_j - e_k, over the real diagonal of the Fock matrix
+ *     (no level shift).
+ * The arithmetic is FP64 throughout. W comes from batched complex GEMMs on the FP64 tensor
+ * path, one occupied pair i<j at a time, with up to max_batch consecutive k > j per batch.
+ *   max_batch <= 0 sizes the batch to a quarter of the free device memory, at most 8 GB.
+ *   Each triple of a batch needs 2 * v * v(v-1)/2 complex elements of workspace.
+ * out: host, 3 doubles.
+ * pair_terms: NULL, or host with o*o*3 doubles. pair_terms[(i*o + j)*3 + m] receives the
+ * contribution of the triples (i, j, k > j) to out[m]; it is zero unless i < j. out[m] is
+ * the sum of these contributions in pair order.
+ * The workspace is allocated by this call and freed before it returns. Synchronises the
+ * stream. The result is reproducible run to run.
+ * Errors: CCSD_ERR_ARG for a NULL out or a negative max_batch; CCSD_ERR_OOM when the
+ * workspace for one triple does not fit.
+ */
+ccsd_status ccsd_triples(ccsd_ctx* ctx, int max_batch, double* out, double* pair_terms);
+
 /* Copy the current amplitudes out / in (checkpoint and resume). Setting resets DIIS. */
 ccsd_status ccsd_get_amplitudes(ccsd_ctx* ctx, ccsd_z* t1, ccsd_z* t2, int on_device);
 ccsd_status ccsd_set_amplitudes(ccsd_ctx* ctx, const ccsd_z* t1, const ccsd_z* t2, int on_device);

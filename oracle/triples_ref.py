@@ -135,3 +135,42 @@ def corrections(f: np.ndarray, V: dict, t1: np.ndarray, t2: np.ndarray) -> dict:
     Ys = cyclic_virtual(y_intermediate(t1, t2))
     e5m = np.sum(np.real(X * np.conj(Ys))) / 36.0                                # Eq. for E(-T)
     return {"+T": float(e4), "(T)": float(e4 + e5), "-T": float(e4 + e5m)}
+
+
+def pair_contributions(f: np.ndarray, V: dict, t1: np.ndarray, t2: np.ndarray, i: int, j: int) -> np.ndarray:
+    """Contributions of the triples (i, j, k), k > j, to [E(+T), E((T)), E(-T)] (i < j).
+
+    The same equations evaluated at fixed occupied labels: W, Z and Y of one triple by the
+    printed terms with i, j, k held fixed, summed over the unique a < b < c (the full sum over
+    the virtual labels / 6, by antisymmetry). Needs only the blocks "oovv", "ooov" and "vovv"
+    of V, so it runs at sizes where <ab||cd> cannot be formed.
+    """
+    o, v = t1.shape
+    vvov, vooo, _ = _blocks(V, o)
+    oovv, fov = V["oovv"], f[:o, o:]
+    e = np.real(np.diag(f))
+    es = np.einsum
+    out = np.zeros(3)
+    for k in range(j + 1, o):
+        W = (es("abe,ec->abc", vvov[:, :, i, :], t2[j, k]) + es("abe,ec->abc", vvov[:, :, j, :], t2[k, i])
+             + es("abe,ec->abc", vvov[:, :, k, :], t2[i, j])
+             + es("am,mbc->abc", vooo[:, :, i, j], t2[k]) + es("am,mbc->abc", vooo[:, :, j, k], t2[i])
+             + es("am,mbc->abc", vooo[:, :, k, i], t2[j]))
+        X = W + W.transpose(2, 0, 1) + W.transpose(1, 2, 0)              # W^{abc} + W^{bca} + W^{cab}
+        Z = np.zeros((v, v, v), complex)
+        Y = np.zeros((v, v, v), complex)
+        for p, q, r in ((i, j, k), (j, k, i), (k, i, j)):
+            Z += es("ab,c->abc", oovv[p, q], np.conj(t1[r])) + es("ab,c->abc", np.conj(t2[p, q]), fov[r])
+            Y += es("ab,c->abc", t2[p, q], t1[r])
+        Zs = Z + Z.transpose(2, 0, 1) + Z.transpose(1, 2, 0)
+        rows = t1[[i, j, k]]                 # 3 x v; the six signed orderings of Eq. Y-term (their
+                                             # cyclic virtual sum is 3 times the same determinant)
+        det = (es("a,b,c->abc", rows[0], rows[1], rows[2]) - es("a,b,c->abc", rows[1], rows[0], rows[2])
+               + es("a,b,c->abc", rows[1], rows[2], rows[0]) - es("a,b,c->abc", rows[2], rows[1], rows[0])
+               + es("a,b,c->abc", rows[2], rows[0], rows[1]) - es("a,b,c->abc", rows[0], rows[2], rows[1]))
+        Ys = det + Y + Y.transpose(2, 0, 1) + Y.transpose(1, 2, 0)
+        ev = e[o:]
+        D = ev[:, None, None] + ev[None, :, None] + ev[None, None, :] - e[i] - e[j] - e[k]
+        e4 = -np.sum(np.abs(X) ** 2 / D) / 6.0
+        out += [e4, e4 - np.sum(np.real(X * Zs) / D) / 6.0, e4 + np.sum(np.real(X * np.conj(Ys))) / 6.0]
+    return out

@@ -52,6 +52,7 @@ SIGNATURES = [
     ("ccsd_residual", C.c_int, [_P, _P, _P, _P, _P, C.c_int]),
     ("ccsd_iterate", C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     ("ccsd_energy", C.c_int, [_P, C.POINTER(ccsd_z)]),
+    ("ccsd_triples", C.c_int, [_P, C.c_int, _P, _P]),
     ("ccsd_get_amplitudes", C.c_int, [_P, _P, _P, C.c_int]),
     ("ccsd_set_amplitudes", C.c_int, [_P, _P, _P, C.c_int]),
     ("ccsd_get_tensor", C.c_int, [_P, C.c_char_p, _P, C.c_size_t, C.c_int]),
@@ -225,6 +226,16 @@ class CCSD:
         e = ccsd_z()
         self._check(self._lib.ccsd_energy(self._h, C.byref(e)))
         return complex(e.re, e.im)
+
+    def triples(self, max_batch=0, pair_terms=False):
+        """Triples corrections {"+T", "(T)", "-T"} at the current amplitudes; with pair_terms,
+        also the (o, o, 3) array of each pair's contributions."""
+        out = np.zeros(3)
+        pt = np.zeros((self.o, self.o, 3)) if pair_terms else None
+        self._check(self._lib.ccsd_triples(self._h, int(max_batch), out.ctypes.data_as(C.c_void_p),
+                                           pt.ctypes.data_as(C.c_void_p) if pt is not None else None))
+        e = {"+T": float(out[0]), "(T)": float(out[1]), "-T": float(out[2])}
+        return (e, pt) if pair_terms else e
 
     def get_amplitudes(self, out=None):
         s1, s2 = self.shapes

@@ -17,6 +17,7 @@
 #include "ops.h"
 #include "plan.h"
 #include "split.h"
+#include "triples.h"
 #include "zgemm.h"
 
 using namespace ccsd;
@@ -1473,6 +1474,76 @@ ccsd_status ccsd_energy(ccsd_ctx* ctx, ccsd_z* e) {
   CK(cudaStreamSynchronize(ctx->stream));
   e->re = ctx->e_host->x;
   e->im = ctx->e_host->y;
+  return CCSD_OK;
+}
+
+ccsd_status ccsd_triples(ccsd_ctx* ctx, int max_batch, double* out, double* pair_terms) {
+  if (!ctx) return CCSD_ERR_ARG;
+  if (!out) return set_err(ctx, CCSD_ERR_ARG, "out must not be NULL");
+  if (max_batch < 0) return set_err(ctx, CCSD_ERR_ARG, "max_batch must be >= 0");
+  const int o = ctx->o, v = ctx->v;
+  std::vector<double> acc((size_t)o * o * 3, 0.0);
+  if (o >= 3 && v >= 3) {
+    const int64_t per = triples_batch_elems(v) * (int64_t)sizeof(z);
+    int nb = max_batch;
+    if (nb == 0) {
+      size_t fr = 0, tot = 0;
+      CK(cudaMemGetInfo(&fr, &tot));
+      const int64_t budget = std::min<int64_t>((int64_t)(fr / 4), int64_t(8) << 30);
+      nb = (int)std::max<int64_t>(1, std::min<int64_t>(o - 2, budget / per));
+    }
+    nb = std::min(nb, o - 2);
+    // workspace of this call only, freed on every return path
+    struct Scratch {
+      std::vector<void*> p;
+      ~Scratch() {
+        for (void* q : p) cudaFree(q);
+      }
+      bool get(void** out, size_t bytes) {
+        if (cudaMalloc(out, bytes) != cudaSuccess) {
+          cudaGetLastError();
+          return false;
+        }
+        p.push_back(*out);
+        return true;
+      }
+    } mem;
+    TriplesArgs a;
+    a.o = o;
+    a.v = v;
+    a.t1 = ctx->t1;
+    a.t2 = ctx->t2;
+    a.oovv = ctx->oovv;
+    a.ooov = ctx->ooov;
+    a.vovv_pk = ctx->vovv_pk;
+    a.fov = ctx->fov;
+    a.d = ctx->dvec;
+    a.max_batch = nb;
+    void *t2pk = nullptr, *work = nullptr, *partials = nullptr, *pacc = nullptr;
+    if (!mem.get(&t2pk, sizeof(z) * (size_t)o * o * ctx->Pv) || !mem.get(&work, (size_t)per * nb) ||
+        !mem.get(&partials, sizeof(double) * (size_t)triples_partials(a)) ||
+        !mem.get(&pacc, sizeof(double) * acc.size()))
+      return set_err(ctx, CCSD_ERR_OOM, "triples workspace");
+    a.t2pk = (z*)t2pk;
+    a.work = (z*)work;
+    a.partials = (double*)partials;
+    a.pair_acc = (double*)pacc;
+    CK(cudaMemsetAsync(pacc, 0, sizeof(double) * acc.size(), ctx->stream));
+    CK(triples_eval(a, ctx->stream));
+    CK(cudaMemcpyAsync(acc.data(), pacc, sizeof(double) * acc.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  // per-pair contributions to the three energies, and their sums in pair order
+  out[0] = out[1] = out[2] = 0.0;
+  for (int i = 0; i < o; ++i)
+    for (int j = 0; j < o; ++j) {
+      const double* s = &acc[((size_t)i * o + j) * 3];
+      const double c[3] = {-s[0], -s[0] - s[1], -s[0] + s[2]};
+      for (int m = 0; m < 3; ++m) {
+        out[m] += c[m];
+        if (pair_terms) pair_terms[((size_t)i * o + j) * 3 + m] = c[m];
+      }
+    }
   return CCSD_OK;
 }
 

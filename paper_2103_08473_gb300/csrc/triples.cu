@@ -1,0 +1,268 @@
+// Perturbative triples corrections E(+T), E((T)), E(-T) at converged CCSD amplitudes
+// (appendix "Working equations for perturbative Triples", Eqs. W-term, Z-term, Y-term,
+// 4order-term and 5order-term).
+//
+// Readings (the same as the CPU oracle's): the integrals of W are the Hermitian partners
+// <ab||ie> and <am||jk> of the printed <ie||ab> and <jk||am>; D = e_a + e_b + e_c - e_i - e_j - e_k
+// over the real diagonal of f; E(+T) = -sum |X|^2 / D; the (T) term is -sum Re(X Z) / D with
+// Z = conj(<Phi_3| V T1 + F T2 |Phi_0>); the -T term is +sum Re(X conj(Y)). X is the cyclic sum of
+// W over the virtual labels. Sums run over unique i<j<k, a<b<c (the appendix's full sums / 36).
+//
+// Work plan. For every occupied pair i<j the triples (i, j, k), k > j, are taken in batches of
+// consecutive k. For a batch, six batched FP64 GEMMs form W in two antisymmetry-packed parts:
+//   E[t][P(a,b)][c] = sum_{(L;pq) in (i;jk),(j;ki),(k;ij)} sum_e <ab||Le> t^{ec}_{pq}
+//                    (rows of the packed <eL||ab>, conjugated, times t2[p][q] as [e][c]),
+//   M[t][a][P(b,c)] = sum_{(pq;L) in (ij;k),(jk;i),(ki;j)} sum_m <am||pq> t^{bc}_{Lm}
+//                    (<pq||ma> conjugated, times the pair-packed t2[L] as [m][P(b,c)]).
+// The e-terms are antisymmetric in (a,b) and the m-terms in (b,c), so each part is stored packed
+// and the GEMMs do half the work of the full contractions. One fused kernel then reads the six
+// elements that make X at each unique (a<b<c), builds Z, Y and D on the fly from t1, t2, <ij||ab>,
+// f_ov and the orbital energies, and reduces the three energy terms. Per-block partial sums go to a
+// fixed slot and are added to the pair's accumulator in a fixed order, so the result is
+// reproducible run to run.
+
+#include "triples.h"
+
+#include "ops.h"
+#include "zgemm.h"
+
+namespace ccsd {
+
+namespace {
+
+constexpr int kTriplesThreads = 256;
+
+struct EnergyArgs {
+  int o = 0, v = 0;
+  int64_t Pv = 0;
+  int i = 0, j = 0, k0 = 0, nk = 0;
+  const z *E = nullptr, *M = nullptr;
+  const z *t1 = nullptr, *t2 = nullptr, *oovv = nullptr, *fov = nullptr;
+  const double* d = nullptr;
+  double* partials = nullptr;  // gridDim.x * 3
+};
+
+__device__ __forceinline__ z zfma_conj_a(z a, z b, z acc) {  // acc + conj(a) * b
+  return make_double2(acc.x + a.x * b.x + a.y * b.y, acc.y + a.x * b.y - a.y * b.x);
+}
+
+__global__ void __launch_bounds__(kTriplesThreads) triples_energy_kernel(EnergyArgs g) {
+  const int64_t v = g.v, o = g.o, Pv = g.Pv;
+  const int64_t per = v * v * v;
+  const int64_t total = per * g.nk;
+  double s4 = 0.0, s5 = 0.0, s5m = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e % v);
+    const int b = (int)((e / v) % v);
+    const int64_t r = e / (v * v);
+    const int a = (int)(r % v);
+    const int t = (int)(r / v);
+    if (!(a < b && b < c)) continue;
+    const int k = g.k0 + t;
+    const z* E = g.E + (int64_t)t * Pv * v;
+    const z* M = g.M + (int64_t)t * v * Pv;
+    const int64_t pab = pair_index(a, b, v), pbc = pair_index(b, c, v), pac = pair_index(a, c, v);
+    // X = W^{abc} + W^{bca} + W^{cab}, W = E (antisymmetric in its first two virtual labels)
+    //                                  + M (antisymmetric in its last two)
+    z X = E[pab * v + c];
+    X = zadd(X, E[pbc * v + a]);
+    X = zsub(X, E[pac * v + b]);
+    X = zadd(X, M[a * Pv + pbc]);
+    X = zsub(X, M[b * Pv + pac]);
+    X = zadd(X, M[c * Pv + pab]);
+    const double D = g.d[o + a] + g.d[o + b] + g.d[o + c] - g.d[g.i] - g.d[g.j] - g.d[k];
+    // Z and Y summed over the cyclic orders of the occupied and of the virtual labels
+    const int occ[3] = {g.i, g.j, k};
+    const int vir[3] = {a, b, c};
+    z Zs = make_double2(0.0, 0.0), Ys = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      const int64_t p = occ[s], q = occ[(s + 1) % 3], rr = occ[(s + 2) % 3];
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const int64_t x = vir[u], y = vir[(u + 1) % 3], zz = vir[(u + 2) % 3];
+        const int64_t idx = ((p * o + q) * v + x) * v + y;
+        const z w = g.oovv[idx], tt = g.t2[idx];
+        const z a1 = g.t1[rr * v + zz], f = g.fov[rr * v + zz];
+        // <pq||xy> conj(t^z_r) + conj(t^{xy}_{pq}) f_rz
+        Zs = zfma_conj_a(a1, w, Zs);
+        Zs = zfma_conj_a(tt, f, Zs);
+        // t^{xy}_{pq} t^z_r
+        Ys = zadd(Ys, zmul(tt, a1));
+      }
+    }
+    // the determinant of t1 over rows (i, j, k) and columns (a, b, c)
+    z m[3][3];
+#pragma unroll
+    for (int rr = 0; rr < 3; ++rr)
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) m[rr][cc] = g.t1[(int64_t)occ[rr] * v + vir[cc]];
+    const z c0 = zsub(zmul(m[1][1], m[2][2]), zmul(m[1][2], m[2][1]));
+    const z c1 = zsub(zmul(m[1][0], m[2][2]), zmul(m[1][2], m[2][0]));
+    const z c2 = zsub(zmul(m[1][0], m[2][1]), zmul(m[1][1], m[2][0]));
+    Ys = zadd(Ys, zadd(zsub(zmul(m[0][0], c0), zmul(m[0][1], c1)), zmul(m[0][2], c2)));
+    const double inv = 1.0 / D;
+    s4 += (X.x * X.x + X.y * X.y) * inv;
+    s5 += (X.x * Zs.x - X.y * Zs.y) * inv;
+    s5m += X.x * Ys.x + X.y * Ys.y;
+  }
+  // fixed-shape block reduction
+  __shared__ double red[3][kTriplesThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    s4 += __shfl_down_sync(0xffffffffu, s4, off);
+    s5 += __shfl_down_sync(0xffffffffu, s5, off);
+    s5m += __shfl_down_sync(0xffffffffu, s5m, off);
+  }
+  if (lane == 0) {
+    red[0][warp] = s4;
+    red[1][warp] = s5;
+    red[2][warp] = s5m;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double acc = 0.0;
+    for (int w = 0; w < kTriplesThreads / 32; ++w) acc += red[threadIdx.x][w];
+    g.partials[(int64_t)blockIdx.x * 3 + threadIdx.x] = acc;
+  }
+}
+
+// pair_acc[0..2] += the block partials, summed in block order by one thread per term.
+__global__ void triples_accumulate_kernel(const double* __restrict__ partials, int nblocks,
+                                          double* __restrict__ pair_acc) {
+  const int m = threadIdx.x;
+  if (m >= 3) return;
+  double acc = 0.0;
+  for (int b = 0; b < nblocks; ++b) acc += partials[(int64_t)b * 3 + m];
+  pair_acc[m] += acc;
+}
+
+int energy_grid(int64_t work) {
+  int64_t g = (work + kTriplesThreads - 1) / kTriplesThreads;
+  const int64_t cap = 152 * 8;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+int64_t triples_partials(const TriplesArgs& a) {
+  (void)a;
+  return 152 * 8 * 3;
+}
+
+int64_t triples_batch_elems(int v) { return 2 * pair_count(v) * (int64_t)v; }
+
+cudaError_t triples_eval(const TriplesArgs& a, cudaStream_t s) {
+  const int o = a.o, v = a.v;
+  if (o < 3 || v < 3) return cudaSuccess;
+  const int64_t Pv = pair_count(v), v2 = (int64_t)v * v;
+  const int64_t part = Pv * v;  // elements of E (and of M) per triple
+  z* Ebuf = a.work;
+  z* Mbuf = a.work + part * a.max_batch;
+  cudaError_t e = pack_pairs(a.t2, a.t2pk, (int64_t)o * o, v, 0, s);
+  if (e != cudaSuccess) return e;
+  const z minus1 = make_double2(-1.0, 0.0), one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
+  for (int i = 0; i < o - 2; ++i) {
+    for (int j = i + 1; j < o - 1; ++j) {
+      for (int k0 = j + 1; k0 < o; k0 += a.max_batch) {
+        const int nk = (o - k0) < a.max_batch ? (o - k0) : a.max_batch;
+        // ---- e-terms: E[t][P(a,b)][c] over k = k0 + t
+        ZGemmArgs g;
+        g.M = Pv;
+        g.N = v;
+        g.K = v;
+        g.batch = nk;
+        g.transA = 1;
+        g.conjA = 1;
+        g.lda = (int64_t)o * Pv;
+        g.ldb = v;
+        g.C = Ebuf;
+        g.ldc = v;
+        g.sC = part;
+        g.alpha = minus1;  // <ab||Le> = -conj(<eL||ab>)
+        // (i; jk): A = rows L = i, B = t2[j][k]
+        g.A = a.vovv_pk + (int64_t)i * Pv;
+        g.sA = 0;
+        g.B = a.t2 + ((int64_t)j * o + k0) * v2;
+        g.sB = v2;
+        g.beta = zero;
+        if ((e = zgemm_f64(g, s)) != cudaSuccess) return e;
+        // (j; ki): A = rows L = j, B = t2[k][i]
+        g.A = a.vovv_pk + (int64_t)j * Pv;
+        g.B = a.t2 + ((int64_t)k0 * o + i) * v2;
+        g.sB = (int64_t)o * v2;
+        g.beta = one;
+        if ((e = zgemm_f64(g, s)) != cudaSuccess) return e;
+        // (k; ij): A = rows L = k, B = t2[i][j]
+        g.A = a.vovv_pk + (int64_t)k0 * Pv;
+        g.sA = Pv;
+        g.B = a.t2 + ((int64_t)i * o + j) * v2;
+        g.sB = 0;
+        if ((e = zgemm_f64(g, s)) != cudaSuccess) return e;
+        // ---- m-terms: M[t][a][P(b,c)]
+        ZGemmArgs h;
+        h.M = v;
+        h.N = Pv;
+        h.K = o;
+        h.batch = nk;
+        h.transA = 1;
+        h.conjA = 1;
+        h.lda = v;
+        h.ldb = Pv;
+        h.C = Mbuf;
+        h.ldc = Pv;
+        h.sC = part;
+        h.alpha = minus1;  // <am||pq> = -conj(<pq||ma>)
+        const int64_t ov = (int64_t)o * v;
+        // (ij; k): A = ooov[i][j], B = t2pk[k]
+        h.A = a.ooov + ((int64_t)i * o + j) * ov;
+        h.sA = 0;
+        h.B = a.t2pk + (int64_t)k0 * o * Pv;
+        h.sB = (int64_t)o * Pv;
+        h.beta = zero;
+        if ((e = zgemm_f64(h, s)) != cudaSuccess) return e;
+        // (jk; i): A = ooov[j][k], B = t2pk[i]
+        h.A = a.ooov + ((int64_t)j * o + k0) * ov;
+        h.sA = ov;
+        h.B = a.t2pk + (int64_t)i * o * Pv;
+        h.sB = 0;
+        h.beta = one;
+        if ((e = zgemm_f64(h, s)) != cudaSuccess) return e;
+        // (ki; j): A = ooov[k][i], B = t2pk[j]
+        h.A = a.ooov + ((int64_t)k0 * o + i) * ov;
+        h.sA = (int64_t)o * ov;
+        h.B = a.t2pk + (int64_t)j * o * Pv;
+        if ((e = zgemm_f64(h, s)) != cudaSuccess) return e;
+        // ---- energies of the batch
+        EnergyArgs q;
+        q.o = o;
+        q.v = v;
+        q.Pv = Pv;
+        q.i = i;
+        q.j = j;
+        q.k0 = k0;
+        q.nk = nk;
+        q.E = Ebuf;
+        q.M = Mbuf;
+        q.t1 = a.t1;
+        q.t2 = a.t2;
+        q.oovv = a.oovv;
+        q.fov = a.fov;
+        q.d = a.d;
+        q.partials = a.partials;
+        const int grid = energy_grid((int64_t)nk * v * v * v);
+        triples_energy_kernel<<<grid, kTriplesThreads, 0, s>>>(q);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        triples_accumulate_kernel<<<1, 32, 0, s>>>(a.partials, grid, a.pair_acc + ((int64_t)i * o + j) * 3);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      }
+    }
+  }
+  return cudaSuccess;
+}
+
+}  // namespace ccsd

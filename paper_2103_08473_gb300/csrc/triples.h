@@ -1,0 +1,33 @@
+// Perturbative triples corrections at converged CCSD amplitudes (host side).
+#pragma once
+
+#include "common.cuh"
+
+namespace ccsd {
+
+// Device pointers of the context's constant blocks and amplitudes, and the call's workspace.
+struct TriplesArgs {
+  int o = 0, v = 0;
+  const z* t1 = nullptr;       // [i][a]
+  const z* t2 = nullptr;       // [i][j][a][b]
+  const z* oovv = nullptr;     // <ij||ab> [i][j][a][b]
+  const z* ooov = nullptr;     // <kl||ic> [k][l][i][c]
+  const z* vovv_pk = nullptr;  // <ak||cd> [(a,k)][P(c,d)]
+  const z* fov = nullptr;      // f_ia [i][a]
+  const double* d = nullptr;   // real diagonal of the Fock matrix (o + v)
+  z* t2pk = nullptr;           // o*o*P(v): t2 packed over its virtual pair
+  z* work = nullptr;           // max_batch * triples_batch_elems(v)
+  int max_batch = 1;           // triples (i, j, k) per batch, k consecutive
+  double* partials = nullptr;  // triples_partials() doubles
+  double* pair_acc = nullptr;  // o*o*3 doubles, zeroed by the caller; [(i*o + j)*3 + m] += the
+                               // pair's sums of |X|^2/D (m=0), Re(X Z)/D (1), Re(X conj Y) (2)
+};
+
+// Complex elements of workspace per triple of a batch (the two packed parts of W).
+int64_t triples_batch_elems(int v);
+// Doubles of block partials the energy kernel writes per batch.
+int64_t triples_partials(const TriplesArgs& a);
+// Enqueue the whole evaluation on s (no synchronisation). o < 3 or v < 3: nothing to do.
+cudaError_t triples_eval(const TriplesArgs& a, cudaStream_t s);
+
+}  // namespace ccsd

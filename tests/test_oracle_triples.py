@@ -244,3 +244,15 @@ def test_pins_catch_the_integrals_as_printed(monkeypatch):
     t2p = t2 * uo[:, None, None, None] * uo[None, :, None, None] \
         * np.conj(uv)[None, None, :, None] * np.conj(uv)[None, None, None, :]
     assert abs(T3.corrections(f, R.integrals(Bp, o), t1, t2p)["+T"] - printed) > 1e-6
+
+
+def test_pair_contributions_sum_to_the_corrections():
+    """The per-pair form (fixed occupied labels, blocks oovv/ooov/vovv only) sums to the full one."""
+    o, v = 5, 6
+    s, f, Vf, V = _system(o, v, 12, 101, scale=0.4, fock_offdiag=0.1)
+    t1, t2 = inputs.random_amplitudes(o, v, 102, scale=0.1)
+    ref = T3.corrections(f, V, t1, t2)
+    small = {k: V[k] for k in ("oovv", "ooov", "vovv")}
+    tot = sum(T3.pair_contributions(f, small, t1, t2, i, j) for i in range(o) for j in range(i + 1, o))
+    for m, key in enumerate(("+T", "(T)", "-T")):
+        assert abs(tot[m] - ref[key]) < 1e-13 * abs(ref[key]), key
