@@ -413,6 +413,130 @@ def run_ours(args, wl):
     print(json.dumps(line), flush=True)
 
 
+def oracle_triples_time(wl, ntriples: int = 2):
+    """Time the oracle's per-pair triples on the last pairs (one triple each) at full size and
+    extrapolate by the number of triples i<j<k. Returns (seconds, sample description)."""
+    from oracle import ccsd_ref as R
+    from oracle import triples_ref as T3
+    from paper_2103_08473_gb300 import inputs
+
+    s = inputs.make_system(wl["o"], wl["v"], wl["naux"], wl["seed"])
+    o, v = s.o, s.v
+    f = R.fock_matrix(s.eps)
+    t1, t2 = inputs.random_amplitudes(o, v, wl["seed"] + 77, scale=0.01)
+    V = {k: R.antisym_block(s.B, o, k) for k in ("oovv", "ooov", "vovv")}
+    pairs = [(o - 3 - n, o - 2) for n in range(ntriples)]  # j = o-2: the single triple k = o-1
+    t0 = time.perf_counter()
+    for i, j in pairs:
+        T3.pair_contributions(f, V, t1, t2, i, j)
+    dt = time.perf_counter() - t0
+    nt = o * (o - 1) * (o - 2) // 6
+    return dt / len(pairs) * nt, (f"the oracle's triples (numpy complex128, per-pair form): {len(pairs)} triples "
+                                  f"(i, {o - 2}, {o - 1}) at full size in {dt:.1f} s, extrapolated by the {nt} "
+                                  f"triples i<j<k of {wl['name']}; integral blocks untimed")
+
+
+def run_triples(args, wl):
+    """One step = one evaluation of E(+T), E((T)), E(-T) (FP64) at the workload's MP2 amplitudes
+    with random singles; the amplitudes' values do not change the work."""
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2103_08473_gb300 import build, flops, inputs
+    from paper_2103_08473_gb300 import ccsd as ccmod
+
+    ccmod.load(build.build())
+    s = inputs.make_system(wl["o"], wl["v"], wl["naux"], wl["seed"])
+    o, v = s.o, s.v
+    stream = torch.cuda.Stream()
+    cc = make_ctx(ccmod, s, wl, "fp64", SPLIT_SLICES, stream)
+    t1, _ = inputs.random_amplitudes(o, v, wl["seed"] + 77, scale=0.01)
+    _, t2 = cc.get_amplitudes()
+    cc.set_amplitudes(t1, t2)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        cc.triples()
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    eg = mg = en = 0.0
+    for _ in range(args.steps):
+        res = cc.triples()
+        eg += cc.query("triples_egemm_ms")
+        mg += cc.query("triples_mgemm_ms")
+        en += cc.query("triples_energy_ms")
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    launches = int(cc.query("triples_launches"))
+    batches = int(cc.query("triples_batches"))
+    nb = int(cc.query("triples_batch"))
+
+    # end to end through the C ABI with host buffers: H2D of the amplitudes from pinned memory, the
+    # evaluation, the three energies back
+    t1h = torch.from_numpy(t1).pin_memory()
+    t2h = torch.from_numpy(t2).pin_memory()
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for _ in range(max(2, args.steps)):
+        cc.set_amplitudes(t1h.numpy(), t2h.numpy())
+        cc.triples()
+    e2e = (time.perf_counter() - w0) / max(2, args.steps)
+    cc.close()
+    if rank != 0:
+        return
+    cm = flops.triples_cmacs(o, v)
+    peaks, peak_kind = load_peaks()
+    fp64_peak = peaks["bf16_tflops_sustained"] * FP64_OVER_BF16_NOMINAL
+    eg_s = eg / args.steps * 1e-3
+    ex_fl = 6.0 * cm["e"]  # 3M: three real GEMMs per complex GEMM
+    ach = ex_fl / eg_s / 1e12 if eg_s > 0 else None
+    roofline = {"kernel": "zgemm_dmma_kernel<3M> (triples e-terms: M = v(v-1)/2, N = K = v, batched over k)",
+                "bound": "tensor", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": (ach / fp64_peak) if ach else None,
+                "peak_basis": f"{peak_kind} bf16_tflops_sustained x 1.25/2250 (nominal dense FP64/BF16 ratio)",
+                "algorithmic_flops_per_launch": ex_fl / (3 * batches), "launch_ms": eg / args.steps / (3 * batches),
+                "launches_per_step": 3 * batches,
+                "zgemm_equivalent_tflops": 8.0 * cm["e"] / eg_s / 1e12 if eg_s > 0 else None,
+                "traffic": recorded_traffic("zgemm_f64.cu", f"triples_egemm_{wl['name']}")}
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        est, sample = oracle_triples_time(wl)
+        cpu = {"value": est, "unit": "s", "cores": os.cpu_count(), "kind": "oracle", "sample": sample}
+    value = whole_job_seconds_per_iteration(ms, args.steps, world)
+    line = {"metric": "triples corrections time (s)", "value": value, "unit": "s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{wl['name']} triples", "o": o, "v": v, "naux": wl["naux"],
+                       "amplitudes": "MP2 doubles, random singles (scale 0.01)", "max_batch": nb,
+                       "batches": batches,
+                       "l2": "inputs larger than L2 (packed vovv and the W batch exceed 129 MB)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "step_ms_split": {"e_gemm": eg / args.steps, "m_gemm": mg / args.steps, "energy": en / args.steps},
+            "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": 16 * (o * v + o * o * v * v),
+                    "d2h_bytes_per_step": 3 * 8},
+            "clocks": clocks, "gpu_launches": launches * args.steps,
+            "energies": res}
+    print(json.dumps(line), flush=True)
+
+
 def run_batch(args, wl):
     """64 uneven systems solved to convergence in one batch vs one after another."""
     import numpy as np
@@ -575,6 +699,8 @@ def main():
                     help="ccd: the doubles equations with t1 held at zero")
     ap.add_argument("--complex-4m", action="store_true",
                     help="FP64 GEMMs with four real products per complex product instead of three")
+    ap.add_argument("--triples", action="store_true",
+                    help="time the triples corrections E(+T), E((T)), E(-T) on the workload instead of an iteration")
     ap.add_argument("--residual-once", action="store_true",
                     help="create the context and evaluate one residual eagerly (for ncu captures), no timing")
     args = ap.parse_args()
@@ -588,6 +714,8 @@ def main():
         run_batch(args, wl)
     elif args.residual_once:
         residual_once(wl, args.precision or wl["precision"], args.slices or SPLIT_SLICES)
+    elif args.triples and args.impl == "ours":
+        run_triples(args, wl)
     elif args.impl == "reference":
         run_reference(args, wl)
     else:

@@ -211,7 +211,11 @@ ccsd_status ccsd_timings(ccsd_ctx* ctx, const char** names, double* ms, int cap,
 /*
  * Scalar facts about a context: "kernels_per_iteration" (kernel nodes of the
  * iteration graph), "device_bytes" (device memory held), "iterations_run",
- * "plan_ops", "o", "v". CCSD_ERR_ARG for an unknown key.
+ * "plan_ops", "o", "v". Of the last ccsd_triples call: "triples_batch" (triples per
+ * batch), "triples_batches", "triples_launches" (kernels launched), and with
+ * opts.profile = 1 the device time in ms of its e-term GEMMs ("triples_egemm_ms"),
+ * m-term GEMMs ("triples_mgemm_ms") and energy kernels ("triples_energy_ms"), summed
+ * over the batches (0 without profiling). CCSD_ERR_ARG for an unknown key.
  */
 ccsd_status ccsd_query(const ccsd_ctx* ctx, const char* key, double* value);
 

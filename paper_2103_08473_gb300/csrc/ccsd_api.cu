@@ -92,6 +92,10 @@ struct ccsd_ctx {
   int kernels_per_iter = 0;
   int64_t device_bytes = 0;
   int64_t iterations_run = 0;
+  // the last ccsd_triples call: batch size, batches, kernel launches and (profile = 1) device time of
+  // its e-term GEMMs, m-term GEMMs and energy kernels
+  int64_t tri_batch = 0, tri_batches = 0, tri_launches = 0;
+  double tri_ms[3] = {0.0, 0.0, 0.0};
 };
 
 namespace {
@@ -1528,10 +1532,20 @@ ccsd_status ccsd_triples(ccsd_ctx* ctx, int max_batch, double* out, double* pair
     a.work = (z*)work;
     a.partials = (double*)partials;
     a.pair_acc = (double*)pacc;
+    TriplesTimer timer;
+    if (ctx->opts.profile) a.timer = &timer;
     CK(cudaMemsetAsync(pacc, 0, sizeof(double) * acc.size(), ctx->stream));
     CK(triples_eval(a, ctx->stream));
     CK(cudaMemcpyAsync(acc.data(), pacc, sizeof(double) * acc.size(), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    ctx->tri_batch = nb;
+    ctx->tri_batches = a.batches;
+    ctx->tri_launches = 1 + 8 * a.batches;  // t2 packing; per batch 6 GEMMs, energy, accumulation
+    ctx->tri_ms[0] = ctx->tri_ms[1] = ctx->tri_ms[2] = 0.0;
+    if (a.timer) CK(timer.sums(ctx->tri_ms));
+  } else {
+    ctx->tri_batch = ctx->tri_batches = ctx->tri_launches = 0;
+    ctx->tri_ms[0] = ctx->tri_ms[1] = ctx->tri_ms[2] = 0.0;
   }
   // per-pair contributions to the three energies, and their sums in pair order
   out[0] = out[1] = out[2] = 0.0;
@@ -1633,6 +1647,12 @@ ccsd_status ccsd_query(const ccsd_ctx* ctx, const char* key, double* value) {
   else if (k == "device_bytes") *value = (double)ctx->device_bytes;
   else if (k == "iterations_run") *value = (double)ctx->iterations_run;
   else if (k == "plan_ops") *value = (double)ctx->plan->ops().size();
+  else if (k == "triples_batch") *value = (double)ctx->tri_batch;
+  else if (k == "triples_batches") *value = (double)ctx->tri_batches;
+  else if (k == "triples_launches") *value = (double)ctx->tri_launches;
+  else if (k == "triples_egemm_ms") *value = ctx->tri_ms[0];
+  else if (k == "triples_mgemm_ms") *value = ctx->tri_ms[1];
+  else if (k == "triples_energy_ms") *value = ctx->tri_ms[2];
   else if (k == "o") *value = ctx->o;
   else if (k == "v") *value = ctx->v;
   else return CCSD_ERR_ARG;

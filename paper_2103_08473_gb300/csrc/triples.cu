@@ -156,7 +156,7 @@ int64_t triples_partials(const TriplesArgs& a) {
 
 int64_t triples_batch_elems(int v) { return 2 * pair_count(v) * (int64_t)v; }
 
-cudaError_t triples_eval(const TriplesArgs& a, cudaStream_t s) {
+cudaError_t triples_eval(TriplesArgs& a, cudaStream_t s) {
   const int o = a.o, v = a.v;
   if (o < 3 || v < 3) return cudaSuccess;
   const int64_t Pv = pair_count(v), v2 = (int64_t)v * v;
@@ -170,6 +170,8 @@ cudaError_t triples_eval(const TriplesArgs& a, cudaStream_t s) {
     for (int j = i + 1; j < o - 1; ++j) {
       for (int k0 = j + 1; k0 < o; k0 += a.max_batch) {
         const int nk = (o - k0) < a.max_batch ? (o - k0) : a.max_batch;
+        ++a.batches;
+        if (a.timer && (e = a.timer->mark(s)) != cudaSuccess) return e;
         // ---- e-terms: E[t][P(a,b)][c] over k = k0 + t
         ZGemmArgs g;
         g.M = Pv;
@@ -203,6 +205,7 @@ cudaError_t triples_eval(const TriplesArgs& a, cudaStream_t s) {
         g.B = a.t2 + ((int64_t)i * o + j) * v2;
         g.sB = 0;
         if ((e = zgemm_f64(g, s)) != cudaSuccess) return e;
+        if (a.timer && (e = a.timer->mark(s)) != cudaSuccess) return e;
         // ---- m-terms: M[t][a][P(b,c)]
         ZGemmArgs h;
         h.M = v;
@@ -237,6 +240,7 @@ cudaError_t triples_eval(const TriplesArgs& a, cudaStream_t s) {
         h.sA = (int64_t)o * ov;
         h.B = a.t2pk + (int64_t)j * o * Pv;
         if ((e = zgemm_f64(h, s)) != cudaSuccess) return e;
+        if (a.timer && (e = a.timer->mark(s)) != cudaSuccess) return e;
         // ---- energies of the batch
         EnergyArgs q;
         q.o = o;
@@ -259,6 +263,7 @@ cudaError_t triples_eval(const TriplesArgs& a, cudaStream_t s) {
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         triples_accumulate_kernel<<<1, 32, 0, s>>>(a.partials, grid, a.pair_acc + ((int64_t)i * o + j) * 3);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (a.timer && (e = a.timer->mark(s)) != cudaSuccess) return e;
       }
     }
   }

@@ -1,9 +1,40 @@
 // Perturbative triples corrections at converged CCSD amplitudes (host side).
 #pragma once
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace ccsd {
+
+// Optional timing: four events per batch (before the e-term GEMMs, before the m-term GEMMs,
+// before the energy kernel, after its accumulation), recorded on the evaluation's stream.
+struct TriplesTimer {
+  std::vector<cudaEvent_t> ev;
+  cudaError_t mark(cudaStream_t s) {
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return r;
+    ev.push_back(e);
+    return cudaEventRecord(e, s);
+  }
+  // After the stream is synchronised: ms[0..2] = time of the e-term GEMMs, the m-term GEMMs and
+  // the energy kernels, summed over the batches.
+  cudaError_t sums(double ms[3]) const {
+    ms[0] = ms[1] = ms[2] = 0.0;
+    for (size_t b = 0; b + 3 < ev.size(); b += 4)
+      for (int g = 0; g < 3; ++g) {
+        float t = 0.f;
+        cudaError_t r = cudaEventElapsedTime(&t, ev[b + g], ev[b + g + 1]);
+        if (r != cudaSuccess) return r;
+        ms[g] += t;
+      }
+    return cudaSuccess;
+  }
+  ~TriplesTimer() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
+};
 
 // Device pointers of the context's constant blocks and amplitudes, and the call's workspace.
 struct TriplesArgs {
@@ -21,6 +52,8 @@ struct TriplesArgs {
   double* partials = nullptr;  // triples_partials() doubles
   double* pair_acc = nullptr;  // o*o*3 doubles, zeroed by the caller; [(i*o + j)*3 + m] += the
                                // pair's sums of |X|^2/D (m=0), Re(X Z)/D (1), Re(X conj Y) (2)
+  TriplesTimer* timer = nullptr;  // optional
+  int64_t batches = 0;            // out: batches run
 };
 
 // Complex elements of workspace per triple of a batch (the two packed parts of W).
@@ -28,6 +61,6 @@ int64_t triples_batch_elems(int v);
 // Doubles of block partials the energy kernel writes per batch.
 int64_t triples_partials(const TriplesArgs& a);
 // Enqueue the whole evaluation on s (no synchronisation). o < 3 or v < 3: nothing to do.
-cudaError_t triples_eval(const TriplesArgs& a, cudaStream_t s);
+cudaError_t triples_eval(TriplesArgs& a, cudaStream_t s);
 
 }  // namespace ccsd

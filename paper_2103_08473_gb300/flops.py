@@ -48,3 +48,11 @@ def ladder_flops_dense(o: int, v: int) -> int:
 def ring_flops(o: int, v: int) -> int:
     """8 (ov)^3: the ring GEMM (ai) x (ck) x (bj)."""
     return 8 * (o * v) ** 3
+
+
+def triples_cmacs(o: int, v: int) -> dict:
+    """Complex multiply-adds of the triples GEMMs over all i<j<k: the three e-terms form
+    [v(v-1)/2] x v outputs over K = v, the three m-terms v x [v(v-1)/2] over K = o."""
+    nt = o * (o - 1) * (o - 2) // 6
+    pv = pairs(v)
+    return {"e": 3.0 * nt * pv * v * v, "m": 3.0 * nt * v * pv * o}
