@@ -454,7 +454,8 @@ def run_triples(args, wl):
     s = inputs.make_system(wl["o"], wl["v"], wl["naux"], wl["seed"])
     o, v = s.o, s.v
     stream = torch.cuda.Stream()
-    cc = make_ctx(ccmod, s, wl, "fp64", SPLIT_SLICES, stream)
+    precision = args.precision or "fp64"
+    cc = make_ctx(ccmod, s, wl, precision, SPLIT_SLICES, stream)
     t1, _ = inputs.random_amplitudes(o, v, wl["seed"] + 77, scale=0.01)
     _, t2 = cc.get_amplitudes()
     cc.set_amplitudes(t1, t2)
@@ -502,18 +503,34 @@ def run_triples(args, wl):
         return
     cm = flops.triples_cmacs(o, v)
     peaks, peak_kind = load_peaks()
-    fp64_peak = peaks["bf16_tflops_sustained"] * FP64_OVER_BF16_NOMINAL
     eg_s = eg / args.steps * 1e-3
-    ex_fl = 6.0 * cm["e"]  # 3M: three real GEMMs per complex GEMM
-    ach = ex_fl / eg_s / 1e12 if eg_s > 0 else None
-    roofline = {"kernel": "zgemm_dmma_kernel<3M> (triples e-terms: M = v(v-1)/2, N = K = v, batched over k)",
-                "bound": "tensor", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": (ach / fp64_peak) if ach else None,
-                "peak_basis": f"{peak_kind} bf16_tflops_sustained x 1.25/2250 (nominal dense FP64/BF16 ratio)",
-                "algorithmic_flops_per_launch": ex_fl / (3 * batches), "launch_ms": eg / args.steps / (3 * batches),
-                "launches_per_step": 3 * batches,
-                "zgemm_equivalent_tflops": 8.0 * cm["e"] / eg_s / 1e12 if eg_s > 0 else None,
-                "traffic": recorded_traffic("zgemm_f64.cu", f"triples_egemm_{wl['name']}")}
+    nt = o * (o - 1) * (o - 2) // 6
+    if precision == "fp64":
+        fp64_peak = peaks["bf16_tflops_sustained"] * FP64_OVER_BF16_NOMINAL
+        ex_fl = 6.0 * cm["e"]  # 3M: three real GEMMs per complex GEMM
+        ach = ex_fl / eg_s / 1e12 if eg_s > 0 else None
+        nl = 3 * batches
+        roofline = {"kernel": "zgemm_dmma_kernel<3M> (triples e-terms: M = v(v-1)/2, N = K = v, batched over k)",
+                    "bound": "tensor", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                    "frac": (ach / fp64_peak) if ach else None,
+                    "peak_basis": f"{peak_kind} bf16_tflops_sustained x 1.25/2250 (nominal dense FP64/BF16 ratio)",
+                    "traffic": recorded_traffic("zgemm_f64.cu", f"triples_egemm_{wl['name']}")}
+    else:
+        # per triple and term: s(s+1)/2 digit pairs x 4 real e4m3 GEMMs of 2 M N K flops
+        pairs = SPLIT_SLICES * (SPLIT_SLICES + 1) // 2
+        ex_fl = pairs * 8.0 * cm["e"]
+        fp8_peak = peaks["bf16_tflops"] * 2.0
+        ach = ex_fl / eg_s / 1e12 if eg_s > 0 else None
+        nl = 3 * nt
+        roofline = {"kernel": "split_smallk_kernel<e4m3> (triples e-terms: one launch per triple and term, "
+                              "M = v(v-1)/2, N = K = v)",
+                    "bound": "tensor", "achieved": ach, "peak": fp8_peak, "unit": "TFLOP/s",
+                    "frac": (ach / fp8_peak) if ach else None,
+                    "peak_basis": f"{peak_kind} bf16_tflops (burst) x 2 (nominal dense FP8/BF16 ratio)",
+                    "traffic": recorded_traffic("zgemm_split.cu", f"triples_egemm_{wl['name']}")}
+    roofline.update({"algorithmic_flops_per_launch": ex_fl / nl, "launch_ms": eg / args.steps / nl,
+                     "launches_per_step": nl,
+                     "zgemm_equivalent_tflops": 8.0 * cm["e"] / eg_s / 1e12 if eg_s > 0 else None})
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         est, sample = oracle_triples_time(wl)
@@ -521,9 +538,11 @@ def run_triples(args, wl):
     value = whole_job_seconds_per_iteration(ms, args.steps, world)
     line = {"metric": "triples corrections time (s)", "value": value, "unit": "s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if precision == "fp64" else "e4m3 digits, f32 accumulate, f64 (e-terms); f64 (rest)",
             "data": "synthetic",
             "config": {"workload": f"{wl['name']} triples", "o": o, "v": v, "naux": wl["naux"],
+                       "precision": precision, "slices": SPLIT_SLICES if precision == "split" else None,
                        "amplitudes": "MP2 doubles, random singles (scale 0.01)", "max_batch": nb,
                        "batches": batches,
                        "l2": "inputs larger than L2 (packed vovv and the W batch exceed 129 MB)",

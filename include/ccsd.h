@@ -169,8 +169,12 @@ ccsd_status ccsd_energy(ccsd_ctx* ctx, ccsd_z* e);
  *   - Y is the triples part of exp(T1 + T2)|Phi_0>.
  *   - D = e_a + e_b + e_c - e_i - e_j - e_k, over the real diagonal of the Fock matrix
  *     (no level shift).
- * The arithmetic is FP64 throughout. W comes from batched complex GEMMs on the FP64 tensor
- * path, one occupied pair i<j at a time, with up to max_batch consecutive k > j per batch.
+ * W comes from complex GEMMs, one occupied pair i<j at a time, with up to max_batch
+ * consecutive k > j per batch. In an FP64 context every step is FP64: batched GEMMs on the
+ * FP64 tensor path. In a split-precision context (opts.precision) the e-terms of W, three
+ * P(v) x v x v products per triple, are split GEMMs on the tensor cores. Their digits are cut
+ * once per call; their error is that of the split GEMM, 2^(1 - bits*slices) relative to each
+ * row's scale. Everything else stays FP64.
  *   max_batch <= 0 sizes the batch to a quarter of the free device memory, at most 8 GB.
  *   Each triple of a batch needs 2 * v * v(v-1)/2 complex elements of workspace.
  * out: host, 3 doubles.
@@ -180,7 +184,8 @@ ccsd_status ccsd_energy(ccsd_ctx* ctx, ccsd_z* e);
  * The workspace is allocated by this call and freed before it returns. Synchronises the
  * stream. The result is reproducible run to run.
  * Errors: CCSD_ERR_ARG for a NULL out or a negative max_batch; CCSD_ERR_OOM when the
- * workspace for one triple does not fit.
+ * workspace for one triple (and, split, the digit sets) does not fit; CCSD_ERR_TIMEOUT if a
+ * bounded wait of the split GEMM gave up.
  */
 ccsd_status ccsd_triples(ccsd_ctx* ctx, int max_batch, double* out, double* pair_terms);
 

@@ -1532,15 +1532,39 @@ ccsd_status ccsd_triples(ccsd_ctx* ctx, int max_batch, double* out, double* pair
     a.work = (z*)work;
     a.partials = (double*)partials;
     a.pair_acc = (double*)pacc;
+    SliceSet SA, SB;
+    int64_t setup_launches = 0;
+    if (ctx->use_split) {
+      // digits of <ab||Le> for every L (rows L*P(v) + P over K = e, straight from vovv_pk) and of t2
+      // with its virtual labels swapped (rows (p*o + q)*v + c over K = e)
+      void *t2T = nullptr, *sam = nullptr, *sbm = nullptr;
+      const int64_t ra = (int64_t)o * ctx->Pv, rb = (int64_t)o * o * v;
+      if (!mem.get(&t2T, sizeof(z) * (size_t)rb * v) || !mem.get(&sam, (size_t)slice_bytes(ra, v, ctx->split)) ||
+          !mem.get(&sbm, (size_t)slice_bytes(rb, v, ctx->split)))
+        return set_err(ctx, CCSD_ERR_OOM, "triples digit sets");
+      const int64_t d_t2[4] = {o, o, v, v};
+      const int pT[4] = {0, 1, 3, 2};
+      CK(permute4(ctx->t2, d_t2, pT, (z*)t2T, zmake(1, 0), 0.0, 0, ctx->stream));
+      CK(make_slices(ctx->vovv_pk, ra, v, ra, 1, 1, ctx->split, SA, sam, ctx->stream));
+      CK(make_slices((const z*)t2T, rb, v, v, 0, 0, ctx->split, SB, sbm, ctx->stream));
+      a.sa = &SA;
+      a.sb = &SB;
+      a.split_err = ctx->split_err;
+      setup_launches = 1 + 3 + 3;
+    }
     TriplesTimer timer;
     if (ctx->opts.profile) a.timer = &timer;
     CK(cudaMemsetAsync(pacc, 0, sizeof(double) * acc.size(), ctx->stream));
     CK(triples_eval(a, ctx->stream));
     CK(cudaMemcpyAsync(acc.data(), pacc, sizeof(double) * acc.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    if (ctx->use_split) CK(cudaMemcpyAsync(ctx->err_host, ctx->split_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    if (ctx->use_split && *ctx->err_host)
+      return set_err(ctx, CCSD_ERR_TIMEOUT, "a bounded wait in the tensor-core GEMM gave up (code " +
+                                                std::to_string(*ctx->err_host) + ")");
     ctx->tri_batch = nb;
     ctx->tri_batches = a.batches;
-    ctx->tri_launches = 1 + 8 * a.batches;  // t2 packing; per batch 6 GEMMs, energy, accumulation
+    ctx->tri_launches = setup_launches + a.launches;
     ctx->tri_ms[0] = ctx->tri_ms[1] = ctx->tri_ms[2] = 0.0;
     if (a.timer) CK(timer.sums(ctx->tri_ms));
   } else {

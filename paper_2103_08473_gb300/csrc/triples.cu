@@ -165,6 +165,7 @@ cudaError_t triples_eval(TriplesArgs& a, cudaStream_t s) {
   z* Mbuf = a.work + part * a.max_batch;
   cudaError_t e = pack_pairs(a.t2, a.t2pk, (int64_t)o * o, v, 0, s);
   if (e != cudaSuccess) return e;
+  a.launches += 1;
   const z minus1 = make_double2(-1.0, 0.0), one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
   for (int i = 0; i < o - 2; ++i) {
     for (int j = i + 1; j < o - 1; ++j) {
@@ -173,38 +174,55 @@ cudaError_t triples_eval(TriplesArgs& a, cudaStream_t s) {
         ++a.batches;
         if (a.timer && (e = a.timer->mark(s)) != cudaSuccess) return e;
         // ---- e-terms: E[t][P(a,b)][c] over k = k0 + t
-        ZGemmArgs g;
-        g.M = Pv;
-        g.N = v;
-        g.K = v;
-        g.batch = nk;
-        g.transA = 1;
-        g.conjA = 1;
-        g.lda = (int64_t)o * Pv;
-        g.ldb = v;
-        g.C = Ebuf;
-        g.ldc = v;
-        g.sC = part;
-        g.alpha = minus1;  // <ab||Le> = -conj(<eL||ab>)
-        // (i; jk): A = rows L = i, B = t2[j][k]
-        g.A = a.vovv_pk + (int64_t)i * Pv;
-        g.sA = 0;
-        g.B = a.t2 + ((int64_t)j * o + k0) * v2;
-        g.sB = v2;
-        g.beta = zero;
-        if ((e = zgemm_f64(g, s)) != cudaSuccess) return e;
-        // (j; ki): A = rows L = j, B = t2[k][i]
-        g.A = a.vovv_pk + (int64_t)j * Pv;
-        g.B = a.t2 + ((int64_t)k0 * o + i) * v2;
-        g.sB = (int64_t)o * v2;
-        g.beta = one;
-        if ((e = zgemm_f64(g, s)) != cudaSuccess) return e;
-        // (k; ij): A = rows L = k, B = t2[i][j]
-        g.A = a.vovv_pk + (int64_t)k0 * Pv;
-        g.sA = Pv;
-        g.B = a.t2 + ((int64_t)i * o + j) * v2;
-        g.sB = 0;
-        if ((e = zgemm_f64(g, s)) != cudaSuccess) return e;
+        if (a.sa) {
+          // one split GEMM per triple and term: C = -A_L B_pq^T over K = e
+          for (int t = 0; t < nk; ++t) {
+            const int k = k0 + t;
+            z* C = Ebuf + (int64_t)t * part;
+            const int L[3] = {i, j, k};
+            const int64_t pq[3] = {(int64_t)j * o + k, (int64_t)k * o + i, (int64_t)i * o + j};
+            for (int u = 0; u < 3; ++u) {
+              e = split_gemm(slice_rows(*a.sa, (int64_t)L[u] * Pv, Pv), slice_rows(*a.sb, pq[u] * v, v), C, v,
+                             minus1, u == 0 ? zero : one, a.split_err, nullptr, 0, s);
+              if (e != cudaSuccess) return e;
+            }
+          }
+          a.launches += 3 * nk;
+        } else {
+          ZGemmArgs g;
+          g.M = Pv;
+          g.N = v;
+          g.K = v;
+          g.batch = nk;
+          g.transA = 1;
+          g.conjA = 1;
+          g.lda = (int64_t)o * Pv;
+          g.ldb = v;
+          g.C = Ebuf;
+          g.ldc = v;
+          g.sC = part;
+          g.alpha = minus1;  // <ab||Le> = -conj(<eL||ab>)
+          // (i; jk): A = rows L = i, B = t2[j][k]
+          g.A = a.vovv_pk + (int64_t)i * Pv;
+          g.sA = 0;
+          g.B = a.t2 + ((int64_t)j * o + k0) * v2;
+          g.sB = v2;
+          g.beta = zero;
+          if ((e = zgemm_f64(g, s)) != cudaSuccess) return e;
+          // (j; ki): A = rows L = j, B = t2[k][i]
+          g.A = a.vovv_pk + (int64_t)j * Pv;
+          g.B = a.t2 + ((int64_t)k0 * o + i) * v2;
+          g.sB = (int64_t)o * v2;
+          g.beta = one;
+          if ((e = zgemm_f64(g, s)) != cudaSuccess) return e;
+          // (k; ij): A = rows L = k, B = t2[i][j]
+          g.A = a.vovv_pk + (int64_t)k0 * Pv;
+          g.sA = Pv;
+          g.B = a.t2 + ((int64_t)i * o + j) * v2;
+          g.sB = 0;
+          if ((e = zgemm_f64(g, s)) != cudaSuccess) return e;
+          a.launches += 3;
+        }
         if (a.timer && (e = a.timer->mark(s)) != cudaSuccess) return e;
         // ---- m-terms: M[t][a][P(b,c)]
         ZGemmArgs h;
@@ -263,6 +281,7 @@ cudaError_t triples_eval(TriplesArgs& a, cudaStream_t s) {
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         triples_accumulate_kernel<<<1, 32, 0, s>>>(a.partials, grid, a.pair_acc + ((int64_t)i * o + j) * 3);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        a.launches += 3 + 2;  // the m-term GEMMs, the energy kernel and its accumulation
         if (a.timer && (e = a.timer->mark(s)) != cudaSuccess) return e;
       }
     }

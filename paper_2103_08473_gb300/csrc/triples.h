@@ -4,6 +4,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "split.h"
 
 namespace ccsd {
 
@@ -52,8 +53,15 @@ struct TriplesArgs {
   double* partials = nullptr;  // triples_partials() doubles
   double* pair_acc = nullptr;  // o*o*3 doubles, zeroed by the caller; [(i*o + j)*3 + m] += the
                                // pair's sums of |X|^2/D (m=0), Re(X Z)/D (1), Re(X conj Y) (2)
+  // Split precision for the e-term GEMMs (null: FP64): digits of <ab||Le> over K = e for every L
+  // (rows L*P(v) + P(a,b)) and of t2 over K = e (rows (p*o + q)*v + c); each e-term is one split
+  // GEMM of two row views per triple.
+  const SliceSet* sa = nullptr;
+  const SliceSet* sb = nullptr;
+  int* split_err = nullptr;
   TriplesTimer* timer = nullptr;  // optional
   int64_t batches = 0;            // out: batches run
+  int64_t launches = 0;           // out: kernels launched
 };
 
 // Complex elements of workspace per triple of a batch (the two packed parts of W).

@@ -5,7 +5,10 @@ The three energies and the per-pair contributions are compared with
 sizes, its per-pair form at sizes where o^3 v^3 arrays do not fit, and sampled
 pairs at the o20/v120 workload's full size. The arithmetic is FP64 on both sides
 in a different summation order, so the bar is 1e-11 relative on every energy
-and per-pair term. Batches of 1, 2 and as many triples as fit must agree.
+and per-pair term. Batches of 1, 2 and as many triples as fit must agree. In a
+split-precision context the e-terms of W are split GEMMs with 8 digits of 5 bits:
+each product carries a relative error of at most ~2^-38 of its row and column
+scales, and the energies, quadratic in W, are held to 1e-9 relative.
 """
 import numpy as np
 import pytest
@@ -110,14 +113,33 @@ def test_bad_arguments(ccsd):
             cc.triples(max_batch=-1)
 
 
-def test_o20_v120_sampled_pairs(ccsd):
+@pytest.mark.parametrize("o,v,naux,seed,fs", [(4, 9, 18, 311, 0.05), (6, 33, 40, 312, 0.02)])
+def test_split_triples_match_oracle(ccsd, o, v, naux, seed, fs):
+    s, f, fock, t1, t2 = _case(o, v, naux, seed, 0.2, fs)
+    V = {k: R.antisym_block(s.B, o, k) for k in ("oovv", "ooov", "vovv")}
+    ref = sum(T3.pair_contributions(f, V, t1, t2, i, j) for i in range(o) for j in range(i + 1, o))
+    with ccsd.CCSD(o, v, s.eps, B=s.B, fock=fock, precision=ccsd.PREC_SPLIT) as cc:
+        cc.set_amplitudes(t1, t2)
+        got = cc.triples(max_batch=2)
+        launches = cc.query("triples_launches")
+    for m, key in enumerate(KEYS):
+        assert _close(got[key], ref[m], 1e-9), (key, got[key], ref[m])
+    # split mode: three tensor-core launches per triple for the e-terms
+    nt = o * (o - 1) * (o - 2) // 6
+    assert launches >= 3 * nt
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+def test_o20_v120_sampled_pairs(ccsd, precision):
     """The o20/v120 workload at full size: MP2 doubles from the context, random singles;
     pairs whose triples the per-pair oracle evaluates in seconds."""
     s = inputs.make_config("o20v120")
     o, v = s.o, s.v
     f = R.fock_matrix(s.eps)
     t1, _ = inputs.random_amplitudes(o, v, 309, scale=0.01)
-    with ccsd.CCSD(o, v, s.eps, B=s.B) as cc:
+    kw = {"precision": ccsd.PREC_SPLIT} if precision == "split" else {}
+    tol = 1e-9 if precision == "split" else 1e-11
+    with ccsd.CCSD(o, v, s.eps, B=s.B, **kw) as cc:
         _, t2 = cc.get_amplitudes()
         cc.set_amplitudes(t1, t2)
         got, pt = cc.triples(pair_terms=True)
@@ -125,5 +147,5 @@ def test_o20_v120_sampled_pairs(ccsd):
     for i, j in ((17, 18), (0, 18), (5, 17), (18, 19)):
         ref = T3.pair_contributions(f, V, t1, t2, i, j)
         for m in range(3):
-            assert _close(pt[i, j, m], ref[m]), (i, j, m, pt[i, j, m], ref[m])
+            assert _close(pt[i, j, m], ref[m], tol), (i, j, m, pt[i, j, m], ref[m])
     assert got["+T"] < 0.0
