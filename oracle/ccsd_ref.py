@@ -175,6 +175,26 @@ def ladder_rows(B: np.ndarray, o: int, tau: np.ndarray, pairs) -> np.ndarray:
     return out
 
 
+def _singles_terms(f: np.ndarray, V: dict, t1: np.ndarray, t2: np.ndarray, I: dict) -> dict:
+    """The printed terms of S^a_i (Appendix A), given the intermediates I."""
+    o = t1.shape[0]
+    fov = f[:o, o:]
+    ooov, vovo, vovv = V["ooov"], V["vovo"], V["vovv"]
+    ta = I["tau"]
+    es = lambda s, *ops: np.einsum(s, *ops, optimize=True)
+    Hvv, Hoo, Hov = I["Hvv"], I["Hoo"], I["Hov"]
+    t1terms = {}
+    t1terms["f"] = np.conj(fov)                                       # F^{i+}_a
+    t1terms["hvv"] = es("ac,ic->ia", Hvv, t1)                         # sum_c H^a_c t^c_i
+    t1terms["hoo"] = es("ki,ka->ia", Hoo, t1)                         # sum_k H^k_i t^a_k
+    t1terms["hov"] = es("kc,ikac->ia", Hov, t2)                       # sum_kc H^k_c t^{ac}_{ik}
+    t1terms["hf"] = es("kc,ic,ka->ia", Hov - 2.0 * fov, t1, t1)       # sum_k (sum_c (H^k_c - 2F^k_c) t^c_i) t^a_k
+    t1terms["vovv"] = 0.5 * es("akcd,ikcd->ia", vovv, ta)             # 1/2 sum_kcd V^{ak}_{cd} tau^{cd}_{ik}
+    t1terms["ooov"] = 0.5 * es("klic,klca->ia", ooov, ta)             # 1/2 sum_klc V^{kl}_{ic} tau^{ca}_{kl}
+    t1terms["vovo"] = -es("akci,kc->ia", vovo, t1)                    # - sum_kc V^{ak}_{ci} t^c_k
+    return t1terms
+
+
 def residual(f: np.ndarray, V: dict, t1: np.ndarray, t2: np.ndarray, parts: dict | None = None):
     """S^a_i and S^{ab}_{ij} of Appendix A at amplitudes (t1, t2).
 
@@ -207,19 +227,59 @@ def residual(f: np.ndarray, V: dict, t1: np.ndarray, t2: np.ndarray, parts: dict
     terms["driver"] = np.conj(oovv)
     S2 = sum(terms.values())
 
-    Hvv, Hoo, Hov = I["Hvv"], I["Hoo"], I["Hov"]
-    t1terms = {}
-    t1terms["f"] = np.conj(fov)                                       # F^{i+}_a
-    t1terms["hvv"] = es("ac,ic->ia", Hvv, t1)                         # sum_c H^a_c t^c_i
-    t1terms["hoo"] = es("ki,ka->ia", Hoo, t1)                         # sum_k H^k_i t^a_k
-    t1terms["hov"] = es("kc,ikac->ia", Hov, t2)                       # sum_kc H^k_c t^{ac}_{ik}
-    t1terms["hf"] = es("kc,ic,ka->ia", Hov - 2.0 * fov, t1, t1)       # sum_k (sum_c (H^k_c - 2F^k_c) t^c_i) t^a_k
-    t1terms["vovv"] = 0.5 * es("akcd,ikcd->ia", vovv, ta)             # 1/2 sum_kcd V^{ak}_{cd} tau^{cd}_{ik}
-    t1terms["ooov"] = 0.5 * es("klic,klca->ia", ooov, ta)             # 1/2 sum_klc V^{kl}_{ic} tau^{ca}_{kl}
-    t1terms["vovo"] = -es("akci,kc->ia", vovo, t1)                    # - sum_kc V^{ak}_{ci} t^c_k
+    t1terms = _singles_terms(f, V, t1, t2, I)
     S1 = sum(t1terms.values())
     if parts is not None:
         parts.update(I)
+        parts.update({"S2_" + k: v for k, v in terms.items()})
+        parts.update({"S1_" + k: v for k, v in t1terms.items()})
+    return S1, S2
+
+
+def residual_cc2(f: np.ndarray, V: dict, t1: np.ndarray, t2: np.ndarray, parts: dict | None = None):
+    """CC2 residuals (appendix "Working equations for CC2 amplitude equations").
+
+    S^a_i is the singles residual of Appendix A, unchanged. S^{ab}_{ij} is the CC2 doubles
+    equation: the driver V^{ab}_{ij}, four terms in t1 with the CC2 intermediates W^{ab}_{ej},
+    W^{mb}_{ij}, W^{mn}_{ij}, W^{ab}_{ef}, and the Fock terms in t2. The sums over m<n and
+    e<f are taken as half the full sums; their summands are symmetric under m <-> n and e <-> f.
+    The notation and readings are those of ``residual``: V^{pq}_{rs} = <pq||rs>, f^p_q = f[p,q].
+    Returns (S1[i,a], S2[i,j,a,b]).
+    """
+    o = t1.shape[0]
+    oooo, ooov, oovv, vovo, vovv = V["oooo"], V["ooov"], V["oovv"], V["vovo"], V["vovv"]
+    fo, fv = f[:o, :o], f[o:, o:]
+    es = lambda s, *ops: np.einsum(s, *ops, optimize=True)
+    # the blocks with the labels of the CC2 equations
+    v_abij = np.conj(oovv)                              # V^{ab}_{ij} = conj <ij||ab>, as [i,j,a,b]
+    v_abej = np.conj(vovv).transpose(2, 3, 0, 1)        # V^{ab}_{ej} = conj <ej||ab>, as [a,b,e,j]
+    v_mbij = np.conj(ooov).transpose(2, 3, 0, 1)        # V^{mb}_{ij} = conj <ij||mb>, as [m,b,i,j]
+    v_mbej = -vovo.transpose(1, 0, 2, 3)                # V^{mb}_{ej} = -<bm||ej>, as [m,b,e,j]
+
+    # W^{mn}_{ij} = V^{mn}_{ij} + sum_e P^-_ij t^e_j V^{mn}_{ie} + 1/4 sum_ef P^-_ij t^e_i t^f_j V^{mn}_{ef}
+    w_mnij = (oooo + p_minus(es("je,mnie->mnij", t1, ooov), 2, 3)
+              + 0.25 * p_minus(es("ie,jf,mnef->mnij", t1, t1, oovv), 2, 3))
+    # W^{ab}_{ef} = V^{ab}_{ef} - sum_m P^-_ab t^b_m V^{am}_{ef} + 1/4 sum_mn P^-_ab t^a_m t^b_n V^{mn}_{ef}
+    w_abef = (V["vvvv"] - p_minus(es("mb,amef->abef", t1, vovv), 0, 1)
+              + 0.25 * p_minus(es("ma,nb,mnef->abef", t1, t1, oovv), 0, 1))
+    # W^{ab}_{ej} = V^{ab}_{ej} - 1/2 sum_m P^-_ab t^a_m V^{mb}_{ej}
+    w_abej = v_abej - 0.5 * p_minus(es("ma,mbej->abej", t1, v_mbej), 0, 1)
+    # W^{mb}_{ij} = V^{mb}_{ij} + 1/2 sum_e P^-_ij t^e_i V^{mb}_{ej}
+    w_mbij = v_mbij + 0.5 * p_minus(es("ie,mbej->mbij", t1, v_mbej), 2, 3)
+
+    terms = {}
+    terms["driver"] = v_abij                                                      # V^{ab}_{ij}
+    terms["t1_abej"] = p_minus(es("ie,abej->ijab", t1, w_abej), 0, 1)             # sum_e P^-_ij t^e_i W^{ab}_{ej}
+    terms["t1_mbij"] = -p_minus(es("ma,mbij->ijab", t1, w_mbij), 2, 3)            # - sum_m P^-_ab t^a_m W^{mb}_{ij}
+    terms["t1t1_mnij"] = 0.5 * p_minus(es("ma,nb,mnij->ijab", t1, t1, w_mnij), 2, 3)  # sum_{m<n} P^-_ab t^a_m t^b_n W^{mn}_{ij}
+    terms["t1t1_abef"] = 0.5 * p_minus(es("ie,jf,abef->ijab", t1, t1, w_abef), 0, 1)  # sum_{e<f} P^-_ij t^e_i t^f_j W^{ab}_{ef}
+    terms["f_vv"] = p_minus(es("be,ijae->ijab", fv, t2), 2, 3)                    # sum_e P^-_ab f^b_e t^{ae}_{ij}
+    terms["f_oo"] = -p_minus(es("mj,imab->ijab", fo, t2), 0, 1)                   # - sum_m P^-_ij f^m_j t^{ab}_{im}
+    S2 = sum(terms.values())
+    I = intermediates(f, V, t1, t2)
+    t1terms = _singles_terms(f, V, t1, t2, I)
+    S1 = sum(t1terms.values())
+    if parts is not None:
         parts.update({"S2_" + k: v for k, v in terms.items()})
         parts.update({"S1_" + k: v for k, v in t1terms.items()})
     return S1, S2
@@ -309,7 +369,8 @@ def solve(f: np.ndarray, V: dict, o: int, v: int, max_iter: int = 50, tol: float
           diis_dim: int = 8, diis_start: int = 2, shift: float = 0.0, t_init=None,
           callback=None, method: str = "ccsd"):
     """CCSD iterations from the MP2 guess (or ``t_init``); method="ccd" holds t1 at zero (CCD:
-    the doubles equations of Appendix A with T1 = 0, the variant the paper also times).
+    the doubles equations of Appendix A with T1 = 0, the variant the paper also times);
+    method="cc2" iterates the CC2 residuals (``residual_cc2``).
 
     Each iteration: S = residual(t); d = S/D; norm = max|d|; t <- t + d; then, if DIIS is on
     and the iteration number is >= diis_start with >= 2 stored vectors, t <- sum_i c_i t_i.
@@ -322,14 +383,15 @@ def solve(f: np.ndarray, V: dict, o: int, v: int, max_iter: int = 50, tol: float
         t1, t2 = (np.array(x, dtype=np.complex128) for x in t_init)
     if method == "ccd":
         t1 = np.zeros_like(t1)
-    elif method != "ccsd":
-        raise ValueError("method must be 'ccsd' or 'ccd'")
+    elif method not in ("ccsd", "cc2"):
+        raise ValueError("method must be 'ccsd', 'ccd' or 'cc2'")
+    res = residual_cc2 if method == "cc2" else residual
     diis = DIIS(diis_dim) if diis_dim > 0 else None
     norm = np.inf
     it = 0
     converged = False
     for it in range(1, max_iter + 1):
-        S1, S2 = residual(f, V, t1, t2)
+        S1, S2 = res(f, V, t1, t2)
         d1, d2 = S1 / D1, S2 / D2
         if method == "ccd":
             d1 = np.zeros_like(d1)
