@@ -79,9 +79,18 @@ typedef enum {
 
 typedef enum {
   CCSD_METHOD_CCSD = 0, /* singles and doubles (Appendix A) */
-  CCSD_METHOD_CCD = 1   /* doubles only: the same doubles equations with t1 held at zero (its
+  CCSD_METHOD_CCD = 1,  /* doubles only: the same doubles equations with t1 held at zero (its
                            update is zeroed each iteration; the singles terms are evaluated and
                            vanish); the variant the paper also times */
+  CCSD_METHOD_CC2 = 2   /* CC2 (appendix "Working equations for CC2 amplitude equations"): the
+                           singles equations of Appendix A unchanged, the doubles equation
+                           S^{ab}_{ij} = <ab||ij>~ + P^-_ab sum_e f_be t^{ae}_{ij}
+                           - P^-_ij sum_m f_mj t^{ab}_{im}, where <ab||ij>~ is the integral of
+                           exp(-T1) H exp(T1). It is evaluated from the T1-dressed DF factors
+                           (1 - t1) B^Q (1 + t1), which reproduce the appendix's W terms exactly.
+                           Needs DF integrals (CCSD_ERR_UNSUPPORTED otherwise); <ab||cd> is
+                           never built. ccsd_get_tensor then has only "tau", "Hvv", "Hoo" and
+                           "Hov". */
 } ccsd_method;
 
 typedef struct {

@@ -20,7 +20,7 @@ STATUS = {0: "CCSD_OK", 1: "CCSD_ERR_ARG", 2: "CCSD_ERR_OOM", 3: "CCSD_ERR_CUDA"
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NOT_CONVERGED, ERR_DIVERGED, ERR_TIMEOUT, ERR_UNSUPPORTED = range(8)
 INT_DF, INT_FULL = 0, 1
 PREC_FP64, PREC_SPLIT = 0, 1
-METHOD_CCSD, METHOD_CCD = 0, 1
+METHOD_CCSD, METHOD_CCD, METHOD_CC2 = 0, 1, 2
 
 
 class ccsd_z(C.Structure):

@@ -71,6 +71,9 @@ struct ccsd_ctx {
   // store_w = 0: B^Q over virtuals, and per-block (ac|bd) and packed <ab||cd> rows
   z *Bvv = nullptr, *Dblk = nullptr, *Wblk = nullptr;
   SliceSet Bsl;  // split mode: digits of B^Q_vv as rows (a, c) over Q, cut once (both operands of the rebuild)
+  // CC2: the DF factor blocks B^Q_vo, B^Q_oo, B^Q_ov (B^Q_vv is Bvv) and the per-evaluation dressed
+  // factors Bt[Q][a][i] = ((1 - t1) B^Q (1 + t1))_ai and Dt[Q][j][i] = (B^Q (1 + t1))_ji
+  z *c2_Bvo = nullptr, *c2_Boo = nullptr, *c2_Bov = nullptr, *c2_Bt = nullptr, *c2_Dt = nullptr;
   int df_block = 0;
   std::function<bool(const ZGemmArgs&)> routes_split;
   // iteration state
@@ -624,10 +627,13 @@ cudaError_t split_gemm_chunked(ccsd_ctx* ctx, const ZGemmArgs& g, cudaStream_t s
 // ---------------------------------------------------------------------------
 ccsd_status build_residual_plan(ccsd_ctx* ctx) {
   const int o = ctx->o, v = ctx->v;
+  // CC2: the singles of Appendix A with their intermediates tau, H^a_c, H^k_i, H^k_c, and the CC2
+  // doubles; the CCSD-only intermediates and doubles terms are not planned
+  const bool cc2 = ctx->opts.method == CCSD_METHOD_CC2;
   const int64_t Po = ctx->Po, Pv = ctx->Pv;
   // rows a of <ak||cd> unpacked at a time for the H^{ak}_{ci} term (at most about 1 GB)
   ctx->vblk_rows = std::max<int64_t>(1, std::min<int64_t>(v, (int64_t)(1.0e9 / (16.0 * o * (double)v * v))));
-  CS(dalloc(ctx, &ctx->vblk, ctx->vblk_rows * o * (int64_t)v * v));
+  if (!cc2) CS(dalloc(ctx, &ctx->vblk, ctx->vblk_rows * o * (int64_t)v * v));
   Plan* P = new Plan(o, v, &ctx->scratch, ctx->stream);
   ctx->plan = P;
   // In split mode a single GEMM of at least split_min_flops goes to the tensor-core digit
@@ -671,246 +677,345 @@ ccsd_status build_residual_plan(ccsd_ctx* ctx) {
     if (e != cudaSuccess) return e;
     return pack_pairs(tau, taupk, o, v, 1, s);
   });
-  // X^{ad}_{li} = 1/2 t^{ad}_{li} + t^a_l t^d_i (the pair amplitude of the H^{ak}_{ci} term)
-  P->custom("Hvoov", [=](cudaStream_t s) { return tau_build(t1, t2, X, o, v, 0.5, 1.0, 0, s); });
+  if (!cc2) {
+    // X^{ad}_{li} = 1/2 t^{ad}_{li} + t^a_l t^d_i (the pair amplitude of the H^{ak}_{ci} term)
+    P->custom("Hvoov", [=](cudaStream_t s) { return tau_build(t1, t2, X, o, v, 0.5, 1.0, 0, s); });
+  }
 
   // H^a_c = F^a_c + 1/2 sum_kld V^{kl}_{cd} tau^{da}_{kl}
   P->add("Hvv", W(ctx->Hvv, "ac"), one, V(ctx->fvv, "ac"), false, 0.0);
   P->contract("Hvv", W(ctx->Hvv, "ac"), half, V(ctx->oovv, "klcd"), false, W(tau, "klda"), false, 1.0);
-  // T[i][a][k][c] = sum_d V^{ak}_{cd} t^d_i (the second term of H^{ak}_{ci}) first, into Hr: the rows of
-  // <ak||cd> are unpacked from vovv_pk block by block of a (the dense vovv is never stored) and each
-  // block is one GEMM writing the columns (a, k, c) of its a range in every row i.
-  {
-    const int64_t vb = ctx->vblk_rows, Pv_ = Pv;
-    for (int64_t a0 = 0; a0 < v; a0 += vb) {
-      ZGemmArgs g;
-      g.M = o;
-      g.N = std::min<int64_t>(vb, v - a0) * o * v;
-      g.K = v;
-      g.transB = 1;
-      P->note_gemm(g);
-    }
-    z *vpk = ctx->vovv_pk, *vblk = ctx->vblk, *hr = ctx->Hr;
-    P->custom("Hvoov:gemm", [ctx, o, v, vb, Pv_, vpk, vblk, hr, t1](cudaStream_t s) {
-      const GemmFn& gemm = ctx->plan->gemm_fn();
-      cudaError_t e = cudaSuccess;
-      for (int64_t a0 = 0; a0 < v && e == cudaSuccess; a0 += vb) {
-        const int64_t na = std::min<int64_t>(vb, v - a0);
-        UnpackArgs u;  // vblk[(a - a0, k)][c][d] = <ak||cd>
-        u.in = vpk + a0 * o * Pv_;
-        u.out = vblk;
-        u.n1 = na * o;
-        u.n2 = v;
-        u.beta = 0.0;
-        e = unpack_pairs(u, s);
-        if (e != cudaSuccess) break;
-        ZGemmArgs g;  // Hr[i][(a,k,c)] = sum_d t1[i][d] vblk[(a,k,c)][d]
+  if (!cc2) {
+    // T[i][a][k][c] = sum_d V^{ak}_{cd} t^d_i (the second term of H^{ak}_{ci}) first, into Hr: the rows of
+    // <ak||cd> are unpacked from vovv_pk block by block of a (the dense vovv is never stored) and each
+    // block is one GEMM writing the columns (a, k, c) of its a range in every row i.
+    {
+      const int64_t vb = ctx->vblk_rows, Pv_ = Pv;
+      for (int64_t a0 = 0; a0 < v; a0 += vb) {
+        ZGemmArgs g;
         g.M = o;
-        g.N = na * o * v;
+        g.N = std::min<int64_t>(vb, v - a0) * o * v;
         g.K = v;
-        g.A = t1;
-        g.lda = v;
-        g.B = vblk;
-        g.ldb = v;
         g.transB = 1;
-        g.C = hr + a0 * o * v;
-        g.ldc = (int64_t)v * o * v;
-        e = gemm(g, s);
+        P->note_gemm(g);
       }
-      return e;
-    }, 8.0 * o * (double)v * o * v * v);
+      z *vpk = ctx->vovv_pk, *vblk = ctx->vblk, *hr = ctx->Hr;
+      P->custom("Hvoov:gemm", [ctx, o, v, vb, Pv_, vpk, vblk, hr, t1](cudaStream_t s) {
+        const GemmFn& gemm = ctx->plan->gemm_fn();
+        cudaError_t e = cudaSuccess;
+        for (int64_t a0 = 0; a0 < v && e == cudaSuccess; a0 += vb) {
+          const int64_t na = std::min<int64_t>(vb, v - a0);
+          UnpackArgs u;  // vblk[(a - a0, k)][c][d] = <ak||cd>
+          u.in = vpk + a0 * o * Pv_;
+          u.out = vblk;
+          u.n1 = na * o;
+          u.n2 = v;
+          u.beta = 0.0;
+          e = unpack_pairs(u, s);
+          if (e != cudaSuccess) break;
+          ZGemmArgs g;  // Hr[i][(a,k,c)] = sum_d t1[i][d] vblk[(a,k,c)][d]
+          g.M = o;
+          g.N = na * o * v;
+          g.K = v;
+          g.A = t1;
+          g.lda = v;
+          g.B = vblk;
+          g.ldb = v;
+          g.transB = 1;
+          g.C = hr + a0 * o * v;
+          g.ldc = (int64_t)v * o * v;
+          e = gemm(g, s);
+        }
+        return e;
+      }, 8.0 * o * (double)v * o * v * v);
+    }
+    // G^a_c = H^a_c + sum_kd V^{ak}_{cd} t^d_k - sum_k F^k_c t^a_k; the middle term is the trace
+    // sum_k T[k][a][k][c] of the product above
+    P->add("Gvv", W(ctx->Gvv, "ac"), one, W(ctx->Hvv, "ac"), false, 0.0);
+    {
+      z *hr = ctx->Hr, *gvv = ctx->Gvv;
+      P->custom("Gvv", [=](cudaStream_t s) { return trace_ik(hr, o, v, gvv, 1.0, 1.0, s); });
+    }
+    P->contract("Gvv", W(ctx->Gvv, "ac"), mone, V(ctx->fov, "kc"), false, W(t1, "ka"), false, 1.0);
   }
-  // G^a_c = H^a_c + sum_kd V^{ak}_{cd} t^d_k - sum_k F^k_c t^a_k; the middle term is the trace
-  // sum_k T[k][a][k][c] of the product above
-  P->add("Gvv", W(ctx->Gvv, "ac"), one, W(ctx->Hvv, "ac"), false, 0.0);
-  {
-    z *hr = ctx->Hr, *gvv = ctx->Gvv;
-    P->custom("Gvv", [=](cudaStream_t s) { return trace_ik(hr, o, v, gvv, 1.0, 1.0, s); });
-  }
-  P->contract("Gvv", W(ctx->Gvv, "ac"), mone, V(ctx->fov, "kc"), false, W(t1, "ka"), false, 1.0);
   // H^k_i = -F^k_i + 1/2 sum_lcd V^{kl}_{cd} tau^{cd}_{li}
   P->add("Hoo", W(ctx->Hoo, "ki"), mone, V(ctx->foo, "ki"), false, 0.0);
   P->contract("Hoo", W(ctx->Hoo, "ki"), half, V(ctx->oovv, "klcd"), false, W(tau, "licd"), false, 1.0);
-  // G^k_i = H^k_i - sum_lc V^{kl}_{ic} t^c_l - sum_c F^k_c t^c_i
-  P->add("Goo", W(ctx->Goo, "ki"), one, W(ctx->Hoo, "ki"), false, 0.0);
-  P->contract("Goo", W(ctx->Goo, "ki"), mone, V(ctx->ooov, "klic"), false, W(t1, "lc"), false, 1.0);
-  P->contract("Goo", W(ctx->Goo, "ki"), mone, V(ctx->fov, "kc"), false, W(t1, "ic"), false, 1.0);
+  if (!cc2) {
+    // G^k_i = H^k_i - sum_lc V^{kl}_{ic} t^c_l - sum_c F^k_c t^c_i
+    P->add("Goo", W(ctx->Goo, "ki"), one, W(ctx->Hoo, "ki"), false, 0.0);
+    P->contract("Goo", W(ctx->Goo, "ki"), mone, V(ctx->ooov, "klic"), false, W(t1, "lc"), false, 1.0);
+    P->contract("Goo", W(ctx->Goo, "ki"), mone, V(ctx->fov, "kc"), false, W(t1, "ic"), false, 1.0);
+  }
   // H^k_c = F^k_c + sum_ld V^{kl}_{cd} t^d_l
   P->add("Hov", W(ctx->Hov, "kc"), one, V(ctx->fov, "kc"), false, 0.0);
   P->contract("Hov", W(ctx->Hov, "kc"), one, V(ctx->oovv, "klcd"), false, W(t1, "ld"), false, 1.0);
-  // H^{ak}_{ci} (stored [i][a][k][c]) = V^{ak}_{ci} + sum_d V^{ak}_{cd} t^d_i - sum_l V^{kl}_{ic} t^a_l
-  //                                   + sum_ld V^{kl}_{cd} (1/2 t^{ad}_{li} + t^a_l t^d_i)
-  P->add("Hvoov", W(ctx->Hr, "iakc"), one, V(ctx->J, "iakc"), false, 1.0);
-  P->contract("Hvoov", W(ctx->Hr, "iakc"), mone, V(ctx->ooov, "klic"), false, W(t1, "la"), false, 1.0);
-  P->contract("Hvoov", W(ctx->Hr, "iakc"), one, W(X, "liad"), false, V(ctx->oovv, "klcd"), false, 1.0);
-  // C^{kb}_{ij} = V^{ij+}_{kb} + P^-_ij sum_c V^{bk}_{ci} t^c_j - 1/2 sum_cd V^{bk}_{cd} tau^{cd}_{ij}
-  P->add("C", W(ctx->C, "kbij"), one, V(ctx->Cinit, "kbij"), false, 0.0);
-  // Yovoo[i][b][k][j] = sum_c V^{bk}_{ci} t^c_j = sum_c J[i][b][k][c] t^c_j
-  P->contract("C", W(ctx->Yovoo, "ibkj"), one, V(ctx->J, "ibkc"), false, W(t1, "jc"), false, 0.0);
-  P->add("C", W(ctx->C, "kbij"), one, W(ctx->Yovoo, "ibkj"), false, 1.0);
-  P->add("C", W(ctx->C, "kbij"), mone, W(ctx->Yovoo, "jbki"), false, 1.0);
-  {
-    ZGemmArgs g;  // Ypk[(b,k)][P(ij)] = sum_{c<d} V^{bk}_{cd} tau^{cd}_{ij}
-    g.M = (int64_t)v * o;
-    g.N = Po;
-    g.K = Pv;
-    g.A = ctx->vovv_pk;
-    g.lda = Pv;
-    g.B = taupk;
-    g.ldb = Pv;
-    g.transB = 1;
-    g.C = ctx->Ypk;
-    g.ldc = Po;
-    P->gemm("C:gemm", g);
-    z *ypk = ctx->Ypk, *yf = ctx->Yfull;
-    P->custom("C:unpack", [=](cudaStream_t s) {
-      UnpackArgs u;
-      u.in = ypk;
-      u.out = yf;
-      u.n1 = (int64_t)v * o;
-      u.n2 = o;
-      u.alpha = mone;
-      u.beta = 0.0;
-      return unpack_pairs(u, s);
-    });
-    P->add("C", W(ctx->C, "kbij"), one, W(ctx->Yfull, "bkij"), false, 1.0);
-  }
-  // A^{kl}_{ij} = V^{kl}_{ij} + P^-_ij sum_c V^{kl}_{ic} t^c_j + 1/2 sum_cd V^{kl}_{cd} tau^{cd}_{ij}
-  P->add("A", W(ctx->Afull, "klij"), one, V(ctx->oooo, "klij"), false, 0.0);
-  P->contract("A", W(ctx->Yoooo, "klij"), one, V(ctx->ooov, "klic"), false, W(t1, "jc"), false, 0.0);
-  P->add("A", W(ctx->Afull, "klij"), one, W(ctx->Yoooo, "klij"), false, 1.0);
-  P->add("A", W(ctx->Afull, "klij"), mone, W(ctx->Yoooo, "klji"), false, 1.0);
-  {
-    z *af = ctx->Afull, *apk = ctx->Apk;
-    P->custom("A:pack", [=](cudaStream_t s) { return pack_pairs(af, apk, o, o, 1, s); });
-    ZGemmArgs g;  // Apk[P(kl)][P(ij)] += sum_{c<d} V^{kl}_{cd} tau^{cd}_{ij}
-    g.M = Po;
-    g.N = Po;
-    g.K = Pv;
-    g.A = ctx->oovv_pk;
-    g.lda = Pv;
-    g.B = taupk;
-    g.ldb = Pv;
-    g.transB = 1;
-    g.C = ctx->Apk;
-    g.ldc = Po;
-    g.beta = one;
-    P->gemm("A:gemm", g);
-  }
-
-  // S^{ab}_{ij}: driver V^{ij+}_{ab}
-  P->add("driver", W(ctx->S2, "ijab"), one, V(ctx->oovv, "ijab"), true, 0.0);
-  // ring: sum_kc P^-_ij P^-_ab (H^{ak}_{ci} t^{cb}_{jk}),  R[i][a][j][b] = sum_kc H^{ak}_{ci} t^{cb}_{jk}
-  P->contract("ring", W(ctx->R, "iajb"), one, W(ctx->Hr, "iakc"), false, W(t2, "jkcb"), false, 0.0);
-  P->add("ring", W(ctx->S2, "ijab"), one, W(ctx->R, "iajb"), false, 1.0);
-  P->add("ring", W(ctx->S2, "ijab"), mone, W(ctx->R, "jaib"), false, 1.0);
-  P->add("ring", W(ctx->S2, "ijab"), mone, W(ctx->R, "ibja"), false, 1.0);
-  P->add("ring", W(ctx->S2, "ijab"), one, W(ctx->R, "jbia"), false, 1.0);
-  // sum_k P^-_ji G^k_j t^{ab}_{ik}:  W1[j][i][a][b] = sum_k G^k_j t^{ab}_{ik}
-  P->contract("goo", W(ctx->R, "jiab"), one, W(ctx->Goo, "kj"), false, W(t2, "ikab"), false, 0.0);
-  P->add("goo", W(ctx->S2, "ijab"), one, W(ctx->R, "jiab"), false, 1.0);
-  P->add("goo", W(ctx->S2, "ijab"), mone, W(ctx->R, "ijab"), false, 1.0);
-  // sum_c P^-_ij (V^{cj+}_{ab} t^c_i):  W1[i][j][a][b] = sum_c t^c_i conj(V^{cj}_{ab}); (a, b) is the
-  // antisymmetric pair of both, so the product is formed packed, straight from vovv_pk
-  // (W1pk[i][(j, P(a,b))] in R) and added to S2 with (i, j) antisymmetrised in one pass
-  {
-    ZGemmArgs g;
-    g.M = o;
-    g.N = (int64_t)o * Pv;
-    g.K = v;
-    g.A = t1;
-    g.lda = v;
-    g.B = ctx->vovv_pk;
-    g.ldb = (int64_t)o * Pv;
-    g.conjB = 1;
-    g.C = ctx->R;
-    g.ldc = (int64_t)o * Pv;
-    P->gemm("vt1:gemm", g);
-    z *w1pk = ctx->R, *s2 = ctx->S2;
-    P->custom("vt1", [=](cudaStream_t s) {
-      UnpackArgs u;  // S2[i][j][a][b] += W1[i][j][a][b] - W1[j][i][a][b]
-      u.in = w1pk;
-      u.out = s2;
-      u.n1 = (int64_t)o * o;
-      u.n2 = v;
-      u.anti_rows = o;
-      u.beta = 1.0;
-      return unpack_pairs(u, s);
-    });
-  }
-  // sum_c P^-_ab G^a_c t^{cb}_{ij}:  W1[a][i][j][b] = sum_c G^a_c t^{cb}_{ij}
-  P->contract("gvv", W(ctx->R, "aijb"), one, W(ctx->Gvv, "ac"), false, W(t2, "ijcb"), false, 0.0);
-  P->add("gvv", W(ctx->S2, "ijab"), one, W(ctx->R, "aijb"), false, 1.0);
-  P->add("gvv", W(ctx->S2, "ijab"), mone, W(ctx->R, "bija"), false, 1.0);
-  // sum_k P^-_ab (C^{ka}_{ij} t^b_k):  W1[a][i][j][b] = sum_k C^{ka}_{ij} t^b_k
-  P->contract("ct1", W(ctx->R, "aijb"), one, W(ctx->C, "kaij"), false, W(t1, "kb"), false, 0.0);
-  P->add("ct1", W(ctx->S2, "ijab"), one, W(ctx->R, "aijb"), false, 1.0);
-  P->add("ct1", W(ctx->S2, "ijab"), mone, W(ctx->R, "bija"), false, 1.0);
-  // 1/2 sum_kl A^{kl}_{ij} tau^{ab}_{kl}  (packed: sum_{k<l})
-  {
-    ZGemmArgs g;  // Hpk[P(ij)][P(ab)] = sum_{k<l} A^{kl}_{ij} tau^{ab}_{kl}
-    g.M = Po;
-    g.N = Pv;
-    g.K = Po;
-    g.A = ctx->Apk;
-    g.lda = Po;
-    g.transA = 1;
-    g.B = taupk;
-    g.ldb = Pv;
-    g.C = ctx->Hpk;
-    g.ldc = Pv;
-    P->gemm("hole:gemm", g);
-    z *hpk = ctx->Hpk, *s2 = ctx->S2;
-    P->custom("hole:unpack", [=](cudaStream_t s) {
-      UnpackArgs u;
-      u.in = hpk;
-      u.out = s2;
-      u.n1 = o;
-      u.n2 = v;
-      u.unpack_rows = 1;
-      return unpack_pairs(u, s);
-    });
-  }
-  // particle-particle ladder 1/2 sum_cd V^{ab}_{cd} tau^{cd}_{ij}  (packed: sum_{c<d})
-  {
-    ZGemmArgs g;  // Lpk[P(ij)][P(ab)] = sum_{c<d} tau^{cd}_{ij} <ab||cd>
-    g.M = Po;
-    g.N = Pv;
-    g.K = Pv;
-    g.A = taupk;
-    g.lda = Pv;
-    g.B = ctx->Wpk;
-    g.ldb = Pv;
-    g.transB = 1;
-    g.C = ctx->Lpk;
-    g.ldc = Pv;
-    if (!ctx->opts.store_w) {
-      CS(plan_df_ladder(ctx, P));
-    } else if (ctx->use_split) {
-      // W digits were cut once at creation; only tau is sliced per evaluation
-      P->note_aux_bytes(slice_bytes(Po, Pv, ctx->split) + split_part_bytes(Po, Pv, Pv, ctx->split));
-      z* lpk = ctx->Lpk;
-      P->custom("ladder:gemm", [ctx, taupk, lpk, Po, Pv](cudaStream_t s) {
-        cudaError_t e = make_slices(taupk, Po, Pv, Pv, 0, 0, ctx->split, ctx->tausl, ctx->split_ws, s);
-        uint8_t* part = static_cast<uint8_t*>(ctx->split_ws) + slice_bytes(Po, Pv, ctx->split);
-        if (e == cudaSuccess)
-          e = split_gemm(ctx->tausl, ctx->Wsl, lpk, Pv, zmake(1, 0), zmake(0, 0), ctx->split_err, part,
-                         split_part_bytes(Po, Pv, Pv, ctx->split), s);
-        return e;
-      }, 8.0 * (double)Po * (double)Pv * (double)Pv);
-    } else {
-      P->gemm("ladder:gemm", g);
+  if (!cc2) {
+    // H^{ak}_{ci} (stored [i][a][k][c]) = V^{ak}_{ci} + sum_d V^{ak}_{cd} t^d_i - sum_l V^{kl}_{ic} t^a_l
+    //                                   + sum_ld V^{kl}_{cd} (1/2 t^{ad}_{li} + t^a_l t^d_i)
+    P->add("Hvoov", W(ctx->Hr, "iakc"), one, V(ctx->J, "iakc"), false, 1.0);
+    P->contract("Hvoov", W(ctx->Hr, "iakc"), mone, V(ctx->ooov, "klic"), false, W(t1, "la"), false, 1.0);
+    P->contract("Hvoov", W(ctx->Hr, "iakc"), one, W(X, "liad"), false, V(ctx->oovv, "klcd"), false, 1.0);
+    // C^{kb}_{ij} = V^{ij+}_{kb} + P^-_ij sum_c V^{bk}_{ci} t^c_j - 1/2 sum_cd V^{bk}_{cd} tau^{cd}_{ij}
+    P->add("C", W(ctx->C, "kbij"), one, V(ctx->Cinit, "kbij"), false, 0.0);
+    // Yovoo[i][b][k][j] = sum_c V^{bk}_{ci} t^c_j = sum_c J[i][b][k][c] t^c_j
+    P->contract("C", W(ctx->Yovoo, "ibkj"), one, V(ctx->J, "ibkc"), false, W(t1, "jc"), false, 0.0);
+    P->add("C", W(ctx->C, "kbij"), one, W(ctx->Yovoo, "ibkj"), false, 1.0);
+    P->add("C", W(ctx->C, "kbij"), mone, W(ctx->Yovoo, "jbki"), false, 1.0);
+    {
+      ZGemmArgs g;  // Ypk[(b,k)][P(ij)] = sum_{c<d} V^{bk}_{cd} tau^{cd}_{ij}
+      g.M = (int64_t)v * o;
+      g.N = Po;
+      g.K = Pv;
+      g.A = ctx->vovv_pk;
+      g.lda = Pv;
+      g.B = taupk;
+      g.ldb = Pv;
+      g.transB = 1;
+      g.C = ctx->Ypk;
+      g.ldc = Po;
+      P->gemm("C:gemm", g);
+      z *ypk = ctx->Ypk, *yf = ctx->Yfull;
+      P->custom("C:unpack", [=](cudaStream_t s) {
+        UnpackArgs u;
+        u.in = ypk;
+        u.out = yf;
+        u.n1 = (int64_t)v * o;
+        u.n2 = o;
+        u.alpha = mone;
+        u.beta = 0.0;
+        return unpack_pairs(u, s);
+      });
+      P->add("C", W(ctx->C, "kbij"), one, W(ctx->Yfull, "bkij"), false, 1.0);
     }
-    z *lpk = ctx->Lpk, *s2 = ctx->S2;
-    P->custom("ladder:unpack", [=](cudaStream_t s) {
-      UnpackArgs u;
-      u.in = lpk;
-      u.out = s2;
-      u.n1 = o;
-      u.n2 = v;
-      u.unpack_rows = 1;
-      return unpack_pairs(u, s);
-    });
+    // A^{kl}_{ij} = V^{kl}_{ij} + P^-_ij sum_c V^{kl}_{ic} t^c_j + 1/2 sum_cd V^{kl}_{cd} tau^{cd}_{ij}
+    P->add("A", W(ctx->Afull, "klij"), one, V(ctx->oooo, "klij"), false, 0.0);
+    P->contract("A", W(ctx->Yoooo, "klij"), one, V(ctx->ooov, "klic"), false, W(t1, "jc"), false, 0.0);
+    P->add("A", W(ctx->Afull, "klij"), one, W(ctx->Yoooo, "klij"), false, 1.0);
+    P->add("A", W(ctx->Afull, "klij"), mone, W(ctx->Yoooo, "klji"), false, 1.0);
+    {
+      z *af = ctx->Afull, *apk = ctx->Apk;
+      P->custom("A:pack", [=](cudaStream_t s) { return pack_pairs(af, apk, o, o, 1, s); });
+      ZGemmArgs g;  // Apk[P(kl)][P(ij)] += sum_{c<d} V^{kl}_{cd} tau^{cd}_{ij}
+      g.M = Po;
+      g.N = Po;
+      g.K = Pv;
+      g.A = ctx->oovv_pk;
+      g.lda = Pv;
+      g.B = taupk;
+      g.ldb = Pv;
+      g.transB = 1;
+      g.C = ctx->Apk;
+      g.ldc = Po;
+      g.beta = one;
+      P->gemm("A:gemm", g);
+    }
+
+    // S^{ab}_{ij}: driver V^{ij+}_{ab}
+    P->add("driver", W(ctx->S2, "ijab"), one, V(ctx->oovv, "ijab"), true, 0.0);
+    // ring: sum_kc P^-_ij P^-_ab (H^{ak}_{ci} t^{cb}_{jk}),  R[i][a][j][b] = sum_kc H^{ak}_{ci} t^{cb}_{jk}
+    P->contract("ring", W(ctx->R, "iajb"), one, W(ctx->Hr, "iakc"), false, W(t2, "jkcb"), false, 0.0);
+    P->add("ring", W(ctx->S2, "ijab"), one, W(ctx->R, "iajb"), false, 1.0);
+    P->add("ring", W(ctx->S2, "ijab"), mone, W(ctx->R, "jaib"), false, 1.0);
+    P->add("ring", W(ctx->S2, "ijab"), mone, W(ctx->R, "ibja"), false, 1.0);
+    P->add("ring", W(ctx->S2, "ijab"), one, W(ctx->R, "jbia"), false, 1.0);
+    // sum_k P^-_ji G^k_j t^{ab}_{ik}:  W1[j][i][a][b] = sum_k G^k_j t^{ab}_{ik}
+    P->contract("goo", W(ctx->R, "jiab"), one, W(ctx->Goo, "kj"), false, W(t2, "ikab"), false, 0.0);
+    P->add("goo", W(ctx->S2, "ijab"), one, W(ctx->R, "jiab"), false, 1.0);
+    P->add("goo", W(ctx->S2, "ijab"), mone, W(ctx->R, "ijab"), false, 1.0);
+    // sum_c P^-_ij (V^{cj+}_{ab} t^c_i):  W1[i][j][a][b] = sum_c t^c_i conj(V^{cj}_{ab}); (a, b) is the
+    // antisymmetric pair of both, so the product is formed packed, straight from vovv_pk
+    // (W1pk[i][(j, P(a,b))] in R) and added to S2 with (i, j) antisymmetrised in one pass
+    {
+      ZGemmArgs g;
+      g.M = o;
+      g.N = (int64_t)o * Pv;
+      g.K = v;
+      g.A = t1;
+      g.lda = v;
+      g.B = ctx->vovv_pk;
+      g.ldb = (int64_t)o * Pv;
+      g.conjB = 1;
+      g.C = ctx->R;
+      g.ldc = (int64_t)o * Pv;
+      P->gemm("vt1:gemm", g);
+      z *w1pk = ctx->R, *s2 = ctx->S2;
+      P->custom("vt1", [=](cudaStream_t s) {
+        UnpackArgs u;  // S2[i][j][a][b] += W1[i][j][a][b] - W1[j][i][a][b]
+        u.in = w1pk;
+        u.out = s2;
+        u.n1 = (int64_t)o * o;
+        u.n2 = v;
+        u.anti_rows = o;
+        u.beta = 1.0;
+        return unpack_pairs(u, s);
+      });
+    }
+    // sum_c P^-_ab G^a_c t^{cb}_{ij}:  W1[a][i][j][b] = sum_c G^a_c t^{cb}_{ij}
+    P->contract("gvv", W(ctx->R, "aijb"), one, W(ctx->Gvv, "ac"), false, W(t2, "ijcb"), false, 0.0);
+    P->add("gvv", W(ctx->S2, "ijab"), one, W(ctx->R, "aijb"), false, 1.0);
+    P->add("gvv", W(ctx->S2, "ijab"), mone, W(ctx->R, "bija"), false, 1.0);
+    // sum_k P^-_ab (C^{ka}_{ij} t^b_k):  W1[a][i][j][b] = sum_k C^{ka}_{ij} t^b_k
+    P->contract("ct1", W(ctx->R, "aijb"), one, W(ctx->C, "kaij"), false, W(t1, "kb"), false, 0.0);
+    P->add("ct1", W(ctx->S2, "ijab"), one, W(ctx->R, "aijb"), false, 1.0);
+    P->add("ct1", W(ctx->S2, "ijab"), mone, W(ctx->R, "bija"), false, 1.0);
+    // 1/2 sum_kl A^{kl}_{ij} tau^{ab}_{kl}  (packed: sum_{k<l})
+    {
+      ZGemmArgs g;  // Hpk[P(ij)][P(ab)] = sum_{k<l} A^{kl}_{ij} tau^{ab}_{kl}
+      g.M = Po;
+      g.N = Pv;
+      g.K = Po;
+      g.A = ctx->Apk;
+      g.lda = Po;
+      g.transA = 1;
+      g.B = taupk;
+      g.ldb = Pv;
+      g.C = ctx->Hpk;
+      g.ldc = Pv;
+      P->gemm("hole:gemm", g);
+      z *hpk = ctx->Hpk, *s2 = ctx->S2;
+      P->custom("hole:unpack", [=](cudaStream_t s) {
+        UnpackArgs u;
+        u.in = hpk;
+        u.out = s2;
+        u.n1 = o;
+        u.n2 = v;
+        u.unpack_rows = 1;
+        return unpack_pairs(u, s);
+      });
+    }
+    // particle-particle ladder 1/2 sum_cd V^{ab}_{cd} tau^{cd}_{ij}  (packed: sum_{c<d})
+    {
+      ZGemmArgs g;  // Lpk[P(ij)][P(ab)] = sum_{c<d} tau^{cd}_{ij} <ab||cd>
+      g.M = Po;
+      g.N = Pv;
+      g.K = Pv;
+      g.A = taupk;
+      g.lda = Pv;
+      g.B = ctx->Wpk;
+      g.ldb = Pv;
+      g.transB = 1;
+      g.C = ctx->Lpk;
+      g.ldc = Pv;
+      if (!ctx->opts.store_w) {
+        CS(plan_df_ladder(ctx, P));
+      } else if (ctx->use_split) {
+        // W digits were cut once at creation; only tau is sliced per evaluation
+        P->note_aux_bytes(slice_bytes(Po, Pv, ctx->split) + split_part_bytes(Po, Pv, Pv, ctx->split));
+        z* lpk = ctx->Lpk;
+        P->custom("ladder:gemm", [ctx, taupk, lpk, Po, Pv](cudaStream_t s) {
+          cudaError_t e = make_slices(taupk, Po, Pv, Pv, 0, 0, ctx->split, ctx->tausl, ctx->split_ws, s);
+          uint8_t* part = static_cast<uint8_t*>(ctx->split_ws) + slice_bytes(Po, Pv, ctx->split);
+          if (e == cudaSuccess)
+            e = split_gemm(ctx->tausl, ctx->Wsl, lpk, Pv, zmake(1, 0), zmake(0, 0), ctx->split_err, part,
+                           split_part_bytes(Po, Pv, Pv, ctx->split), s);
+          return e;
+        }, 8.0 * (double)Po * (double)Pv * (double)Pv);
+      } else {
+        P->gemm("ladder:gemm", g);
+      }
+      z *lpk = ctx->Lpk, *s2 = ctx->S2;
+      P->custom("ladder:unpack", [=](cudaStream_t s) {
+        UnpackArgs u;
+        u.in = lpk;
+        u.out = s2;
+        u.n1 = o;
+        u.n2 = v;
+        u.unpack_rows = 1;
+        return unpack_pairs(u, s);
+      });
+    }
+  } else {
+    // CC2 doubles: S^{ab}_{ij} = <ab||ij>~ + P^-_ab sum_e f_be t^{ae}_{ij} - P^-_ij sum_m f_mj t^{ab}_{im},
+    // <ab||ij>~ = (ai|bj)~ - (aj|bi)~ over the T1-dressed factors Bt^Q = ((1 - t1) B^Q (1 + t1))_vo:
+    //   Bt[Q] = B_vo + B_vv t1^T - t1^T (B_oo + B_ov t1^T)
+    // (one batched GEMM over Q per product; the appendix's W intermediates expanded in t1 are the
+    // same integral)
+    const int64_t nq = ctx->naux;
+    z *bvo = ctx->c2_Bvo, *bvv = ctx->Bvv, *boo = ctx->c2_Boo, *bov = ctx->c2_Bov, *bt = ctx->c2_Bt,
+      *dt = ctx->c2_Dt;
+    const int m4 = ctx->opts.complex_4m;
+    P->custom("cc2:dress", [=](cudaStream_t s) {
+      cudaError_t e = cudaMemcpyAsync(bt, bvo, sizeof(z) * nq * v * o, cudaMemcpyDeviceToDevice, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(dt, boo, sizeof(z) * nq * o * o, cudaMemcpyDeviceToDevice, s);
+      ZGemmArgs g;  // Bt[Q][a][i] += sum_b B_vv[Q][a][b] t^b_i
+      g.M = v;
+      g.N = o;
+      g.K = v;
+      g.batch = (int)nq;
+      g.A = bvv;
+      g.lda = v;
+      g.sA = (int64_t)v * v;
+      g.B = t1;
+      g.ldb = v;
+      g.transB = 1;
+      g.C = bt;
+      g.ldc = o;
+      g.sC = (int64_t)v * o;
+      g.beta = one;
+      g.mult4 = m4;
+      if (e == cudaSuccess) e = zgemm_f64(g, s);
+      ZGemmArgs h;  // Dt[Q][j][i] += sum_b B_ov[Q][j][b] t^b_i
+      h.M = o;
+      h.N = o;
+      h.K = v;
+      h.batch = (int)nq;
+      h.A = bov;
+      h.lda = v;
+      h.sA = (int64_t)o * v;
+      h.B = t1;
+      h.ldb = v;
+      h.transB = 1;
+      h.C = dt;
+      h.ldc = o;
+      h.sC = (int64_t)o * o;
+      h.beta = one;
+      h.mult4 = m4;
+      if (e == cudaSuccess) e = zgemm_f64(h, s);
+      ZGemmArgs u;  // Bt[Q][a][i] -= sum_j t^a_j Dt[Q][j][i]
+      u.M = v;
+      u.N = o;
+      u.K = o;
+      u.batch = (int)nq;
+      u.A = t1;
+      u.lda = v;
+      u.transA = 1;
+      u.B = dt;
+      u.ldb = o;
+      u.sB = (int64_t)o * o;
+      u.C = bt;
+      u.ldc = o;
+      u.sC = (int64_t)v * o;
+      u.alpha = mone;
+      u.beta = one;
+      u.mult4 = m4;
+      if (e == cudaSuccess) e = zgemm_f64(u, s);
+      return e;
+    }, 8.0 * (double)nq * ((double)v * o * v + (double)o * o * v + (double)v * o * o));
+    {
+      ZGemmArgs g;  // R[a][i][b][j] = (ai|bj)~ = sum_Q Bt[Q][a][i] Bt[Q][b][j]
+      g.M = (int64_t)v * o;
+      g.N = (int64_t)v * o;
+      g.K = nq;
+      g.A = bt;
+      g.lda = (int64_t)v * o;
+      g.transA = 1;
+      g.B = bt;
+      g.ldb = (int64_t)v * o;
+      g.C = ctx->R;
+      g.ldc = (int64_t)v * o;
+      P->gemm("cc2:J", g);
+    }
+    P->add("cc2:driver", W(ctx->S2, "ijab"), one, W(ctx->R, "aibj"), false, 0.0);
+    P->add("cc2:driver", W(ctx->S2, "ijab"), mone, W(ctx->R, "ajbi"), false, 1.0);
+    // sum_e P^-_ab f_be t^{ae}_{ij}
+    P->contract("cc2:fvv", W(ctx->R, "ijab"), one, W(t2, "ijae"), false, V(ctx->fvv, "be"), false, 0.0);
+    P->add("cc2:fvv", W(ctx->S2, "ijab"), one, W(ctx->R, "ijab"), false, 1.0);
+    P->add("cc2:fvv", W(ctx->S2, "ijab"), mone, W(ctx->R, "ijba"), false, 1.0);
+    // - sum_m P^-_ij f_mj t^{ab}_{im}
+    P->contract("cc2:foo", W(ctx->R, "ijab"), one, W(t2, "imab"), false, V(ctx->foo, "mj"), false, 0.0);
+    P->add("cc2:foo", W(ctx->S2, "ijab"), mone, W(ctx->R, "ijab"), false, 1.0);
+    P->add("cc2:foo", W(ctx->S2, "ijab"), one, W(ctx->R, "jiab"), false, 1.0);
   }
 
   // S^a_i
@@ -1111,8 +1216,14 @@ ccsd_status create_impl(int o, int v, const double* eps, const ccsd_z* fock, ccs
   if (opts) ctx->opts = *opts;
   else ccsd_default_opts(&ctx->opts);
   if (ctx->opts.diis_dim < 0 || ctx->opts.diis_dim > 16) return set_err(ctx, CCSD_ERR_ARG, "diis_dim must be in [0, 16]");
-  if (ctx->opts.method != CCSD_METHOD_CCSD && ctx->opts.method != CCSD_METHOD_CCD)
+  if (ctx->opts.method != CCSD_METHOD_CCSD && ctx->opts.method != CCSD_METHOD_CCD &&
+      ctx->opts.method != CCSD_METHOD_CC2)
     return set_err(ctx, CCSD_ERR_ARG, "unknown method");
+  if (ctx->opts.method == CCSD_METHOD_CC2) {
+    if (kind != CCSD_INT_DF)
+      return set_err(ctx, CCSD_ERR_UNSUPPORTED, "CC2 is built on the T1-dressed DF factors: DF integrals needed");
+    ctx->opts.store_w = 0;  // CC2 never uses <ab||cd>: keep only B^Q_vv
+  }
   if (ctx->opts.precision != CCSD_PREC_FP64 && ctx->opts.precision != CCSD_PREC_SPLIT)
     return set_err(ctx, CCSD_ERR_ARG, "unknown precision mode");
   if (ctx->opts.precision == CCSD_PREC_SPLIT) {
@@ -1173,6 +1284,13 @@ ccsd_status create_impl(int o, int v, const double* eps, const ccsd_z* fock, ccs
   CS(dalloc(ctx, &ctx->J, ov * ov));
   if (ctx->opts.store_w) CS(dalloc(ctx, &ctx->Wpk, ctx->Pv * ctx->Pv));
   else CS(dalloc(ctx, &ctx->Bvv, (int64_t)naux * v * v));
+  if (ctx->opts.method == CCSD_METHOD_CC2) {
+    CS(dalloc(ctx, &ctx->c2_Bvo, (int64_t)naux * v * o));
+    CS(dalloc(ctx, &ctx->c2_Boo, (int64_t)naux * o * o));
+    CS(dalloc(ctx, &ctx->c2_Bov, (int64_t)naux * o * v));
+    CS(dalloc(ctx, &ctx->c2_Bt, (int64_t)naux * v * o));
+    CS(dalloc(ctx, &ctx->c2_Dt, (int64_t)naux * o * o));
+  }
   {
     void* dints = nullptr;
     const int64_t cnt = kind == CCSD_INT_DF ? (int64_t)naux * n * n : (int64_t)n * n * n * n;
@@ -1207,6 +1325,11 @@ ccsd_status create_impl(int o, int v, const double* eps, const ccsd_z* fock, ccs
     if (st == CCSD_OK) {
       if (kind == CCSD_INT_DF && !ctx->opts.store_w) {
         e = extract_B(ctx, (const z*)dints, 'v', 'v', ctx->Bvv, ctx->stream);
+        if (e == cudaSuccess && ctx->opts.method == CCSD_METHOD_CC2) {
+          e = extract_B(ctx, (const z*)dints, 'v', 'o', ctx->c2_Bvo, ctx->stream);
+          if (e == cudaSuccess) e = extract_B(ctx, (const z*)dints, 'o', 'o', ctx->c2_Boo, ctx->stream);
+          if (e == cudaSuccess) e = extract_B(ctx, (const z*)dints, 'o', 'v', ctx->c2_Bov, ctx->stream);
+        }
         if (e != cudaSuccess) st = set_err(ctx, CCSD_ERR_CUDA, cudaGetErrorString(e));
       } else if (kind == CCSD_INT_DF) {
         st = build_w_df(ctx, (const z*)dints);

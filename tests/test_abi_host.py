@@ -62,7 +62,7 @@ def _create(lib, o, v, eps, B, naux, opts=None):
     return st, h
 
 
-@pytest.mark.parametrize("case", ["o0", "v0", "naux0", "null_eps", "null_ints", "nonhermitian", "diis17", "bits6", "bits_x_slices", "method2"])
+@pytest.mark.parametrize("case", ["o0", "v0", "naux0", "null_eps", "null_ints", "nonhermitian", "diis17", "bits6", "bits_x_slices", "method3"])
 def test_create_rejects_bad_arguments(lib, case):
     from paper_2103_08473_gb300 import ccsd, inputs
     s = inputs.make_system(2, 3, 4, seed=1)
@@ -84,14 +84,29 @@ def test_create_rejects_bad_arguments(lib, case):
         opts = ccsd.default_opts(diis_dim=17)
     elif case == "bits6":  # e4m3 holds every integer digit only up to 16: at most 5 bits
         opts = ccsd.default_opts(precision=ccsd.PREC_SPLIT, digit_bits=6)
-    elif case == "method2":
-        opts = ccsd.default_opts(method=2)
+    elif case == "method3":
+        opts = ccsd.default_opts(method=3)
     elif case == "bits_x_slices":
         opts = ccsd.default_opts(precision=ccsd.PREC_SPLIT, digit_bits=5, slices=12)
     st, h = _create(lib, o, v, eps, B, naux, opts)
     assert st == ccsd.ERR_ARG
     assert not h.value
     assert len(lib.ccsd_last_error(None)) > 0
+
+
+def test_cc2_rejects_full_integrals_before_device_work(lib):
+    """CC2 is built on the T1-dressed DF factors: full integrals are refused up front."""
+    from paper_2103_08473_gb300 import ccsd, inputs
+    o, v = 2, 3
+    s = inputs.make_system(o, v, 4, seed=1)
+    Vf = np.ascontiguousarray(np.zeros((o + v,) * 4, np.complex128))
+    h = C.c_void_p()
+    opts = ccsd.default_opts(method=ccsd.METHOD_CC2)
+    st = lib.ccsd_create(o, v, s.eps.ctypes.data_as(C.c_void_p), None, ccsd.INT_FULL,
+                         Vf.ctypes.data_as(C.c_void_p), 0, C.byref(opts), C.byref(h))
+    assert st == ccsd.ERR_UNSUPPORTED
+    assert not h.value
+    assert b"DF" in lib.ccsd_last_error(None)
 
 
 def test_null_context_calls_return_arg_error(lib):
