@@ -144,7 +144,7 @@ def whole_job_seconds_per_iteration(ms: float, steps: int, world: int) -> float:
     return ms / 1e3 / steps / world
 
 
-def oracle_iteration_time(wl, steps: int = 1):
+def oracle_iteration_time(wl, steps: int = 1, method: str = "ccsd"):
     """Time the CPU oracle on the same workload: integrals untimed, then `steps` full iterations."""
     import numpy as np
     from oracle import ccsd_ref as R
@@ -158,7 +158,7 @@ def oracle_iteration_time(wl, steps: int = 1):
     times = []
     for _ in range(steps):
         t0 = time.perf_counter()
-        S1, S2 = R.residual(f, V, t1, t2)
+        S1, S2 = (R.residual_cc2 if method == "cc2" else R.residual)(f, V, t1, t2)
         d1, d2 = S1 / D1, S2 / D2
         t1, t2 = t1 + d1, t2 + d2
         _ = max(np.max(np.abs(d1)), np.max(np.abs(d2)))
@@ -271,7 +271,7 @@ def run_ours(args, wl):
     slices = args.slices or SPLIT_SLICES
     stream = torch.cuda.Stream()  # a real stream: the library captures its iteration graph on it
     m4 = 1 if args.complex_4m else 0
-    meth = ccmod.METHOD_CCD if args.method == "ccd" else ccmod.METHOD_CCSD
+    meth = {"ccsd": ccmod.METHOD_CCSD, "ccd": ccmod.METHOD_CCD, "cc2": ccmod.METHOD_CC2}[args.method]
     cc = make_ctx(ccmod, s, wl, precision, slices, stream, complex_4m=m4, method=meth)
 
     def barrier():
@@ -309,7 +309,7 @@ def run_ours(args, wl):
     # split-precision speedup and its energy / amplitude error against the FP64 GPU path
     companion = None
     if precision == "fp64" and not args.no_split_companion:
-        cs = make_ctx(ccmod, s, wl, "split", slices, stream)
+        cs = make_ctx(ccmod, s, wl, "split", slices, stream, method=meth)
         ms2, opd2, _ = timed_iterations(ccmod, cs, stream, args.warmup, args.steps)
         e_split = cs.energy()
         t_split = cs.get_amplitudes()
@@ -329,7 +329,7 @@ def run_ours(args, wl):
         n = args.fp64_companion
         res = {}
         for prec in ("split", "fp64"):
-            cx = make_ctx(ccmod, s, wl, prec, slices, stream)
+            cx = make_ctx(ccmod, s, wl, prec, slices, stream, method=meth)
             ms_n, _, _ = timed_iterations(ccmod, cx, stream, 0, n)
             res[prec] = (ms_n / n, cx.energy(), cx.get_amplitudes())
             cx.close()
@@ -382,13 +382,27 @@ def run_ours(args, wl):
                     "algorithmic_flops_per_launch": fp8_fl, "launch_ms": lad_ms,
                     "fp64_equivalent_tflops": lad_tf,
                     "traffic": recorded_traffic("zgemm_split.cu", f"ladder_{wl['name']}")}
+    if args.method == "cc2":
+        # CC2 has no ladder: its largest GEMM is (ai|bj)~ over the T1-dressed factors, M = N = ov, K = naux
+        j_ms = opd.get("cc2:J")
+        cm = float(o * v) ** 2 * wl["naux"]
+        if precision == "fp64":
+            ex_fl, peak = 6.0 * cm, peaks["bf16_tflops_sustained"] * FP64_OVER_BF16_NOMINAL
+            kname, basis = "zgemm_dmma_kernel<3M> (CC2 (ai|bj)~ launch)", roofline["peak_basis"]
+        else:
+            ex_fl, peak = slices * (slices + 1) // 2 * 8.0 * cm, peaks["bf16_tflops"] * 2.0
+            kname, basis = "split_kernel<e4m3> (CC2 (ai|bj)~ launch)", roofline["peak_basis"]
+        ach = ex_fl / (j_ms * 1e-3) / 1e12 if j_ms else None
+        roofline = {"kernel": kname, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": (ach / peak) if ach else None, "peak_basis": basis,
+                    "algorithmic_flops_per_launch": ex_fl, "launch_ms": j_ms, "traffic": None}
     top = sorted(opd.items(), key=lambda kv: -kv[1])[:8]
     cores = os.cpu_count()
     cpu = None
     if world == 1 and not args.no_cpu_baseline and wl["o"] * wl["v"] <= 2400:
-        ct = oracle_iteration_time(wl, 1)
+        ct = oracle_iteration_time(wl, 1, args.method)
         cpu = {"value": ct[0], "unit": "s", "cores": cores, "kind": "oracle",
-               "sample": f"one full oracle iteration (Appendix A residual + update, numpy complex128) of the "
+               "sample": f"one full oracle iteration ({'CC2' if args.method == 'cc2' else 'Appendix A'} residual + update, numpy complex128) of the "
                          f"{wl['name']} workload, integrals untimed"}
     elif world == 1 and not args.no_cpu_baseline:
         est, sample = oracle_ladder_rows_time(wl, 12 if wl["v"] <= 240 else 3)
@@ -714,8 +728,8 @@ def main():
                     help="split runs: also run N iterations from the MP2 guess in split and in FP64 and compare")
     ap.add_argument("--gemm-once", nargs=4, metavar=("KIND", "M", "N", "K"),
                     help="one GEMM (KIND fp64 or split) of M x N x K for profiling, then exit")
-    ap.add_argument("--method", choices=["ccsd", "ccd"], default="ccsd",
-                    help="ccd: the doubles equations with t1 held at zero")
+    ap.add_argument("--method", choices=["ccsd", "ccd", "cc2"], default="ccsd",
+                    help="ccd: the doubles equations with t1 held at zero; cc2: the CC2 doubles")
     ap.add_argument("--complex-4m", action="store_true",
                     help="FP64 GEMMs with four real products per complex product instead of three")
     ap.add_argument("--triples", action="store_true",
