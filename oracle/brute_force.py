@@ -8,8 +8,10 @@ C(n, N) Slater determinants, forms the similarity-transformed Hamiltonian
 H_bar = exp(-T) H exp(T) of Eq. CCSD with explicit operator matrices for T1 and T2
 (Eq. t_amp, with the 1/4 normalisation of T2), and projects on the reference, the
 singles and the doubles. It also diagonalises H (full CI), projects on the
-triple excitations, and gives the Moller-Plesset perturbed wavefunctions through
-second order (the pins of the triples corrections).
+triple excitations, gives the Moller-Plesset perturbed wavefunctions through
+second order (the pins of the triples corrections), and evaluates the Lambda
+equations as <0|(1 + Lambda)[H_bar, tau]|0>, the one-body density
+<0|(1 + Lambda) exp(-T) a+_p a_q exp(T)|0> and the full-CI left vector.
 
 Conventions: spinors 0..n-1 with the N = o lowest occupied in the reference;
 a determinant is a sorted tuple of occupied spinors; a+_p acting on a determinant
@@ -163,6 +165,57 @@ class Space:
         e1 = self.ref @ W @ self.ref
         psi2 = q * ((W - e1 * np.eye(len(self.dets))) @ psi1) / gap
         return H, W, psi1, psi2
+
+
+    def excitation_vectors(self):
+        """(|ia> as [i,a,x], |ijab> as [i,j,a,b,x]) with |ia> = E_ai|0>, |ijab> = E_ai E_bj|0>."""
+        Evo = self.E[self.o:, :self.o]
+        singles = np.einsum("aixy,y->iax", Evo, self.ref)
+        doubles = np.einsum("aixz,bjzy,y->ijabx", Evo, Evo, self.ref, optimize=True)
+        return singles, doubles
+
+    def left_vector(self, l1: np.ndarray, l2: np.ndarray) -> np.ndarray:
+        """<0| (1 + Lambda) as a row vector, Lambda = sum_ia l^i_a (E_ai)^+ + 1/4 sum_ijab
+        l^{ij}_{ab} (E_ai E_bj)^+: 1 on the reference, lambda_mu on each |mu> (i<j, a<b)."""
+        singles, doubles = self.excitation_vectors()
+        return (self.ref.astype(np.complex128) + np.einsum("ia,iax->x", l1, singles)
+                + 0.25 * np.einsum("ijab,ijabx->x", l2, doubles, optimize=True))
+
+    def lagrangian_gradient(self, f, V, t1, t2, l1, l2):
+        """<0| (1 + Lambda) [H_bar, tau_nu] |0> for tau_nu = E_ai and E_ai E_bj, H_bar = exp(-T) H exp(T)."""
+        o = self.o
+        H = hamiltonian(core_hamiltonian(f, V, o), V, self.E)
+        T = self.cluster_operator(t1, t2)
+        Hb = self.expm_nilpotent(-T) @ H @ self.expm_nilpotent(T)
+        bra = self.left_vector(l1, l2)
+        Evo = self.E[o:, :o]
+        singles, doubles = self.excitation_vectors()
+        w = bra @ Hb                      # <L| H_bar
+        h0 = Hb @ self.ref                # H_bar |0>
+        # <L| tau_nu as row vectors
+        b1 = np.einsum("x,aixy->iay", bra, Evo)
+        b2 = np.einsum("x,aixz,bjzy->ijaby", bra, Evo, Evo, optimize=True)
+        R1 = np.einsum("x,iax->ia", w, singles) - np.einsum("iay,y->ia", b1, h0)
+        R2 = np.einsum("x,ijabx->ijab", w, doubles) - np.einsum("ijaby,y->ijab", b2, h0)
+        return R1, R2
+
+    def density(self, t1, t2, l1, l2):
+        """gamma_pq = <0| (1 + Lambda) exp(-T) a+_p a_q exp(T) |0>."""
+        T = self.cluster_operator(t1, t2)
+        bra = self.left_vector(l1, l2) @ self.expm_nilpotent(-T)
+        ket = self.expm_nilpotent(T) @ self.ref
+        return np.einsum("x,pqxy,y->pq", bra, self.E, ket, optimize=True)
+
+    def fci_left_lambda(self, f, V, t1, t2):
+        """For a state that CCSD describes exactly (two electrons): the left eigenvector of H_bar,
+        <Psi| exp(T) / <Psi| exp(T) |0>, as (l1, l2) on the singles and doubles."""
+        H = hamiltonian(core_hamiltonian(f, V, self.o), V, self.E)
+        w, U = np.linalg.eigh(H)
+        k = int(np.argmax(np.abs(self.ref @ U)))
+        bra = np.conj(U[:, k]) @ self.expm_nilpotent(self.cluster_operator(t1, t2))
+        bra = bra / (bra @ self.ref)
+        singles, doubles = self.excitation_vectors()
+        return np.einsum("x,iax->ia", bra, singles), np.einsum("x,ijabx->ijab", bra, doubles)
 
 
 def n_determinants(o: int, v: int) -> int:

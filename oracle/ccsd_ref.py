@@ -92,14 +92,28 @@ def fock_matrix(eps: np.ndarray, fock: np.ndarray | None = None) -> np.ndarray:
 # Appendix A: CCSD amplitude equations
 # ---------------------------------------------------------------------------
 
+def _es(spec: str, *ops):
+    """einsum over numpy arrays, or over torch tensors (the Lambda oracle differentiates these
+    same equations with torch's autograd); the arithmetic is the same either way."""
+    if type(ops[0]).__module__.split(".")[0] == "torch":
+        import torch
+        return torch.einsum(spec, *ops)
+    return np.einsum(spec, *ops, optimize=True)
+
+
+def _perm(x, axes):
+    """Axes permutation of a numpy array or a torch tensor."""
+    return x.permute(*axes) if type(x).__module__.split(".")[0] == "torch" else x.transpose(*axes)
+
+
 def p_minus(x: np.ndarray, ax1: int, ax2: int) -> np.ndarray:
     """P^-_{pq} f(p,q) = f(p,q) - f(q,p), acting on axes ax1, ax2."""
-    return x - np.swapaxes(x, ax1, ax2)
+    return x - x.swapaxes(ax1, ax2)
 
 
 def tau(t1: np.ndarray, t2: np.ndarray) -> np.ndarray:
     """tau^{ab}_{ij} = t^{ab}_{ij} + P^-_ij (t^a_i t^b_j)."""
-    return t2 + p_minus(np.einsum("ia,jb->ijab", t1, t1), 0, 1)
+    return t2 + p_minus(_es("ia,jb->ijab", t1, t1), 0, 1)
 
 
 def intermediates(f: np.ndarray, V: dict, t1: np.ndarray, t2: np.ndarray) -> dict:
@@ -109,7 +123,7 @@ def intermediates(f: np.ndarray, V: dict, t1: np.ndarray, t2: np.ndarray) -> dic
     oooo, ooov, oovv = V["oooo"], V["ooov"], V["oovv"]
     vovo, vovv = V["vovo"], V["vovv"]
     ta = tau(t1, t2)
-    es = lambda s, *ops: np.einsum(s, *ops, optimize=True)
+    es = _es
 
     # H^a_c = F^a_c + 1/2 sum_kld V^{kl}_{cd} tau^{da}_{kl}
     Hvv = fvv + 0.5 * es("klcd,klda->ac", oovv, ta)
@@ -128,7 +142,7 @@ def intermediates(f: np.ndarray, V: dict, t1: np.ndarray, t2: np.ndarray) -> dic
              - es("klic,la->akci", ooov, t1)
              + es("klcd,liad->akci", oovv, 0.5 * t2 + es("la,id->liad", t1, t1)))
     # C^{kb}_{ij} = V^{ij+}_{kb} + sum_c P^-_ij (V^{bk}_{ci} t^c_j) - 1/2 sum_cd V^{bk}_{cd} tau^{cd}_{ij}
-    C = (np.conj(ooov).transpose(2, 3, 0, 1)
+    C = (_perm(ooov.conj(), (2, 3, 0, 1))
          + p_minus(es("bkci,jc->kbij", vovo, t1), 2, 3)
          - 0.5 * es("bkcd,ijcd->kbij", vovv, ta))
     # A^{kl}_{ij} = V^{kl}_{ij} + sum_c P^-_ij (V^{kl}_{ic} t^c_j) + 1/2 sum_cd V^{kl}_{cd} tau^{cd}_{ij}
@@ -140,7 +154,7 @@ def intermediates(f: np.ndarray, V: dict, t1: np.ndarray, t2: np.ndarray) -> dic
 
 def ladder(vvvv: np.ndarray, ta: np.ndarray) -> np.ndarray:
     """Particle-particle ladder 1/2 sum_cd V^{ab}_{cd} tau^{cd}_{ij}, as [i,j,a,b]."""
-    return 0.5 * np.einsum("abcd,ijcd->ijab", vvvv, ta, optimize=True)
+    return 0.5 * _es("abcd,ijcd->ijab", vvvv, ta)
 
 
 def ladder_elements(B: np.ndarray, o: int, t1: np.ndarray, t2: np.ndarray, idx) -> np.ndarray:
@@ -181,10 +195,10 @@ def _singles_terms(f: np.ndarray, V: dict, t1: np.ndarray, t2: np.ndarray, I: di
     fov = f[:o, o:]
     ooov, vovo, vovv = V["ooov"], V["vovo"], V["vovv"]
     ta = I["tau"]
-    es = lambda s, *ops: np.einsum(s, *ops, optimize=True)
+    es = _es
     Hvv, Hoo, Hov = I["Hvv"], I["Hoo"], I["Hov"]
     t1terms = {}
-    t1terms["f"] = np.conj(fov)                                       # F^{i+}_a
+    t1terms["f"] = fov.conj()                                         # F^{i+}_a
     t1terms["hvv"] = es("ac,ic->ia", Hvv, t1)                         # sum_c H^a_c t^c_i
     t1terms["hoo"] = es("ki,ka->ia", Hoo, t1)                         # sum_k H^k_i t^a_k
     t1terms["hov"] = es("kc,ikac->ia", Hov, t2)                       # sum_kc H^k_c t^{ac}_{ik}
@@ -206,7 +220,7 @@ def residual(f: np.ndarray, V: dict, t1: np.ndarray, t2: np.ndarray, parts: dict
     ooov, oovv, vovo, vovv = V["ooov"], V["oovv"], V["vovo"], V["vovv"]
     I = intermediates(f, V, t1, t2)
     ta = I["tau"]
-    es = lambda s, *ops: np.einsum(s, *ops, optimize=True)
+    es = _es
 
     terms = {}
     # sum_kc P^-_ij P^-_ab (H^{ak}_{ci} t^{cb}_{jk})
@@ -214,7 +228,7 @@ def residual(f: np.ndarray, V: dict, t1: np.ndarray, t2: np.ndarray, parts: dict
     # sum_k P^-_ji G^k_j t^{ab}_{ik}
     terms["goo"] = p_minus(es("kj,ikab->ijab", I["Goo"], t2), 0, 1)
     # sum_c P^-_ij (V^{cj+}_{ab} t^c_i)
-    terms["vt1"] = p_minus(es("cjab,ic->ijab", np.conj(vovv), t1), 0, 1)
+    terms["vt1"] = p_minus(es("cjab,ic->ijab", vovv.conj(), t1), 0, 1)
     # sum_c P^-_ab G^a_c t^{cb}_{ij}
     terms["gvv"] = p_minus(es("ac,ijcb->ijab", I["Gvv"], t2), 2, 3)
     # sum_k P^-_ab (C^{ka}_{ij} t^b_k)
@@ -224,7 +238,7 @@ def residual(f: np.ndarray, V: dict, t1: np.ndarray, t2: np.ndarray, parts: dict
     # 1/2 sum_cd V^{ab}_{cd} tau^{cd}_{ij}
     terms["ladder"] = ladder(V["vvvv"], ta)
     # V^{ij+}_{ab}
-    terms["driver"] = np.conj(oovv)
+    terms["driver"] = oovv.conj()
     S2 = sum(terms.values())
 
     t1terms = _singles_terms(f, V, t1, t2, I)
