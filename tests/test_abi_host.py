@@ -113,6 +113,8 @@ def test_null_context_calls_return_arg_error(lib):
     from paper_2103_08473_gb300 import ccsd
     assert lib.ccsd_iterate(None, 1, None, None) == ccsd.ERR_ARG
     assert lib.ccsd_energy(None, None) == ccsd.ERR_ARG
+    out = (C.c_double * 3)()
+    assert lib.ccsd_triples(None, 0, out, None) == ccsd.ERR_ARG
     lib.ccsd_destroy(None)
 
 
