@@ -101,3 +101,17 @@ def test_pins_catch_planted_mistakes(monkeypatch):
     gb = sp.density(t1, t2, l1, l2).T
     gb[:o, :o] -= np.eye(o)
     assert np.max(np.abs(g[:o, :o].T - gb[:o, :o])) > 1e-3
+
+
+@pytest.mark.parametrize("o,v,naux,seed", [(3, 5, 7, 51), (4, 6, 9, 52), (5, 7, 10, 53)])
+def test_explicit_adjoint_equals_the_derivative(o, v, naux, seed):
+    """The term-by-term adjoint of the Appendix-A residual (the device contraction list) equals the
+    differentiated Lagrangian."""
+    s, f, Vf, V = _system(o, v, naux, seed, scale=0.5, fock_offdiag=0.2)
+    t1, t2 = inputs.random_amplitudes(o, v, seed + 600, scale=0.3)
+    l1, l2 = inputs.random_amplitudes(o, v, seed + 700, scale=0.3)
+    R1, R2 = L.lagrangian_gradient(f, V, t1, t2, l1, l2)
+    E1, E2 = L.lagrangian_gradient_explicit(f, V, t1, t2, l1, l2)
+    scale = max(np.max(np.abs(R2)), 1.0)
+    assert np.max(np.abs(E1 - R1)) < 1e-12 * scale
+    assert np.max(np.abs(E2 - R2)) < 1e-12 * scale
