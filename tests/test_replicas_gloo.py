@@ -31,7 +31,7 @@ def test_two_replicas_take_the_slowest_rank():
     mp = pytest.importorskip("torch.multiprocessing")
     world, port = 2, _free_port()
     times = [120.0, 200.0]  # ms of the timed region on each rank
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:  # no fork of a process that already runs threads
         out = m.dict()
         mp.spawn(_rank, args=(world, port, times, out), nprocs=world, join=True)
         res = dict(out)
