@@ -198,6 +198,36 @@ ccsd_status ccsd_energy(ccsd_ctx* ctx, ccsd_z* e);
  */
 ccsd_status ccsd_triples(ccsd_ctx* ctx, int max_batch, double* out, double* pair_terms);
 
+/*
+ * Lambda equations and the one-body density at the current amplitudes (normally converged),
+ * appendices "Working equations for CCSD lambda equations" and "... Lagrange 1-body density
+ * matrix". The appendix prints the Lambda equations with intermediates it leaves to its
+ * reference. They are the stationarity conditions of the coupled-cluster Lagrangian
+ * L = E(t) + sum_mu lambda_mu S_mu(t) with respect to t, and this is how the library evaluates
+ * them: R = dL/dt, the adjoint of the residual, term by term. The multipliers are
+ * l1[i*v + a] = lambda^i_a and l2 [i][j][a][b] = lambda^{ij}_{ab}, antisymmetric like t2.
+ * Available for method = CCSD with store_w = 1 (CCSD_ERR_UNSUPPORTED otherwise). The
+ * multipliers and their DIIS history are created, at zero, by the first call that needs them.
+ *
+ * ccsd_lambda_residual: R1 (o*v) and R2 (o*o*v*v; the derivative with respect to each unique
+ *   t^{ab}_{ij}, extended antisymmetrically) at the given multipliers. With l1 and l2 given
+ *   they become the context's multipliers; with both NULL the context's own are used.
+ * ccsd_lambda_iterate: up to max_iter updates lambda <- lambda + R/D, with the amplitudes'
+ *   denominators, level shift, DIIS and norm. Returns CCSD_OK on convergence (norm <= tol),
+ *   CCSD_ERR_NOT_CONVERGED at the cap, CCSD_ERR_DIVERGED on NaN/Inf.
+ * ccsd_get_lambda: copy the multipliers out.
+ * ccsd_density: gamma (host, n*n, occupied first) =
+ *   <0| (1 + Lambda) exp(-T) a+_q a_p exp(T) |0>, less the reference occupation delta_ij, at
+ *   the current amplitudes and multipliers. The printed blocks are used, with the occupied
+ *   block transposed into the convention of the other three. With symmetrize != 0, the
+ *   Hermitian part (gamma + gamma^+)/2 is returned.
+ */
+ccsd_status ccsd_lambda_residual(ccsd_ctx* ctx, const ccsd_z* l1, const ccsd_z* l2, ccsd_z* r1, ccsd_z* r2,
+                                 int on_device);
+ccsd_status ccsd_lambda_iterate(ccsd_ctx* ctx, int max_iter, int* iters_done, double* res_norm);
+ccsd_status ccsd_get_lambda(ccsd_ctx* ctx, ccsd_z* l1, ccsd_z* l2, int on_device);
+ccsd_status ccsd_density(ccsd_ctx* ctx, ccsd_z* gamma, int symmetrize);
+
 /* Copy the current amplitudes out / in (checkpoint and resume). Setting resets DIIS. */
 ccsd_status ccsd_get_amplitudes(ccsd_ctx* ctx, ccsd_z* t1, ccsd_z* t2, int on_device);
 ccsd_status ccsd_set_amplitudes(ccsd_ctx* ctx, const ccsd_z* t1, const ccsd_z* t2, int on_device);
@@ -225,7 +255,7 @@ ccsd_status ccsd_timings(ccsd_ctx* ctx, const char** names, double* ms, int cap,
 /*
  * Scalar facts about a context: "kernels_per_iteration" (kernel nodes of the
  * iteration graph), "device_bytes" (device memory held), "iterations_run",
- * "plan_ops", "o", "v". Of the last ccsd_triples call: "triples_batch" (triples per
+ * "plan_ops", "o", "v", "lambda_iterations". Of the last ccsd_triples call: "triples_batch" (triples per
  * batch), "triples_batches", "triples_launches" (kernels launched), and with
  * opts.profile = 1 the device time in ms of its e-term GEMMs ("triples_egemm_ms"),
  * m-term GEMMs ("triples_mgemm_ms") and energy kernels ("triples_energy_ms"), summed

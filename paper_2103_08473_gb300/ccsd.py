@@ -53,6 +53,10 @@ SIGNATURES = [
     ("ccsd_iterate", C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     ("ccsd_energy", C.c_int, [_P, C.POINTER(ccsd_z)]),
     ("ccsd_triples", C.c_int, [_P, C.c_int, _P, _P]),
+    ("ccsd_lambda_residual", C.c_int, [_P, _P, _P, _P, _P, C.c_int]),
+    ("ccsd_lambda_iterate", C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    ("ccsd_get_lambda", C.c_int, [_P, _P, _P, C.c_int]),
+    ("ccsd_density", C.c_int, [_P, _P, C.c_int]),
     ("ccsd_get_amplitudes", C.c_int, [_P, _P, _P, C.c_int]),
     ("ccsd_set_amplitudes", C.c_int, [_P, _P, _P, C.c_int]),
     ("ccsd_get_tensor", C.c_int, [_P, C.c_char_p, _P, C.c_size_t, C.c_int]),
@@ -236,6 +240,40 @@ class CCSD:
                                            pt.ctypes.data_as(C.c_void_p) if pt is not None else None))
         e = {"+T": float(out[0]), "(T)": float(out[1]), "-T": float(out[2])}
         return (e, pt) if pair_terms else e
+
+    def lambda_residual(self, l1=None, l2=None):
+        """(R1, R2) of the Lambda equations at (l1, l2), which become the context's multipliers;
+        with none given, at the context's own."""
+        s1, s2 = self.shapes
+        r1, r2 = np.empty(s1, np.complex128), np.empty(s2, np.complex128)
+        a1 = None if l1 is None else np.ascontiguousarray(l1, dtype=np.complex128)
+        a2 = None if l2 is None else np.ascontiguousarray(l2, dtype=np.complex128)
+        self._check(self._lib.ccsd_lambda_residual(
+            self._h, None if a1 is None else a1.ctypes.data_as(C.c_void_p),
+            None if a2 is None else a2.ctypes.data_as(C.c_void_p),
+            r1.ctypes.data_as(C.c_void_p), r2.ctypes.data_as(C.c_void_p), 0))
+        return r1, r2
+
+    def lambda_iterate(self, max_iter=0):
+        """Iterate the Lambda equations; returns (status, iterations, norm)."""
+        it = C.c_int(0)
+        nrm = C.c_double(0.0)
+        st = self._lib.ccsd_lambda_iterate(self._h, int(max_iter), C.byref(it), C.byref(nrm))
+        self._check(st, allow=(ERR_NOT_CONVERGED, ERR_DIVERGED))
+        return st, it.value, nrm.value
+
+    def get_lambda(self):
+        s1, s2 = self.shapes
+        l1, l2 = np.empty(s1, np.complex128), np.empty(s2, np.complex128)
+        self._check(self._lib.ccsd_get_lambda(self._h, l1.ctypes.data_as(C.c_void_p),
+                                              l2.ctypes.data_as(C.c_void_p), 0))
+        return l1, l2
+
+    def density(self, symmetrize=False):
+        """The one-body density (n x n, occupied first), less the reference occupation."""
+        g = np.empty((self.n, self.n), np.complex128)
+        self._check(self._lib.ccsd_density(self._h, g.ctypes.data_as(C.c_void_p), int(bool(symmetrize))))
+        return g
 
     def get_amplitudes(self, out=None):
         s1, s2 = self.shapes

@@ -95,6 +95,19 @@ struct ccsd_ctx {
   int kernels_per_iter = 0;
   int64_t device_bytes = 0;
   int64_t iterations_run = 0;
+  // Lambda equations (built on first use): multipliers, the plan of their residual (the adjoint of
+  // the residual plan), its buffers and DIIS subspace; the density plan
+  z *l1 = nullptr, *l2 = nullptr;
+  Plan *lplan = nullptr, *dplan = nullptr;
+  z *lscratch = nullptr, *dscratch = nullptr;
+  DiisArgs ldiis;
+  z *lG = nullptr, *ltaub = nullptr, *lHrb = nullptr, *lXb = nullptr, *lzb = nullptr, *lCb = nullptr,
+    *lCanti = nullptr, *lCp = nullptr, *lAb = nullptr, *lAanti = nullptr, *lAfull = nullptr, *lpk = nullptr,
+    *lpk2 = nullptr, *lout = nullptr, *lout2 = nullptr, *lout3 = nullptr;
+  z *lGvvb = nullptr, *lHvvb = nullptr, *lGoob = nullptr, *lHoob = nullptr, *lHovb = nullptr;
+  z *dgoo = nullptr, *dgvo = nullptr, *dgvv = nullptr, *dq1 = nullptr, *dq2 = nullptr, *dq3 = nullptr, *dgam = nullptr,
+    *dgam2 = nullptr;
+  int64_t lambda_iterations = 0;
   // the last ccsd_triples call: batch size, batches, kernel launches and (profile = 1) device time of
   // its e-term GEMMs, m-term GEMMs and energy kernels
   int64_t tri_batch = 0, tri_batches = 0, tri_launches = 0;
@@ -625,6 +638,25 @@ cudaError_t split_gemm_chunked(ccsd_ctx* ctx, const ZGemmArgs& g, cudaStream_t s
 // The residual plan: Appendix A, one contraction per printed term.
 // Labels i,j,k,l run over occupied and a,b,c,d over virtual spinors.
 // ---------------------------------------------------------------------------
+// The GEMM back end of a plan: split precision where ctx->routes_split says so, else the FP64 DMMA
+// kernel with the context's split-K workspace.
+void set_plan_gemm(ccsd_ctx* ctx, Plan* P) {
+  const std::function<bool(const ZGemmArgs&)> to_split = ctx->routes_split;
+  P->set_gemm(
+      [ctx, to_split](const ZGemmArgs& g, cudaStream_t s) {
+        if (to_split(g)) return split_gemm_chunked(ctx, g, s);
+        ZGemmArgs h = g;
+        h.ws = ctx->gemm_ws;
+        h.ws_elems = ctx->gemm_ws_elems;
+        h.mult4 = ctx->opts.complex_4m;
+        return zgemm_f64(h, s, h.cfg);
+      },
+      [to_split](const ZGemmArgs& g) { return to_split(g) ? (int64_t)0 : zgemm_f64_workspace(g); },
+      [ctx, to_split](const ZGemmArgs& g) {
+        return to_split(g) ? split_chunked_bytes(g.M, g.N, g.K, ctx->split, ctx->split_budget) : 0;
+      });
+}
+
 ccsd_status build_residual_plan(ccsd_ctx* ctx) {
   const int o = ctx->o, v = ctx->v;
   // CC2: the singles of Appendix A with their intermediates tau, H^a_c, H^k_i, H^k_c, and the CC2
@@ -650,19 +682,7 @@ ccsd_status build_residual_plan(ccsd_ctx* ctx) {
   ctx->routes_split = to_split;
   if (ctx->use_split)
     ctx->split_budget = ctx->opts.split_budget > 0.0 ? (int64_t)ctx->opts.split_budget : split_call_budget();
-  P->set_gemm(
-      [ctx, to_split](const ZGemmArgs& g, cudaStream_t s) {
-        if (to_split(g)) return split_gemm_chunked(ctx, g, s);
-        ZGemmArgs h = g;
-        h.ws = ctx->gemm_ws;
-        h.ws_elems = ctx->gemm_ws_elems;
-        h.mult4 = ctx->opts.complex_4m;
-        return zgemm_f64(h, s, h.cfg);
-      },
-      [to_split](const ZGemmArgs& g) { return to_split(g) ? (int64_t)0 : zgemm_f64_workspace(g); },
-      [ctx, to_split](const ZGemmArgs& g) {
-        return to_split(g) ? split_chunked_bytes(g.M, g.N, g.K, ctx->split, ctx->split_budget) : 0;
-      });
+  set_plan_gemm(ctx, P);
   const z one = zmake(1, 0), mone = zmake(-1, 0), half = zmake(0.5, 0);
   auto V = [&](z* p, const char* lab) { return P->view(p, lab, true); };
   auto W = [&](z* p, const char* lab) { return P->view(p, lab, false); };
@@ -1462,6 +1482,390 @@ void free_ctx(ccsd_ctx* ctx) {
   delete ctx;
 }
 
+// ---------------------------------------------------------------------------
+// Lambda equations. R = dL/dt of L = E(t) + sum_mu lambda_mu S_mu(t), the stationarity conditions
+// that the appendix "Working equations for CCSD lambda equations" writes with Hbar intermediates.
+// The plan is the adjoint of the residual plan, term by term in reverse order (one op per line of
+// the CPU oracle's explicit adjoint). It reads the intermediates that the residual plan leaves at
+// the current amplitudes: tau, H^a_c, G^a_c, H^k_i, G^k_i, H^k_c, Yov = H^k_c - 2 F^k_c, Zoo,
+// H^{ak}_{ci} in Hr, C, and A from its packed copy. It writes R1 into S1 and R2 into S2.
+// ---------------------------------------------------------------------------
+ccsd_status build_lambda_plan(ccsd_ctx* ctx) {
+  const int o = ctx->o, v = ctx->v;
+  const int64_t Po = ctx->Po, Pv = ctx->Pv, ov = (int64_t)o * v, n2 = ov * ov, o4 = (int64_t)o * o * o * o;
+  CS(dalloc(ctx, &ctx->l1, ov));
+  CS(dalloc(ctx, &ctx->l2, n2));
+  for (z** p : {&ctx->lG, &ctx->ltaub, &ctx->lHrb, &ctx->lXb, &ctx->lzb}) CS(dalloc(ctx, p, n2));
+  for (z** p : {&ctx->lCb, &ctx->lCanti, &ctx->lCp}) CS(dalloc(ctx, p, ov * o * o));
+  for (z** p : {&ctx->lAb, &ctx->lAanti, &ctx->lAfull}) CS(dalloc(ctx, p, o4));
+  CS(dalloc(ctx, &ctx->lpk, (int64_t)o * o * Pv));
+  CS(dalloc(ctx, &ctx->lpk2, Po * Pv));
+  CS(dalloc(ctx, &ctx->lout, Po * Pv));
+  CS(dalloc(ctx, &ctx->lout2, (int64_t)o * o * Pv));
+  CS(dalloc(ctx, &ctx->lout3, (int64_t)o * o * Pv));
+  CS(dalloc(ctx, &ctx->lGvvb, (int64_t)v * v));
+  CS(dalloc(ctx, &ctx->lHvvb, (int64_t)v * v));
+  CS(dalloc(ctx, &ctx->lGoob, (int64_t)o * o));
+  CS(dalloc(ctx, &ctx->lHoob, (int64_t)o * o));
+  CS(dalloc(ctx, &ctx->lHovb, ov));
+  CK(cudaMemsetAsync(ctx->l1, 0, ov * sizeof(z), ctx->stream));
+  CK(cudaMemsetAsync(ctx->l2, 0, n2 * sizeof(z), ctx->stream));
+  if (ctx->opts.diis_dim > 0) {
+    DiisArgs& d = ctx->ldiis;
+    d = ctx->diis;  // same shape and options; its own history
+    CS(dalloc(ctx, &d.hist_t, d.m * d.L));
+    CS(dalloc(ctx, &d.hist_e, d.m * d.L));
+    CS(dalloc(ctx, &d.Bmat, (int64_t)d.m * d.m));
+    CS(dalloc(ctx, &d.coef, d.m));
+    CS(dalloc(ctx, &d.partials, (int64_t)d.m * diis_blocks()));
+    CS(dalloc(ctx, &d.state, 1));
+    CK(diis_reset(d, ctx->stream));
+  }
+  Plan* P = new Plan(o, v, &ctx->lscratch, ctx->stream);
+  ctx->lplan = P;
+  set_plan_gemm(ctx, P);
+  const z one = zmake(1, 0), mone = zmake(-1, 0), half = zmake(0.5, 0), quarter = zmake(0.25, 0),
+          eighth = zmake(0.125, 0);
+  auto V = [&](z* p, const char* lab) { return P->view(p, lab, true); };
+  auto W = [&](z* p, const char* lab) { return P->view(p, lab, false); };
+  z *t1 = ctx->t1, *t2 = ctx->t2, *l1 = ctx->l1, *l2 = ctx->l2, *r1 = ctx->S1, *G = ctx->lG, *taub = ctx->ltaub;
+  z *Hrb = ctx->lHrb, *Xb = ctx->lXb, *zb = ctx->lzb;
+
+  // A^{kl}_{ij} in full from its packed copy (the residual plan adds its tau term packed)
+  {
+    z *apk = ctx->Apk, *af = ctx->lAfull;
+    P->custom("L:A", [=](cudaStream_t s) {
+      UnpackArgs u;
+      u.in = apk;
+      u.out = af;
+      u.n1 = o;
+      u.n2 = o;
+      u.unpack_rows = 1;
+      u.beta = 0.0;
+      return unpack_pairs(u, s);
+    });
+  }
+  // energy: dE/dt1 = f_ia, dE/dtau = 1/4 <ij||ab>
+  P->add("L:E", W(r1, "ia"), one, V(ctx->fov, "ia"), false, 0.0);
+  P->add("L:E", W(taub, "ijab"), quarter, V(ctx->oovv, "ijab"), false, 0.0);
+  // S2 terms, weighted by 1/4 l2 (unique doubles); each antisymmetriser's adjoint on l2 gives 2
+  P->contract("L:ring", W(Hrb, "iakc"), one, W(l2, "ijab"), false, W(t2, "jkcb"), false, 0.0);
+  P->contract("L:ring", W(G, "jkcb"), one, W(l2, "ijab"), false, W(ctx->Hr, "iakc"), false, 0.0);
+  P->contract("L:goo", W(ctx->lGoob, "kj"), half, W(l2, "ijab"), false, W(t2, "ikab"), false, 0.0);
+  P->contract("L:goo", W(G, "ikab"), half, W(l2, "ijab"), false, W(ctx->Goo, "kj"), false, 1.0);
+  {
+    // sum_c P^-_ij conj(V^{cj}_{ab}) t^c_i:  R1[i][c] += sum_{j, a<b} l2[i][j][P(a,b)] conj(<cj||ab>)
+    z* lpk = ctx->lpk;
+    P->custom("L:vt1", [=](cudaStream_t s) { return pack_pairs(l2, lpk, (int64_t)o * o, v, 0, s); });
+    ZGemmArgs g;
+    g.M = o;
+    g.N = v;
+    g.K = (int64_t)o * Pv;
+    g.A = lpk;
+    g.lda = (int64_t)o * Pv;
+    g.B = ctx->vovv_pk;
+    g.ldb = (int64_t)o * Pv;
+    g.transB = 1;
+    g.conjB = 1;
+    g.C = r1;
+    g.ldc = v;
+    g.beta = one;
+    P->gemm("L:vt1:gemm", g);
+  }
+  P->contract("L:gvv", W(ctx->lGvvb, "ac"), half, W(l2, "ijab"), false, W(t2, "ijcb"), false, 0.0);
+  P->contract("L:gvv", W(G, "ijcb"), half, W(l2, "ijab"), false, W(ctx->Gvv, "ac"), false, 1.0);
+  P->contract("L:ct1", W(ctx->lCb, "kaij"), half, W(l2, "ijab"), false, W(t1, "kb"), false, 0.0);
+  P->contract("L:ct1", W(r1, "kb"), half, W(l2, "ijab"), false, W(ctx->C, "kaij"), false, 1.0);
+  P->contract("L:hole", W(ctx->lAb, "klij"), eighth, W(l2, "ijab"), false, W(ctx->tau, "klab"), false, 0.0);
+  P->contract("L:hole", W(taub, "klab"), eighth, W(l2, "ijab"), false, W(ctx->lAfull, "klij"), false, 1.0);
+  {
+    // ladder: 1/8 sum_ab l2[ijab] <ab||cd> = 1/4 sum_{a<b}, one packed GEMM against <ab||cd>
+    z *lpk2 = ctx->lpk2, *lout = ctx->lout;
+    P->custom("L:ladder", [=](cudaStream_t s) { return pack_pairs(l2, lpk2, o, v, 1, s); });
+    ZGemmArgs g;
+    g.M = Po;
+    g.N = Pv;
+    g.K = Pv;
+    g.A = lpk2;
+    g.lda = Pv;
+    g.B = ctx->Wpk;
+    g.ldb = Pv;
+    g.C = lout;
+    g.ldc = Pv;
+    P->gemm("L:ladder:gemm", g);
+    P->custom("L:ladder", [=](cudaStream_t s) {
+      UnpackArgs u;
+      u.in = lout;
+      u.out = taub;
+      u.n1 = o;
+      u.n2 = v;
+      u.unpack_rows = 1;
+      u.alpha = quarter;
+      u.beta = 1.0;
+      return unpack_pairs(u, s);
+    });
+  }
+  // S1 terms, weighted by l1
+  P->contract("L:hvv", W(ctx->lHvvb, "ac"), one, W(l1, "ia"), false, W(t1, "ic"), false, 0.0);
+  P->contract("L:hvv", W(r1, "ic"), one, W(l1, "ia"), false, W(ctx->Hvv, "ac"), false, 1.0);
+  P->contract("L:hoo", W(ctx->lHoob, "ki"), one, W(l1, "ia"), false, W(t1, "ka"), false, 0.0);
+  P->contract("L:hoo", W(r1, "ka"), one, W(l1, "ia"), false, W(ctx->Hoo, "ki"), false, 1.0);
+  P->contract("L:hov", W(ctx->lHovb, "kc"), one, W(l1, "ia"), false, W(t2, "ikac"), false, 0.0);
+  {
+    // the t2 adjoint of sum_kc H^k_c t^{ac}_{ik} is the outer product l1[i][a] H[k][c]: a K = 1 GEMM
+    ZGemmArgs g;
+    g.M = ov;
+    g.N = ov;
+    g.K = 1;
+    g.A = l1;
+    g.lda = 1;
+    g.B = ctx->Hov;
+    g.ldb = ov;
+    g.C = zb;
+    g.ldc = ov;
+    P->gemm("L:hov:outer", g);
+    P->add("L:hov", W(G, "ikac"), one, W(zb, "iakc"), false, 1.0);
+  }
+  // hf: sum_k (sum_c (H^k_c - 2F^k_c) t^c_i) t^a_k, with Q[k][i] = sum_a l1[i][a] t1[k][a] (lHoob above)
+  P->contract("L:hf", W(ctx->lHovb, "kc"), one, W(ctx->lHoob, "ki"), false, W(t1, "ic"), false, 1.0);
+  P->contract("L:hf", W(r1, "ic"), one, W(ctx->lHoob, "ki"), false, W(ctx->Yov, "kc"), false, 1.0);
+  P->contract("L:hf", W(r1, "ka"), one, W(ctx->Zoo, "ik"), false, W(l1, "ia"), false, 1.0);
+  {
+    // 1/2 sum_kcd V^{ak}_{cd} tau^{cd}_{ik}:  tau-bar[i][k][c][d] += 1/2 sum_a l1[i][a] <ak||cd>, packed
+    z* o2 = ctx->lout2;
+    ZGemmArgs g;
+    g.M = o;
+    g.N = (int64_t)o * Pv;
+    g.K = v;
+    g.A = l1;
+    g.lda = v;
+    g.B = ctx->vovv_pk;
+    g.ldb = (int64_t)o * Pv;
+    g.C = o2;
+    g.ldc = (int64_t)o * Pv;
+    P->gemm("L:vovv:gemm", g);
+    P->custom("L:vovv", [=](cudaStream_t s) {
+      UnpackArgs u;
+      u.in = o2;
+      u.out = taub;
+      u.n1 = (int64_t)o * o;
+      u.n2 = v;
+      u.alpha = half;
+      u.beta = 1.0;
+      return unpack_pairs(u, s);
+    });
+  }
+  P->contract("L:ooov", W(taub, "klca"), half, W(l1, "ia"), false, V(ctx->ooov, "klic"), false, 1.0);
+  P->contract("L:vovo", W(r1, "kc"), mone, W(l1, "ia"), false, V(ctx->J, "iakc"), false, 1.0);
+  // A^{kl}_{ij}
+  P->contract("L:A", W(taub, "ijcd"), half, W(ctx->lAb, "klij"), false, V(ctx->oovv, "klcd"), false, 1.0);
+  P->add("L:A", W(ctx->lAanti, "klij"), one, W(ctx->lAb, "klij"), false, 0.0);
+  P->add("L:A", W(ctx->lAanti, "klij"), mone, W(ctx->lAb, "klji"), false, 1.0);
+  P->contract("L:A", W(r1, "jc"), one, W(ctx->lAanti, "klij"), false, V(ctx->ooov, "klic"), false, 1.0);
+  // C^{kb}_{ij}: -1/2 sum_kb C-bar[k][b][i][j] <bk||cd> into tau-bar, packed over c<d
+  {
+    z *cp = ctx->lCp, *o3 = ctx->lout3;
+    P->add("L:C", W(cp, "ijbk"), one, W(ctx->lCb, "kbij"), false, 0.0);
+    ZGemmArgs g;
+    g.M = (int64_t)o * o;
+    g.N = Pv;
+    g.K = (int64_t)v * o;
+    g.A = cp;
+    g.lda = (int64_t)v * o;
+    g.B = ctx->vovv_pk;
+    g.ldb = Pv;
+    g.C = o3;
+    g.ldc = Pv;
+    P->gemm("L:C:gemm", g);
+    P->custom("L:C", [=](cudaStream_t s) {
+      UnpackArgs u;
+      u.in = o3;
+      u.out = taub;
+      u.n1 = (int64_t)o * o;
+      u.n2 = v;
+      u.alpha = zmake(-0.5, 0);
+      u.beta = 1.0;
+      return unpack_pairs(u, s);
+    });
+  }
+  P->add("L:C", W(ctx->lCanti, "kbij"), one, W(ctx->lCb, "kbij"), false, 0.0);
+  P->add("L:C", W(ctx->lCanti, "kbij"), mone, W(ctx->lCb, "kbji"), false, 1.0);
+  P->contract("L:C", W(r1, "jc"), one, W(ctx->lCanti, "kbij"), false, V(ctx->J, "ibkc"), false, 1.0);
+  // H^{ak}_{ci}: the ooov and X terms read H-bar before G-bar's diagonal is added to it
+  P->contract("L:Hvoov", W(r1, "la"), mone, W(Hrb, "iakc"), false, V(ctx->ooov, "klic"), false, 1.0);
+  P->contract("L:Hvoov", W(Xb, "liad"), one, W(Hrb, "iakc"), false, V(ctx->oovv, "klcd"), false, 0.0);
+  // G^a_c = H^a_c + sum_kd V^{ak}_{cd} t^d_k - sum_k F^k_c t^a_k: the fov term here; the vovv term
+  // rides on the diagonal k = i of H-bar (the adjoint of the trace the residual plan takes)
+  P->contract("L:Gvv", W(r1, "ka"), mone, W(ctx->lGvvb, "ac"), false, V(ctx->fov, "kc"), false, 1.0);
+  {
+    z *hrb = Hrb, *gvb = ctx->lGvvb;
+    P->custom("L:Gvv", [=](cudaStream_t s) { return diag_add_ik(hrb, o, v, gvb, 1.0, s); });
+  }
+  {
+    // R1[i][d] += sum_{akc} H-bar[i][a][k][c] <ak||cd>, over blocks of a of <ak||cd> unpacked from vovv_pk
+    const int64_t vb = ctx->vblk_rows, Pv_ = Pv;
+    for (int64_t a0 = 0; a0 < v; a0 += vb) {
+      ZGemmArgs g;
+      g.M = o;
+      g.N = v;
+      g.K = std::min<int64_t>(vb, v - a0) * o * v;
+      P->note_gemm(g);
+    }
+    z *vpk = ctx->vovv_pk, *vblk = ctx->vblk, *hrb = Hrb;
+    P->custom("L:Hvoov:gemm", [ctx, o, v, vb, Pv_, vpk, vblk, hrb, r1](cudaStream_t s) {
+      const GemmFn& gemm = ctx->lplan->gemm_fn();
+      cudaError_t e = cudaSuccess;
+      for (int64_t a0 = 0; a0 < v && e == cudaSuccess; a0 += vb) {
+        const int64_t na = std::min<int64_t>(vb, v - a0);
+        UnpackArgs u;  // vblk[(a - a0, k)][c][d] = <ak||cd>
+        u.in = vpk + a0 * o * Pv_;
+        u.out = vblk;
+        u.n1 = na * o;
+        u.n2 = v;
+        u.beta = 0.0;
+        e = unpack_pairs(u, s);
+        if (e != cudaSuccess) break;
+        ZGemmArgs g;  // R1[i][d] += sum_{(a,k,c)} H-bar[i][(a,k,c)] vblk[(a,k,c)][d]
+        g.M = o;
+        g.N = v;
+        g.K = na * o * v;
+        g.A = hrb + a0 * o * v;
+        g.lda = (int64_t)v * o * v;
+        g.B = vblk;
+        g.ldb = v;
+        g.C = r1;
+        g.ldc = v;
+        g.beta = zmake(1, 0);
+        e = gemm(g, s);
+      }
+      return e;
+    }, 8.0 * o * (double)v * o * v * v);
+  }
+  // X = 1/2 t2 + t1 t1
+  P->add("L:X", W(G, "liad"), half, W(Xb, "liad"), false, 1.0);
+  P->contract("L:X", W(r1, "la"), one, W(Xb, "liad"), false, W(t1, "id"), false, 1.0);
+  P->contract("L:X", W(r1, "id"), one, W(Xb, "liad"), false, W(t1, "la"), false, 1.0);
+  // H^k_c, G^k_i, H^k_i, G^a_c -> H^a_c
+  P->contract("L:Hov", W(r1, "ld"), one, W(ctx->lHovb, "kc"), false, V(ctx->oovv, "klcd"), false, 1.0);
+  P->add("L:Goo", W(ctx->lHoob, "ki"), one, W(ctx->lGoob, "ki"), false, 1.0);
+  P->contract("L:Goo", W(r1, "lc"), mone, W(ctx->lGoob, "ki"), false, V(ctx->ooov, "klic"), false, 1.0);
+  P->contract("L:Goo", W(r1, "ic"), mone, W(ctx->lGoob, "ki"), false, V(ctx->fov, "kc"), false, 1.0);
+  P->contract("L:Hoo", W(taub, "licd"), half, W(ctx->lHoob, "ki"), false, V(ctx->oovv, "klcd"), false, 1.0);
+  P->add("L:Gvv", W(ctx->lHvvb, "ac"), one, W(ctx->lGvvb, "ac"), false, 1.0);
+  P->contract("L:Hvv", W(taub, "klda"), half, W(ctx->lHvvb, "ac"), false, V(ctx->oovv, "klcd"), false, 1.0);
+  // tau = t2 + P^-_ij t1 t1
+  P->add("L:tau", W(G, "ijab"), one, W(taub, "ijab"), false, 1.0);
+  P->add("L:tau", W(zb, "ijab"), one, W(taub, "ijab"), false, 0.0);
+  P->add("L:tau", W(zb, "ijab"), mone, W(taub, "jiab"), false, 1.0);
+  P->contract("L:tau", W(r1, "ia"), one, W(zb, "ijab"), false, W(t1, "jb"), false, 1.0);
+  P->contract("L:tau", W(r1, "jb"), one, W(zb, "ijab"), false, W(t1, "ia"), false, 1.0);
+  // R2: the derivative with respect to each unique t^{ab}_{ij}, extended antisymmetrically
+  P->add("L:R2", W(ctx->S2, "ijab"), one, W(G, "ijab"), false, 0.0);
+  P->add("L:R2", W(ctx->S2, "ijab"), mone, W(G, "jiab"), false, 1.0);
+  P->add("L:R2", W(ctx->S2, "ijab"), mone, W(G, "ijba"), false, 1.0);
+  P->add("L:R2", W(ctx->S2, "ijab"), one, W(G, "jiba"), false, 1.0);
+
+  if (P->status() != cudaSuccess) return set_err(ctx, CCSD_ERR_CUDA, "lambda plan: " + P->error());
+  for (void* m : P->owned()) ctx->allocs.push_back(m);
+  P->owned().clear();
+  CS(dalloc(ctx, &ctx->lscratch, P->scratch_elems()));
+  if (P->gemm_workspace_elems() > ctx->gemm_ws_elems) {
+    CS(dalloc(ctx, &ctx->gemm_ws, P->gemm_workspace_elems()));
+    ctx->gemm_ws_elems = P->gemm_workspace_elems();
+  }
+  if (ctx->use_split && P->aux_bytes() > ctx->split_ws_bytes) {
+    uint8_t* w = nullptr;
+    CS(dalloc(ctx, &w, P->aux_bytes()));
+    ctx->split_ws = w;
+    ctx->split_ws_bytes = P->aux_bytes();
+  }
+  return CCSD_OK;
+}
+
+// The Lagrange one-body density (appendix "Working equations for Lagrange 1-body density matrix"),
+// block by block; the occupied block is written transposed (the convention of the other three).
+ccsd_status build_density_plan(ccsd_ctx* ctx) {
+  const int o = ctx->o, v = ctx->v, n = ctx->n;
+  CS(dalloc(ctx, &ctx->dgoo, (int64_t)o * o));
+  CS(dalloc(ctx, &ctx->dgvo, (int64_t)v * o));
+  CS(dalloc(ctx, &ctx->dgvv, (int64_t)v * v));
+  CS(dalloc(ctx, &ctx->dq1, (int64_t)o * o));
+  CS(dalloc(ctx, &ctx->dq2, (int64_t)o * o));
+  CS(dalloc(ctx, &ctx->dq3, (int64_t)v * v));
+  CS(dalloc(ctx, &ctx->dgam, (int64_t)n * n));
+  CS(dalloc(ctx, &ctx->dgam2, (int64_t)n * n));
+  Plan* D = new Plan(o, v, &ctx->dscratch, ctx->stream);
+  ctx->dplan = D;
+  set_plan_gemm(ctx, D);
+  const z one = zmake(1, 0), mone = zmake(-1, 0), half = zmake(0.5, 0), mhalf = zmake(-0.5, 0);
+  auto W = [&](z* p, const char* lab) { return D->view(p, lab, false); };
+  z *t1 = ctx->t1, *t2 = ctx->t2, *l1 = ctx->l1, *l2 = ctx->l2;
+  // gamma_ij = 1/2 sum_mef t^{ef}_{im} lambda^{mj}_{ef} - sum_e t^e_i lambda^j_e, stored at [j][i]
+  D->contract("D:oo", W(ctx->dgoo, "ji"), half, W(t2, "imef"), false, W(l2, "mjef"), false, 0.0);
+  D->contract("D:oo", W(ctx->dgoo, "ji"), mone, W(t1, "ie"), false, W(l1, "je"), false, 1.0);
+  // gamma_ai = t^a_i + sum_me lambda^m_e (t^{ae}_{im} - t^e_i t^a_m)
+  //            - 1/2 sum_mnef lambda^{mn}_{ef} (t^{ef}_{in} t^a_m + t^e_i t^{af}_{mn})
+  D->add("D:vo", W(ctx->dgvo, "ai"), one, W(t1, "ia"), false, 0.0);
+  D->contract("D:vo", W(ctx->dgvo, "ai"), one, W(l1, "me"), false, W(t2, "imae"), false, 1.0);
+  D->contract("D:vo", W(ctx->dq1, "mi"), one, W(l1, "me"), false, W(t1, "ie"), false, 0.0);
+  D->contract("D:vo", W(ctx->dgvo, "ai"), mone, W(ctx->dq1, "mi"), false, W(t1, "ma"), false, 1.0);
+  D->contract("D:vo", W(ctx->dq2, "mi"), one, W(l2, "mnef"), false, W(t2, "inef"), false, 0.0);
+  D->contract("D:vo", W(ctx->dgvo, "ai"), mhalf, W(ctx->dq2, "mi"), false, W(t1, "ma"), false, 1.0);
+  D->contract("D:vo", W(ctx->dq3, "ea"), one, W(l2, "mnef"), false, W(t2, "mnaf"), false, 0.0);
+  D->contract("D:vo", W(ctx->dgvo, "ai"), mhalf, W(t1, "ie"), false, W(ctx->dq3, "ea"), false, 1.0);
+  // gamma_ab = 1/2 sum_mne t^{ae}_{mn} lambda^{mn}_{be} + sum_m t^a_m lambda^m_b
+  D->contract("D:vv", W(ctx->dgvv, "ab"), half, W(t2, "mnae"), false, W(l2, "mnbe"), false, 0.0);
+  D->contract("D:vv", W(ctx->dgvv, "ab"), one, W(t1, "ma"), false, W(l1, "mb"), false, 1.0);
+  if (D->status() != cudaSuccess) return set_err(ctx, CCSD_ERR_CUDA, "density plan: " + D->error());
+  for (void* m : D->owned()) ctx->allocs.push_back(m);
+  D->owned().clear();
+  CS(dalloc(ctx, &ctx->dscratch, D->scratch_elems()));
+  if (D->gemm_workspace_elems() > ctx->gemm_ws_elems) {
+    CS(dalloc(ctx, &ctx->gemm_ws, D->gemm_workspace_elems()));
+    ctx->gemm_ws_elems = D->gemm_workspace_elems();
+  }
+  if (ctx->use_split && D->aux_bytes() > ctx->split_ws_bytes) {
+    uint8_t* w = nullptr;
+    CS(dalloc(ctx, &w, D->aux_bytes()));
+    ctx->split_ws = w;
+    ctx->split_ws_bytes = D->aux_bytes();
+  }
+  (void)n;
+  return CCSD_OK;
+}
+
+ccsd_status lambda_ready(ccsd_ctx* ctx) {
+  if (ctx->opts.method != CCSD_METHOD_CCSD)
+    return set_err(ctx, CCSD_ERR_UNSUPPORTED, "the Lambda equations are built for CCSD (method = CCSD)");
+  if (!ctx->opts.store_w)
+    return set_err(ctx, CCSD_ERR_UNSUPPORTED, "the Lambda equations need the stored <ab||cd> (store_w = 1)");
+  if (!ctx->lplan) CS(build_lambda_plan(ctx));
+  return CCSD_OK;
+}
+
+cudaError_t run_plan(Plan* P, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  for (auto& op : P->ops())
+    if ((e = op.run(s)) != cudaSuccess) break;
+  return e;
+}
+
+// A block of an n x n matrix: out[(r0 + r) * n + c0 + c] = in[r * cols + c].
+cudaError_t put_block(const z* in, int64_t rows, int64_t cols, z* out, int64_t n, int64_t r0, int64_t c0,
+                      cudaStream_t s) {
+  PermuteArgs a;
+  a.rank = 2;
+  a.dims[0] = rows;
+  a.dims[1] = cols;
+  a.istr[0] = cols;
+  a.istr[1] = 1;
+  a.ostr[0] = n;
+  a.ostr[1] = 1;
+  a.in = in;
+  a.out = out + r0 * n + c0;
+  return permute_add(a, s);
+}
+
 }  // namespace
 
 extern "C" {
@@ -1708,6 +2112,114 @@ ccsd_status ccsd_triples(ccsd_ctx* ctx, int max_batch, double* out, double* pair
   return CCSD_OK;
 }
 
+ccsd_status ccsd_lambda_residual(ccsd_ctx* ctx, const ccsd_z* l1, const ccsd_z* l2, ccsd_z* r1, ccsd_z* r2,
+                                 int on_device) {
+  if (!ctx) return CCSD_ERR_ARG;
+  if ((l1 == nullptr) != (l2 == nullptr)) return set_err(ctx, CCSD_ERR_ARG, "l1 and l2 must both be given or both NULL");
+  CS(lambda_ready(ctx));
+  const int64_t n1 = (int64_t)ctx->o * ctx->v, n2 = n1 * ctx->o * ctx->v;
+  if (l1) {
+    CS(copy_in(ctx, ctx->l1, l1, n1, on_device));
+    CS(copy_in(ctx, ctx->l2, l2, n2, on_device));
+  }
+  CK(run_ops(ctx, false));  // the residual plan's intermediates at the current amplitudes
+  CK(run_plan(ctx->lplan, ctx->stream));
+  if (ctx->use_split) CK(cudaMemcpyAsync(ctx->err_host, ctx->split_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  if (r1) CS(copy_out(ctx, r1, ctx->S1, n1, on_device));
+  if (r2) CS(copy_out(ctx, r2, ctx->S2, n2, on_device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (ctx->use_split && *ctx->err_host)
+    return set_err(ctx, CCSD_ERR_TIMEOUT, "a bounded wait in the tensor-core GEMM gave up");
+  return CCSD_OK;
+}
+
+ccsd_status ccsd_lambda_iterate(ccsd_ctx* ctx, int max_iter, int* iters_done, double* res_norm) {
+  if (!ctx) return CCSD_ERR_ARG;
+  CS(lambda_ready(ctx));
+  if (max_iter <= 0) max_iter = ctx->opts.max_iter;
+  CK(run_ops(ctx, false));  // the intermediates stay fixed: the amplitudes do not change
+  int it = 0;
+  double nrm = INFINITY;
+  ccsd_status st = CCSD_ERR_NOT_CONVERGED;
+  for (it = 1; it <= max_iter; ++it) {
+    CK(run_plan(ctx->lplan, ctx->stream));
+    CK(denom_update(ctx->l1, ctx->l2, ctx->S1, ctx->S2, ctx->dvec, ctx->o, ctx->v, ctx->opts.level_shift,
+                    ctx->upd_partials, ctx->stream));
+    CK(norm_finalize(ctx->upd_partials, update_blocks(), ctx->stats, ctx->stream));
+    if (ctx->opts.diis_dim > 0) CK(diis_step(ctx->ldiis, ctx->l1, ctx->l2, ctx->S1, ctx->S2, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->stats_host, ctx->stats, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (ctx->use_split) CK(cudaMemcpyAsync(ctx->err_host, ctx->split_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (ctx->use_split && *ctx->err_host) {
+      st = set_err(ctx, CCSD_ERR_TIMEOUT, "a bounded wait in the tensor-core GEMM gave up");
+      break;
+    }
+    ctx->lambda_iterations += 1;
+    nrm = ctx->opts.norm == 1 ? ctx->stats_host[1] : ctx->stats_host[0];
+    if (!std::isfinite(ctx->stats_host[0]) || !std::isfinite(ctx->stats_host[1])) {
+      st = set_err(ctx, CCSD_ERR_DIVERGED, "non-finite multiplier update at iteration " + std::to_string(it));
+      break;
+    }
+    if (nrm <= ctx->opts.tol) {
+      st = CCSD_OK;
+      break;
+    }
+  }
+  if (it > max_iter) it = max_iter;
+  if (iters_done) *iters_done = it;
+  if (res_norm) *res_norm = nrm;
+  if (st == CCSD_ERR_NOT_CONVERGED) set_err(ctx, st, "not converged in " + std::to_string(max_iter) + " iterations");
+  return st;
+}
+
+ccsd_status ccsd_get_lambda(ccsd_ctx* ctx, ccsd_z* l1, ccsd_z* l2, int on_device) {
+  if (!ctx) return CCSD_ERR_ARG;
+  CS(lambda_ready(ctx));
+  const int64_t n1 = (int64_t)ctx->o * ctx->v, n2 = n1 * ctx->o * ctx->v;
+  if (l1) CS(copy_out(ctx, l1, ctx->l1, n1, on_device));
+  if (l2) CS(copy_out(ctx, l2, ctx->l2, n2, on_device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return CCSD_OK;
+}
+
+ccsd_status ccsd_density(ccsd_ctx* ctx, ccsd_z* gamma, int symmetrize) {
+  if (!ctx) return CCSD_ERR_ARG;
+  if (!gamma) return set_err(ctx, CCSD_ERR_ARG, "gamma must not be NULL");
+  CS(lambda_ready(ctx));
+  if (!ctx->dplan) CS(build_density_plan(ctx));
+  const int o = ctx->o, v = ctx->v, n = ctx->n;
+  CK(run_plan(ctx->dplan, ctx->stream));
+  CK(put_block(ctx->dgoo, o, o, ctx->dgam, n, 0, 0, ctx->stream));
+  CK(put_block(ctx->l1, o, v, ctx->dgam, n, 0, o, ctx->stream));
+  CK(put_block(ctx->dgvo, v, o, ctx->dgam, n, o, 0, ctx->stream));
+  CK(put_block(ctx->dgvv, v, v, ctx->dgam, n, o, o, ctx->stream));
+  const z* out = ctx->dgam;
+  if (symmetrize) {
+    // the Hermitian part: 1/2 gamma + 1/2 gamma^+
+    PermuteArgs a;
+    a.rank = 2;
+    a.dims[0] = n;
+    a.dims[1] = n;
+    a.istr[0] = n;
+    a.istr[1] = 1;
+    a.ostr[0] = n;
+    a.ostr[1] = 1;
+    a.in = ctx->dgam;
+    a.out = ctx->dgam2;
+    a.alpha = zmake(0.5, 0);
+    CK(permute_add(a, ctx->stream));
+    a.istr[0] = 1;
+    a.istr[1] = n;
+    a.conj = 1;
+    a.beta = 1.0;
+    CK(permute_add(a, ctx->stream));
+    out = ctx->dgam2;
+  }
+  CK(cudaMemcpyAsync(gamma, out, sizeof(z) * (size_t)n * n, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return CCSD_OK;
+}
+
 ccsd_status ccsd_get_amplitudes(ccsd_ctx* ctx, ccsd_z* t1, ccsd_z* t2, int on_device) {
   if (!ctx) return CCSD_ERR_ARG;
   const int64_t n1 = (int64_t)ctx->o * ctx->v, n2 = n1 * ctx->o * ctx->v;
@@ -1794,6 +2306,7 @@ ccsd_status ccsd_query(const ccsd_ctx* ctx, const char* key, double* value) {
   else if (k == "device_bytes") *value = (double)ctx->device_bytes;
   else if (k == "iterations_run") *value = (double)ctx->iterations_run;
   else if (k == "plan_ops") *value = (double)ctx->plan->ops().size();
+  else if (k == "lambda_iterations") *value = (double)ctx->lambda_iterations;
   else if (k == "triples_batch") *value = (double)ctx->tri_batch;
   else if (k == "triples_batches") *value = (double)ctx->tri_batches;
   else if (k == "triples_launches") *value = (double)ctx->tri_launches;

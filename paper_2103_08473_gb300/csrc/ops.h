@@ -61,6 +61,8 @@ cudaError_t pack_vvvv_rows(const z* D, z* W, int64_t v, int64_t a0, int64_t a1, 
 cudaError_t pack_vovv_rows(const z* D, z* W, int64_t na, int64_t o, int64_t v, cudaStream_t s);
 // out[a][c] = alpha * sum_k H[k][a][k][c] + beta * out[a][c] for H stored [i][a][k][c] (o, v, o, v).
 cudaError_t trace_ik(const z* H, int64_t o, int64_t v, z* out, double alpha, double beta, cudaStream_t s);
+// The adjoint of trace_ik: H[k][a][k][c] += alpha * G[a][c] for every k (H stored [i][a][k][c]).
+cudaError_t diag_add_ik(z* H, int64_t o, int64_t v, const z* G, double alpha, cudaStream_t s);
 
 // Denominator update over t1 (o*v) and full t2 (o*o*v*v):
 //   d = S / D, t += d, S <- d.   D^a_i = e_i - e_a - shift, D^{ab}_{ij} = e_i + e_j - e_a - e_b - 2 shift

@@ -217,6 +217,17 @@ __global__ void trace_ik_kernel(const z* __restrict__ H, int64_t o, int64_t v, z
   }
 }
 
+// The adjoint of trace_ik: H[k][a][k][c] += alpha * G[a][c] for every k.
+__global__ void diag_add_ik_kernel(z* __restrict__ H, int64_t o, int64_t v, const z* __restrict__ G, double alpha) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < o * v * v;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = e / (v * v), a = (e / v) % v, c = e % v;
+    z* h = H + ((k * v + a) * o + k) * v + c;
+    const z g = G[a * v + c];
+    *h = make_double2(h->x + alpha * g.x, h->y + alpha * g.y);
+  }
+}
+
 // ---- update and norms ------------------------------------------------------
 
 template <typename T>
@@ -573,6 +584,11 @@ cudaError_t pack_vovv_rows(const z* D, z* W, int64_t na, int64_t o, int64_t v, c
   const int64_t total = na * o * pair_count(v);
   if (total <= 0) return cudaSuccess;
   pack_vovv_rows_kernel<<<grid_for(total, kThreads), kThreads, 0, s>>>(D, W, na, o, v);
+  return cudaGetLastError();
+}
+
+cudaError_t diag_add_ik(z* H, int64_t o, int64_t v, const z* G, double alpha, cudaStream_t s) {
+  diag_add_ik_kernel<<<grid_for(o * v * v, kThreads), kThreads, 0, s>>>(H, o, v, G, alpha);
   return cudaGetLastError();
 }
 
