@@ -570,6 +570,98 @@ def run_triples(args, wl):
     print(json.dumps(line), flush=True)
 
 
+def run_lambda(args, wl):
+    """One step = one iteration of the Lambda equations at the workload's amplitudes (FP64 or split);
+    the amplitudes' values do not change the work. Each timed call runs the residual plan once
+    to refresh the intermediates, then `steps` Lambda iterations."""
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2103_08473_gb300 import build, flops, inputs
+    from paper_2103_08473_gb300 import ccsd as ccmod
+
+    ccmod.load(build.build())
+    s = inputs.make_system(wl["o"], wl["v"], wl["naux"], wl["seed"])
+    o, v = s.o, s.v
+    precision = args.precision or "fp64"
+    stream = torch.cuda.Stream()
+    cc = make_ctx(ccmod, s, wl, precision, SPLIT_SLICES, stream)
+    cc.lambda_iterate(args.warmup)
+    nops = cc.query("lambda_iterations")
+    sampler = ClockSampler(local)
+    sampler.start()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    cc.lambda_iterate(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    lad_ms = cc.query("lambda_op_ms:L:ladder:gemm")
+    ring_ms = cc.query("lambda_op_ms:L:ring")
+    # end to end through the C ABI: multipliers in from pinned host memory, one residual, out
+    l1, l2 = cc.get_lambda()
+    l1h = torch.from_numpy(l1).pin_memory()
+    l2h = torch.from_numpy(l2).pin_memory()
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for _ in range(max(2, args.steps)):
+        cc.lambda_residual(l1h.numpy(), l2h.numpy())
+    e2e = (time.perf_counter() - w0) / max(2, args.steps)
+    cc.close()
+    if rank != 0:
+        return
+    peaks, peak_kind = load_peaks()
+    lad_fl = flops.ladder_flops_packed(o, v)  # lambda . <ab||cd>: the forward ladder's shape
+    if precision == "fp64":
+        ex_fl, peak = 0.75 * lad_fl, peaks["bf16_tflops_sustained"] * FP64_OVER_BF16_NOMINAL
+        kname = "zgemm_dmma_kernel<3M> (Lambda ladder adjoint, lambda . <ab||cd>)"
+        basis = f"{peak_kind} bf16_tflops_sustained x 1.25/2250 (nominal dense FP64/BF16 ratio)"
+    else:
+        ex_fl = SPLIT_SLICES * (SPLIT_SLICES + 1) // 2 * lad_fl
+        peak = peaks["bf16_tflops"] * 2.0
+        kname = "split_kernel<e4m3> (Lambda ladder adjoint, lambda . <ab||cd>)"
+        basis = f"{peak_kind} bf16_tflops (burst) x 2 (nominal dense FP8/BF16 ratio)"
+    ach = ex_fl / (lad_ms * 1e-3) / 1e12 if lad_ms else None
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline and o * v <= 2400:
+        from oracle import ccsd_ref as R
+        from oracle import lambda_ref as L
+        f = R.fock_matrix(s.eps)
+        V = R.integrals(s.B, o)
+        t1, t2 = inputs.random_amplitudes(o, v, wl["seed"] + 77, scale=0.01)
+        t0 = time.perf_counter()
+        L.lagrangian_gradient(f, V, t1, t2, l1, l2)
+        cpu = {"value": time.perf_counter() - t0, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"one Lambda residual of the oracle (torch autograd through the Appendix-A residual, "
+                         f"CPU complex128) at {wl['name']}"}
+    line = {"metric": "Lambda iteration time (s)", "value": whole_job_seconds_per_iteration(ms, args.steps, world),
+            "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if precision == "fp64" else "e4m3 digits, f32 accumulate, f64", "data": "synthetic",
+            "config": {"workload": f"{wl['name']} lambda", "o": o, "v": v, "naux": wl["naux"],
+                       "precision": precision, "amplitudes": "MP2 guess",
+                       "timed": "one call: a residual-plan refresh, then steps Lambda iterations",
+                       "l2": "inputs larger than L2 (packed <ab||cd> exceeds 129 MB)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "lambda_plan_ms": {"ladder_adjoint": lad_ms, "ring_adjoint": ring_ms},
+            "roofline": {"kernel": kname, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                         "frac": (ach / peak) if ach else None, "peak_basis": basis,
+                         "algorithmic_flops_per_launch": ex_fl, "launch_ms": lad_ms, "traffic": None},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": 16 * (o * v + o * o * v * v),
+                    "d2h_bytes_per_step": 16 * (o * v + o * o * v * v)},
+            "clocks": clocks, "gpu_launches": None, "lambda_iterations_before": nops}
+    print(json.dumps(line), flush=True)
+
+
 def run_batch(args, wl):
     """64 uneven systems solved to convergence in one batch vs one after another."""
     import numpy as np
@@ -734,6 +826,8 @@ def main():
                     help="FP64 GEMMs with four real products per complex product instead of three")
     ap.add_argument("--triples", action="store_true",
                     help="time the triples corrections E(+T), E((T)), E(-T) on the workload instead of an iteration")
+    ap.add_argument("--lambda", dest="lam", action="store_true",
+                    help="time iterations of the Lambda equations on the workload instead of the amplitudes'")
     ap.add_argument("--residual-once", action="store_true",
                     help="create the context and evaluate one residual eagerly (for ncu captures), no timing")
     args = ap.parse_args()
@@ -749,6 +843,8 @@ def main():
         residual_once(wl, args.precision or wl["precision"], args.slices or SPLIT_SLICES)
     elif args.triples and args.impl == "ours":
         run_triples(args, wl)
+    elif args.lam and args.impl == "ours":
+        run_lambda(args, wl)
     elif args.impl == "reference":
         run_reference(args, wl)
     else:

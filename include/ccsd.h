@@ -255,7 +255,9 @@ ccsd_status ccsd_timings(ccsd_ctx* ctx, const char** names, double* ms, int cap,
 /*
  * Scalar facts about a context: "kernels_per_iteration" (kernel nodes of the
  * iteration graph), "device_bytes" (device memory held), "iterations_run",
- * "plan_ops", "o", "v", "lambda_iterations". Of the last ccsd_triples call: "triples_batch" (triples per
+ * "plan_ops", "o", "v", "lambda_iterations", and with opts.profile = 1
+ * "lambda_op_ms:<op>" (average device ms per Lambda iteration of the Lambda-plan ops named <op>,
+ * e.g. "L:ladder:gemm"). Of the last ccsd_triples call: "triples_batch" (triples per
  * batch), "triples_batches", "triples_launches" (kernels launched), and with
  * opts.profile = 1 the device time in ms of its e-term GEMMs ("triples_egemm_ms"),
  * m-term GEMMs ("triples_mgemm_ms") and energy kernels ("triples_energy_ms"), summed

@@ -108,6 +108,10 @@ struct ccsd_ctx {
   z *dgoo = nullptr, *dgvo = nullptr, *dgvv = nullptr, *dq1 = nullptr, *dq2 = nullptr, *dq3 = nullptr, *dgam = nullptr,
     *dgam2 = nullptr;
   int64_t lambda_iterations = 0;
+  // profile = 1: one event per Lambda-plan op boundary, and the summed device time per op
+  std::vector<cudaEvent_t> lev;
+  std::vector<double> ltsum;
+  int64_t ltcount = 0;
   // the last ccsd_triples call: batch size, batches, kernel launches and (profile = 1) device time of
   // its e-term GEMMs, m-term GEMMs and energy kernels
   int64_t tri_batch = 0, tri_batches = 0, tri_launches = 0;
@@ -1471,13 +1475,15 @@ void free_ctx(ccsd_ctx* ctx) {
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
   for (auto e : ctx->tev) cudaEventDestroy(e);
   for (void* p : ctx->allocs) cudaFree(p);
-  if (ctx->plan) {
-    for (void* p : ctx->plan->owned()) cudaFree(p);
-    delete ctx->plan;
-  }
+  for (Plan* P : {ctx->plan, ctx->lplan, ctx->dplan})
+    if (P) {
+      for (void* p : P->owned()) cudaFree(p);
+      delete P;
+    }
   if (ctx->stats_host) cudaFreeHost(ctx->stats_host);
   if (ctx->e_host) cudaFreeHost(ctx->e_host);
   if (ctx->err_host) cudaFreeHost(ctx->err_host);
+  for (auto ev : ctx->lev) cudaEventDestroy(ev);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
@@ -1850,6 +1856,32 @@ cudaError_t run_plan(Plan* P, cudaStream_t s) {
   return e;
 }
 
+// The Lambda plan with an event at every op boundary (profile = 1); lambda_collect adds the
+// elapsed times once the stream is synchronised.
+cudaError_t run_lambda_timed(ccsd_ctx* ctx) {
+  auto& ops = ctx->lplan->ops();
+  if (ctx->lev.empty()) {
+    ctx->lev.resize(ops.size() + 1);
+    for (auto& ev : ctx->lev) cudaEventCreate(&ev);
+    ctx->ltsum.assign(ops.size(), 0.0);
+  }
+  cudaError_t e = cudaEventRecord(ctx->lev[0], ctx->stream);
+  for (size_t k = 0; k < ops.size() && e == cudaSuccess; ++k) {
+    e = ops[k].run(ctx->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->lev[k + 1], ctx->stream);
+  }
+  return e;
+}
+
+void lambda_collect(ccsd_ctx* ctx) {
+  for (size_t k = 0; k + 1 < ctx->lev.size(); ++k) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->lev[k], ctx->lev[k + 1]) == cudaSuccess) ctx->ltsum[k] += ms;
+  }
+  cudaGetLastError();
+  ctx->ltcount += 1;
+}
+
 // A block of an n x n matrix: out[(r0 + r) * n + c0 + c] = in[r * cols + c].
 cudaError_t put_block(const z* in, int64_t rows, int64_t cols, z* out, int64_t n, int64_t r0, int64_t c0,
                       cudaStream_t s) {
@@ -2141,8 +2173,9 @@ ccsd_status ccsd_lambda_iterate(ccsd_ctx* ctx, int max_iter, int* iters_done, do
   int it = 0;
   double nrm = INFINITY;
   ccsd_status st = CCSD_ERR_NOT_CONVERGED;
+  const bool timed = ctx->opts.profile != 0;
   for (it = 1; it <= max_iter; ++it) {
-    CK(run_plan(ctx->lplan, ctx->stream));
+    CK(timed ? run_lambda_timed(ctx) : run_plan(ctx->lplan, ctx->stream));
     CK(denom_update(ctx->l1, ctx->l2, ctx->S1, ctx->S2, ctx->dvec, ctx->o, ctx->v, ctx->opts.level_shift,
                     ctx->upd_partials, ctx->stream));
     CK(norm_finalize(ctx->upd_partials, update_blocks(), ctx->stats, ctx->stream));
@@ -2155,6 +2188,7 @@ ccsd_status ccsd_lambda_iterate(ccsd_ctx* ctx, int max_iter, int* iters_done, do
       break;
     }
     ctx->lambda_iterations += 1;
+    if (timed) lambda_collect(ctx);
     nrm = ctx->opts.norm == 1 ? ctx->stats_host[1] : ctx->stats_host[0];
     if (!std::isfinite(ctx->stats_host[0]) || !std::isfinite(ctx->stats_host[1])) {
       st = set_err(ctx, CCSD_ERR_DIVERGED, "non-finite multiplier update at iteration " + std::to_string(it));
@@ -2307,6 +2341,15 @@ ccsd_status ccsd_query(const ccsd_ctx* ctx, const char* key, double* value) {
   else if (k == "iterations_run") *value = (double)ctx->iterations_run;
   else if (k == "plan_ops") *value = (double)ctx->plan->ops().size();
   else if (k == "lambda_iterations") *value = (double)ctx->lambda_iterations;
+  else if (k.rfind("lambda_op_ms:", 0) == 0) {
+    // average device time per timed Lambda iteration of the ops with that name (profile = 1)
+    const std::string nm = k.substr(13);
+    double sum = 0.0;
+    if (ctx->lplan && ctx->ltcount > 0)
+      for (size_t i = 0; i < ctx->lplan->ops().size() && i < ctx->ltsum.size(); ++i)
+        if (ctx->lplan->ops()[i].name == nm) sum += ctx->ltsum[i];
+    *value = ctx->ltcount > 0 ? sum / (double)ctx->ltcount : 0.0;
+  }
   else if (k == "triples_batch") *value = (double)ctx->tri_batch;
   else if (k == "triples_batches") *value = (double)ctx->tri_batches;
   else if (k == "triples_launches") *value = (double)ctx->tri_launches;
