@@ -20,3 +20,10 @@ def test_reference_arm_prints_one_json_line():
     assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert d["config"]["workload"] == "ccsd_fp64_o10_v30_naux120"
+
+
+def test_triples_cpu_baseline_helper():
+    """The triples CPU baseline times the oracle's per-pair form on a bounded sample."""
+    import bench
+    est, sample = bench.oracle_triples_time(dict(bench.WORKLOADS["o10v30"]))
+    assert est > 0.0 and "extrapolated" in sample

@@ -32,3 +32,20 @@ def test_df_rebuild_count_one_row_per_block_closed_form():
         assert flops.df_rebuild_cmacs(v, naux, blk=1) == naux * v ** 3 * (v - 1) / 2
         # any blocking covers the same (a, c, b > a0, d) rectangle rows: never fewer than that
         assert flops.df_rebuild_cmacs(v, naux, blk=3) >= naux * v ** 3 * (v - 1) / 2
+
+
+def test_triples_counts_follow_the_gemm_shapes():
+    """Per triple i<j<k: three e-term GEMMs of P(v) x v over K = v and three m-term GEMMs of
+    v x P(v) over K = o, counted triple by triple."""
+    from paper_2103_08473_gb300 import flops
+    for o, v in ((3, 3), (5, 7), (20, 120)):
+        pv = v * (v - 1) // 2
+        e = m = 0
+        for i in range(o):
+            for j in range(i + 1, o):
+                for k in range(j + 1, o):
+                    e += 3 * pv * v * v
+                    m += 3 * v * pv * o
+        c = flops.triples_cmacs(o, v)
+        assert c["e"] == e and c["m"] == m
+    assert flops.triples_cmacs(2, 10) == {"e": 0.0, "m": 0.0}
