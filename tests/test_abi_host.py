@@ -115,6 +115,10 @@ def test_null_context_calls_return_arg_error(lib):
     assert lib.ccsd_energy(None, None) == ccsd.ERR_ARG
     out = (C.c_double * 3)()
     assert lib.ccsd_triples(None, 0, out, None) == ccsd.ERR_ARG
+    assert lib.ccsd_lambda_iterate(None, 1, None, None) == ccsd.ERR_ARG
+    assert lib.ccsd_lambda_residual(None, None, None, None, None, 0) == ccsd.ERR_ARG
+    assert lib.ccsd_get_lambda(None, None, None, 0) == ccsd.ERR_ARG
+    assert lib.ccsd_density(None, None, 0) == ccsd.ERR_ARG
     lib.ccsd_destroy(None)
 
 
