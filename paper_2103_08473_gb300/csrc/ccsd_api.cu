@@ -7,6 +7,7 @@
 #include <cstring>
 #include <functional>
 #include <map>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -1496,6 +1497,14 @@ void free_ctx(ccsd_ctx* ctx) {
 // the current amplitudes: tau, H^a_c, G^a_c, H^k_i, G^k_i, H^k_c, Yov = H^k_c - 2 F^k_c, Zoo,
 // H^{ak}_{ci} in Hr, C, and A from its packed copy. It writes R1 into S1 and R2 into S2.
 // ---------------------------------------------------------------------------
+// Frees a plan that never reached the context, with the cached permutations it still owns.
+struct PlanDeleter {
+  void operator()(Plan* p) const {
+    for (void* m : p->owned()) cudaFree(m);
+    delete p;
+  }
+};
+
 ccsd_status build_lambda_plan(ccsd_ctx* ctx) {
   const int o = ctx->o, v = ctx->v;
   const int64_t Po = ctx->Po, Pv = ctx->Pv, ov = (int64_t)o * v, n2 = ov * ov, o4 = (int64_t)o * o * o * o;
@@ -1527,8 +1536,9 @@ ccsd_status build_lambda_plan(ccsd_ctx* ctx) {
     CS(dalloc(ctx, &d.state, 1));
     CK(diis_reset(d, ctx->stream));
   }
-  Plan* P = new Plan(o, v, &ctx->lscratch, ctx->stream);
-  ctx->lplan = P;
+  // the context takes the plan only once it is complete (a failed build leaves no plan behind)
+  std::unique_ptr<Plan, PlanDeleter> holder(new Plan(o, v, &ctx->lscratch, ctx->stream));
+  Plan* P = holder.get();
   set_plan_gemm(ctx, P);
   const z one = zmake(1, 0), mone = zmake(-1, 0), half = zmake(0.5, 0), quarter = zmake(0.25, 0),
           eighth = zmake(0.125, 0);
@@ -1785,6 +1795,7 @@ ccsd_status build_lambda_plan(ccsd_ctx* ctx) {
     ctx->split_ws = w;
     ctx->split_ws_bytes = P->aux_bytes();
   }
+  ctx->lplan = holder.release();
   return CCSD_OK;
 }
 
@@ -1800,8 +1811,8 @@ ccsd_status build_density_plan(ccsd_ctx* ctx) {
   CS(dalloc(ctx, &ctx->dq3, (int64_t)v * v));
   CS(dalloc(ctx, &ctx->dgam, (int64_t)n * n));
   CS(dalloc(ctx, &ctx->dgam2, (int64_t)n * n));
-  Plan* D = new Plan(o, v, &ctx->dscratch, ctx->stream);
-  ctx->dplan = D;
+  std::unique_ptr<Plan, PlanDeleter> holder(new Plan(o, v, &ctx->dscratch, ctx->stream));
+  Plan* D = holder.get();
   set_plan_gemm(ctx, D);
   const z one = zmake(1, 0), mone = zmake(-1, 0), half = zmake(0.5, 0), mhalf = zmake(-0.5, 0);
   auto W = [&](z* p, const char* lab) { return D->view(p, lab, false); };
@@ -1837,6 +1848,7 @@ ccsd_status build_density_plan(ccsd_ctx* ctx) {
     ctx->split_ws_bytes = D->aux_bytes();
   }
   (void)n;
+  ctx->dplan = holder.release();
   return CCSD_OK;
 }
 
