@@ -334,3 +334,127 @@ def test_ladder_rows_match_full_ladder():
     got = R.ladder_rows(s.B, o, tau, pairs)
     for n, (a, b) in enumerate(pairs):
         np.testing.assert_allclose(got[n], full[:, :, a, b], atol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# Level shift (keyword .LSHIFT of the input-keyword table; Sec. "Coupled cluster
+# implementation": the update scales the residual by the orbital-energy denominators).
+# Read as: +shift on every virtual orbital energy, in the denominators only. The shift
+# changes the path of the iteration, never its fixed point S = 0.
+# ---------------------------------------------------------------------------
+
+def _hand_denominators(eps, o, shift):
+    """D^a_i = e_i - e_a - shift and D^{ab}_{ij} = e_i + e_j - e_a - e_b - 2 shift, by loops."""
+    v = len(eps) - o
+    D1 = np.empty((o, v))
+    D2 = np.empty((o, o, v, v))
+    for i in range(o):
+        for a in range(v):
+            D1[i, a] = eps[i] - eps[o + a] - shift
+            for j in range(o):
+                for b in range(v):
+                    D2[i, j, a, b] = eps[i] + eps[j] - eps[o + a] - eps[o + b] - 2.0 * shift
+    return D1, D2
+
+
+def _shifted_guess_error(oracle_guess, shift):
+    """max relative distance between the oracle's shifted MP2 guess and S_bf(0) / D_hand."""
+    o, v = 3, 4
+    s, f, Vf, V = _system(o, v, 6, 91, scale=0.5, fock_offdiag=0.2)
+    eps = np.real(np.diag(f))
+    z1, z2 = np.zeros((o, v), complex), np.zeros((o, o, v, v), complex)
+    _, _, S1b, S2b = BF.Space(o, v).projections(f, Vf, z1, z2)
+    D1, D2 = _hand_denominators(eps, o, shift)
+    t1, t2 = oracle_guess(f, V, o, v, shift)
+    want1, want2 = S1b / D1, S2b / D2
+    return max(np.max(np.abs(t1 - want1)) / np.max(np.abs(want1)),
+               np.max(np.abs(t2 - want2)) / np.max(np.abs(want2)))
+
+
+@pytest.mark.parametrize("shift", [0.0, 0.5, 5.0, 20.0])
+def test_shifted_mp2_guess_is_brute_force_driver_over_hand_denominators(shift):
+    """t1 = S1(0)/(D1 - s), t2 = S2(0)/(D2 - 2s), with S(0) from the determinant space
+    and D from the orbital energies by explicit loops."""
+    assert _shifted_guess_error(R.mp2_guess, shift) < 1e-13
+
+
+def _planted(kind):
+    """The oracle's denominators with a plausible misreading of the shift planted."""
+    def den(f, o, shift=0.0):
+        d = np.real(np.diag(f)).astype(np.float64)
+        if kind == "occupied":      # shift added to the occupied energies
+            eo, ev = d[:o] + shift, d[o:]
+        elif kind == "sign":        # shift subtracted from the virtual energies
+            eo, ev = d[:o], d[o:] - shift
+        elif kind == "once":        # doubles shifted once instead of once per virtual label
+            eo, ev = d[:o], d[o:]
+            D1 = eo[:, None] - ev[None, :] - shift
+            D2 = (eo[:, None, None, None] + eo[None, :, None, None] - ev[None, None, :, None]
+                  - ev[None, None, None, :] - shift)
+            return D1, D2
+        D1 = eo[:, None] - ev[None, :]
+        D2 = eo[:, None, None, None] + eo[None, :, None, None] - ev[None, None, :, None] - ev[None, None, None, :]
+        return D1, D2
+    return den
+
+
+@pytest.mark.parametrize("kind", ["occupied", "sign", "once"])
+def test_shift_pin_catches_planted_misreadings(kind, monkeypatch):
+    monkeypatch.setattr(R, "denominators", _planted(kind))
+    assert _shifted_guess_error(R.mp2_guess, 5.0) > 1e-3
+
+
+@pytest.mark.parametrize("shift", [0.5, 5.0])
+def test_one_shifted_step_is_brute_force_residual_over_shifted_denominators(shift):
+    """One Jacobi step from random amplitudes (no DIIS): t + S_bf(t) / D_hand(shift)."""
+    o, v = 3, 4
+    s, f, Vf, V = _system(o, v, 6, 92, scale=0.5, fock_offdiag=0.2)
+    t1, t2 = inputs.random_amplitudes(o, v, 292, scale=0.2)
+    _, _, S1b, S2b = BF.Space(o, v).projections(f, Vf, t1, t2)
+    D1, D2 = _hand_denominators(np.real(np.diag(f)), o, shift)
+    res = R.solve(f, V, o, v, max_iter=1, tol=0.0, diis_dim=0, shift=shift, t_init=(t1, t2))
+    np.testing.assert_allclose(res["t1"], t1 + S1b / D1, atol=1e-13)
+    np.testing.assert_allclose(res["t2"], t2 + S2b / D2, atol=1e-13)
+
+
+SHIFT_CASES = [(2, 4, 6, 93, 0.3, 0.05), (3, 4, 6, 94, 0.3, 0.05), (4, 12, 30, 95, 0.05, 0.0)]
+
+
+@pytest.mark.parametrize("o,v,naux,seed,scale,offdiag", SHIFT_CASES)
+def test_level_shift_moves_the_path_not_the_fixed_point(o, v, naux, seed, scale, offdiag):
+    """Converged solves with shifts 0.5, 5 and 20 reach the unshifted fixed point (energy
+    1e-10, amplitudes 1e-9). At the brute-force sizes, the shifted fixed point also zeroes
+    <Phi_l| exp(-T) H exp(T) |Phi_0> in the determinant space."""
+    s, f, Vf, V = _system(o, v, naux, seed, scale=scale, fock_offdiag=offdiag)
+    ref = R.solve(f, V, o, v, max_iter=400, tol=1e-13)
+    assert ref["converged"]
+    space = BF.Space(o, v) if BF.n_determinants(o, v) <= 500 else None
+    for shift in (0.5, 5.0, 20.0):
+        res = R.solve(f, V, o, v, max_iter=2000, tol=1e-13, shift=shift)
+        assert res["converged"], (shift, res["iterations"], res["norm"])
+        assert abs(res["energy"] - ref["energy"]) < 1e-10
+        assert np.max(np.abs(res["t1"] - ref["t1"])) < 1e-9
+        assert np.max(np.abs(res["t2"] - ref["t2"])) < 1e-9
+        if space is not None:
+            _, _, S1b, S2b = space.projections(f, Vf, res["t1"], res["t2"])
+            assert max(np.max(np.abs(S1b)), np.max(np.abs(S2b))) < 1e-10
+
+
+def test_fixed_point_pin_catches_a_shift_leaking_into_the_residual(monkeypatch):
+    """If the shift entered the residual (a shifted virtual Fock block in S) the iteration
+    would converge to a different point, where the brute-force projections do not vanish."""
+    o, v, naux, seed = 2, 4, 6, 93
+    s, f, Vf, V = _system(o, v, naux, seed, scale=0.3, fock_offdiag=0.05)
+    shift = 5.0
+    good_residual = R.residual
+
+    def leaky(fm, Vm, t1, t2, **kw):
+        g = fm.copy()
+        g[o:, o:] += shift * np.eye(v)
+        return good_residual(g, Vm, t1, t2, **kw)
+
+    monkeypatch.setattr(R, "residual", leaky)
+    res = R.solve(f, V, o, v, max_iter=2000, tol=1e-13, shift=shift)
+    assert res["converged"]
+    _, _, S1b, S2b = BF.Space(o, v).projections(f, Vf, res["t1"], res["t2"])
+    assert max(np.max(np.abs(S1b)), np.max(np.abs(S2b))) > 1e-4
