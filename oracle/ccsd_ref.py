@@ -379,15 +379,76 @@ class DIIS:
         return t1, t2
 
 
+class CROP:
+    """CROP, the conjugate residual method with optimal trial vectors (Ziolkowski, Weijo,
+    Jorgensen and Olsen 2008), the lighter-memory alternative to DIIS the paper names in
+    Sec. "Coupled cluster implementation".
+
+    The subspace holds the OPTIMAL vectors of the last iterations, x~_i and their residuals
+    r~_i (here the preconditioned residual, the update S/D), over the unique amplitudes.
+    Iteration n, with the new trial vector x^(n) and its residual r^(n):
+      1. the subspace is [x~_{n-m+1}, ..., x~_{n-1}, x^(n)] with residuals likewise;
+      2. real c minimises |sum_i c_i r_i|^2 subject to sum_i c_i = 1, from
+         [[B, 1], [1^T, 0]] [c; lam] = [0; 1] with B_ij = Re<r_i, r_j> (as DIIS);
+      3. x~^(n) = sum_i c_i x_i and r~^(n) = sum_i c_i r_i replace (x^(n), r^(n));
+      4. the next trial vector is the preconditioned step from the optimum,
+         x^(n+1) = x~^(n) + r~^(n).
+    At most ``max_vec`` optimal vectors are kept, the oldest dropped first; the usual choice
+    is 3. Before extrapolation starts (iteration < start, or a single vector) c = (1) and
+    the step is the plain update.
+    """
+
+    def __init__(self, max_vec: int = 3):
+        self.max_vec = max_vec
+        self.x: list = []  # optimal (t1, t2)
+        self.r: list = []  # their residuals (e1, e2)
+
+    @staticmethod
+    def _flat(e1, e2):
+        return np.concatenate([e1.ravel(), _unique_t2(e2).ravel()])
+
+    def coefficients(self) -> np.ndarray:
+        m = len(self.r)
+        flat = [self._flat(*r) for r in self.r]
+        Bm = np.zeros((m + 1, m + 1))
+        for a in range(m):
+            for b in range(m):
+                Bm[a, b] = np.real(np.vdot(flat[a], flat[b]))
+        Bm[m, :m] = 1.0
+        Bm[:m, m] = 1.0
+        rhs = np.zeros(m + 1)
+        rhs[m] = 1.0
+        return np.linalg.solve(Bm, rhs)[:m]
+
+    def step(self, t1, t2, e1, e2, extrapolate: bool = True):
+        """Add the trial (t, e = S/D at t); return the next trial vector (step 4)."""
+        self.x.append((t1.copy(), t2.copy()))
+        self.r.append((e1.copy(), e2.copy()))
+        if extrapolate and len(self.x) >= 2:
+            c = self.coefficients()
+            xo = (sum(ci * xi[0] for ci, xi in zip(c, self.x)), sum(ci * xi[1] for ci, xi in zip(c, self.x)))
+            ro = (sum(ci * ri[0] for ci, ri in zip(c, self.r)), sum(ci * ri[1] for ci, ri in zip(c, self.r)))
+            self.x[-1], self.r[-1] = xo, ro
+        if len(self.x) > self.max_vec:
+            self.x.pop(0)
+            self.r.pop(0)
+        xo, ro = self.x[-1], self.r[-1]
+        return xo[0] + ro[0], xo[1] + ro[1]
+
+
 def solve(f: np.ndarray, V: dict, o: int, v: int, max_iter: int = 50, tol: float = 1e-10,
           diis_dim: int = 8, diis_start: int = 2, shift: float = 0.0, t_init=None,
-          callback=None, method: str = "ccsd"):
+          callback=None, method: str = "ccsd", accelerator: str = "diis"):
     """CCSD iterations from the MP2 guess (or ``t_init``); method="ccd" holds t1 at zero (CCD:
     the doubles equations of Appendix A with T1 = 0, the variant the paper also times);
     method="cc2" iterates the CC2 residuals (``residual_cc2``).
 
-    Each iteration: S = residual(t); d = S/D; norm = max|d|; t <- t + d; then, if DIIS is on
-    and the iteration number is >= diis_start with >= 2 stored vectors, t <- sum_i c_i t_i.
+    Each iteration: S = residual(t); d = S/D; norm = max|d|; then
+      * DIIS (accelerator="diis"): t <- t + d; if the iteration number is >= diis_start with
+        >= 2 stored vectors, t <- sum_i c_i t_i;
+      * CROP (accelerator="crop", ``diis_dim`` optimal vectors): t <- x~ + r~ (class CROP),
+        extrapolating from iteration diis_start on;
+      * neither (diis_dim = 0): t <- t + d.
     Stops when norm <= tol. Returns dict(t1, t2, energy, iterations, norm, converged).
     """
     D1, D2 = denominators(f, o, shift)
@@ -400,7 +461,10 @@ def solve(f: np.ndarray, V: dict, o: int, v: int, max_iter: int = 50, tol: float
     elif method not in ("ccsd", "cc2"):
         raise ValueError("method must be 'ccsd', 'ccd' or 'cc2'")
     res = residual_cc2 if method == "cc2" else residual
-    diis = DIIS(diis_dim) if diis_dim > 0 else None
+    if accelerator not in ("diis", "crop"):
+        raise ValueError("accelerator must be 'diis' or 'crop'")
+    diis = DIIS(diis_dim) if diis_dim > 0 and accelerator == "diis" else None
+    crop = CROP(diis_dim) if diis_dim > 0 and accelerator == "crop" else None
     norm = np.inf
     it = 0
     converged = False
@@ -410,7 +474,10 @@ def solve(f: np.ndarray, V: dict, o: int, v: int, max_iter: int = 50, tol: float
         if method == "ccd":
             d1 = np.zeros_like(d1)
         norm = max(np.max(np.abs(d1), initial=0.0), np.max(np.abs(d2), initial=0.0))
-        t1, t2 = t1 + d1, t2 + d2
+        if crop is not None:
+            t1, t2 = crop.step(t1, t2, d1, d2, extrapolate=it >= diis_start)
+        else:
+            t1, t2 = t1 + d1, t2 + d2
         if diis is not None:
             diis.push(t1, t2, d1, d2)
             if it >= diis_start and len(diis.t) >= 2:
