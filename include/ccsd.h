@@ -62,7 +62,8 @@ typedef enum {
   CCSD_ERR_OOM = 2,           /* device allocation failed */
   CCSD_ERR_CUDA = 3,          /* a CUDA runtime call or kernel launch failed */
   CCSD_ERR_NOT_CONVERGED = 4, /* iteration cap reached before the tolerance */
-  CCSD_ERR_DIVERGED = 5,      /* NaN/Inf in the update; amplitudes left at the last finite iterate */
+  CCSD_ERR_DIVERGED = 5,      /* NaN/Inf in the update, or sustained growth of its norm; amplitudes
+                                 left at the last finite iterate */
   CCSD_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up */
   CCSD_ERR_UNSUPPORTED = 7    /* option combination not built */
 } ccsd_status;
@@ -92,6 +93,16 @@ typedef enum {
                            never built. ccsd_get_tensor then has only "tau", "Hvv", "Hoo" and
                            "Hov". */
 } ccsd_method;
+
+typedef enum {
+  CCSD_ACCEL_DIIS = 0, /* Pulay DIIS (Sec. "Coupled cluster implementation"): diis_dim amplitude and
+                          error vectors, t <- sum_i c_i t_i with sum_i c_i = 1 minimising
+                          |sum_i c_i e_i|, e = S/D; the oldest vector is dropped */
+  CCSD_ACCEL_CROP = 1  /* CROP (Ziolkowski et al. 2008; the lighter-memory alternative the same
+                          section names): the same solve, but the subspace keeps the optimal
+                          combinations (sum c t, sum c e) in place of the newest raw pair, so
+                          that few vectors suffice (diis_dim = 3 is the usual choice) */
+} ccsd_accelerator;
 
 typedef struct {
   int max_iter;       /* iteration cap for ccsd_iterate (default 50) */
@@ -125,6 +136,13 @@ typedef struct {
                           may hold; larger GEMMs run in chunks of M, N and then K (default 0 = a
                           quarter of the free device memory at creation, 4 to 16 GB) */
   int method;          /* ccsd_method (default CCSD_METHOD_CCSD) */
+  int accelerator;     /* ccsd_accelerator: the subspace method of ccsd_iterate and ccsd_lambda_iterate
+                          when diis_dim > 0 (default CCSD_ACCEL_DIIS) */
+  int diverge_iters;   /* growth check of ccsd_iterate / ccsd_lambda_iterate / ccsd_batch_iterate: the
+                          update norm rising in this many consecutive iterations, by more than
+                          diverge_factor overall, is CCSD_ERR_DIVERGED (default 8; 0 = off). The rule is
+                          ccsd_divergence_index */
+  double diverge_factor; /* growth check factor (default 1e3) */
 } ccsd_opts;
 
 /* Fill opts with the defaults listed above. */
@@ -155,9 +173,23 @@ ccsd_status ccsd_residual(ccsd_ctx* ctx, const ccsd_z* t1, const ccsd_z* t2, ccs
  * Run up to max_iter iterations from the current amplitudes (max_iter <= 0:
  * opts.max_iter): residual, denominator update t <- t + S/D, DIIS, norm.
  * Returns CCSD_OK on convergence (norm <= opts.tol), CCSD_ERR_NOT_CONVERGED at
- * the cap, CCSD_ERR_DIVERGED on NaN/Inf. iters_done / res_norm may be NULL.
+ * the cap, CCSD_ERR_DIVERGED on NaN/Inf (amplitudes restored to the last finite
+ * iterate) or on sustained growth of the norm (opts.diverge_iters, diverge_factor;
+ * the amplitudes are those of the last, finite, iteration). The growth record runs
+ * across calls and restarts at ccsd_set_amplitudes. iters_done / res_norm may be NULL.
  */
 ccsd_status ccsd_iterate(ccsd_ctx* ctx, int max_iter, int* iters_done, double* res_norm);
+
+/*
+ * The growth rule of the iterations (the paper has no counterpart; a safeguard of the
+ * library), applied to a host sequence of update norms: the 1-based index of the first
+ * norm norms[k] that ends a run of `iters` or more consecutive increases
+ * (norms[k-r] < ... < norms[k], r >= iters) with norms[k] > factor * norms[k-r], the norm
+ * where the run began; 0 if there is none, or if iters <= 0. A non-finite norm ends the
+ * sequence (the iterations report it as divergence on their own). count < 0 or a NULL
+ * norms with count > 0 returns -1.
+ */
+int ccsd_divergence_index(const double* norms, int count, int iters, double factor);
 
 /* Energy of the current amplitudes: sum_ia f_ia t^a_i + 1/4 sum <ij||ab> tau^{ab}_{ij}. */
 ccsd_status ccsd_energy(ccsd_ctx* ctx, ccsd_z* e);
@@ -213,8 +245,9 @@ ccsd_status ccsd_triples(ccsd_ctx* ctx, int max_batch, double* out, double* pair
  *   t^{ab}_{ij}, extended antisymmetrically) at the given multipliers. With l1 and l2 given
  *   they become the context's multipliers; with both NULL the context's own are used.
  * ccsd_lambda_iterate: up to max_iter updates lambda <- lambda + R/D, with the amplitudes'
- *   denominators, level shift, DIIS and norm. Returns CCSD_OK on convergence (norm <= tol),
- *   CCSD_ERR_NOT_CONVERGED at the cap, CCSD_ERR_DIVERGED on NaN/Inf.
+ *   denominators, level shift, subspace accelerator (DIIS or CROP) and norm. Returns CCSD_OK
+ *   on convergence (norm <= tol), CCSD_ERR_NOT_CONVERGED at the cap, CCSD_ERR_DIVERGED on
+ *   NaN/Inf or sustained growth (as ccsd_iterate; the record restarts with each call).
  * ccsd_get_lambda: copy the multipliers out.
  * ccsd_density: gamma (host, n*n, occupied first) =
  *   <0| (1 + Lambda) exp(-T) a+_q a_p exp(T) |0>, less the reference occupation delta_ij, at
@@ -272,7 +305,9 @@ ccsd_status ccsd_query(const ccsd_ctx* ctx, const char* key, double* value);
  * with (k,n) = transB ? B[n*ldb + k] : B[k*ldb + n]. precision: CCSD_PREC_FP64 (FP64
  * tensor-core path). cfg < 0 picks the tile shape, cfg >= 0 forces one (0..6). The
  * optional workspace (ws_elems complex elements, device) enables split-K for small
- * outputs; without it the GEMM does not split. Synchronous on `stream`.
+ * outputs; without it the GEMM does not split, and a workspace smaller than the
+ * preferred split count takes as many partials (M*N each) as it holds, when that is
+ * at least two. Synchronous on `stream`.
  * CCSD_ERR_ARG for negative sizes, NULL pointers or a bad cfg.
  */
 ccsd_status ccsd_zgemm(int precision, int transA, int conjA, int transB, int conjB, long long M, long long N,
@@ -338,10 +373,11 @@ ccsd_status ccsd_split_wait_selftest(void* stream);
  * partials go to a fixed array of 2^18 complex doubles (4 MiB) that the library
  * keeps in device memory; every GPU that loads the library holds it until the
  * process exits. The call allocates nothing (no cudaMalloc, cudaFree or any
- * allocating library routine). The first call on a device, with that device
- * current, looks up the array's device address (cudaGetSymbolAddress); make
- * that first call before any stream capture. Limit: M*N <= 2^17 complex
- * elements (at least two split partials must fit); larger outputs return
+ * allocating library routine). Each call looks up the array's address on the
+ * current device (cudaGetSymbolAddress, which allocates nothing), so the
+ * address stays valid after a device reset. Limit: M*N <= 2^17 complex
+ * elements (at least two split partials must fit, and up to
+ * 2^18 / (M*N) of them are used); larger outputs return
  * CCSD_ERR_ARG with a message naming the limit (use ccsd_zgemm with a
  * workspace for those). All calls share the one array and it keeps the last
  * call's contents; nothing in it has to start at zero, because every partial a
@@ -369,7 +405,7 @@ ccsd_status ccsd_batch_create(int nsys, const int* o, const int* v, const double
                               const ccsd_z* const* B, const int* naux, const ccsd_opts* opts, ccsd_batch** out);
 /* Up to max_iter batch iterations (<= 0: opts.max_iter). Per system (arrays of nsys, may be
  * NULL): iterations run, last norm, and status (CCSD_OK converged, CCSD_ERR_NOT_CONVERGED,
- * CCSD_ERR_DIVERGED). Returns CCSD_OK if every system converged, else CCSD_ERR_NOT_CONVERGED
+ * CCSD_ERR_DIVERGED on NaN/Inf or sustained growth, as ccsd_iterate). Returns CCSD_OK if every system converged, else CCSD_ERR_NOT_CONVERGED
  * (or the first CUDA error). */
 ccsd_status ccsd_batch_iterate(ccsd_batch* b, int max_iter, int* iters_done, double* res_norm, int* status);
 /* Energies of the current amplitudes of every system (nsys values). */

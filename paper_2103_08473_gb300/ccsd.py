@@ -21,6 +21,7 @@ OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NOT_CONVERGED, ERR_DIVERGED, ERR_TIMEOUT, ER
 INT_DF, INT_FULL = 0, 1
 PREC_FP64, PREC_SPLIT = 0, 1
 METHOD_CCSD, METHOD_CCD, METHOD_CC2 = 0, 1, 2
+ACCEL_DIIS, ACCEL_CROP = 0, 1
 
 
 class ccsd_z(C.Structure):
@@ -33,7 +34,8 @@ class ccsd_opts(C.Structure):
                 ("slices", C.c_int), ("store_w", C.c_int), ("profile", C.c_int), ("stream", C.c_void_p),
                 ("split_min_flops", C.c_double), ("df_block", C.c_int), ("autotune", C.c_int),
                 ("digit_bits", C.c_int), ("complex_4m", C.c_int), ("split_budget", C.c_double),
-                ("method", C.c_int)]
+                ("method", C.c_int), ("accelerator", C.c_int), ("diverge_iters", C.c_int),
+                ("diverge_factor", C.c_double)]
 
 
 class CCSDError(RuntimeError):
@@ -51,6 +53,7 @@ SIGNATURES = [
     ("ccsd_create", C.c_int, [C.c_int, C.c_int, _P, _P, C.c_int, _P, C.c_int, C.POINTER(ccsd_opts), C.POINTER(_P)]),
     ("ccsd_residual", C.c_int, [_P, _P, _P, _P, _P, C.c_int]),
     ("ccsd_iterate", C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    ("ccsd_divergence_index", C.c_int, [_P, C.c_int, C.c_int, C.c_double]),
     ("ccsd_energy", C.c_int, [_P, C.POINTER(ccsd_z)]),
     ("ccsd_triples", C.c_int, [_P, C.c_int, _P, _P]),
     ("ccsd_lambda_residual", C.c_int, [_P, _P, _P, _P, _P, C.c_int]),
@@ -314,6 +317,17 @@ class CCSD:
         self._check(self._lib.ccsd_query(self._h, key.encode(), C.byref(val)))
         return val.value
 
+
+
+def divergence_index(norms, iters=8, factor=1e3) -> int:
+    """ccsd_divergence_index: 1-based index of the norm at which the iterations would report
+    sustained growth, 0 if none."""
+    lib = load()
+    a = np.ascontiguousarray(norms, dtype=np.float64)
+    r = lib.ccsd_divergence_index(a.ctypes.data_as(C.c_void_p), len(a), int(iters), float(factor))
+    if r < 0:
+        raise CCSDError(ERR_ARG, "bad norm sequence")
+    return r
 
 
 def zgemm(a, b, c, alpha=1.0, beta=0.0, transA=False, conjA=False, transB=False, conjB=False,

@@ -96,6 +96,25 @@ struct ccsd_ctx {
   int kernels_per_iter = 0;
   int64_t device_bytes = 0;
   int64_t iterations_run = 0;
+  // growth record of the update norm (ccsd_divergence_index's rule, kept across ccsd_iterate calls)
+  struct Growth {
+    int up = 0;
+    double base = 0.0, last = 0.0;
+    bool started = false;
+    void reset() { *this = Growth(); }
+    // true when norm ends a run of >= iters consecutive increases with norm > factor * base
+    bool push(double norm, int iters, double factor) {
+      if (!started || !(norm > last)) {
+        up = 0;
+        base = norm;
+      } else {
+        up += 1;
+      }
+      started = true;
+      last = norm;
+      return iters > 0 && up >= iters && norm > factor * base;
+    }
+  } growth, lgrowth;
   // Lambda equations (built on first use): multipliers, the plan of their residual (the adjoint of
   // the residual plan), its buffers and DIIS subspace; the density plan
   z *l1 = nullptr, *l2 = nullptr;
@@ -1241,6 +1260,10 @@ ccsd_status create_impl(int o, int v, const double* eps, const ccsd_z* fock, ccs
   if (opts) ctx->opts = *opts;
   else ccsd_default_opts(&ctx->opts);
   if (ctx->opts.diis_dim < 0 || ctx->opts.diis_dim > 16) return set_err(ctx, CCSD_ERR_ARG, "diis_dim must be in [0, 16]");
+  if (ctx->opts.accelerator != CCSD_ACCEL_DIIS && ctx->opts.accelerator != CCSD_ACCEL_CROP)
+    return set_err(ctx, CCSD_ERR_ARG, "accelerator must be CCSD_ACCEL_DIIS or CCSD_ACCEL_CROP");
+  if (ctx->opts.diverge_iters < 0 || !(ctx->opts.diverge_factor >= 1.0))
+    return set_err(ctx, CCSD_ERR_ARG, "diverge_iters must be >= 0 and diverge_factor >= 1");
   if (ctx->opts.method != CCSD_METHOD_CCSD && ctx->opts.method != CCSD_METHOD_CCD &&
       ctx->opts.method != CCSD_METHOD_CC2)
     return set_err(ctx, CCSD_ERR_ARG, "unknown method");
@@ -1444,6 +1467,7 @@ ccsd_status create_impl(int o, int v, const double* eps, const ccsd_z* fock, ccs
     d.v = v;
     d.m = ctx->opts.diis_dim;
     d.start = ctx->opts.diis_start;
+    d.crop = ctx->opts.accelerator == CCSD_ACCEL_CROP ? 1 : 0;
     d.L = ov + ctx->Po * ctx->Pv;
     CS(dalloc(ctx, &d.hist_t, d.m * d.L));
     CS(dalloc(ctx, &d.hist_e, d.m * d.L));
@@ -1935,6 +1959,19 @@ void ccsd_default_opts(ccsd_opts* o) {
   o->complex_4m = 0;
   o->split_budget = 0.0;
   o->method = CCSD_METHOD_CCSD;
+  o->accelerator = CCSD_ACCEL_DIIS;
+  o->diverge_iters = 8;
+  o->diverge_factor = 1e3;
+}
+
+int ccsd_divergence_index(const double* norms, int count, int iters, double factor) {
+  if (count < 0 || (count > 0 && !norms)) return -1;
+  ccsd_ctx::Growth g;
+  for (int k = 0; k < count; ++k) {
+    if (!std::isfinite(norms[k])) return 0;
+    if (g.push(norms[k], iters, factor)) return k + 1;
+  }
+  return 0;
 }
 
 ccsd_status ccsd_create(int o, int v, const double* eps, const ccsd_z* fock, ccsd_int_kind kind, const ccsd_z* ints,
@@ -2032,6 +2069,13 @@ ccsd_status ccsd_iterate(ccsd_ctx* ctx, int max_iter, int* iters_done, double* r
     }
     if (nrm <= ctx->opts.tol) {
       st = CCSD_OK;
+      break;
+    }
+    if (ctx->growth.push(nrm, ctx->opts.diverge_iters, ctx->opts.diverge_factor)) {
+      st = set_err(ctx, CCSD_ERR_DIVERGED, "update norm rose in " + std::to_string(ctx->growth.up) +
+                                               " consecutive iterations to " + std::to_string(nrm) + " (from " +
+                                               std::to_string(ctx->growth.base) + ") at iteration " +
+                                               std::to_string(it));
       break;
     }
   }
@@ -2186,6 +2230,7 @@ ccsd_status ccsd_lambda_iterate(ccsd_ctx* ctx, int max_iter, int* iters_done, do
   double nrm = INFINITY;
   ccsd_status st = CCSD_ERR_NOT_CONVERGED;
   const bool timed = ctx->opts.profile != 0;
+  ctx->lgrowth.reset();
   for (it = 1; it <= max_iter; ++it) {
     CK(timed ? run_lambda_timed(ctx) : run_plan(ctx->lplan, ctx->stream));
     CK(denom_update(ctx->l1, ctx->l2, ctx->S1, ctx->S2, ctx->dvec, ctx->o, ctx->v, ctx->opts.level_shift,
@@ -2208,6 +2253,11 @@ ccsd_status ccsd_lambda_iterate(ccsd_ctx* ctx, int max_iter, int* iters_done, do
     }
     if (nrm <= ctx->opts.tol) {
       st = CCSD_OK;
+      break;
+    }
+    if (ctx->lgrowth.push(nrm, ctx->opts.diverge_iters, ctx->opts.diverge_factor)) {
+      st = set_err(ctx, CCSD_ERR_DIVERGED, "multiplier update norm rose in " + std::to_string(ctx->lgrowth.up) +
+                                               " consecutive iterations at iteration " + std::to_string(it));
       break;
     }
   }
@@ -2282,6 +2332,7 @@ ccsd_status ccsd_set_amplitudes(ccsd_ctx* ctx, const ccsd_z* t1, const ccsd_z* t
   CS(copy_in(ctx, ctx->t1, t1, n1, on_device));
   CS(copy_in(ctx, ctx->t2, t2, n2, on_device));
   if (ctx->opts.diis_dim > 0) CK(diis_reset(ctx->diis, ctx->stream));
+  ctx->growth.reset();
   CK(cudaStreamSynchronize(ctx->stream));
   return CCSD_OK;
 }
@@ -2568,6 +2619,8 @@ ccsd_status ccsd_batch_iterate(ccsd_batch* b, int max_iter, int* iters_done, dou
         b->status[k] = CCSD_ERR_DIVERGED;
       } else if (nrm <= c->opts.tol) {
         b->status[k] = CCSD_OK;
+      } else if (c->growth.push(nrm, c->opts.diverge_iters, c->opts.diverge_factor)) {
+        b->status[k] = CCSD_ERR_DIVERGED;
       } else {
         still.push_back(k);
       }

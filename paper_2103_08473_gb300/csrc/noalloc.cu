@@ -12,10 +12,10 @@
 //
 // The array is a file-scope __device__ variable of kStaticSplitElems complex
 // doubles (4 MiB). Every GPU that loads the library holds it until the process
-// exits. In host code its name is only a host-side stand-in, so the device
-// address is looked up with cudaGetSymbolAddress, once per device, on the
-// first call made while that device is current.
-#include <mutex>
+// exits. In host code its name is only a host-side stand-in, so each call looks
+// up the array's device address with cudaGetSymbolAddress while the caller's
+// device is current. The lookup allocates nothing and is redone on every call,
+// so the address stays right after a device reset reloads the module.
 #include <string>
 
 #include "ccsd.h"
@@ -28,10 +28,6 @@ using ccsd::z;
 
 constexpr long long kStaticSplitElems = 1LL << 18;  // complex doubles: 4 MiB
 static __device__ __align__(256) z g_splitk_scratch[kStaticSplitElems];
-
-constexpr int kMaxDevices = 256;
-std::mutex g_mu;
-z* g_scratch_ptr[kMaxDevices] = {};
 
 // The message is read back with ccsd_last_error(NULL).
 ccsd_status fail(ccsd_status st, const std::string& msg) {
@@ -53,22 +49,11 @@ extern "C" ccsd_status ccsd_zgemm_noalloc(int precision, int transA, int conjA, 
     return fail(CCSD_ERR_ARG, "ccsd_zgemm_noalloc: output of " + std::to_string(M * N) +
                                   " complex elements exceeds the limit of " + std::to_string(kStaticSplitElems / 2) +
                                   " (M*N) for the static split-K scratch; use ccsd_zgemm with a workspace");
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return fail(CCSD_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return fail(CCSD_ERR_UNSUPPORTED, "ccsd_zgemm_noalloc: device index too large");
-  z* scratch = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[dev]) {
-      void* p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_splitk_scratch);
-      if (e != cudaSuccess)
-        return fail(CCSD_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-      g_scratch_ptr[dev] = static_cast<z*>(p);
-    }
-    scratch = g_scratch_ptr[dev];
-  }
+  // the array's address on the current device (the lookup allocates nothing)
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_splitk_scratch);
+  if (e != cudaSuccess) return fail(CCSD_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+  z* scratch = static_cast<z*>(p);
   ccsd::ZGemmArgs g;
   g.M = M;
   g.N = N;

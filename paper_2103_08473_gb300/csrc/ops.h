@@ -89,6 +89,7 @@ struct DiisState {
 };
 struct DiisArgs {
   int o = 0, v = 0, m = 0, start = 2;
+  int crop = 0;  // 1: CROP, the newest slot is replaced by the optimal combination after each solve
   int64_t L = 0;
   z* hist_t = nullptr;   // m * L
   z* hist_e = nullptr;   // m * L
@@ -100,7 +101,9 @@ struct DiisArgs {
 int diis_blocks();
 cudaError_t diis_reset(const DiisArgs& d, cudaStream_t s);
 // Push (t, e) (full t1/t2 layout), update the subspace matrix, and if the iteration number is
-// >= start with >= 2 vectors, overwrite t1/t2 with the extrapolated amplitudes.
+// >= start with >= 2 vectors, overwrite t1/t2 with the extrapolated amplitudes. With crop = 1
+// the pushed pair is then replaced in the subspace by the combination itself (sum c t, sum c e)
+// and its rows of the subspace matrix by the matching combinations of the old rows.
 cudaError_t diis_step(const DiisArgs& d, z* t1, z* t2, const z* e1, const z* e2, cudaStream_t s);
 
 }  // namespace ccsd

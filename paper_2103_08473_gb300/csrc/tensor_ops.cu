@@ -461,6 +461,50 @@ __global__ void diis_solve_kernel(DiisArgs d, int nb) {
   }
   for (int r = 0; r < count; ++r) d.coef[r] = x[r];
   st->used = 1;
+  if (!d.crop) return;
+  // CROP: the newest slot will hold the optimal pair (sum_r c_r t_r, sum_r c_r e_r). Its inner
+  // products follow from the old ones: Re<e~, e_s> = sum_r c_r B[r][s], Re<e~, e~> = sum_r c_r
+  // Re<e~, e_r>, all taken from B before it is overwritten.
+  double rowc[16];
+  for (int q = 0; q < count; ++q) {
+    const int sq = (oldest + q) % d.m;
+    double acc = 0.0;
+    for (int r = 0; r < count; ++r) acc += x[r] * d.Bmat[((oldest + r) % d.m) * d.m + sq];
+    rowc[q] = acc;
+  }
+  double bnn = 0.0;
+  for (int r = 0; r < count; ++r) bnn += x[r] * rowc[r];
+  for (int q = 0; q < count; ++q) {
+    const int sq = (oldest + q) % d.m;
+    if (sq == newslot) continue;
+    d.Bmat[newslot * d.m + sq] = rowc[q];
+    d.Bmat[sq * d.m + newslot] = rowc[q];
+  }
+  d.Bmat[newslot * d.m + newslot] = bnn;
+}
+
+// CROP: replace the newest subspace pair by the optimal combination (unique-element layout).
+// Every thread reads all slots at its own elements before writing the newest slot there.
+__global__ void crop_writeback_kernel(DiisArgs d) {
+  const DiisState st = *d.state;
+  if (!st.used) return;
+  const int oldest = (st.head - st.count + d.m) % d.m;
+  const int newest = (st.head - 1 + d.m) % d.m;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < d.L;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    z at = make_double2(0.0, 0.0), ae = make_double2(0.0, 0.0);
+    for (int r = 0; r < st.count; ++r) {
+      const double c = d.coef[r];
+      const int64_t off = (int64_t)((oldest + r) % d.m) * d.L + k;
+      const z ht = d.hist_t[off], he = d.hist_e[off];
+      at.x += c * ht.x;
+      at.y += c * ht.y;
+      ae.x += c * he.x;
+      ae.y += c * he.y;
+    }
+    d.hist_t[(int64_t)newest * d.L + k] = at;
+    d.hist_e[(int64_t)newest * d.L + k] = ae;
+  }
 }
 
 // t = sum_r coef[r] * hist_t[slot(r)], written to the full t1 / t2 (antisymmetric fill).
@@ -634,6 +678,7 @@ cudaError_t diis_step(const DiisArgs& d, z* t1, z* t2, const z* e1, const z* e2,
   diis_solve_kernel<<<1, 1024, 0, s>>>(d, kDiisBlocks);
   const int64_t n = (int64_t)d.o * d.v + (int64_t)d.o * d.o * d.v * d.v;
   diis_combine_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(d, t1, t2);
+  if (d.crop) crop_writeback_kernel<<<grid_for(d.L, kThreads), kThreads, 0, s>>>(d);
   return cudaGetLastError();
 }
 

@@ -243,7 +243,11 @@ template <int BM, int BN, int WM, int WN, bool M3>
 cudaError_t launch(const ZGemmArgs& g, cudaStream_t s) {
   const int64_t tm = (g.M + BM - 1) / BM, tn = (g.N + BN - 1) / BN;
   int splits = splits_for(g, tm * tn * g.batch);
-  if (splits > 1 && (g.ws == nullptr || g.ws_elems < splits * g.M * g.N * g.batch)) splits = 1;
+  // a workspace smaller than the preferred split count takes as many partials as it holds
+  if (splits > 1) {
+    const int64_t fit = g.ws == nullptr ? 0 : g.ws_elems / (g.M * g.N * g.batch);
+    if (fit < splits) splits = fit >= 2 ? (int)fit : 1;
+  }
   const int64_t kslice = splits > 1 ? ((g.K + splits - 1) / splits + BK - 1) / BK * BK : g.K;
   if (splits > 1) splits = (int)((g.K + kslice - 1) / kslice);
   // rasterise so that consecutive blocks share a tile of the larger operand

@@ -51,6 +51,7 @@ def test_default_opts(lib):
     assert o.max_iter == 50 and o.diis_dim == 8 and o.diis_start == 2 and o.tol == 1e-10 and o.store_w == 1
     assert o.split_min_flops == 1e8 and o.precision == 0
     assert o.slices == 0 and o.digit_bits == 0 and o.complex_4m == 0 and o.method == ccsd.METHOD_CCSD
+    assert o.accelerator == ccsd.ACCEL_DIIS and o.diverge_iters == 8 and o.diverge_factor == 1e3
 
 
 def _create(lib, o, v, eps, B, naux, opts=None):
@@ -62,7 +63,7 @@ def _create(lib, o, v, eps, B, naux, opts=None):
     return st, h
 
 
-@pytest.mark.parametrize("case", ["o0", "v0", "naux0", "null_eps", "null_ints", "nonhermitian", "diis17", "bits6", "bits_x_slices", "method3"])
+@pytest.mark.parametrize("case", ["o0", "v0", "naux0", "null_eps", "null_ints", "nonhermitian", "diis17", "bits6", "bits_x_slices", "method3", "accel2", "diverge_neg", "diverge_factor"])
 def test_create_rejects_bad_arguments(lib, case):
     from paper_2103_08473_gb300 import ccsd, inputs
     s = inputs.make_system(2, 3, 4, seed=1)
@@ -86,6 +87,12 @@ def test_create_rejects_bad_arguments(lib, case):
         opts = ccsd.default_opts(precision=ccsd.PREC_SPLIT, digit_bits=6)
     elif case == "method3":
         opts = ccsd.default_opts(method=3)
+    elif case == "accel2":
+        opts = ccsd.default_opts(accelerator=2)
+    elif case == "diverge_neg":
+        opts = ccsd.default_opts(diverge_iters=-1)
+    elif case == "diverge_factor":
+        opts = ccsd.default_opts(diverge_factor=0.5)
     elif case == "bits_x_slices":
         opts = ccsd.default_opts(precision=ccsd.PREC_SPLIT, digit_bits=5, slices=12)
     st, h = _create(lib, o, v, eps, B, naux, opts)
@@ -126,3 +133,29 @@ def test_binding_fails_loudly_without_library(tmp_path):
     from paper_2103_08473_gb300 import ccsd
     with pytest.raises(OSError):
         ccsd.load(str(tmp_path / "missing.so"))
+
+
+def test_divergence_rule_on_synthetic_norm_sequences(lib):
+    """The growth rule the iterations apply (ccsd_divergence_index), on host sequences."""
+    from paper_2103_08473_gb300 import ccsd
+    # converging, and converging with DIIS-like bumps: never
+    assert ccsd.divergence_index(np.geomspace(1.0, 1e-12, 60)) == 0
+    bumpy = [(1.8 if k % 2 else 1.0) * 0.5 ** (k // 2) for k in range(40)]  # up, down, up, ...
+    assert ccsd.divergence_index(bumpy, iters=2, factor=1.5) == 0
+    assert ccsd.divergence_index(bumpy, iters=1, factor=1.5) == 2
+    # steady growth by 3x per iteration from norm 1: the run reaches 8 increases at index 9,
+    # and 3^8 > 1e3 there
+    grow = 3.0 ** np.arange(20)
+    assert ccsd.divergence_index(grow, iters=8, factor=1e3) == 9
+    # slow growth: eight increases, but not by the factor yet; the first index with
+    # 1.5^r > 1e3 is r = 18
+    slow = 1.5 ** np.arange(30)
+    assert ccsd.divergence_index(slow, iters=8, factor=1e3) == 19
+    # a drop restarts the run (and its base)
+    seq = list(3.0 ** np.arange(7)) + [0.5] + list(0.5 * 3.0 ** np.arange(1, 10))
+    assert ccsd.divergence_index(seq, iters=8, factor=1e3) == 16  # 0.5 at index 8 (1-based), then 8 rises
+    # off, empty, non-finite, and bad arguments
+    assert ccsd.divergence_index(grow, iters=0) == 0
+    assert ccsd.divergence_index([], iters=8) == 0
+    assert ccsd.divergence_index([1.0, 2.0, float("nan"), 1e9], iters=1, factor=1.0) == 2
+    assert lib.ccsd_divergence_index(None, 3, 8, 1e3) == -1

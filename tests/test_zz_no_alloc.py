@@ -54,3 +54,26 @@ def test_noalloc_rejects_outputs_beyond_the_static_scratch(env):
     c = torch.zeros((400, 400), dtype=torch.complex128, device="cuda")
     with pytest.raises(ccsd.CCSDError, match="static split-K scratch"):
         ccsd.zgemm_noalloc(a, b, c)
+
+
+def test_noalloc_keeps_split_k_near_its_output_limit(env):
+    """An output just under the 2^17-element limit has room for two split partials in the
+    fixed array: the call still splits K (bitwise equal to ccsd_zgemm given a workspace of
+    the same 2^18 elements, and different in rounding from the unsplit GEMM)."""
+    torch, ccsd = env
+    M, N, K = 362, 362, 4096  # M*N = 131044 <= 2^17
+    rng = np.random.default_rng(7)
+    a, b = _rand(rng, M, K), _rand(rng, K, N)
+    da, db = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    ws = torch.empty(1 << 18, dtype=torch.complex128, device="cuda")
+    split = torch.zeros((M, N), dtype=torch.complex128, device="cuda")
+    ccsd.zgemm(da, db, split, workspace=ws)
+    plain = torch.zeros((M, N), dtype=torch.complex128, device="cuda")
+    ccsd.zgemm(da, db, plain)
+    for _ in range(2):
+        got = torch.zeros((M, N), dtype=torch.complex128, device="cuda")
+        ccsd.zgemm_noalloc(da, db, got)
+        assert torch.equal(got, split)
+    assert not torch.equal(got, plain)
+    exact = a @ b
+    assert np.max(np.abs(got.cpu().numpy() - exact)) <= 1e-13 * np.max(np.abs(exact)) * np.sqrt(K)
