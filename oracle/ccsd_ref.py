@@ -387,7 +387,8 @@ class CROP:
     The subspace holds the OPTIMAL vectors of the last iterations, x~_i and their residuals
     r~_i (here the preconditioned residual, the update S/D), over the unique amplitudes.
     Iteration n, with the new trial vector x^(n) and its residual r^(n):
-      1. the subspace is [x~_{n-m+1}, ..., x~_{n-1}, x^(n)] with residuals likewise;
+      1. the subspace is [x~_{n-m+1}, ..., x~_{n-1}, x^(n)] with residuals likewise (m =
+         ``max_vec`` vectors, the new trial vector included);
       2. real c minimises |sum_i c_i r_i|^2 subject to sum_i c_i = 1, from
          [[B, 1], [1^T, 0]] [c; lam] = [0; 1] with B_ij = Re<r_i, r_j> (as DIIS);
       3. x~^(n) = sum_i c_i x_i and r~^(n) = sum_i c_i r_i replace (x^(n), r^(n));
@@ -424,14 +425,14 @@ class CROP:
         """Add the trial (t, e = S/D at t); return the next trial vector (step 4)."""
         self.x.append((t1.copy(), t2.copy()))
         self.r.append((e1.copy(), e2.copy()))
+        if len(self.x) > self.max_vec:  # the subspace of step 1 holds max_vec vectors, the new one included
+            self.x.pop(0)
+            self.r.pop(0)
         if extrapolate and len(self.x) >= 2:
             c = self.coefficients()
             xo = (sum(ci * xi[0] for ci, xi in zip(c, self.x)), sum(ci * xi[1] for ci, xi in zip(c, self.x)))
             ro = (sum(ci * ri[0] for ci, ri in zip(c, self.r)), sum(ci * ri[1] for ci, ri in zip(c, self.r)))
             self.x[-1], self.r[-1] = xo, ro
-        if len(self.x) > self.max_vec:
-            self.x.pop(0)
-            self.r.pop(0)
         xo, ro = self.x[-1], self.r[-1]
         return xo[0] + ro[0], xo[1] + ro[1]
 

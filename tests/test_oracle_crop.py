@@ -179,3 +179,13 @@ def test_crop_coefficients_minimise_the_error_norm_over_its_optimal_vectors():
     null = np.linalg.svd(np.ones((1, m)))[2][1:].T
     y = np.linalg.lstsq(Er @ null, -Er @ c0, rcond=None)[0]
     np.testing.assert_allclose(acc.coefficients(), c0 + null @ y, rtol=1e-9, atol=1e-11)
+
+
+def test_two_vector_crop_is_not_the_krylov_minimum():
+    """The subspace size counts the new trial vector: CROP with two vectors (one previous optimum
+    and the new trial) is steepest-descent-like and leaves the Krylov minimum, while three
+    vectors (the conjugate residual recurrence) stay on it."""
+    A, b = _linear_problem(40, 1)
+    want = _krylov_min_residuals(A, b, 10)
+    two = _crop_residual_norms(A, b, 10, 2)
+    assert np.max(np.abs(two[3:] / want[3:] - 1)) > 1e-3
