@@ -139,9 +139,17 @@ def max_over_ranks(ms: float, device: str = "cuda") -> float:
     return float(t.item())
 
 
-def whole_job_seconds_per_iteration(ms: float, steps: int, world: int) -> float:
-    """N replicas each doing one iteration in the (slowest) time t: the job does N in t."""
-    return ms / 1e3 / steps / world
+def seconds_per_step(ms: float, steps: int) -> float:
+    """Seconds per step of the slowest rank. Replicas do not make one system iterate faster, so
+    the per-iteration time is not divided by the number of GPUs; the whole job's rate is
+    ``replica_throughput``."""
+    return ms / 1e3 / steps
+
+
+def replica_throughput(ms: float, steps: int, world: int) -> dict:
+    """N replicas each doing `steps` steps within the slowest rank's time: steps/s of the job."""
+    return {"steps_per_s": world * steps / (ms / 1e3), "replicas": world,
+            "note": "independent replicas of the same system, one per GPU; no data-path collective"}
 
 
 def oracle_iteration_time(wl, steps: int = 1, method: str = "ccsd"):
@@ -252,6 +260,52 @@ def timed_iterations(ccmod, cc, stream, warmup, steps, barrier=lambda: None, sam
     return e0.elapsed_time(e1), ops, clocks
 
 
+def split_target_companion(ccmod, inputs, flops, stream, local, meth, n_cmp=2, n_time=3):
+    """The o40/v240/naux800 workload in both precisions on fresh contexts from the MP2 guess:
+    n_cmp iterations each (the split-vs-FP64 energy and amplitude difference after them, and
+    the FP64 time per iteration), then n_time more split iterations timed on their own (the
+    split time per iteration and its ladder launch). Contexts are created one after the other
+    so that only one holds device memory at a time."""
+    import numpy as np
+    wl3 = WORKLOADS["o40v240"]
+    s3 = inputs.make_system(wl3["o"], wl3["v"], wl3["naux"], wl3["seed"])
+    o, v = s3.o, s3.v
+    sampler = ClockSampler(local)
+    t0 = time.perf_counter()
+    cs = make_ctx(ccmod, s3, wl3, "split", SPLIT_SLICES, stream, method=meth)
+    create_split = time.perf_counter() - t0
+    ms_cmp_s, _, _ = timed_iterations(ccmod, cs, stream, 0, n_cmp)
+    e_s, t_s = cs.energy(), cs.get_amplitudes()
+    ms_s, opd_s, clocks_s = timed_iterations(ccmod, cs, stream, 0, n_time, sampler=sampler)
+    bytes_s = cs.query("device_bytes")
+    cs.close()
+    t0 = time.perf_counter()
+    cf = make_ctx(ccmod, s3, wl3, "fp64", None, stream, method=meth)
+    create_fp64 = time.perf_counter() - t0
+    ms_f, _, clocks_f = timed_iterations(ccmod, cf, stream, 0, n_cmp, sampler=sampler)
+    e_f, t_f = cf.energy(), cf.get_amplitudes()
+    bytes_f = cf.query("device_bytes")
+    cf.close()
+    peaks, peak_kind = load_peaks()
+    lad_ms = opd_s.get("ladder:gemm")
+    pairs = SPLIT_SLICES * (SPLIT_SLICES + 1) // 2
+    fp8_fl = pairs * 8.0 * float(flops.pairs(o)) * flops.pairs(v) ** 2
+    fp8_peak = peaks["bf16_tflops"] * 2.0
+    lad_frac = fp8_fl / (lad_ms * 1e-3) / 1e12 / fp8_peak if lad_ms else None
+    amp = float(max(np.max(np.abs(t_s[0] - t_f[0])), np.max(np.abs(t_s[1] - t_f[1]))))
+    return {"workload": wl3["name"], "o": o, "v": v, "naux": wl3["naux"], "level_shift": wl3["level_shift"],
+            "slices": SPLIT_SLICES, "bits_per_slice": SPLIT_BITS, "digit_type": "e4m3",
+            "split_s_per_iteration": ms_s / 1e3 / n_time, "fp64_s_per_iteration": ms_f / 1e3 / n_cmp,
+            "speedup_split_vs_fp64": (ms_f / n_cmp) / (ms_s / n_time),
+            "iterations_compared": n_cmp, "abs_dE_split_vs_fp64": abs(e_s - e_f), "max_amp_err_split_vs_fp64": amp,
+            "energy_fp64": [e_f.real, e_f.imag],
+            "ladder_ms": lad_ms, "ladder_e4m3_frac": lad_frac,
+            "ladder_peak_basis": f"{peak_kind} bf16_tflops (burst) x 2 (nominal dense FP8/BF16 ratio)",
+            "device_bytes": {"split": bytes_s, "fp64": bytes_f},
+            "create_s": {"split": create_split, "fp64": create_fp64},
+            "clocks": {"split": clocks_s, "fp64": clocks_f}}
+
+
 def run_ours(args, wl):
     import numpy as np
     import torch
@@ -340,9 +394,14 @@ def run_ours(args, wl):
                                                           np.max(np.abs(t_s[1] - t_f[1])))),
                    "energy_fp64": [e_f.real, e_f.imag]}
 
+    # the split-precision target workload (o40/v240/naux800): split against FP64 on the same GPU
+    target = None
+    if args.config == "o20v120" and world == 1 and not args.no_split_target and precision == "fp64":
+        target = split_target_companion(ccmod, inputs, flops, stream, local, meth)
+
     if rank != 0:
         return
-    value = whole_job_seconds_per_iteration(ms, args.steps, world)
+    value = seconds_per_step(ms, args.steps)
     peaks, peak_kind = load_peaks()
     lad_ms = opd.get("ladder:gemm")
     lad_fl = flops.ladder_flops_packed(o, v)
@@ -419,9 +478,11 @@ def run_ours(args, wl):
                        "parallelism": "replicas" if world > 1 else "single"},
             "ladder_tflops": lad_tf,
             "gemm_share_of_iteration": gemm_ms / total_op_ms if total_op_ms else None,
-            "roofline": roofline, "split": companion, "fp64_after_n": after_n, "cpu_baseline": cpu,
+            "roofline": roofline, "split": companion, "fp64_after_n": after_n, "split_o40v240": target,
+            "cpu_baseline": cpu,
             "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "clocks": clocks, "gpu_launches": kernels * args.steps,
+            "throughput": replica_throughput(ms, args.steps, world) if world > 1 else None,
             "energy": [e_main.real, e_main.imag],
             "top_ops_ms": {k: round(t, 4) for k, t in top}}
     print(json.dumps(line), flush=True)
@@ -549,7 +610,7 @@ def run_triples(args, wl):
     if world == 1 and not args.no_cpu_baseline:
         est, sample = oracle_triples_time(wl)
         cpu = {"value": est, "unit": "s", "cores": os.cpu_count(), "kind": "oracle", "sample": sample}
-    value = whole_job_seconds_per_iteration(ms, args.steps, world)
+    value = seconds_per_step(ms, args.steps)
     line = {"metric": "triples corrections time (s)", "value": value, "unit": "s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
@@ -566,6 +627,7 @@ def run_triples(args, wl):
             "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": 16 * (o * v + o * o * v * v),
                     "d2h_bytes_per_step": 3 * 8},
             "clocks": clocks, "gpu_launches": launches * args.steps,
+            "throughput": replica_throughput(ms, args.steps, world) if world > 1 else None,
             "energies": res}
     print(json.dumps(line), flush=True)
 
@@ -642,7 +704,7 @@ def run_lambda(args, wl):
         cpu = {"value": time.perf_counter() - t0, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"one Lambda residual of the oracle (torch autograd through the Appendix-A residual, "
                          f"CPU complex128) at {wl['name']}"}
-    line = {"metric": "Lambda iteration time (s)", "value": whole_job_seconds_per_iteration(ms, args.steps, world),
+    line = {"metric": "Lambda iteration time (s)", "value": seconds_per_step(ms, args.steps),
             "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if precision == "fp64" else "e4m3 digits, f32 accumulate, f64", "data": "synthetic",
@@ -658,68 +720,100 @@ def run_lambda(args, wl):
             "cpu_baseline": cpu,
             "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": 16 * (o * v + o * o * v * v),
                     "d2h_bytes_per_step": 16 * (o * v + o * o * v * v)},
-            "clocks": clocks, "gpu_launches": None, "lambda_iterations_before": nops}
+            "clocks": clocks, "gpu_launches": None, "lambda_iterations_before": nops,
+            "throughput": replica_throughput(ms, args.steps, world) if world > 1 else None}
     print(json.dumps(line), flush=True)
 
 
 def run_batch(args, wl):
-    """64 uneven systems solved to convergence in one batch vs one after another."""
+    """64 uneven systems solved to convergence in one batch vs one after another. Under torchrun
+    the systems are partitioned across the ranks by their o^2 v^4 (no exchange while solving);
+    the per-system results come to every rank with one all_gather at the end."""
     import numpy as np
     import torch
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
-    from paper_2103_08473_gb300 import build, inputs
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2103_08473_gb300 import build, inputs, shard
     from paper_2103_08473_gb300 import ccsd as ccmod
 
     ccmod.load(build.build())
-    systems = inputs.make_batch(wl["nsys"], wl["seed"])
-    spec = [(s.o, s.v, s.eps, s.B) for s in systems]
+    shapes = inputs.batch_shapes(wl["nsys"], wl["seed"])
+    n = len(shapes)
+    parts = shard.partition([shard.ladder_cost(o, v) for (o, v, _, _) in shapes], world)
+    mine = parts[rank]
+    systems = {k: inputs.make_system(*shapes[k]) for k in mine}
+    spec = [(systems[k].o, systems[k].v, systems[k].eps, systems[k].B) for k in mine]
     tol, maxit = wl["tol"], 200
     precision = args.precision or wl["precision"]
     slices = args.slices or SPLIT_SLICES
     popts = dict(precision=ccmod.PREC_SPLIT, slices=slices, digit_bits=SPLIT_BITS) if precision == "split" else {}
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
     # warm-up (module load, first graph instantiation)
     with ccmod.Batch(spec[:4], tol=tol, max_iter=maxit, **popts) as b:
         b.iterate(3)
     sampler = ClockSampler(local)
     # batched, end to end from host arrays: create (H2D, integral blocks, MP2 guess, autotune),
     # iterate to convergence, energies back to the host
+    barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     bt = ccmod.Batch(spec, tol=tol, max_iter=maxit, autotune=0 if precision == "split" else 1, **popts)
     torch.cuda.synchronize()
     t_create = time.perf_counter() - t0
     sampler.start()
+    barrier()
     t1 = time.perf_counter()
     st, its, norms, sts = bt.iterate()
     torch.cuda.synchronize()
     t_solve = time.perf_counter() - t1
+    barrier()
     clocks = sampler.stop()
     eb = bt.energies()
     t_e2e = time.perf_counter() - t0
     bt.close()
     # sequential plain solves of the same systems (contexts created beforehand, cost-model tiles)
     ctxs = [ccmod.CCSD(o, v, e, B=B, tol=tol, max_iter=maxit) for (o, v, e, B) in spec]
+    barrier()
     torch.cuda.synchronize()
     t2 = time.perf_counter()
-    seq_e, seq_it = [], []
+    seq_it = []
     for c in ctxs:
         r = c.iterate()
         seq_it.append(r[1])
     torch.cuda.synchronize()
     t_seq = time.perf_counter() - t2
     seq_e = [c.energy() for c in ctxs]
-    launches = int(sum(c.query("kernels_per_iteration") * k for c, k in zip(ctxs, its)))
+    launches = [c.query("kernels_per_iteration") * k for c, k in zip(ctxs, its)]
     for c in ctxs:
         c.close()
-    n = len(spec)
-    dE = max(abs(a - b) for a, b in zip(eb, seq_e))  # batch (this precision) vs sequential plain FP64
+    # per-system rows: batch energy (re, im), status, iterations, sequential energy (re, im),
+    # sequential iterations, kernel launches of the batch solve
+    rows = {k: [eb[q].real, eb[q].imag, sts[q], its[q], seq_e[q].real, seq_e[q].imag, seq_it[q], launches[q]]
+            for q, k in enumerate(mine)}
+    table = shard.gather_results(rows, n, 8)
+    t_solve = max_over_ranks(t_solve * 1e3) / 1e3
+    t_seq = max_over_ranks(t_seq * 1e3) / 1e3
+    t_e2e = max_over_ranks(t_e2e * 1e3) / 1e3
+    t_create = max_over_ranks(t_create * 1e3) / 1e3
+    if rank != 0:
+        return
+    e_batch = table[:, 0] + 1j * table[:, 1]
+    e_seq = table[:, 4] + 1j * table[:, 5]
+    dE = float(np.max(np.abs(e_batch - e_seq)))  # batch (this precision) vs sequential plain FP64
+    all_conv = bool(np.all(table[:, 2] == ccmod.OK))
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         from oracle import ccsd_ref as R
         # the three systems nearest the median ladder cost o^2 v^4, solved fully by the oracle
-        cost = sorted(range(n), key=lambda k: spec[k][0] ** 2 * spec[k][1] ** 4)
+        cost = sorted(range(n), key=lambda k: shard.ladder_cost(shapes[k][0], shapes[k][1]))
         pick = cost[n // 2 - 1:n // 2 + 2]
         tc = time.perf_counter()
         for k in pick:
@@ -728,25 +822,62 @@ def run_batch(args, wl):
         tc = time.perf_counter() - tc
         cpu = {"value": len(pick) / tc, "unit": "systems/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": "the 3 systems nearest the median o^2 v^4 of the 64 ("
-                         + ", ".join(f"o={spec[k][0]} v={spec[k][1]}" for k in pick)
+                         + ", ".join(f"o={shapes[k][0]} v={shapes[k][1]}" for k in pick)
                          + f") solved to {tol:g} by the oracle, integrals included"}
+    h2d = int(sum(16 * sh[2] * (sh[0] + sh[1]) ** 2 + 8 * (sh[0] + sh[1]) for sh in shapes))
+    par = ("one fork/join CUDA graph per batch iteration" if world == 1 else
+           f"{world} GPUs: systems partitioned by o^2 v^4 (largest first, to the least-loaded rank), one "
+           f"fork/join CUDA graph per batch iteration on each; no exchange while solving, one all_gather "
+           f"of the per-system results")
     line = {"metric": "systems/s (64 uneven systems solved to convergence)", "value": n / t_solve,
             "unit": "systems/s", "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": t_solve * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
             "dtype": "f64" if precision == "fp64" else "e4m3 digits, f32 accumulate, f64", "data": "synthetic",
             "config": {"workload": wl["name"], "nsys": n, "tol": tol, "autotune": precision == "fp64",
                        "precision": precision, "slices": slices if precision == "split" else None,
-                       "iterations_max": max(its), "iterations_total": int(sum(its)), "all_converged": st == 0,
-                       "parallelism": "one fork/join CUDA graph per batch iteration"},
-            "sequential": {"systems_per_s": n / t_seq, "seconds": t_seq, "iterations_total": int(sum(seq_it))},
+                       "iterations_max": int(np.max(table[:, 3])), "iterations_total": int(np.sum(table[:, 3])),
+                       "all_converged": all_conv, "parallelism": par,
+                       "systems_per_rank": [len(p) for p in parts],
+                       "cost_per_rank": [sum(shard.ladder_cost(shapes[k][0], shapes[k][1]) for k in p)
+                                         for p in parts]},
+            "sequential": {"systems_per_s": n / t_seq, "seconds": t_seq,
+                           "iterations_total": int(np.sum(table[:, 6]))},
             "speedup_vs_sequential": t_seq / t_solve, "max_abs_dE_batch_vs_sequential_fp64": dE,
             "create_s": t_create, "roofline": None, "cpu_baseline": cpu,
-            "e2e": {"value": n / t_e2e, "unit": "systems/s", "h2d_bytes_per_step": int(sum(B.nbytes + e.nbytes
-                                                                                          for (_, _, e, B) in spec)),
+            "e2e": {"value": n / t_e2e, "unit": "systems/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": 16 * n + 24 * n},
-            "clocks": clocks, "gpu_launches": launches}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+            "clocks": clocks, "gpu_launches": int(np.sum(table[:, 7]))}
+    print(json.dumps(line), flush=True)
+
+
+def batch_once(args, wl):
+    """One batch iteration with all systems active (after creation and two iterations), inside the
+    NVTX range "batch_iteration" and timed with CUDA events on the batch stream, for a launch
+    list of one batch iteration."""
+    import torch
+    from paper_2103_08473_gb300 import build, inputs
+    from paper_2103_08473_gb300 import ccsd as ccmod
+
+    ccmod.load(build.build())
+    systems = inputs.make_batch(wl["nsys"], wl["seed"])
+    spec = [(s.o, s.v, s.eps, s.B) for s in systems]
+    precision = args.precision or wl["precision"]
+    slices = args.slices or SPLIT_SLICES
+    popts = dict(precision=ccmod.PREC_SPLIT, slices=slices, digit_bits=SPLIT_BITS) if precision == "split" else {}
+    stream = torch.cuda.Stream()
+    with ccmod.Batch(spec, tol=wl["tol"], max_iter=200, stream=stream.cuda_stream, **popts) as b:
+        b.iterate(2)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("batch_iteration")
+        e0.record(stream)
+        st, its, norms, sts = b.iterate(1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+    active = sum(1 for k in its if k == 3)
+    print(json.dumps({"batch_iteration_ms": e0.elapsed_time(e1), "systems_active": active,
+                      "precision": precision, "workload": wl["name"]}), flush=True)
 
 
 def residual_once(wl, precision, slices):
@@ -816,6 +947,8 @@ def main():
                     help="default: fp64 for o10v30/o20v120/batch64, split for o40v240/o60v400")
     ap.add_argument("--slices", type=int, default=0, help=f"split digits per operand (default {SPLIT_SLICES})")
     ap.add_argument("--no-split-companion", action="store_true")
+    ap.add_argument("--no-split-target", action="store_true",
+                    help="o20v120: skip the o40v240 split-vs-FP64 companion (split_o40v240 in the line)")
     ap.add_argument("--fp64-companion", type=int, default=0, metavar="N",
                     help="split runs: also run N iterations from the MP2 guess in split and in FP64 and compare")
     ap.add_argument("--gemm-once", nargs=4, metavar=("KIND", "M", "N", "K"),
@@ -828,6 +961,8 @@ def main():
                     help="time the triples corrections E(+T), E((T)), E(-T) on the workload instead of an iteration")
     ap.add_argument("--lambda", dest="lam", action="store_true",
                     help="time iterations of the Lambda equations on the workload instead of the amplitudes'")
+    ap.add_argument("--batch-once", action="store_true",
+                    help="batch64: one profiled batch iteration (NVTX range batch_iteration), then exit")
     ap.add_argument("--residual-once", action="store_true",
                     help="create the context and evaluate one residual eagerly (for ncu captures), no timing")
     args = ap.parse_args()
@@ -837,7 +972,9 @@ def main():
         return
     args.warmup = max(args.warmup, 3)  # timing rule: at least 3 untimed warm-up steps
     wl = WORKLOADS[args.config]
-    if args.config == "batch64":
+    if args.config == "batch64" and args.batch_once:
+        batch_once(args, wl)
+    elif args.config == "batch64":
         run_batch(args, wl)
     elif args.residual_once:
         residual_once(wl, args.precision or wl["precision"], args.slices or SPLIT_SLICES)

@@ -69,6 +69,25 @@ def test_split_full_size_o20_v120_two_iterations(ccsd):
     assert max(np.max(np.abs(t1 - ref["t1"])), np.max(np.abs(t2 - ref["t2"]))) < 1e-8
 
 
+def test_split_full_size_o20_v120_unshifted_tracks_oracle(ccsd):
+    """o20/v120/naux400 without the level shift (undamped updates, DIIS on), in the split form
+    with the default digits and routing: the energy and amplitudes after three iterations
+    from the MP2 guess against the oracle's (the split-precision target |dE| <= 1e-8 Eh).
+    Without the shift the updates are large (norms 0.9, 194, 44), so per-iteration errors are
+    tested on full-size steps, not on steps shrunk by D / (D - 2 shift)."""
+    s = inputs.make_config("o20v120")
+    f = R.fock_matrix(s.eps)
+    V = R.integrals(s.B, s.o)
+    ref = R.solve(f, V, s.o, s.v, max_iter=3, tol=0.0)
+    with ccsd.CCSD(s.o, s.v, s.eps, B=s.B, precision=ccsd.PREC_SPLIT, tol=0.0) as cc:
+        st, it, nrm = cc.iterate(3)
+        e = cc.energy()
+        t1, t2 = cc.get_amplitudes()
+    assert it == 3 and abs(nrm - ref["norm"]) < 1e-8 * ref["norm"]
+    assert abs(e - ref["energy"]) < 1e-8
+    assert max(np.max(np.abs(t1 - ref["t1"])), np.max(np.abs(t2 - ref["t2"]))) < 1e-8
+
+
 def test_split_df_ladder_without_stored_w(ccsd):
     o, v, naux, seed = 6, 29, 40, 211
     s = inputs.make_system(o, v, naux, seed, scale=0.05)
