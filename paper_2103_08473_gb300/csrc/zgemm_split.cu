@@ -1,20 +1,23 @@
 // Split-precision complex GEMM on tcgen05 (see split.h for the scheme).
 //
-// Kernel structure (one CTA per 128 x 128 complex output tile, 6 warps):
+// Kernel structure (one CTA per 128 x BN complex output tile, BN = 128, 96 or 64;
+// 6 warps):
 //   warp 0  TMA producer: per K block (128 bytes of digits per row) and slice
 //           pair of the current level group, loads the A_re, A_im (128 rows) and
-//           B_re, B_im (128 rows) digit tiles into a 3-stage ring of 128B-swizzled
-//           shared tiles. K blocks are the outer loop and the group's pairs the
-//           inner one, so all CTAs walk the same narrow K front of the small
-//           operand and it stays in L2.
-//   warp 1  allocates all 512 TMEM columns; one thread issues the UMMAs
-//           (M = 128, N = 128, K = 32 e4m3 / 16 bf16 per instruction):
+//           B_re, B_im (BN rows) digit tiles into a 3- or 4-stage ring of
+//           128B-swizzled shared tiles. K blocks are the outer loop and the group's
+//           pairs the inner one, so all CTAs walk the same narrow K front of the
+//           small operand and it stays in L2.
+//   warp 1  allocates the TMEM columns (512; 256 for BN = 64); one thread issues
+//           the UMMAs (M = 128, N = BN, K = 32 e4m3 / 16 bf16 per instruction):
 //             re += Ar Br, re += Ai (-Bi), im += Ar Bi, im += Ai Br
-//           into one of two TMEM accumulator sets (re, im: 128 columns each),
+//           into one of two TMEM accumulator sets (re, im: BN columns each),
 //           and commits each smem stage back to the producer.
 //   warps 2-5  epilogue: after each level group, read the FP32 accumulator rows
 //           (tcgen05.ld 32x32b), scale by 2^(e_row + e_col - b L) and add
-//           alpha * value into C in FP64, then release the TMEM set.
+//           alpha * value into C in FP64, then release the TMEM set. With the
+//           operands swapped (a short M on the BN side) the tile is the transpose
+//           of C's and each warp stores 32 consecutive elements of a row of C.
 // Every mbarrier wait is bounded (clock64 budget); a wait that gives up sets the
 // error word and the CTA drains its in-flight copies, frees TMEM and exits.
 #include <cuda_bf16.h>
@@ -31,11 +34,23 @@
 namespace ccsd {
 namespace {
 
-constexpr int kStages = 3;
-constexpr uint32_t kTile = 128 * 128;        // bytes of one 128-row x 128-byte digit tile
-constexpr uint32_t kStageBytes = 4 * kTile;  // A_re, A_im, B_re, B_im
-constexpr uint32_t kSmemBytes = kStages * kStageBytes + 1024 + 256;
 constexpr int kMaxLevels = 16;
+
+// Shared-memory and tensor-memory shape of the main kernel for an output tile of 128 x BN
+// (BN = 128, 96 or 64 columns): a stage holds the A_re, A_im tiles (128 rows) and the B_re,
+// B_im tiles (BN rows) of one K block and digit pair; the two TMEM accumulator sets hold
+// BN real and BN imaginary FP32 columns each.
+template <int BN>
+struct MainTile {
+  static constexpr uint32_t kTileA = 128 * 128;
+  static constexpr uint32_t kTileB = BN * 128;
+  static constexpr uint32_t kStageBytes = 2 * kTileA + 2 * kTileB;
+  static constexpr int kStages = BN == 128 ? 3 : 4;
+  static constexpr uint32_t kSmemBytes = kStages * kStageBytes + 1024 + 256;
+  static constexpr uint32_t kTmemCols = 4 * BN <= 256 ? 256u : 512u;
+  static_assert(BN == 128 || BN == 96 || BN == 64, "output tile width");
+  static_assert(kSmemBytes <= 232448, "shared memory per CTA");
+};
 
 // Level groups are enumerated on the fly by every role in the same order:
 // for level L = 0..lmax (weight 2^{-b(L+2)}), for K chunks of kbper[L] blocks
@@ -59,6 +74,7 @@ struct SplitArgs {
   int* err;
   long long wait_cycles;
   int stall_loads;          // self-test only: the producer issues no loads, so the first wait runs out
+  int transC;               // 1: the kernel's (m, n) is the caller's C[n][m] (operands swapped)
 };
 
 // ---- PTX wrappers ----------------------------------------------------------
@@ -118,10 +134,10 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor: D = F32, A/B K-major, M = 128, N = 128.
-__host__ __device__ constexpr uint32_t make_idesc(int kind, int negB) {
+// Instruction descriptor: D = F32, A/B K-major, M = 128, N = n (a multiple of 16, <= 256).
+__host__ __device__ constexpr uint32_t make_idesc(int kind, int negB, uint32_t n = 128u) {
   return (1u << 4) | ((kind == kSplitBF16 ? 1u : 0u) << 7) | ((kind == kSplitBF16 ? 1u : 0u) << 10) |
-         ((uint32_t)negB << 14) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+         ((uint32_t)negB << 14) | ((n >> 3) << 17) | ((128u >> 4) << 24);
 }
 
 template <int KIND>
@@ -155,10 +171,13 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 
 // ---- the GEMM kernel ----------------------------------------------------------
 
-template <int KIND, bool PROBE>
+template <int KIND, bool PROBE, int BN>
 __global__ void __launch_bounds__(192, 1)
     split_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                  const __grid_constant__ SplitArgs args) {
+  using T = MainTile<BN>;
+  constexpr int kStages = T::kStages;
+  constexpr uint32_t kStageBytes = T::kStageBytes, kTileA = T::kTileA, kTileB = T::kTileB;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -176,7 +195,7 @@ __global__ void __launch_bounds__(192, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tile = blockIdx.x % args.tiles, ks = blockIdx.x / args.tiles;
   const int tm = tile % args.tiles_m, tn = tile / args.tiles_m;
-  const int64_t m0 = (int64_t)tm * 128, n0 = (int64_t)tn * 128;
+  const int64_t m0 = (int64_t)tm * 128, n0 = (int64_t)tn * BN;
   const int klo = ks * args.kb_split, khi = min(args.kblocks, klo + args.kb_split);
   constexpr int BKE = KIND == kSplitBF16 ? 64 : 128;  // digits per 128-byte row segment
 
@@ -195,7 +214,7 @@ __global__ void __launch_bounds__(192, 1)
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
-                 "r"(512));
+                 "r"(T::kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     tc_fence_before();
   }
@@ -224,12 +243,12 @@ __global__ void __launch_bounds__(192, 1)
               }
               const uint32_t sa = base + st * kStageBytes;
               const int x = kb * BKE;
-              mbar_expect_tx(full(st), PROBE ? 2 * kTile : 4 * kTile);
+              mbar_expect_tx(full(st), PROBE ? kTileA + kTileB : 2 * (kTileA + kTileB));
               const int64_t ya = args.a_row0 + m0, yb = args.b_row0 + n0;
               tma_load_2d(sa, &tmA, x, (int)((p * 2 + 0) * args.Mp + ya), full(st));
-              if (!PROBE) tma_load_2d(sa + kTile, &tmA, x, (int)((p * 2 + 1) * args.Mp + ya), full(st));
-              tma_load_2d(sa + 2 * kTile, &tmB, x, (int)((q * 2 + 0) * args.Np + yb), full(st));
-              if (!PROBE) tma_load_2d(sa + 3 * kTile, &tmB, x, (int)((q * 2 + 1) * args.Np + yb), full(st));
+              if (!PROBE) tma_load_2d(sa + kTileA, &tmA, x, (int)((p * 2 + 1) * args.Mp + ya), full(st));
+              tma_load_2d(sa + 2 * kTileA, &tmB, x, (int)((q * 2 + 0) * args.Np + yb), full(st));
+              if (!PROBE) tma_load_2d(sa + 2 * kTileA + kTileB, &tmB, x, (int)((q * 2 + 1) * args.Np + yb), full(st));
             }
         }
       if (!ok) {
@@ -244,7 +263,7 @@ __global__ void __launch_bounds__(192, 1)
   } else if (warp == 1) {
     // ---------------- UMMA issuer ----------------
     if (lane == 0) {
-      const uint32_t id = make_idesc(KIND, 0), idn = make_idesc(KIND, 1);
+      const uint32_t id = make_idesc(KIND, 0, BN), idn = make_idesc(KIND, 1, BN);
       int it = 0, g = 0;
       bool ok = true;
       for (int L = 0; L <= args.lmax && ok; ++L)
@@ -258,7 +277,7 @@ __global__ void __launch_bounds__(192, 1)
             break;
           }
           tc_fence_after();
-          const uint32_t dre = tmem + (uint32_t)buf * 256u, dim = dre + 128u;
+          const uint32_t dre = tmem + (uint32_t)buf * (2u * BN), dim = dre + (uint32_t)BN;
           bool first = true;
           for (int kb = gb0; kb < gb1 && ok; ++kb)
             for (int p = p0; p <= p1; ++p, ++it) {
@@ -273,10 +292,11 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
               for (int kk = 0; kk < 4; ++kk) {
                 const uint32_t acc = (first && kk == 0) ? 0u : 1u;
-                const uint64_t aR = sw128_desc(sa + kk * 32), bR = sw128_desc(sa + 2 * kTile + kk * 32);
+                const uint64_t aR = sw128_desc(sa + kk * 32), bR = sw128_desc(sa + 2 * kTileA + kk * 32);
                 umma<KIND>(dre, aR, bR, id, acc);
                 if (!PROBE) {
-                  const uint64_t aI = sw128_desc(sa + kTile + kk * 32), bI = sw128_desc(sa + 3 * kTile + kk * 32);
+                  const uint64_t aI = sw128_desc(sa + kTileA + kk * 32),
+                                 bI = sw128_desc(sa + 2 * kTileA + kTileB + kk * 32);
                   umma<KIND>(dre, aI, bI, idn, 1u);
                   umma<KIND>(dim, aR, bI, id, acc);
                   umma<KIND>(dim, aI, bR, id, 1u);
@@ -304,7 +324,9 @@ __global__ void __launch_bounds__(192, 1)
     const bool mrow = m < args.M;
     const double rsc = (!PROBE && mrow) ? args.rs[m] : 0.0;
     z* const out = args.ksplits > 1 ? args.part + (int64_t)ks * args.M * args.N : args.C;
-    const int64_t ldo = args.ksplits > 1 ? args.N : args.ldc;
+    // transC: the kernel's (m, n) goes to out[n * ldo + m] (the partials likewise, in the
+    // caller's orientation), so that the 32 lanes of a warp store 32 consecutive elements
+    const int64_t ldo = args.ksplits > 1 ? (args.transC ? args.M : args.N) : args.ldc;
     const z alpha = args.ksplits > 1 ? make_double2(1.0, 0.0) : args.alpha;
     int g = 0;
     bool ok = true;
@@ -320,19 +342,47 @@ __global__ void __launch_bounds__(192, 1)
           break;
         }
         tc_fence_after();
-        const uint32_t trow = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)buf * 256u;
+        const uint32_t trow = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)buf * (2u * BN);
         const double gs = ldexp(1.0, -args.b * (L + 2));
         // real alpha folds into the per-row factor: 1 DMUL + 2 DFMA per complex element
         const bool real_alpha = alpha.y == 0.0;
         const double rowf = rsc * gs * (real_alpha ? alpha.x : 1.0);
 #pragma unroll 1
-        for (int c = 0; c < 128; c += 32) {
+        for (int c = 0; c < BN; c += 32) {
           uint32_t re[32], im[32];
           tmem_ld32(trow + c, re);
-          if (!PROBE) tmem_ld32(trow + 128 + c, im);
+          if (!PROBE) tmem_ld32(trow + BN + c, im);
           tmem_wait_ld();
           if (mrow) {
-            if (PROBE) {
+            if (!PROBE && args.transC) {
+              const double* csc = args.cs + n0 + c;
+              const int64_t rem = args.N - (n0 + c);
+              z* ocol = out + (n0 + c) * ldo + m;
+#pragma unroll
+              for (int j0 = 0; j0 < 32; j0 += 8) {
+                double sc[8];
+                z ov[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                  if (j0 + j < rem) {
+                    sc[j] = csc[j0 + j];
+                    ov[j] = ocol[(int64_t)(j0 + j) * ldo];
+                  }
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                  if (j0 + j < rem) {
+                    const double f = rowf * sc[j];
+                    const double vr = (double)__uint_as_float(re[j0 + j]), vi = (double)__uint_as_float(im[j0 + j]);
+                    if (real_alpha) {
+                      ov[j].x = fma(vr, f, ov[j].x);
+                      ov[j].y = fma(vi, f, ov[j].y);
+                    } else {
+                      ov[j] = zadd(ov[j], zmul(alpha, make_double2(vr * f, vi * f)));
+                    }
+                    ocol[(int64_t)(j0 + j) * ldo] = ov[j];
+                  }
+              }
+            } else if (PROBE) {
               for (int j = 0; j < 32; ++j) {
                 const int64_t n = n0 + c + j;
                 if (n < args.N) args.probe[m * args.N + n] = (double)__uint_as_float(re[j]);
@@ -392,7 +442,7 @@ __global__ void __launch_bounds__(192, 1)
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(T::kTmemCols));
   }
 }
 
@@ -1005,30 +1055,66 @@ bool smallk_eligible(const SplitArgs& a) {
   return true;
 }
 
-// K split across CTAs when the output has too few tiles to fill the GPU.
-// Each split keeps >= 16 K blocks so that a level group's MMA work stays above its
-// FP64 flush in the epilogue.
+// K split across CTAs when the output has too few tiles to fill the GPU, or a few waves of
+// tiles that leave the last wave partly idle. With fewer tiles than SMs the split starts at
+// about two CTAs per SM (a 20 x 20 output with a long K runs on every SM, not on a few);
+// from there, or from no split with one to four waves of tiles, the factor that best fills
+// whole waves (CTAs / (waves x SMs)) is taken where it beats the smaller factors by more
+// than 5%. Each split keeps >= kMinKbPerSplit K blocks so that a level group's MMA work
+// stays above its FP64 flush in the epilogue.
+constexpr int kMinKbPerSplit = 12;
 void plan_ksplit(int64_t tiles, int kblocks, int& ksplits, int& kb_split) {
   ksplits = 1;
   const int64_t sms = num_sms();
-  if (tiles < sms) {
-    int64_t want = (2 * sms + tiles - 1) / tiles;
-    ksplits = (int)std::max<int64_t>(1, std::min<int64_t>(want, kblocks / 16));
-  } else if (tiles < 4 * sms) {
-    // a few waves of tiles: the split factor that best fills whole waves (a last wave of
-    // 1.5 waves leaves a third of the GPU idle), if it beats no split by more than 5%
-    double best = (double)tiles / (double)(((tiles + sms - 1) / sms) * sms);
-    for (int ks = 2; ks <= 8 && ks <= kblocks / 16; ++ks) {
-      const int64_t ctas = tiles * ks;
-      const double fill = (double)ctas / (double)(((ctas + sms - 1) / sms) * sms);
-      if (fill > best + 0.05) {
-        best = fill;
-        ksplits = ks;
+  const int64_t kmax = std::max(1, kblocks / kMinKbPerSplit);
+  auto fill = [&](int64_t ctas) { return (double)ctas / (double)(((ctas + sms - 1) / sms) * sms); };
+  if (tiles > 0 && tiles < 4 * sms) {
+    const int64_t lo = tiles < sms ? std::min<int64_t>((2 * sms + tiles - 1) / tiles, kmax) : 1;
+    const int64_t hi = std::min<int64_t>(kmax, std::max<int64_t>(2 * lo, 32));
+    ksplits = (int)lo;
+    double best = fill(tiles * lo);
+    for (int64_t ks = lo + 1; ks <= hi; ++ks) {
+      const double f = fill(tiles * ks);
+      if (f > best + 0.05) {
+        best = f;
+        ksplits = (int)ks;
       }
     }
   }
   kb_split = (kblocks + ksplits - 1) / ksplits;
   ksplits = (kblocks + kb_split - 1) / kb_split;
+}
+
+// Orientation and tile width of the main kernel for C (M x N): the operand whose rows go to
+// the 128-row side, and BN. The least padded tile area wins, each width weighted by its
+// tensor-pipe efficiency (narrower tiles re-read A from shared memory for fewer columns);
+// a change from 128-wide tiles without swap must gain more than 3%. A short M (few pair
+// rows, e.g. the occupied pairs of the ladder) then swaps to the BN side.
+struct MainTiling {
+  bool swap = false;
+  int bn = 128;
+  int64_t tiles_m = 0, tiles = 0;
+  double area = 0.0;  // padded tile area over the tensor-pipe efficiency
+};
+MainTiling choose_tiling(int64_t M, int64_t N) {
+  static const int widths[3] = {128, 96, 64};
+  static const double eff[3] = {1.0, 0.97, 0.85};
+  MainTiling t;
+  t.area = (double)round_up(M, 128) * (double)round_up(N, 128);
+  for (int sw = 0; sw < 2; ++sw)
+    for (int w = 0; w < 3; ++w) {
+      const int64_t rows = sw ? N : M, cols = sw ? M : N;
+      const double area = (double)round_up(rows, 128) * (double)round_up(cols, widths[w]) / eff[w];
+      if (area < t.area * 0.97) {
+        t.area = area;
+        t.swap = sw != 0;
+        t.bn = widths[w];
+      }
+    }
+  const int64_t rows = t.swap ? N : M, cols = t.swap ? M : N;
+  t.tiles_m = (rows + 127) / 128;
+  t.tiles = t.tiles_m * ((cols + t.bn - 1) / t.bn);
+  return t;
 }
 
 // C = alpha * sum_ks part[ks] + beta * C, summed in split order.
@@ -1049,20 +1135,30 @@ __global__ void part_reduce_kernel(const z* __restrict__ part, int ks, int64_t M
   }
 }
 
-template <int KIND, bool PROBE>
-cudaError_t launch_split(const SliceSet& A, const SliceSet& B, const SplitArgs& a, cudaStream_t s) {
-  auto kern = split_kernel<KIND, PROBE>;
+template <int KIND, bool PROBE, int BN>
+cudaError_t launch_split(const CUtensorMap& mapA, const CUtensorMap& mapB, const SplitArgs& a, cudaStream_t s) {
+  auto kern = split_kernel<KIND, PROBE, BN>;
+  constexpr uint32_t smem = MainTile<BN>::kSmemBytes;
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [&]() {
-    attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
   if (attr_err != cudaSuccess) return attr_err;
   const int64_t grid = (int64_t)a.tiles * a.ksplits;
   if (grid <= 0) return cudaSuccess;
   if (grid > 0x7fffffff) return cudaErrorInvalidValue;
-  kern<<<(unsigned)grid, 192, kSmemBytes, s>>>(A.tmap, B.tmap, a);
+  kern<<<(unsigned)grid, 192, smem, s>>>(mapA, mapB, a);
   return cudaGetLastError();
+}
+
+template <int KIND>
+cudaError_t launch_main(const CUtensorMap& mapA, const CUtensorMap& mapB, const SplitArgs& a, int bn, cudaStream_t s) {
+  switch (bn) {
+    case 96: return launch_split<KIND, false, 96>(mapA, mapB, a, s);
+    case 64: return launch_split<KIND, false, 64>(mapA, mapB, a, s);
+    default: return launch_split<KIND, false, 128>(mapA, mapB, a, s);
+  }
 }
 
 template <int KIND>
@@ -1195,16 +1291,16 @@ double split_cost_estimate(int64_t M, int64_t N, int64_t K, const SplitConfig& c
   // operations/s (fitted to short-K launches, where the flushes dominate), and slicing both operands
   // (read twice, digits written once) at ~5 TB/s. Padding to whole tiles and K blocks counted.
   const int bk = bke(cfg.kind);
-  const double Mp = (double)round_up(M, 128), Np = (double)round_up(N, 128), Kp = (double)round_up(K, bk);
+  const MainTiling tl = choose_tiling(M, N);  // padded area (over the width's efficiency) of the main kernel
+  const double Kp = (double)round_up(K, bk);
   const double pairs = 0.5 * cfg.s * (cfg.s + 1);
-  const double mma = pairs * 8.0 * Mp * Np * Kp / (cfg.kind == kSplitBF16 ? 1.4e15 : 2.8e15);
+  const double mma = pairs * 8.0 * tl.area * Kp / (cfg.kind == kSplitBF16 ? 1.4e15 : 2.8e15);
   SplitArgs a;
   std::memset(&a, 0, sizeof(a));
   const int kblocks = (int)(Kp / bk);
   double groups = 0.0;
   if (!fill_levels(a, cfg.s, cfg.b, kblocks, cfg.kind)) return 1e30;
   for (int L = 0; L <= a.lmax; ++L) groups += std::ceil((double)kblocks / a.kbper[L]);
-  const double tiles = (Mp / 128.0) * (Np / 128.0);
   const double slicing0 = ((double)(M + N) * K * 32.0 + (double)(M + N) * Kp * 2.0 * cfg.s * esize(cfg.kind)) / 5e12;
   if (smallk_eligible(a)) {
     // short K: 128 x 32 tiles with the long side as rows, products at ~40% of the tensor rate
@@ -1215,13 +1311,13 @@ double split_cost_estimate(int64_t M, int64_t N, int64_t K, const SplitConfig& c
     const double store = (double)M * N * 32.0 / 5e12;
     return std::max(sk_mma, store) + slicing0;
   }
-  const double flush = tiles * groups * 16384.0 * 6.0 / 3.8e11;
+  const double flush = (double)tl.tiles * groups * 128.0 * tl.bn * 6.0 / 3.8e11;
   const double slicing = ((double)(M + N) * K * 32.0 + (double)(M + N) * Kp * 2.0 * cfg.s * esize(cfg.kind)) / 5e12;
   return std::max(mma, flush) + slicing;
 }
 
 int64_t split_part_bytes(int64_t M, int64_t N, int64_t K, const SplitConfig& cfg) {
-  const int64_t tiles = ((M + 127) / 128) * ((N + 127) / 128);
+  const int64_t tiles = choose_tiling(M, N).tiles;
   const int kblocks = (int)((std::max<int64_t>(K, 1) + bke(cfg.kind) - 1) / bke(cfg.kind));
   int ks, kbs;
   plan_ksplit(tiles, kblocks, ks, kbs);
@@ -1234,19 +1330,29 @@ cudaError_t split_gemm(const SliceSet& A, const SliceSet& B, z* C, int64_t ldc, 
     return cudaErrorInvalidValue;
   SplitArgs a;
   std::memset(&a, 0, sizeof(a));
-  a.M = A.rows;
-  a.N = B.rows;
-  a.Mp = A.rows_pad;
-  a.Np = B.rows_pad;
-  a.a_row0 = A.row0;
-  a.b_row0 = B.row0;
-  a.tiles_m = (int)((A.rows + 127) / 128);
-  a.tiles = a.tiles_m * (int)((B.rows + 127) / 128);
+  // the failure-path self-test keeps the plain orientation and 128-wide tiles
+  MainTiling tl = stall_loads ? MainTiling() : choose_tiling(A.rows, B.rows);
+  if (stall_loads) {
+    tl.tiles_m = (A.rows + 127) / 128;
+    tl.tiles = tl.tiles_m * ((B.rows + 127) / 128);
+  }
+  const SliceSet& KA = tl.swap ? B : A;  // the kernel's 128-row operand
+  const SliceSet& KB = tl.swap ? A : B;  // its BN-row operand
+  if (tl.tiles > 0x7fffffff) return cudaErrorInvalidValue;
+  a.M = KA.rows;
+  a.N = KB.rows;
+  a.Mp = KA.rows_pad;
+  a.Np = KB.rows_pad;
+  a.a_row0 = KA.row0;
+  a.b_row0 = KB.row0;
+  a.tiles_m = (int)tl.tiles_m;
+  a.tiles = (int)tl.tiles;
+  a.transC = tl.swap ? 1 : 0;
   a.C = C;
   a.ldc = ldc;
   a.alpha = alpha;
-  a.rs = A.scale;
-  a.cs = B.scale;
+  a.rs = KA.scale;
+  a.cs = KB.scale;
   a.err = err;
   a.wait_cycles = wait_cycles > 0 ? wait_cycles : 4000000000LL;  // default ~2 s at 2 GHz
   a.stall_loads = stall_loads;
@@ -1259,11 +1365,15 @@ cudaError_t split_gemm(const SliceSet& A, const SliceSet& B, z* C, int64_t ldc, 
     a.ksplits = 1;
     a.kb_split = kblocks;
   }
-  const int64_t need = a.ksplits > 1 ? (int64_t)a.ksplits * a.M * a.N * (int64_t)sizeof(z) : 0;
-  if (a.ksplits > 1 && (part_ws == nullptr || part_bytes < need)) {
-    a.ksplits = 1;
-    a.kb_split = kblocks;
+  const int64_t part1 = a.M * a.N * (int64_t)sizeof(z);  // one split partial
+  if (a.ksplits > 1 && (part_ws == nullptr || part_bytes < (int64_t)a.ksplits * part1)) {
+    // a smaller workspace: as many partials as it holds (at least two), else no split
+    const int64_t fit = part_ws == nullptr || part1 == 0 ? 0 : part_bytes / part1;
+    a.ksplits = (int)std::max<int64_t>(1, std::min<int64_t>(fit, a.ksplits));
+    a.kb_split = (kblocks + a.ksplits - 1) / a.ksplits;
+    a.ksplits = (kblocks + a.kb_split - 1) / a.kb_split;
   }
+  const int64_t need = a.ksplits > 1 ? (int64_t)a.ksplits * part1 : 0;
   cudaError_t e = cudaSuccess;
   if (a.ksplits > 1) {
     a.part = static_cast<z*>(part_ws);
@@ -1278,9 +1388,17 @@ cudaError_t split_gemm(const SliceSet& A, const SliceSet& B, z* C, int64_t ldc, 
     e = zscale_matrix(g, s);
   }
   if (e != cudaSuccess) return e;
-  e = A.kind == kSplitBF16 ? launch_split<kSplitBF16, false>(A, B, a, s) : launch_split<kSplitE4M3, false>(A, B, a, s);
+  CUtensorMap mapB = KB.tmap;
+  if (tl.bn != 128) {
+    e = encode_map_rows(KB, (uint32_t)tl.bn, &mapB);
+    if (e != cudaSuccess) return e;
+  }
+  e = A.kind == kSplitBF16 ? launch_main<kSplitBF16>(KA.tmap, mapB, a, tl.bn, s)
+                           : launch_main<kSplitE4M3>(KA.tmap, mapB, a, tl.bn, s);
   if (e != cudaSuccess || a.ksplits == 1) return e;
-  part_reduce_kernel<<<grid_for(a.M * a.N, 256), 256, 0, s>>>(a.part, a.ksplits, a.M, a.N, C, ldc, alpha, beta);
+  // the partials are in C's orientation (A.rows x B.rows) whichever operand took the 128-row side
+  part_reduce_kernel<<<grid_for(A.rows * B.rows, 256), 256, 0, s>>>(a.part, a.ksplits, A.rows, B.rows, C, ldc, alpha,
+                                                                      beta);
   return cudaGetLastError();
 }
 
@@ -1334,7 +1452,8 @@ cudaError_t split_probe_raw(int kind, const double* Aint, const double* Bint, in
   a.kbper[0] = a.kblocks;
   a.ksplits = 1;
   a.kb_split = a.kblocks;
-  return kind == kSplitBF16 ? launch_split<kSplitBF16, true>(A, B, a, s) : launch_split<kSplitE4M3, true>(A, B, a, s);
+  return kind == kSplitBF16 ? launch_split<kSplitBF16, true, 128>(A.tmap, B.tmap, a, s)
+                            : launch_split<kSplitE4M3, true, 128>(A.tmap, B.tmap, a, s);
 }
 
 }  // namespace ccsd

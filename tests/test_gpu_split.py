@@ -158,3 +158,36 @@ def test_split_zgemm_k_split_filling_whole_waves(env):
     assert np.array_equal(outs[0], outs[1])
     want = a.cpu().numpy() @ b.cpu().numpy().T - 0.5 * c0
     assert np.max(np.abs(outs[0] - want)) / np.max(np.abs(want)) < 2e-10
+
+
+@pytest.mark.parametrize("M,N,K,tA,cA,tB,cB", [(190, 1500, 1000, 0, 0, 1, 0), (190, 3000, 3000, 0, 0, 1, 1),
+                                              (40, 1500, 1000, 1, 1, 0, 0), (40, 900, 2000, 0, 1, 1, 0),
+                                              (100, 1500, 700, 0, 0, 0, 0)])
+def test_split_zgemm_short_m_on_the_narrow_tile_side(env, M, N, K, tA, cA, tB, cB):
+    """A short M (the occupied pairs of the ladder, 190 at o20/v120) goes to the BN side of the
+    main kernel (96- or 64-wide tiles, output stored transposed), with and without K split;
+    the result is the same GEMM to the digit bound."""
+    torch, ccsd = env
+    rng = np.random.default_rng(M * 7 + N + K)
+    a = _rand(rng, *((K, M) if tA else (M, K)))
+    b = _rand(rng, *((N, K) if tB else (K, N)))
+    c0 = _rand(rng, M, N)
+    oa = (a.T if tA else a)
+    ob = (b.T if tB else b)
+    oa = oa.conj() if cA else oa
+    ob = ob.conj() if cB else ob
+    alpha, beta = 0.5 + 0.25j, -0.75 + 0.5j
+    want = alpha * (oa @ ob) + beta * c0
+    dc = torch.from_numpy(c0).cuda()
+    ccsd.split_zgemm(torch.from_numpy(np.ascontiguousarray(a)).cuda(), torch.from_numpy(np.ascontiguousarray(b)).cuda(),
+                     dc, alpha, beta, transA=bool(tA), conjA=bool(cA), transB=bool(tB), conjB=bool(cB), bits=5,
+                     slices=8)
+    got = dc.cpu().numpy()
+    err = np.max(np.abs(got - want)) / np.max(np.abs(want))
+    assert err < 6e-11, err
+    # run to run bitwise
+    dc2 = torch.from_numpy(c0).cuda()
+    ccsd.split_zgemm(torch.from_numpy(np.ascontiguousarray(a)).cuda(), torch.from_numpy(np.ascontiguousarray(b)).cuda(),
+                     dc2, alpha, beta, transA=bool(tA), conjA=bool(cA), transB=bool(tB), conjB=bool(cB), bits=5,
+                     slices=8)
+    assert torch.equal(dc, dc2)
