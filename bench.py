@@ -326,7 +326,17 @@ def run_ours(args, wl):
     stream = torch.cuda.Stream()  # a real stream: the library captures its iteration graph on it
     m4 = 1 if args.complex_4m else 0
     meth = {"ccsd": ccmod.METHOD_CCSD, "ccd": ccmod.METHOD_CCD, "cc2": ccmod.METHOD_CC2}[args.method]
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info(local)[0]
     cc = make_ctx(ccmod, s, wl, precision, slices, stream, complex_4m=m4, method=meth)
+    torch.cuda.synchronize()
+    # device memory of the context: what its allocations add up to, and what the free memory
+    # reported by the driver fell by (the latter includes allocator rounding)
+    memory = {"ctx_device_bytes": cc.query("device_bytes"),
+              "free_memory_drop_bytes": float(free0 - torch.cuda.mem_get_info(local)[0])}
+    for key in ("plan_scratch_bytes", "plan_cached_bytes", "gemm_workspace_bytes", "split_workspace_bytes",
+                "diis_bytes"):
+        memory[key] = cc.query(key)
 
     def barrier():
         if world > 1:
@@ -374,7 +384,8 @@ def run_ours(args, wl):
                      "max_amp_err_vs_fp64_gpu": float(max(np.max(np.abs(t_split[0] - t_main[0])),
                                                           np.max(np.abs(t_split[1] - t_main[1])))),
                      "iterations_compared": args.warmup + args.steps,
-                     "ladder_ms": opd2.get("ladder:gemm")}
+                     "ladder_ms": opd2.get("ladder:gemm"),
+                     "top_ops_ms": {k: round(t, 4) for k, t in sorted(opd2.items(), key=lambda kv: -kv[1])[:10]}}
 
     # opt-in: both precisions from the MP2 guess for the same number of iterations on fresh
     # contexts (the split-vs-FP64 error after N iterations, and both iteration times)
@@ -483,7 +494,7 @@ def run_ours(args, wl):
             "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "clocks": clocks, "gpu_launches": kernels * args.steps,
             "throughput": replica_throughput(ms, args.steps, world) if world > 1 else None,
-            "energy": [e_main.real, e_main.imag],
+            "energy": [e_main.real, e_main.imag], "device_memory": memory,
             "top_ops_ms": {k: round(t, 4) for k, t in top}}
     print(json.dumps(line), flush=True)
 
@@ -596,9 +607,9 @@ def run_triples(args, wl):
         ex_fl = pairs * 8.0 * cm["e"]
         fp8_peak = peaks["bf16_tflops"] * 2.0
         ach = ex_fl / eg_s / 1e12 if eg_s > 0 else None
-        nl = 3 * nt
-        roofline = {"kernel": "split_smallk_kernel<e4m3> (triples e-terms: one launch per triple and term, "
-                              "M = v(v-1)/2, N = K = v)",
+        nl = 3 * batches
+        roofline = {"kernel": "split_smallk_kernel<e4m3> (triples e-terms: one launch per batch of k and term, "
+                              "M = nk v(v-1)/2 or v(v-1)/2, N = v or nk v, K = v)",
                     "bound": "tensor", "achieved": ach, "peak": fp8_peak, "unit": "TFLOP/s",
                     "frac": (ach / fp8_peak) if ach else None,
                     "peak_basis": f"{peak_kind} bf16_tflops (burst) x 2 (nominal dense FP8/BF16 ratio)",
@@ -614,7 +625,7 @@ def run_triples(args, wl):
     line = {"metric": "triples corrections time (s)", "value": value, "unit": "s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if precision == "fp64" else "e4m3 digits, f32 accumulate, f64 (e-terms); f64 (rest)",
+            "dtype": "f64" if precision == "fp64" else "e4m3 digits, f32 accumulate, f64 (e- and m-terms); f64 (rest)",
             "data": "synthetic",
             "config": {"workload": f"{wl['name']} triples", "o": o, "v": v, "naux": wl["naux"],
                        "precision": precision, "slices": SPLIT_SLICES if precision == "split" else None,
@@ -667,6 +678,7 @@ def run_lambda(args, wl):
     clocks = sampler.stop()
     ms = max_over_ranks(e0.elapsed_time(e1))
     lad_ms = cc.query("lambda_op_ms:L:ladder:gemm")
+    lkern = int(cc.query("lambda_kernels_per_iteration"))
     ring_ms = cc.query("lambda_op_ms:L:ring")
     # end to end through the C ABI: multipliers in from pinned host memory, one residual, out
     l1, l2 = cc.get_lambda()
@@ -720,7 +732,7 @@ def run_lambda(args, wl):
             "cpu_baseline": cpu,
             "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": 16 * (o * v + o * o * v * v),
                     "d2h_bytes_per_step": 16 * (o * v + o * o * v * v)},
-            "clocks": clocks, "gpu_launches": None, "lambda_iterations_before": nops,
+            "clocks": clocks, "gpu_launches": lkern * args.steps, "lambda_iterations_before": nops,
             "throughput": replica_throughput(ms, args.steps, world) if world > 1 else None}
     print(json.dumps(line), flush=True)
 

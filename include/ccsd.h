@@ -80,9 +80,11 @@ typedef enum {
 
 typedef enum {
   CCSD_METHOD_CCSD = 0, /* singles and doubles (Appendix A) */
-  CCSD_METHOD_CCD = 1,  /* doubles only: the same doubles equations with t1 held at zero (its
-                           update is zeroed each iteration; the singles terms are evaluated and
-                           vanish); the variant the paper also times */
+  CCSD_METHOD_CCD = 1,  /* doubles only: the doubles equations of Appendix A at T1 = 0, the
+                           variant the paper also times. The residual plan leaves out every term
+                           with a t1 factor and the intermediates that only feed them (C^{kb}_{ij},
+                           H^k_c, the singles): ccsd_residual returns S1 = 0 and the CCD S2
+                           whatever t1 it is given, and the iterations keep t1 at zero */
   CCSD_METHOD_CC2 = 2   /* CC2 (appendix "Working equations for CC2 amplitude equations"): the
                            singles equations of Appendix A unchanged, the doubles equation
                            S^{ab}_{ij} = <ab||ij>~ + P^-_ab sum_e f_be t^{ae}_{ij}
@@ -123,7 +125,7 @@ typedef struct {
                              that is faster than FP64; the ladder always does; <= 0 sends every GEMM
                              there (default 1e8) */
   int df_block;       /* store_w = 0: virtual indices a per rebuilt block of <ab||cd> rows
-                         (default 0 = as many as fit about 6 GB of (ac|bd)) */
+                         (default 0 = as many as fit about 3 GB of (ac|bd)) */
   int autotune;       /* 1: at creation, time every FP64 GEMM of the plan in each tile shape and keep
                          the fastest (default 0: a cost model picks the shape) */
   int digit_bits;     /* split precision: bits per digit, 1..5 (default 0 = 5). Digits are integers
@@ -134,7 +136,7 @@ typedef struct {
                          1.28x fewer FP64 operations (default 0) */
   double split_budget; /* split precision: bytes of digits (both operands) one tensor-core GEMM call
                           may hold; larger GEMMs run in chunks of M, N and then K (default 0 = a
-                          quarter of the free device memory at creation, 4 to 16 GB) */
+                          quarter of the free device memory at creation, 4 to 8 GB) */
   int method;          /* ccsd_method (default CCSD_METHOD_CCSD) */
   int accelerator;     /* ccsd_accelerator: the subspace method of ccsd_iterate and ccsd_lambda_iterate
                           when diis_dim > 0 (default CCSD_ACCEL_DIIS) */
@@ -143,6 +145,8 @@ typedef struct {
                           diverge_factor overall, is CCSD_ERR_DIVERGED (default 8; 0 = off). The rule is
                           ccsd_divergence_index */
   double diverge_factor; /* growth check factor (default 1e3) */
+  int vovv_block;      /* rows a of <ak||cd> unpacked at a time for the H^{ak}_{ci} term and its Lambda
+                          adjoint (default 0 = as many as fit about 1 GB) */
 } ccsd_opts;
 
 /* Fill opts with the defaults listed above. */
@@ -164,7 +168,10 @@ ccsd_status ccsd_create(int o, int v, const double* eps, const ccsd_z* fock, ccs
 /*
  * Residuals S^a_i, S^{ab}_{ij} of Appendix A at the given amplitudes
  * (t1: o*v, t2: o*o*v*v; outputs r1, r2 of the same sizes). Does not change the
- * context's current amplitudes. t1/t2 may be NULL to use the current ones.
+ * context's current amplitudes: they are restored afterwards from a copy of t1 and of the
+ * unique doubles (i<j, a<b), which rebuilds t2 exactly when it is antisymmetric in both
+ * pairs (as every t2 of the iterations is, to rounding). t1/t2 may be NULL to use the
+ * current ones.
  */
 ccsd_status ccsd_residual(ccsd_ctx* ctx, const ccsd_z* t1, const ccsd_z* t2, ccsd_z* r1, ccsd_z* r2,
                           int on_device);
@@ -174,7 +181,7 @@ ccsd_status ccsd_residual(ccsd_ctx* ctx, const ccsd_z* t1, const ccsd_z* t2, ccs
  * opts.max_iter): residual, denominator update t <- t + S/D, DIIS, norm.
  * Returns CCSD_OK on convergence (norm <= opts.tol), CCSD_ERR_NOT_CONVERGED at
  * the cap, CCSD_ERR_DIVERGED on NaN/Inf (amplitudes restored to the last finite
- * iterate) or on sustained growth of the norm (opts.diverge_iters, diverge_factor;
+ * iterate: t1 and the unique doubles, t2 rebuilt from them) or on sustained growth of the norm (opts.diverge_iters, diverge_factor;
  * the amplitudes are those of the last, finite, iteration). The growth record runs
  * across calls and restarts at ccsd_set_amplitudes. iters_done / res_norm may be NULL.
  */
@@ -287,8 +294,13 @@ ccsd_status ccsd_timings(ccsd_ctx* ctx, const char** names, double* ms, int cap,
 
 /*
  * Scalar facts about a context: "kernels_per_iteration" (kernel nodes of the
- * iteration graph), "device_bytes" (device memory held), "iterations_run",
- * "plan_ops", "o", "v", "lambda_iterations", and with opts.profile = 1
+ * iteration graph), "device_bytes" (device memory the context allocated, the cached
+ * operand permutations of its plans included), and parts of it: "plan_scratch_bytes" (the
+ * residual plan's temporaries), "plan_cached_bytes" (its permuted copies of integral blocks),
+ * "gemm_workspace_bytes", "split_workspace_bytes", "diis_bytes" (the subspace history);
+ * "iterations_run", "plan_ops", "o", "v",
+ * "lambda_iterations", "lambda_kernels_per_iteration" (kernel nodes of the Lambda iteration
+ * graph, captured at the first ccsd_lambda_iterate), and with opts.profile = 1
  * "lambda_op_ms:<op>" (average device ms per Lambda iteration of the Lambda-plan ops named <op>,
  * e.g. "L:ladder:gemm"). Of the last ccsd_triples call: "triples_batch" (triples per
  * batch), "triples_batches", "triples_launches" (kernels launched), and with

@@ -44,7 +44,7 @@ struct ccsd_ctx {
   double* dvec = nullptr;  // real diagonal of the Fock matrix (n)
   z *foo = nullptr, *fov = nullptr, *fvv = nullptr;
   z *oooo = nullptr, *ooov = nullptr, *oovv = nullptr;
-  z *Wpk = nullptr, *vovv_pk = nullptr, *oovv_pk = nullptr, *J = nullptr, *Cinit = nullptr;
+  z *Wpk = nullptr, *vovv_pk = nullptr, *oovv_pk = nullptr, *J = nullptr;
   // amplitudes and residual
   z *t1 = nullptr, *t2 = nullptr, *S1 = nullptr, *S2 = nullptr;
   z *t1_prev = nullptr, *t2_prev = nullptr, *t1_save = nullptr, *t2_save = nullptr;
@@ -65,6 +65,7 @@ struct ccsd_ctx {
   double split_min_flops = 2e10;
   void* split_ws = nullptr;  // per-call digit slices of both operands
   int64_t split_ws_bytes = 0;
+  int64_t plan_cached_bytes = 0;  // permuted copies of constant operands the residual plan keeps
   int64_t split_budget = int64_t(4) << 30;  // digit bytes of both operands per split call
   int* split_err = nullptr;  // set by the tensor-core kernel if a bounded wait gave up
   SliceSet Wsl, tausl;       // <ab||cd> digits (built once) and tau digits (per evaluation)
@@ -130,6 +131,8 @@ struct ccsd_ctx {
   int64_t lambda_iterations = 0;
   // profile = 1: one event per Lambda-plan op boundary, and the summed device time per op
   std::vector<cudaEvent_t> lev;
+  cudaGraphExec_t lgraph = nullptr;  // one Lambda iteration (plan, update, norms, DIIS), captured once
+  int lkernels_per_iter = 0;
   std::vector<double> ltsum;
   int64_t ltcount = 0;
   // the last ccsd_triples call: batch size, batches, kernel launches and (profile = 1) device time of
@@ -472,7 +475,7 @@ std::vector<DfBlock> df_blocks(int64_t v, int64_t blk) {
 ccsd_status plan_df_ladder(ccsd_ctx* ctx, Plan* P) {
   const int64_t v = ctx->v, naux = ctx->naux, Po = ctx->Po, Pv = ctx->Pv;
   int64_t blk = ctx->opts.df_block;
-  if (blk <= 0) blk = std::max<int64_t>(1, (int64_t)(6e9 / (16.0 * (double)v * v * v)));
+  if (blk <= 0) blk = std::max<int64_t>(1, (int64_t)(3e9 / (16.0 * (double)v * v * v)));
   blk = std::min<int64_t>(blk, std::max<int64_t>(v - 1, 1));
   ctx->df_block = (int)blk;
   const auto blocks = df_blocks(v, blk);
@@ -570,7 +573,7 @@ ccsd_status plan_df_ladder(ccsd_ctx* ctx, Plan* P) {
 
 // ---------------------------------------------------------------------------
 // Split GEMMs of the plan in chunks: the digits of both operands of one call are held to a
-// budget (a quarter of the device memory free when the plan is made, 4 to 16 GB) by cutting
+// budget (a quarter of the device memory free when the plan is made, 4 to 8 GB) by cutting
 // M, N (whole 128-row tiles) and, where a single row tile is still too long, K (each K chunk
 // is a GEMM of its own, with its own scales, accumulated in FP64).
 // ---------------------------------------------------------------------------
@@ -580,7 +583,7 @@ int64_t split_call_budget() {
     cudaGetLastError();
     free_b = 0;
   }
-  const int64_t lo = int64_t(4) << 30, hi = int64_t(16) << 30;
+  const int64_t lo = int64_t(4) << 30, hi = int64_t(8) << 30;
   return std::min(hi, std::max(lo, (int64_t)(free_b / 4)));
 }
 
@@ -662,6 +665,11 @@ cudaError_t split_gemm_chunked(ccsd_ctx* ctx, const ZGemmArgs& g, cudaStream_t s
 // The residual plan: Appendix A, one contraction per printed term.
 // Labels i,j,k,l run over occupied and a,b,c,d over virtual spinors.
 // ---------------------------------------------------------------------------
+// Constant operands (integral blocks) of up to this size keep a permuted copy for the plan; larger
+// ones (oovv from o60/v400 on: 9.2 GB) are permuted into the plan's scratch at each use, one more
+// HBM pass per use instead of a resident copy.
+constexpr int64_t kCacheLimitBytes = int64_t(2) << 30;
+
 // The GEMM back end of a plan: split precision where ctx->routes_split says so, else the FP64 DMMA
 // kernel with the context's split-K workspace.
 void set_plan_gemm(ccsd_ctx* ctx, Plan* P) {
@@ -686,11 +694,19 @@ ccsd_status build_residual_plan(ccsd_ctx* ctx) {
   // CC2: the singles of Appendix A with their intermediates tau, H^a_c, H^k_i, H^k_c, and the CC2
   // doubles; the CCSD-only intermediates and doubles terms are not planned
   const bool cc2 = ctx->opts.method == CCSD_METHOD_CC2;
+  // CCD: the doubles equations at T1 = 0. Every term with a t1 factor vanishes, and so does every
+  // term that only feeds one (C^{kb}_{ij} enters S2 only through C t1; S1 is not solved): the
+  // plan leaves them out and writes S1 = 0, whatever t1 holds
+  const bool ccd = ctx->opts.method == CCSD_METHOD_CCD;
+  const double t1f = ccd ? 0.0 : 1.0;  // weight of the t1 t1 products in tau and X
   const int64_t Po = ctx->Po, Pv = ctx->Pv;
   // rows a of <ak||cd> unpacked at a time for the H^{ak}_{ci} term (at most about 1 GB)
-  ctx->vblk_rows = std::max<int64_t>(1, std::min<int64_t>(v, (int64_t)(1.0e9 / (16.0 * o * (double)v * v))));
+  ctx->vblk_rows = ctx->opts.vovv_block > 0
+                       ? std::min<int64_t>(v, ctx->opts.vovv_block)
+                       : std::max<int64_t>(1, std::min<int64_t>(v, (int64_t)(1.0e9 / (16.0 * o * (double)v * v))));
   if (!cc2) CS(dalloc(ctx, &ctx->vblk, ctx->vblk_rows * o * (int64_t)v * v));
   Plan* P = new Plan(o, v, &ctx->scratch, ctx->stream);
+  P->set_cache_limit(kCacheLimitBytes);
   ctx->plan = P;
   // In split mode a single GEMM of at least split_min_flops goes to the tensor-core digit
   // path when its modelled time beats the FP64 path (measured on this chip: 1.3e12 of the
@@ -717,19 +733,20 @@ ccsd_status build_residual_plan(ccsd_ctx* ctx) {
   // (c<d) for S1 (their lifetimes do not overlap)
   z *t1 = ctx->t1, *t2 = ctx->t2, *tau = ctx->tau, *taupk = ctx->tau_pk, *X = ctx->R;
   P->custom("tau", [=](cudaStream_t s) {
-    cudaError_t e = tau_build(t1, t2, tau, o, v, 1.0, 1.0, 1, s);
+    cudaError_t e = tau_build(t1, t2, tau, o, v, 1.0, t1f, 1, s);
     if (e != cudaSuccess) return e;
     return pack_pairs(tau, taupk, o, v, 1, s);
   });
   if (!cc2) {
-    // X^{ad}_{li} = 1/2 t^{ad}_{li} + t^a_l t^d_i (the pair amplitude of the H^{ak}_{ci} term)
-    P->custom("Hvoov", [=](cudaStream_t s) { return tau_build(t1, t2, X, o, v, 0.5, 1.0, 0, s); });
+    // X^{ad}_{li} = 1/2 t^{ad}_{li} + t^a_l t^d_i (the pair amplitude of the H^{ak}_{ci} term), stored
+    // X[i][a][l][d]: the [free][summed] layout its GEMM reads without a permutation
+    P->custom("Hvoov", [=](cudaStream_t s) { return tau_build(t1, t2, X, o, v, 0.5, t1f, 0, s, 1); });
   }
 
   // H^a_c = F^a_c + 1/2 sum_kld V^{kl}_{cd} tau^{da}_{kl}
   P->add("Hvv", W(ctx->Hvv, "ac"), one, V(ctx->fvv, "ac"), false, 0.0);
   P->contract("Hvv", W(ctx->Hvv, "ac"), half, V(ctx->oovv, "klcd"), false, W(tau, "klda"), false, 1.0);
-  if (!cc2) {
+  if (!cc2 && !ccd) {
     // T[i][a][k][c] = sum_d V^{ak}_{cd} t^d_i (the second term of H^{ak}_{ci}) first, into Hr: the rows of
     // <ak||cd> are unpacked from vovv_pk block by block of a (the dense vovv is never stored) and each
     // block is one GEMM writing the columns (a, k, c) of its a range in every row i.
@@ -781,6 +798,8 @@ ccsd_status build_residual_plan(ccsd_ctx* ctx) {
       P->custom("Gvv", [=](cudaStream_t s) { return trace_ik(hr, o, v, gvv, 1.0, 1.0, s); });
     }
     P->contract("Gvv", W(ctx->Gvv, "ac"), mone, V(ctx->fov, "kc"), false, W(t1, "ka"), false, 1.0);
+  } else if (ccd) {
+    P->add("Gvv", W(ctx->Gvv, "ac"), one, W(ctx->Hvv, "ac"), false, 0.0);  // G^a_c = H^a_c at T1 = 0
   }
   // H^k_i = -F^k_i + 1/2 sum_lcd V^{kl}_{cd} tau^{cd}_{li}
   P->add("Hoo", W(ctx->Hoo, "ki"), mone, V(ctx->foo, "ki"), false, 0.0);
@@ -788,20 +807,29 @@ ccsd_status build_residual_plan(ccsd_ctx* ctx) {
   if (!cc2) {
     // G^k_i = H^k_i - sum_lc V^{kl}_{ic} t^c_l - sum_c F^k_c t^c_i
     P->add("Goo", W(ctx->Goo, "ki"), one, W(ctx->Hoo, "ki"), false, 0.0);
-    P->contract("Goo", W(ctx->Goo, "ki"), mone, V(ctx->ooov, "klic"), false, W(t1, "lc"), false, 1.0);
-    P->contract("Goo", W(ctx->Goo, "ki"), mone, V(ctx->fov, "kc"), false, W(t1, "ic"), false, 1.0);
+    if (!ccd) {
+      P->contract("Goo", W(ctx->Goo, "ki"), mone, V(ctx->ooov, "klic"), false, W(t1, "lc"), false, 1.0);
+      P->contract("Goo", W(ctx->Goo, "ki"), mone, V(ctx->fov, "kc"), false, W(t1, "ic"), false, 1.0);
+    }
   }
-  // H^k_c = F^k_c + sum_ld V^{kl}_{cd} t^d_l
-  P->add("Hov", W(ctx->Hov, "kc"), one, V(ctx->fov, "kc"), false, 0.0);
-  P->contract("Hov", W(ctx->Hov, "kc"), one, V(ctx->oovv, "klcd"), false, W(t1, "ld"), false, 1.0);
+  // H^k_c = F^k_c + sum_ld V^{kl}_{cd} t^d_l (it feeds S1 only: not needed in CCD)
+  if (!ccd) {
+    P->add("Hov", W(ctx->Hov, "kc"), one, V(ctx->fov, "kc"), false, 0.0);
+    P->contract("Hov", W(ctx->Hov, "kc"), one, V(ctx->oovv, "klcd"), false, W(t1, "ld"), false, 1.0);
+  }
   if (!cc2) {
     // H^{ak}_{ci} (stored [i][a][k][c]) = V^{ak}_{ci} + sum_d V^{ak}_{cd} t^d_i - sum_l V^{kl}_{ic} t^a_l
     //                                   + sum_ld V^{kl}_{cd} (1/2 t^{ad}_{li} + t^a_l t^d_i)
-    P->add("Hvoov", W(ctx->Hr, "iakc"), one, V(ctx->J, "iakc"), false, 1.0);
-    P->contract("Hvoov", W(ctx->Hr, "iakc"), mone, V(ctx->ooov, "klic"), false, W(t1, "la"), false, 1.0);
-    P->contract("Hvoov", W(ctx->Hr, "iakc"), one, W(X, "liad"), false, V(ctx->oovv, "klcd"), false, 1.0);
+    // (in CCD the t1 terms are absent and V^{ak}_{ci} starts Hr)
+    P->add("Hvoov", W(ctx->Hr, "iakc"), one, V(ctx->J, "iakc"), false, ccd ? 0.0 : 1.0);
+    if (!ccd)
+      P->contract("Hvoov", W(ctx->Hr, "iakc"), mone, V(ctx->ooov, "klic"), false, W(t1, "la"), false, 1.0);
+    P->contract("Hvoov", W(ctx->Hr, "iakc"), one, W(X, "iald"), false, V(ctx->oovv, "klcd"), false, 1.0);
+  }
+  if (!cc2 && !ccd) {
     // C^{kb}_{ij} = V^{ij+}_{kb} + P^-_ij sum_c V^{bk}_{ci} t^c_j - 1/2 sum_cd V^{bk}_{cd} tau^{cd}_{ij}
-    P->add("C", W(ctx->C, "kbij"), one, V(ctx->Cinit, "kbij"), false, 0.0);
+    // V^{ij+}_{kb} = conj(<ij||kb>), read from ooov[i][j][k][b] with the permutation of the add
+    P->add("C", W(ctx->C, "kbij"), one, V(ctx->ooov, "ijkb"), true, 0.0);
     // Yovoo[i][b][k][j] = sum_c V^{bk}_{ci} t^c_j = sum_c J[i][b][k][c] t^c_j
     P->contract("C", W(ctx->Yovoo, "ibkj"), one, V(ctx->J, "ibkc"), false, W(t1, "jc"), false, 0.0);
     P->add("C", W(ctx->C, "kbij"), one, W(ctx->Yovoo, "ibkj"), false, 1.0);
@@ -832,11 +860,15 @@ ccsd_status build_residual_plan(ccsd_ctx* ctx) {
       });
       P->add("C", W(ctx->C, "kbij"), one, W(ctx->Yfull, "bkij"), false, 1.0);
     }
+  }
+  if (!cc2) {
     // A^{kl}_{ij} = V^{kl}_{ij} + P^-_ij sum_c V^{kl}_{ic} t^c_j + 1/2 sum_cd V^{kl}_{cd} tau^{cd}_{ij}
     P->add("A", W(ctx->Afull, "klij"), one, V(ctx->oooo, "klij"), false, 0.0);
-    P->contract("A", W(ctx->Yoooo, "klij"), one, V(ctx->ooov, "klic"), false, W(t1, "jc"), false, 0.0);
-    P->add("A", W(ctx->Afull, "klij"), one, W(ctx->Yoooo, "klij"), false, 1.0);
-    P->add("A", W(ctx->Afull, "klij"), mone, W(ctx->Yoooo, "klji"), false, 1.0);
+    if (!ccd) {
+      P->contract("A", W(ctx->Yoooo, "klij"), one, V(ctx->ooov, "klic"), false, W(t1, "jc"), false, 0.0);
+      P->add("A", W(ctx->Afull, "klij"), one, W(ctx->Yoooo, "klij"), false, 1.0);
+      P->add("A", W(ctx->Afull, "klij"), mone, W(ctx->Yoooo, "klji"), false, 1.0);
+    }
     {
       z *af = ctx->Afull, *apk = ctx->Apk;
       P->custom("A:pack", [=](cudaStream_t s) { return pack_pairs(af, apk, o, o, 1, s); });
@@ -870,7 +902,7 @@ ccsd_status build_residual_plan(ccsd_ctx* ctx) {
     // sum_c P^-_ij (V^{cj+}_{ab} t^c_i):  W1[i][j][a][b] = sum_c t^c_i conj(V^{cj}_{ab}); (a, b) is the
     // antisymmetric pair of both, so the product is formed packed, straight from vovv_pk
     // (W1pk[i][(j, P(a,b))] in R) and added to S2 with (i, j) antisymmetrised in one pass
-    {
+    if (!ccd) {
       ZGemmArgs g;
       g.M = o;
       g.N = (int64_t)o * Pv;
@@ -900,9 +932,11 @@ ccsd_status build_residual_plan(ccsd_ctx* ctx) {
     P->add("gvv", W(ctx->S2, "ijab"), one, W(ctx->R, "aijb"), false, 1.0);
     P->add("gvv", W(ctx->S2, "ijab"), mone, W(ctx->R, "bija"), false, 1.0);
     // sum_k P^-_ab (C^{ka}_{ij} t^b_k):  W1[a][i][j][b] = sum_k C^{ka}_{ij} t^b_k
-    P->contract("ct1", W(ctx->R, "aijb"), one, W(ctx->C, "kaij"), false, W(t1, "kb"), false, 0.0);
-    P->add("ct1", W(ctx->S2, "ijab"), one, W(ctx->R, "aijb"), false, 1.0);
-    P->add("ct1", W(ctx->S2, "ijab"), mone, W(ctx->R, "bija"), false, 1.0);
+    if (!ccd) {
+      P->contract("ct1", W(ctx->R, "aijb"), one, W(ctx->C, "kaij"), false, W(t1, "kb"), false, 0.0);
+      P->add("ct1", W(ctx->S2, "ijab"), one, W(ctx->R, "aijb"), false, 1.0);
+      P->add("ct1", W(ctx->S2, "ijab"), mone, W(ctx->R, "bija"), false, 1.0);
+    }
     // 1/2 sum_kl A^{kl}_{ij} tau^{ab}_{kl}  (packed: sum_{k<l})
     {
       ZGemmArgs g;  // Hpk[P(ij)][P(ab)] = sum_{k<l} A^{kl}_{ij} tau^{ab}_{kl}
@@ -1062,39 +1096,46 @@ ccsd_status build_residual_plan(ccsd_ctx* ctx) {
     P->add("cc2:foo", W(ctx->S2, "ijab"), one, W(ctx->R, "jiab"), false, 1.0);
   }
 
-  // S^a_i
-  P->add("S1", W(ctx->S1, "ia"), one, V(ctx->fov, "ia"), true, 0.0);                                   // F^{i+}_a
-  P->contract("S1", W(ctx->S1, "ia"), one, W(ctx->Hvv, "ac"), false, W(t1, "ic"), false, 1.0);          // H^a_c t^c_i
-  P->contract("S1", W(ctx->S1, "ia"), one, W(ctx->Hoo, "ki"), false, W(t1, "ka"), false, 1.0);          // H^k_i t^a_k
-  P->contract("S1", W(ctx->S1, "ia"), one, W(ctx->Hov, "kc"), false, W(t2, "ikac"), false, 1.0);        // H^k_c t^{ac}_{ik}
-  P->add("S1", W(ctx->Yov, "kc"), one, W(ctx->Hov, "kc"), false, 0.0);                                   // H^k_c - 2 F^k_c
-  P->add("S1", W(ctx->Yov, "kc"), zmake(-2, 0), V(ctx->fov, "kc"), false, 1.0);
-  P->contract("S1", W(ctx->Zoo, "ik"), one, W(ctx->Yov, "kc"), false, W(t1, "ic"), false, 0.0);
-  P->contract("S1", W(ctx->S1, "ia"), one, W(ctx->Zoo, "ik"), false, W(t1, "ka"), false, 1.0);
-  {
-    // 1/2 sum_kcd V^{ak}_{cd} tau^{cd}_{ik} = sum_k sum_{c<d}: tau packed over (c<d) into R, one GEMM
-    // against vovv_pk
-    z *taur = ctx->R;
-    P->custom("S1", [=](cudaStream_t s) { return pack_pairs(tau, taur, (int64_t)o * o, v, 0, s); });
-    ZGemmArgs g;
-    g.M = o;
-    g.N = v;
-    g.K = (int64_t)o * Pv;
-    g.A = ctx->R;
-    g.lda = (int64_t)o * Pv;
-    g.B = ctx->vovv_pk;
-    g.ldb = (int64_t)o * Pv;
-    g.transB = 1;
-    g.C = ctx->S1;
-    g.ldc = v;
-    g.beta = one;
-    P->gemm("S1:gemm", g);
+  // S^a_i (CCD: zero)
+  if (ccd) {
+    z* s1 = ctx->S1;
+    P->custom("S1", [=](cudaStream_t s) { return cudaMemsetAsync(s1, 0, sizeof(z) * (size_t)o * v, s); });
+  } else {
+    P->add("S1", W(ctx->S1, "ia"), one, V(ctx->fov, "ia"), true, 0.0);                                   // F^{i+}_a
+    P->contract("S1", W(ctx->S1, "ia"), one, W(ctx->Hvv, "ac"), false, W(t1, "ic"), false, 1.0);          // H^a_c t^c_i
+    P->contract("S1", W(ctx->S1, "ia"), one, W(ctx->Hoo, "ki"), false, W(t1, "ka"), false, 1.0);          // H^k_i t^a_k
+    P->contract("S1", W(ctx->S1, "ia"), one, W(ctx->Hov, "kc"), false, W(t2, "ikac"), false, 1.0);        // H^k_c t^{ac}_{ik}
+    P->add("S1", W(ctx->Yov, "kc"), one, W(ctx->Hov, "kc"), false, 0.0);                                   // H^k_c - 2 F^k_c
+    P->add("S1", W(ctx->Yov, "kc"), zmake(-2, 0), V(ctx->fov, "kc"), false, 1.0);
+    P->contract("S1", W(ctx->Zoo, "ik"), one, W(ctx->Yov, "kc"), false, W(t1, "ic"), false, 0.0);
+    P->contract("S1", W(ctx->S1, "ia"), one, W(ctx->Zoo, "ik"), false, W(t1, "ka"), false, 1.0);
+    {
+      // 1/2 sum_kcd V^{ak}_{cd} tau^{cd}_{ik} = sum_k sum_{c<d}: tau packed over (c<d) into R, one GEMM
+      // against vovv_pk
+      z *taur = ctx->R;
+      P->custom("S1", [=](cudaStream_t s) { return pack_pairs(tau, taur, (int64_t)o * o, v, 0, s); });
+      ZGemmArgs g;
+      g.M = o;
+      g.N = v;
+      g.K = (int64_t)o * Pv;
+      g.A = ctx->R;
+      g.lda = (int64_t)o * Pv;
+      g.B = ctx->vovv_pk;
+      g.ldb = (int64_t)o * Pv;
+      g.transB = 1;
+      g.C = ctx->S1;
+      g.ldc = v;
+      g.beta = one;
+      P->gemm("S1:gemm", g);
+    }
+    P->contract("S1", W(ctx->S1, "ia"), half, V(ctx->ooov, "klic"), false, W(tau, "klca"), false, 1.0);    // 1/2 V^{kl}_{ic} tau^{ca}_{kl}
+    P->contract("S1", W(ctx->S1, "ia"), mone, V(ctx->J, "iakc"), false, W(t1, "kc"), false, 1.0);         // - V^{ak}_{ci} t^c_k
   }
-  P->contract("S1", W(ctx->S1, "ia"), half, V(ctx->ooov, "klic"), false, W(tau, "klca"), false, 1.0);    // 1/2 V^{kl}_{ic} tau^{ca}_{kl}
-  P->contract("S1", W(ctx->S1, "ia"), mone, V(ctx->J, "iakc"), false, W(t1, "kc"), false, 1.0);         // - V^{ak}_{ci} t^c_k
 
   if (P->status() != cudaSuccess) return set_err(ctx, CCSD_ERR_CUDA, "residual plan: " + P->error());
   for (void* m : P->owned()) ctx->allocs.push_back(m);
+  ctx->device_bytes += P->owned_bytes();
+  ctx->plan_cached_bytes = P->owned_bytes();
   P->owned().clear();
   CS(dalloc(ctx, &ctx->scratch, P->scratch_elems()));
   ctx->gemm_ws_elems = P->gemm_workspace_elems();
@@ -1150,13 +1191,36 @@ void collect_timers(ccsd_ctx* ctx, size_t last) {
   ctx->tcount += 1;
 }
 
+// The amplitude backup (before an iteration, or around ccsd_residual with the caller's amplitudes)
+// keeps t1 and the unique doubles (i<j, a<b): t2 is antisymmetric in both pairs, and the restore
+// rebuilds it from them (its diagonal pairs are zero), exactly for antisymmetric amplitudes, in a
+// quarter of the memory of a full copy.
+cudaError_t backup_amplitudes(ccsd_ctx* ctx, z* t1_to, z* t2pk_to) {
+  const int64_t n1 = (int64_t)ctx->o * ctx->v;
+  cudaError_t e = cudaMemcpyAsync(t1_to, ctx->t1, n1 * sizeof(z), cudaMemcpyDeviceToDevice, ctx->stream);
+  if (e == cudaSuccess) e = pack_pairs(ctx->t2, t2pk_to, ctx->o, ctx->v, 1, ctx->stream);
+  return e;
+}
+
+cudaError_t restore_amplitudes(ccsd_ctx* ctx, const z* t1_from, const z* t2pk_from) {
+  const int64_t n1 = (int64_t)ctx->o * ctx->v;
+  cudaError_t e = cudaMemcpyAsync(ctx->t1, t1_from, n1 * sizeof(z), cudaMemcpyDeviceToDevice, ctx->stream);
+  if (e != cudaSuccess) return e;
+  UnpackArgs u;
+  u.in = t2pk_from;
+  u.out = ctx->t2;
+  u.n1 = ctx->o;
+  u.n2 = ctx->v;
+  u.unpack_rows = 1;
+  u.beta = 0.0;
+  return unpack_pairs(u, ctx->stream);
+}
+
 // One iteration: backup, residual, t <- t + S/D (S <- S/D), norms, DIIS.
 cudaError_t iteration_ops(ccsd_ctx* ctx, bool timed) {
-  const int64_t n1 = (int64_t)ctx->o * ctx->v, n2 = n1 * ctx->o * ctx->v;
+  const int64_t n1 = (int64_t)ctx->o * ctx->v;
   const size_t nops = ctx->plan->ops().size();
-  cudaError_t e = cudaMemcpyAsync(ctx->t1_prev, ctx->t1, n1 * sizeof(z), cudaMemcpyDeviceToDevice, ctx->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(ctx->t2_prev, ctx->t2, n2 * sizeof(z), cudaMemcpyDeviceToDevice, ctx->stream);
+  cudaError_t e = backup_amplitudes(ctx, ctx->t1_prev, ctx->t2_prev);
   if (e == cudaSuccess) e = run_ops(ctx, timed);
   // CCD: the singles equations are not solved, t1 stays zero (its update is zeroed)
   if (e == cudaSuccess && ctx->opts.method == CCSD_METHOD_CCD)
@@ -1264,6 +1328,7 @@ ccsd_status create_impl(int o, int v, const double* eps, const ccsd_z* fock, ccs
     return set_err(ctx, CCSD_ERR_ARG, "accelerator must be CCSD_ACCEL_DIIS or CCSD_ACCEL_CROP");
   if (ctx->opts.diverge_iters < 0 || !(ctx->opts.diverge_factor >= 1.0))
     return set_err(ctx, CCSD_ERR_ARG, "diverge_iters must be >= 0 and diverge_factor >= 1");
+  if (ctx->opts.vovv_block < 0) return set_err(ctx, CCSD_ERR_ARG, "vovv_block must be >= 0");
   if (ctx->opts.method != CCSD_METHOD_CCSD && ctx->opts.method != CCSD_METHOD_CCD &&
       ctx->opts.method != CCSD_METHOD_CC2)
     return set_err(ctx, CCSD_ERR_ARG, "unknown method");
@@ -1409,13 +1474,7 @@ ccsd_status create_impl(int o, int v, const double* eps, const ccsd_z* fock, ccs
   }
   // derived constant layouts
   CS(dalloc(ctx, &ctx->oovv_pk, ctx->Po * ctx->Pv));
-  CS(dalloc(ctx, &ctx->Cinit, ov * oo));
   CK(pack_pairs(ctx->oovv, ctx->oovv_pk, o, v, 1, ctx->stream));
-  {
-    const int64_t d_ooov[4] = {o, o, o, v};  // [i][j][k][b] -> Cinit[k][b][i][j] = conj
-    const int pC[4] = {2, 3, 0, 1};
-    CK(permute4(ctx->ooov, d_ooov, pC, ctx->Cinit, zmake(1, 0), 0.0, 1, ctx->stream));
-  }
 
   // amplitudes, residuals and intermediates
   const int64_t n2 = oo * vv;
@@ -1424,7 +1483,7 @@ ccsd_status create_impl(int o, int v, const double* eps, const ccsd_z* fock, ccs
   CS(dalloc(ctx, &ctx->S1, ov));
   CS(dalloc(ctx, &ctx->S2, n2));
   CS(dalloc(ctx, &ctx->t1_prev, ov));
-  CS(dalloc(ctx, &ctx->t2_prev, n2));
+  CS(dalloc(ctx, &ctx->t2_prev, ctx->Po * ctx->Pv));  // the backup: unique doubles only
   // the backup of ccsd_residual (amplitudes given by the caller) and the one an iteration keeps
   // for a non-finite update are never live at the same time: one buffer serves both
   ctx->t1_save = ctx->t1_prev;
@@ -1441,14 +1500,28 @@ ccsd_status create_impl(int o, int v, const double* eps, const ccsd_z* fock, ccs
   CS(dalloc(ctx, &ctx->Hr, n2));
   CS(dalloc(ctx, &ctx->R, n2));
   CS(dalloc(ctx, &ctx->C, ov * oo));
-  CS(dalloc(ctx, &ctx->Yovoo, ov * oo));
-  CS(dalloc(ctx, &ctx->Ypk, ov * ctx->Po));
-  CS(dalloc(ctx, &ctx->Yfull, ov * oo));
+  {
+    // Yovoo, Yfull and Ypk are temporaries of the C^{kb}_{ij} block only, which runs while R is
+    // free (after the H^{ak}_{ci} term has read X from it, before the ring product): they live
+    // in R when they fit
+    auto r16 = [](int64_t x) { return (x + 15) / 16 * 16; };
+    const int64_t y1 = r16(ov * oo), yp = ov * ctx->Po;
+    if (2 * y1 + yp <= n2) {
+      ctx->Yovoo = ctx->R;
+      ctx->Yfull = ctx->R + y1;
+      ctx->Ypk = ctx->R + 2 * y1;
+    } else {
+      CS(dalloc(ctx, &ctx->Yovoo, ov * oo));
+      CS(dalloc(ctx, &ctx->Ypk, ov * ctx->Po));
+      CS(dalloc(ctx, &ctx->Yfull, ov * oo));
+    }
+  }
   CS(dalloc(ctx, &ctx->Afull, oo * oo));
   CS(dalloc(ctx, &ctx->Yoooo, oo * oo));
   CS(dalloc(ctx, &ctx->Apk, ctx->Po * ctx->Po));
+  // the hole-ladder product (Hpk) is unpacked into S2 before the particle ladder writes Lpk
   CS(dalloc(ctx, &ctx->Lpk, ctx->Po * ctx->Pv));
-  CS(dalloc(ctx, &ctx->Hpk, ctx->Po * ctx->Pv));
+  ctx->Hpk = ctx->Lpk;
   CS(dalloc(ctx, &ctx->upd_partials, 2 * update_blocks()));
   CS(dalloc(ctx, &ctx->stats, 4));
   CS(dalloc(ctx, &ctx->e_partials, energy_blocks()));
@@ -1498,6 +1571,7 @@ void free_ctx(ccsd_ctx* ctx) {
   if (!ctx) return;
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+  if (ctx->lgraph) cudaGraphExecDestroy(ctx->lgraph);
   for (auto e : ctx->tev) cudaEventDestroy(e);
   for (void* p : ctx->allocs) cudaFree(p);
   for (Plan* P : {ctx->plan, ctx->lplan, ctx->dplan})
@@ -1532,36 +1606,46 @@ struct PlanDeleter {
 ccsd_status build_lambda_plan(ccsd_ctx* ctx) {
   const int o = ctx->o, v = ctx->v;
   const int64_t Po = ctx->Po, Pv = ctx->Pv, ov = (int64_t)o * v, n2 = ov * ov, o4 = (int64_t)o * o * o * o;
-  CS(dalloc(ctx, &ctx->l1, ov));
-  CS(dalloc(ctx, &ctx->l2, n2));
-  for (z** p : {&ctx->lG, &ctx->ltaub, &ctx->lHrb, &ctx->lXb, &ctx->lzb}) CS(dalloc(ctx, p, n2));
-  for (z** p : {&ctx->lCb, &ctx->lCanti, &ctx->lCp}) CS(dalloc(ctx, p, ov * o * o));
-  for (z** p : {&ctx->lAb, &ctx->lAanti, &ctx->lAfull}) CS(dalloc(ctx, p, o4));
-  CS(dalloc(ctx, &ctx->lpk, (int64_t)o * o * Pv));
-  CS(dalloc(ctx, &ctx->lpk2, Po * Pv));
-  CS(dalloc(ctx, &ctx->lout, Po * Pv));
-  CS(dalloc(ctx, &ctx->lout2, (int64_t)o * o * Pv));
-  CS(dalloc(ctx, &ctx->lout3, (int64_t)o * o * Pv));
-  CS(dalloc(ctx, &ctx->lGvvb, (int64_t)v * v));
-  CS(dalloc(ctx, &ctx->lHvvb, (int64_t)v * v));
-  CS(dalloc(ctx, &ctx->lGoob, (int64_t)o * o));
-  CS(dalloc(ctx, &ctx->lHoob, (int64_t)o * o));
-  CS(dalloc(ctx, &ctx->lHovb, ov));
+  // buffers an earlier build that failed (out of memory further on) already allocated are reused
+  auto once = [ctx](auto** p, int64_t count) { return *p ? CCSD_OK : dalloc(ctx, p, count); };
+  CS(once(&ctx->l1, ov));
+  CS(once(&ctx->l2, n2));
+  for (z** p : {&ctx->lG, &ctx->ltaub, &ctx->lHrb, &ctx->lXb, &ctx->lzb}) CS(once(p, n2));
+  for (z** p : {&ctx->lCb, &ctx->lCanti, &ctx->lCp}) CS(once(p, ov * o * o));
+  for (z** p : {&ctx->lAb, &ctx->lAanti, &ctx->lAfull}) CS(once(p, o4));
+  CS(once(&ctx->lpk, (int64_t)o * o * Pv));
+  CS(once(&ctx->lpk2, Po * Pv));
+  CS(once(&ctx->lout, Po * Pv));
+  CS(once(&ctx->lout2, (int64_t)o * o * Pv));
+  CS(once(&ctx->lout3, (int64_t)o * o * Pv));
+  CS(once(&ctx->lGvvb, (int64_t)v * v));
+  CS(once(&ctx->lHvvb, (int64_t)v * v));
+  CS(once(&ctx->lGoob, (int64_t)o * o));
+  CS(once(&ctx->lHoob, (int64_t)o * o));
+  CS(once(&ctx->lHovb, ov));
   CK(cudaMemsetAsync(ctx->l1, 0, ov * sizeof(z), ctx->stream));
   CK(cudaMemsetAsync(ctx->l2, 0, n2 * sizeof(z), ctx->stream));
   if (ctx->opts.diis_dim > 0) {
     DiisArgs& d = ctx->ldiis;
+    const DiisArgs earlier = d;
     d = ctx->diis;  // same shape and options; its own history
-    CS(dalloc(ctx, &d.hist_t, d.m * d.L));
-    CS(dalloc(ctx, &d.hist_e, d.m * d.L));
-    CS(dalloc(ctx, &d.Bmat, (int64_t)d.m * d.m));
-    CS(dalloc(ctx, &d.coef, d.m));
-    CS(dalloc(ctx, &d.partials, (int64_t)d.m * diis_blocks()));
-    CS(dalloc(ctx, &d.state, 1));
+    d.hist_t = earlier.hist_t;
+    d.hist_e = earlier.hist_e;
+    d.Bmat = earlier.Bmat;
+    d.coef = earlier.coef;
+    d.partials = earlier.partials;
+    d.state = earlier.state;
+    CS(once(&d.hist_t, d.m * d.L));
+    CS(once(&d.hist_e, d.m * d.L));
+    CS(once(&d.Bmat, (int64_t)d.m * d.m));
+    CS(once(&d.coef, d.m));
+    CS(once(&d.partials, (int64_t)d.m * diis_blocks()));
+    CS(once(&d.state, 1));
     CK(diis_reset(d, ctx->stream));
   }
   // the context takes the plan only once it is complete (a failed build leaves no plan behind)
   std::unique_ptr<Plan, PlanDeleter> holder(new Plan(o, v, &ctx->lscratch, ctx->stream));
+  holder->set_cache_limit(kCacheLimitBytes);
   Plan* P = holder.get();
   set_plan_gemm(ctx, P);
   const z one = zmake(1, 0), mone = zmake(-1, 0), half = zmake(0.5, 0), quarter = zmake(0.25, 0),
@@ -1807,8 +1891,9 @@ ccsd_status build_lambda_plan(ccsd_ctx* ctx) {
 
   if (P->status() != cudaSuccess) return set_err(ctx, CCSD_ERR_CUDA, "lambda plan: " + P->error());
   for (void* m : P->owned()) ctx->allocs.push_back(m);
+  ctx->device_bytes += P->owned_bytes();
   P->owned().clear();
-  CS(dalloc(ctx, &ctx->lscratch, P->scratch_elems()));
+  CS(once(&ctx->lscratch, P->scratch_elems()));
   if (P->gemm_workspace_elems() > ctx->gemm_ws_elems) {
     CS(dalloc(ctx, &ctx->gemm_ws, P->gemm_workspace_elems()));
     ctx->gemm_ws_elems = P->gemm_workspace_elems();
@@ -1859,6 +1944,7 @@ ccsd_status build_density_plan(ccsd_ctx* ctx) {
   D->contract("D:vv", W(ctx->dgvv, "ab"), one, W(t1, "ma"), false, W(l1, "mb"), false, 1.0);
   if (D->status() != cudaSuccess) return set_err(ctx, CCSD_ERR_CUDA, "density plan: " + D->error());
   for (void* m : D->owned()) ctx->allocs.push_back(m);
+  ctx->device_bytes += D->owned_bytes();
   D->owned().clear();
   CS(dalloc(ctx, &ctx->dscratch, D->scratch_elems()));
   if (D->gemm_workspace_elems() > ctx->gemm_ws_elems) {
@@ -1894,18 +1980,33 @@ cudaError_t run_plan(Plan* P, cudaStream_t s) {
 
 // The Lambda plan with an event at every op boundary (profile = 1); lambda_collect adds the
 // elapsed times once the stream is synchronised.
+void lambda_timers_init(ccsd_ctx* ctx) {
+  if (!ctx->lev.empty()) return;
+  const size_t n = ctx->lplan->ops().size();
+  ctx->lev.resize(n + 1);
+  for (auto& ev : ctx->lev) cudaEventCreate(&ev);
+  ctx->ltsum.assign(n, 0.0);
+}
+
 cudaError_t run_lambda_timed(ccsd_ctx* ctx) {
   auto& ops = ctx->lplan->ops();
-  if (ctx->lev.empty()) {
-    ctx->lev.resize(ops.size() + 1);
-    for (auto& ev : ctx->lev) cudaEventCreate(&ev);
-    ctx->ltsum.assign(ops.size(), 0.0);
-  }
-  cudaError_t e = cudaEventRecord(ctx->lev[0], ctx->stream);
+  lambda_timers_init(ctx);
+  cudaError_t e = cudaEventRecordWithFlags(ctx->lev[0], ctx->stream, cudaEventRecordExternal);
   for (size_t k = 0; k < ops.size() && e == cudaSuccess; ++k) {
     e = ops[k].run(ctx->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(ctx->lev[k + 1], ctx->stream);
+    if (e == cudaSuccess) e = cudaEventRecordWithFlags(ctx->lev[k + 1], ctx->stream, cudaEventRecordExternal);
   }
+  return e;
+}
+
+// One Lambda iteration: the plan (timed or not), t <- t + R/D on the multipliers, norms, DIIS.
+cudaError_t lambda_iteration_ops(ccsd_ctx* ctx, bool timed) {
+  cudaError_t e = timed ? run_lambda_timed(ctx) : run_plan(ctx->lplan, ctx->stream);
+  if (e == cudaSuccess)
+    e = denom_update(ctx->l1, ctx->l2, ctx->S1, ctx->S2, ctx->dvec, ctx->o, ctx->v, ctx->opts.level_shift,
+                     ctx->upd_partials, ctx->stream);
+  if (e == cudaSuccess) e = norm_finalize(ctx->upd_partials, update_blocks(), ctx->stats, ctx->stream);
+  if (e == cudaSuccess && ctx->opts.diis_dim > 0) e = diis_step(ctx->ldiis, ctx->l1, ctx->l2, ctx->S1, ctx->S2, ctx->stream);
   return e;
 }
 
@@ -1962,6 +2063,7 @@ void ccsd_default_opts(ccsd_opts* o) {
   o->accelerator = CCSD_ACCEL_DIIS;
   o->diverge_iters = 8;
   o->diverge_factor = 1e3;
+  o->vovv_block = 0;
 }
 
 int ccsd_divergence_index(const double* norms, int count, int iters, double factor) {
@@ -1994,8 +2096,7 @@ ccsd_status ccsd_residual(ccsd_ctx* ctx, const ccsd_z* t1, const ccsd_z* t2, ccs
   if ((t1 == nullptr) != (t2 == nullptr)) return set_err(ctx, CCSD_ERR_ARG, "t1 and t2 must both be given or both NULL");
   const int64_t n1 = (int64_t)ctx->o * ctx->v, n2 = n1 * ctx->o * ctx->v;
   if (t1) {
-    CK(cudaMemcpyAsync(ctx->t1_save, ctx->t1, n1 * sizeof(z), cudaMemcpyDeviceToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->t2_save, ctx->t2, n2 * sizeof(z), cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(backup_amplitudes(ctx, ctx->t1_save, ctx->t2_save));
     CS(copy_in(ctx, ctx->t1, t1, n1, on_device));
     CS(copy_in(ctx, ctx->t2, t2, n2, on_device));
   }
@@ -2005,8 +2106,7 @@ ccsd_status ccsd_residual(ccsd_ctx* ctx, const ccsd_z* t1, const ccsd_z* t2, ccs
   if (r1) CS(copy_out(ctx, r1, ctx->S1, n1, on_device));
   if (r2) CS(copy_out(ctx, r2, ctx->S2, n2, on_device));
   if (t1) {
-    CK(cudaMemcpyAsync(ctx->t1, ctx->t1_save, n1 * sizeof(z), cudaMemcpyDeviceToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->t2, ctx->t2_save, n2 * sizeof(z), cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(restore_amplitudes(ctx, ctx->t1_save, ctx->t2_save));
   }
   CK(cudaStreamSynchronize(ctx->stream));
   if (timed) collect_timers(ctx, ctx->plan->ops().size());
@@ -2060,9 +2160,7 @@ ccsd_status ccsd_iterate(ccsd_ctx* ctx, int max_iter, int* iters_done, double* r
     if (timed) collect_timers(ctx, ctx->tnames.size());
     nrm = ctx->opts.norm == 1 ? ctx->stats_host[1] : ctx->stats_host[0];
     if (!std::isfinite(ctx->stats_host[0]) || !std::isfinite(ctx->stats_host[1])) {
-      const int64_t n1 = (int64_t)ctx->o * ctx->v, n2 = n1 * ctx->o * ctx->v;
-      CK(cudaMemcpyAsync(ctx->t1, ctx->t1_prev, n1 * sizeof(z), cudaMemcpyDeviceToDevice, ctx->stream));
-      CK(cudaMemcpyAsync(ctx->t2, ctx->t2_prev, n2 * sizeof(z), cudaMemcpyDeviceToDevice, ctx->stream));
+      CK(restore_amplitudes(ctx, ctx->t1_prev, ctx->t2_prev));
       CK(cudaStreamSynchronize(ctx->stream));
       st = set_err(ctx, CCSD_ERR_DIVERGED, "non-finite amplitude update at iteration " + std::to_string(it));
       break;
@@ -2103,7 +2201,7 @@ ccsd_status ccsd_triples(ccsd_ctx* ctx, int max_batch, double* out, double* pair
   const int o = ctx->o, v = ctx->v;
   std::vector<double> acc((size_t)o * o * 3, 0.0);
   if (o >= 3 && v >= 3) {
-    const int64_t per = triples_batch_elems(v) * (int64_t)sizeof(z);
+    const int64_t per = triples_batch_elems(v, ctx->use_split) * (int64_t)sizeof(z);
     int nb = max_batch;
     if (nb == 0) {
       size_t fr = 0, tot = 0;
@@ -2147,25 +2245,41 @@ ccsd_status ccsd_triples(ccsd_ctx* ctx, int max_batch, double* out, double* pair
     a.work = (z*)work;
     a.partials = (double*)partials;
     a.pair_acc = (double*)pacc;
-    SliceSet SA, SB;
+    SliceSet SA, SB, SM, ST;
     int64_t setup_launches = 0;
     if (ctx->use_split) {
-      // digits of <ab||Le> for every L (rows L*P(v) + P over K = e, straight from vovv_pk) and of t2
-      // with its virtual labels swapped (rows (p*o + q)*v + c over K = e)
-      void *t2T = nullptr, *sam = nullptr, *sbm = nullptr;
+      // e-terms: digits of <ab||Le> for every L (rows L*P(v) + P over K = e, straight from vovv_pk)
+      // and of t2 with its virtual labels swapped (rows (p*o + q)*v + c over K = e).
+      // m-terms: digits of conj(<pq||ma>) (ooov with its last two labels swapped, rows
+      // (p*o + q)*v + a over K = m) and of the pair-packed t2 with m last (rows L*P(v) + P(b,c)).
+      void *t2T = nullptr, *sam = nullptr, *sbm = nullptr, *oT = nullptr, *tpT = nullptr, *smm = nullptr,
+           *stm = nullptr;
       const int64_t ra = (int64_t)o * ctx->Pv, rb = (int64_t)o * o * v;
       if (!mem.get(&t2T, sizeof(z) * (size_t)rb * v) || !mem.get(&sam, (size_t)slice_bytes(ra, v, ctx->split)) ||
-          !mem.get(&sbm, (size_t)slice_bytes(rb, v, ctx->split)))
+          !mem.get(&sbm, (size_t)slice_bytes(rb, v, ctx->split)) || !mem.get(&oT, sizeof(z) * (size_t)rb * o) ||
+          !mem.get(&tpT, sizeof(z) * (size_t)ra * o) || !mem.get(&smm, (size_t)slice_bytes(rb, o, ctx->split)) ||
+          !mem.get(&stm, (size_t)slice_bytes(ra, o, ctx->split)))
         return set_err(ctx, CCSD_ERR_OOM, "triples digit sets");
       const int64_t d_t2[4] = {o, o, v, v};
       const int pT[4] = {0, 1, 3, 2};
       CK(permute4(ctx->t2, d_t2, pT, (z*)t2T, zmake(1, 0), 0.0, 0, ctx->stream));
       CK(make_slices(ctx->vovv_pk, ra, v, ra, 1, 1, ctx->split, SA, sam, ctx->stream));
       CK(make_slices((const z*)t2T, rb, v, v, 0, 0, ctx->split, SB, sbm, ctx->stream));
+      const int64_t d_ooov[4] = {o, o, o, v};
+      CK(permute4(ctx->ooov, d_ooov, pT, (z*)oT, zmake(1, 0), 0.0, 0, ctx->stream));
+      CK(make_slices((const z*)oT, rb, o, o, 0, 1, ctx->split, SM, smm, ctx->stream));
+      // the packed t2 goes through the triples' own buffer first
+      CK(pack_pairs(ctx->t2, (z*)t2pk, (int64_t)o * o, v, 0, ctx->stream));
+      const int64_t d_pk[4] = {o, o, ctx->Pv, 1};
+      const int pP[4] = {0, 2, 1, 3};
+      CK(permute4((const z*)t2pk, d_pk, pP, (z*)tpT, zmake(1, 0), 0.0, 0, ctx->stream));
+      CK(make_slices((const z*)tpT, ra, o, o, 0, 0, ctx->split, ST, stm, ctx->stream));
       a.sa = &SA;
       a.sb = &SB;
+      a.sm = &SM;
+      a.st = &ST;
       a.split_err = ctx->split_err;
-      setup_launches = 1 + 3 + 3;
+      setup_launches = 1 + 3 + 3 + 1 + 3 + 1 + 1 + 3;
     }
     TriplesTimer timer;
     if (ctx->opts.profile) a.timer = &timer;
@@ -2231,12 +2345,35 @@ ccsd_status ccsd_lambda_iterate(ccsd_ctx* ctx, int max_iter, int* iters_done, do
   ccsd_status st = CCSD_ERR_NOT_CONVERGED;
   const bool timed = ctx->opts.profile != 0;
   ctx->lgrowth.reset();
+  if (!ctx->lgraph) {
+    // the iteration is captured once and replayed (its buffers never move)
+    if (timed) lambda_timers_init(ctx);
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = lambda_iteration_ops(ctx, timed);
+    cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return set_err(ctx, CCSD_ERR_CUDA,
+                     std::string("Lambda graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    cudaGraphGetNodes(g, nodes.data(), &nn);
+    ctx->lkernels_per_iter = 0;
+    for (auto nd : nodes) {
+      cudaGraphNodeType ty;
+      if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++ctx->lkernels_per_iter;
+    }
+    e = cudaGraphInstantiate(&ctx->lgraph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess)
+      return set_err(ctx, CCSD_ERR_CUDA, std::string("Lambda graph instantiate: ") + cudaGetErrorString(e));
+  }
   for (it = 1; it <= max_iter; ++it) {
-    CK(timed ? run_lambda_timed(ctx) : run_plan(ctx->lplan, ctx->stream));
-    CK(denom_update(ctx->l1, ctx->l2, ctx->S1, ctx->S2, ctx->dvec, ctx->o, ctx->v, ctx->opts.level_shift,
-                    ctx->upd_partials, ctx->stream));
-    CK(norm_finalize(ctx->upd_partials, update_blocks(), ctx->stats, ctx->stream));
-    if (ctx->opts.diis_dim > 0) CK(diis_step(ctx->ldiis, ctx->l1, ctx->l2, ctx->S1, ctx->S2, ctx->stream));
+    CK(cudaGraphLaunch(ctx->lgraph, ctx->stream));
     CK(cudaMemcpyAsync(ctx->stats_host, ctx->stats, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     if (ctx->use_split) CK(cudaMemcpyAsync(ctx->err_host, ctx->split_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -2401,9 +2538,15 @@ ccsd_status ccsd_query(const ccsd_ctx* ctx, const char* key, double* value) {
   const std::string k(key);
   if (k == "kernels_per_iteration") *value = ctx->kernels_per_iter;
   else if (k == "device_bytes") *value = (double)ctx->device_bytes;
+  else if (k == "plan_scratch_bytes") *value = 16.0 * (double)ctx->plan->scratch_elems();
+  else if (k == "plan_cached_bytes") *value = (double)ctx->plan_cached_bytes;
+  else if (k == "gemm_workspace_bytes") *value = 16.0 * (double)ctx->gemm_ws_elems;
+  else if (k == "split_workspace_bytes") *value = (double)ctx->split_ws_bytes;
+  else if (k == "diis_bytes") *value = 2.0 * 16.0 * (double)ctx->diis.m * (double)ctx->diis.L;
   else if (k == "iterations_run") *value = (double)ctx->iterations_run;
   else if (k == "plan_ops") *value = (double)ctx->plan->ops().size();
   else if (k == "lambda_iterations") *value = (double)ctx->lambda_iterations;
+  else if (k == "lambda_kernels_per_iteration") *value = (double)ctx->lkernels_per_iter;
   else if (k.rfind("lambda_op_ms:", 0) == 0) {
     // average device time per timed Lambda iteration of the ops with that name (profile = 1)
     const std::string nm = k.substr(13);
@@ -2612,9 +2755,7 @@ ccsd_status ccsd_batch_iterate(ccsd_batch* b, int max_iter, int* iters_done, dou
       if (c->use_split && b->err_host[k]) {
         b->status[k] = CCSD_ERR_TIMEOUT;
       } else if (!std::isfinite(mx) || !std::isfinite(l2)) {
-        const int64_t n1 = (int64_t)c->o * c->v, n2 = n1 * c->o * c->v;
-        cudaMemcpyAsync(c->t1, c->t1_prev, n1 * sizeof(z), cudaMemcpyDeviceToDevice, c->stream);
-        cudaMemcpyAsync(c->t2, c->t2_prev, n2 * sizeof(z), cudaMemcpyDeviceToDevice, c->stream);
+        restore_amplitudes(c, c->t1_prev, c->t2_prev);
         cudaStreamSynchronize(c->stream);
         b->status[k] = CCSD_ERR_DIVERGED;
       } else if (nrm <= c->opts.tol) {

@@ -25,9 +25,10 @@ struct PermuteArgs {
 };
 cudaError_t permute_add(const PermuteArgs& a, cudaStream_t s);
 
-// out[x][y][a][b] = c2 * t2[x][y][a][b] + c11 * (t1[x][a] t1[y][b] - anti * t1[y][a] t1[x][b])
+// out[x][y][a][b] = c2 * t2[x][y][a][b] + c11 * (t1[x][a] t1[y][b] - anti * t1[y][a] t1[x][b]);
+// with yaxb = 1 the same values are stored as out[y][a][x][b].
 cudaError_t tau_build(const z* t1, const z* t2, z* out, int o, int v, double c2, double c11, int anti,
-                      cudaStream_t s);
+                      cudaStream_t s, int yaxb = 0);
 
 // Pack the antisymmetric trailing pair: out[r][P(a,b)] = in[r][a][b] for a < b, r over R rows.
 // With pack_rows, r itself runs over the pairs x < y of an n1 x n1 leading pair (R = n1*n1 in

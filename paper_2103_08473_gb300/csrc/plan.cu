@@ -158,7 +158,7 @@ T Plan::permuted(const T& src, const std::string& lab, bool conj, const std::str
   T out;
   out.lab = lab;
   for (char c : lab) out.dims.push_back(src.dims[src.lab.find(c)]);
-  if (src.cnst && src.p.direct) {
+  if (src.cnst && src.p.direct && src.size() * (int64_t)sizeof(z) <= cache_limit_) {
     std::ostringstream key;
     key << (const void*)src.p.direct << ":" << src.lab << ">" << lab << (conj ? "*" : "");
     auto it = const_cache_.find(key.str());
@@ -170,6 +170,7 @@ T Plan::permuted(const T& src, const std::string& lab, bool conj, const std::str
       return out;
     }
     owned_.push_back(mem);
+    owned_bytes_ += std::max<int64_t>(src.size(), 1) * (int64_t)sizeof(z);
     out.p.direct = (z*)mem;
     out.cnst = true;
     // run the permutation once, now

@@ -17,6 +17,7 @@
 #pragma once
 
 #include <algorithm>
+#include <cstdint>
 #include <functional>
 #include <map>
 #include <memory>
@@ -103,8 +104,13 @@ class Plan {
 
   std::vector<Op>& ops() { return ops_; }
   int64_t scratch_elems() const { return scratch_peak_; }
-  // Persistent buffers created by the planner (cached permutations of constants).
+  // Persistent buffers created by the planner (cached permutations of constants), and their bytes.
   std::vector<void*>& owned() { return owned_; }
+  int64_t owned_bytes() const { return owned_bytes_; }
+  // Constant operands larger than this (bytes) are not cached in their permuted layout: each use
+  // permutes them into the scratch region instead (default: no limit). Large problems trade one
+  // extra pass over such an integral block per use for its permuted copy's memory.
+  void set_cache_limit(int64_t bytes) { cache_limit_ = bytes; }
   cudaError_t status() const { return status_; }
   const std::string& error() const { return error_; }
 
@@ -124,6 +130,8 @@ class Plan {
   int64_t scratch_off_ = 0, scratch_peak_ = 0;
   std::map<std::string, T> const_cache_;
   std::vector<void*> owned_;
+  int64_t owned_bytes_ = 0;
+  int64_t cache_limit_ = INT64_MAX;
   cudaError_t status_ = cudaSuccess;
   std::string error_;
 };

@@ -37,6 +37,8 @@ struct EnergyArgs {
   int64_t Pv = 0;
   int i = 0, j = 0, k0 = 0, nk = 0;
   const z *E = nullptr, *M = nullptr;
+  // split precision: the products of the second layout, E2[P(a,b)][t][c] and M2[a][t][P(b,c)]
+  const z *E2 = nullptr, *M2 = nullptr;
   const z *t1 = nullptr, *t2 = nullptr, *oovv = nullptr, *fov = nullptr;
   const double* d = nullptr;
   double* partials = nullptr;  // gridDim.x * 3
@@ -47,22 +49,22 @@ __device__ __forceinline__ z zfma_conj_a(z a, z b, z acc) {  // acc + conj(a) * 
 }
 
 __global__ void __launch_bounds__(kTriplesThreads) triples_energy_kernel(EnergyArgs g) {
-  const int64_t v = g.v, o = g.o, Pv = g.Pv;
-  const int64_t per = v * v * v;
-  const int64_t total = per * g.nk;
+  const int64_t v = g.v, o = g.o, Pv = g.Pv, nk = g.nk;
+  // one thread per (t, P(a,b), c), c fastest; only c > b is a unique triple a<b<c
+  const int64_t total = nk * Pv * v;
   double s4 = 0.0, s5 = 0.0, s5m = 0.0;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(e % v);
-    const int b = (int)((e / v) % v);
-    const int64_t r = e / (v * v);
-    const int a = (int)(r % v);
-    const int t = (int)(r / v);
-    if (!(a < b && b < c)) continue;
+    const int64_t c = e % v;
+    const int64_t pab = (e / v) % Pv;
+    const int t = (int)(e / (v * Pv));
+    int64_t a, b;
+    pair_decode(pab, v, a, b);
+    if (c <= b) continue;
     const int k = g.k0 + t;
     const z* E = g.E + (int64_t)t * Pv * v;
     const z* M = g.M + (int64_t)t * v * Pv;
-    const int64_t pab = pair_index(a, b, v), pbc = pair_index(b, c, v), pac = pair_index(a, c, v);
+    const int64_t pbc = pair_index(b, c, v), pac = pair_index(a, c, v);
     // X = W^{abc} + W^{bca} + W^{cab}, W = E (antisymmetric in its first two virtual labels)
     //                                  + M (antisymmetric in its last two)
     z X = E[pab * v + c];
@@ -71,6 +73,16 @@ __global__ void __launch_bounds__(kTriplesThreads) triples_energy_kernel(EnergyA
     X = zadd(X, M[a * Pv + pbc]);
     X = zsub(X, M[b * Pv + pac]);
     X = zadd(X, M[c * Pv + pab]);
+    if (g.E2) {
+      const z* E2 = g.E2 + (int64_t)t * v;  // [P][t][c]: row stride nk * v
+      const z* M2 = g.M2 + (int64_t)t * Pv;  // [a][t][P]: row stride nk * Pv
+      X = zadd(X, E2[pab * nk * v + c]);
+      X = zadd(X, E2[pbc * nk * v + a]);
+      X = zsub(X, E2[pac * nk * v + b]);
+      X = zadd(X, M2[a * nk * Pv + pbc]);
+      X = zsub(X, M2[b * nk * Pv + pac]);
+      X = zadd(X, M2[c * nk * Pv + pab]);
+    }
     const double D = g.d[o + a] + g.d[o + b] + g.d[o + c] - g.d[g.i] - g.d[g.j] - g.d[k];
     // Z and Y summed over the cyclic orders of the occupied and of the virtual labels
     const int occ[3] = {g.i, g.j, k};
@@ -154,7 +166,7 @@ int64_t triples_partials(const TriplesArgs& a) {
   return 152 * 8 * 3;
 }
 
-int64_t triples_batch_elems(int v) { return 2 * pair_count(v) * (int64_t)v; }
+int64_t triples_batch_elems(int v, bool split) { return (split ? 4 : 2) * pair_count(v) * (int64_t)v; }
 
 cudaError_t triples_eval(TriplesArgs& a, cudaStream_t s) {
   const int o = a.o, v = a.v;
@@ -163,6 +175,8 @@ cudaError_t triples_eval(TriplesArgs& a, cudaStream_t s) {
   const int64_t part = Pv * v;  // elements of E (and of M) per triple
   z* Ebuf = a.work;
   z* Mbuf = a.work + part * a.max_batch;
+  z* E2buf = a.sa ? a.work + 2 * part * a.max_batch : nullptr;
+  z* M2buf = a.sa ? a.work + 3 * part * a.max_batch : nullptr;
   cudaError_t e = pack_pairs(a.t2, a.t2pk, (int64_t)o * o, v, 0, s);
   if (e != cudaSuccess) return e;
   a.launches += 1;
@@ -175,19 +189,24 @@ cudaError_t triples_eval(TriplesArgs& a, cudaStream_t s) {
         if (a.timer && (e = a.timer->mark(s)) != cudaSuccess) return e;
         // ---- e-terms: E[t][P(a,b)][c] over k = k0 + t
         if (a.sa) {
-          // one split GEMM per triple and term: C = -A_L B_pq^T over K = e
-          for (int t = 0; t < nk; ++t) {
-            const int k = k0 + t;
-            z* C = Ebuf + (int64_t)t * part;
-            const int L[3] = {i, j, k};
-            const int64_t pq[3] = {(int64_t)j * o + k, (int64_t)k * o + i, (int64_t)i * o + j};
-            for (int u = 0; u < 3; ++u) {
-              e = split_gemm(slice_rows(*a.sa, (int64_t)L[u] * Pv, Pv), slice_rows(*a.sb, pq[u] * v, v), C, v,
-                             minus1, u == 0 ? zero : one, a.split_err, nullptr, 0, s);
-              if (e != cudaSuccess) return e;
-            }
-          }
-          a.launches += 3 * nk;
+          // one split GEMM per term over the whole batch, C = -A_L B_pq^T over K = e:
+          //   (k; ij): rows L = k of <eL||ab> for every k of the batch against t2[i][j]
+          //            -> E[t][P(a,b)][c];
+          //   (i; jk) and (j; ki) = -(j; ik): rows L = i (L = j) against t2[j][k] (t2[i][k]) for
+          //            every k of the batch -> E2[P(a,b)][t][c]
+          const int64_t ij = (int64_t)i * o + j;
+          e = split_gemm(slice_rows(*a.sa, (int64_t)k0 * Pv, (int64_t)nk * Pv), slice_rows(*a.sb, ij * v, v), Ebuf,
+                         v, minus1, zero, a.split_err, nullptr, 0, s);
+          if (e == cudaSuccess)
+            e = split_gemm(slice_rows(*a.sa, (int64_t)i * Pv, Pv),
+                           slice_rows(*a.sb, ((int64_t)j * o + k0) * v, (int64_t)nk * v), E2buf, (int64_t)nk * v,
+                           minus1, zero, a.split_err, nullptr, 0, s);
+          if (e == cudaSuccess)
+            e = split_gemm(slice_rows(*a.sa, (int64_t)j * Pv, Pv),
+                           slice_rows(*a.sb, ((int64_t)i * o + k0) * v, (int64_t)nk * v), E2buf, (int64_t)nk * v,
+                           one, one, a.split_err, nullptr, 0, s);
+          if (e != cudaSuccess) return e;
+          a.launches += 3;
         } else {
           ZGemmArgs g;
           g.M = Pv;
@@ -225,6 +244,22 @@ cudaError_t triples_eval(TriplesArgs& a, cudaStream_t s) {
         }
         if (a.timer && (e = a.timer->mark(s)) != cudaSuccess) return e;
         // ---- m-terms: M[t][a][P(b,c)]
+        if (a.sm) {
+          // one split GEMM per term over the batch, C = -A_pq B_L^T over K = m:
+          //   (jk; i) and (ki; j) = -(ik; j): rows (j,k) ((i,k)) of conj(<pq||ma>) for every k of
+          //            the batch against the packed t2[i] (t2[j]) -> M[t][a][P(b,c)];
+          //   (ij; k): rows (i,j) against the packed t2[k] of every k -> M2[a][t][P(b,c)]
+          const int64_t ij = (int64_t)i * o + j;
+          e = split_gemm(slice_rows(*a.sm, ((int64_t)j * o + k0) * v, (int64_t)nk * v),
+                         slice_rows(*a.st, (int64_t)i * Pv, Pv), Mbuf, Pv, minus1, zero, a.split_err, nullptr, 0, s);
+          if (e == cudaSuccess)
+            e = split_gemm(slice_rows(*a.sm, ((int64_t)i * o + k0) * v, (int64_t)nk * v),
+                           slice_rows(*a.st, (int64_t)j * Pv, Pv), Mbuf, Pv, one, one, a.split_err, nullptr, 0, s);
+          if (e == cudaSuccess)
+            e = split_gemm(slice_rows(*a.sm, ij * v, v), slice_rows(*a.st, (int64_t)k0 * Pv, (int64_t)nk * Pv),
+                           M2buf, (int64_t)nk * Pv, minus1, zero, a.split_err, nullptr, 0, s);
+          if (e != cudaSuccess) return e;
+        } else {
         ZGemmArgs h;
         h.M = v;
         h.N = Pv;
@@ -258,6 +293,7 @@ cudaError_t triples_eval(TriplesArgs& a, cudaStream_t s) {
         h.sA = (int64_t)o * ov;
         h.B = a.t2pk + (int64_t)j * o * Pv;
         if ((e = zgemm_f64(h, s)) != cudaSuccess) return e;
+        }
         if (a.timer && (e = a.timer->mark(s)) != cudaSuccess) return e;
         // ---- energies of the batch
         EnergyArgs q;
@@ -270,13 +306,15 @@ cudaError_t triples_eval(TriplesArgs& a, cudaStream_t s) {
         q.nk = nk;
         q.E = Ebuf;
         q.M = Mbuf;
+        q.E2 = E2buf;
+        q.M2 = M2buf;
         q.t1 = a.t1;
         q.t2 = a.t2;
         q.oovv = a.oovv;
         q.fov = a.fov;
         q.d = a.d;
         q.partials = a.partials;
-        const int grid = energy_grid((int64_t)nk * v * v * v);
+        const int grid = energy_grid((int64_t)nk * Pv * v);
         triples_energy_kernel<<<grid, kTriplesThreads, 0, s>>>(q);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         triples_accumulate_kernel<<<1, 32, 0, s>>>(a.partials, grid, a.pair_acc + ((int64_t)i * o + j) * 3);

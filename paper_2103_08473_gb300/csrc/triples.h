@@ -53,19 +53,26 @@ struct TriplesArgs {
   double* partials = nullptr;  // triples_partials() doubles
   double* pair_acc = nullptr;  // o*o*3 doubles, zeroed by the caller; [(i*o + j)*3 + m] += the
                                // pair's sums of |X|^2/D (m=0), Re(X Z)/D (1), Re(X conj Y) (2)
-  // Split precision for the e-term GEMMs (null: FP64): digits of <ab||Le> over K = e for every L
-  // (rows L*P(v) + P(a,b)) and of t2 over K = e (rows (p*o + q)*v + c); each e-term is one split
-  // GEMM of two row views per triple.
+  // Split precision (null: FP64). The e-terms: digits of conj(<eL||ab>) over K = e for every L
+  // (rows L*P(v) + P(a,b)) and of t2 over K = e (rows (p*o + q)*v + c). The m-terms: digits of
+  // conj(<pq||ma>) over K = m (rows (p*o + q)*v + a) and of the pair-packed t2 over K = m (rows
+  // L*P(v) + P(b,c)). Each term is then ONE split GEMM per batch of k, of row views whose rows
+  // run over the batch's k (the antisymmetry of t2 and of <pq||ma> in their occupied pair turns
+  // the (k,i) rows into the contiguous (i,k) ones); two of the six products come out in a
+  // second layout, E2[P(a,b)][t][c] and M2[a][t][P(b,c)].
   const SliceSet* sa = nullptr;
   const SliceSet* sb = nullptr;
+  const SliceSet* sm = nullptr;
+  const SliceSet* st = nullptr;
   int* split_err = nullptr;
   TriplesTimer* timer = nullptr;  // optional
   int64_t batches = 0;            // out: batches run
   int64_t launches = 0;           // out: kernels launched
 };
 
-// Complex elements of workspace per triple of a batch (the two packed parts of W).
-int64_t triples_batch_elems(int v);
+// Complex elements of workspace per triple of a batch (the packed parts of W: two in FP64, four
+// in split precision).
+int64_t triples_batch_elems(int v, bool split);
 // Doubles of block partials the energy kernel writes per batch.
 int64_t triples_partials(const TriplesArgs& a);
 // Enqueue the whole evaluation on s (no synchronisation). o < 3 or v < 3: nothing to do.

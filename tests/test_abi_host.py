@@ -52,6 +52,7 @@ def test_default_opts(lib):
     assert o.split_min_flops == 1e8 and o.precision == 0
     assert o.slices == 0 and o.digit_bits == 0 and o.complex_4m == 0 and o.method == ccsd.METHOD_CCSD
     assert o.accelerator == ccsd.ACCEL_DIIS and o.diverge_iters == 8 and o.diverge_factor == 1e3
+    assert o.vovv_block == 0
 
 
 def _create(lib, o, v, eps, B, naux, opts=None):
@@ -63,7 +64,7 @@ def _create(lib, o, v, eps, B, naux, opts=None):
     return st, h
 
 
-@pytest.mark.parametrize("case", ["o0", "v0", "naux0", "null_eps", "null_ints", "nonhermitian", "diis17", "bits6", "bits_x_slices", "method3", "accel2", "diverge_neg", "diverge_factor"])
+@pytest.mark.parametrize("case", ["o0", "v0", "naux0", "null_eps", "null_ints", "nonhermitian", "diis17", "bits6", "bits_x_slices", "method3", "accel2", "diverge_neg", "diverge_factor", "vovv_block_neg"])
 def test_create_rejects_bad_arguments(lib, case):
     from paper_2103_08473_gb300 import ccsd, inputs
     s = inputs.make_system(2, 3, 4, seed=1)
@@ -93,6 +94,8 @@ def test_create_rejects_bad_arguments(lib, case):
         opts = ccsd.default_opts(diverge_iters=-1)
     elif case == "diverge_factor":
         opts = ccsd.default_opts(diverge_factor=0.5)
+    elif case == "vovv_block_neg":
+        opts = ccsd.default_opts(vovv_block=-1)
     elif case == "bits_x_slices":
         opts = ccsd.default_opts(precision=ccsd.PREC_SPLIT, digit_bits=5, slices=12)
     st, h = _create(lib, o, v, eps, B, naux, opts)

@@ -60,6 +60,26 @@ def test_lambda_residual_matches_oracle(ccsd, o, v, naux, seed, scale, fs):
     assert _maxrel(gs, L.density(t1, t2, l1, l2, symmetrize=True)) < 1e-12
 
 
+@pytest.mark.parametrize("vblock", [1, 2, 3])
+def test_blocked_vovv_terms_match_oracle(ccsd, vblock):
+    """<ak||cd> unpacked a few rows a at a time (vovv_block; large systems take about 1 GB of rows
+    per block): the H^{ak}_{ci} term of the residual and its adjoint in the Lambda residual run
+    over several blocks, including a short last one, and still match the oracle."""
+    o, v, naux, seed = 5, 13, 20, 507
+    s, f, fock = _sys(o, v, naux, seed, 0.2, 0.05)
+    V = R.integrals(s.B, o)
+    t1, t2 = inputs.random_amplitudes(o, v, seed + 1, scale=0.1)
+    l1, l2 = inputs.random_amplitudes(o, v, seed + 2, scale=0.1)
+    S1, S2 = R.residual(f, V, t1, t2)
+    R1, R2 = L.lagrangian_gradient(f, V, t1, t2, l1, l2)
+    with ccsd.CCSD(o, v, s.eps, B=s.B, fock=fock, vovv_block=vblock) as cc:
+        r1, r2 = cc.residual(t1, t2)
+        cc.set_amplitudes(t1, t2)
+        q1, q2 = cc.lambda_residual(l1, l2)
+    assert _maxrel(r1, S1) < 1e-12 and _maxrel(r2, S2) < 1e-12
+    assert _maxrel(q1, R1) < 1e-12 and _maxrel(q2, R2) < 1e-12
+
+
 def test_lambda_converges_to_the_oracle(ccsd):
     o, v, naux = 4, 10, 24
     s, f, fock = _sys(o, v, naux, 505, 0.05, 0.0)

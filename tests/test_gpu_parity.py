@@ -228,6 +228,21 @@ def test_degenerate_shapes_match_oracle(ccsd, o, v, precision):
         assert abs(cc.energy() - ref["energy"]) < 1e-9
 
 
+@pytest.mark.parametrize("o,v,naux,seed", [(3, 5, 7, 131), (5, 14, 30, 132), (6, 21, 40, 133)])
+def test_ccd_residual_is_the_doubles_residual_at_zero_singles(ccsd, o, v, naux, seed):
+    """The CCD plan (no t1 terms, no C^{kb}_{ij}, no singles): at random amplitudes with a nonzero
+    t1 it returns S1 = 0 and the Appendix-A doubles residual of the oracle at t1 = 0, with a
+    non-diagonal Fock matrix (its off-diagonal occupied-virtual block feeds only the t1 terms)."""
+    s, f, fock = _sys(o, v, naux, seed, 0.2, 0.05)
+    V = R.integrals(s.B, o)
+    t1, t2 = inputs.random_amplitudes(o, v, seed + 1, scale=0.1)
+    _, S2 = R.residual(f, V, np.zeros_like(t1), t2)
+    with ccsd.CCSD(o, v, s.eps, B=s.B, fock=fock, method=ccsd.METHOD_CCD) as cc:
+        r1, r2 = cc.residual(t1, t2)
+    assert np.max(np.abs(r1)) == 0.0
+    assert _maxrel(r2, S2) < 1e-12
+
+
 @pytest.mark.parametrize("precision", ["fp64", "split"])
 def test_ccd_tracks_oracle(ccsd, precision):
     """CCD (method = CCD): t1 stays exactly zero, and fixed iterations and the energy follow the

@@ -6,9 +6,10 @@ sizes, its per-pair form at sizes where o^3 v^3 arrays do not fit, and sampled
 pairs at the o20/v120 workload's full size. The arithmetic is FP64 on both sides
 in a different summation order, so the bar is 1e-11 relative on every energy
 and per-pair term. Batches of 1, 2 and as many triples as fit must agree. In a
-split-precision context the e-terms of W are split GEMMs with 8 digits of 5 bits:
-each product carries a relative error of at most ~2^-38 of its row and column
-scales, and the energies, quadratic in W, are held to 1e-9 relative.
+split-precision context the six products that make W (e- and m-terms) are split
+GEMMs with 8 digits of 5 bits, one per term and batch of k: each product carries a
+relative error of at most ~2^-38 of its row and column scales, and the energies,
+quadratic in W, are held to 1e-9 relative.
 """
 import numpy as np
 import pytest
@@ -122,11 +123,19 @@ def test_split_triples_match_oracle(ccsd, o, v, naux, seed, fs):
         cc.set_amplitudes(t1, t2)
         got = cc.triples(max_batch=2)
         launches = cc.query("triples_launches")
+        batches = cc.query("triples_batches")
+        whole = cc.triples(max_batch=0)
+        single = cc.triples(max_batch=1)
     for m, key in enumerate(KEYS):
         assert _close(got[key], ref[m], 1e-9), (key, got[key], ref[m])
-    # split mode: three tensor-core launches per triple for the e-terms
-    nt = o * (o - 1) * (o - 2) // 6
-    assert launches >= 3 * nt
+    # split mode: per batch of k one tensor-core GEMM for each of the three e-terms and the
+    # three m-terms, the energy kernel and its accumulation (after 16 launches that cut the digits
+    # and one that packs t2)
+    assert launches == 17 + 8 * batches
+    # the batch's k run along the rows of the GEMM operands: the grouping does not change W
+    for r in (whole, single):
+        for key in KEYS:
+            assert _close(r[key], got[key], 1e-13), (key, r[key], got[key])
 
 
 @pytest.mark.parametrize("precision", ["fp64", "split"])
