@@ -679,7 +679,10 @@ def run_lambda(args, wl):
     ms = max_over_ranks(e0.elapsed_time(e1))
     lad_ms = cc.query("lambda_op_ms:L:ladder:gemm")
     lkern = int(cc.query("lambda_kernels_per_iteration"))
-    ring_ms = cc.query("lambda_op_ms:L:ring")
+    lops = {}
+    for name, t in cc.timings():
+        if name.startswith("L:"):
+            lops[name] = lops.get(name, 0.0) + t
     # end to end through the C ABI: multipliers in from pinned host memory, one residual, out
     l1, l2 = cc.get_lambda()
     l1h = torch.from_numpy(l1).pin_memory()
@@ -725,7 +728,8 @@ def run_lambda(args, wl):
                        "timed": "one call: a residual-plan refresh, then steps Lambda iterations",
                        "l2": "inputs larger than L2 (packed <ab||cd> exceeds 129 MB)",
                        "parallelism": "replicas" if world > 1 else "single"},
-            "lambda_plan_ms": {"ladder_adjoint": lad_ms, "ring_adjoint": ring_ms},
+            "lambda_plan_ms": {"ladder_adjoint": lad_ms,
+                               "top_ops": {k: round(t, 4) for k, t in sorted(lops.items(), key=lambda kv: -kv[1])[:12]}},
             "roofline": {"kernel": kname, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                          "frac": (ach / peak) if ach else None, "peak_basis": basis,
                          "algorithmic_flops_per_launch": ex_fl, "launch_ms": lad_ms, "traffic": None},
@@ -762,7 +766,10 @@ def run_batch(args, wl):
     tol, maxit = wl["tol"], 200
     precision = args.precision or wl["precision"]
     slices = args.slices or SPLIT_SLICES
-    popts = dict(precision=ccmod.PREC_SPLIT, slices=slices, digit_bits=SPLIT_BITS) if precision == "split" else {}
+    # split batches route GEMMs from 3e7 flops up (the library default is 1e8): measured on the 64
+    # systems, 33.8 systems/s against 31.5 (1e8) and 21.1 (1e9)
+    popts = (dict(precision=ccmod.PREC_SPLIT, slices=slices, digit_bits=SPLIT_BITS, split_min_flops=3e7)
+             if precision == "split" else {})
 
     def barrier():
         if world > 1:
@@ -875,7 +882,10 @@ def batch_once(args, wl):
     spec = [(s.o, s.v, s.eps, s.B) for s in systems]
     precision = args.precision or wl["precision"]
     slices = args.slices or SPLIT_SLICES
-    popts = dict(precision=ccmod.PREC_SPLIT, slices=slices, digit_bits=SPLIT_BITS) if precision == "split" else {}
+    # split batches route GEMMs from 3e7 flops up (the library default is 1e8): measured on the 64
+    # systems, 33.8 systems/s against 31.5 (1e8) and 21.1 (1e9)
+    popts = (dict(precision=ccmod.PREC_SPLIT, slices=slices, digit_bits=SPLIT_BITS, split_min_flops=3e7)
+             if precision == "split" else {})
     stream = torch.cuda.Stream()
     with ccmod.Batch(spec, tol=wl["tol"], max_iter=200, stream=stream.cuda_stream, **popts) as b:
         b.iterate(2)

@@ -125,7 +125,8 @@ typedef struct {
                              that is faster than FP64; the ladder always does; <= 0 sends every GEMM
                              there (default 1e8) */
   int df_block;       /* store_w = 0: virtual indices a per rebuilt block of <ab||cd> rows
-                         (default 0 = as many as fit about 3 GB of (ac|bd)) */
+                         (default 0 = as many as fit about 6 GB of (ac|bd), held in the residual plan's
+                         scratch region) */
   int autotune;       /* 1: at creation, time every FP64 GEMM of the plan in each tile shape and keep
                          the fastest (default 0: a cost model picks the shape) */
   int digit_bits;     /* split precision: bits per digit, 1..5 (default 0 = 5). Digits are integers
@@ -285,10 +286,12 @@ ccsd_status ccsd_get_tensor(ccsd_ctx* ctx, const char* name, ccsd_z* out, size_t
 /*
  * Per-op device timings (opts.profile = 1): CUDA events recorded between the
  * ops of the residual plan and the update / norm / DIIS steps, inside the
- * iteration's CUDA graph. Writes up to `cap` (name, average milliseconds per
- * evaluation) pairs, averaged over the evaluations since the previous call,
- * and resets the averages (cap <= 0 only queries *n). *n receives the number
- * of timed segments (0 if nothing was timed). Names are owned by the context.
+ * iteration's CUDA graph, followed by the ops of the Lambda plan (names "L:...",
+ * per Lambda iteration) when Lambda iterations were timed. Writes up to `cap`
+ * (name, average milliseconds per evaluation) pairs, averaged over the evaluations
+ * since the previous call, and resets the averages (cap <= 0 only queries *n). *n
+ * receives the number of timed segments (0 if nothing was timed). Names are owned by
+ * the context.
  */
 ccsd_status ccsd_timings(ccsd_ctx* ctx, const char** names, double* ms, int cap, int* n);
 

@@ -72,6 +72,7 @@ struct ccsd_ctx {
   void* tausl_mem = nullptr; // tau digits of the on-the-fly ladder (kept across its blocks)
   // store_w = 0: B^Q over virtuals, and per-block (ac|bd) and packed <ab||cd> rows
   z *Bvv = nullptr, *Dblk = nullptr, *Wblk = nullptr;
+  int64_t df_w_off = -1;  // store_w = 0: offset of the packed rows after D in the plan's scratch
   SliceSet Bsl;  // split mode: digits of B^Q_vv as rows (a, c) over Q, cut once (both operands of the rebuild)
   // CC2: the DF factor blocks B^Q_vo, B^Q_oo, B^Q_ov (B^Q_vv is Bvv) and the per-evaluation dressed
   // factors Bt[Q][a][i] = ((1 - t1) B^Q (1 + t1))_ai and Dt[Q][j][i] = (B^Q (1 + t1))_ji
@@ -475,7 +476,7 @@ std::vector<DfBlock> df_blocks(int64_t v, int64_t blk) {
 ccsd_status plan_df_ladder(ccsd_ctx* ctx, Plan* P) {
   const int64_t v = ctx->v, naux = ctx->naux, Po = ctx->Po, Pv = ctx->Pv;
   int64_t blk = ctx->opts.df_block;
-  if (blk <= 0) blk = std::max<int64_t>(1, (int64_t)(3e9 / (16.0 * (double)v * v * v)));
+  if (blk <= 0) blk = std::max<int64_t>(1, (int64_t)(6e9 / (16.0 * (double)v * v * v)));
   blk = std::min<int64_t>(blk, std::max<int64_t>(v - 1, 1));
   ctx->df_block = (int)blk;
   const auto blocks = df_blocks(v, blk);
@@ -484,8 +485,10 @@ ccsd_status plan_df_ladder(ccsd_ctx* ctx, Plan* P) {
     dmax = std::max(dmax, (b.a1 - b.a0) * v * (v - b.a0 - 1) * v);
     wmax = std::max(wmax, b.AB1 - b.AB0);
   }
-  CS(dalloc(ctx, &ctx->Dblk, dmax));
-  CS(dalloc(ctx, &ctx->Wblk, wmax * Pv));
+  // D and the packed rows live at the start of the plan's scratch region (set once it exists):
+  // no temporary of the plan is live while the ladder op runs
+  ctx->df_w_off = (dmax + 15) / 16 * 16;
+  P->reserve_scratch(ctx->df_w_off + wmax * Pv);
   if (ctx->use_split) {
     // B^Q_vv is constant: its digits (rows (a, c), K = Q) are cut once; every block's rebuild
     // reads row ranges of them
@@ -1138,6 +1141,10 @@ ccsd_status build_residual_plan(ccsd_ctx* ctx) {
   ctx->plan_cached_bytes = P->owned_bytes();
   P->owned().clear();
   CS(dalloc(ctx, &ctx->scratch, P->scratch_elems()));
+  if (ctx->df_w_off >= 0) {
+    ctx->Dblk = ctx->scratch;
+    ctx->Wblk = ctx->scratch + ctx->df_w_off;
+  }
   ctx->gemm_ws_elems = P->gemm_workspace_elems();
   CS(dalloc(ctx, &ctx->gemm_ws, ctx->gemm_ws_elems));
   if (ctx->use_split) {
@@ -2522,14 +2529,22 @@ ccsd_status ccsd_get_tensor(ccsd_ctx* ctx, const char* name, ccsd_z* out, size_t
 ccsd_status ccsd_timings(ccsd_ctx* ctx, const char** names, double* ms, int cap, int* n) {
   if (!ctx) return CCSD_ERR_ARG;
   const int cnt = ctx->tcount > 0 ? (int)ctx->tnames.size() : 0;
-  if (n) *n = cnt;
+  const int lcnt = (ctx->lplan && ctx->ltcount > 0) ? (int)ctx->ltsum.size() : 0;
+  if (n) *n = cnt + lcnt;
   if (cap <= 0) return CCSD_OK;
   for (int k = 0; k < cnt && k < cap; ++k) {
     if (names) names[k] = ctx->tnames[k].c_str();
     if (ms) ms[k] = ctx->tsum[k] / ctx->tcount;
   }
+  // then the Lambda plan's ops, per timed Lambda iteration
+  for (int k = 0; k < lcnt && cnt + k < cap; ++k) {
+    if (names) names[cnt + k] = ctx->lplan->ops()[k].name.c_str();
+    if (ms) ms[cnt + k] = ctx->ltsum[k] / ctx->ltcount;
+  }
   std::fill(ctx->tsum.begin(), ctx->tsum.end(), 0.0);
   ctx->tcount = 0;
+  std::fill(ctx->ltsum.begin(), ctx->ltsum.end(), 0.0);
+  ctx->ltcount = 0;
   return CCSD_OK;
 }
 

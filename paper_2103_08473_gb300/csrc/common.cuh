@@ -31,10 +31,12 @@ __host__ __device__ __forceinline__ int64_t pair_count(int64_t n) { return n * (
 __host__ __device__ __forceinline__ int64_t pair_index(int64_t x, int64_t y, int64_t n) {
   return x * (2 * n - x - 1) / 2 + (y - x - 1);
 }
-// Inverse of pair_index: the row x is the largest x with pair_index(x, x+1) <= P.
+// Inverse of pair_index: the row x is the largest x with pair_index(x, x+1) <= P. A single-precision
+// estimate from the quadratic formula (the FP64 pipe is narrow here), then exact integer
+// corrections in both directions, so the result does not depend on the estimate's rounding.
 __device__ __forceinline__ void pair_decode(int64_t P, int64_t n, int64_t& x, int64_t& y) {
-  double nn = (double)(2 * n - 1);
-  int64_t xx = (int64_t)((nn - sqrt(nn * nn - 8.0 * (double)P)) * 0.5);
+  const float nn = (float)(2 * n - 1);
+  int64_t xx = (int64_t)((nn - sqrtf(fmaxf(nn * nn - 8.0f * (float)P, 0.0f))) * 0.5f);
   if (xx < 0) xx = 0;
   if (xx > n - 2) xx = n - 2;
   while (xx > 0 && xx * (2 * n - xx - 1) / 2 > P) --xx;

@@ -104,6 +104,9 @@ class Plan {
 
   std::vector<Op>& ops() { return ops_; }
   int64_t scratch_elems() const { return scratch_peak_; }
+  // A custom op that keeps its own temporaries at the start of the scratch region (none of the
+  // plan's temporaries is live while a custom op runs) makes the region at least this large.
+  void reserve_scratch(int64_t elems) { scratch_peak_ = std::max(scratch_peak_, elems); }
   // Persistent buffers created by the planner (cached permutations of constants), and their bytes.
   std::vector<void*>& owned() { return owned_; }
   int64_t owned_bytes() const { return owned_bytes_; }

@@ -50,78 +50,81 @@ __device__ __forceinline__ z zfma_conj_a(z a, z b, z acc) {  // acc + conj(a) * 
 
 __global__ void __launch_bounds__(kTriplesThreads) triples_energy_kernel(EnergyArgs g) {
   const int64_t v = g.v, o = g.o, Pv = g.Pv, nk = g.nk;
-  // one thread per (t, P(a,b), c), c fastest; only c > b is a unique triple a<b<c
-  const int64_t total = nk * Pv * v;
+  // one warp per row (t, P(a,b)), decoded once; its lanes walk c = b+1 .. v-1, the unique
+  // triples a<b<c of the row
+  const int lane = threadIdx.x & 31;
+  const int64_t rows = nk * Pv;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   double s4 = 0.0, s5 = 0.0, s5m = 0.0;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c = e % v;
-    const int64_t pab = (e / v) % Pv;
-    const int t = (int)(e / (v * Pv));
+  for (int64_t row = w0; row < rows; row += nw) {
+    const int64_t pab = row % Pv;
+    const int t = (int)(row / Pv);
     int64_t a, b;
     pair_decode(pab, v, a, b);
-    if (c <= b) continue;
-    const int k = g.k0 + t;
-    const z* E = g.E + (int64_t)t * Pv * v;
-    const z* M = g.M + (int64_t)t * v * Pv;
-    const int64_t pbc = pair_index(b, c, v), pac = pair_index(a, c, v);
-    // X = W^{abc} + W^{bca} + W^{cab}, W = E (antisymmetric in its first two virtual labels)
-    //                                  + M (antisymmetric in its last two)
-    z X = E[pab * v + c];
-    X = zadd(X, E[pbc * v + a]);
-    X = zsub(X, E[pac * v + b]);
-    X = zadd(X, M[a * Pv + pbc]);
-    X = zsub(X, M[b * Pv + pac]);
-    X = zadd(X, M[c * Pv + pab]);
-    if (g.E2) {
-      const z* E2 = g.E2 + (int64_t)t * v;  // [P][t][c]: row stride nk * v
-      const z* M2 = g.M2 + (int64_t)t * Pv;  // [a][t][P]: row stride nk * Pv
-      X = zadd(X, E2[pab * nk * v + c]);
-      X = zadd(X, E2[pbc * nk * v + a]);
-      X = zsub(X, E2[pac * nk * v + b]);
-      X = zadd(X, M2[a * nk * Pv + pbc]);
-      X = zsub(X, M2[b * nk * Pv + pac]);
-      X = zadd(X, M2[c * nk * Pv + pab]);
-    }
-    const double D = g.d[o + a] + g.d[o + b] + g.d[o + c] - g.d[g.i] - g.d[g.j] - g.d[k];
-    // Z and Y summed over the cyclic orders of the occupied and of the virtual labels
-    const int occ[3] = {g.i, g.j, k};
-    const int vir[3] = {a, b, c};
-    z Zs = make_double2(0.0, 0.0), Ys = make_double2(0.0, 0.0);
-#pragma unroll
-    for (int s = 0; s < 3; ++s) {
-      const int64_t p = occ[s], q = occ[(s + 1) % 3], rr = occ[(s + 2) % 3];
-#pragma unroll
-      for (int u = 0; u < 3; ++u) {
-        const int64_t x = vir[u], y = vir[(u + 1) % 3], zz = vir[(u + 2) % 3];
-        const int64_t idx = ((p * o + q) * v + x) * v + y;
-        const z w = g.oovv[idx], tt = g.t2[idx];
-        const z a1 = g.t1[rr * v + zz], f = g.fov[rr * v + zz];
-        // <pq||xy> conj(t^z_r) + conj(t^{xy}_{pq}) f_rz
-        Zs = zfma_conj_a(a1, w, Zs);
-        Zs = zfma_conj_a(tt, f, Zs);
-        // t^{xy}_{pq} t^z_r
-        Ys = zadd(Ys, zmul(tt, a1));
+    for (int64_t c = b + 1 + lane; c < v; c += 32) {
+      const int k = g.k0 + t;
+      const z* E = g.E + (int64_t)t * Pv * v;
+      const z* M = g.M + (int64_t)t * v * Pv;
+      const int64_t pbc = pair_index(b, c, v), pac = pair_index(a, c, v);
+      // X = W^{abc} + W^{bca} + W^{cab}, W = E (antisymmetric in its first two virtual labels)
+      //                                  + M (antisymmetric in its last two)
+      z X = E[pab * v + c];
+      X = zadd(X, E[pbc * v + a]);
+      X = zsub(X, E[pac * v + b]);
+      X = zadd(X, M[a * Pv + pbc]);
+      X = zsub(X, M[b * Pv + pac]);
+      X = zadd(X, M[c * Pv + pab]);
+      if (g.E2) {
+        const z* E2 = g.E2 + (int64_t)t * v;  // [P][t][c]: row stride nk * v
+        const z* M2 = g.M2 + (int64_t)t * Pv;  // [a][t][P]: row stride nk * Pv
+        X = zadd(X, E2[pab * nk * v + c]);
+        X = zadd(X, E2[pbc * nk * v + a]);
+        X = zsub(X, E2[pac * nk * v + b]);
+        X = zadd(X, M2[a * nk * Pv + pbc]);
+        X = zsub(X, M2[b * nk * Pv + pac]);
+        X = zadd(X, M2[c * nk * Pv + pab]);
       }
+      const double D = g.d[o + a] + g.d[o + b] + g.d[o + c] - g.d[g.i] - g.d[g.j] - g.d[k];
+      // Z and Y summed over the cyclic orders of the occupied and of the virtual labels
+      const int occ[3] = {g.i, g.j, k};
+      const int vir[3] = {a, b, c};
+      z Zs = make_double2(0.0, 0.0), Ys = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int s = 0; s < 3; ++s) {
+        const int64_t p = occ[s], q = occ[(s + 1) % 3], rr = occ[(s + 2) % 3];
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+          const int64_t x = vir[u], y = vir[(u + 1) % 3], zz = vir[(u + 2) % 3];
+          const int64_t idx = ((p * o + q) * v + x) * v + y;
+          const z w = g.oovv[idx], tt = g.t2[idx];
+          const z a1 = g.t1[rr * v + zz], f = g.fov[rr * v + zz];
+          // <pq||xy> conj(t^z_r) + conj(t^{xy}_{pq}) f_rz
+          Zs = zfma_conj_a(a1, w, Zs);
+          Zs = zfma_conj_a(tt, f, Zs);
+          // t^{xy}_{pq} t^z_r
+          Ys = zadd(Ys, zmul(tt, a1));
+        }
+      }
+      // the determinant of t1 over rows (i, j, k) and columns (a, b, c)
+      z m[3][3];
+#pragma unroll
+      for (int rr = 0; rr < 3; ++rr)
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) m[rr][cc] = g.t1[(int64_t)occ[rr] * v + vir[cc]];
+      const z c0 = zsub(zmul(m[1][1], m[2][2]), zmul(m[1][2], m[2][1]));
+      const z c1 = zsub(zmul(m[1][0], m[2][2]), zmul(m[1][2], m[2][0]));
+      const z c2 = zsub(zmul(m[1][0], m[2][1]), zmul(m[1][1], m[2][0]));
+      Ys = zadd(Ys, zadd(zsub(zmul(m[0][0], c0), zmul(m[0][1], c1)), zmul(m[0][2], c2)));
+      const double inv = 1.0 / D;
+      s4 += (X.x * X.x + X.y * X.y) * inv;
+      s5 += (X.x * Zs.x - X.y * Zs.y) * inv;
+      s5m += X.x * Ys.x + X.y * Ys.y;
     }
-    // the determinant of t1 over rows (i, j, k) and columns (a, b, c)
-    z m[3][3];
-#pragma unroll
-    for (int rr = 0; rr < 3; ++rr)
-#pragma unroll
-      for (int cc = 0; cc < 3; ++cc) m[rr][cc] = g.t1[(int64_t)occ[rr] * v + vir[cc]];
-    const z c0 = zsub(zmul(m[1][1], m[2][2]), zmul(m[1][2], m[2][1]));
-    const z c1 = zsub(zmul(m[1][0], m[2][2]), zmul(m[1][2], m[2][0]));
-    const z c2 = zsub(zmul(m[1][0], m[2][1]), zmul(m[1][1], m[2][0]));
-    Ys = zadd(Ys, zadd(zsub(zmul(m[0][0], c0), zmul(m[0][1], c1)), zmul(m[0][2], c2)));
-    const double inv = 1.0 / D;
-    s4 += (X.x * X.x + X.y * X.y) * inv;
-    s5 += (X.x * Zs.x - X.y * Zs.y) * inv;
-    s5m += X.x * Ys.x + X.y * Ys.y;
   }
   // fixed-shape block reduction
   __shared__ double red[3][kTriplesThreads / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int warp = threadIdx.x >> 5;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
     s4 += __shfl_down_sync(0xffffffffu, s4, off);
@@ -314,7 +317,7 @@ cudaError_t triples_eval(TriplesArgs& a, cudaStream_t s) {
         q.fov = a.fov;
         q.d = a.d;
         q.partials = a.partials;
-        const int grid = energy_grid((int64_t)nk * Pv * v);
+        const int grid = energy_grid((int64_t)nk * Pv * 32);
         triples_energy_kernel<<<grid, kTriplesThreads, 0, s>>>(q);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         triples_accumulate_kernel<<<1, 32, 0, s>>>(a.partials, grid, a.pair_acc + ((int64_t)i * o + j) * 3);
