@@ -301,6 +301,7 @@ def split_target_companion(ccmod, inputs, flops, stream, local, meth, n_cmp=2, n
             "energy_fp64": [e_f.real, e_f.imag],
             "ladder_ms": lad_ms, "ladder_e4m3_frac": lad_frac,
             "ladder_peak_basis": f"{peak_kind} bf16_tflops (burst) x 2 (nominal dense FP8/BF16 ratio)",
+            "top_ops_ms": {k: round(t, 3) for k, t in sorted(opd_s.items(), key=lambda kv: -kv[1])[:10]},
             "device_bytes": {"split": bytes_s, "fp64": bytes_f},
             "create_s": {"split": create_split, "fp64": create_fp64},
             "clocks": {"split": clocks_s, "fp64": clocks_f}}

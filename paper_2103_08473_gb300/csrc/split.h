@@ -86,9 +86,10 @@ int64_t split_part_bytes(int64_t M, int64_t N, int64_t K, const SplitConfig& cfg
 // memory for the K-split partials (split_part_bytes); without it K is not split.
 // wait_cycles: budget of every device wait (0 = about 2 s). stall_loads (self-test of the
 // failure path only): the producer issues no copies, so the MMA issuer's first wait runs out.
+// conjB: C = alpha * A conj(B)^T + beta * C (the digits of B are those of the unconjugated rows).
 cudaError_t split_gemm(const SliceSet& A, const SliceSet& B, z* C, int64_t ldc, z alpha, z beta,
                        int* err, void* part_ws, int64_t part_bytes, cudaStream_t s, long long wait_cycles = 0,
-                       int stall_loads = 0);
+                       int stall_loads = 0, int conjB = 0);
 // Probe: C (FP64 real, M x N) = A B^T for integer-valued A (M x K) and B (N x K) stored as
 // single digits, summed in one FP32 accumulator over all of K (exactness checks of the
 // tensor-core accumulation). mem: 2 slice sets of one digit each.

@@ -75,6 +75,7 @@ struct SplitArgs {
   long long wait_cycles;
   int stall_loads;          // self-test only: the producer issues no loads, so the first wait runs out
   int transC;               // 1: the kernel's (m, n) is the caller's C[n][m] (operands swapped)
+  int conjA, conjB;         // conjugate the kernel's A / B operand (the sign of its imaginary digits)
 };
 
 // ---- PTX wrappers ----------------------------------------------------------
@@ -121,6 +122,32 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// d * 2^k by adding k to the exponent field (integer pipe; the FP64 pipe of this chip is the
+// scarce one): exact, and the same value as the FP64 multiply, whenever both d and the result are
+// normal numbers; zero, subnormal or out-of-range cases take the FP64 multiply.
+__device__ __forceinline__ double scale_pow2(double d, int k) {
+  const long long bits = __double_as_longlong(d);
+  const int e = (int)((bits >> 52) & 0x7FF);
+  if (e == 0 || e + k <= 0 || e + k >= 0x7FF) return d * ldexp(1.0, k);
+  return __longlong_as_double(bits + ((long long)k << 52));
+}
+// An FP32 accumulator value (an integer below 2^24 in magnitude, so zero or normal) times 2^k, as
+// a double, built by integer arithmetic: the sign moves to bit 63, the exponent is rebiased by
+// 1023 - 127 + k and the mantissa shifted into place. The same value as (double)v * 2^k; out of
+// the normal range it takes that FP64 path.
+__device__ __forceinline__ double f32_times_pow2(uint32_t fbits, int k) {
+  if ((fbits & 0x7FFFFFFFu) == 0u) return 0.0;
+  const long long e = (long long)((fbits >> 23) & 0xFFu) - 127 + 1023 + k;
+  if (e <= 0 || e >= 0x7FF) return (double)__uint_as_float(fbits) * ldexp(1.0, k);
+  const unsigned long long bits = ((unsigned long long)(fbits >> 31) << 63) | ((unsigned long long)e << 52) |
+                                  ((unsigned long long)(fbits & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)bits);
+}
+// The power of two of a positive normal double that is one (a digit row or column scale).
+__device__ __forceinline__ int pow2_exponent(double s) {
+  return (int)((__double_as_longlong(s) >> 52) & 0x7FF) - 1023;
+}
 
 // Shared-memory matrix descriptor: K-major operand in the canonical 128-byte
 // swizzled layout written by TMA (8-row groups 1024 bytes apart).
@@ -264,6 +291,8 @@ __global__ void __launch_bounds__(192, 1)
     // ---------------- UMMA issuer ----------------
     if (lane == 0) {
       const uint32_t id = make_idesc(KIND, 0, BN), idn = make_idesc(KIND, 1, BN);
+      const uint32_t idRI = (args.conjA ^ args.conjB) ? id : idn, idIm1 = args.conjB ? idn : id,
+                     idIm2 = args.conjA ? idn : id;
       int it = 0, g = 0;
       bool ok = true;
       for (int L = 0; L <= args.lmax && ok; ++L)
@@ -289,17 +318,20 @@ __global__ void __launch_bounds__(192, 1)
               }
               tc_fence_after();
               const uint32_t sa = base + st * kStageBytes;
+              // descriptors of the stage's four tiles; each 32-byte K step adds 2 to the start address
+              // (16-byte units), the issuing thread's only per-MMA arithmetic
+              const uint64_t aR0 = sw128_desc(sa), aI0 = sw128_desc(sa + kTileA);
+              const uint64_t bR0 = sw128_desc(sa + 2 * kTileA), bI0 = sw128_desc(sa + 2 * kTileA + kTileB);
 #pragma unroll
               for (int kk = 0; kk < 4; ++kk) {
                 const uint32_t acc = (first && kk == 0) ? 0u : 1u;
-                const uint64_t aR = sw128_desc(sa + kk * 32), bR = sw128_desc(sa + 2 * kTileA + kk * 32);
-                umma<KIND>(dre, aR, bR, id, acc);
+                const uint64_t o = 2u * (uint64_t)kk;
+                umma<KIND>(dre, aR0 + o, bR0 + o, id, acc);
                 if (!PROBE) {
-                  const uint64_t aI = sw128_desc(sa + kTileA + kk * 32),
-                                 bI = sw128_desc(sa + 2 * kTileA + kTileB + kk * 32);
-                  umma<KIND>(dre, aI, bI, idn, 1u);
-                  umma<KIND>(dim, aR, bI, id, acc);
-                  umma<KIND>(dim, aI, bR, id, 1u);
+                  // conjugating an operand flips the sign of its imaginary digits' products
+                  umma<KIND>(dre, aI0 + o, bI0 + o, idRI, 1u);
+                  umma<KIND>(dim, aR0 + o, bI0 + o, idIm1, acc);
+                  umma<KIND>(dim, aI0 + o, bR0 + o, idIm2, 1u);
                 }
               }
               umma_commit(empty(st));
@@ -344,8 +376,13 @@ __global__ void __launch_bounds__(192, 1)
         tc_fence_after();
         const uint32_t trow = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)buf * (2u * BN);
         const double gs = ldexp(1.0, -args.b * (L + 2));
-        // real alpha folds into the per-row factor: 1 DMUL + 2 DFMA per complex element
+        // alpha = +-1 (every K-split partial, and most calls): the accumulator values go to FP64 by
+        // integer arithmetic, scaled by the row and column powers of two on the way, so each part
+        // costs one DADD on the FP64 pipe; other real alpha: 1 DMUL + 2 DFMA per complex element
         const bool real_alpha = alpha.y == 0.0;
+        const bool unit_alpha = real_alpha && (alpha.x == 1.0 || alpha.x == -1.0);
+        const uint32_t flip = (unit_alpha && alpha.x < 0.0) ? 0x80000000u : 0u;  // sign of alpha on the FP32 bits
+        const int krow = (!PROBE && mrow) ? pow2_exponent(rsc) - args.b * (L + 2) : 0;
         const double rowf = rsc * gs * (real_alpha ? alpha.x : 1.0);
 #pragma unroll 1
         for (int c = 0; c < BN; c += 32) {
@@ -371,13 +408,19 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
                 for (int j = 0; j < 8; ++j)
                   if (j0 + j < rem) {
-                    const double f = rowf * sc[j];
-                    const double vr = (double)__uint_as_float(re[j0 + j]), vi = (double)__uint_as_float(im[j0 + j]);
-                    if (real_alpha) {
-                      ov[j].x = fma(vr, f, ov[j].x);
-                      ov[j].y = fma(vi, f, ov[j].y);
+                    if (unit_alpha) {
+                      const int k = krow + pow2_exponent(sc[j]);
+                      ov[j].x += f32_times_pow2(re[j0 + j] ^ flip, k);
+                      ov[j].y += f32_times_pow2(im[j0 + j] ^ flip, k);
                     } else {
-                      ov[j] = zadd(ov[j], zmul(alpha, make_double2(vr * f, vi * f)));
+                      const double f = rowf * sc[j];
+                      const double vr = (double)__uint_as_float(re[j0 + j]), vi = (double)__uint_as_float(im[j0 + j]);
+                      if (real_alpha) {
+                        ov[j].x = fma(vr, f, ov[j].x);
+                        ov[j].y = fma(vi, f, ov[j].y);
+                      } else {
+                        ov[j] = zadd(ov[j], zmul(alpha, make_double2(vr * f, vi * f)));
+                      }
                     }
                     ocol[(int64_t)(j0 + j) * ldo] = ov[j];
                   }
@@ -404,13 +447,19 @@ __global__ void __launch_bounds__(192, 1)
                   }
 #pragma unroll
                   for (int j = 0; j < 8; ++j) {
-                    const double f = rowf * sc[j];
-                    const double vr = (double)__uint_as_float(re[j0 + j]), vi = (double)__uint_as_float(im[j0 + j]);
-                    if (real_alpha) {
-                      ov[j].x = fma(vr, f, ov[j].x);
-                      ov[j].y = fma(vi, f, ov[j].y);
+                    if (unit_alpha) {
+                      const int k = krow + pow2_exponent(sc[j]);
+                      ov[j].x += f32_times_pow2(re[j0 + j] ^ flip, k);
+                      ov[j].y += f32_times_pow2(im[j0 + j] ^ flip, k);
                     } else {
-                      ov[j] = zadd(ov[j], zmul(alpha, make_double2(vr * f, vi * f)));
+                      const double f = rowf * sc[j];
+                      const double vr = (double)__uint_as_float(re[j0 + j]), vi = (double)__uint_as_float(im[j0 + j]);
+                      if (real_alpha) {
+                        ov[j].x = fma(vr, f, ov[j].x);
+                        ov[j].y = fma(vi, f, ov[j].y);
+                      } else {
+                        ov[j] = zadd(ov[j], zmul(alpha, make_double2(vr * f, vi * f)));
+                      }
                     }
                     orow[j0 + j] = ov[j];
                   }
@@ -419,14 +468,20 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                   if (j >= rem) break;
-                  const double f = rowf * csc[j];
-                  const double vr = (double)__uint_as_float(re[j]), vi = (double)__uint_as_float(im[j]);
                   z o = orow[j];
-                  if (real_alpha) {
-                    o.x = fma(vr, f, o.x);
-                    o.y = fma(vi, f, o.y);
+                  if (unit_alpha) {
+                    const int k = krow + pow2_exponent(csc[j]);
+                    o.x += f32_times_pow2(re[j] ^ flip, k);
+                    o.y += f32_times_pow2(im[j] ^ flip, k);
                   } else {
-                    o = zadd(o, zmul(alpha, make_double2(vr * f, vi * f)));
+                    const double f = rowf * csc[j];
+                    const double vr = (double)__uint_as_float(re[j]), vi = (double)__uint_as_float(im[j]);
+                    if (real_alpha) {
+                      o.x = fma(vr, f, o.x);
+                      o.y = fma(vi, f, o.y);
+                    } else {
+                      o = zadd(o, zmul(alpha, make_double2(vr * f, vi * f)));
+                    }
                   }
                   orow[j] = o;
                 }
@@ -474,6 +529,11 @@ __host__ __device__ constexpr uint32_t make_idesc_n32(int kind, int negB) {
          ((uint32_t)negB << 14) | (((uint32_t)kSkBN >> 3) << 17) | ((128u >> 4) << 24);
 }
 
+// Order in which the short-K kernel takes the A digit planes: 0, s-1, 1, s-2, ... Plane p joins
+// s - p products, so alternating heavy and light planes keeps each stage of the A ring busy
+// long enough to cover the next plane's load. Each level's FP32 sum is exact in any order.
+__device__ __forceinline__ int plane_at(int i, int s) { return (i & 1) ? s - 1 - (i >> 1) : (i >> 1); }
+
 struct SmallKArgs {
   int64_t M, N, Mp, Np, a_row0, b_row0;
   int tiles_m, tiles;
@@ -486,7 +546,20 @@ struct SmallKArgs {
   const double* cs;
   int* err;
   long long wait_cycles;
+  int conjA, conjB;  // conjugate the kernel's A / B operand
+  int tiles_n;       // column tiles; nfast: consecutive tiles step through the columns first
+  int nfast;
 };
+
+// Origin of a tile. With few column tiles (a short N), consecutive tiles, which neighbouring
+// CTAs run at the same time, are the column tiles of one row tile: the A digits of that row tile
+// come from DRAM once and from L2 for the others. Otherwise the row tiles step first.
+__device__ __forceinline__ void sk_tile_origin(const SmallKArgs& a, int tile, int64_t& m0, int64_t& n0) {
+  const int tm = a.nfast ? tile / a.tiles_n : tile % a.tiles_m;
+  const int tn = a.nfast ? tile % a.tiles_n : tile / a.tiles_m;
+  m0 = (int64_t)tm * 128;
+  n0 = (int64_t)tn * kSkBN;
+}
 
 // Per K block: every B digit plane is loaded once into a B buffer, then each A plane p once
 // into an A stage, and the products of p with every q <= s - 1 - p are issued from them.
@@ -548,7 +621,8 @@ __global__ void __launch_bounds__(192, 1)
       int ja = 0, jb = 0;
       bool ok = true;
       for (int tile = blockIdx.x; tile < args.tiles && ok; tile += gridDim.x) {
-        const int64_t m0 = (int64_t)(tile % args.tiles_m) * 128, n0 = (int64_t)(tile / args.tiles_m) * kSkBN;
+        int64_t m0, n0;
+        sk_tile_origin(args, tile, m0, n0);
         const int64_t ya = args.a_row0 + m0, yb = args.b_row0 + n0;
         for (int kb = 0; kb < args.kblocks && ok; ++kb, ++jb) {
           const int x = kb * BKE;
@@ -565,7 +639,8 @@ __global__ void __launch_bounds__(192, 1)
                 tma_load_2d(dst + (uint32_t)(q * 2 + r) * kSkTileB, &tmB, x, (int)((q * 2 + r) * args.Np + yb),
                             bfull(bs));
           }
-          for (int p = 0; p < S; ++p, ++ja) {
+          for (int pi = 0; pi < S; ++pi, ++ja) {
+            const int p = plane_at(pi, S);
             const int as = ja % kSkAStages;
             if (!mbar_wait(aempty(as), ((uint32_t)(ja / kSkAStages) & 1u) ^ 1u, budget, abort_flag)) {
               ok = false;
@@ -592,6 +667,8 @@ __global__ void __launch_bounds__(192, 1)
     // ---------------- UMMA issuer: pair (p, q) into level p + q's accumulator ----------------
     if (lane == 0) {
       const uint32_t id = make_idesc_n32(KIND, 0), idn = make_idesc_n32(KIND, 1);
+      const uint32_t idRI = (args.conjA ^ args.conjB) ? id : idn, idIm1 = args.conjB ? idn : id,
+                     idIm2 = args.conjA ? idn : id;
       int ja = 0, jb = 0, t = 0;
       bool ok = true;
       for (int tile = blockIdx.x; tile < args.tiles && ok; tile += gridDim.x, ++t) {
@@ -609,7 +686,8 @@ __global__ void __launch_bounds__(192, 1)
           }
           tc_fence_after();
           const uint32_t sb = bbase + bs * kSkBBuf;
-          for (int p = 0; p < S && ok; ++p, ++ja) {
+          for (int pi = 0; pi < S && ok; ++pi, ++ja) {
+            const int p = plane_at(pi, S);
             const int as = ja % kSkAStages;
             if (!mbar_wait(afull(as), (uint32_t)(ja / kSkAStages) & 1u, budget, abort_flag)) {
               ok = false;
@@ -617,20 +695,21 @@ __global__ void __launch_bounds__(192, 1)
             }
             tc_fence_after();
             const uint32_t sa = abase + as * kSkAStage;
+            const uint64_t aR0 = sw128_desc(sa), aI0 = sw128_desc(sa + kSkTileA);
             for (int q = 0; q < S - p; ++q) {
               const int L = p + q;
               const uint32_t dre = tmem + (uint32_t)L * 64u, dim = dre + 32u;
-              const uint32_t sbr = sb + (uint32_t)(q * 2) * kSkTileB, sbi = sbr + kSkTileB;
+              const uint32_t sbr = sb + (uint32_t)(q * 2) * kSkTileB;
+              const uint64_t bR0 = sw128_desc(sbr), bI0 = sw128_desc(sbr + kSkTileB);
               const bool first = !(started & (1u << L));
 #pragma unroll
               for (int kk = 0; kk < 4; ++kk) {
                 const uint32_t acc = (first && kk == 0) ? 0u : 1u;
-                const uint64_t aR = sw128_desc(sa + kk * 32), aI = sw128_desc(sa + kSkTileA + kk * 32);
-                const uint64_t bR = sw128_desc(sbr + kk * 32), bI = sw128_desc(sbi + kk * 32);
-                umma<KIND>(dre, aR, bR, id, acc);
-                umma<KIND>(dre, aI, bI, idn, 1u);
-                umma<KIND>(dim, aR, bI, id, acc);
-                umma<KIND>(dim, aI, bR, id, 1u);
+                const uint64_t o = 2u * (uint64_t)kk;  // 32 bytes of K, in the 16-byte address units
+                umma<KIND>(dre, aR0 + o, bR0 + o, id, acc);
+                umma<KIND>(dre, aI0 + o, bI0 + o, idRI, 1u);
+                umma<KIND>(dim, aR0 + o, bI0 + o, idIm1, acc);
+                umma<KIND>(dim, aI0 + o, bR0 + o, idIm2, 1u);
               }
               started |= 1u << L;
             }
@@ -659,7 +738,8 @@ __global__ void __launch_bounds__(192, 1)
         break;
       }
       tc_fence_after();
-      const int64_t m0 = (int64_t)(tile % args.tiles_m) * 128, n0 = (int64_t)(tile / args.tiles_m) * kSkBN;
+      int64_t m0, n0;
+      sk_tile_origin(args, tile, m0, n0);
       const int64_t m = m0 + q4 * 32 + lane;
       // Every level's sum is an integer below 2^24 in magnitude (exact in FP32); the levels are
       // combined exactly in 64-bit integers, sum_L acc_L 2^(b (lmax - L)) < 2^62, on the integer
@@ -683,16 +763,30 @@ __global__ void __launch_bounds__(192, 1)
       tc_fence_before();
       mbar_arrive(accempty);  // tensor memory is free for the next tile
       if (m < args.M) {
-        const double rsc = args.rs[m] * ldexp(1.0, -args.b * (args.lmax + 2));
+        // With alpha = +-1 (the common case) the scales, all powers of two, are applied by
+        // exponent arithmetic and the sign by negating the integers: the FP64 pipe only converts
+        // the two integers (and adds C when beta = 1). Otherwise: FP64 products.
+        const bool unit_alpha = args.alpha.y == 0.0 && (args.alpha.x == 1.0 || args.alpha.x == -1.0);
         const bool read_c = args.beta.x != 0.0 || args.beta.y != 0.0;
+        const bool beta_one = args.beta.x == 1.0 && args.beta.y == 0.0;
+        const int krow = pow2_exponent(args.rs[m]) - args.b * (args.lmax + 2);
+        const double rsc = args.rs[m] * ldexp(1.0, -args.b * (args.lmax + 2));
+        const bool neg = unit_alpha && args.alpha.x < 0.0;
 #pragma unroll
         for (int j = 0; j < kSkBN; ++j) {
           const int64_t n = n0 + j;
           if (n >= args.N) break;
-          const double f = rsc * args.cs[n];
-          z val = zmul(args.alpha, make_double2((double)ar[j] * f, (double)ai[j] * f));
+          z val;
+          if (unit_alpha) {
+            const int k = krow + pow2_exponent(args.cs[n]);
+            val = make_double2(scale_pow2((double)(neg ? -ar[j] : ar[j]), k),
+                               scale_pow2((double)(neg ? -ai[j] : ai[j]), k));
+          } else {
+            const double f = rsc * args.cs[n];
+            val = zmul(args.alpha, make_double2((double)ar[j] * f, (double)ai[j] * f));
+          }
           z* cp = args.transC ? args.C + n * args.ldc + m : args.C + m * args.ldc + n;
-          if (read_c) val = zadd(val, zmul(args.beta, *cp));
+          if (read_c) val = zadd(val, beta_one ? *cp : zmul(args.beta, *cp));
           *cp = val;
         }
       }
@@ -1176,15 +1270,21 @@ cudaError_t launch_smallk(const CUtensorMap& mapA, const CUtensorMap& mapB, cons
   return cudaGetLastError();
 }
 
-// C = alpha A B^T + beta C on the short-K kernel; the operand with more rows goes to the
-// 128-row side (with the output transposed when that is B).
+// C = alpha A B^T + beta C on the short-K kernel. B's rows (the caller's N, C's contiguous
+// dimension) go to the 128-row side, the output transposed, so that the lanes of a warp store
+// consecutive elements of a row of C; unless that pads much more than the other orientation
+// (a short N on the 128-row side).
 cudaError_t split_gemm_smallk(const SliceSet& A, const SliceSet& B, const SplitArgs& lv, z* C, int64_t ldc, z alpha,
-                              z beta, int* err, long long wait_cycles, cudaStream_t s) {
-  const bool swap = A.rows < B.rows;
+                              z beta, int* err, long long wait_cycles, cudaStream_t s, int conjB) {
+  const double area_keep = (double)round_up(A.rows, 128) * (double)round_up(B.rows, kSkBN);
+  const double area_swap = (double)round_up(B.rows, 128) * (double)round_up(A.rows, kSkBN);
+  const bool swap = area_swap <= 1.05 * area_keep;
   const SliceSet& KA = swap ? B : A;
   const SliceSet& KB = swap ? A : B;
   SmallKArgs k;
   std::memset(&k, 0, sizeof(k));
+  k.conjA = swap ? conjB : 0;  // the caller's B is the kernel's A when swapped
+  k.conjB = swap ? 0 : conjB;
   k.M = KA.rows;
   k.N = KB.rows;
   k.Mp = KA.rows_pad;
@@ -1194,6 +1294,8 @@ cudaError_t split_gemm_smallk(const SliceSet& A, const SliceSet& B, const SplitA
   const int64_t tm = (k.M + 127) / 128, tn = (k.N + kSkBN - 1) / kSkBN;
   if (tm * tn > 0x7fffffff) return cudaErrorInvalidValue;
   k.tiles_m = (int)tm;
+  k.tiles_n = (int)tn;
+  k.nfast = tn <= tm ? 1 : 0;
   k.tiles = (int)(tm * tn);
   k.s = lv.s;
   k.b = lv.b;
@@ -1325,7 +1427,8 @@ int64_t split_part_bytes(int64_t M, int64_t N, int64_t K, const SplitConfig& cfg
 }
 
 cudaError_t split_gemm(const SliceSet& A, const SliceSet& B, z* C, int64_t ldc, z alpha, z beta, int* err,
-                       void* part_ws, int64_t part_bytes, cudaStream_t s, long long wait_cycles, int stall_loads) {
+                       void* part_ws, int64_t part_bytes, cudaStream_t s, long long wait_cycles, int stall_loads,
+                       int conjB) {
   if (A.kind != B.kind || A.Kp != B.Kp || A.s != B.s || A.b != B.b || !A.have_map || !B.have_map)
     return cudaErrorInvalidValue;
   SplitArgs a;
@@ -1348,6 +1451,8 @@ cudaError_t split_gemm(const SliceSet& A, const SliceSet& B, z* C, int64_t ldc, 
   a.tiles_m = (int)tl.tiles_m;
   a.tiles = (int)tl.tiles;
   a.transC = tl.swap ? 1 : 0;
+  a.conjA = tl.swap ? conjB : 0;  // the caller's B is the kernel's A when swapped
+  a.conjB = tl.swap ? 0 : conjB;
   a.C = C;
   a.ldc = ldc;
   a.alpha = alpha;
@@ -1359,7 +1464,7 @@ cudaError_t split_gemm(const SliceSet& A, const SliceSet& B, z* C, int64_t ldc, 
   const int kblocks = (int)(A.Kp / bke(A.kind));
   if (!fill_levels(a, A.s, A.b, kblocks, A.kind)) return cudaErrorInvalidValue;
   if (!stall_loads && smallk_eligible(a))
-    return split_gemm_smallk(A, B, a, C, ldc, alpha, beta, err, wait_cycles, s);
+    return split_gemm_smallk(A, B, a, C, ldc, alpha, beta, err, wait_cycles, s, conjB);
   plan_ksplit(a.tiles, kblocks, a.ksplits, a.kb_split);
   if (stall_loads) {
     a.ksplits = 1;
