@@ -124,8 +124,8 @@ struct ccsd_ctx {
   z *lscratch = nullptr, *dscratch = nullptr;
   DiisArgs ldiis;
   z *lG = nullptr, *ltaub = nullptr, *lHrb = nullptr, *lXb = nullptr, *lzb = nullptr, *lCb = nullptr,
-    *lCanti = nullptr, *lCp = nullptr, *lAb = nullptr, *lAanti = nullptr, *lAfull = nullptr, *lpk = nullptr,
-    *lpk2 = nullptr, *lout = nullptr, *lout2 = nullptr, *lout3 = nullptr;
+    *lCanti = nullptr, *lCp = nullptr, *lAb = nullptr, *lAanti = nullptr, *lpk = nullptr,
+    *lpk2 = nullptr, *lout = nullptr, *lout2 = nullptr, *lout3 = nullptr, *lApk = nullptr;
   z *lGvvb = nullptr, *lHvvb = nullptr, *lGoob = nullptr, *lHoob = nullptr, *lHovb = nullptr;
   z *dgoo = nullptr, *dgvo = nullptr, *dgvv = nullptr, *dq1 = nullptr, *dq2 = nullptr, *dq3 = nullptr, *dgam = nullptr,
     *dgam2 = nullptr;
@@ -1619,12 +1619,13 @@ ccsd_status build_lambda_plan(ccsd_ctx* ctx) {
   CS(once(&ctx->l2, n2));
   for (z** p : {&ctx->lG, &ctx->ltaub, &ctx->lHrb, &ctx->lXb, &ctx->lzb}) CS(once(p, n2));
   for (z** p : {&ctx->lCb, &ctx->lCanti, &ctx->lCp}) CS(once(p, ov * o * o));
-  for (z** p : {&ctx->lAb, &ctx->lAanti, &ctx->lAfull}) CS(once(p, o4));
+  for (z** p : {&ctx->lAb, &ctx->lAanti}) CS(once(p, o4));
+  CS(once(&ctx->lApk, Po * Po));
   CS(once(&ctx->lpk, (int64_t)o * o * Pv));
   CS(once(&ctx->lpk2, Po * Pv));
   CS(once(&ctx->lout, Po * Pv));
   CS(once(&ctx->lout2, (int64_t)o * o * Pv));
-  CS(once(&ctx->lout3, (int64_t)o * o * Pv));
+  CS(once(&ctx->lout3, std::max<int64_t>((int64_t)o * o * Pv, ov * Po)));  // also C-bar packed over (i<j)
   CS(once(&ctx->lGvvb, (int64_t)v * v));
   CS(once(&ctx->lHvvb, (int64_t)v * v));
   CS(once(&ctx->lGoob, (int64_t)o * o));
@@ -1662,20 +1663,6 @@ ccsd_status build_lambda_plan(ccsd_ctx* ctx) {
   z *t1 = ctx->t1, *t2 = ctx->t2, *l1 = ctx->l1, *l2 = ctx->l2, *r1 = ctx->S1, *G = ctx->lG, *taub = ctx->ltaub;
   z *Hrb = ctx->lHrb, *Xb = ctx->lXb, *zb = ctx->lzb;
 
-  // A^{kl}_{ij} in full from its packed copy (the residual plan adds its tau term packed)
-  {
-    z *apk = ctx->Apk, *af = ctx->lAfull;
-    P->custom("L:A", [=](cudaStream_t s) {
-      UnpackArgs u;
-      u.in = apk;
-      u.out = af;
-      u.n1 = o;
-      u.n2 = o;
-      u.unpack_rows = 1;
-      u.beta = 0.0;
-      return unpack_pairs(u, s);
-    });
-  }
   // energy: dE/dt1 = f_ia, dE/dtau = 1/4 <ij||ab>
   P->add("L:E", W(r1, "ia"), one, V(ctx->fov, "ia"), false, 0.0);
   P->add("L:E", W(taub, "ijab"), quarter, V(ctx->oovv, "ijab"), false, 0.0);
@@ -1707,23 +1694,89 @@ ccsd_status build_lambda_plan(ccsd_ctx* ctx) {
   P->contract("L:gvv", W(G, "ijcb"), half, W(l2, "ijab"), false, W(ctx->Gvv, "ac"), false, 1.0);
   P->contract("L:ct1", W(ctx->lCb, "kaij"), half, W(l2, "ijab"), false, W(t1, "kb"), false, 0.0);
   P->contract("L:ct1", W(r1, "kb"), half, W(l2, "ijab"), false, W(ctx->C, "kaij"), false, 1.0);
-  P->contract("L:hole", W(ctx->lAb, "klij"), eighth, W(l2, "ijab"), false, W(ctx->tau, "klab"), false, 0.0);
-  P->contract("L:hole", W(taub, "klab"), eighth, W(l2, "ijab"), false, W(ctx->lAfull, "klij"), false, 1.0);
   {
-    // ladder: 1/8 sum_ab l2[ijab] <ab||cd> = 1/4 sum_{a<b}, one packed GEMM against <ab||cd>
-    z *lpk2 = ctx->lpk2, *lout = ctx->lout;
-    P->custom("L:ladder", [=](cudaStream_t s) { return pack_pairs(l2, lpk2, o, v, 1, s); });
+    // hole ladder 1/2 sum_kl A^{kl}_{ij} tau^{ab}_{kl}, all three labels pairs antisymmetric: over
+    // packed pairs, as in the residual. A-bar[kl][ij] = 1/8 sum_ab l2[ijab] tau[klab]
+    //   -> lApk[P(kl)][P(ij)] = 1/4 sum_{a<b} tau_pk[P(kl)][P(ab)] l2_pk[P(ij)][P(ab)];
+    // tau-bar[klab] += 1/8 sum_ij l2[ijab] A[klij] -> 1/4 sum_{i<j} Apk[P(kl)][P(ij)] l2_pk[P(ij)][P(ab)]
+    z *lpk2 = ctx->lpk2, *lout = ctx->lout, *lapk = ctx->lApk, *lab = ctx->lAb;
+    P->custom("L:hole", [=](cudaStream_t s) { return pack_pairs(l2, lpk2, o, v, 1, s); });
     ZGemmArgs g;
     g.M = Po;
-    g.N = Pv;
+    g.N = Po;
     g.K = Pv;
-    g.A = lpk2;
+    g.A = ctx->tau_pk;
     g.lda = Pv;
-    g.B = ctx->Wpk;
+    g.B = lpk2;
     g.ldb = Pv;
-    g.C = lout;
-    g.ldc = Pv;
-    P->gemm("L:ladder:gemm", g);
+    g.transB = 1;
+    g.C = lapk;
+    g.ldc = Po;
+    g.alpha = quarter;
+    P->gemm("L:hole:gemm", g);
+    P->custom("L:hole", [=](cudaStream_t s) {
+      UnpackArgs u;  // A-bar in full, for the terms that read it unpacked
+      u.in = lapk;
+      u.out = lab;
+      u.n1 = o;
+      u.n2 = o;
+      u.unpack_rows = 1;
+      u.beta = 0.0;
+      return unpack_pairs(u, s);
+    });
+    ZGemmArgs h;
+    h.M = Po;
+    h.N = Pv;
+    h.K = Po;
+    h.A = ctx->Apk;
+    h.lda = Po;
+    h.B = lpk2;
+    h.ldb = Pv;
+    h.C = lout;
+    h.ldc = Pv;
+    h.alpha = quarter;
+    P->gemm("L:hole:gemm", h);
+    P->custom("L:hole", [=](cudaStream_t s) {
+      UnpackArgs u;
+      u.in = lout;
+      u.out = taub;
+      u.n1 = o;
+      u.n2 = v;
+      u.unpack_rows = 1;
+      u.beta = 1.0;
+      return unpack_pairs(u, s);
+    });
+  }
+  {
+    // ladder: 1/8 sum_ab l2[ijab] <ab||cd> = 1/4 sum_{a<b}, one packed GEMM against <ab||cd>
+    // (l2 packed over both pairs by the hole term above)
+    z *lpk2 = ctx->lpk2, *lout = ctx->lout;
+    if (ctx->use_split) {
+      // against the digits of <ab||cd> cut at creation (rows (a<b) over K = (c<d)): the GEMM wants
+      // rows (c<d) over K = (a<b), i.e. <ab||cd> = conj(<cd||ab>), the cached rows conjugated
+      P->note_aux_bytes(slice_bytes(Po, Pv, ctx->split) + split_part_bytes(Po, Pv, Pv, ctx->split));
+      P->custom("L:ladder:gemm", [ctx, lpk2, lout, Po, Pv](cudaStream_t s) {
+        SliceSet SA;
+        uint8_t* w = static_cast<uint8_t*>(ctx->split_ws);
+        cudaError_t e = make_slices(lpk2, Po, Pv, Pv, 0, 0, ctx->split, SA, w, s);
+        if (e == cudaSuccess)
+          e = split_gemm(SA, ctx->Wsl, lout, Pv, zmake(1, 0), zmake(0, 0), ctx->split_err,
+                         w + slice_bytes(Po, Pv, ctx->split), split_part_bytes(Po, Pv, Pv, ctx->split), s, 0, 0, 1);
+        return e;
+      }, 8.0 * (double)Po * (double)Pv * (double)Pv);
+    } else {
+      ZGemmArgs g;
+      g.M = Po;
+      g.N = Pv;
+      g.K = Pv;
+      g.A = lpk2;
+      g.lda = Pv;
+      g.B = ctx->Wpk;
+      g.ldb = Pv;
+      g.C = lout;
+      g.ldc = Pv;
+      P->gemm("L:ladder:gemm", g);
+    }
     P->custom("L:ladder", [=](cudaStream_t s) {
       UnpackArgs u;
       u.in = lout;
@@ -1789,31 +1842,61 @@ ccsd_status build_lambda_plan(ccsd_ctx* ctx) {
   P->contract("L:ooov", W(taub, "klca"), half, W(l1, "ia"), false, V(ctx->ooov, "klic"), false, 1.0);
   P->contract("L:vovo", W(r1, "kc"), mone, W(l1, "ia"), false, V(ctx->J, "iakc"), false, 1.0);
   // A^{kl}_{ij}
-  P->contract("L:A", W(taub, "ijcd"), half, W(ctx->lAb, "klij"), false, V(ctx->oovv, "klcd"), false, 1.0);
+  {
+    // tau-bar[ijcd] += 1/2 sum_kl A-bar[klij] <kl||cd> = sum_{k<l}, packed over (i<j) and (c<d)
+    z *lout = ctx->lout;
+    ZGemmArgs g;
+    g.M = Po;
+    g.N = Pv;
+    g.K = Po;
+    g.A = ctx->lApk;
+    g.lda = Po;
+    g.transA = 1;
+    g.B = ctx->oovv_pk;
+    g.ldb = Pv;
+    g.C = lout;
+    g.ldc = Pv;
+    P->gemm("L:A:gemm", g);
+    P->custom("L:A", [=](cudaStream_t s) {
+      UnpackArgs u;
+      u.in = lout;
+      u.out = taub;
+      u.n1 = o;
+      u.n2 = v;
+      u.unpack_rows = 1;
+      u.beta = 1.0;
+      return unpack_pairs(u, s);
+    });
+  }
   P->add("L:A", W(ctx->lAanti, "klij"), one, W(ctx->lAb, "klij"), false, 0.0);
   P->add("L:A", W(ctx->lAanti, "klij"), mone, W(ctx->lAb, "klji"), false, 1.0);
   P->contract("L:A", W(r1, "jc"), one, W(ctx->lAanti, "klij"), false, V(ctx->ooov, "klic"), false, 1.0);
-  // C^{kb}_{ij}: -1/2 sum_kb C-bar[k][b][i][j] <bk||cd> into tau-bar, packed over c<d
+  // C^{kb}_{ij}: -1/2 sum_kb C-bar[k][b][i][j] <bk||cd> into tau-bar, packed over c<d and (C-bar
+  // is antisymmetric in i, j) over i<j: C-bar as [(b,k)][P(i,j)], one GEMM with the (b,k) rows summed
   {
     z *cp = ctx->lCp, *o3 = ctx->lout3;
-    P->add("L:C", W(cp, "ijbk"), one, W(ctx->lCb, "kbij"), false, 0.0);
+    P->add("L:C", W(cp, "bkij"), one, W(ctx->lCb, "kbij"), false, 0.0);
+    P->custom("L:C", [=](cudaStream_t s) { return pack_pairs(cp, o3, (int64_t)v * o, o, 0, s); });
+    z* out = ctx->lout;
     ZGemmArgs g;
-    g.M = (int64_t)o * o;
+    g.M = Po;
     g.N = Pv;
     g.K = (int64_t)v * o;
-    g.A = cp;
-    g.lda = (int64_t)v * o;
+    g.A = o3;
+    g.lda = Po;
+    g.transA = 1;
     g.B = ctx->vovv_pk;
     g.ldb = Pv;
-    g.C = o3;
+    g.C = out;
     g.ldc = Pv;
     P->gemm("L:C:gemm", g);
     P->custom("L:C", [=](cudaStream_t s) {
       UnpackArgs u;
-      u.in = o3;
+      u.in = out;
       u.out = taub;
-      u.n1 = (int64_t)o * o;
+      u.n1 = o;
       u.n2 = v;
+      u.unpack_rows = 1;
       u.alpha = zmake(-0.5, 0);
       u.beta = 1.0;
       return unpack_pairs(u, s);
@@ -2243,13 +2326,15 @@ ccsd_status ccsd_triples(ccsd_ctx* ctx, int max_batch, double* out, double* pair
     a.fov = ctx->fov;
     a.d = ctx->dvec;
     a.max_batch = nb;
-    void *t2pk = nullptr, *work = nullptr, *partials = nullptr, *pacc = nullptr;
+    void *t2pk = nullptr, *work = nullptr, *partials = nullptr, *pacc = nullptr, *dsf = nullptr;
     if (!mem.get(&t2pk, sizeof(z) * (size_t)o * o * ctx->Pv) || !mem.get(&work, (size_t)per * nb) ||
+        !mem.get(&dsf, sizeof(float4) * (size_t)triples_dsf_elems(o, v)) ||
         !mem.get(&partials, sizeof(double) * (size_t)triples_partials(a)) ||
         !mem.get(&pacc, sizeof(double) * acc.size()))
       return set_err(ctx, CCSD_ERR_OOM, "triples workspace");
     a.t2pk = (z*)t2pk;
     a.work = (z*)work;
+    a.dsf = (float4*)dsf;
     a.partials = (double*)partials;
     a.pair_acc = (double*)pacc;
     SliceSet SA, SB, SM, ST;

@@ -40,33 +40,6 @@ __global__ void permute_direct_kernel(PermuteArgs g, int64_t total) {
   }
 }
 
-// The same copy one output row (all but the innermost output dim fixed) per warp: the row's
-// offsets are decoded once, and the lanes walk the innermost dim with unit output stride
-// (coalesced loads too when that dim is innermost in the input). For rows of >= 32 elements.
-__global__ void permute_rows_kernel(PermuteArgs g, int64_t outer) {
-  const int q = g.rank - 1;
-  const int64_t nq = g.dims[q], iq = g.istr[q], oq = g.ostr[q];
-  const int lane = threadIdx.x & 31;
-  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t r = w0; r < outer; r += nw) {
-    int64_t rr = r, io = 0, oo = 0;
-    for (int d = q - 1; d >= 0; --d) {
-      const int64_t c = rr % g.dims[d];
-      rr /= g.dims[d];
-      io += c * g.istr[d];
-      oo += c * g.ostr[d];
-    }
-    const z* in = g.in + io;
-    z* out = g.out + oo;
-    for (int64_t c = lane; c < nq; c += 32) {
-      const z v = ld_conj(in + c * iq, g.conj);
-      z* o = out + c * oq;
-      *o = g.beta != 0.0 ? zaxpby(g.alpha, v, g.beta, *o) : zmul(g.alpha, v);
-    }
-  }
-}
-
 // 32 x 32 shared-memory transpose over output dims (p, q): q is innermost in the
 // output, p is innermost (stride 1) in the input, so both the loads and the
 // stores are coalesced. The remaining dims are walked by blockIdx.y.
@@ -614,10 +587,7 @@ cudaError_t permute_add(const PermuteArgs& a, cudaStream_t s) {
   if (a.istr[q] != 1 && a.dims[q] > 1)
     for (int d = 0; d < q; ++d)
       if (a.istr[d] == 1 && a.dims[d] > 1) p = d;
-  if (p < 0 && a.dims[q] >= 32) {
-    const int64_t outer = total / a.dims[q];
-    permute_rows_kernel<<<grid_for(outer * 32, kThreads), kThreads, 0, s>>>(a, outer);
-  } else if (p < 0) {
+  if (p < 0) {
     permute_direct_kernel<<<grid_for(total, kThreads), kThreads, 0, s>>>(a, total);
   } else {
     const int64_t tp = (a.dims[p] + 31) / 32, tq = (a.dims[q] + 31) / 32;

@@ -23,6 +23,8 @@
 
 #include "triples.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ops.h"
 #include "zgemm.h"
 
@@ -40,12 +42,66 @@ struct EnergyArgs {
   // split precision: the products of the second layout, E2[P(a,b)][t][c] and M2[a][t][P(b,c)]
   const z *E2 = nullptr, *M2 = nullptr;
   const z *t1 = nullptr, *t2 = nullptr, *oovv = nullptr, *fov = nullptr;
+  // the same four in double-single form (float4 per complex: re hi, re lo, im hi, im lo)
+  const float4 *t1f = nullptr, *t2f = nullptr, *oovvf = nullptr, *fovf = nullptr;
   const double* d = nullptr;
   double* partials = nullptr;  // gridDim.x * 3
 };
 
-__device__ __forceinline__ z zfma_conj_a(z a, z b, z acc) {  // acc + conj(a) * b
-  return make_double2(acc.x + a.x * b.x + a.y * b.y, acc.y + a.x * b.y - a.y * b.x);
+// ---- double-single arithmetic --------------------------------------------------------
+// A value is the unevaluated sum hi + lo of two floats (|lo| <= ulp(hi) / 2), about 48 bits.
+// Knuth's two-sum and the fused-multiply-add form of Dekker's two-product make each step's
+// rounding error exact, so sums and products carry ~2^-47 relative error. The fifth-order
+// terms Z and Y (and t1's determinant) are formed this way on the FP32 pipe, which this chip
+// has ~64x more of than FP64; X, D and the energy sums stay in FP64.
+struct dsf {
+  float h, l;
+};
+struct dsc {
+  dsf r, i;
+};
+__device__ __forceinline__ dsf ds_quick(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dsf ds_add(dsf x, dsf y) {
+  const float s = __fadd_rn(x.h, y.h);
+  const float bb = __fsub_rn(s, x.h);
+  const float e = __fadd_rn(__fsub_rn(x.h, __fsub_rn(s, bb)), __fsub_rn(y.h, bb));
+  return ds_quick(s, __fadd_rn(e, __fadd_rn(x.l, y.l)));
+}
+__device__ __forceinline__ dsf ds_neg(dsf x) { return {-x.h, -x.l}; }
+__device__ __forceinline__ dsf ds_mul(dsf x, dsf y) {
+  const float p = __fmul_rn(x.h, y.h);
+  float e = __fmaf_rn(x.h, y.h, -p);
+  e = __fmaf_rn(x.h, y.l, e);
+  e = __fmaf_rn(x.l, y.h, e);
+  return ds_quick(p, e);
+}
+__device__ __forceinline__ dsc dsc_load(const float4* p) {
+  const float4 q = *p;
+  return {{q.x, q.y}, {q.z, q.w}};
+}
+__device__ __forceinline__ dsc dsc_add(dsc a, dsc b) { return {ds_add(a.r, b.r), ds_add(a.i, b.i)}; }
+__device__ __forceinline__ dsc dsc_sub(dsc a, dsc b) { return {ds_add(a.r, ds_neg(b.r)), ds_add(a.i, ds_neg(b.i))}; }
+__device__ __forceinline__ dsc dsc_mul(dsc a, dsc b) {
+  return {ds_add(ds_mul(a.r, b.r), ds_neg(ds_mul(a.i, b.i))), ds_add(ds_mul(a.r, b.i), ds_mul(a.i, b.r))};
+}
+__device__ __forceinline__ dsc dsc_conj_mul(dsc a, dsc b) {  // conj(a) * b
+  return {ds_add(ds_mul(a.r, b.r), ds_mul(a.i, b.i)), ds_add(ds_mul(a.r, b.i), ds_neg(ds_mul(a.i, b.r)))};
+}
+__device__ __forceinline__ z dsc_to_z(dsc a) {
+  return make_double2((double)a.r.h + (double)a.r.l, (double)a.i.h + (double)a.i.l);
+}
+
+// float4 (re hi, re lo, im hi, im lo) of every complex element: the double-single copies the
+// energy kernel reads.
+__global__ void to_double_single_kernel(const z* __restrict__ in, float4* __restrict__ out, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const z x = in[e];
+    const float rh = __double2float_rn(x.x), ih = __double2float_rn(x.y);
+    out[e] = make_float4(rh, __double2float_rn(x.x - (double)rh), ih, __double2float_rn(x.y - (double)ih));
+  }
 }
 
 __global__ void __launch_bounds__(kTriplesThreads) triples_energy_kernel(EnergyArgs g) {
@@ -89,7 +145,7 @@ __global__ void __launch_bounds__(kTriplesThreads) triples_energy_kernel(EnergyA
       // Z and Y summed over the cyclic orders of the occupied and of the virtual labels
       const int occ[3] = {g.i, g.j, k};
       const int vir[3] = {a, b, c};
-      z Zs = make_double2(0.0, 0.0), Ys = make_double2(0.0, 0.0);
+      dsc Zd = {{0.f, 0.f}, {0.f, 0.f}}, Yd = {{0.f, 0.f}, {0.f, 0.f}};
 #pragma unroll
       for (int s = 0; s < 3; ++s) {
         const int64_t p = occ[s], q = occ[(s + 1) % 3], rr = occ[(s + 2) % 3];
@@ -97,25 +153,25 @@ __global__ void __launch_bounds__(kTriplesThreads) triples_energy_kernel(EnergyA
         for (int u = 0; u < 3; ++u) {
           const int64_t x = vir[u], y = vir[(u + 1) % 3], zz = vir[(u + 2) % 3];
           const int64_t idx = ((p * o + q) * v + x) * v + y;
-          const z w = g.oovv[idx], tt = g.t2[idx];
-          const z a1 = g.t1[rr * v + zz], f = g.fov[rr * v + zz];
+          const dsc w = dsc_load(g.oovvf + idx), tt = dsc_load(g.t2f + idx);
+          const dsc a1 = dsc_load(g.t1f + rr * v + zz), f = dsc_load(g.fovf + rr * v + zz);
           // <pq||xy> conj(t^z_r) + conj(t^{xy}_{pq}) f_rz
-          Zs = zfma_conj_a(a1, w, Zs);
-          Zs = zfma_conj_a(tt, f, Zs);
+          Zd = dsc_add(Zd, dsc_add(dsc_conj_mul(a1, w), dsc_conj_mul(tt, f)));
           // t^{xy}_{pq} t^z_r
-          Ys = zadd(Ys, zmul(tt, a1));
+          Yd = dsc_add(Yd, dsc_mul(tt, a1));
         }
       }
       // the determinant of t1 over rows (i, j, k) and columns (a, b, c)
-      z m[3][3];
+      dsc m[3][3];
 #pragma unroll
       for (int rr = 0; rr < 3; ++rr)
 #pragma unroll
-        for (int cc = 0; cc < 3; ++cc) m[rr][cc] = g.t1[(int64_t)occ[rr] * v + vir[cc]];
-      const z c0 = zsub(zmul(m[1][1], m[2][2]), zmul(m[1][2], m[2][1]));
-      const z c1 = zsub(zmul(m[1][0], m[2][2]), zmul(m[1][2], m[2][0]));
-      const z c2 = zsub(zmul(m[1][0], m[2][1]), zmul(m[1][1], m[2][0]));
-      Ys = zadd(Ys, zadd(zsub(zmul(m[0][0], c0), zmul(m[0][1], c1)), zmul(m[0][2], c2)));
+        for (int cc = 0; cc < 3; ++cc) m[rr][cc] = dsc_load(g.t1f + (int64_t)occ[rr] * v + vir[cc]);
+      const dsc c0 = dsc_sub(dsc_mul(m[1][1], m[2][2]), dsc_mul(m[1][2], m[2][1]));
+      const dsc c1 = dsc_sub(dsc_mul(m[1][0], m[2][2]), dsc_mul(m[1][2], m[2][0]));
+      const dsc c2 = dsc_sub(dsc_mul(m[1][0], m[2][1]), dsc_mul(m[1][1], m[2][0]));
+      Yd = dsc_add(Yd, dsc_add(dsc_sub(dsc_mul(m[0][0], c0), dsc_mul(m[0][1], c1)), dsc_mul(m[0][2], c2)));
+      const z Zs = dsc_to_z(Zd), Ys = dsc_to_z(Yd);
       const double inv = 1.0 / D;
       s4 += (X.x * X.x + X.y * X.y) * inv;
       s5 += (X.x * Zs.x - X.y * Zs.y) * inv;
@@ -169,6 +225,11 @@ int64_t triples_partials(const TriplesArgs& a) {
   return 152 * 8 * 3;
 }
 
+int64_t triples_dsf_elems(int o, int v) {
+  const int64_t ov = (int64_t)o * v;
+  return 2 * ov + 2 * ov * ov;
+}
+
 int64_t triples_batch_elems(int v, bool split) { return (split ? 4 : 2) * pair_count(v) * (int64_t)v; }
 
 cudaError_t triples_eval(TriplesArgs& a, cudaStream_t s) {
@@ -183,6 +244,15 @@ cudaError_t triples_eval(TriplesArgs& a, cudaStream_t s) {
   cudaError_t e = pack_pairs(a.t2, a.t2pk, (int64_t)o * o, v, 0, s);
   if (e != cudaSuccess) return e;
   a.launches += 1;
+  // double-single copies for the energy kernel: t1, f_ov, t2, <ij||ab>
+  const int64_t ov = (int64_t)o * v, o2v2 = ov * ov;
+  float4 *t1f = a.dsf, *fovf = a.dsf + ov, *t2f = a.dsf + 2 * ov, *oovvf = a.dsf + 2 * ov + o2v2;
+  to_double_single_kernel<<<grid_for(ov, kTriplesThreads), kTriplesThreads, 0, s>>>(a.t1, t1f, ov);
+  to_double_single_kernel<<<grid_for(ov, kTriplesThreads), kTriplesThreads, 0, s>>>(a.fov, fovf, ov);
+  to_double_single_kernel<<<grid_for(o2v2, kTriplesThreads), kTriplesThreads, 0, s>>>(a.t2, t2f, o2v2);
+  to_double_single_kernel<<<grid_for(o2v2, kTriplesThreads), kTriplesThreads, 0, s>>>(a.oovv, oovvf, o2v2);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  a.launches += 4;
   const z minus1 = make_double2(-1.0, 0.0), one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
   for (int i = 0; i < o - 2; ++i) {
     for (int j = i + 1; j < o - 1; ++j) {
@@ -192,6 +262,7 @@ cudaError_t triples_eval(TriplesArgs& a, cudaStream_t s) {
         if (a.timer && (e = a.timer->mark(s)) != cudaSuccess) return e;
         // ---- e-terms: E[t][P(a,b)][c] over k = k0 + t
         if (a.sa) {
+          nvtxRangePushA("triples_eterms");  // a profiler selects these launches by this range
           // one split GEMM per term over the whole batch, C = -A_L B_pq^T over K = e:
           //   (k; ij): rows L = k of <eL||ab> for every k of the batch against t2[i][j]
           //            -> E[t][P(a,b)][c];
@@ -208,6 +279,7 @@ cudaError_t triples_eval(TriplesArgs& a, cudaStream_t s) {
             e = split_gemm(slice_rows(*a.sa, (int64_t)j * Pv, Pv),
                            slice_rows(*a.sb, ((int64_t)i * o + k0) * v, (int64_t)nk * v), E2buf, (int64_t)nk * v,
                            one, one, a.split_err, nullptr, 0, s);
+          nvtxRangePop();
           if (e != cudaSuccess) return e;
           a.launches += 3;
         } else {
@@ -315,6 +387,10 @@ cudaError_t triples_eval(TriplesArgs& a, cudaStream_t s) {
         q.t2 = a.t2;
         q.oovv = a.oovv;
         q.fov = a.fov;
+        q.t1f = t1f;
+        q.fovf = fovf;
+        q.t2f = t2f;
+        q.oovvf = oovvf;
         q.d = a.d;
         q.partials = a.partials;
         const int grid = energy_grid((int64_t)nk * Pv * 32);

@@ -50,6 +50,8 @@ struct TriplesArgs {
   z* t2pk = nullptr;           // o*o*P(v): t2 packed over its virtual pair
   z* work = nullptr;           // max_batch * triples_batch_elems(v)
   int max_batch = 1;           // triples (i, j, k) per batch, k consecutive
+  float4* dsf = nullptr;       // triples_dsf_elems(o, v): double-single copies of t1, f_ov, t2 and
+                               // <ij||ab> for the energy kernel's fifth-order terms
   double* partials = nullptr;  // triples_partials() doubles
   double* pair_acc = nullptr;  // o*o*3 doubles, zeroed by the caller; [(i*o + j)*3 + m] += the
                                // pair's sums of |X|^2/D (m=0), Re(X Z)/D (1), Re(X conj Y) (2)
@@ -73,6 +75,8 @@ struct TriplesArgs {
 // Complex elements of workspace per triple of a batch (the packed parts of W: two in FP64, four
 // in split precision).
 int64_t triples_batch_elems(int v, bool split);
+// float4 elements of the double-single copies (t1, f_ov: o v each; t2, <ij||ab>: o^2 v^2 each).
+int64_t triples_dsf_elems(int o, int v);
 // Doubles of block partials the energy kernel writes per batch.
 int64_t triples_partials(const TriplesArgs& a);
 // Enqueue the whole evaluation on s (no synchronisation). o < 3 or v < 3: nothing to do.

@@ -80,6 +80,42 @@ def test_blocked_vovv_terms_match_oracle(ccsd, vblock):
     assert _maxrel(q1, R1) < 1e-12 and _maxrel(q2, R2) < 1e-12
 
 
+@pytest.mark.parametrize("o,v,naux,seed,vblock", [(5, 13, 20, 508, 0), (4, 40, 30, 509, 7), (7, 23, 40, 510, 0)])
+def test_split_lambda_residual_matches_oracle(ccsd, o, v, naux, seed, vblock):
+    """The Lambda residual in split precision with every GEMM on the tensor cores (8 digits of
+    5 bits): its ladder adjoint runs against the digits of <ab||cd> cut at creation, read as
+    the conjugates of the rows it needs (<ab||cd> = conj <cd||ab>). The digits' relative error
+    ~2^-38 per product puts the residual within 1e-10 of the oracle's."""
+    s, f, fock = _sys(o, v, naux, seed, 0.2, 0.02)
+    V = R.integrals(s.B, o)
+    t1, t2 = inputs.random_amplitudes(o, v, seed + 1, scale=0.1)
+    l1, l2 = inputs.random_amplitudes(o, v, seed + 2, scale=0.1)
+    R1, R2 = L.lagrangian_gradient(f, V, t1, t2, l1, l2)
+    with ccsd.CCSD(o, v, s.eps, B=s.B, fock=fock, precision=ccsd.PREC_SPLIT, split_min_flops=0.0,
+                   vovv_block=vblock) as cc:
+        cc.set_amplitudes(t1, t2)
+        r1, r2 = cc.lambda_residual(l1, l2)
+        again = cc.lambda_residual(l1, l2)
+    assert _maxrel(r1, R1) < 1e-10 and _maxrel(r2, R2) < 1e-10
+    assert np.array_equal(again[0], r1) and np.array_equal(again[1], r2)
+
+
+def test_split_lambda_iterations_track_fp64(ccsd):
+    """Eight Lambda iterations (CUDA graph replay) in split precision against the FP64 ones."""
+    o, v, naux = 5, 17, 30
+    s, f, fock = _sys(o, v, naux, 511, 0.05, 0.0)
+    out = {}
+    for prec in ("fp64", "split"):
+        kw = dict(precision=ccsd.PREC_SPLIT, split_min_flops=0.0) if prec == "split" else {}
+        with ccsd.CCSD(o, v, s.eps, B=s.B, tol=0.0, **kw) as cc:
+            cc.iterate(10)
+            st, it, nrm = cc.lambda_iterate(8)
+            out[prec] = cc.get_lambda()
+        assert it == 8
+    d = max(np.max(np.abs(out["split"][0] - out["fp64"][0])), np.max(np.abs(out["split"][1] - out["fp64"][1])))
+    assert d < 1e-9
+
+
 def test_lambda_converges_to_the_oracle(ccsd):
     o, v, naux = 4, 10, 24
     s, f, fock = _sys(o, v, naux, 505, 0.05, 0.0)
