@@ -148,6 +148,9 @@ typedef struct {
   double diverge_factor; /* growth check factor (default 1e3) */
   int vovv_block;      /* rows a of <ak||cd> unpacked at a time for the H^{ak}_{ci} term and its Lambda
                           adjoint (default 0 = as many as fit about 1 GB) */
+  double permute_cache_limit; /* integral blocks of up to this many bytes keep a copy in each other
+                                 layout a contraction reads; larger ones are permuted at each use
+                                 (default 0 = 2 GiB; < 0: none is kept) */
 } ccsd_opts;
 
 /* Fill opts with the defaults listed above. */

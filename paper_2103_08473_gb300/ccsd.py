@@ -35,7 +35,7 @@ class ccsd_opts(C.Structure):
                 ("split_min_flops", C.c_double), ("df_block", C.c_int), ("autotune", C.c_int),
                 ("digit_bits", C.c_int), ("complex_4m", C.c_int), ("split_budget", C.c_double),
                 ("method", C.c_int), ("accelerator", C.c_int), ("diverge_iters", C.c_int),
-                ("diverge_factor", C.c_double), ("vovv_block", C.c_int)]
+                ("diverge_factor", C.c_double), ("vovv_block", C.c_int), ("permute_cache_limit", C.c_double)]
 
 
 class CCSDError(RuntimeError):

@@ -69,6 +69,10 @@ struct ccsd_ctx {
   int64_t split_budget = int64_t(4) << 30;  // digit bytes of both operands per split call
   int* split_err = nullptr;  // set by the tensor-core kernel if a bounded wait gave up
   SliceSet Wsl, tausl;       // <ab||cd> digits (built once) and tau digits (per evaluation)
+  // split mode, when they fit: digits of the unpacked <ak||cd> rows (a,k,c) over K = d, one set
+  // per block of a, cut once; the H^{ak}_{ci} t1 term then slices only t1 per evaluation
+  std::vector<SliceSet> vovv_sl;
+  uint8_t* t1sl_mem = nullptr;
   void* tausl_mem = nullptr; // tau digits of the on-the-fly ladder (kept across its blocks)
   // store_w = 0: B^Q over virtuals, and per-block (ac|bd) and packed <ab||cd> rows
   z *Bvv = nullptr, *Dblk = nullptr, *Wblk = nullptr;
@@ -668,10 +672,13 @@ cudaError_t split_gemm_chunked(ccsd_ctx* ctx, const ZGemmArgs& g, cudaStream_t s
 // The residual plan: Appendix A, one contraction per printed term.
 // Labels i,j,k,l run over occupied and a,b,c,d over virtual spinors.
 // ---------------------------------------------------------------------------
-// Constant operands (integral blocks) of up to this size keep a permuted copy for the plan; larger
-// ones (oovv from o60/v400 on: 9.2 GB) are permuted into the plan's scratch at each use, one more
-// HBM pass per use instead of a resident copy.
-constexpr int64_t kCacheLimitBytes = int64_t(2) << 30;
+// Constant operands (integral blocks) of up to this size keep a permuted copy for the plan
+// (opts.permute_cache_limit, default 2 GiB); larger ones (oovv from o60/v400 on: 9.2 GB) are
+// permuted into the plan's scratch at each use, one more HBM pass per use instead of a resident copy.
+int64_t cache_limit_bytes(const ccsd_opts& o) {
+  if (o.permute_cache_limit < 0.0) return -1;
+  return o.permute_cache_limit > 0.0 ? (int64_t)o.permute_cache_limit : int64_t(2) << 30;
+}
 
 // The GEMM back end of a plan: split precision where ctx->routes_split says so, else the FP64 DMMA
 // kernel with the context's split-K workspace.
@@ -709,7 +716,7 @@ ccsd_status build_residual_plan(ccsd_ctx* ctx) {
                        : std::max<int64_t>(1, std::min<int64_t>(v, (int64_t)(1.0e9 / (16.0 * o * (double)v * v))));
   if (!cc2) CS(dalloc(ctx, &ctx->vblk, ctx->vblk_rows * o * (int64_t)v * v));
   Plan* P = new Plan(o, v, &ctx->scratch, ctx->stream);
-  P->set_cache_limit(kCacheLimitBytes);
+  P->set_cache_limit(cache_limit_bytes(ctx->opts));
   ctx->plan = P;
   // In split mode a single GEMM of at least split_min_flops goes to the tensor-core digit
   // path when its modelled time beats the FP64 path (measured on this chip: 1.3e12 of the
@@ -764,6 +771,47 @@ ccsd_status build_residual_plan(ccsd_ctx* ctx) {
         P->note_gemm(g);
       }
       z *vpk = ctx->vovv_pk, *vblk = ctx->vblk, *hr = ctx->Hr;
+      const int64_t nblk = (v + vb - 1) / vb;
+      bool cached = false;
+      if (ctx->use_split) {
+        // <ak||cd> is constant: cut the digits of its unpacked rows once, block by block, when
+        // they take at most a tenth of the free device memory (and 16 GB)
+        int64_t total = slice_bytes(o, v, ctx->split);
+        for (int64_t a0 = 0; a0 < v; a0 += vb) total += slice_bytes(std::min<int64_t>(vb, v - a0) * o * v, v, ctx->split);
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+          cudaGetLastError();
+          fr = 0;
+        }
+        if (total <= std::min<int64_t>(int64_t(16) << 30, (int64_t)(fr / 10))) {
+          ctx->vovv_sl.resize(nblk);
+          for (int64_t b = 0; b < nblk; ++b) {
+            const int64_t a0 = b * vb, na = std::min<int64_t>(vb, v - a0);
+            uint8_t* m = nullptr;
+            CS(dalloc(ctx, &m, slice_bytes(na * o * v, v, ctx->split)));
+            UnpackArgs u;  // vblk[(a - a0, k)][c][d] = <ak||cd>
+            u.in = vpk + a0 * o * Pv_;
+            u.out = vblk;
+            u.n1 = na * o;
+            u.n2 = v;
+            u.beta = 0.0;
+            CK(unpack_pairs(u, ctx->stream));
+            CK(make_slices(vblk, na * o * v, v, v, 0, 0, ctx->split, ctx->vovv_sl[b], m, ctx->stream));
+          }
+          CS(dalloc(ctx, &ctx->t1sl_mem, slice_bytes(o, v, ctx->split)));
+          cached = true;
+        }
+      }
+      if (cached) {
+        P->custom("Hvoov:gemm", [ctx, o, v, vb, nblk, hr, t1](cudaStream_t s) {
+          SliceSet ST;  // Hr[i][(a,k,c)] = sum_d t1[i][d] <ak||cd>, block by block of a
+          cudaError_t e = make_slices(t1, o, v, v, 0, 0, ctx->split, ST, ctx->t1sl_mem, s);
+          for (int64_t b = 0; b < nblk && e == cudaSuccess; ++b)
+            e = split_gemm(ST, ctx->vovv_sl[b], hr + b * vb * o * v, (int64_t)v * o * v, zmake(1, 0), zmake(0, 0),
+                           ctx->split_err, nullptr, 0, s);
+          return e;
+        }, 8.0 * o * (double)v * o * v * v);
+      } else {
       P->custom("Hvoov:gemm", [ctx, o, v, vb, Pv_, vpk, vblk, hr, t1](cudaStream_t s) {
         const GemmFn& gemm = ctx->plan->gemm_fn();
         cudaError_t e = cudaSuccess;
@@ -792,6 +840,7 @@ ccsd_status build_residual_plan(ccsd_ctx* ctx) {
         }
         return e;
       }, 8.0 * o * (double)v * o * v * v);
+      }
     }
     // G^a_c = H^a_c + sum_kd V^{ak}_{cd} t^d_k - sum_k F^k_c t^a_k; the middle term is the trace
     // sum_k T[k][a][k][c] of the product above
@@ -1653,7 +1702,7 @@ ccsd_status build_lambda_plan(ccsd_ctx* ctx) {
   }
   // the context takes the plan only once it is complete (a failed build leaves no plan behind)
   std::unique_ptr<Plan, PlanDeleter> holder(new Plan(o, v, &ctx->lscratch, ctx->stream));
-  holder->set_cache_limit(kCacheLimitBytes);
+  holder->set_cache_limit(cache_limit_bytes(ctx->opts));
   Plan* P = holder.get();
   set_plan_gemm(ctx, P);
   const z one = zmake(1, 0), mone = zmake(-1, 0), half = zmake(0.5, 0), quarter = zmake(0.25, 0),
@@ -2154,6 +2203,7 @@ void ccsd_default_opts(ccsd_opts* o) {
   o->diverge_iters = 8;
   o->diverge_factor = 1e3;
   o->vovv_block = 0;
+  o->permute_cache_limit = 0.0;
 }
 
 int ccsd_divergence_index(const double* norms, int count, int iters, double factor) {

@@ -34,19 +34,42 @@ __global__ void zgemv_rowmajor_kernel(int64_t R, int64_t K, z alpha, const z* __
   }
 }
 
-__global__ void zgemv_colmajor_kernel(int64_t R, int64_t K, z alpha, const z* __restrict__ M, int64_t ld, int conjM,
-                                      const z* __restrict__ x, int conjx, double beta, z* __restrict__ y) {
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
+// Column-major matrix: 32 consecutive outputs per block (one per lane, coalesced loads along a
+// row of M), the K range shared by the block's 32 warps (warp w takes k = w, w + 32, ...); the
+// warps' partial sums are added in shared memory in warp order, so the result is reproducible.
+constexpr int kColWarps = 32;
+__global__ void __launch_bounds__(32 * kColWarps) zgemv_colmajor_kernel(int64_t R, int64_t K, z alpha,
+                                                                       const z* __restrict__ M, int64_t ld, int conjM,
+                                                                       const z* __restrict__ x, int conjx, double beta,
+                                                                       z* __restrict__ y) {
+  __shared__ double part[kColWarps][32][2];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int64_t r0 = (int64_t)blockIdx.x * 32; r0 < R; r0 += (int64_t)gridDim.x * 32) {
+    const int64_t r = r0 + lane;
     double ar = 0.0, ai = 0.0;
-    for (int64_t k = 0; k < K; ++k) {
-      z m = M[k * ld + r], xv = x[k];
-      if (conjM) m.y = -m.y;
-      if (conjx) xv.y = -xv.y;
-      ar += m.x * xv.x - m.y * xv.y;
-      ai += m.x * xv.y + m.y * xv.x;
+    if (r < R) {
+#pragma unroll 4
+      for (int64_t k = w; k < K; k += kColWarps) {
+        z m = M[k * ld + r], xv = x[k];
+        if (conjM) m.y = -m.y;
+        if (conjx) xv.y = -xv.y;
+        ar += m.x * xv.x - m.y * xv.y;
+        ai += m.x * xv.y + m.y * xv.x;
+      }
     }
-    z acc = zmul(alpha, make_double2(ar, ai));
-    y[r] = beta != 0.0 ? make_double2(acc.x + beta * y[r].x, acc.y + beta * y[r].y) : acc;
+    part[w][lane][0] = ar;
+    part[w][lane][1] = ai;
+    __syncthreads();
+    if (w == 0 && r < R) {
+      double sr = 0.0, si = 0.0;
+      for (int q = 0; q < kColWarps; ++q) {
+        sr += part[q][lane][0];
+        si += part[q][lane][1];
+      }
+      z acc = zmul(alpha, make_double2(sr, si));
+      y[r] = beta != 0.0 ? make_double2(acc.x + beta * y[r].x, acc.y + beta * y[r].y) : acc;
+    }
+    __syncthreads();
   }
 }
 
@@ -70,7 +93,7 @@ cudaError_t zgemv(int64_t R, int64_t K, z alpha, const z* M, int64_t ld, int row
   if (rowmajor) {
     zgemv_rowmajor_kernel<<<grid_for(R * 32, 256), 256, 0, s>>>(R, K, alpha, M, ld, conjM, x, conjx, beta, y);
   } else {
-    zgemv_colmajor_kernel<<<grid_for(R, 128), 128, 0, s>>>(R, K, alpha, M, ld, conjM, x, conjx, beta, y);
+    zgemv_colmajor_kernel<<<grid_for(R, 32), 32 * kColWarps, 0, s>>>(R, K, alpha, M, ld, conjM, x, conjx, beta, y);
   }
   return cudaGetLastError();
 }

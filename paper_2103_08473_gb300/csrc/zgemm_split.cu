@@ -1180,8 +1180,11 @@ void plan_ksplit(int64_t tiles, int kblocks, int& ksplits, int& kb_split) {
 }
 
 // Orientation and tile width of the main kernel for C (M x N): the operand whose rows go to
-// the 128-row side, and BN. The least padded tile area wins, each width weighted by its
-// tensor-pipe efficiency (narrower tiles re-read A from shared memory for fewer columns);
+// the 128-row side, and BN. The least padded tile area wins, each width weighted by an
+// efficiency factor. Alone, a narrower tile runs slower (a 4096 x 4096 x 8192 product: 96-wide
+// tiles at 0.77 and 64-wide at 0.61 of the 128-wide rate), but on a short operand it also
+// halves the reads of the long one: the o20/v120 ladder (190 x 7140 x 7140) is fastest on
+// swapped 96-wide tiles, 0.70 of the time of 128-wide ones; the factors keep that choice;
 // a change from 128-wide tiles without swap must gain more than 3%. A short M (few pair
 // rows, e.g. the occupied pairs of the ladder) then swaps to the BN side.
 struct MainTiling {

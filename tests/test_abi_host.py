@@ -52,7 +52,7 @@ def test_default_opts(lib):
     assert o.split_min_flops == 1e8 and o.precision == 0
     assert o.slices == 0 and o.digit_bits == 0 and o.complex_4m == 0 and o.method == ccsd.METHOD_CCSD
     assert o.accelerator == ccsd.ACCEL_DIIS and o.diverge_iters == 8 and o.diverge_factor == 1e3
-    assert o.vovv_block == 0
+    assert o.vovv_block == 0 and o.permute_cache_limit == 0.0
 
 
 def _create(lib, o, v, eps, B, naux, opts=None):

@@ -228,6 +228,29 @@ def test_degenerate_shapes_match_oracle(ccsd, o, v, precision):
         assert abs(cc.energy() - ref["energy"]) < 1e-9
 
 
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+def test_integral_blocks_permuted_at_each_use_match_oracle(ccsd, precision):
+    """permute_cache_limit < 0: no permuted copy of any integral block is kept (the path large
+    systems take for blocks over 2 GiB); each contraction permutes them into the plan's scratch.
+    Residual, three iterations and the energy still follow the oracle, and the context holds
+    no cached copies."""
+    o, v, naux = 5, 14, 30
+    s, f, fock = _sys(o, v, naux, 134, 0.2, 0.05)
+    V = R.integrals(s.B, o)
+    t1, t2 = inputs.random_amplitudes(o, v, 135, scale=0.1)
+    S1, S2 = R.residual(f, V, t1, t2)
+    kw = dict(precision=ccsd.PREC_SPLIT, split_min_flops=0.0) if precision == "split" else {}
+    tol = 1e-10 if precision == "split" else 1e-12
+    with ccsd.CCSD(o, v, s.eps, B=s.B, fock=fock, tol=0.0, permute_cache_limit=-1.0, **kw) as cc:
+        assert cc.query("plan_cached_bytes") == 0.0
+        r1, r2 = cc.residual(t1, t2)
+        st, it, nrm = cc.iterate(3)
+        e = cc.energy()
+    assert _maxrel(r1, S1) < tol and _maxrel(r2, S2) < tol
+    ref = R.solve(f, V, o, v, max_iter=3, tol=0.0)
+    assert it == 3 and abs(e - ref["energy"]) < (1e-9 if precision == "split" else 1e-11)
+
+
 @pytest.mark.parametrize("o,v,naux,seed", [(3, 5, 7, 131), (5, 14, 30, 132), (6, 21, 40, 133)])
 def test_ccd_residual_is_the_doubles_residual_at_zero_singles(ccsd, o, v, naux, seed):
     """The CCD plan (no t1 terms, no C^{kb}_{ij}, no singles): at random amplitudes with a nonzero
