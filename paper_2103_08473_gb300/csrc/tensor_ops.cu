@@ -271,46 +271,56 @@ __device__ double block_reduce_max(double x, double* sh) {
   return r;
 }
 
+// One update element: d = S/D (one FP64 reciprocal for both parts), t += d, S = d; returns |d|^2.
+// The max-abs norm is taken on |d|^2 (one square root per block, not per element).
+__device__ __forceinline__ double update_one(z* __restrict__ t, z* __restrict__ S, double D) {
+  const double inv = 1.0 / D;
+  z d = *S;
+  d.x *= inv;
+  d.y *= inv;
+  *t = zadd(*t, d);
+  *S = d;
+  return d.x * d.x + d.y * d.y;
+}
+
+// Index arithmetic in I (32-bit when every index fits: the 64-bit divisions cost more than the
+// update itself on this chip's integer pipes).
+template <typename I>
+__device__ __forceinline__ void denom_update_range(z* __restrict__ t1, z* __restrict__ t2, z* __restrict__ S1,
+                                                   z* __restrict__ S2, const double* __restrict__ e, I o, I v,
+                                                   double shift, double& mx2, double& s2) {
+  const I n1 = o * v, n2 = o * o * v * v, vv = v * v;
+  for (I k = (I)(blockIdx.x * blockDim.x + threadIdx.x); k < n1 + n2; k += (I)(gridDim.x * blockDim.x)) {
+    double m2;
+    if (k < n1) {
+      const I a = k % v, i = k / v;
+      m2 = update_one(t1 + k, S1 + k, e[i] - (e[o + a] + shift));
+      s2 += m2;
+    } else {
+      const I q = k - n1;
+      const I ab = q % vv, ij = q / vv;
+      const I b = ab % v, a = ab / v, j = ij % o, i = ij / o;
+      m2 = update_one(t2 + q, S2 + q, e[i] + e[j] - (e[o + a] + shift) - (e[o + b] + shift));
+      if (i < j && a < b) s2 += m2;
+    }
+    mx2 = (m2 > mx2 || m2 != m2) ? m2 : mx2;  // NaN wins
+  }
+}
+
 __global__ void denom_update_kernel(z* __restrict__ t1, z* __restrict__ t2, z* __restrict__ S1,
                                     z* __restrict__ S2, const double* __restrict__ e, int o, int v, double shift,
                                     double* partials) {
   __shared__ double sh[32];
-  const int64_t n1 = (int64_t)o * v, n2 = (int64_t)o * o * v * v;
-  double mx = 0.0, s2 = 0.0;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n1 + n2;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    if (k < n1) {
-      const int a = (int)(k % v), i = (int)(k / v);
-      const double D = e[i] - (e[o + a] + shift);
-      z d = S1[k];
-      d.x /= D;
-      d.y /= D;
-      t1[k] = zadd(t1[k], d);
-      S1[k] = d;
-      const double m2 = d.x * d.x + d.y * d.y;
-      const double am = sqrt(m2);
-      mx = (am > mx || am != am) ? am : mx;
-      s2 += m2;
-    } else {
-      const int64_t q = k - n1;
-      const int b = (int)(q % v), a = (int)((q / v) % v);
-      const int j = (int)((q / ((int64_t)v * v)) % o), i = (int)(q / ((int64_t)v * v * o));
-      const double D = e[i] + e[j] - (e[o + a] + shift) - (e[o + b] + shift);
-      z d = S2[q];
-      d.x /= D;
-      d.y /= D;
-      t2[q] = zadd(t2[q], d);
-      S2[q] = d;
-      const double m2 = d.x * d.x + d.y * d.y;
-      const double am = sqrt(m2);
-      mx = (am > mx || am != am) ? am : mx;
-      if (i < j && a < b) s2 += m2;
-    }
-  }
-  const double bm = block_reduce_max(mx, sh);
+  const int64_t n = (int64_t)o * v + (int64_t)o * o * v * v;
+  double mx2 = 0.0, s2 = 0.0;
+  if (n + (int64_t)gridDim.x * blockDim.x < ((int64_t)1 << 31))
+    denom_update_range<int>(t1, t2, S1, S2, e, o, v, shift, mx2, s2);
+  else
+    denom_update_range<int64_t>(t1, t2, S1, S2, e, o, v, shift, mx2, s2);
+  const double bm = block_reduce_max(mx2, sh);
   const double bs = block_reduce_sum(s2, sh);
   if (threadIdx.x == 0) {
-    partials[2 * blockIdx.x] = bm;
+    partials[2 * blockIdx.x] = sqrt(bm);  // max |d| of the block
     partials[2 * blockIdx.x + 1] = bs;
   }
 }
