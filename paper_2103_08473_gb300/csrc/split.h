@@ -28,8 +28,9 @@ namespace ccsd {
 
 enum SplitKind { kSplitE4M3 = 0, kSplitBF16 = 1 };
 
-// Digit slices of one operand, laid out for TMA: rows (p*2 + part) * rows_pad + r,
-// columns k in [0, Kp) (zero padded), one byte (e4m3) or two bytes (bf16) per digit.
+// Digit slices of one operand, laid out for TMA: planes p*2 + part (real, imaginary) of
+// rows_pad rows each (rows rounded up to 32, the padding rows zero), columns k in [0, Kp)
+// (zero padded), one byte (e4m3) or two bytes (bf16) per digit.
 struct SliceSet {
   void* digits = nullptr;   // device
   double* scale = nullptr;  // device, 2^e per row (rows entries)
@@ -37,7 +38,7 @@ struct SliceSet {
   int s = 0, b = 0, kind = kSplitE4M3;
   int64_t chunk = 0, nchunks = 1;  // K chunking of the slicing work (rows with K contiguous)
   int64_t row0 = 0;                // a row view: its first row within the digit set
-  CUtensorMap tmap;  // 2D map over the digit array, box {128 bytes, 128 rows}, 128B swizzle
+  CUtensorMap tmap;  // 3D map (K, row, plane), box {128 bytes, 128 rows, 1 plane}, 128B swizzle
   bool have_map = false;
 };
 

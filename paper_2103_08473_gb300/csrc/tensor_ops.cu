@@ -271,10 +271,23 @@ __device__ double block_reduce_max(double x, double* sh) {
   return r;
 }
 
-// One update element: d = S/D (one FP64 reciprocal for both parts), t += d, S = d; returns |d|^2.
+// 1/D by Newton's iteration for the reciprocal, r <- r + r (1 - D r), from the correctly rounded
+// FP32 reciprocal: each step squares the relative error (2^-24 -> ~2^-48 -> within an ulp of
+// FP64), for four FMAs on this chip's narrow FP64 pipe. Outside FP32's range (and for zero,
+// infinite or NaN D) the IEEE quotient.
+__device__ __forceinline__ double recip_newton(double D) {
+  const float f = __frcp_rn((float)D);
+  if (!(fabsf(f) > 0.0f && fabsf(f) < INFINITY)) return 1.0 / D;
+  double r = (double)f;
+  r = fma(r, fma(-D, r, 1.0), r);
+  r = fma(r, fma(-D, r, 1.0), r);
+  return r;
+}
+
+// One update element: d = S/D (one reciprocal for both parts), t += d, S = d; returns |d|^2.
 // The max-abs norm is taken on |d|^2 (one square root per block, not per element).
 __device__ __forceinline__ double update_one(z* __restrict__ t, z* __restrict__ S, double D) {
-  const double inv = 1.0 / D;
+  const double inv = recip_newton(D);
   z d = *S;
   d.x *= inv;
   d.y *= inv;
@@ -283,41 +296,58 @@ __device__ __forceinline__ double update_one(z* __restrict__ t, z* __restrict__ 
   return d.x * d.x + d.y * d.y;
 }
 
-// Index arithmetic in I (32-bit when every index fits: the 64-bit divisions cost more than the
-// update itself on this chip's integer pipes).
-template <typename I>
-__device__ __forceinline__ void denom_update_range(z* __restrict__ t1, z* __restrict__ t2, z* __restrict__ S1,
-                                                   z* __restrict__ S2, const double* __restrict__ e, I o, I v,
-                                                   double shift, double& mx2, double& s2) {
-  const I n1 = o * v, n2 = o * o * v * v, vv = v * v;
-  for (I k = (I)(blockIdx.x * blockDim.x + threadIdx.x); k < n1 + n2; k += (I)(gridDim.x * blockDim.x)) {
-    double m2;
-    if (k < n1) {
-      const I a = k % v, i = k / v;
-      m2 = update_one(t1 + k, S1 + k, e[i] - (e[o + a] + shift));
-      s2 += m2;
-    } else {
-      const I q = k - n1;
-      const I ab = q % vv, ij = q / vv;
-      const I b = ab % v, a = ab / v, j = ij % o, i = ij / o;
-      m2 = update_one(t2 + q, S2 + q, e[i] + e[j] - (e[o + a] + shift) - (e[o + b] + shift));
-      if (i < j && a < b) s2 += m2;
-    }
-    mx2 = (m2 > mx2 || m2 != m2) ? m2 : mx2;  // NaN wins
-  }
+// The largest |d|^2 as an integer max over the bit patterns (|d|^2 >= 0, and a NaN, sign
+// cleared, orders above infinity), off the FP64 pipe.
+__device__ __forceinline__ void max_bits(unsigned long long& mx, double m2) {
+  mx = max(mx, (unsigned long long)__double_as_longlong(m2) & 0x7FFFFFFFFFFFFFFFull);
 }
 
+// Work items are (row, chunk): rows 0..o-1 are t1's rows i (v elements, D = e_i - e_a - shift),
+// rows o.. are t2's pair rows ij (v^2 elements, D = e_i + e_j - e_a - e_b - 2 shift), each cut
+// into nc chunks. A row's e_i + e_j is formed once; the shifted virtual energies sit in shared
+// memory (SH) or are formed per element.
+template <bool SH>
 __global__ void denom_update_kernel(z* __restrict__ t1, z* __restrict__ t2, z* __restrict__ S1,
                                     z* __restrict__ S2, const double* __restrict__ e, int o, int v, double shift,
-                                    double* partials) {
+                                    int nc, double* partials) {
+  extern __shared__ double es_sh[];
   __shared__ double sh[32];
-  const int64_t n = (int64_t)o * v + (int64_t)o * o * v * v;
-  double mx2 = 0.0, s2 = 0.0;
-  if (n + (int64_t)gridDim.x * blockDim.x < ((int64_t)1 << 31))
-    denom_update_range<int>(t1, t2, S1, S2, e, o, v, shift, mx2, s2);
-  else
-    denom_update_range<int64_t>(t1, t2, S1, S2, e, o, v, shift, mx2, s2);
-  const double bm = block_reduce_max(mx2, sh);
+  if (SH) {
+    for (int a = threadIdx.x; a < v; a += blockDim.x) es_sh[a] = e[o + a] + shift;
+    __syncthreads();
+  }
+  auto es = [&](int a) { return SH ? es_sh[a] : e[o + a] + shift; };
+  const int vv = v * v;
+  const int64_t items = (int64_t)(o + o * o) * nc;
+  double s2 = 0.0;
+  unsigned long long mx = 0;
+  for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+    const int row = (int)(it / nc), c = (int)(it % nc);
+    if (row < o) {
+      const int chunk = (v + nc - 1) / nc, lo = c * chunk, hi = min(v, lo + chunk);
+      const double ei = e[row];
+      z* tr = t1 + (int64_t)row * v;
+      z* sr = S1 + (int64_t)row * v;
+      for (int a = lo + threadIdx.x; a < hi; a += blockDim.x) {
+        const double m2 = update_one(tr + a, sr + a, ei - es(a));
+        s2 += m2;
+        max_bits(mx, m2);
+      }
+    } else {
+      const int ij = row - o, i = ij / o, j = ij - i * o;
+      const int chunk = (vv + nc - 1) / nc, lo = c * chunk, hi = min(vv, lo + chunk);
+      const double eij = e[i] + e[j];
+      z* tr = t2 + (int64_t)ij * vv;
+      z* sr = S2 + (int64_t)ij * vv;
+      for (int ab = lo + threadIdx.x; ab < hi; ab += blockDim.x) {
+        const int a = ab / v, b = ab - a * v;
+        const double m2 = update_one(tr + ab, sr + ab, eij - (es(a) + es(b)));
+        if (i < j && a < b) s2 += m2;
+        max_bits(mx, m2);
+      }
+    }
+  }
+  const double bm = block_reduce_max(__longlong_as_double((long long)mx), sh);
   const double bs = block_reduce_sum(s2, sh);
   if (threadIdx.x == 0) {
     partials[2 * blockIdx.x] = sqrt(bm);  // max |d| of the block
@@ -670,7 +700,16 @@ int update_blocks() { return kUpdateBlocks; }
 
 cudaError_t denom_update(z* t1, z* t2, z* S1, z* S2, const double* e, int o, int v, double shift,
                          double* partials, cudaStream_t s) {
-  denom_update_kernel<<<kUpdateBlocks, kThreads, 0, s>>>(t1, t2, S1, S2, e, o, v, shift, partials);
+  if (o < 0 || v < 0 || (int64_t)v * v > 0x7fffffff || (int64_t)o * o > 0x7fffffff) return cudaErrorInvalidValue;
+  // chunks per row: enough items for two per block, each at least one pass of the block
+  const int64_t rows = (int64_t)o + (int64_t)o * o, vv = (int64_t)v * v;
+  const int nc =
+      rows > 0 ? (int)std::max<int64_t>(1, std::min<int64_t>((2 * kUpdateBlocks + rows - 1) / rows, vv / kThreads)) : 1;
+  const size_t smem = (size_t)v * sizeof(double);
+  if (smem <= 32768)
+    denom_update_kernel<true><<<kUpdateBlocks, kThreads, smem, s>>>(t1, t2, S1, S2, e, o, v, shift, nc, partials);
+  else
+    denom_update_kernel<false><<<kUpdateBlocks, kThreads, 0, s>>>(t1, t2, S1, S2, e, o, v, shift, nc, partials);
   return cudaGetLastError();
 }
 

@@ -58,7 +58,7 @@ struct MainTile {
 // intersected with this CTA's K range [klo, khi); the pairs of a level are
 // (p, L - p), p = max(0, L - s + 1) .. min(L, s - 1).
 struct SplitArgs {
-  int64_t M, N, Mp, Np;
+  int64_t M, N;
   int64_t a_row0, b_row0;   // first digit row of each operand (row views of a larger digit set)
   int tiles_m, tiles;       // output tiles along M, and in total
   int s, b, lmax, kblocks;  // digits, bits, last level, K blocks
@@ -112,11 +112,14 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long lo
   return true;
 }
 
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+// One box of digits: K offset x (a multiple of the 128-byte row segment), row y, plane z
+// (digit p's real part at z = 2p, imaginary at 2p + 1). Rows past the set read as zeros.
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z,
+                                            uint32_t bar) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          dst),
-      "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+          "r"(dst),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(bar)
       : "memory");
 }
 
@@ -272,10 +275,10 @@ __global__ void __launch_bounds__(192, 1)
               const int x = kb * BKE;
               mbar_expect_tx(full(st), PROBE ? kTileA + kTileB : 2 * (kTileA + kTileB));
               const int64_t ya = args.a_row0 + m0, yb = args.b_row0 + n0;
-              tma_load_2d(sa, &tmA, x, (int)((p * 2 + 0) * args.Mp + ya), full(st));
-              if (!PROBE) tma_load_2d(sa + kTileA, &tmA, x, (int)((p * 2 + 1) * args.Mp + ya), full(st));
-              tma_load_2d(sa + 2 * kTileA, &tmB, x, (int)((q * 2 + 0) * args.Np + yb), full(st));
-              if (!PROBE) tma_load_2d(sa + 2 * kTileA + kTileB, &tmB, x, (int)((q * 2 + 1) * args.Np + yb), full(st));
+              tma_load_3d(sa, &tmA, x, (int)ya, p * 2 + 0, full(st));
+              if (!PROBE) tma_load_3d(sa + kTileA, &tmA, x, (int)ya, p * 2 + 1, full(st));
+              tma_load_3d(sa + 2 * kTileA, &tmB, x, (int)yb, q * 2 + 0, full(st));
+              if (!PROBE) tma_load_3d(sa + 2 * kTileA + kTileB, &tmB, x, (int)yb, q * 2 + 1, full(st));
             }
         }
       if (!ok) {
@@ -535,7 +538,7 @@ __host__ __device__ constexpr uint32_t make_idesc_n32(int kind, int negB) {
 __device__ __forceinline__ int plane_at(int i, int s) { return (i & 1) ? s - 1 - (i >> 1) : (i >> 1); }
 
 struct SmallKArgs {
-  int64_t M, N, Mp, Np, a_row0, b_row0;
+  int64_t M, N, a_row0, b_row0;
   int tiles_m, tiles;
   int s, b, lmax, kblocks;
   z* C;
@@ -636,8 +639,7 @@ __global__ void __launch_bounds__(192, 1)
             mbar_expect_tx(bfull(bs), (uint32_t)S * 2u * kSkTileB);
             for (int q = 0; q < S; ++q)
               for (int r = 0; r < 2; ++r)
-                tma_load_2d(dst + (uint32_t)(q * 2 + r) * kSkTileB, &tmB, x, (int)((q * 2 + r) * args.Np + yb),
-                            bfull(bs));
+                tma_load_3d(dst + (uint32_t)(q * 2 + r) * kSkTileB, &tmB, x, (int)yb, q * 2 + r, bfull(bs));
           }
           for (int pi = 0; pi < S; ++pi, ++ja) {
             const int p = plane_at(pi, S);
@@ -648,8 +650,8 @@ __global__ void __launch_bounds__(192, 1)
             }
             const uint32_t dst = abase + as * kSkAStage;
             mbar_expect_tx(afull(as), kSkAStage);
-            tma_load_2d(dst, &tmA, x, (int)((p * 2 + 0) * args.Mp + ya), afull(as));
-            tma_load_2d(dst + kSkTileA, &tmA, x, (int)((p * 2 + 1) * args.Mp + ya), afull(as));
+            tma_load_3d(dst, &tmA, x, (int)ya, p * 2 + 0, afull(as));
+            tma_load_3d(dst + kSkTileA, &tmA, x, (int)ya, p * 2 + 1, afull(as));
           }
         }
       }
@@ -1071,35 +1073,31 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 int esize(int kind) { return kind == kSplitBF16 ? 2 : 1; }
 int bke(int kind) { return kind == kSplitBF16 ? 64 : 128; }
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+// Rows of each digit plane are padded to whole 32-row blocks of the transposing slicer (tiles
+// past them are zero filled by the tensor map).
+constexpr int64_t kRowPad = 32;
 
-cudaError_t encode_map(SliceSet& S) {
-  auto enc = get_encode();
-  if (!enc) return cudaErrorNotSupported;
-  const int es = esize(S.kind);
-  cuuint64_t dims[2] = {(cuuint64_t)S.Kp, (cuuint64_t)(S.s * 2 * S.rows_pad)};
-  cuuint64_t strides[1] = {(cuuint64_t)(S.Kp * es)};
-  cuuint32_t box[2] = {(cuuint32_t)(128 / es), 128u};
-  cuuint32_t estr[2] = {1u, 1u};
-  CUresult r = enc(&S.tmap, S.kind == kSplitBF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
-                   S.digits, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  S.have_map = (r == CUDA_SUCCESS);
-  return S.have_map ? cudaSuccess : cudaErrorInvalidValue;
-}
-
-// The same map over the digit array with a box of box_rows rows.
+// 3-D map over the digit array: K (128-byte segments of the box), rows, planes. A box of
+// box_rows rows that runs past the rows of a plane is zero filled without reading memory, so a
+// short operand (e.g. 20 occupied rows under a 128-row tile) costs only its own rows.
 cudaError_t encode_map_rows(const SliceSet& S, uint32_t box_rows, CUtensorMap* out) {
   auto enc = get_encode();
   if (!enc) return cudaErrorNotSupported;
   const int es = esize(S.kind);
-  cuuint64_t dims[2] = {(cuuint64_t)S.Kp, (cuuint64_t)(S.s * 2 * S.rows_pad)};
-  cuuint64_t strides[1] = {(cuuint64_t)(S.Kp * es)};
-  cuuint32_t box[2] = {(cuuint32_t)(128 / es), box_rows};
-  cuuint32_t estr[2] = {1u, 1u};
-  CUresult r = enc(out, S.kind == kSplitBF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+  cuuint64_t dims[3] = {(cuuint64_t)S.Kp, (cuuint64_t)S.rows_pad, (cuuint64_t)(S.s * 2)};
+  cuuint64_t strides[2] = {(cuuint64_t)(S.Kp * es), (cuuint64_t)(S.rows_pad * S.Kp * es)};
+  cuuint32_t box[3] = {(cuuint32_t)(128 / es), box_rows, 1u};
+  cuuint32_t estr[3] = {1u, 1u, 1u};
+  CUresult r = enc(out, S.kind == kSplitBF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 3,
                    S.digits, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// The set's own map, box {128 bytes, 128 rows, 1 plane}.
+cudaError_t encode_map(SliceSet& S) {
+  S.have_map = encode_map_rows(S, 128u, &S.tmap) == cudaSuccess;
+  return S.have_map ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 int num_sms() {
@@ -1156,7 +1154,10 @@ bool smallk_eligible(const SplitArgs& a) {
 // whole waves (CTAs / (waves x SMs)) is taken where it beats the smaller factors by more
 // than 5%. Each split keeps >= kMinKbPerSplit K blocks so that a level group's MMA work
 // stays above its FP64 flush in the epilogue.
-constexpr int kMinKbPerSplit = 12;
+#ifndef SPLIT_MIN_KB_PER_SPLIT
+#define SPLIT_MIN_KB_PER_SPLIT 12
+#endif
+constexpr int kMinKbPerSplit = SPLIT_MIN_KB_PER_SPLIT;
 void plan_ksplit(int64_t tiles, int kblocks, int& ksplits, int& kb_split) {
   ksplits = 1;
   const int64_t sms = num_sms();
@@ -1290,8 +1291,6 @@ cudaError_t split_gemm_smallk(const SliceSet& A, const SliceSet& B, const SplitA
   k.conjB = swap ? 0 : conjB;
   k.M = KA.rows;
   k.N = KB.rows;
-  k.Mp = KA.rows_pad;
-  k.Np = KB.rows_pad;
   k.a_row0 = KA.row0;
   k.b_row0 = KB.row0;
   const int64_t tm = (k.M + 127) / 128, tn = (k.N + kSkBN - 1) / kSkBN;
@@ -1323,7 +1322,7 @@ cudaError_t split_gemm_smallk(const SliceSet& A, const SliceSet& B, const SplitA
 }  // namespace
 
 int64_t slice_bytes(int64_t rows, int64_t K, const SplitConfig& cfg) {
-  const int64_t rows_pad = round_up(std::max<int64_t>(rows, 1), 128);
+  const int64_t rows_pad = round_up(std::max<int64_t>(rows, 1), kRowPad);
   const int64_t Kp = round_up(std::max<int64_t>(K, 1), bke(cfg.kind));
   // digits, then per-row scale and inverse scale (doubles) and exponent (int)
   return round_up((int64_t)cfg.s * 2 * rows_pad * Kp * esize(cfg.kind), 1024) + 3 * round_up(rows_pad * 8, 1024);
@@ -1334,7 +1333,7 @@ cudaError_t make_slices(const z* X, int64_t rows, int64_t K, int64_t ld, int tra
   if (cfg.s < 1 || cfg.s > 14 || cfg.b < 1 || cfg.b > split_max_bits(cfg.kind) || cfg.b * cfg.s > 56)
     return cudaErrorInvalidValue;
   out.rows = rows;
-  out.rows_pad = round_up(std::max<int64_t>(rows, 1), 128);
+  out.rows_pad = round_up(std::max<int64_t>(rows, 1), kRowPad);
   out.K = K;
   out.Kp = round_up(std::max<int64_t>(K, 1), bke(cfg.kind));
   out.s = cfg.s;
@@ -1447,8 +1446,6 @@ cudaError_t split_gemm(const SliceSet& A, const SliceSet& B, z* C, int64_t ldc, 
   if (tl.tiles > 0x7fffffff) return cudaErrorInvalidValue;
   a.M = KA.rows;
   a.N = KB.rows;
-  a.Mp = KA.rows_pad;
-  a.Np = KB.rows_pad;
   a.a_row0 = KA.row0;
   a.b_row0 = KB.row0;
   a.tiles_m = (int)tl.tiles_m;
@@ -1522,7 +1519,7 @@ cudaError_t split_probe_raw(int kind, const double* Aint, const double* Bint, in
   for (SliceSet* S : {&A, &B}) {
     const int64_t rows = S == &A ? M : N;
     S->rows = rows;
-    S->rows_pad = round_up(std::max<int64_t>(rows, 1), 128);
+    S->rows_pad = round_up(std::max<int64_t>(rows, 1), kRowPad);
     S->K = K;
     S->Kp = round_up(std::max<int64_t>(K, 1), bke(kind));
     S->s = 1;
@@ -1545,8 +1542,6 @@ cudaError_t split_probe_raw(int kind, const double* Aint, const double* Bint, in
   std::memset(&a, 0, sizeof(a));
   a.M = M;
   a.N = N;
-  a.Mp = A.rows_pad;
-  a.Np = B.rows_pad;
   a.tiles_m = (int)((M + 127) / 128);
   a.tiles = a.tiles_m * (int)((N + 127) / 128);
   a.probe = C;
