@@ -357,6 +357,16 @@ ccsd_status ccsd_split_zgemm(int kind, int bits, int slices, int transA, int con
                              void* workspace, size_t ws_bytes, void* stream);
 
 /*
+ * How ccsd_split_zgemm runs an M x N x K product (a scheduling record, the paper has no
+ * counterpart): out[6] (host) receives 1 for the short-K kernel (else 0), 1 when the
+ * operands are swapped (M on the narrow tile side), the tile width, the CTAs per cluster
+ * (2: two CTAs share the long operand's tile by TMA multicast), the CTAs along K and the
+ * output tiles (the last four 0 for the short-K kernel). Queries the current device's
+ * cluster occupancy; launches nothing. CCSD_ERR_ARG on a bad configuration or NULL.
+ */
+ccsd_status ccsd_split_describe(int kind, int bits, int slices, long long M, long long N, long long K, int* out);
+
+/*
  * Accumulation probe of the split GEMM's tensor-core path: C[m][n] = sum_k A[m][k] B[n][k]
  * (real, row-major, device) for integer-valued A, B that fit the digit type of `kind`
  * (|x| <= 16 for e4m3, <= 256 for bf16), accumulated in one FP32 TMEM accumulator over

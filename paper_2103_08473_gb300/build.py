@@ -49,7 +49,13 @@ def _digest(extra=()) -> str:
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compile and link libccsd.so; return its path."""
+    """Compile and link libccsd.so; return its path.
+
+    Flags in the environment variable CCSD_NVCC_FLAGS (space separated, e.g. the tuning
+    macros -DSPLIT_CLUSTER=0 or -DSPLIT_MIN_KB_PER_SPLIT=8) are added to extra_flags, so
+    that every later build() call of the process keeps them.
+    """
+    extra_flags = tuple(extra_flags) + tuple(os.environ.get("CCSD_NVCC_FLAGS", "").split())
     os.makedirs(BUILD, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
     stamp = os.path.join(BUILD, "stamp")

@@ -75,6 +75,7 @@ SIGNATURES = [
     ("ccsd_split_zgemm", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_longlong,
                                    C.c_longlong, C.c_longlong, ccsd_z, _P, C.c_longlong, _P, C.c_longlong, ccsd_z, _P,
                                    C.c_longlong, _P, C.c_size_t, _P]),
+    ("ccsd_split_describe", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_longlong, C.c_longlong, C.c_longlong, _P]),
     ("ccsd_split_probe", C.c_int, [C.c_int, C.c_longlong, C.c_longlong, C.c_longlong, _P, _P, _P, _P, C.c_size_t,
                                    _P]),
     ("ccsd_split_wait_selftest", C.c_int, [_P]),
@@ -385,6 +386,17 @@ def split_zgemm(a, b, c, alpha=1.0, beta=0.0, transA=False, conjA=False, transB=
     if st != OK:
         raise CCSDError(st, lib.ccsd_last_error(None).decode())
     return c
+
+
+def split_describe(M, N, K, kind=SPLIT_E4M3, bits=5, slices=8):
+    """ccsd_split_describe: how ccsd_split_zgemm runs an M x N x K product, as a dict."""
+    lib = load()
+    out = (C.c_int * 6)()
+    st = lib.ccsd_split_describe(kind, bits, slices, M, N, K, C.cast(out, C.c_void_p))
+    if st != OK:
+        raise CCSDError(st, lib.ccsd_last_error(None).decode())
+    return {"short_k": out[0], "swap": out[1], "tile_n": out[2], "cluster": out[3], "ksplits": out[4],
+            "tiles": out[5]}
 
 
 def split_probe(a, b, kind=SPLIT_E4M3):

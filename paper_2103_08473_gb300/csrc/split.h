@@ -91,6 +91,10 @@ int64_t split_part_bytes(int64_t M, int64_t N, int64_t K, const SplitConfig& cfg
 cudaError_t split_gemm(const SliceSet& A, const SliceSet& B, z* C, int64_t ldc, z alpha, z beta,
                        int* err, void* part_ws, int64_t part_bytes, cudaStream_t s, long long wait_cycles = 0,
                        int stall_loads = 0, int conjB = 0);
+// How split_gemm runs C (M x N) = A B^T over K: out[0] = 1 for the short-K kernel (0 main),
+// out[1] = 1 when the operands are swapped (A's rows on the narrow side), out[2] = the tile
+// width, out[3] = CTAs per cluster (1 or 2), out[4] = CTAs along K, out[5] = output tiles.
+void split_describe(int64_t M, int64_t N, int64_t K, const SplitConfig& cfg, int out[6]);
 // Probe: C (FP64 real, M x N) = A B^T for integer-valued A (M x K) and B (N x K) stored as
 // single digits, summed in one FP32 accumulator over all of K (exactness checks of the
 // tensor-core accumulation). mem: 2 slice sets of one digit each.

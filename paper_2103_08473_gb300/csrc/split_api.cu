@@ -68,6 +68,13 @@ ccsd_status ccsd_split_zgemm(int kind, int bits, int slices, int transA, int con
   return CCSD_OK;
 }
 
+ccsd_status ccsd_split_describe(int kind, int bits, int slices, long long M, long long N, long long K, int* out) {
+  if (!config_ok(kind, bits, slices) || M < 0 || N < 0 || K < 0 || !out)
+    return fail(CCSD_ERR_ARG, "ccsd_split_describe: bad kind/bits/slices, sizes or NULL");
+  split_describe(M, N, K, config(kind, bits, slices), out);
+  return CCSD_OK;
+}
+
 ccsd_status ccsd_split_probe(int kind, long long M, long long N, long long K, const double* A, const double* B,
                              double* C, void* workspace, size_t ws_bytes, void* stream) {
   if (kind != kSplitE4M3 && kind != kSplitBF16) return fail(CCSD_ERR_ARG, "ccsd_split_probe: bad kind");

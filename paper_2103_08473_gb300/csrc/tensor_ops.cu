@@ -40,6 +40,70 @@ __global__ void permute_direct_kernel(PermuteArgs g, int64_t total) {
   }
 }
 
+// Division by a divisor fixed at launch, as a multiply and a shift (Granlund and Montgomery,
+// "Division by invariant integers using multiplication", 1994): with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1, n / d = (umulhi(m, n) + n) >> l for every n < 2^31.
+struct FastDiv {
+  uint32_t d = 1, m = 1, l = 0;
+};
+FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f;
+  f.d = d;
+  while ((1ull << f.l) < d) ++f.l;
+  f.m = (uint32_t)(((1ull << 32) * ((1ull << f.l) - d)) / d + 1);
+  return f;
+}
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) { return (__umulhi(f.m, n) + n) >> f.l; }
+
+// The direct permutation with every element offset below 2^31: 32-bit index arithmetic, each
+// division by a dimension a multiply and a shift, and four elements per thread in flight (all
+// four loads issued before the stores).
+struct PermuteFast {
+  const z* in;
+  z* out;
+  int rank;
+  FastDiv dims[kMaxRank];
+  uint32_t istr[kMaxRank], ostr[kMaxRank];
+  z alpha;
+  double beta;
+  int conj;
+};
+__global__ void __launch_bounds__(256) permute_fast_kernel(PermuteFast g, uint32_t total) {
+  constexpr int U = 4;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t e0 = blockIdx.x * blockDim.x + threadIdx.x; e0 < total; e0 += U * stride) {
+    uint32_t io[U], oo[U];
+    bool live[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint32_t e = e0 + (uint32_t)u * stride;
+      live[u] = e < total;
+      uint32_t r = live[u] ? e : 0u, i = 0, o = 0;
+#pragma unroll
+      for (int d = kMaxRank - 1; d >= 0; --d) {
+        if (d >= g.rank) continue;
+        const uint32_t q = fdiv(r, g.dims[d]);
+        const uint32_t c = r - q * g.dims[d].d;
+        i += c * g.istr[d];
+        o += c * g.ostr[d];
+        r = q;
+      }
+      io[u] = i;
+      oo[u] = o;
+    }
+    z v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (live[u]) v[u] = ld_conj(g.in + io[u], g.conj);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (live[u]) {
+        z* o = g.out + oo[u];
+        *o = g.beta != 0.0 ? zaxpby(g.alpha, v[u], g.beta, *o) : zmul(g.alpha, v[u]);
+      }
+  }
+}
+
 // 32 x 32 shared-memory transpose over output dims (p, q): q is innermost in the
 // output, p is innermost (stride 1) in the input, so both the loads and the
 // stores are coalesced. The remaining dims are walked by blockIdx.y.
@@ -617,18 +681,64 @@ cudaError_t zscale_matrix(const ZGemmArgs& g, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t permute_add(const PermuteArgs& a, cudaStream_t s) {
-  if (a.rank < 1 || a.rank > kMaxRank) return cudaErrorInvalidValue;
-  int64_t total = 1;
-  for (int d = 0; d < a.rank; ++d) total *= a.dims[d];
-  if (total == 0) return cudaSuccess;
+cudaError_t permute_add(const PermuteArgs& a0, cudaStream_t s) {
+  if (a0.rank < 1 || a0.rank > kMaxRank) return cudaErrorInvalidValue;
+  // the same permutation with dims of extent 1 dropped and neighbours that are contiguous in
+  // both the input and the output merged into one
+  PermuteArgs a = a0;
+  a.rank = 0;
+  for (int d = 0; d < a0.rank; ++d) {
+    if (a0.dims[d] == 0) return cudaSuccess;
+    if (a0.dims[d] == 1) continue;
+    if (a.rank > 0) {
+      const int t = a.rank - 1;
+      if (a.istr[t] == a0.dims[d] * a0.istr[d] && a.ostr[t] == a0.dims[d] * a0.ostr[d]) {
+        a.dims[t] *= a0.dims[d];
+        a.istr[t] = a0.istr[d];
+        a.ostr[t] = a0.ostr[d];
+        continue;
+      }
+    }
+    a.dims[a.rank] = a0.dims[d];
+    a.istr[a.rank] = a0.istr[d];
+    a.ostr[a.rank] = a0.ostr[d];
+    ++a.rank;
+  }
+  if (a.rank == 0) {  // a single element
+    a.rank = 1;
+    a.dims[0] = 1;
+    a.istr[0] = a.ostr[0] = 1;
+  }
+  int64_t total = 1, imax = 0, omax = 0;
+  for (int d = 0; d < a.rank; ++d) {
+    total *= a.dims[d];
+    imax += (a.dims[d] - 1) * a.istr[d];
+    omax += (a.dims[d] - 1) * a.ostr[d];
+  }
   const int q = a.rank - 1;
   int p = -1;
   if (a.istr[q] != 1 && a.dims[q] > 1)
     for (int d = 0; d < q; ++d)
       if (a.istr[d] == 1 && a.dims[d] > 1) p = d;
   if (p < 0) {
-    permute_direct_kernel<<<grid_for(total, kThreads), kThreads, 0, s>>>(a, total);
+    constexpr int64_t kLim = (int64_t)1 << 31;
+    if (total < kLim && imax < kLim && omax < kLim) {
+      PermuteFast f;
+      f.in = a.in;
+      f.out = a.out;
+      f.rank = a.rank;
+      for (int d = 0; d < a.rank; ++d) {
+        f.dims[d] = make_fastdiv((uint32_t)a.dims[d]);
+        f.istr[d] = (uint32_t)a.istr[d];
+        f.ostr[d] = (uint32_t)a.ostr[d];
+      }
+      f.alpha = a.alpha;
+      f.beta = a.beta;
+      f.conj = a.conj;
+      permute_fast_kernel<<<grid_for((total + 3) / 4, kThreads), kThreads, 0, s>>>(f, (uint32_t)total);
+    } else {
+      permute_direct_kernel<<<grid_for(total, kThreads), kThreads, 0, s>>>(a, total);
+    }
   } else {
     const int64_t tp = (a.dims[p] + 31) / 32, tq = (a.dims[q] + 31) / 32;
     const int64_t nrest = total / (a.dims[p] * a.dims[q]);

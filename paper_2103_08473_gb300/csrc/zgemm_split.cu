@@ -76,6 +76,7 @@ struct SplitArgs {
   int stall_loads;          // self-test only: the producer issues no loads, so the first wait runs out
   int transC;               // 1: the kernel's (m, n) is the caller's C[n][m] (operands swapped)
   int conjA, conjB;         // conjugate the kernel's A / B operand (the sign of its imaginary digits)
+  int a_stream;             // clusters only: A's tile is read by no other resident cluster (evict first)
 };
 
 // ---- PTX wrappers ----------------------------------------------------------
@@ -121,6 +122,40 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
           "r"(dst),
       "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(bar)
       : "memory");
+}
+
+// The same box written to every CTA of the cluster in cta_mask, at this CTA's shared offset, each
+// destination's mbarrier (same offset) receiving the byte count.
+__device__ __forceinline__ void tma_load_3d_mc(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar,
+                                               uint16_t cta_mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+      " [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(dst),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(bar), "h"(cta_mask)
+      : "memory");
+}
+// As above, with an L2 eviction policy for the copied lines.
+__device__ __forceinline__ void tma_load_3d_mc_hint(uint32_t dst, const CUtensorMap* map, int x, int y, int z,
+                                                    uint32_t bar, uint16_t cta_mask, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster.L2::cache_hint"
+      " [%0], [%1, {%2, %3, %4}], [%5], %6, %7;" ::"r"(dst),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(bar), "h"(cta_mask), "l"(policy)
+      : "memory");
+}
+// Lines read once per pass (a digit stream with no reuse among the resident CTAs) go first.
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release;\nbarrier.cluster.wait.acquire;" ::: "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -187,6 +222,13 @@ __device__ __forceinline__ void umma(uint32_t d, uint64_t a, uint64_t b, uint32_
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
+// Arrive on the mbarrier at this shared offset in every CTA of cta_mask once the MMAs issued so
+// far have completed.
+__device__ __forceinline__ void umma_commit_mc(uint32_t bar, uint16_t cta_mask) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::
+                   "r"(bar), "h"(cta_mask)
+               : "memory");
+}
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -201,10 +243,16 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 
 // ---- the GEMM kernel ----------------------------------------------------------
 
-template <int KIND, bool PROBE, int BN>
+// CL = 2: the two CTAs of a cluster take the two N tiles of one M tile and K range; each loads
+// one part (real or imaginary) of the shared 128-row digit tile into both CTAs' shared memory
+// (TMA multicast), so the long operand crosses the memory system once per cluster, and each
+// releases a stage to both producers.
+template <int KIND, bool PROBE, int BN, int CL>
 __global__ void __launch_bounds__(192, 1)
     split_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                  const __grid_constant__ SplitArgs args) {
+  static_assert(CL == 1 || (CL == 2 && !PROBE), "cluster of two CTAs (both parts of A) or none");
+  constexpr uint16_t kMask = (uint16_t)((1u << CL) - 1u);
   using T = MainTile<BN>;
   constexpr int kStages = T::kStages;
   constexpr uint32_t kStageBytes = T::kStageBytes, kTileA = T::kTileA, kTileB = T::kTileB;
@@ -223,8 +271,21 @@ __global__ void __launch_bounds__(192, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tile = blockIdx.x % args.tiles, ks = blockIdx.x / args.tiles;
-  const int tm = tile % args.tiles_m, tn = tile / args.tiles_m;
+  int tm, tn, ks;
+  uint32_t crank = 0;
+  if constexpr (CL > 1) {
+    // cluster u of the grid: M tile u % tiles_m, N tiles CL (u / tiles_m) + rank, K range u / units
+    crank = cluster_rank();
+    const int units = args.tiles / CL, u = blockIdx.x / CL;
+    ks = u / units;
+    tm = (u % units) % args.tiles_m;
+    tn = ((u % units) / args.tiles_m) * CL + (int)crank;
+  } else {
+    const int tile = blockIdx.x % args.tiles;
+    ks = blockIdx.x / args.tiles;
+    tm = tile % args.tiles_m;
+    tn = tile / args.tiles_m;
+  }
   const int64_t m0 = (int64_t)tm * 128, n0 = (int64_t)tn * BN;
   const int klo = ks * args.kb_split, khi = min(args.kblocks, klo + args.kb_split);
   constexpr int BKE = KIND == kSplitBF16 ? 64 : 128;  // digits per 128-byte row segment
@@ -232,7 +293,7 @@ __global__ void __launch_bounds__(192, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(full(s), 1);
-      mbar_init(empty(s), 1);
+      mbar_init(empty(s), CL);  // every CTA of the cluster releases the stage
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(accfull(b), 1);
@@ -249,6 +310,8 @@ __global__ void __launch_bounds__(192, 1)
     tc_fence_before();
   }
   __syncthreads();
+  // the peer's copies and releases reach this CTA's barriers only once they are initialised
+  if constexpr (CL > 1) cluster_sync_all();
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
   const long long budget = args.wait_cycles;
@@ -256,6 +319,7 @@ __global__ void __launch_bounds__(192, 1)
   if (warp == 0) {
     // ---------------- TMA producer ----------------
     if (lane == 0 && !args.stall_loads) {
+      const uint64_t a_policy = policy_evict_first();
       int it = 0;
       bool ok = true;
       for (int L = 0; L <= args.lmax && ok; ++L)
@@ -275,8 +339,17 @@ __global__ void __launch_bounds__(192, 1)
               const int x = kb * BKE;
               mbar_expect_tx(full(st), PROBE ? kTileA + kTileB : 2 * (kTileA + kTileB));
               const int64_t ya = args.a_row0 + m0, yb = args.b_row0 + n0;
-              tma_load_3d(sa, &tmA, x, (int)ya, p * 2 + 0, full(st));
-              if (!PROBE) tma_load_3d(sa + kTileA, &tmA, x, (int)ya, p * 2 + 1, full(st));
+              if constexpr (CL > 1) {
+                // this CTA's part of the shared A tile, into the same stage of every CTA
+                if (args.a_stream)
+                  tma_load_3d_mc_hint(sa + crank * kTileA, &tmA, x, (int)ya, p * 2 + (int)crank, full(st), kMask,
+                                      a_policy);
+                else
+                  tma_load_3d_mc(sa + crank * kTileA, &tmA, x, (int)ya, p * 2 + (int)crank, full(st), kMask);
+              } else {
+                tma_load_3d(sa, &tmA, x, (int)ya, p * 2 + 0, full(st));
+                if (!PROBE) tma_load_3d(sa + kTileA, &tmA, x, (int)ya, p * 2 + 1, full(st));
+              }
               tma_load_3d(sa + 2 * kTileA, &tmB, x, (int)yb, q * 2 + 0, full(st));
               if (!PROBE) tma_load_3d(sa + 2 * kTileA + kTileB, &tmB, x, (int)yb, q * 2 + 1, full(st));
             }
@@ -289,6 +362,10 @@ __global__ void __launch_bounds__(192, 1)
       const int last = it;
       for (int j = (last > kStages ? last - kStages : 0); j < last; ++j)
         mbar_wait(full(j % kStages), (uint32_t)(j / kStages) & 1u, budget, abort_flag, true);
+      // and every CTA of the cluster has released the last stages (their arrivals land here)
+      if constexpr (CL > 1)
+        for (int j = (last > kStages ? last - kStages : 0); j < last; ++j)
+          mbar_wait(empty(j % kStages), (uint32_t)(j / kStages) & 1u, budget, abort_flag, true);
     }
   } else if (warp == 1) {
     // ---------------- UMMA issuer ----------------
@@ -337,7 +414,10 @@ __global__ void __launch_bounds__(192, 1)
                   umma<KIND>(dim, aI0 + o, bR0 + o, idIm2, 1u);
                 }
               }
-              umma_commit(empty(st));
+              if constexpr (CL > 1)
+                umma_commit_mc(empty(st), kMask);
+              else
+                umma_commit(empty(st));
               first = false;
             }
           if (ok) umma_commit(accfull(buf));
@@ -498,6 +578,8 @@ __global__ void __launch_bounds__(192, 1)
       }
   }
   __syncthreads();
+  // no CTA leaves while its peer may still write to its shared memory or barriers
+  if constexpr (CL > 1) cluster_sync_all();
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(T::kTmemCols));
@@ -1158,9 +1240,9 @@ bool smallk_eligible(const SplitArgs& a) {
 #define SPLIT_MIN_KB_PER_SPLIT 12
 #endif
 constexpr int kMinKbPerSplit = SPLIT_MIN_KB_PER_SPLIT;
-void plan_ksplit(int64_t tiles, int kblocks, int& ksplits, int& kb_split) {
+void plan_ksplit(int64_t tiles, int kblocks, int& ksplits, int& kb_split, int64_t slots) {
   ksplits = 1;
-  const int64_t sms = num_sms();
+  const int64_t sms = slots;
   const int64_t kmax = std::max(1, kblocks / kMinKbPerSplit);
   auto fill = [&](int64_t ctas) { return (double)ctas / (double)(((ctas + sms - 1) / sms) * sms); };
   if (tiles > 0 && tiles < 4 * sms) {
@@ -1233,9 +1315,9 @@ __global__ void part_reduce_kernel(const z* __restrict__ part, int ks, int64_t M
   }
 }
 
-template <int KIND, bool PROBE, int BN>
+template <int KIND, bool PROBE, int BN, int CL>
 cudaError_t launch_split(const CUtensorMap& mapA, const CUtensorMap& mapB, const SplitArgs& a, cudaStream_t s) {
-  auto kern = split_kernel<KIND, PROBE, BN>;
+  auto kern = split_kernel<KIND, PROBE, BN, CL>;
   constexpr uint32_t smem = MainTile<BN>::kSmemBytes;
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
@@ -1245,17 +1327,84 @@ cudaError_t launch_split(const CUtensorMap& mapA, const CUtensorMap& mapB, const
   if (attr_err != cudaSuccess) return attr_err;
   const int64_t grid = (int64_t)a.tiles * a.ksplits;
   if (grid <= 0) return cudaSuccess;
-  if (grid > 0x7fffffff) return cudaErrorInvalidValue;
-  kern<<<(unsigned)grid, 192, smem, s>>>(mapA, mapB, a);
+  if (grid > 0x7fffffff || grid % CL != 0) return cudaErrorInvalidValue;
+  if constexpr (CL == 1) {
+    kern<<<(unsigned)grid, 192, smem, s>>>(mapA, mapB, a);
+  } else {
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3((unsigned)grid, 1, 1);
+    cfg.blockDim = dim3(192, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, mapA, mapB, a);
+    if (e != cudaSuccess) return e;
+  }
   return cudaGetLastError();
 }
 
+// CTAs of the main kernel resident at once: one per SM, or, in clusters of two, twice the
+// clusters the GPU can hold (a GPC with an odd number of free SMs leaves one idle).
+template <int KIND, int BN>
+int64_t main_slots(int cl) {
+  if (cl == 1) return num_sms();
+  static int64_t slots = 0;
+  static std::once_flag once;
+  std::call_once(once, [&]() {
+    auto kern = split_kernel<KIND, false, BN, 2>;
+    constexpr uint32_t smem = MainTile<BN>::kSmemBytes;
+    int n = 0;
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(2 * (unsigned)num_sms(), 1, 1);
+    cfg.blockDim = dim3(192, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess &&
+        cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess && n > 0)
+      slots = 2 * (int64_t)n;
+    else
+      cudaGetLastError();
+  });
+  return slots;  // 0: clusters unavailable
+}
+
 template <int KIND>
-cudaError_t launch_main(const CUtensorMap& mapA, const CUtensorMap& mapB, const SplitArgs& a, int bn, cudaStream_t s) {
+int64_t main_slots_bn(int bn, int cl) {
   switch (bn) {
-    case 96: return launch_split<KIND, false, 96>(mapA, mapB, a, s);
-    case 64: return launch_split<KIND, false, 64>(mapA, mapB, a, s);
-    default: return launch_split<KIND, false, 128>(mapA, mapB, a, s);
+    case 96: return main_slots<KIND, 96>(cl);
+    case 64: return main_slots<KIND, 64>(cl);
+    default: return main_slots<KIND, 128>(cl);
+  }
+}
+
+template <int KIND>
+cudaError_t launch_main(const CUtensorMap& mapA, const CUtensorMap& mapB, const SplitArgs& a, int bn, int cl,
+                        cudaStream_t s) {
+  if (cl == 2) {
+    switch (bn) {
+      case 96: return launch_split<KIND, false, 96, 2>(mapA, mapB, a, s);
+      case 64: return launch_split<KIND, false, 64, 2>(mapA, mapB, a, s);
+      default: return launch_split<KIND, false, 128, 2>(mapA, mapB, a, s);
+    }
+  }
+  switch (bn) {
+    case 96: return launch_split<KIND, false, 96, 1>(mapA, mapB, a, s);
+    case 64: return launch_split<KIND, false, 64, 1>(mapA, mapB, a, s);
+    default: return launch_split<KIND, false, 128, 1>(mapA, mapB, a, s);
   }
 }
 
@@ -1317,6 +1466,37 @@ cudaError_t split_gemm_smallk(const SliceSet& A, const SliceSet& B, const SplitA
   if (e != cudaSuccess) return e;
   return KA.kind == kSplitBF16 ? launch_smallk<kSplitBF16>(KA.tmap, mapB, k, s)
                                : launch_smallk<kSplitE4M3>(KA.tmap, mapB, k, s);
+}
+
+// Tiling, cluster and K split of a main-kernel launch. An output two N tiles wide (the ladder's
+// occupied pairs on the narrow side, or a long operand against up to 256 rows) runs in clusters
+// of two CTAs that share the 128-row operand's tile (read once per pair of N tiles); also with
+// four N tiles, where each pair shares it.
+#ifndef SPLIT_CLUSTER
+#define SPLIT_CLUSTER 1
+#endif
+#ifndef SPLIT_STREAM_HINT
+#define SPLIT_STREAM_HINT 1
+#endif
+struct MainPlan {
+  MainTiling tl;
+  int cl = 1;
+  int ksplits = 1, kb_split = 1;
+};
+MainPlan plan_main(int64_t M, int64_t N, int kblocks, int kind) {
+  MainPlan P;
+  P.tl = choose_tiling(M, N);
+  int64_t slots = num_sms();
+  const int64_t tiles_n = P.tl.tiles_m > 0 ? P.tl.tiles / P.tl.tiles_m : 0;
+  if (SPLIT_CLUSTER && (tiles_n == 2 || tiles_n == 4)) {
+    const int64_t sl = kind == kSplitBF16 ? main_slots_bn<kSplitBF16>(P.tl.bn, 2) : main_slots_bn<kSplitE4M3>(P.tl.bn, 2);
+    if (sl > 0) {
+      P.cl = 2;
+      slots = sl;
+    }
+  }
+  plan_ksplit(P.tl.tiles, kblocks, P.ksplits, P.kb_split, slots);
+  return P;
 }
 
 }  // namespace
@@ -1421,11 +1601,27 @@ double split_cost_estimate(int64_t M, int64_t N, int64_t K, const SplitConfig& c
 }
 
 int64_t split_part_bytes(int64_t M, int64_t N, int64_t K, const SplitConfig& cfg) {
-  const int64_t tiles = choose_tiling(M, N).tiles;
   const int kblocks = (int)((std::max<int64_t>(K, 1) + bke(cfg.kind) - 1) / bke(cfg.kind));
-  int ks, kbs;
-  plan_ksplit(tiles, kblocks, ks, kbs);
-  return ks > 1 ? (int64_t)ks * M * N * (int64_t)sizeof(z) : 0;
+  const MainPlan P = plan_main(M, N, kblocks, cfg.kind);
+  return P.ksplits > 1 ? (int64_t)P.ksplits * M * N * (int64_t)sizeof(z) : 0;
+}
+
+void split_describe(int64_t M, int64_t N, int64_t K, const SplitConfig& cfg, int out[6]) {
+  const int kblocks = (int)(round_up(std::max<int64_t>(K, 1), bke(cfg.kind)) / bke(cfg.kind));
+  SplitArgs a;
+  std::memset(&a, 0, sizeof(a));
+  for (int i = 0; i < 6; ++i) out[i] = 0;
+  if (!fill_levels(a, cfg.s, cfg.b, kblocks, cfg.kind)) return;
+  if (smallk_eligible(a)) {
+    out[0] = 1;
+    return;
+  }
+  const MainPlan P = plan_main(M, N, kblocks, cfg.kind);
+  out[1] = P.tl.swap ? 1 : 0;
+  out[2] = P.tl.bn;
+  out[3] = P.cl;
+  out[4] = P.ksplits;
+  out[5] = (int)P.tl.tiles;
 }
 
 cudaError_t split_gemm(const SliceSet& A, const SliceSet& B, z* C, int64_t ldc, z alpha, z beta, int* err,
@@ -1435,8 +1631,11 @@ cudaError_t split_gemm(const SliceSet& A, const SliceSet& B, z* C, int64_t ldc, 
     return cudaErrorInvalidValue;
   SplitArgs a;
   std::memset(&a, 0, sizeof(a));
-  // the failure-path self-test keeps the plain orientation and 128-wide tiles
-  MainTiling tl = stall_loads ? MainTiling() : choose_tiling(A.rows, B.rows);
+  // the failure-path self-test keeps the plain orientation, 128-wide tiles and no cluster
+  const int kblocks = (int)(A.Kp / bke(A.kind));
+  MainPlan mp;
+  if (!stall_loads) mp = plan_main(A.rows, B.rows, kblocks, A.kind);
+  MainTiling& tl = mp.tl;
   if (stall_loads) {
     tl.tiles_m = (A.rows + 127) / 128;
     tl.tiles = tl.tiles_m * ((B.rows + 127) / 128);
@@ -1461,11 +1660,14 @@ cudaError_t split_gemm(const SliceSet& A, const SliceSet& B, z* C, int64_t ldc, 
   a.err = err;
   a.wait_cycles = wait_cycles > 0 ? wait_cycles : 4000000000LL;  // default ~2 s at 2 GHz
   a.stall_loads = stall_loads;
-  const int kblocks = (int)(A.Kp / bke(A.kind));
   if (!fill_levels(a, A.s, A.b, kblocks, A.kind)) return cudaErrorInvalidValue;
   if (!stall_loads && smallk_eligible(a))
     return split_gemm_smallk(A, B, a, C, ldc, alpha, beta, err, wait_cycles, s, conjB);
-  plan_ksplit(a.tiles, kblocks, a.ksplits, a.kb_split);
+  a.ksplits = mp.ksplits;
+  a.kb_split = mp.kb_split;
+  // one cluster covers every N tile: no other CTA reads this A tile, so under L2 pressure its
+  // lines go before the partial sums and the narrow operand, which are read again
+  a.a_stream = (SPLIT_STREAM_HINT && mp.cl == 2 && tl.tiles == 2 * tl.tiles_m) ? 1 : 0;
   if (stall_loads) {
     a.ksplits = 1;
     a.kb_split = kblocks;
@@ -1498,8 +1700,8 @@ cudaError_t split_gemm(const SliceSet& A, const SliceSet& B, z* C, int64_t ldc, 
     e = encode_map_rows(KB, (uint32_t)tl.bn, &mapB);
     if (e != cudaSuccess) return e;
   }
-  e = A.kind == kSplitBF16 ? launch_main<kSplitBF16>(KA.tmap, mapB, a, tl.bn, s)
-                           : launch_main<kSplitE4M3>(KA.tmap, mapB, a, tl.bn, s);
+  e = A.kind == kSplitBF16 ? launch_main<kSplitBF16>(KA.tmap, mapB, a, tl.bn, mp.cl, s)
+                           : launch_main<kSplitE4M3>(KA.tmap, mapB, a, tl.bn, mp.cl, s);
   if (e != cudaSuccess || a.ksplits == 1) return e;
   // the partials are in C's orientation (A.rows x B.rows) whichever operand took the 128-row side
   part_reduce_kernel<<<grid_for(A.rows * B.rows, 256), 256, 0, s>>>(a.part, a.ksplits, A.rows, B.rows, C, ldc, alpha,
@@ -1555,8 +1757,8 @@ cudaError_t split_probe_raw(int kind, const double* Aint, const double* Bint, in
   a.kbper[0] = a.kblocks;
   a.ksplits = 1;
   a.kb_split = a.kblocks;
-  return kind == kSplitBF16 ? launch_split<kSplitBF16, true, 128>(A.tmap, B.tmap, a, s)
-                            : launch_split<kSplitE4M3, true, 128>(A.tmap, B.tmap, a, s);
+  return kind == kSplitBF16 ? launch_split<kSplitBF16, true, 128, 1>(A.tmap, B.tmap, a, s)
+                            : launch_split<kSplitE4M3, true, 128, 1>(A.tmap, B.tmap, a, s);
 }
 
 }  // namespace ccsd

@@ -191,3 +191,35 @@ def test_split_zgemm_short_m_on_the_narrow_tile_side(env, M, N, K, tA, cA, tB, c
                      dc2, alpha, beta, transA=bool(tA), conjA=bool(cA), transB=bool(tB), conjB=bool(cB), bits=5,
                      slices=8)
     assert torch.equal(dc, dc2)
+
+
+@pytest.mark.parametrize("M,N,K,tB,cB,kind", [(190, 3000, 3000, 1, 0, 0), (2000, 200, 1500, 1, 1, 0),
+                                              (2000, 200, 6000, 0, 0, 0), (1000, 500, 1200, 1, 0, 0),
+                                              (1000, 500, 1200, 0, 1, 1), (150, 2500, 2000, 1, 1, 0)])
+def test_split_zgemm_cluster_pairs_share_the_long_operand(env, M, N, K, tB, cB, kind):
+    """Two N tiles (or four) of one M tile and K range run as a cluster of two CTAs that each
+    multicast one part (real or imaginary) of the shared 128-row digit tile into both; the
+    product, with and without K split, swapped or not, is the same GEMM to the digit bound and
+    the same bits from run to run."""
+    torch, ccsd = env
+    bits, slices = (5, 8) if kind == 0 else (8, 5)
+    d = ccsd.split_describe(M, N, K, kind=kind, bits=bits, slices=slices)
+    assert d["short_k"] == 0 and d["cluster"] == 2, d
+    rng = np.random.default_rng(M + 3 * N + 7 * K + kind)
+    a = _rand(rng, M, K)
+    b = _rand(rng, *((N, K) if tB else (K, N)))
+    c0 = _rand(rng, M, N)
+    ob = b.T if tB else b
+    ob = ob.conj() if cB else ob
+    alpha, beta = 0.5 - 0.25j, 0.75 + 0.5j
+    want = alpha * (a @ ob) + beta * c0
+    da = torch.from_numpy(a).cuda()
+    db = torch.from_numpy(np.ascontiguousarray(b)).cuda()
+    outs = []
+    for _ in range(2):
+        dc = torch.from_numpy(c0).cuda()
+        ccsd.split_zgemm(da, db, dc, alpha, beta, transB=bool(tB), conjB=bool(cB), kind=kind, bits=bits, slices=slices)
+        outs.append(dc)
+    assert torch.equal(outs[0], outs[1])
+    err = np.max(np.abs(outs[0].cpu().numpy() - want)) / np.max(np.abs(want))
+    assert err < (6e-11 if kind == 0 else 2e-10), err
