@@ -56,8 +56,8 @@ FastDiv make_fastdiv(uint32_t d) {
 __device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) { return (__umulhi(f.m, n) + n) >> f.l; }
 
 // The direct permutation with every element offset below 2^31: 32-bit index arithmetic, each
-// division by a dimension a multiply and a shift, and four elements per thread in flight (all
-// four loads issued before the stores).
+// division by a dimension a multiply and a shift, and each warp over 128 consecutive output
+// elements (four coalesced 512-byte accesses, all loads issued before the stores).
 struct PermuteFast {
   const z* in;
   z* out;
@@ -70,13 +70,14 @@ struct PermuteFast {
 };
 __global__ void __launch_bounds__(256) permute_fast_kernel(PermuteFast g, uint32_t total) {
   constexpr int U = 4;
-  const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t e0 = blockIdx.x * blockDim.x + threadIdx.x; e0 < total; e0 += U * stride) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < (total + 127u) / 128u; w += nwarps) {
     uint32_t io[U], oo[U];
     bool live[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const uint32_t e = e0 + (uint32_t)u * stride;
+      const uint32_t e = w * 128u + (uint32_t)u * 32u + lane;
       live[u] = e < total;
       uint32_t r = live[u] ? e : 0u, i = 0, o = 0;
 #pragma unroll
@@ -681,6 +682,9 @@ cudaError_t zscale_matrix(const ZGemmArgs& g, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+#ifndef PERMUTE_FAST
+#define PERMUTE_FAST 1
+#endif
 cudaError_t permute_add(const PermuteArgs& a0, cudaStream_t s) {
   if (a0.rank < 1 || a0.rank > kMaxRank) return cudaErrorInvalidValue;
   // the same permutation with dims of extent 1 dropped and neighbours that are contiguous in
@@ -722,7 +726,7 @@ cudaError_t permute_add(const PermuteArgs& a0, cudaStream_t s) {
       if (a.istr[d] == 1 && a.dims[d] > 1) p = d;
   if (p < 0) {
     constexpr int64_t kLim = (int64_t)1 << 31;
-    if (total < kLim && imax < kLim && omax < kLim) {
+    if (PERMUTE_FAST && total < kLim && imax < kLim && omax < kLim) {
       PermuteFast f;
       f.in = a.in;
       f.out = a.out;
@@ -735,7 +739,7 @@ cudaError_t permute_add(const PermuteArgs& a0, cudaStream_t s) {
       f.alpha = a.alpha;
       f.beta = a.beta;
       f.conj = a.conj;
-      permute_fast_kernel<<<grid_for((total + 3) / 4, kThreads), kThreads, 0, s>>>(f, (uint32_t)total);
+      permute_fast_kernel<<<grid_for((total + 127) / 128 * 32, kThreads), kThreads, 0, s>>>(f, (uint32_t)total);
     } else {
       permute_direct_kernel<<<grid_for(total, kThreads), kThreads, 0, s>>>(a, total);
     }

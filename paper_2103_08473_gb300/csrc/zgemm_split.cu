@@ -15,9 +15,11 @@
 //           and commits each smem stage back to the producer.
 //   warps 2-5  epilogue: after each level group, read the FP32 accumulator rows
 //           (tcgen05.ld 32x32b), scale by 2^(e_row + e_col - b L) and add
-//           alpha * value into C in FP64, then release the TMEM set. With the
-//           operands swapped (a short M on the BN side) the tile is the transpose
-//           of C's and each warp stores 32 consecutive elements of a row of C.
+//           alpha * value into C in FP64 by reductions in L2 (red.global.add.f64:
+//           each element has one owning thread, so the order of its additions is
+//           fixed), then release the TMEM set. With the operands swapped (a short M
+//           on the BN side) the tile is the transpose of C's and each warp adds into
+//           32 consecutive elements of a row of C.
 // Every mbarrier wait is bounded (clock64 budget); a wait that gives up sets the
 // error word and the CTA drains its in-flight copies, frees TMEM and exits.
 #include <cuda_bf16.h>
@@ -156,6 +158,11 @@ __device__ __forceinline__ uint32_t cluster_rank() {
 }
 __device__ __forceinline__ void cluster_sync_all() {
   asm volatile("barrier.cluster.arrive.release;\nbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
+// *p += v at L2 (no value returned, so the issuing thread does not wait for it).
+__device__ __forceinline__ void red_add_f64(double* p, double v) {
+  asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -460,8 +467,9 @@ __global__ void __launch_bounds__(192, 1)
         const uint32_t trow = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)buf * (2u * BN);
         const double gs = ldexp(1.0, -args.b * (L + 2));
         // alpha = +-1 (every K-split partial, and most calls): the accumulator values go to FP64 by
-        // integer arithmetic, scaled by the row and column powers of two on the way, so each part
-        // costs one DADD on the FP64 pipe; other real alpha: 1 DMUL + 2 DFMA per complex element
+        // integer arithmetic, scaled by the row and column powers of two on the way, and are added
+        // in L2, so no FP64 instruction runs on the SM; other alpha: a DMUL per part (and a complex
+        // product for complex alpha)
         const bool real_alpha = alpha.y == 0.0;
         const bool unit_alpha = real_alpha && (alpha.x == 1.0 || alpha.x == -1.0);
         const uint32_t flip = (unit_alpha && alpha.x < 0.0) ? 0x80000000u : 0u;  // sign of alpha on the FP32 bits
@@ -473,102 +481,42 @@ __global__ void __launch_bounds__(192, 1)
           tmem_ld32(trow + c, re);
           if (!PROBE) tmem_ld32(trow + BN + c, im);
           tmem_wait_ld();
-          if (mrow) {
-            if (!PROBE && args.transC) {
-              const double* csc = args.cs + n0 + c;
-              const int64_t rem = args.N - (n0 + c);
-              z* ocol = out + (n0 + c) * ldo + m;
+          if (mrow && PROBE) {
+            for (int j = 0; j < 32; ++j) {
+              const int64_t n = n0 + c + j;
+              if (n < args.N) args.probe[m * args.N + n] = (double)__uint_as_float(re[j]);
+            }
+          } else if (mrow) {
+            // each output element belongs to this thread alone (one row of the tile, and its own
+            // partial slice under a K split), so its additions land in a fixed order: fire-and-forget
+            // reductions at L2 instead of a read, an add and a write-back per element
+            const double* csc = args.cs + n0 + c;
+            const int64_t left = args.N - (n0 + c);
+            const int rem = left < 32 ? (int)left : 32;
+            // transC: element (m, n) at out[n * ldo + m] (32 lanes, consecutive m); else out[m * ldo + n]
+            double* o = reinterpret_cast<double*>(args.transC ? out + (n0 + c) * ldo + m : out + m * ldo + n0 + c);
+            const int64_t step = 2 * (args.transC ? ldo : 1);  // doubles from column j to j + 1
 #pragma unroll
-              for (int j0 = 0; j0 < 32; j0 += 8) {
-                double sc[8];
-                z ov[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j)
-                  if (j0 + j < rem) {
-                    sc[j] = csc[j0 + j];
-                    ov[j] = ocol[(int64_t)(j0 + j) * ldo];
-                  }
-#pragma unroll
-                for (int j = 0; j < 8; ++j)
-                  if (j0 + j < rem) {
-                    if (unit_alpha) {
-                      const int k = krow + pow2_exponent(sc[j]);
-                      ov[j].x += f32_times_pow2(re[j0 + j] ^ flip, k);
-                      ov[j].y += f32_times_pow2(im[j0 + j] ^ flip, k);
-                    } else {
-                      const double f = rowf * sc[j];
-                      const double vr = (double)__uint_as_float(re[j0 + j]), vi = (double)__uint_as_float(im[j0 + j]);
-                      if (real_alpha) {
-                        ov[j].x = fma(vr, f, ov[j].x);
-                        ov[j].y = fma(vi, f, ov[j].y);
-                      } else {
-                        ov[j] = zadd(ov[j], zmul(alpha, make_double2(vr * f, vi * f)));
-                      }
-                    }
-                    ocol[(int64_t)(j0 + j) * ldo] = ov[j];
-                  }
-              }
-            } else if (PROBE) {
-              for (int j = 0; j < 32; ++j) {
-                const int64_t n = n0 + c + j;
-                if (n < args.N) args.probe[m * args.N + n] = (double)__uint_as_float(re[j]);
-              }
-            } else {
-              z* orow = out + m * ldo + n0 + c;
-              const double* csc = args.cs + n0 + c;
-              const int64_t rem = args.N - (n0 + c);
-              if (rem >= 32) {
-                // whole chunk, 8 columns at a time: all loads first so their latencies overlap
-#pragma unroll
-                for (int j0 = 0; j0 < 32; j0 += 8) {
-                  double sc[8];
-                  z ov[8];
-#pragma unroll
-                  for (int j = 0; j < 8; ++j) {
-                    sc[j] = csc[j0 + j];
-                    ov[j] = orow[j0 + j];
-                  }
-#pragma unroll
-                  for (int j = 0; j < 8; ++j) {
-                    if (unit_alpha) {
-                      const int k = krow + pow2_exponent(sc[j]);
-                      ov[j].x += f32_times_pow2(re[j0 + j] ^ flip, k);
-                      ov[j].y += f32_times_pow2(im[j0 + j] ^ flip, k);
-                    } else {
-                      const double f = rowf * sc[j];
-                      const double vr = (double)__uint_as_float(re[j0 + j]), vi = (double)__uint_as_float(im[j0 + j]);
-                      if (real_alpha) {
-                        ov[j].x = fma(vr, f, ov[j].x);
-                        ov[j].y = fma(vi, f, ov[j].y);
-                      } else {
-                        ov[j] = zadd(ov[j], zmul(alpha, make_double2(vr * f, vi * f)));
-                      }
-                    }
-                    orow[j0 + j] = ov[j];
-                  }
-                }
+            for (int j = 0; j < 32; ++j) {
+              if (j >= rem) break;
+              const double sc = csc[j];
+              double dx, dy;
+              if (unit_alpha) {
+                const int k = krow + pow2_exponent(sc);
+                dx = f32_times_pow2(re[j] ^ flip, k);
+                dy = f32_times_pow2(im[j] ^ flip, k);
               } else {
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                  if (j >= rem) break;
-                  z o = orow[j];
-                  if (unit_alpha) {
-                    const int k = krow + pow2_exponent(csc[j]);
-                    o.x += f32_times_pow2(re[j] ^ flip, k);
-                    o.y += f32_times_pow2(im[j] ^ flip, k);
-                  } else {
-                    const double f = rowf * csc[j];
-                    const double vr = (double)__uint_as_float(re[j]), vi = (double)__uint_as_float(im[j]);
-                    if (real_alpha) {
-                      o.x = fma(vr, f, o.x);
-                      o.y = fma(vi, f, o.y);
-                    } else {
-                      o = zadd(o, zmul(alpha, make_double2(vr * f, vi * f)));
-                    }
-                  }
-                  orow[j] = o;
+                const double f = rowf * sc;
+                dx = (double)__uint_as_float(re[j]) * f;
+                dy = (double)__uint_as_float(im[j]) * f;
+                if (!real_alpha) {
+                  const z w = zmul(alpha, make_double2(dx, dy));
+                  dx = w.x;
+                  dy = w.y;
                 }
               }
+              red_add_f64(o + j * step, dx);
+              red_add_f64(o + j * step + 1, dy);
             }
           }
         }
