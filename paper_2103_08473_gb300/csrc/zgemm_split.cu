@@ -79,6 +79,7 @@ struct SplitArgs {
   int transC;               // 1: the kernel's (m, n) is the caller's C[n][m] (operands swapped)
   int conjA, conjB;         // conjugate the kernel's A / B operand (the sign of its imaginary digits)
   int a_stream;             // clusters only: A's tile is read by no other resident cluster (evict first)
+  int group;                // no cluster: M tiles per band of the tile order (1: M tiles step first)
 };
 
 // ---- PTX wrappers ----------------------------------------------------------
@@ -290,8 +291,17 @@ __global__ void __launch_bounds__(192, 1)
   } else {
     const int tile = blockIdx.x % args.tiles;
     ks = blockIdx.x / args.tiles;
-    tm = tile % args.tiles_m;
-    tn = tile / args.tiles_m;
+    if (args.group > 1) {
+      // bands of `group` M tiles, N tiles stepping within a band: the CTAs resident at once
+      // share a few A and B tiles instead of streaming every A tile against one or two B tiles
+      const int tiles_n = args.tiles / args.tiles_m, per = args.group * tiles_n;
+      const int m_first = (tile / per) * args.group, rows = min(args.tiles_m - m_first, args.group);
+      tm = m_first + (tile % per) % rows;
+      tn = (tile % per) / rows;
+    } else {
+      tm = tile % args.tiles_m;
+      tn = tile / args.tiles_m;
+    }
   }
   const int64_t m0 = (int64_t)tm * 128, n0 = (int64_t)tn * BN;
   const int klo = ks * args.kb_split, khi = min(args.kblocks, klo + args.kb_split);
@@ -860,11 +870,9 @@ __device__ __forceinline__ long long fixed62_scaled(double x, int e) {
   } else if (s < -54) {
     v = 0;  // below half a unit
   } else {
+    // round to nearest, ties to even: add half a unit less one, plus the kept part's low bit
     const int r = -s;
-    unsigned long long q = m >> r;
-    const unsigned long long rem = m & ((1ull << r) - 1ull), half = 1ull << (r - 1);
-    if (rem > half || (rem == half && (q & 1ull))) ++q;
-    v = (long long)q;
+    v = (long long)((m + (1ull << (r - 1)) - 1ull + ((m >> r) & 1ull)) >> r);
   }
   return (bits >> 63) ? -v : v;
 }
@@ -912,6 +920,41 @@ __device__ __forceinline__ uint2 pack4_bf16(int d0, int d1, int d2, int d3) {
   return w;
 }
 
+// The default digits (8 of 5 bits, e4m3) of four consecutive values of one part, with constant
+// shifts: every 5-bit field of W lies within one of its 32-bit halves (bits 57.. of the first
+// digit, then 52, 47, 42, 37, 32 in the high word and 27, 22 in the low one). A field f becomes
+// the float f - 16 by adding it to the bits of 1.5 * 2^23 (exact for these small integers),
+// two floats become two e4m3 bytes in one conversion, and the sign of each value is applied to
+// its four bytes at once (e4m3 is sign-magnitude: the digits of -x are the negated digits of x;
+// a zero digit of a negative value is -0). Plane p is written at out + o + p * plane (bytes).
+__device__ __forceinline__ void cut4_e4m3_8x5(const unsigned long long (&W)[4], const bool (&neg)[4],
+                                              uint8_t* __restrict__ out, int64_t o, int64_t plane) {
+  const uint32_t sgn = (neg[0] ? 0x80u : 0u) | (neg[1] ? 0x8000u : 0u) | (neg[2] ? 0x800000u : 0u) |
+                       (neg[3] ? 0x80000000u : 0u);
+  uint32_t hi[4], lo[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    hi[u] = (uint32_t)(W[u] >> 32);
+    lo[u] = (uint32_t)W[u];
+  }
+  constexpr int kBias = 0x4B400000 - 16;  // float bits of 1.5 * 2^23, less half a digit
+#pragma unroll
+  for (int p = 0; p < 8; ++p) {
+    float f[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      uint32_t fld;
+      if (p == 0) fld = hi[u] >> 25;
+      else if (p < 6) fld = (hi[u] >> (25 - 5 * p)) & 31u;
+      else fld = (lo[u] >> (57 - 5 * p)) & 31u;
+      f[u] = __int_as_float(kBias + (int)fld) - 12582912.0f;
+    }
+    const __nv_fp8x2_storage_t a = __nv_cvt_float2_to_fp8x2(make_float2(f[0], f[1]), __NV_SATFINITE, __NV_E4M3);
+    const __nv_fp8x2_storage_t c = __nv_cvt_float2_to_fp8x2(make_float2(f[2], f[3]), __NV_SATFINITE, __NV_E4M3);
+    *reinterpret_cast<uint32_t*>(out + o + p * plane) = ((uint32_t)a | ((uint32_t)c << 16)) ^ sgn;
+  }
+}
+
 // Rows with K contiguous, in two passes over (row, K chunk) work items, one warp each, so
 // that both many short rows and few long rows keep the GPU busy: pass 1 takes each
 // chunk's largest |re|, |im| and folds its exponent into the row's with an integer
@@ -937,7 +980,7 @@ __global__ void rowexp_n_kernel(const z* __restrict__ X, int64_t rows, int64_t K
 }
 
 template <int KIND>
-__global__ void slice_kernel(const z* __restrict__ X, int64_t rows, int64_t K, int64_t ld, int conj, int s, int b,
+__global__ void __launch_bounds__(256, 4) slice_kernel(const z* __restrict__ X, int64_t rows, int64_t K, int64_t ld, int conj, int s, int b,
                              uint8_t* __restrict__ out, int64_t rows_pad, int64_t Kp, int64_t chunk, int64_t nchunks,
                              const int* __restrict__ ex, unsigned long long doff) {
   const int lane = threadIdx.x & 31;
@@ -966,6 +1009,12 @@ __global__ void slice_kernel(const z* __restrict__ X, int64_t rows, int64_t K, i
         ni[u] = vi < 0;
         Wr[u] = (unsigned long long)(nr[u] ? -vr : vr) + doff;
         Wi[u] = (unsigned long long)(ni[u] ? -vi : vi) + doff;
+      }
+      if (KIND == kSplitE4M3 && s == 8 && b == 5) {
+        const int64_t plane = 2 * rows_pad * Kp;  // from digit p of a part to digit p + 1
+        cut4_e4m3_8x5(Wr, nr, out, r * Kp + k0, plane);
+        cut4_e4m3_8x5(Wi, ni, out, (rows_pad + r) * Kp + k0, plane);
+        continue;
       }
       int shift = 62;
       for (int p = 0; p < s; ++p) {
@@ -1025,7 +1074,7 @@ __global__ void rowexp_finalize_kernel(int* __restrict__ ex, int64_t rows, doubl
 }
 
 template <int KIND>
-__global__ void slice_t_kernel(const z* __restrict__ X, int64_t rows, int64_t K, int64_t ld, int conj, int s, int b,
+__global__ void __launch_bounds__(256, 4) slice_t_kernel(const z* __restrict__ X, int64_t rows, int64_t K, int64_t ld, int conj, int s, int b,
                                uint8_t* __restrict__ out, int64_t rows_pad, int64_t Kp, const int* __restrict__ ex,
                                unsigned long long doff) {
   __shared__ z tile[64][33];
@@ -1051,6 +1100,12 @@ __global__ void slice_t_kernel(const z* __restrict__ X, int64_t rows, int64_t K,
       ni[u] = vi < 0;
       Wr[u] = (unsigned long long)(nr[u] ? -vr : vr) + doff;
       Wi[u] = (unsigned long long)(ni[u] ? -vi : vi) + doff;
+    }
+    if (KIND == kSplitE4M3 && s == 8 && b == 5) {
+      const int64_t plane = 2 * rows_pad * Kp;
+      cut4_e4m3_8x5(Wr, nr, out, r * Kp + k, plane);
+      cut4_e4m3_8x5(Wi, ni, out, (rows_pad + r) * Kp + k, plane);
+      continue;
     }
     int shift = 62;
     for (int p = 0; p < s; ++p) {
@@ -1426,6 +1481,9 @@ cudaError_t split_gemm_smallk(const SliceSet& A, const SliceSet& B, const SplitA
 #ifndef SPLIT_STREAM_HINT
 #define SPLIT_STREAM_HINT 1
 #endif
+#ifndef SPLIT_GROUP
+#define SPLIT_GROUP 8
+#endif
 struct MainPlan {
   MainTiling tl;
   int cl = 1;
@@ -1616,6 +1674,13 @@ cudaError_t split_gemm(const SliceSet& A, const SliceSet& B, z* C, int64_t ldc, 
   // one cluster covers every N tile: no other CTA reads this A tile, so under L2 pressure its
   // lines go before the partial sums and the narrow operand, which are read again
   a.a_stream = (SPLIT_STREAM_HINT && mp.cl == 2 && tl.tiles == 2 * tl.tiles_m) ? 1 : 0;
+  // many tiles both ways (e.g. the (ov)^3 products): bands of SPLIT_GROUP M tiles
+  {
+    const int64_t tiles_n = tl.tiles_m > 0 ? tl.tiles / tl.tiles_m : 0;
+    a.group = (mp.cl == 1 && SPLIT_GROUP > 1 && tl.tiles_m >= 2 * SPLIT_GROUP && tiles_n >= 2 * SPLIT_GROUP)
+                  ? SPLIT_GROUP
+                  : 1;
+  }
   if (stall_loads) {
     a.ksplits = 1;
     a.kb_split = kblocks;
