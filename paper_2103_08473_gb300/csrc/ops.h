@@ -22,6 +22,10 @@ struct PermuteArgs {
   z alpha{1.0, 0.0};
   double beta = 0.0;
   int conj = 0;
+  // set by permute_add: 1 when alpha = +-1 and beta = 0 (a copy with sign flips), 2 when
+  // alpha = +-1 and beta = 1 (one add per part); sx, sy: sign bits to flip on re, im
+  int mode = 0;
+  unsigned long long sx = 0, sy = 0;
 };
 cudaError_t permute_add(const PermuteArgs& a, cudaStream_t s);
 

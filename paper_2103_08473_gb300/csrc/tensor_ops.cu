@@ -14,13 +14,27 @@ constexpr int kUpdateBlocks = 152 * 4;
 constexpr int kEnergyBlocks = 152 * 2;
 constexpr int kDiisBlocks = 152 * 2;
 
-__device__ __forceinline__ z ld_conj(const z* p, int conj) {
-  z v = *p;
-  if (conj) v.y = -v.y;
-  return v;
-}
 
 // ---- permutations ----------------------------------------------------------
+
+// out = alpha op(v) + beta out for one element. The common cases (alpha = +-1 with beta 0 or 1)
+// flip sign bits with integer operations and add at most once per part: the FP64 pipe of this
+// chip is narrow, and the general complex form costs eight FP64 operations per element.
+__device__ __forceinline__ double flip_sign(double x, unsigned long long m) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (long long)m);
+}
+__device__ __forceinline__ void perm_put(z* o, z v, int mode, unsigned long long sx, unsigned long long sy, z alpha,
+                                         double beta, int conj) {
+  if (mode == 1) {
+    *o = make_double2(flip_sign(v.x, sx), flip_sign(v.y, sy));
+  } else if (mode == 2) {
+    const z w = *o;
+    *o = make_double2(w.x + flip_sign(v.x, sx), w.y + flip_sign(v.y, sy));
+  } else {
+    if (conj) v.y = -v.y;
+    *o = beta != 0.0 ? zaxpby(alpha, v, beta, *o) : zmul(alpha, v);
+  }
+}
 
 // Output-ordered elementwise copy: coalesced when the innermost output dim is also
 // innermost in the input.
@@ -34,9 +48,7 @@ __global__ void permute_direct_kernel(PermuteArgs g, int64_t total) {
       io += c * g.istr[d];
       oo += c * g.ostr[d];
     }
-    z v = ld_conj(g.in + io, g.conj);
-    z* o = g.out + oo;
-    *o = g.beta != 0.0 ? zaxpby(g.alpha, v, g.beta, *o) : zmul(g.alpha, v);
+    perm_put(g.out + oo, g.in[io], g.mode, g.sx, g.sy, g.alpha, g.beta, g.conj);
   }
 }
 
@@ -66,7 +78,8 @@ struct PermuteFast {
   uint32_t istr[kMaxRank], ostr[kMaxRank];
   z alpha;
   double beta;
-  int conj;
+  int conj, mode;
+  unsigned long long sx, sy;
 };
 __global__ void __launch_bounds__(256) permute_fast_kernel(PermuteFast g, uint32_t total) {
   constexpr int U = 4;
@@ -95,13 +108,10 @@ __global__ void __launch_bounds__(256) permute_fast_kernel(PermuteFast g, uint32
     z v[U];
 #pragma unroll
     for (int u = 0; u < U; ++u)
-      if (live[u]) v[u] = ld_conj(g.in + io[u], g.conj);
+      if (live[u]) v[u] = g.in[io[u]];
 #pragma unroll
     for (int u = 0; u < U; ++u)
-      if (live[u]) {
-        z* o = g.out + oo[u];
-        *o = g.beta != 0.0 ? zaxpby(g.alpha, v[u], g.beta, *o) : zmul(g.alpha, v[u]);
-      }
+      if (live[u]) perm_put(g.out + oo[u], v[u], g.mode, g.sx, g.sy, g.alpha, g.beta, g.conj);
   }
 }
 
@@ -125,15 +135,14 @@ __global__ void permute_tiled_kernel(PermuteArgs g, int p, int64_t nrest, int64_
       const int64_t p0 = (t / tiles_q) * 32, q0 = (t % tiles_q) * 32;
       for (int yy = ty; yy < 32; yy += 8) {
         int64_t pp = p0 + tx, qq = q0 + yy;
-        if (pp < g.dims[p] && qq < g.dims[q]) tile[yy][tx] = ld_conj(g.in + ib + pp * g.istr[p] + qq * g.istr[q], g.conj);
+        if (pp < g.dims[p] && qq < g.dims[q]) tile[yy][tx] = g.in[ib + pp * g.istr[p] + qq * g.istr[q]];
       }
       __syncthreads();
       for (int yy = ty; yy < 32; yy += 8) {
         int64_t qq = q0 + tx, pp = p0 + yy;
         if (pp < g.dims[p] && qq < g.dims[q]) {
-          z v = tile[tx][yy];
-          z* o = g.out + ob + pp * g.ostr[p] + qq * g.ostr[q];
-          *o = g.beta != 0.0 ? zaxpby(g.alpha, v, g.beta, *o) : zmul(g.alpha, v);
+          perm_put(g.out + ob + pp * g.ostr[p] + qq * g.ostr[q], tile[tx][yy], g.mode, g.sx, g.sy, g.alpha, g.beta,
+                   g.conj);
         }
       }
       __syncthreads();
@@ -201,36 +210,49 @@ __global__ void pack_pairs_kernel(const z* __restrict__ in, z* __restrict__ out,
   }
 }
 
-__global__ void unpack_pairs_kernel(UnpackArgs g) {
-  const int64_t P2 = pair_count(g.n2);
-  const int64_t R = g.unpack_rows ? g.n1 * g.n1 : g.n1;
-  const int64_t total = R * g.n2 * g.n2;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = e % g.n2, a = (e / g.n2) % g.n2, r = e / (g.n2 * g.n2);
-    double sgn = 1.0;
-    int64_t prow = r;
+// IT: the index type, 32-bit when every index is below 2^31 (the divisions by n1 and n2 are the
+// kernel's main cost otherwise). With real alpha = +-1 and beta 0 or 1 the value is moved by sign
+// flips and at most one add per part (no FP64 products on this chip's narrow FP64 pipe).
+template <typename IT>
+__global__ void unpack_pairs_kernel(UnpackArgs g, int unit) {
+  const IT n1 = (IT)g.n1, n2 = (IT)g.n2, anti = (IT)g.anti_rows;
+  const IT P2 = (IT)pair_count(g.n2);
+  const IT R = g.unpack_rows ? n1 * n1 : n1;
+  const IT total = R * n2 * n2;
+  for (IT e = (IT)blockIdx.x * (IT)blockDim.x + (IT)threadIdx.x; e < total; e += (IT)gridDim.x * (IT)blockDim.x) {
+    const IT ab = e % (n2 * n2), r = e / (n2 * n2);
+    const IT b = ab % n2, a = ab / n2;
+    bool neg = false;
+    IT prow = r;
     bool zero = (a == b);
     if (g.unpack_rows) {
-      const int64_t x = r / g.n1, y = r % g.n1;
+      const IT x = r / n1, y = r % n1;
       if (x == y) zero = true;
-      else if (x < y) prow = pair_index(x, y, g.n1);
-      else { prow = pair_index(y, x, g.n1); sgn = -sgn; }
+      else if (x < y) prow = (IT)pair_index(x, y, g.n1);
+      else { prow = (IT)pair_index(y, x, g.n1); neg = !neg; }
     }
     z val = make_double2(0.0, 0.0);
     if (!zero) {
-      int64_t pc;
-      if (a < b) pc = pair_index(a, b, g.n2);
-      else { pc = pair_index(b, a, g.n2); sgn = -sgn; }
+      IT pc;
+      if (a < b) pc = (IT)pair_index(a, b, g.n2);
+      else { pc = (IT)pair_index(b, a, g.n2); neg = !neg; }
       z x = g.in[prow * P2 + pc];
-      if (g.anti_rows > 0) {  // rows r = (x, y): in[(x, y)] - in[(y, x)]
-        const int64_t rx = r / g.anti_rows, ry = r % g.anti_rows;
-        x = zsub(x, g.in[(ry * g.anti_rows + rx) * P2 + pc]);
+      if (anti > 0) {  // rows r = (x, y): in[(x, y)] - in[(y, x)]
+        const IT rx = r / anti, ry = r % anti;
+        x = zsub(x, g.in[(ry * anti + rx) * P2 + pc]);
       }
-      val = zscale(sgn, zmul(g.alpha, x));
+      if (unit) {
+        const long long m = (neg != (g.alpha.x < 0.0)) ? (long long)0x8000000000000000ull : 0ll;
+        val = make_double2(__longlong_as_double(__double_as_longlong(x.x) ^ m),
+                           __longlong_as_double(__double_as_longlong(x.y) ^ m));
+      } else {
+        val = zscale(neg ? -1.0 : 1.0, zmul(g.alpha, x));
+      }
     }
     z* op = g.out + e;
-    *op = g.beta != 0.0 ? make_double2(g.beta * op->x + val.x, g.beta * op->y + val.y) : val;
+    if (g.beta == 0.0) *op = val;
+    else if (unit && g.beta == 1.0) *op = make_double2(op->x + val.x, op->y + val.y);
+    else *op = make_double2(g.beta * op->x + val.x, g.beta * op->y + val.y);
   }
 }
 
@@ -713,6 +735,13 @@ cudaError_t permute_add(const PermuteArgs& a0, cudaStream_t s) {
     a.dims[0] = 1;
     a.istr[0] = a.ostr[0] = 1;
   }
+  {
+    constexpr unsigned long long kSign = 0x8000000000000000ull;
+    const bool unit = a.alpha.y == 0.0 && (a.alpha.x == 1.0 || a.alpha.x == -1.0);
+    a.mode = unit && a.beta == 0.0 ? 1 : unit && a.beta == 1.0 ? 2 : 0;
+    a.sx = a.alpha.x < 0.0 ? kSign : 0ull;
+    a.sy = a.sx ^ (a.conj ? kSign : 0ull);
+  }
   int64_t total = 1, imax = 0, omax = 0;
   for (int d = 0; d < a.rank; ++d) {
     total *= a.dims[d];
@@ -739,6 +768,9 @@ cudaError_t permute_add(const PermuteArgs& a0, cudaStream_t s) {
       f.alpha = a.alpha;
       f.beta = a.beta;
       f.conj = a.conj;
+      f.mode = a.mode;
+      f.sx = a.sx;
+      f.sy = a.sy;
       permute_fast_kernel<<<grid_for((total + 127) / 128 * 32, kThreads), kThreads, 0, s>>>(f, (uint32_t)total);
     } else {
       permute_direct_kernel<<<grid_for(total, kThreads), kThreads, 0, s>>>(a, total);
@@ -772,7 +804,11 @@ cudaError_t pack_pairs(const z* in, z* out, int64_t n1, int64_t n2, int pack_row
 cudaError_t unpack_pairs(const UnpackArgs& a, cudaStream_t s) {
   const int64_t total = (a.unpack_rows ? a.n1 * a.n1 : a.n1) * a.n2 * a.n2;
   if (total == 0) return cudaSuccess;
-  unpack_pairs_kernel<<<grid_for(total, kThreads), kThreads, 0, s>>>(a);
+  const int unit = a.alpha.y == 0.0 && (a.alpha.x == 1.0 || a.alpha.x == -1.0);
+  if (total < ((int64_t)1 << 31) && a.n1 * a.n1 < ((int64_t)1 << 31))
+    unpack_pairs_kernel<uint32_t><<<grid_for(total, kThreads), kThreads, 0, s>>>(a, unit);
+  else
+    unpack_pairs_kernel<int64_t><<<grid_for(total, kThreads), kThreads, 0, s>>>(a, unit);
   return cudaGetLastError();
 }
 
