@@ -202,7 +202,8 @@ ccsd_status ccsd_iterate(ccsd_ctx* ctx, int max_iter, int* iters_done, double* r
  */
 int ccsd_divergence_index(const double* norms, int count, int iters, double factor);
 
-/* Energy of the current amplitudes: sum_ia f_ia t^a_i + 1/4 sum <ij||ab> tau^{ab}_{ij}. */
+/* Energy of the current amplitudes: sum_ia f_ia t^a_i + 1/4 sum <ij||ab> tau^{ab}_{ij}, the second
+ * sum taken once over the unique i < j, a < b (t2 is antisymmetric in (i,j) and in (a,b)). */
 ccsd_status ccsd_energy(ccsd_ctx* ctx, ccsd_z* e);
 
 /*
@@ -272,7 +273,9 @@ ccsd_status ccsd_lambda_iterate(ccsd_ctx* ctx, int max_iter, int* iters_done, do
 ccsd_status ccsd_get_lambda(ccsd_ctx* ctx, ccsd_z* l1, ccsd_z* l2, int on_device);
 ccsd_status ccsd_density(ccsd_ctx* ctx, ccsd_z* gamma, int symmetrize);
 
-/* Copy the current amplitudes out / in (checkpoint and resume). Setting resets DIIS. */
+/* Copy the current amplitudes out / in (checkpoint and resume). Setting resets DIIS. t2 must be
+ * antisymmetric in (i,j) and in (a,b): the packed contractions and the energy read its unique
+ * elements. */
 ccsd_status ccsd_get_amplitudes(ccsd_ctx* ctx, ccsd_z* t1, ccsd_z* t2, int on_device);
 ccsd_status ccsd_set_amplitudes(ccsd_ctx* ctx, const ccsd_z* t1, const ccsd_z* t2, int on_device);
 

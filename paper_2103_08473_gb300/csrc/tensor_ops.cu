@@ -460,23 +460,26 @@ __global__ void norm_finalize_kernel(const double* partials, int nb, double* sta
 
 // ---- energy ----------------------------------------------------------------
 
+// E = sum f_ia t_ia + 1/4 sum <ij||ab> tau_ij^ab. Both factors of the second sum are
+// antisymmetric in (i, j) and in (a, b), so each unique term i < j, a < b appears four times
+// with the same product: the kernel sums the unique terms once (a quarter of the FP64 work,
+// this chip's narrow pipe), over 32-bit indices (IT) where they fit.
+template <typename IT>
 __global__ void energy_kernel(const z* __restrict__ fov, const z* __restrict__ oovv, const z* __restrict__ t1,
                               const z* __restrict__ t2, int o, int v, z* partials) {
   __shared__ double sh[32];
-  const int64_t n1 = (int64_t)o * v, n2 = (int64_t)o * o * v * v;
+  const IT n1 = (IT)o * v, vv = (IT)v * v, n2 = (IT)o * o * vv;
   double er = 0.0, ei = 0.0;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n1 + n2;
-       k += (int64_t)gridDim.x * blockDim.x) {
+  for (IT k = (IT)blockIdx.x * blockDim.x + threadIdx.x; k < n1 + n2; k += (IT)gridDim.x * blockDim.x) {
     z p;
     if (k < n1) {
       p = zmul(fov[k], t1[k]);
     } else {
-      const int64_t q = k - n1;
-      const int b = (int)(q % v), a = (int)((q / v) % v);
-      const int j = (int)((q / ((int64_t)v * v)) % o), i = (int)(q / ((int64_t)v * v * o));
-      z tau = zadd(t2[q], zsub(zmul(t1[(int64_t)i * v + a], t1[(int64_t)j * v + b]),
-                               zmul(t1[(int64_t)j * v + a], t1[(int64_t)i * v + b])));
-      p = zscale(0.25, zmul(oovv[q], tau));
+      const IT q = k - n1, ab = q % vv, ij = q / vv;
+      const IT b = ab % (IT)v, a = ab / (IT)v, j = ij % (IT)o, i = ij / (IT)o;
+      if (i >= j || a >= b) continue;
+      const z tau = zadd(t2[q], zsub(zmul(t1[i * v + a], t1[j * v + b]), zmul(t1[j * v + a], t1[i * v + b])));
+      p = zmul(oovv[q], tau);
     }
     er += p.x;
     ei += p.y;
@@ -872,7 +875,11 @@ int energy_blocks() { return kEnergyBlocks; }
 
 cudaError_t energy_eval(const z* fov, const z* oovv, const z* t1, const z* t2, int o, int v, z* partials,
                         z* e_out, cudaStream_t s) {
-  energy_kernel<<<kEnergyBlocks, kThreads, 0, s>>>(fov, oovv, t1, t2, o, v, partials);
+  const int64_t n = (int64_t)o * v + (int64_t)o * o * v * v;
+  if (n < ((int64_t)1 << 31))
+    energy_kernel<uint32_t><<<kEnergyBlocks, kThreads, 0, s>>>(fov, oovv, t1, t2, o, v, partials);
+  else
+    energy_kernel<int64_t><<<kEnergyBlocks, kThreads, 0, s>>>(fov, oovv, t1, t2, o, v, partials);
   energy_finalize_kernel<<<1, 1024, 0, s>>>(partials, kEnergyBlocks, e_out);
   return cudaGetLastError();
 }

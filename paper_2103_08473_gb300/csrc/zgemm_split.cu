@@ -1237,8 +1237,9 @@ bool smallk_eligible(const SplitArgs& a) {
 // about two CTAs per SM (a 20 x 20 output with a long K runs on every SM, not on a few);
 // from there, or from no split with one to four waves of tiles, the factor that best fills
 // whole waves (CTAs / (waves x SMs)) is taken where it beats the smaller factors by more
-// than 5%. Each split keeps >= kMinKbPerSplit K blocks so that a level group's MMA work
-// stays above its FP64 flush in the epilogue.
+// than 5%. Each split keeps >= kMinKbPerSplit K blocks (half that for outputs of fewer than 16
+// tiles, whose long K is the whole of their work: the skinny products over o^2 v or o v^2)
+// so that a level group's MMA work stays above its FP64 flush in the epilogue.
 #ifndef SPLIT_MIN_KB_PER_SPLIT
 #define SPLIT_MIN_KB_PER_SPLIT 12
 #endif
@@ -1246,7 +1247,8 @@ constexpr int kMinKbPerSplit = SPLIT_MIN_KB_PER_SPLIT;
 void plan_ksplit(int64_t tiles, int kblocks, int& ksplits, int& kb_split, int64_t slots) {
   ksplits = 1;
   const int64_t sms = slots;
-  const int64_t kmax = std::max(1, kblocks / kMinKbPerSplit);
+  const int kb_min = tiles < 16 ? std::max(1, kMinKbPerSplit / 2) : kMinKbPerSplit;
+  const int64_t kmax = std::max(1, kblocks / kb_min);
   auto fill = [&](int64_t ctas) { return (double)ctas / (double)(((ctas + sms - 1) / sms) * sms); };
   if (tiles > 0 && tiles < 4 * sms) {
     const int64_t lo = tiles < sms ? std::min<int64_t>((2 * sms + tiles - 1) / tiles, kmax) : 1;
