@@ -20,6 +20,10 @@
 //           fixed), then release the TMEM set. With the operands swapped (a short M
 //           on the BN side) the tile is the transpose of C's and each warp adds into
 //           32 consecutive elements of a row of C.
+// Where the output is two or four BN tiles wide, pairs of CTAs with the same M tile and K
+// range run as clusters of two that multicast the shared 128-row tile (see CL below);
+// outputs with many tiles both ways take them in bands of M tiles so that a wave shares
+// a few A and B tiles in L2.
 // Every mbarrier wait is bounded (clock64 budget); a wait that gives up sets the
 // error word and the CTA drains its in-flight copies, frees TMEM and exits.
 #include <cuda_bf16.h>
