@@ -18,6 +18,7 @@ import pytest
 from oracle import brute_force as BF
 from oracle import ccsd_ref as R
 from oracle import lambda_ref as L
+import lambda_adjoint as LA
 from paper_2103_08473_gb300 import inputs
 
 
@@ -111,7 +112,7 @@ def test_explicit_adjoint_equals_the_derivative(o, v, naux, seed):
     t1, t2 = inputs.random_amplitudes(o, v, seed + 600, scale=0.3)
     l1, l2 = inputs.random_amplitudes(o, v, seed + 700, scale=0.3)
     R1, R2 = L.lagrangian_gradient(f, V, t1, t2, l1, l2)
-    E1, E2 = L.lagrangian_gradient_explicit(f, V, t1, t2, l1, l2)
+    E1, E2 = LA.lagrangian_gradient_explicit(f, V, t1, t2, l1, l2)
     scale = max(np.max(np.abs(R2)), 1.0)
     assert np.max(np.abs(E1 - R1)) < 1e-12 * scale
     assert np.max(np.abs(E2 - R2)) < 1e-12 * scale
