@@ -162,3 +162,32 @@ def test_divergence_rule_on_synthetic_norm_sequences(lib):
     assert ccsd.divergence_index([], iters=8) == 0
     assert ccsd.divergence_index([1.0, 2.0, float("nan"), 1e9], iters=1, factor=1.0) == 2
     assert lib.ccsd_divergence_index(None, 3, 8, 1e3) == -1
+
+
+def test_gemm_entry_points_refuse_bad_arguments_before_device_work(lib):
+    """ccsd_zgemm, ccsd_zgemm_noalloc and ccsd_split_zgemm check sizes, pointers, the tile shape,
+    the precision and (no-alloc) the static scratch limit on the host and return a status with a
+    message; none of these calls reaches the device."""
+    from paper_2103_08473_gb300 import ccsd
+    z = ccsd.ccsd_z
+    one, zero = z(1.0, 0.0), z(0.0, 0.0)
+    p = C.c_void_p(16)  # never dereferenced: every call below is refused first
+    # ccsd_zgemm: negative size, NULL operand, tile shape out of range, precision not built
+    assert lib.ccsd_zgemm(0, 0, 0, 0, 0, -1, 4, 4, one, p, 4, p, 4, zero, p, 4, None, 0, 0, None) == ccsd.ERR_ARG
+    assert lib.ccsd_zgemm(0, 0, 0, 0, 0, 4, 4, 4, one, None, 4, p, 4, zero, p, 4, None, 0, 0, None) == ccsd.ERR_ARG
+    assert lib.ccsd_zgemm(0, 0, 0, 0, 0, 4, 4, 4, one, p, 4, p, 4, zero, p, 4, None, 0, 7, None) == ccsd.ERR_ARG
+    assert lib.ccsd_zgemm(1, 0, 0, 0, 0, 4, 4, 4, one, p, 4, p, 4, zero, p, 4, None, 0, 0, None) == ccsd.ERR_UNSUPPORTED
+    # ccsd_zgemm_noalloc: the same checks, and an output beyond the static scratch (M*N <= 2^17)
+    assert lib.ccsd_zgemm_noalloc(0, 0, 0, 0, 0, 4, 4, -1, one, p, 4, p, 4, zero, p, 4, 0, None) == ccsd.ERR_ARG
+    assert lib.ccsd_zgemm_noalloc(0, 0, 0, 0, 0, 4, 4, 4, one, p, 4, p, 4, zero, None, 4, 0, None) == ccsd.ERR_ARG
+    assert lib.ccsd_zgemm_noalloc(1, 0, 0, 0, 0, 4, 4, 4, one, p, 4, p, 4, zero, p, 4, 0, None) == ccsd.ERR_UNSUPPORTED
+    big = 1 << 9  # 512 x 512 = 2^18 > 2^17
+    assert lib.ccsd_zgemm_noalloc(0, 0, 0, 0, 0, big, big, 4, one, p, 4, p, 4, zero, p, big, 0, None) == ccsd.ERR_ARG
+    assert "exceeds the limit" in lib.ccsd_last_error(None).decode()
+    # ccsd_split_zgemm: digit configuration, sizes, workspace
+    assert lib.ccsd_split_zgemm(0, 6, 8, 0, 0, 0, 0, 4, 4, 4, one, p, 4, p, 4, zero, p, 4, p, 1 << 30, None) == ccsd.ERR_ARG
+    assert lib.ccsd_split_zgemm(0, 5, 8, 0, 0, 0, 0, 4, 4, 0, one, p, 4, p, 4, zero, p, 4, p, 1 << 30, None) == ccsd.ERR_ARG
+    need = lib.ccsd_split_workspace(0, 5, 8, 4, 4, 4)
+    assert need > 0
+    assert lib.ccsd_split_zgemm(0, 5, 8, 0, 0, 0, 0, 4, 4, 4, one, p, 4, p, 4, zero, p, 4, p, need - 1, None) == ccsd.ERR_ARG
+    assert "workspace needs" in lib.ccsd_last_error(None).decode()
