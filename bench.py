@@ -58,6 +58,17 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+def split_ladder_frac(lad_ms, o: int, v: int, slices: int):
+    """Fraction of the e4m3 peak (2 x the measured bf16 burst rate) reached by a split ladder launch
+    of lad_ms ms: s(s+1)/2 digit pairs x 8 P(o) P(v)^2 e4m3 flops (packed pairs, stored <ab||cd>)."""
+    if not lad_ms:
+        return None
+    from paper_2103_08473_gb300 import flops
+    peaks, _ = load_peaks()
+    fl = slices * (slices + 1) // 2 * 8.0 * float(flops.pairs(o)) * float(flops.pairs(v)) ** 2
+    return fl / (lad_ms * 1e-3) / 1e12 / (peaks["bf16_tflops"] * 2.0)
+
+
 def recorded_traffic(kernel_file: str, key: str):
     """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
     prof = os.path.join(ROOT, "profiles", "traffic.txt")
@@ -386,6 +397,8 @@ def run_ours(args, wl):
                                                           np.max(np.abs(t_split[1] - t_main[1])))),
                      "iterations_compared": args.warmup + args.steps,
                      "ladder_ms": opd2.get("ladder:gemm"),
+                     "ladder_e4m3_frac": (split_ladder_frac(opd2.get("ladder:gemm"), o, v, slices)
+                                          if args.method == "ccsd" and wl.get("store_w", True) else None),
                      "top_ops_ms": {k: round(t, 4) for k, t in sorted(opd2.items(), key=lambda kv: -kv[1])[:10]}}
 
     # opt-in: both precisions from the MP2 guess for the same number of iterations on fresh

@@ -27,3 +27,14 @@ def test_triples_cpu_baseline_helper():
     import bench
     est, sample = bench.oracle_triples_time(dict(bench.WORKLOADS["o10v30"]))
     assert est > 0.0 and "extrapolated" in sample
+
+
+def test_split_ladder_fraction_counts_packed_digit_pair_flops(monkeypatch):
+    """The e4m3 fraction of a split ladder launch: s(s+1)/2 digit pairs x 8 P(o) P(v)^2 flops over
+    the launch time, against twice the measured bf16 burst rate."""
+    import bench
+    monkeypatch.setattr(bench, "load_peaks", lambda: ({"bf16_tflops": 1000.0}, "measured"))
+    o, v, s, ms = 20, 120, 8, 2.0
+    flops = 36 * 8.0 * (20 * 19 // 2) * (120 * 119 // 2) ** 2
+    assert abs(bench.split_ladder_frac(ms, o, v, s) - flops / 2e-3 / 1e12 / 2000.0) < 1e-12
+    assert bench.split_ladder_frac(None, o, v, s) is None
