@@ -349,7 +349,9 @@ ccsd_status ccsd_zgemm(int precision, int transA, int conjA, int transB, int con
  * in FP64. A K of at most 4 blocks (512 e4m3, 256 bf16 elements) with at most 8 digits
  * runs on a second kernel that keeps every weight in tensor memory and writes each output
  * once. Error ~ 2^(-bits*slices) relative to the row/column scales (2^(1-bits*slices)
- * with headroom).
+ * with headroom). Results are bit-reproducible run to run (every output element has one
+ * owning thread; K-split partials are summed in a fixed order). ccsd_split_describe
+ * reports how a shape is scheduled.
  * workspace: device memory of at least ccsd_split_workspace(...) bytes. Synchronous on
  * `stream`. CCSD_ERR_TIMEOUT if a bounded device wait gave up.
  */
