@@ -49,3 +49,11 @@ def test_describe_rejects_bad_configurations(lib):
         M, N, K, kind, bits, slices = args
         with pytest.raises(ccsd.CCSDError):
             ccsd.split_describe(M, N, K, kind=kind, bits=bits, slices=slices)
+
+
+def test_skinny_long_k_products_split_k_across_the_gpu(lib):
+    # H^k_i at o20/v120: a 20 x 20 output over K = 288000 (2250 blocks of 128 digits). One output
+    # tile: K is split so that the CTAs cover the GPU, each split keeping >= 6 K blocks.
+    d = ccsd.split_describe(20, 20, 288000)
+    assert d["short_k"] == 0 and d["tiles"] == 1
+    assert 100 <= d["ksplits"] <= 2250 // 6
